@@ -1,0 +1,40 @@
+/*
+ * pic_oracle.h -- API of the FP64 CPU oracle (test infrastructure only).
+ * Private to oracle/: the CUDA path neither includes nor links it.
+ */
+#ifndef PIC_ORACLE_H
+#define PIC_ORACLE_H
+
+#include <stdint.h>
+
+#define OR_MAX_SPECIES 8
+
+typedef struct osim osim;
+
+osim *or_create(int dim, const long *n, const double *dx, const int *bc, double dt,
+                double rho_bg, int sort_interval, const int *tile);
+void or_destroy(osim *s);
+int or_add_species(osim *s, double q, double m, double w, long cap);
+int or_load(osim *s, int isp, long n, const double *x, const double *y, const double *z,
+            const double *ux, const double *uy, const double *uz);
+int or_get_field(const osim *s, int c, double *out);
+int or_set_field(osim *s, int c, const double *in);
+int or_get_ghost(const osim *s, int c, long i, long j, long k, double *v);
+void or_set_laser(osim *s, int pol, double a0, double waist, double fwhm, double t_peak,
+                  double x_focus, double yc, double zc);
+void or_weights2(double delta, double *w);
+void or_gather(const osim *s, const double *x, double *eb);
+void or_boris(double qm, double dt, const double *E, const double *B, double *u);
+void or_deposit_one(osim *s, const double *x0, const double *x1, const double *v, double qw);
+long or_sort_species(osim *s, int isp, long *perm_out);
+int or_step(osim *s, long nsteps);
+long or_get_particles(const osim *s, int isp, double *x, double *y, double *z, double *ux,
+                      double *uy, double *uz, unsigned char *alive);
+int or_get_rho(const osim *s, double *rho);
+int or_diagnostics(const osim *s, double *out);
+long or_step_count(const osim *s);
+
+void or_philox4x32_10(const uint32_t *ctr, const uint32_t *key, uint32_t *out);
+double or_uniform24(uint32_t x);
+
+#endif

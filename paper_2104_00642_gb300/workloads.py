@@ -1,0 +1,204 @@
+"""Seeded synthetic inputs shaped like the paper's laser-plasma runs.
+
+This module holds no arithmetic of the PIC method itself: it only draws
+particle positions and momenta and derives grid sizes and weights from the
+workload description.  Both the CUDA path (tests, bench) and the CPU oracle
+read their inputs from here, so that they start from identical FP64 states.
+
+All quantities are in the normalised units of Eq. (8) of Song, Wang & Li
+(arXiv:2104.00642, Sec. II.A): c = m_e = e = 1, time in 1/omega_r, length in
+c/omega_r, density in n_r.  Workloads:
+
+* ``langmuir_1d``: cold Langmuir oscillation, 1D periodic, quiet start, fixed
+  ion background (omega_r = omega_p).
+* ``laser_foil_2d``: hydrogen slab hit by a linearly polarised Gaussian laser
+  entering from x-min; absorbing x, periodic y (omega_r = omega_L).
+* ``thermal_3d``: uniform Maxwellian electrons on a neutralising background,
+  3D periodic (omega_r = omega_p).
+"""
+from __future__ import annotations
+
+import math
+from dataclasses import dataclass, field
+
+import numpy as np
+
+PERIODIC, ABSORB = 0, 1
+M_PROTON = 1836.15267343
+MEC2_KEV = 510.99895
+SEED0 = 20210401
+
+
+@dataclass
+class Species:
+    name: str
+    q: float
+    m: float
+    w: float
+    x: np.ndarray
+    y: np.ndarray
+    z: np.ndarray
+    ux: np.ndarray
+    uy: np.ndarray
+    uz: np.ndarray
+    capacity: int = 0
+
+    @property
+    def n(self) -> int:
+        return int(self.ux.shape[0])
+
+
+@dataclass
+class Laser:
+    a0: float
+    waist: float
+    fwhm: float
+    t_peak: float
+    x_focus: float
+    yc: float = 0.0
+    zc: float = 0.0
+    pol: int = 0  # 0 linear along y, 1 circular
+
+
+@dataclass
+class Workload:
+    name: str
+    dim: int
+    n: tuple
+    dx: tuple
+    dt: float
+    bc: tuple
+    species: list
+    steps: int
+    rho_bg: float = 0.0
+    laser: Laser | None = None
+    tile: tuple = (8, 8, 8)
+    notes: dict = field(default_factory=dict)
+
+    @property
+    def n_particles(self) -> int:
+        return sum(s.n for s in self.species)
+
+    @property
+    def n_cells(self) -> int:
+        return int(np.prod(self.n[: self.dim]))
+
+
+def _rng(seed):
+    return np.random.Generator(np.random.Philox(seed))
+
+
+def maxwell_juttner_u(rng, n, theta):
+    """|u| drawn from u^2 exp(-(gamma-1)/theta) by inverse CDF on a fine grid,
+    with isotropic direction (input generation only)."""
+    umax = math.sqrt((1.0 + 60.0 * theta) ** 2 - 1.0)
+    ug = np.linspace(0.0, umax, 200001)
+    g = np.sqrt(1.0 + ug * ug)
+    pdf = ug * ug * np.exp(-(g - 1.0) / theta)
+    cdf = np.concatenate([[0.0], np.cumsum(0.5 * (pdf[1:] + pdf[:-1]) * np.diff(ug))])
+    cdf /= cdf[-1]
+    umag = np.interp(rng.random(n), cdf, ug)
+    ct = rng.uniform(-1.0, 1.0, n)
+    ph = rng.uniform(0.0, 2.0 * math.pi, n)
+    st = np.sqrt(1.0 - ct * ct)
+    return umag * st * np.cos(ph), umag * st * np.sin(ph), umag * ct
+
+
+def langmuir_1d(n_cells=256, dx=0.05, ppc=100, amp=0.01, steps=1000, courant=0.95):
+    """Cold Langmuir oscillation: quiet start x = (i + (k+1/2)/ppc) dx,
+    u_x = amp sin(2 pi x / L), electrons of density 1 on an ion background."""
+    L = n_cells * dx
+    i = np.repeat(np.arange(n_cells), ppc)
+    k = np.tile(np.arange(ppc), n_cells)
+    x = (i + (k + 0.5) / ppc) * dx
+    ux = amp * np.sin(2.0 * math.pi * x / L)
+    z0 = np.zeros_like(x)
+    e = Species("electron", -1.0, 1.0, 1.0 / ppc, x, z0.copy(), z0.copy(), ux, z0.copy(), z0.copy(),
+                capacity=x.size)
+    return Workload("langmuir_1d", 1, (n_cells, 1, 1), (dx, 1.0, 1.0), courant * dx,
+                    (PERIODIC, PERIODIC, PERIODIC), [e], steps, rho_bg=1.0, tile=(16, 1, 1),
+                    notes={"L": L, "k": 2.0 * math.pi / L, "amp": amp})
+
+
+def thermal_3d(n=(256, 256, 256), dx=0.1, ppc=8, T_keV=10.0, steps=200, courant=0.95,
+               seed=SEED0 + 3, tile=(8, 8, 8)):
+    """Uniform Maxwellian electrons (u_i ~ N(0, T/mc^2)) at Philox-uniform
+    positions on a neutralising background, periodic in all axes."""
+    rng = _rng(seed)
+    nc = int(np.prod(n))
+    N = nc * ppc
+    theta = T_keV / MEC2_KEV
+    x = rng.random(N) * (n[0] * dx)
+    y = rng.random(N) * (n[1] * dx)
+    z = rng.random(N) * (n[2] * dx)
+    s = math.sqrt(theta)
+    ux, uy, uz = (rng.standard_normal(N) * s for _ in range(3))
+    e = Species("electron", -1.0, 1.0, 1.0 / ppc, x, y, z, ux, uy, uz, capacity=N)
+    dt = courant * dx / math.sqrt(3.0)
+    return Workload("thermal_3d", 3, tuple(n), (dx, dx, dx), dt, (PERIODIC,) * 3, [e], steps,
+                    rho_bg=1.0, tile=tile, notes={"theta": theta, "ppc": ppc})
+
+
+def thermal_2d(n=(256, 256), dx=0.1, ppc=16, T_keV=10.0, steps=100, courant=0.95, seed=SEED0 + 6,
+               tile=(16, 16, 1)):
+    """2D3V version of ``thermal_3d`` (small parity case)."""
+    rng = _rng(seed)
+    nc = n[0] * n[1]
+    N = nc * ppc
+    theta = T_keV / MEC2_KEV
+    x = rng.random(N) * (n[0] * dx)
+    y = rng.random(N) * (n[1] * dx)
+    s = math.sqrt(theta)
+    ux, uy, uz = (rng.standard_normal(N) * s for _ in range(3))
+    e = Species("electron", -1.0, 1.0, 1.0 / ppc, x, y, np.zeros(N), ux, uy, uz, capacity=N)
+    dt = courant * dx / math.sqrt(2.0)
+    return Workload("thermal_2d", 2, (n[0], n[1], 1), (dx, dx, 1.0), dt, (PERIODIC,) * 3, [e], steps,
+                    rho_bg=1.0, tile=tile, notes={"theta": theta, "ppc": ppc})
+
+
+def laser_foil_2d(nx=2048, ny=1024, cells_per_lambda=64, slab=(1024, 1088), n0=10.0, ppc=32,
+                  T_keV=1.0, a0=20.0, waist_um=3.0, fwhm_fs=30.0, steps=4000, courant=0.95,
+                  seed=SEED0 + 2, tile=(16, 16, 1), x_focus_cell=None):
+    """Hydrogen slab n0 n_c over x-cells [slab), all y, ppc electrons and ppc
+    protons per cell (Maxwell-Juttner), LP Gaussian laser from x-min.
+    Lengths: lambda = 1 um = 2 pi c/omega_L."""
+    rng = _rng(seed)
+    dx = 2.0 * math.pi / cells_per_lambda
+    dt = courant * dx / math.sqrt(2.0)
+    theta = T_keV / MEC2_KEV
+    sx0, sx1 = slab
+    ncell = (sx1 - sx0) * ny
+    N = ncell * ppc
+    ci = np.repeat(np.arange(ncell), ppc)
+    cx = sx0 + ci % (sx1 - sx0)
+    cy = ci // (sx1 - sx0)
+    species = []
+    for name, q, m in (("electron", -1.0, 1.0), ("proton", 1.0, M_PROTON)):
+        x = (cx + rng.random(N)) * dx
+        y = (cy + rng.random(N)) * dx
+        ux, uy, uz = maxwell_juttner_u(rng, N, theta / m)
+        species.append(Species(name, q, m, n0 / ppc, x, y, np.zeros(N), ux, uy, uz, capacity=N))
+    omega_L = 2.0 * math.pi * 2.99792458e8 / 1.0e-6
+    fwhm = fwhm_fs * 1e-15 * omega_L
+    waist = waist_um * 2.0 * math.pi
+    xf = (sx0 if x_focus_cell is None else x_focus_cell) * dx
+    laser = Laser(a0=a0, waist=waist, fwhm=fwhm, t_peak=2.5 * fwhm, x_focus=xf, yc=0.5 * ny * dx)
+    return Workload("laser_foil_2d", 2, (nx, ny, 1), (dx, dx, 1.0), dt, (ABSORB, PERIODIC, PERIODIC),
+                    species, steps, laser=laser, tile=tile,
+                    notes={"theta": theta, "n0": n0, "ppc": ppc, "slab": slab})
+
+
+def vacuum_pulse_1d(n_cells=1024, cells_per_lambda=32, a0=1.0, fwhm=4.0 * 2.0 * math.pi, steps=1500,
+                    courant=0.95, pol=0):
+    """Laser pulse entering an empty 1D absorbing box (boundary tests)."""
+    dx = 2.0 * math.pi / cells_per_lambda
+    laser = Laser(a0=a0, waist=1.0, fwhm=fwhm, t_peak=2.5 * fwhm, x_focus=0.0, pol=pol)
+    return Workload("vacuum_pulse_1d", 1, (n_cells, 1, 1), (dx, 1.0, 1.0), courant * dx,
+                    (ABSORB, PERIODIC, PERIODIC), [], steps, laser=laser, tile=(16, 1, 1))
+
+
+def random_particles(rng, n, dim, L, umax=0.3):
+    """Uniform positions in [0, L_d) and uniform momenta in [-umax, umax]."""
+    x = [rng.random(n) * L[d] if d < dim else np.zeros(n) for d in range(3)]
+    u = [rng.uniform(-umax, umax, n) for _ in range(3)]
+    return x, u

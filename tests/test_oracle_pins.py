@@ -1,0 +1,445 @@
+"""Pins of the FP64 CPU oracle to what the paper and the mathematics fix.
+
+Every test here checks the oracle against something other than itself: the
+paper's definition integrated numerically, a closed form, an invariant, a
+published known-answer vector or a library routine.  No GPU is used.
+"""
+import math
+import os
+
+import numpy as np
+import pytest
+from scipy import integrate
+
+from oracle import oracle as O
+from paper_2104_00642_gb300 import workloads as W
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+
+
+# --------------------------------------------------------------------------
+# Shape weights: W_n(i - i_c) is the integral of S_n over cell i (Sec. II.D)
+# --------------------------------------------------------------------------
+
+def _S2(xi):
+    return max(0.0, 1.0 - abs(xi))  # Eq. (17), the hat
+
+
+@pytest.mark.parametrize("delta", np.linspace(-0.5, 0.4999, 23))
+def test_w2_is_cell_integral_of_hat(delta):
+    w = O.weights2(delta)
+    for m, wm in zip((-1, 0, 1), w):
+        ref, _ = integrate.quad(lambda xi: _S2(xi - delta), m - 0.5, m + 0.5,
+                                points=[delta - 1, delta, delta + 1], epsabs=1e-14)
+        assert abs(wm - ref) < 1e-13
+
+
+def test_w2_moments():
+    for delta in np.linspace(-0.5, 0.49, 50):
+        w = O.weights2(delta)
+        m = np.array([-1.0, 0.0, 1.0])
+        assert abs(w.sum() - 1.0) < 1e-15
+        assert abs(((m - delta) * w).sum()) < 1e-15
+        assert abs((((m - delta) ** 2) * w).sum() - 0.25) < 1e-15
+    assert np.array_equal(O.weights2(0.0), np.array([0.125, 0.75, 0.125]))
+
+
+# --------------------------------------------------------------------------
+# Philox4x32-10: published known-answer vectors
+# --------------------------------------------------------------------------
+
+def test_philox_known_answers():
+    rows = [ln.split() for ln in open(os.path.join(HERE, "golden", "philox4x32_10_kat.txt"))
+            if ln.strip() and not ln.startswith("#")]
+    assert len(rows) == 3
+    for r in rows:
+        v = [int(t, 16) for t in r]
+        out = O.philox4x32_10(v[0:4], v[4:6])
+        assert [int(t) for t in out] == v[6:10]
+
+
+def test_uniform24_exact_and_open():
+    assert O.uniform24(0) == 0.5 * 2.0 ** -24
+    assert O.uniform24(0xFFFFFFFF) == (2 ** 24 - 0.5) * 2.0 ** -24
+    assert 0.0 < O.uniform24(0x12345678) < 1.0
+
+
+# --------------------------------------------------------------------------
+# FDTD (Eqs. (9), (10)): discrete Yee dispersion, exact per mode
+# --------------------------------------------------------------------------
+
+def _phase(dt, dx, k):
+    s = dt * math.sqrt(sum((math.sin(kd * dd / 2) / dd) ** 2 for kd, dd in zip(k, dx)))
+    return 2.0 * math.asin(s)
+
+
+def test_yee_dispersion_1d():
+    n, dx = 64, 0.1
+    dt = 0.95 * dx
+    s = O.OracleSim(1, (n,), (dx,), dt)
+    k = 2 * math.pi * 3 / (n * dx)
+    x = np.arange(n) * dx
+    s.set_field(O.EY, np.sin(k * x)[None, None, :])
+    steps = 57
+    s.step(steps)
+    phi = _phase(dt, (dx,), (k,))
+    ref = np.sin(k * x) * math.cos(steps * phi)
+    assert np.max(np.abs(s.field(O.EY)[0, 0] - ref)) < 1e-13
+    # the continuum value would differ at first order: the pin is discriminating
+    assert np.max(np.abs(np.sin(k * x) * math.cos(steps * k * dt) - ref)) > 1e-4
+
+
+def test_yee_dispersion_2d_te():
+    n, dx = (32, 24), (0.1, 0.13)
+    dt = 0.9 / math.sqrt(1 / dx[0] ** 2 + 1 / dx[1] ** 2)
+    s = O.OracleSim(2, n, dx, dt)
+    k = (2 * math.pi * 2 / (n[0] * dx[0]), 2 * math.pi * 3 / (n[1] * dx[1]))
+    X, Y = np.meshgrid(np.arange(n[0]) * dx[0], np.arange(n[1]) * dx[1])
+    e0 = np.sin(k[0] * X + k[1] * Y)
+    s.set_field(O.EZ, e0[None])
+    steps = 40
+    s.step(steps)
+    ref = e0 * math.cos(steps * _phase(dt, dx, k))
+    assert np.max(np.abs(s.field(O.EZ)[0] - ref)) < 1e-13
+
+
+def test_yee_dispersion_3d_oblique_and_divB():
+    n, dx = (16, 12, 10), (0.1, 0.12, 0.15)
+    dt = 0.95 / math.sqrt(sum(1 / d ** 2 for d in dx))
+    s = O.OracleSim(3, n, dx, dt)
+    m = (1, 2, 1)
+    k = [2 * math.pi * m[d] / (n[d] * dx[d]) for d in range(3)]
+    kap = np.array([2 / dx[d] * math.sin(k[d] * dx[d] / 2) for d in range(3)])
+    A = np.cross(kap, np.array([0.3, -0.7, 0.2]))
+    A /= np.linalg.norm(A)
+    Z, Y, X = np.meshgrid(np.arange(n[2]), np.arange(n[1]), np.arange(n[0]), indexing="ij")
+    init = []
+    for c in range(3):
+        r = [X * dx[0], Y * dx[1], Z * dx[2]]
+        r[c] = r[c] + 0.5 * dx[c]  # E_c sits half a cell along axis c
+        e = A[c] * np.sin(k[0] * r[0] + k[1] * r[1] + k[2] * r[2])
+        init.append(e)
+        s.set_field(O.EX + c, e)
+    steps = 30
+    s.step(steps)
+    cph = math.cos(steps * _phase(dt, dx, k))
+    for c in range(3):
+        assert np.max(np.abs(s.field(O.EX + c) - init[c] * cph)) < 1e-13
+    # div B on cell centres stays zero to round-off
+    B = [s.field(O.BX + c) for c in range(3)]
+    div = ((np.roll(B[0], -1, 2) - B[0]) / dx[0] + (np.roll(B[1], -1, 1) - B[1]) / dx[1]
+           + (np.roll(B[2], -1, 0) - B[2]) / dx[2])
+    assert np.max(np.abs(div)) < 1e-12 * max(1.0, max(np.abs(b).max() for b in B))
+    assert max(np.abs(b).max() for b in B) > 0.1
+
+
+# --------------------------------------------------------------------------
+# Boris pusher (Eqs. (13)-(16))
+# --------------------------------------------------------------------------
+
+def test_boris_pure_B_gamma_and_angle():
+    qm, dt = -1.0, 0.1
+    B = np.array([0.0, 0.0, 2.0])
+    u = np.array([0.5, 0.0, 0.3])
+    g = math.sqrt(1 + u @ u)
+    u1 = O.boris(qm, dt, np.zeros(3), B, u)
+    assert abs(math.sqrt(1 + u1 @ u1) - g) < 1e-15
+    ang = math.atan2(u1[1], u1[0]) - math.atan2(u[1], u[0])
+    theta = 2 * math.atan(abs(qm) * 2.0 * dt / (2 * g))
+    assert abs(abs(ang) - theta) < 1e-14
+    # electron in B_z gyrates counter-clockwise seen from +z: u_y > 0 after a step
+    assert u1[1] > 0
+    assert u1[2] == u[2]
+
+
+def test_boris_pure_E_linear():
+    qm, dt = -1.0, 0.05
+    E = np.array([0.2, -0.1, 0.05])
+    u = np.array([0.1, 0.0, 0.0])
+    u0 = u.copy()
+    for _ in range(100):
+        u = O.boris(qm, dt, E, np.zeros(3), u)
+    assert np.max(np.abs(u - (u0 + 100 * qm * E * dt))) < 1e-13
+
+
+def test_boris_gyro_radius_polygon():
+    qm, dt = 1.0, 0.2
+    B = np.array([0.0, 0.0, 1.5])
+    u = np.array([0.4, 0.0, 0.0])
+    g = math.sqrt(1 + u @ u)
+    theta = 2 * math.atan(qm * 1.5 * dt / (2 * g))
+    x = np.zeros(3)
+    pts = []
+    for _ in range(200):
+        u = O.boris(qm, dt, np.zeros(3), B, u)
+        x = x + dt * u / g
+        pts.append(x[:2].copy())
+    pts = np.array(pts)
+    c = pts.mean(axis=0)  # 200 steps are whole turns only approximately; fit instead
+    A = np.c_[2 * pts, np.ones(len(pts))]
+    sol = np.linalg.lstsq(A, (pts ** 2).sum(1), rcond=None)[0]
+    R = math.sqrt(sol[2] + sol[0] ** 2 + sol[1] ** 2)
+    vperp = 0.4 / g
+    assert abs(R - vperp * dt / (2 * math.sin(theta / 2))) < 1e-12
+    del c
+
+
+def test_boris_ExB_drift():
+    """From rest in crossed fields the orbit is a cycloid; between two cusps
+    (u = 0 again) the mean velocity is the E x B drift."""
+    qm, dt = -1.0, 0.01
+    B = np.array([0.0, 0.0, 1.0])
+    E = np.array([0.1, 0.0, 0.0])
+    u = np.zeros(3)
+    x = np.zeros(3)
+    speeds, xs = [], []
+    for _ in range(8000):
+        u = O.boris(qm, dt, E, B, u)
+        x = x + dt * u / math.sqrt(1 + u @ u)
+        speeds.append(math.sqrt(u @ u))
+        xs.append(x.copy())
+    speeds = np.array(speeds)
+    cusps = [i for i in range(1, len(speeds) - 1)
+             if speeds[i] < speeds[i - 1] and speeds[i] <= speeds[i + 1] and speeds[i] < 0.02]
+    i0, i1 = cusps[0], cusps[-1]
+    vd = (xs[i1] - xs[i0]) / ((i1 - i0) * dt)
+    ref = np.cross(E, B) / (B @ B)
+    assert len(cusps) >= 5
+    assert abs(vd[1] - ref[1]) < 1e-3 * abs(ref[1])
+    assert abs(vd[0]) < 1e-3 * abs(ref[1])
+
+
+# --------------------------------------------------------------------------
+# Esirkepov deposit (Eqs. (20)-(22)): continuity to round-off, path average
+# --------------------------------------------------------------------------
+
+def _w2_numeric(delta):
+    return np.array([integrate.quad(lambda xi: _S2(xi - delta), m - 0.5, m + 0.5,
+                                    points=[delta - 1, delta, delta + 1], epsabs=1e-15)[0]
+                     for m in (-1, 0, 1)])
+
+
+def _rho_nodes(x, n, dx, dim):
+    """density shape on nodes from the numerically integrated W_2"""
+    rho = np.zeros((n[2] if dim > 2 else 1, n[1] if dim > 1 else 1, n[0]))
+    ws, ics = [], []
+    for d in range(3):
+        if d < dim:
+            X = x[d] / dx[d]
+            ic = int(math.floor(X + 0.5))
+            ws.append(_w2_numeric(X - ic))
+            ics.append(ic)
+        else:
+            ws.append(np.array([0.0, 1.0, 0.0]))
+            ics.append(0)
+    for c in range(3):
+        for b in range(3):
+            for a in range(3):
+                w = ws[0][a] * ws[1][b] * ws[2][c]
+                if w == 0:
+                    continue
+                i = (ics[0] + a - 1) % n[0]
+                j = (ics[1] + b - 1) % n[1] if dim > 1 else 0
+                k = (ics[2] + c - 1) % n[2] if dim > 2 else 0
+                rho[k, j, i] += w
+    return rho
+
+
+@pytest.mark.parametrize("dim", [1, 2, 3])
+def test_esirkepov_continuity(dim):
+    rng = np.random.default_rng(11 + dim)
+    n = (12, 10, 9)
+    dx = (0.1, 0.15, 0.12)
+    dt = 0.07
+    s = O.OracleSim(dim, n[:dim], dx[:dim], dt)
+    for _ in range(25):
+        x0 = [rng.uniform(0, n[d] * dx[d]) if d < dim else 0.0 for d in range(3)]
+        dxy = [rng.uniform(-0.95, 0.95) * dx[d] if d < dim else 0.0 for d in range(3)]
+        x1 = [x0[d] + dxy[d] for d in range(3)]
+        v = rng.uniform(-0.5, 0.5, 3)
+        qw = -0.37
+        Jx, Jy, Jz = s.deposit_one(x0, x1, v, qw)
+        r0 = _rho_nodes(x0, n, dx, dim) * qw
+        r1 = _rho_nodes(x1, n, dx, dim) * qw
+        div = (Jx - np.roll(Jx, 1, 2)) / dx[0]
+        if dim > 1:
+            div += (Jy - np.roll(Jy, 1, 1)) / dx[1]
+        if dim > 2:
+            div += (Jz - np.roll(Jz, 1, 0)) / dx[2]
+        res = (r1 - r0) / dt + div
+        assert np.max(np.abs(res)) < 1e-12 * abs(qw) / dt
+        assert np.max(np.abs(Jx)) > 0
+
+
+@pytest.mark.parametrize("dim", [1, 2])
+def test_inactive_axis_current_is_time_average_of_shape(dim):
+    """Along an axis the grid does not resolve, Esirkepov's current is
+    q w v_d times the time average of the node shape, the shape of each node
+    taken linear in time between its values S0 (start) and S1 (end)."""
+    n = (12, 10)
+    dx = (0.1, 0.15)
+    dt = 0.07
+    s = O.OracleSim(dim, n[:dim], dx[:dim], dt)
+    x0 = [0.513, 0.77, 0.0]
+    x1 = [0.513 + 0.061, 0.77 - 0.093 if dim > 1 else 0.77, 0.0]
+    v = np.array([0.3, -0.2, 0.45])
+    qw = 0.8
+    Jx, Jy, Jz = s.deposit_one(x0, x1, v, qw)
+    S0 = _shape_1d(x0, n, dx, dim)
+    S1 = _shape_1d(x1, n, dx, dim)
+    t, wq = np.polynomial.legendre.leggauss(8)
+    t, wq = 0.5 * (t + 1), 0.5 * wq
+    avg = np.zeros_like(Jz)
+    for tt, ww in zip(t, wq):
+        sx = S0[0] + tt * (S1[0] - S0[0])
+        sy = S0[1] + tt * (S1[1] - S0[1]) if dim > 1 else np.ones(1)
+        avg[0] += ww * np.outer(sy, sx)
+    assert np.max(np.abs(Jz - qw * v[2] * avg)) < 1e-15
+    if dim == 1:
+        assert np.max(np.abs(Jy - qw * v[1] * avg)) < 1e-15
+
+
+def _shape_1d(x, n, dx, dim):
+    """per-axis node shapes from the numerically integrated W_2"""
+    out = []
+    for d in range(dim):
+        X = x[d] / dx[d]
+        ic = int(math.floor(X + 0.5))
+        w = _w2_numeric(X - ic)
+        a = np.zeros(n[d])
+        for m in range(3):
+            a[(ic + m - 1) % n[d]] += w[m]
+        out.append(a)
+    return out
+
+
+def test_particle_at_rest_deposits_nothing():
+    s = O.OracleSim(3, (8, 8, 8), (0.1, 0.1, 0.1), 0.05)
+    Jx, Jy, Jz = s.deposit_one([0.33, 0.41, 0.27], [0.33, 0.41, 0.27], [0, 0, 0], 1.0)
+    assert not Jx.any() and not Jy.any() and not Jz.any()
+
+
+# --------------------------------------------------------------------------
+# Stable counting sort by tile = numpy stable argsort
+# --------------------------------------------------------------------------
+
+def test_sort_matches_numpy_stable_argsort():
+    rng = np.random.default_rng(3)
+    n, dx, tile = (32, 24, 16), (0.1, 0.1, 0.1), (8, 8, 4)
+    s = O.OracleSim(3, n, dx, 0.05, tile=tile)
+    N = 5000
+    x = [rng.integers(0, n[d], N) * dx[d] + rng.random(N) * dx[d] * 0.98 + 0.001 * dx[d] for d in range(3)]
+    u = [rng.normal(0, 0.1, N) for _ in range(3)]
+    i = s.add_species(-1, 1, 1, N)
+    s.load(i, *x, *u)
+    key = np.zeros(N, dtype=np.int64)
+    nt = [n[d] // tile[d] for d in range(3)]
+    for d in reversed(range(3)):
+        key = key * nt[d] + (np.floor(x[d] / dx[d]).astype(np.int64) // tile[d])
+    perm = s.sort(i)
+    assert np.array_equal(perm, np.argsort(key, kind="stable"))
+
+
+# --------------------------------------------------------------------------
+# Whole loop: cold Langmuir oscillation at omega_p, energy, continuity
+# --------------------------------------------------------------------------
+
+@pytest.fixture(scope="module")
+def langmuir_run():
+    w = W.langmuir_1d()
+    s = O.OracleSim(w.dim, w.n[:1], w.dx[:1], w.dt, bc=w.bc[:1], rho_bg=w.rho_bg, tile=w.tile[:1])
+    e = w.species[0]
+    i = s.add_species(e.q, e.m, e.w, e.capacity)
+    s.load(i, e.x, None, None, e.ux, e.uy, e.uz)
+    k = w.notes["k"]
+    xh = (np.arange(w.n[0]) + 0.5) * w.dx[0]
+    amp, energy, resid = [], [], {}
+    d0 = s.diagnostics()
+    e0 = d0["U_E"] + d0["U_B"] + d0["U_kin"][0]
+    for st in range(1, w.steps + 1):
+        s.step(1)
+        ex = s.field(O.EX)[0, 0]
+        amp.append(2.0 / w.n[0] * np.sum(ex * np.sin(k * xh)))
+        if st % 50 == 0 or st == 1:
+            d = s.diagnostics()
+            energy.append(d["U_E"] + d["U_B"] + d["U_kin"][0])
+        if st in (1, 500, 1000):
+            Ex = s.field(O.EX)[0, 0]
+            div = (Ex - np.roll(Ex, 1)) / w.dx[0]
+            resid[st] = div - s.rho()[0, 0] - w.rho_bg
+    return w, np.array(amp), e0, np.array(energy), resid
+
+
+def test_langmuir_frequency_and_amplitude(langmuir_run):
+    from scipy.optimize import curve_fit
+    w, amp, e0, energy, resid = langmuir_run
+    t = np.arange(1, w.steps + 1) * w.dt
+    p, _ = curve_fit(lambda t, A, om, ph: A * np.sin(om * t + ph), t, amp, p0=[0.01, 1.0, 0.0])
+    A, om, ph = p
+    assert abs(abs(om) - 1.0) < 1e-3
+    assert abs(abs(A) - 0.01 / abs(om)) < 1e-4  # E_x = (u0/omega) sin(kx) sin(omega t)
+    assert abs(ph) < 0.05 or abs(abs(ph) - math.pi) < 0.05
+
+
+def test_langmuir_energy_conserved(langmuir_run):
+    w, amp, e0, energy, resid = langmuir_run
+    assert np.max(np.abs(energy - e0)) < 1e-3 * e0
+
+
+def test_langmuir_continuity_residual_constant(langmuir_run):
+    w, amp, e0, energy, resid = langmuir_run
+    scale = 1.0  # max |rho| of electrons = n0 = 1
+    for st in (500, 1000):
+        assert np.max(np.abs(resid[st] - resid[1])) < 1e-12 * scale * math.sqrt(st)
+
+
+# --------------------------------------------------------------------------
+# Laser entry and Mur absorbing faces (method chosen here; the paper names
+# absorbing boundaries only): injected amplitude and reflection in vacuum
+# --------------------------------------------------------------------------
+
+def _vacuum(wl):
+    s = O.OracleSim(1, wl.n[:1], wl.dx[:1], wl.dt, bc=wl.bc[:1])
+    L = wl.laser
+    s.set_laser(L.a0, L.waist, L.fwhm, L.t_peak, L.x_focus, pol=L.pol)
+    return s
+
+
+def _reflection(cpl):
+    """energy left in the box after the pulse crossed x = L, over its peak"""
+    wl = W.vacuum_pulse_1d(cells_per_lambda=cpl, n_cells=32 * cpl)
+    s = _vacuum(wl)
+    dx, dt, L = wl.dx[0], wl.dt, wl.laser
+    n_mid = int(round((L.t_peak + 0.5 * wl.n[0] * dx) / dt))
+    s.step(n_mid)
+    d = s.diagnostics()
+    peak = d["U_E"] + d["U_B"]
+    s.step(int(round(0.9 * wl.n[0] * dx / dt)))
+    d = s.diagnostics()
+    return (d["U_E"] + d["U_B"]) / peak, s, wl, n_mid
+
+
+def test_laser_enters_with_prescribed_amplitude():
+    wl = W.vacuum_pulse_1d()
+    s = _vacuum(wl)
+    dx, dt, L = wl.dx[0], wl.dt, wl.laser
+    n_mid = int(round((L.t_peak + 0.5 * wl.n[0] * dx) / dt))
+    s.step(n_mid)
+    t = n_mid * dt
+    x = np.arange(wl.n[0] + 1) * dx
+    ey = s.field(O.EY)[0, 0]
+    tau = (t - x - L.t_peak) / L.fwhm
+    ref = L.a0 * np.exp(-2 * math.log(2) * tau ** 2) * np.sin(t - x - L.t_peak)
+    assert np.max(np.abs(ey - ref)) < 0.03 * L.a0
+    assert np.max(np.abs(ey)) > 0.95 * L.a0
+    # B_z = E_y for the +x wave (B half a cell and half a step away)
+    bz = s.field(O.BZ)[0, 0][:-1]
+    assert np.max(np.abs(bz - 0.5 * (ey[1:] + ey[:-1]))) < 0.03 * L.a0
+
+
+def test_mur_reflection_is_second_order_in_resolution():
+    """A first-order Mur face reflects an energy fraction ~ (k dx)^2."""
+    r32, _, _, _ = _reflection(32)
+    r64, _, _, _ = _reflection(64)
+    assert r32 < 2e-4
+    assert 3.0 < r32 / r64 < 5.0
