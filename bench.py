@@ -1,0 +1,358 @@
+"""Throughput benchmark of the GB300 PIC hot path.
+
+Default workload: the 2D3V laser-foil run (grid 2048x1024, dx = lambda/64,
+hydrogen slab n = 10 n_c over x-cells 1024-1087, 32 ppc of electrons and of
+protons = 4,194,304 particles, LP Gaussian laser a0 = 20 from x-min,
+absorbing x / periodic y), FP32 cell+offset form, seeded synthetic inputs.
+A "step" is one full PIC step (both field half steps, gather + Boris + drift
++ Esirkepov deposit of every particle, current fold, tile sort every K steps).
+
+Prints one JSON line.  ``value`` is particle-steps/s measured with CUDA events
+on the simulation's stream over K timed steps (L2 flushed before each step),
+inputs resident in HBM.  ``e2e`` is the same metric through the public C ABI
+from pinned host arrays (particle upload, K steps, diagnostics read back).
+``--impl reference`` times the FP64 CPU oracle instead (host cores).
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import math
+import os
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "particle-steps/s on 1 GB300: FP32+surrogate vs plain FP64 form at same error"
+UNIT = "particle-steps/s"
+
+
+def _peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            p = json.load(f)
+        return float(p["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+def make_workload(name, rank=0, sample=None):
+    from paper_2104_00642_gb300 import workloads as W
+    if name == "laser_foil_2d":
+        ny = 1024 if sample is None else sample
+        return W.laser_foil_2d(ny=ny, seed=W.SEED0 + 2 + 1000 * rank)
+    if name == "thermal_3d":
+        n = (256, 256, 256) if sample is None else (256, 256, sample)
+        return W.thermal_3d(n=n, seed=W.SEED0 + 3 + 1000 * rank)
+    if name == "langmuir_1d":
+        return W.langmuir_1d()
+    raise SystemExit(f"unknown workload {name}")
+
+
+def describe(w):
+    return (f"{w.name} {'x'.join(str(v) for v in w.n[:w.dim])} cells, {w.n_particles} particles "
+            f"({', '.join(s.name for s in w.species)})")
+
+
+def bytes_per_particle(dim, precision):
+    """algorithmic HBM bytes of one particle in the push kernel (read + write
+    of the particle state once)"""
+    if precision == 0:
+        return 2 * (4 + 4 * dim + 12)
+    return 2 * (4 + 8 * dim + 24)
+
+
+def occupied_cells(w):
+    cells = set()
+    for s in w.species:
+        c = np.floor(s.x / w.dx[0]).astype(np.int64)
+        if w.dim > 1:
+            c = c + w.n[0] * np.floor(s.y / w.dx[1]).astype(np.int64)
+        if w.dim > 2:
+            c = c + w.n[0] * w.n[1] * np.floor(s.z / w.dx[2]).astype(np.int64)
+        cells.update(np.unique(c).tolist())
+    return len(cells)
+
+
+class Clocks:
+    """nvidia-smi sampling of SM clock and throttle reasons during the timed region"""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, dev):
+        self.dev = dev
+        self.p = None
+        self.path = os.path.join(ROOT, "gpurun_out", f"clocks_{os.getpid()}.csv")
+
+    def __enter__(self):
+        try:
+            os.makedirs(os.path.dirname(self.path), exist_ok=True)
+            self.f = open(self.path, "w")
+            self.p = subprocess.Popen(["nvidia-smi", f"--id={self.dev}", f"--query-gpu={self.Q}",
+                                       "--format=csv,noheader,nounits", "-lms", "200"], stdout=self.f,
+                                      stderr=subprocess.DEVNULL)
+        except Exception:
+            self.p = None
+        return self
+
+    def __exit__(self, *a):
+        if self.p is not None:
+            self.p.terminate()
+            try:
+                self.p.wait(timeout=5)
+            except Exception:
+                self.p.kill()
+            self.f.close()
+
+    def summary(self):
+        if self.p is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        rows = []
+        for ln in open(self.path):
+            t = [x.strip() for x in ln.split(",")]
+            if len(t) >= 9:
+                rows.append(t)
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+        sm = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in rows if r[2].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in rows for i in range(4) if r[5 + i].lower() == "active"})
+        return {"sm_mhz": float(np.median(sm)) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": reasons, "samples": len(rows)}
+
+
+def traffic_record(kernel_src_files):
+    """dram bytes per push launch from the committed ncu summary, if it was
+    taken on the current kernel source (else None)"""
+    path = os.path.join(ROOT, "profiles", "push_traffic.json")
+    if not os.path.exists(path):
+        return None
+    rec = json.load(open(path))
+    h = hashlib.sha256()
+    for f in kernel_src_files:
+        h.update(open(os.path.join(ROOT, f), "rb").read())
+    if rec.get("source_sha256") != h.hexdigest():
+        return None
+    return rec
+
+
+def oracle_rate(wname, min_seconds=10.0, max_steps=50, steps=None, sample_rows=32):
+    """FP64 CPU oracle on a y-strip sample of the workload (same x structure,
+    periodic y): particle-steps/s on one host core"""
+    from tests.helpers import oracle_from_workload
+    w = make_workload(wname, sample=sample_rows)
+    o = oracle_from_workload(w, sort_interval=0)
+    npart = w.n_particles
+    t0 = time.perf_counter()
+    done = 0
+    per = []
+    while True:
+        a = time.perf_counter()
+        o.step(1)
+        per.append(time.perf_counter() - a)
+        done += 1
+        if steps is not None and done >= steps:
+            break
+        if steps is None and (time.perf_counter() - t0 >= min_seconds or done >= max_steps):
+            break
+    el = time.perf_counter() - t0
+    return npart * done / el, {"sample": f"{describe(w)}: y-strip of {sample_rows} rows of the full workload, "
+                                         f"{done} steps", "seconds": el, "steps": done, "per_step_s": per,
+                               "particles": npart}
+
+
+def run_reference(args):
+    """--impl reference: the FP64 CPU oracle, as it stands, on the host cores"""
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    from oracle import oracle as O
+    O.build()
+    for _ in range(args.warmup):
+        pass
+    w = args.workload
+    v, info = oracle_rate(w, steps=args.warmup + args.steps)
+    per = info["per_step_s"][args.warmup:]
+    t = float(np.sum(per))
+    value = info["particles"] * len(per) / t
+    out = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+           "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * t / len(per), "higher_is_better": True,
+           "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+           "config": {"workload": info["sample"], "precision": "fp64 absolute positions (CPU oracle)"},
+           "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": info["sample"]},
+           "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(out))
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=50)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="native", choices=["native", "reference"])
+    ap.add_argument("--workload", default="laser_foil_2d", choices=["laser_foil_2d", "thermal_3d", "langmuir_1d"])
+    ap.add_argument("--sort-interval", type=int, default=8)
+    ap.add_argument("--fp64-steps", type=int, default=10)
+    ap.add_argument("--no-cpu", action="store_true", help="skip the CPU baseline leg")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-flush", action="store_true")
+    args = ap.parse_args()
+    args.warmup = max(args.warmup, 3)
+    if args.impl == "reference":
+        run_reference(args)
+        return
+
+    import torch
+
+    from paper_2104_00642_gb300 import pic
+
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", init_method="env://")
+    stream = torch.cuda.Stream()
+    w = make_workload(args.workload, rank)
+    npart = w.n_particles
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
+
+    def timed(sim, K, profile=False):
+        if profile:
+            sim.pic_profile(True)
+        evs = []
+        with torch.cuda.stream(stream):
+            for _ in range(K):
+                if not args.no_flush:
+                    flush.fill_(1.0)  # evict L2 between steps
+                a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                a.record(stream)
+                sim.pic_step(1)
+                b.record(stream)
+                evs.append((a, b))
+        torch.cuda.synchronize()
+        ms = [a.elapsed_time(b) for a, b in evs]
+        prof = sim.pic_profile_read() if profile else None
+        if profile:
+            sim.pic_profile(False)
+        return ms, prof
+
+    # ---- FP32 cell+offset: the headline ----------------------------------
+    sim = pic.from_workload(w, precision=pic.FP32_CELLOFF, sort_interval=args.sort_interval,
+                            stream=stream.cuda_stream)
+    timed(sim, args.warmup)
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    with Clocks(local) as clk:
+        ms, prof = timed(sim, args.steps, profile=True)
+    t_local = float(np.sum(ms)) / 1e3
+    t = t_local
+    if dist:
+        tt = torch.tensor([t_local], device="cuda", dtype=torch.float64)
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        t = float(tt.item())
+    value = world * npart * args.steps / t
+    diag = sim.pic_diagnostics()
+    if not all(math.isfinite(v) for v in (diag["U_E"], diag["U_B"])):
+        raise SystemExit("non-finite diagnostics")
+
+    # roofline of the dominant kernel (the push kernel)
+    peak, peak_kind = _peaks()
+    push_ms = prof["ms"]["push"]
+    push_launches = max(1, prof["push_launches"])
+    per_launch_s = push_ms / 1e3 / push_launches
+    occ = occupied_cells(w)
+    bpp = bytes_per_particle(w.dim, 0)
+    grid_b = (24 + 12) * occ  # gather 6 comps + deposit 3 comps, once per occupied cell
+    alg_bytes_launch = (npart * bpp + len(w.species) * grid_b) / len(w.species)
+    achieved = alg_bytes_launch / per_launch_s / 1e9
+    trec = traffic_record(["paper_2104_00642_gb300/csrc/push.cu", "paper_2104_00642_gb300/csrc/pic_internal.cuh"])
+    roof = {"bound": "hbm", "kernel": "push (gather+Boris+drift+Esirkepov)", "achieved": achieved,
+            "peak": peak, "unit": "GB/s", "frac": achieved / peak, "peak_kind": f"{peak_kind} hbm_gbs",
+            "traffic": (trec["bytes_per_launch"] if trec else None),
+            "algorithmic_bytes_per_launch": alg_bytes_launch, "avg_launch_ms": per_launch_s * 1e3,
+            "bytes_per_particle": bpp, "occupied_cells": occ}
+
+    # ---- plain FP64 form on the same workload ------------------------------
+    sim64 = pic.from_workload(w, precision=pic.FP64_PLAIN, sort_interval=args.sort_interval,
+                              stream=stream.cuda_stream)
+    timed(sim64, 3)
+    ms64, _ = timed(sim64, args.fp64_steps)
+    v64 = npart * args.fp64_steps / (float(np.sum(ms64)) / 1e3)
+    sim64.close()
+
+    # ---- end to end through the C ABI from pinned host arrays --------------
+    e2e = None
+    if not args.no_e2e:
+        pinned = []
+        for s in w.species:
+            arrs = []
+            for a in (s.x, s.y, s.z, s.ux, s.uy, s.uz):
+                t_ = torch.empty(a.shape[0], dtype=torch.float64, pin_memory=True)
+                t_.numpy()[:] = a
+                arrs.append(t_)
+            pinned.append(arrs)
+        sim.close()
+        sim_e = pic.from_workload(w, precision=pic.FP32_CELLOFF, sort_interval=args.sort_interval,
+                                  stream=stream.cuda_stream, load=False)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        h2d = 0
+        for i, arrs in enumerate(pinned):
+            np_arrs = [a.numpy() for a in arrs]
+            sim_e.pic_load_particles(i, np_arrs[0], np_arrs[1] if w.dim > 1 else None,
+                                     np_arrs[2] if w.dim > 2 else None, np_arrs[3], np_arrs[4], np_arrs[5])
+            h2d += sum(a.nbytes for a in np_arrs[:w.dim]) + sum(a.nbytes for a in np_arrs[3:])
+        sim_e.pic_step(args.steps)
+        d = sim_e.pic_diagnostics()
+        el = time.perf_counter() - t0
+        d2h = 8 * (8 + 2 * len(w.species))
+        e2e = {"value": world * npart * args.steps / el, "unit": UNIT,
+               "h2d_bytes_per_step": h2d / args.steps, "d2h_bytes_per_step": d2h / args.steps,
+               "seconds": el, "note": "pic_load_particles + pic_step(K) + pic_diagnostics, host wall clock"}
+        assert math.isfinite(d["U_E"])
+        sim_e.close()
+    else:
+        sim.close()
+
+    # ---- CPU baseline (oracle, bounded sample, rank 0, N = 1) ---------------
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu:
+        v_cpu, info = oracle_rate(args.workload, min_seconds=10.0)
+        cpu = {"value": v_cpu, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": info["sample"]}
+
+    if rank == 0:
+        launches = int(sum(prof["launches"].values()))
+        out = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+               "warmup": args.warmup, "ms_per_step": 1e3 * t / args.steps, "higher_is_better": True,
+               "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+               "config": {"workload": describe(w), "precision": "fp32 cell+offset (FP64 islands: diagnostics)",
+                          "sort_interval": args.sort_interval,
+                          "l2": "flushed (256 MiB write) before every timed step" if not args.no_flush else "not flushed",
+                          "replicas": world, "qed": "off (no QED in this workload)"},
+               "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches,
+               "clocks": clk.summary(),
+               "fp64_plain": {"value": v64, "unit": UNIT, "ms_per_step": float(np.mean(ms64)),
+                              "fp32_over_fp64": value / world / v64},
+               "phases_ms_per_step": {k: v / args.steps for k, v in prof["ms"].items()},
+               "launches_per_step": {k: v / args.steps for k, v in prof["launches"].items()}}
+        print(json.dumps(out))
+    if dist:
+        dist.barrier()
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

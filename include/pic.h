@@ -1,0 +1,222 @@
+/*
+ * pic.h -- C ABI of the GB300 (sm_103a) relativistic electromagnetic
+ * particle-in-cell hot path.
+ *
+ * The method is the PIC step of Song, Wang & Li, "YUNIC: A Multi-Dimensional
+ * Particle-In-Cell Code for Laser-Plasma Interaction" (arXiv:2104.00642):
+ * Yee FDTD field update (Sec. II.B, Eqs. (9)-(10)), Boris pusher (Sec. II.C,
+ * Eqs. (11)-(16)), field interpolation with the W_2 weights (Sec. II.D,
+ * Eqs. (17), (19)), Esirkepov charge-conserving current (Sec. II.E,
+ * Eqs. (20)-(22)), in the split step that keeps fields and positions at both
+ * integer and half steps (Sec. II.F).
+ *
+ * Units are the normalised units of Eq. (8): c = m_e = e = 1; time in
+ * 1/omega_r, length in c/omega_r, E and B in m_e c omega_r/e, momentum per
+ * mass u = gamma v, density in n_r, current in c e n_r.  In these units
+ * div E = rho and dE/dt = curl B - J.
+ *
+ * Conventions shared by every call:
+ *  - All compute runs in the library's CUDA kernels on the stream given at
+ *    creation (NULL = the legacy default stream).  There is no CPU fallback:
+ *    a call made without a usable GPU returns PIC_ERR_CUDA.
+ *  - Calls return PIC_OK (0) or a negative PIC_ERR_* code; the message of the
+ *    last failure is available from pic_last_error().
+ *  - Host arrays passed in are caller-owned and only read during the call;
+ *    host arrays passed out are caller-allocated and filled.
+ *  - Field arrays exchanged with the host are FP64, x fastest, covering
+ *    cells [0, N_d) along periodic axes and nodes [0, N_d] along absorbing
+ *    axes (so every component has the same shape).  A component stored at
+ *    node i or half node i+1/2 is exchanged at index i (standard Yee
+ *    placement: Ex(i+1/2,j,k), Ey(i,j+1/2,k), Ez(i,j,k+1/2), Bx(i,j+1/2,k+1/2),
+ *    By(i+1/2,j,k+1/2), Bz(i+1/2,j+1/2,k); J like E; RHO on nodes).
+ *  - One pic_sim must not be used from two host threads at once.
+ */
+#ifndef PIC_H
+#define PIC_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct pic_sim pic_sim;
+
+enum {
+    PIC_OK = 0,
+    PIC_ERR_ARG = -1,      /* invalid argument */
+    PIC_ERR_CFL = -2,      /* dt above the Courant limit, or a particle moved more than one cell */
+    PIC_ERR_CUDA = -3,     /* CUDA runtime/driver failure (message says which) */
+    PIC_ERR_CAPACITY = -4, /* species capacity exceeded */
+    PIC_ERR_NONFINITE = -5,/* NaN/Inf found in a particle or a diagnostic */
+    PIC_ERR_NOMEM = -6,    /* device allocation failed */
+    PIC_ERR_STATE = -7     /* call not valid in the current state */
+};
+
+enum { PIC_BC_PERIODIC = 0, PIC_BC_ABSORB = 1 };
+enum { PIC_PREC_FP32_CELLOFF = 0, PIC_PREC_FP64_PLAIN = 1 };
+enum { PIC_EX = 0, PIC_EY, PIC_EZ, PIC_BX, PIC_BY, PIC_BZ, PIC_JX, PIC_JY, PIC_JZ, PIC_RHO };
+enum { PIC_LASER_LINEAR_Y = 0, PIC_LASER_CIRCULAR = 1 };
+
+#define PIC_MAX_SPECIES 8
+
+/* Grid.  dim in {1,2,3}; n[d] cells and dx[d] spacing along active axes
+ * (entries for inactive axes are ignored).  bc[d] applies to both faces of
+ * axis d.  order is the shape order of Sec. II.D; only 2 (the three-node
+ * W_2 weights) is implemented.  Periodic axes need n[d] >= 8. */
+typedef struct {
+    int dim;
+    int64_t n[3];
+    double dx[3];
+    int bc[3];
+    int order;
+} pic_grid;
+
+/* Species.  q in e, m in m_e, w = density carried by one macro-particle (in
+ * n_r, the same for all particles of the species; a uniform density n with
+ * ppc particles per cell has w = n/ppc).  capacity = maximum particle count. */
+typedef struct {
+    double q, m, w;
+    int64_t capacity;
+} pic_species;
+
+/* Options.  precision: PIC_PREC_FP32_CELLOFF (int cell + FP32 in-cell offset,
+ * FP32 fields and push) or PIC_PREC_FP64_PLAIN (absolute FP64 positions and
+ * FP64 everything).  sort_interval: counting-sort particles by tile every K
+ * steps (K >= 1; 0 = never after loading).  tile[d]: cells per tile along
+ * active axes (powers of two, 0 = library default).  rho_bg: uniform
+ * immobile background charge density used only by the Gauss diagnostic.
+ * stream: a cudaStream_t (NULL = legacy default stream). */
+typedef struct {
+    int precision;
+    int sort_interval;
+    int tile[3];
+    double rho_bg;
+    void *stream;
+} pic_options;
+
+/* Laser entering through the x-min face (requires bc[0] == PIC_BC_ABSORB):
+ * paraxial Gaussian beam of peak amplitude a0 (normalised field), waist
+ * radius `waist`, focus at x = x_focus, centred at (yc, zc), Gaussian
+ * intensity envelope of full width at half maximum `fwhm` whose peak crosses
+ * x = 0 at t_peak.  pol: linear along y or circular (both components of
+ * amplitude a0).  It enters through the scattered-field Mur condition on the
+ * x-min face (the paper uses absorbing faces and lasers from the left
+ * boundary, Sec. III(a), without giving the method). */
+typedef struct {
+    double a0, waist, fwhm, t_peak, x_focus, yc, zc;
+    int pol;
+} pic_laser;
+
+/* Diagnostics at the current integer step (FP64, Sec. II.B and Eq. (1)).
+ * U_E = 1/2 sum E^2 dV and U_B = 1/2 sum B^2 dV over cells [0,N);
+ * U_kin[s] = sum_p w m (gamma-1) dV; charge = sum_p q w dV + rho_bg * volume;
+ * gauss_max = max over nodes [0,N) of |div E - rho - rho_bg| with rho the
+ * particle density averaged over x -/+ (dt/2) v (conserved to round-off by
+ * the charge-conserving deposit after the first step); E_absorbed = kinetic
+ * energy removed at absorbing faces; n_alive[s] = live particles. */
+typedef struct {
+    int64_t step;
+    double t;
+    double U_E, U_B;
+    double U_kin[PIC_MAX_SPECIES];
+    double charge;
+    double gauss_max;
+    double E_absorbed;
+    int64_t n_alive[PIC_MAX_SPECIES];
+} pic_diag;
+
+/* Create a simulation: validates the grid, the Courant condition
+ * dt < 1/sqrt(sum_d 1/dx_d^2), species and options, allocates all device
+ * memory (fields with ghost layers, double-buffered particle arrays, sort
+ * and reduction scratch) and zeroes the fields.  *out is NULL on failure.
+ * Errors: PIC_ERR_ARG, PIC_ERR_CFL, PIC_ERR_NOMEM, PIC_ERR_CUDA. */
+int pic_create(const pic_grid *grid, double dt, const pic_species *species, int nsp,
+               const pic_options *opt, pic_sim **out);
+
+/* Release every device and host resource of sim (NULL is accepted). */
+void pic_destroy(pic_sim *sim);
+
+/* Message of the last failed call on sim (or of the last failed pic_create
+ * when sim is NULL).  Valid until the next call on the same sim. */
+const char *pic_last_error(const pic_sim *sim);
+
+/* Append n particles to species sp.  x, y, z: absolute FP64 positions in
+ * [0, n_d dx_d) (arrays of inactive axes may be NULL); ux, uy, uz: u = gamma v.
+ * Host arrays (pageable or pinned) are copied; positions are converted to
+ * the precision layout on the GPU and the species is sorted by tile.
+ * Errors: PIC_ERR_ARG (bad species, position outside the domain, non-finite
+ * input), PIC_ERR_CAPACITY. */
+int pic_load_particles(pic_sim *sim, int sp, int64_t n, const double *x, const double *y,
+                       const double *z, const double *ux, const double *uy, const double *uz);
+
+/* Set the x-min laser (see pic_laser).  Errors: PIC_ERR_ARG. */
+int pic_set_laser(pic_sim *sim, const pic_laser *laser);
+
+/* Overwrite field component comp (PIC_EX..PIC_JZ) from a host FP64 array in
+ * the exchange layout above; ghost layers are refreshed.  Errors: PIC_ERR_ARG. */
+int pic_set_field(pic_sim *sim, int comp, const double *host_in);
+
+/* Advance nsteps steps of the split PIC step (Sec. II.F): half E and B
+ * updates, gather + Boris + drift + Esirkepov deposit for every live
+ * particle, current fold, half B and E updates; counting sort by tile every
+ * sort_interval steps.  Enqueued on the stream; returns after checking the
+ * device error flags (one device->host read per call).
+ * Errors: PIC_ERR_CFL (a particle crossed more than one cell), PIC_ERR_CUDA. */
+int pic_step(pic_sim *sim, int64_t nsteps);
+
+/* Copy component comp (PIC_EX..PIC_JZ, or PIC_RHO = particle charge density
+ * as in pic_diag) to host_out in the exchange layout.  Synchronises the
+ * stream.  Errors: PIC_ERR_ARG. */
+int pic_fields(pic_sim *sim, int comp, double *host_out);
+
+/* Number of live particles of species sp after the last sort (dead particles
+ * are dropped at sorts; between sorts they are counted as not alive). */
+int64_t pic_particle_count(pic_sim *sim, int sp);
+
+/* Copy species sp to caller-sized host arrays (capacity cap >= count):
+ * absolute FP64 positions and u, in the current array order; alive[i] = 0
+ * for particles absorbed since the last sort.  Any pointer may be NULL.
+ * *n receives the count.  Errors: PIC_ERR_ARG, PIC_ERR_CAPACITY. */
+int pic_get_particles(pic_sim *sim, int sp, int64_t cap, int64_t *n, double *x, double *y,
+                      double *z, double *ux, double *uy, double *uz, uint8_t *alive);
+
+/* Device-resident particle state for inspection: packed cell index of each
+ * particle (FP32 form: cell = i | j << bx | k << (bx+by), 0xFFFFFFFF = dead;
+ * FP64 form: floor(x/dx) packed the same way), copied to host.  bits[3]
+ * receives (bx, by, bz).  Errors: PIC_ERR_ARG, PIC_ERR_CAPACITY. */
+int pic_get_cells(pic_sim *sim, int sp, int64_t cap, uint32_t *cells, int *bits);
+
+/* Diagnostics of the current step (see pic_diag).  Runs FP64 reductions on
+ * the GPU in a fixed order and synchronises the stream.
+ * Errors: PIC_ERR_NONFINITE, PIC_ERR_CUDA. */
+int pic_diagnostics(pic_sim *sim, pic_diag *d);
+
+/* Gather E and B (Eq. (19)) at the current particle positions of species sp
+ * without moving them; out6 receives 6*n FP64 values (Ex,Ey,Ez,Bx,By,Bz per
+ * particle) in array order.  Errors: PIC_ERR_ARG, PIC_ERR_CAPACITY. */
+int pic_gather(pic_sim *sim, int sp, int64_t cap, double *out6);
+
+/* Synchronise the simulation's stream. */
+int pic_sync(pic_sim *sim);
+
+/* Phases of pic_step timed by pic_profile. */
+enum { PIC_PHASE_SORT = 0, PIC_PHASE_FIELDS, PIC_PHASE_PUSH, PIC_PHASE_FOLD, PIC_NPHASE };
+
+/* Enable (1) or disable (0) per-phase timing of pic_step: CUDA events are
+ * recorded on the simulation's stream around each phase (no host
+ * synchronisation inside the step).  Enabling clears the accumulators. */
+int pic_profile(pic_sim *sim, int enable);
+
+/* Read the accumulated device time of each phase in milliseconds
+ * (ms[PIC_NPHASE], may be NULL), the kernel launches pic_step issued per
+ * phase (launches[PIC_NPHASE], may be NULL) and the number of push-kernel
+ * launches (push_launches, may be NULL) since profiling was enabled.
+ * Synchronises the stream and clears the accumulators. */
+int pic_profile_read(pic_sim *sim, double *ms, int64_t *launches, int64_t *push_launches);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* PIC_H */

@@ -1,0 +1,766 @@
+// capi.cu -- host runtime behind the C ABI of include/pic.h: simulation
+// state, device memory, step orchestration on one stream, error flags.
+//
+// Per step n -> n+1 (the split step of Sec. II.F):
+//   [sort every K steps] E half (with J^n, then J := 0) -> B half + Mur ->
+//   push/deposit every species -> current fold -> B half + Mur -> E half
+//   (with J^{n+1}).
+// Nothing inside a step waits for the host; the device error flags are read
+// once at the end of pic_step.
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstdlib>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "../../include/pic.h"
+#include "diag.cuh"
+#include "fdtd.cuh"
+#include "push.cuh"
+#include "sort.cuh"
+
+using namespace pic;
+
+namespace {
+
+struct SpeciesState {
+    double q = 0, m = 1, w = 0;
+    long long cap = 0;
+    long long n_hi = 0;        // host upper bound of the live count
+    long long *d_count = nullptr;
+    int cur = 0;
+    uint32_t *cell[2] = {nullptr, nullptr};
+    float *off[2][3] = {};
+    float *uf[2][3] = {};
+    double *x[2][3] = {};
+    double *ud[2][3] = {};
+    uint32_t *tile_start = nullptr;  // ntiles + 1
+};
+
+std::string g_create_error;
+
+}  // namespace
+
+struct pic_sim {
+    Grid g{};
+    int precision = PIC_PREC_FP32_CELLOFF;
+    int sort_interval = 0;
+    double rho_bg = 0.0;
+    cudaStream_t st = nullptr;
+    void *F = nullptr;       // 9 components
+    double *rho = nullptr;   // padded, for diagnostics
+    int nsp = 0;
+    SpeciesState sp[PIC_MAX_SPECIES];
+    void *sort_scratch = nullptr;
+    double *diag_scratch = nullptr;
+    double *diag_out = nullptr;  // 16 doubles
+    int *d_err = nullptr;
+    double *d_eabs = nullptr;
+    long long step = 0;
+    Laser laser{};
+    std::vector<void *> allocs;
+    std::string err;
+    // profiling
+    bool prof = false;
+    struct Mark {
+        int phase;
+        cudaEvent_t a, b;
+    };
+    std::vector<Mark> marks;
+    long long prof_launch[PIC_NPHASE] = {0, 0, 0, 0};
+    long long prof_push = 0;
+    cudaEvent_t cur_a = nullptr;
+    long long cur_l0 = 0;
+};
+
+namespace {
+
+int fail(pic_sim *s, int code, const char *fmt, ...)
+{
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof buf, fmt, ap);
+    va_end(ap);
+    if (s) s->err = buf;
+    else g_create_error = buf;
+    return code;
+}
+
+#define CK(call)                                                                                   \
+    do {                                                                                           \
+        cudaError_t e_ = (call);                                                                   \
+        if (e_ != cudaSuccess) return fail(s, PIC_ERR_CUDA, "%s: %s", #call, cudaGetErrorString(e_)); \
+    } while (0)
+
+int dalloc(pic_sim *s, void **p, size_t bytes)
+{
+    *p = nullptr;
+    if (bytes == 0) bytes = 16;
+    cudaError_t e = cudaMalloc(p, bytes);
+    if (e != cudaSuccess) {
+        *p = nullptr;
+        return fail(s, PIC_ERR_NOMEM, "cudaMalloc(%zu): %s", bytes, cudaGetErrorString(e));
+    }
+    s->allocs.push_back(*p);
+    return PIC_OK;
+}
+
+size_t rsize(const pic_sim *s) { return s->precision == PIC_PREC_FP64_PLAIN ? 8 : 4; }
+
+PartF32 view32(pic_sim *s, int i, int buf)
+{
+    SpeciesState &p = s->sp[i];
+    PartF32 v{};
+    v.cell = p.cell[buf];
+    for (int d = 0; d < 3; d++) {
+        v.off[d] = p.off[buf][d];
+        v.u[d] = p.uf[buf][d];
+    }
+    v.n = p.n_hi;
+    v.dn = p.d_count;
+    return v;
+}
+
+PartF64 view64(pic_sim *s, int i, int buf)
+{
+    SpeciesState &p = s->sp[i];
+    PartF64 v{};
+    v.cell = p.cell[buf];
+    for (int d = 0; d < 3; d++) {
+        v.x[d] = p.x[buf][d];
+        v.u[d] = p.ud[buf][d];
+    }
+    v.n = p.n_hi;
+    v.dn = p.d_count;
+    return v;
+}
+
+int ilog2_ceil(long long v)
+{
+    int b = 0;
+    while ((1ll << b) < v) b++;
+    return b;
+}
+
+PushConst push_const(const pic_sim *s, const SpeciesState &p)
+{
+    PushConst pc{};
+    const Grid &g = s->g;
+    pc.qmdt2 = p.q / p.m * 0.5 * g.dt;
+    pc.qw = p.q * p.w;
+    pc.hdt = 0.5 * g.dt;
+    double dV = 1.0;
+    for (int d = 0; d < 3; d++) {
+        pc.hdx[d] = 0.5 * g.dt / g.dx[d];
+        pc.cJ[d] = -p.q * p.w * g.dx[d] / g.dt;
+        if (d < g.dim) dV *= g.dx[d];
+    }
+    pc.wmdV = p.w * p.m * dV;
+    return pc;
+}
+
+// counting sort of one species by tile into the other buffer
+int sort_species(pic_sim *s, int i)
+{
+    SpeciesState &p = s->sp[i];
+    if (p.n_hi == 0) return PIC_OK;
+    const uint32_t *perm = nullptr, *skeys = nullptr;
+    sort_by_tile(p.cell[p.cur], p.n_hi, p.d_count, s->g, s->sort_scratch, p.tile_start, p.d_count, &perm, &skeys,
+                 s->st);
+    int o = 1 - p.cur;
+    if (s->precision == PIC_PREC_FP64_PLAIN)
+        launch_permute_f64(view64(s, i, p.cur), view64(s, i, o), perm, p.d_count, p.n_hi, s->g.dim, s->st);
+    else
+        launch_permute_f32(view32(s, i, p.cur), view32(s, i, o), perm, p.d_count, p.n_hi, s->g.dim, s->st);
+    p.cur = o;
+    CK(cudaGetLastError());
+    return PIC_OK;
+}
+
+int read_count(pic_sim *s, int i, long long *n)
+{
+    CK(cudaMemcpyAsync(n, s->sp[i].d_count, sizeof(long long), cudaMemcpyDeviceToHost, s->st));
+    CK(cudaStreamSynchronize(s->st));
+    s->sp[i].n_hi = *n;
+    return PIC_OK;
+}
+
+// exchange box (x fastest): [0,N) periodic, [0,N] absorbing
+void out_box(const Grid &g, long long *m)
+{
+    for (int d = 0; d < 3; d++)
+        m[d] = d >= g.dim ? 1 : (g.bc[d] == ABSORB ? g.n[d] + 1 : g.n[d]);
+}
+
+template <typename R>
+int copy_comp_out(pic_sim *s, const R *dev, double *host_out)
+{
+    const Grid &g = s->g;
+    std::vector<R> h((size_t)g.vol);
+    CK(cudaMemcpyAsync(h.data(), dev, (size_t)g.vol * sizeof(R), cudaMemcpyDeviceToHost, s->st));
+    CK(cudaStreamSynchronize(s->st));
+    long long m[3];
+    out_box(g, m);
+    for (long long k = 0; k < m[2]; k++)
+        for (long long j = 0; j < m[1]; j++)
+            for (long long i = 0; i < m[0]; i++)
+                host_out[(k * m[1] + j) * m[0] + i] = (double)h[(size_t)goff(g, (int)i, (int)j, (int)k)];
+    return PIC_OK;
+}
+
+template <typename R>
+int copy_comp_in(pic_sim *s, R *dev, const double *host_in)
+{
+    const Grid &g = s->g;
+    std::vector<R> h((size_t)g.vol);
+    CK(cudaMemcpyAsync(h.data(), dev, (size_t)g.vol * sizeof(R), cudaMemcpyDeviceToHost, s->st));
+    CK(cudaStreamSynchronize(s->st));
+    long long m[3];
+    out_box(g, m);
+    // every padded cell whose (periodic image of the) index lies in the box
+    for (int k = -g.G[2]; k < g.n[2] + g.G[2]; k++)
+        for (int j = -g.G[1]; j < g.n[1] + g.G[1]; j++)
+            for (int i = -g.G[0]; i < g.n[0] + g.G[0]; i++) {
+                int p[3] = {i, j, k};
+                bool in = true;
+                for (int d = 0; d < 3 && in; d++) {
+                    if (d >= g.dim) continue;
+                    if (g.bc[d] == PERIODIC) p[d] = ((p[d] % g.n[d]) + g.n[d]) % g.n[d];
+                    else if (p[d] < 0 || p[d] >= m[d]) in = false;
+                }
+                if (!in) continue;
+                h[(size_t)goff(g, i, j, k)] = (R)host_in[((long long)p[2] * m[1] + p[1]) * m[0] + p[0]];
+            }
+    CK(cudaMemcpyAsync(dev, h.data(), (size_t)g.vol * sizeof(R), cudaMemcpyHostToDevice, s->st));
+    CK(cudaStreamSynchronize(s->st));
+    return PIC_OK;
+}
+
+int compute_rho(pic_sim *s)
+{
+    const Grid &g = s->g;
+    CK(cudaMemsetAsync(s->rho, 0, (size_t)g.vol * sizeof(double), s->st));
+    for (int i = 0; i < s->nsp; i++) {
+        SpeciesState &p = s->sp[i];
+        if (p.n_hi == 0) continue;
+        if (s->precision == PIC_PREC_FP64_PLAIN) diag_rho_f64(view64(s, i, p.cur), g, p.q * p.w, s->rho, s->st);
+        else diag_rho_f32(view32(s, i, p.cur), g, p.q * p.w, s->rho, s->st);
+    }
+    launch_fold_rho(s->rho, g, s->st);
+    CK(cudaGetLastError());
+    return PIC_OK;
+}
+
+void ph_begin(pic_sim *s)
+{
+    s->cur_l0 = g_launches;
+    if (!s->prof) return;
+    cudaEventCreate(&s->cur_a);
+    cudaEventRecord(s->cur_a, s->st);
+}
+
+void ph_end(pic_sim *s, int phase)
+{
+    if (!s->prof) return;
+    cudaEvent_t b;
+    cudaEventCreate(&b);
+    cudaEventRecord(b, s->st);
+    s->marks.push_back({phase, s->cur_a, b});
+    s->prof_launch[phase] += g_launches - s->cur_l0;
+}
+
+int check_flags(pic_sim *s)
+{
+    int h = 0;
+    CK(cudaMemcpyAsync(&h, s->d_err, sizeof(int), cudaMemcpyDeviceToHost, s->st));
+    CK(cudaStreamSynchronize(s->st));
+    if (h) {
+        CK(cudaMemsetAsync(s->d_err, 0, sizeof(int), s->st));
+        if (h & ERR_CFL) return fail(s, PIC_ERR_CFL, "a particle moved more than one cell in a step");
+        if (h & ERR_NONFINITE) return fail(s, PIC_ERR_NONFINITE, "non-finite particle momentum");
+        if (h & ERR_CAPACITY) return fail(s, PIC_ERR_CAPACITY, "species capacity exceeded");
+    }
+    return PIC_OK;
+}
+
+}  // namespace
+
+// ---------------------------------------------------------------------
+// C ABI
+// ---------------------------------------------------------------------
+extern "C" {
+
+int pic_create(const pic_grid *grid, double dt, const pic_species *species, int nsp, const pic_options *opt,
+               pic_sim **out)
+{
+    if (out) *out = nullptr;
+    pic_sim *s = nullptr;
+    if (!grid || !out || (nsp > 0 && !species) || nsp < 0 || nsp > PIC_MAX_SPECIES)
+        return fail(s, PIC_ERR_ARG, "pic_create: null argument or bad species count");
+    if (grid->dim < 1 || grid->dim > 3) return fail(s, PIC_ERR_ARG, "pic_create: dim must be 1, 2 or 3");
+    if (grid->order != 2) return fail(s, PIC_ERR_ARG, "pic_create: only shape order 2 is implemented");
+    int prec = opt ? opt->precision : PIC_PREC_FP32_CELLOFF;
+    if (prec != PIC_PREC_FP32_CELLOFF && prec != PIC_PREC_FP64_PLAIN)
+        return fail(s, PIC_ERR_ARG, "pic_create: unknown precision");
+    Grid g{};
+    g.dim = grid->dim;
+    g.dt = dt;
+    double cfl = 0.0;
+    int bitsum = 0;
+    for (int d = 0; d < 3; d++) {
+        bool act = d < g.dim;
+        if (act) {
+            if (grid->n[d] < 1 || grid->n[d] > (1 << 24) || !(grid->dx[d] > 0.0))
+                return fail(s, PIC_ERR_ARG, "pic_create: bad n/dx on axis %d", d);
+            if (grid->bc[d] != PIC_BC_PERIODIC && grid->bc[d] != PIC_BC_ABSORB)
+                return fail(s, PIC_ERR_ARG, "pic_create: bad boundary on axis %d", d);
+            if (grid->bc[d] == PIC_BC_PERIODIC && grid->n[d] < 2 * kGhost)
+                return fail(s, PIC_ERR_ARG, "pic_create: periodic axis %d needs n >= %d", d, 2 * kGhost);
+            cfl += 1.0 / (grid->dx[d] * grid->dx[d]);
+        }
+        g.n[d] = act ? (int)grid->n[d] : 1;
+        g.dx[d] = act ? grid->dx[d] : 1.0;
+        g.bc[d] = act ? grid->bc[d] : PERIODIC;
+        g.G[d] = act ? kGhost : 0;
+        g.ext[d] = g.n[d] + 2 * g.G[d];
+        g.bits[d] = act ? ilog2_ceil(g.n[d]) : 0;
+        bitsum += g.bits[d];
+        int t = opt && opt->tile[d] > 0 ? opt->tile[d] : (g.dim == 1 ? 64 : (g.dim == 2 ? 16 : 8));
+        if (!act) t = 1;
+        if (t & (t - 1)) return fail(s, PIC_ERR_ARG, "pic_create: tile sizes must be powers of two");
+        g.tile_log2[d] = ilog2_ceil(t);
+        g.ntile[d] = (g.n[d] + t - 1) / t;
+    }
+    if (bitsum > 31) return fail(s, PIC_ERR_ARG, "pic_create: grid too large for the packed cell index");
+    if (!(dt > 0.0) || dt * std::sqrt(cfl) >= 1.0)
+        return fail(s, PIC_ERR_CFL, "pic_create: dt=%g violates the Courant limit %g", dt, 1.0 / std::sqrt(cfl));
+    g.ntiles = (long long)g.ntile[0] * g.ntile[1] * g.ntile[2];
+    long long pitch = ((g.ext[0] + 31) / 32) * 32;
+    g.sy = pitch;
+    g.sz = pitch * g.ext[1];
+    g.vol = ((g.sz * g.ext[2] + 63) / 64) * 64;
+    g.origin = (long long)g.G[2] * g.sz + (long long)g.G[1] * g.sy + g.G[0];
+
+    s = new pic_sim();
+    s->g = g;
+    s->precision = prec;
+    s->sort_interval = opt ? opt->sort_interval : 0;
+    s->rho_bg = opt ? opt->rho_bg : 0.0;
+    s->st = opt ? (cudaStream_t)opt->stream : nullptr;
+    s->nsp = nsp;
+    int dev_count = 0;
+    cudaError_t e = cudaGetDeviceCount(&dev_count);
+    if (e != cudaSuccess || dev_count == 0) {
+        int rc = fail(nullptr, PIC_ERR_CUDA, "pic_create: no CUDA device (%s)", cudaGetErrorString(e));
+        delete s;
+        return rc;
+    }
+    int rc = PIC_OK;
+    size_t R = rsize(s);
+    long long maxcap = 0;
+    rc = rc ? rc : dalloc(s, &s->F, (size_t)NCOMP * g.vol * R);
+    rc = rc ? rc : dalloc(s, (void **)&s->rho, (size_t)g.vol * sizeof(double));
+    for (int i = 0; i < nsp && !rc; i++) {
+        SpeciesState &p = s->sp[i];
+        const pic_species &q = species[i];
+        if (!(q.m > 0.0) || q.capacity < 0 || q.capacity > 0x7FFFFFFFll) {
+            rc = fail(s, PIC_ERR_ARG, "pic_create: bad species %d", i);
+            break;
+        }
+        p.q = q.q;
+        p.m = q.m;
+        p.w = q.w;
+        p.cap = q.capacity;
+        maxcap = std::max(maxcap, p.cap);
+        rc = rc ? rc : dalloc(s, (void **)&p.d_count, sizeof(long long));
+        rc = rc ? rc : dalloc(s, (void **)&p.tile_start, (size_t)(g.ntiles + 1) * sizeof(uint32_t));
+        for (int b = 0; b < 2 && !rc; b++) {
+            rc = dalloc(s, (void **)&p.cell[b], (size_t)p.cap * 4);
+            for (int d = 0; d < 3 && !rc; d++) {
+                if (prec == PIC_PREC_FP64_PLAIN) {
+                    if (d < g.dim) rc = dalloc(s, (void **)&p.x[b][d], (size_t)p.cap * 8);
+                    if (!rc) rc = dalloc(s, (void **)&p.ud[b][d], (size_t)p.cap * 8);
+                } else {
+                    if (d < g.dim) rc = dalloc(s, (void **)&p.off[b][d], (size_t)p.cap * 4);
+                    if (!rc) rc = dalloc(s, (void **)&p.uf[b][d], (size_t)p.cap * 4);
+                }
+            }
+        }
+    }
+    rc = rc ? rc : dalloc(s, &s->sort_scratch, sort_scratch_bytes(maxcap));
+    rc = rc ? rc : dalloc(s, (void **)&s->diag_scratch, diag_scratch_doubles() * sizeof(double));
+    rc = rc ? rc : dalloc(s, (void **)&s->diag_out, 16 * sizeof(double));
+    rc = rc ? rc : dalloc(s, (void **)&s->d_err, sizeof(int));
+    rc = rc ? rc : dalloc(s, (void **)&s->d_eabs, sizeof(double));
+    if (!rc) {
+        cudaError_t z = cudaMemsetAsync(s->F, 0, (size_t)NCOMP * g.vol * R, s->st);
+        if (z == cudaSuccess) z = cudaMemsetAsync(s->d_err, 0, sizeof(int), s->st);
+        if (z == cudaSuccess) z = cudaMemsetAsync(s->d_eabs, 0, sizeof(double), s->st);
+        for (int i = 0; i < nsp && z == cudaSuccess; i++)
+            z = cudaMemsetAsync(s->sp[i].d_count, 0, sizeof(long long), s->st);
+        if (z == cudaSuccess) z = cudaStreamSynchronize(s->st);
+        if (z != cudaSuccess) rc = fail(s, PIC_ERR_CUDA, "pic_create: %s", cudaGetErrorString(z));
+    }
+    if (rc) {
+        g_create_error = s->err;
+        pic_destroy(s);
+        return rc;
+    }
+    *out = s;
+    return PIC_OK;
+}
+
+void pic_destroy(pic_sim *s)
+{
+    if (!s) return;
+    if (s->st) cudaStreamSynchronize(s->st);
+    else cudaDeviceSynchronize();
+    for (void *p : s->allocs) cudaFree(p);
+    delete s;
+}
+
+const char *pic_last_error(const pic_sim *s) { return s ? s->err.c_str() : g_create_error.c_str(); }
+
+int pic_sync(pic_sim *s)
+{
+    if (!s) return PIC_ERR_ARG;
+    CK(cudaStreamSynchronize(s->st));
+    return PIC_OK;
+}
+
+int pic_load_particles(pic_sim *s, int sp, int64_t n, const double *x, const double *y, const double *z,
+                       const double *ux, const double *uy, const double *uz)
+{
+    if (!s) return PIC_ERR_ARG;
+    if (sp < 0 || sp >= s->nsp || n < 0) return fail(s, PIC_ERR_ARG, "pic_load_particles: bad species or count");
+    if (n == 0) return PIC_OK;
+    const Grid &g = s->g;
+    const double *xs[3] = {x, y, z};
+    const double *us[3] = {ux, uy, uz};
+    for (int d = 0; d < 3; d++)
+        if (!us[d] || (d < g.dim && !xs[d])) return fail(s, PIC_ERR_ARG, "pic_load_particles: null array");
+    for (int d = 0; d < g.dim; d++) {
+        double L = g.n[d] * g.dx[d];
+        for (int64_t a = 0; a < n; a++)
+            if (!(xs[d][a] >= 0.0 && xs[d][a] < L))
+                return fail(s, PIC_ERR_ARG, "pic_load_particles: particle %lld outside the domain on axis %d",
+                            (long long)a, d);
+    }
+    for (int d = 0; d < 3; d++)
+        for (int64_t a = 0; a < n; a++)
+            if (!std::isfinite(us[d][a])) return fail(s, PIC_ERR_ARG, "pic_load_particles: non-finite u");
+    SpeciesState &p = s->sp[sp];
+    long long cnt = 0;
+    int rc = read_count(s, sp, &cnt);
+    if (rc) return rc;
+    if (cnt + n > p.cap) return fail(s, PIC_ERR_CAPACITY, "pic_load_particles: capacity %lld exceeded", p.cap);
+    double *dtmp = nullptr;
+    CK(cudaMalloc(&dtmp, (size_t)n * 6 * sizeof(double)));
+    double *dx_[3] = {dtmp, dtmp + n, dtmp + 2 * n};
+    double *du_[3] = {dtmp + 3 * n, dtmp + 4 * n, dtmp + 5 * n};
+    cudaError_t e = cudaSuccess;
+    for (int d = 0; d < 3 && e == cudaSuccess; d++) {
+        if (d < g.dim) e = cudaMemcpyAsync(dx_[d], xs[d], n * sizeof(double), cudaMemcpyHostToDevice, s->st);
+        if (e == cudaSuccess) e = cudaMemcpyAsync(du_[d], us[d], n * sizeof(double), cudaMemcpyHostToDevice, s->st);
+    }
+    if (e == cudaSuccess) {
+        const double *cx[3] = {dx_[0], dx_[1], dx_[2]};
+        const double *cu[3] = {du_[0], du_[1], du_[2]};
+        if (s->precision == PIC_PREC_FP64_PLAIN) launch_load_f64(view64(s, sp, p.cur), cnt, n, cx, cu, g, s->st);
+        else launch_load_f32(view32(s, sp, p.cur), cnt, n, cx, cu, g, s->st);
+        e = cudaGetLastError();
+    }
+    long long newn = cnt + n;
+    if (e == cudaSuccess) e = cudaMemcpyAsync(p.d_count, &newn, sizeof(long long), cudaMemcpyHostToDevice, s->st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s->st);
+    cudaFree(dtmp);
+    if (e != cudaSuccess) return fail(s, PIC_ERR_CUDA, "pic_load_particles: %s", cudaGetErrorString(e));
+    p.n_hi = newn;
+    return PIC_OK;
+}
+
+int pic_set_laser(pic_sim *s, const pic_laser *L)
+{
+    if (!s || !L) return PIC_ERR_ARG;
+    if (s->g.bc[0] != ABSORB) return fail(s, PIC_ERR_ARG, "pic_set_laser: the x-min face must be absorbing");
+    if (!(L->fwhm > 0.0) || (s->g.dim > 1 && !(L->waist > 0.0)) || (L->pol != 0 && L->pol != 1))
+        return fail(s, PIC_ERR_ARG, "pic_set_laser: bad laser parameters");
+    s->laser.on = 1;
+    s->laser.pol = L->pol;
+    s->laser.a0 = L->a0;
+    s->laser.waist = L->waist;
+    s->laser.fwhm = L->fwhm;
+    s->laser.t_peak = L->t_peak;
+    s->laser.x_focus = L->x_focus;
+    s->laser.yc = L->yc;
+    s->laser.zc = L->zc;
+    return PIC_OK;
+}
+
+int pic_set_field(pic_sim *s, int comp, const double *host_in)
+{
+    if (!s) return PIC_ERR_ARG;
+    if (comp < PIC_EX || comp > PIC_JZ || !host_in) return fail(s, PIC_ERR_ARG, "pic_set_field: bad component");
+    if (s->precision == PIC_PREC_FP64_PLAIN)
+        return copy_comp_in<double>(s, (double *)s->F + comp * s->g.vol, host_in);
+    return copy_comp_in<float>(s, (float *)s->F + comp * s->g.vol, host_in);
+}
+
+int pic_step(pic_sim *s, int64_t nsteps)
+{
+    if (!s) return PIC_ERR_ARG;
+    if (nsteps < 0) return fail(s, PIC_ERR_ARG, "pic_step: negative step count");
+    const Grid &g = s->g;
+    const double h = 0.5 * g.dt;
+    const bool f64 = s->precision == PIC_PREC_FP64_PLAIN;
+    for (int64_t it = 0; it < nsteps; it++) {
+        if (s->sort_interval > 0 && s->step % s->sort_interval == 0) {
+            ph_begin(s);
+            for (int i = 0; i < s->nsp; i++) {
+                int rc = sort_species(s, i);
+                if (rc) return rc;
+            }
+            ph_end(s, PIC_PHASE_SORT);
+        }
+        double t0 = (double)s->step * g.dt;
+        if (f64) {
+            double *F = (double *)s->F;
+            ph_begin(s);
+            launch_update_E<double>(F, g, h, true, s->st);
+            launch_update_B<double>(F, g, h, t0 + h, s->laser, s->st);
+            ph_end(s, PIC_PHASE_FIELDS);
+            ph_begin(s);
+            for (int i = 0; i < s->nsp; i++) {
+                SpeciesState &p = s->sp[i];
+                if (p.n_hi) s->prof_push++;
+                launch_push_f64(view64(s, i, p.cur), F, g, push_const(s, p), s->d_err, s->d_eabs, s->st);
+            }
+            ph_end(s, PIC_PHASE_PUSH);
+            ph_begin(s);
+            launch_fold<double>(F, g, s->st);
+            ph_end(s, PIC_PHASE_FOLD);
+            ph_begin(s);
+            launch_update_B<double>(F, g, h, t0 + g.dt, s->laser, s->st);
+            launch_update_E<double>(F, g, h, false, s->st);
+            ph_end(s, PIC_PHASE_FIELDS);
+        } else {
+            float *F = (float *)s->F;
+            ph_begin(s);
+            launch_update_E<float>(F, g, h, true, s->st);
+            launch_update_B<float>(F, g, h, t0 + h, s->laser, s->st);
+            ph_end(s, PIC_PHASE_FIELDS);
+            ph_begin(s);
+            for (int i = 0; i < s->nsp; i++) {
+                SpeciesState &p = s->sp[i];
+                if (p.n_hi) s->prof_push++;
+                launch_push_f32(view32(s, i, p.cur), F, g, push_const(s, p), s->d_err, s->d_eabs, s->st);
+            }
+            ph_end(s, PIC_PHASE_PUSH);
+            ph_begin(s);
+            launch_fold<float>(F, g, s->st);
+            ph_end(s, PIC_PHASE_FOLD);
+            ph_begin(s);
+            launch_update_B<float>(F, g, h, t0 + g.dt, s->laser, s->st);
+            launch_update_E<float>(F, g, h, false, s->st);
+            ph_end(s, PIC_PHASE_FIELDS);
+        }
+        CK(cudaGetLastError());
+        s->step++;
+    }
+    return check_flags(s);
+}
+
+int pic_profile(pic_sim *s, int enable)
+{
+    if (!s) return PIC_ERR_ARG;
+    CK(cudaStreamSynchronize(s->st));
+    for (auto &m : s->marks) {
+        cudaEventDestroy(m.a);
+        cudaEventDestroy(m.b);
+    }
+    s->marks.clear();
+    for (int p = 0; p < PIC_NPHASE; p++) s->prof_launch[p] = 0;
+    s->prof_push = 0;
+    s->prof = enable != 0;
+    return PIC_OK;
+}
+
+int pic_profile_read(pic_sim *s, double *ms, int64_t *launches, int64_t *push_launches)
+{
+    if (!s) return PIC_ERR_ARG;
+    CK(cudaStreamSynchronize(s->st));
+    double acc[PIC_NPHASE] = {0, 0, 0, 0};
+    for (auto &m : s->marks) {
+        float t = 0.f;
+        cudaEventElapsedTime(&t, m.a, m.b);
+        acc[m.phase] += t;
+        cudaEventDestroy(m.a);
+        cudaEventDestroy(m.b);
+    }
+    s->marks.clear();
+    for (int p = 0; p < PIC_NPHASE; p++) {
+        if (ms) ms[p] = acc[p];
+        if (launches) launches[p] = s->prof_launch[p];
+        s->prof_launch[p] = 0;
+    }
+    if (push_launches) *push_launches = s->prof_push;
+    s->prof_push = 0;
+    return PIC_OK;
+}
+
+int pic_fields(pic_sim *s, int comp, double *host_out)
+{
+    if (!s) return PIC_ERR_ARG;
+    if (comp < PIC_EX || comp > PIC_RHO || !host_out) return fail(s, PIC_ERR_ARG, "pic_fields: bad component");
+    if (comp == PIC_RHO) {
+        int rc = compute_rho(s);
+        if (rc) return rc;
+        return copy_comp_out<double>(s, s->rho, host_out);
+    }
+    if (s->precision == PIC_PREC_FP64_PLAIN)
+        return copy_comp_out<double>(s, (const double *)s->F + comp * s->g.vol, host_out);
+    return copy_comp_out<float>(s, (const float *)s->F + comp * s->g.vol, host_out);
+}
+
+int64_t pic_particle_count(pic_sim *s, int sp)
+{
+    if (!s || sp < 0 || sp >= s->nsp) return -1;
+    long long n = 0;
+    if (read_count(s, sp, &n)) return -1;
+    return n;
+}
+
+int pic_get_particles(pic_sim *s, int sp, int64_t cap, int64_t *n, double *x, double *y, double *z, double *ux,
+                      double *uy, double *uz, uint8_t *alive)
+{
+    if (!s) return PIC_ERR_ARG;
+    if (sp < 0 || sp >= s->nsp || !n) return fail(s, PIC_ERR_ARG, "pic_get_particles: bad arguments");
+    long long cnt = 0;
+    int rc = read_count(s, sp, &cnt);
+    if (rc) return rc;
+    *n = cnt;
+    if (cnt > cap) return fail(s, PIC_ERR_CAPACITY, "pic_get_particles: %lld particles, room for %lld", cnt, (long long)cap);
+    if (cnt == 0) return PIC_OK;
+    SpeciesState &p = s->sp[sp];
+    double *dtmp = nullptr;
+    uint8_t *dal = nullptr;
+    CK(cudaMalloc(&dtmp, (size_t)cnt * 6 * sizeof(double)));
+    cudaError_t e = cudaMalloc(&dal, (size_t)cnt);
+    if (e != cudaSuccess) {
+        cudaFree(dtmp);
+        return fail(s, PIC_ERR_CUDA, "pic_get_particles: %s", cudaGetErrorString(e));
+    }
+    double *dx_[3] = {dtmp, dtmp + cnt, dtmp + 2 * cnt};
+    double *du_[3] = {dtmp + 3 * cnt, dtmp + 4 * cnt, dtmp + 5 * cnt};
+    if (s->precision == PIC_PREC_FP64_PLAIN) launch_unload_f64(view64(s, sp, p.cur), s->g, dx_, du_, dal, s->st);
+    else launch_unload_f32(view32(s, sp, p.cur), s->g, dx_, du_, dal, s->st);
+    e = cudaGetLastError();
+    double *hs[6] = {x, y, z, ux, uy, uz};
+    double *ds[6] = {dx_[0], dx_[1], dx_[2], du_[0], du_[1], du_[2]};
+    for (int q = 0; q < 6 && e == cudaSuccess; q++)
+        if (hs[q]) e = cudaMemcpyAsync(hs[q], ds[q], cnt * sizeof(double), cudaMemcpyDeviceToHost, s->st);
+    if (e == cudaSuccess && alive) e = cudaMemcpyAsync(alive, dal, cnt, cudaMemcpyDeviceToHost, s->st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s->st);
+    cudaFree(dtmp);
+    cudaFree(dal);
+    if (e != cudaSuccess) return fail(s, PIC_ERR_CUDA, "pic_get_particles: %s", cudaGetErrorString(e));
+    return PIC_OK;
+}
+
+int pic_get_cells(pic_sim *s, int sp, int64_t cap, uint32_t *cells, int *bits)
+{
+    if (!s) return PIC_ERR_ARG;
+    if (sp < 0 || sp >= s->nsp || !cells) return fail(s, PIC_ERR_ARG, "pic_get_cells: bad arguments");
+    long long cnt = 0;
+    int rc = read_count(s, sp, &cnt);
+    if (rc) return rc;
+    if (cnt > cap) return fail(s, PIC_ERR_CAPACITY, "pic_get_cells: capacity");
+    if (bits)
+        for (int d = 0; d < 3; d++) bits[d] = s->g.bits[d];
+    if (cnt == 0) return PIC_OK;
+    SpeciesState &p = s->sp[sp];
+    CK(cudaMemcpyAsync(cells, p.cell[p.cur], cnt * 4, cudaMemcpyDeviceToHost, s->st));
+    CK(cudaStreamSynchronize(s->st));
+    return PIC_OK;
+}
+
+int pic_gather(pic_sim *s, int sp, int64_t cap, double *out6)
+{
+    if (!s) return PIC_ERR_ARG;
+    if (sp < 0 || sp >= s->nsp || !out6) return fail(s, PIC_ERR_ARG, "pic_gather: bad arguments");
+    long long cnt = 0;
+    int rc = read_count(s, sp, &cnt);
+    if (rc) return rc;
+    if (cnt > cap) return fail(s, PIC_ERR_CAPACITY, "pic_gather: capacity");
+    if (cnt == 0) return PIC_OK;
+    SpeciesState &p = s->sp[sp];
+    double *d = nullptr;
+    CK(cudaMalloc(&d, (size_t)cnt * 6 * sizeof(double)));
+    if (s->precision == PIC_PREC_FP64_PLAIN)
+        launch_gather_f64(view64(s, sp, p.cur), (const double *)s->F, s->g, d, s->st);
+    else
+        launch_gather_f32(view32(s, sp, p.cur), (const float *)s->F, s->g, d, s->st);
+    cudaError_t e = cudaGetLastError();
+    if (e == cudaSuccess) e = cudaMemcpyAsync(out6, d, cnt * 6 * sizeof(double), cudaMemcpyDeviceToHost, s->st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s->st);
+    cudaFree(d);
+    if (e != cudaSuccess) return fail(s, PIC_ERR_CUDA, "pic_gather: %s", cudaGetErrorString(e));
+    return PIC_OK;
+}
+
+int pic_diagnostics(pic_sim *s, pic_diag *d)
+{
+    if (!s || !d) return PIC_ERR_ARG;
+    const Grid &g = s->g;
+    std::memset(d, 0, sizeof *d);
+    double dV = 1.0, vol = 1.0;
+    for (int a = 0; a < g.dim; a++) {
+        dV *= g.dx[a];
+        vol *= g.dx[a] * g.n[a];
+    }
+    double h[16] = {0};
+    // field energy
+    if (s->precision == PIC_PREC_FP64_PLAIN)
+        diag_field_energy<double>((const double *)s->F, g, s->diag_scratch, s->diag_out, s->st);
+    else
+        diag_field_energy<float>((const float *)s->F, g, s->diag_scratch, s->diag_out, s->st);
+    CK(cudaMemcpyAsync(h, s->diag_out, 2 * sizeof(double), cudaMemcpyDeviceToHost, s->st));
+    CK(cudaStreamSynchronize(s->st));
+    d->U_E = 0.5 * h[0] * dV;
+    d->U_B = 0.5 * h[1] * dV;
+    double charge = 0.0;
+    for (int i = 0; i < s->nsp; i++) {
+        SpeciesState &p = s->sp[i];
+        if (s->precision == PIC_PREC_FP64_PLAIN) diag_kinetic_f64(view64(s, i, p.cur), s->diag_scratch, s->diag_out, s->st);
+        else diag_kinetic_f32(view32(s, i, p.cur), s->diag_scratch, s->diag_out, s->st);
+        CK(cudaMemcpyAsync(h, s->diag_out, 2 * sizeof(double), cudaMemcpyDeviceToHost, s->st));
+        CK(cudaStreamSynchronize(s->st));
+        d->U_kin[i] = h[0] * p.w * p.m * dV;
+        d->n_alive[i] = (int64_t)llround(h[1]);
+        charge += p.q * p.w * h[1] * dV;
+    }
+    d->charge = charge + s->rho_bg * vol;
+    int rc = compute_rho(s);
+    if (rc) return rc;
+    if (s->precision == PIC_PREC_FP64_PLAIN)
+        diag_gauss<double>((const double *)s->F, s->rho, g, s->rho_bg, s->diag_scratch, s->diag_out, s->st);
+    else
+        diag_gauss<float>((const float *)s->F, s->rho, g, s->rho_bg, s->diag_scratch, s->diag_out, s->st);
+    CK(cudaMemcpyAsync(h, s->diag_out, sizeof(double), cudaMemcpyDeviceToHost, s->st));
+    CK(cudaMemcpyAsync(h + 1, s->d_eabs, sizeof(double), cudaMemcpyDeviceToHost, s->st));
+    CK(cudaStreamSynchronize(s->st));
+    CK(cudaGetLastError());
+    d->gauss_max = h[0];
+    d->E_absorbed = h[1];
+    d->step = s->step;
+    d->t = (double)s->step * g.dt;
+    bool finite = std::isfinite(d->U_E) && std::isfinite(d->U_B) && std::isfinite(d->gauss_max);
+    for (int i = 0; i < s->nsp; i++) finite = finite && std::isfinite(d->U_kin[i]);
+    if (!finite) return fail(s, PIC_ERR_NONFINITE, "pic_diagnostics: non-finite value");
+    return PIC_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,133 @@
+// pic_internal.cuh -- device-side layout and helpers of the GB300 PIC path.
+//
+// Field layout in HBM: one allocation per simulation holding the 9 field
+// components (Ex..Bz, Jx..Jz) back to back, each a padded box
+// [-G, N+G) per active axis (G = 4 ghost layers), x fastest, the x pitch
+// rounded up to 32 elements so that rows start on 128-byte boundaries and
+// the interior origin sits 16 bytes into the row.  Along periodic axes the
+// ghosts always hold copies of their periodic images (the solver computes
+// them directly); along absorbing axes the ghosts are zero except the one
+// layer of tangential B kept by the Mur condition.
+//
+// Particles: structure of arrays.  FP32 form: packed cell index (u32,
+// i | j << bx | k << (bx+by), 0xFFFFFFFF = dead), FP32 offset in [0,1) per
+// active axis, FP32 u per component.  FP64 form: absolute FP64 position per
+// active axis, FP64 u, plus the packed cell as sort key.
+#pragma once
+
+#include <cstdint>
+#include <cuda_runtime.h>
+
+namespace pic {
+
+constexpr int kGhost = 4;
+constexpr uint32_t kDead = 0xFFFFFFFFu;
+
+enum Comp { EX = 0, EY, EZ, BX, BY, BZ, JX, JY, JZ, NCOMP };
+enum Bc { PERIODIC = 0, ABSORB = 1 };
+
+// device error flags (bit mask, read by the host once per pic_step)
+enum ErrFlag : int { ERR_CFL = 1, ERR_NONFINITE = 2, ERR_CAPACITY = 4 };
+
+struct Grid {
+    int dim;
+    int n[3];          // cells per axis (1 on inactive axes)
+    int G[3];          // ghost layers per side (kGhost on active axes, 0 otherwise)
+    int ext[3];        // n + 2G
+    long long sy, sz;  // element strides of y and z
+    long long vol;     // elements per component (padded, rounded to 64)
+    long long origin;  // offset of interior (0,0,0)
+    int bc[3];
+    double dx[3];
+    double dt;
+    int bits[3];       // packed-cell bit widths
+    int tile_log2[3];  // log2 of tile edge per axis
+    int ntile[3];      // tiles per axis
+    long long ntiles;
+};
+
+struct Laser {
+    int on, pol;
+    double a0, waist, fwhm, t_peak, x_focus, yc, zc;
+};
+
+// staggering of component c along axis d: 1 = half node
+__host__ __device__ inline int stag(int c, int d)
+{
+    int b = c % 3;
+    return (c >= BX && c <= BZ) ? (d != b) : (d == b);
+}
+
+__host__ __device__ inline long long goff(const Grid &g, int i, int j, int k)
+{
+    return g.origin + (long long)k * g.sz + (long long)j * g.sy + i;
+}
+
+// packed cell helpers
+__host__ __device__ inline uint32_t pack_cell(const Grid &g, int i, int j, int k)
+{
+    return (uint32_t)i | ((uint32_t)j << g.bits[0]) | ((uint32_t)k << (g.bits[0] + g.bits[1]));
+}
+__host__ __device__ inline void unpack_cell(const Grid &g, uint32_t c, int &i, int &j, int &k)
+{
+    i = (int)(c & ((1u << g.bits[0]) - 1u));
+    j = g.bits[1] ? (int)((c >> g.bits[0]) & ((1u << g.bits[1]) - 1u)) : 0;
+    k = g.bits[2] ? (int)((c >> (g.bits[0] + g.bits[1])) & ((1u << g.bits[2]) - 1u)) : 0;
+}
+__host__ __device__ inline uint32_t tile_of(const Grid &g, int i, int j, int k)
+{
+    return (uint32_t)(((long long)(k >> g.tile_log2[2]) * g.ntile[1] + (j >> g.tile_log2[1])) * g.ntile[0] +
+                      (i >> g.tile_log2[0]));
+}
+
+// W_2 weights (the cell integral of the hat shape S_2, Sec. II.D): nodes
+// ic-1, ic, ic+1 for a particle at delta = X - ic in [-1/2, 1/2).
+template <typename R>
+__device__ __forceinline__ void w2(R delta, R *w)
+{
+    const R h = R(0.5);
+    R a = h - delta, b = h + delta;
+    w[0] = h * a * a;
+    w[1] = R(0.75) - delta * delta;
+    w[2] = h * b * b;
+}
+
+// Boris rotation (Eqs. (13)-(16)); E, B already multiplied by q_m dt / 2.
+template <typename R>
+__device__ __forceinline__ void boris(R &ux, R &uy, R &uz, R ex, R ey, R ez, R bx, R by, R bz)
+{
+    R umx = ux + ex, umy = uy + ey, umz = uz + ez;
+    R ginv = R(1) / sqrt(R(1) + umx * umx + umy * umy + umz * umz);
+    R tx = bx * ginv, ty = by * ginv, tz = bz * ginv;
+    R t2 = tx * tx + ty * ty + tz * tz;
+    R upx = umx + (umy * tz - umz * ty);
+    R upy = umy + (umz * tx - umx * tz);
+    R upz = umz + (umx * ty - umy * tx);
+    R f = R(2) / (R(1) + t2);
+    R sx = tx * f, sy = ty * f, sz = tz * f;
+    ux = umx + (upy * sz - upz * sy) + ex;
+    uy = umy + (upz * sx - upx * sz) + ey;
+    uz = umz + (upx * sy - upy * sx) + ez;
+}
+
+// 1/gamma: FP32 below u^2 = 1e8 (gamma ~ 1e4), FP64 above, where 1 + u^2
+// loses the 1 in FP32.
+__device__ __forceinline__ float inv_gamma(float ux, float uy, float uz)
+{
+    float u2 = ux * ux + uy * uy + uz * uz;
+    if (u2 < 1e8f) return 1.0f / sqrtf(1.0f + u2);
+    double d2 = (double)ux * ux + (double)uy * uy + (double)uz * uz;
+    return (float)(1.0 / sqrt(1.0 + d2));
+}
+__device__ __forceinline__ double inv_gamma(double ux, double uy, double uz)
+{
+    return 1.0 / sqrt(1.0 + ux * ux + uy * uy + uz * uz);
+}
+
+inline int div_up(long long a, long long b) { return (int)((a + b - 1) / b); }
+
+// host-side count of kernel launches issued by the library (profiling)
+extern long long g_launches;
+inline void note_launch(long long n = 1) { g_launches += n; }
+
+}  // namespace pic

@@ -1,0 +1,300 @@
+// sort.cu -- stable counting sort of particles by tile (the tile holding a
+// particle's cell), dead particles last, and the per-tile start offsets.
+//
+// The sort is a least-significant-digit radix sort of (tile key, index)
+// pairs with 8-bit digits.  Each pass is reduce-then-scan: per-block digit
+// histograms (4096 keys per block), one device-wide exclusive scan of the
+// (digit, block) counts, then a scatter in which every block walks its keys
+// in order, 256 at a time, ranking equal digits with warp match masks and a
+// per-warp prefix.  Every pass is stable, so the final permutation is the
+// one a stable sort by key gives, independent of scheduling.
+#include "sort.cuh"
+
+namespace pic {
+
+constexpr int kSortThreads = 256;
+constexpr int kSortRounds = 16;
+constexpr int kSortItems = kSortThreads * kSortRounds;  // keys per block
+constexpr int kScanItems = 4096;                        // per scan block (1024 threads x 4)
+
+__global__ void k_make_keys(const uint32_t *__restrict__ cell, const long long *__restrict__ dn, long long n,
+                            Grid g, uint32_t *key, uint32_t *val)
+{
+    long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    uint32_t c = i < *dn ? cell[i] : kDead;
+    uint32_t k;
+    if (c == kDead) k = (uint32_t)g.ntiles;
+    else {
+        int a, b, d;
+        unpack_cell(g, c, a, b, d);
+        k = tile_of(g, a, b, d);
+    }
+    key[i] = k;
+    val[i] = (uint32_t)i;
+}
+
+__global__ void __launch_bounds__(kSortThreads) k_radix_hist(const uint32_t *__restrict__ kin, long long n,
+                                                            int shift, uint32_t *counts, int nb)
+{
+    __shared__ uint32_t h[256];
+    int tid = threadIdx.x;
+    h[tid] = 0;
+    __syncthreads();
+    long long start = (long long)blockIdx.x * kSortItems;
+    for (int r = 0; r < kSortRounds; r++) {
+        long long i = start + r * kSortThreads + tid;
+        if (i < n) atomicAdd(&h[(kin[i] >> shift) & 255u], 1u);
+    }
+    __syncthreads();
+    counts[(long long)tid * nb + blockIdx.x] = h[tid];
+}
+
+__global__ void __launch_bounds__(kSortThreads) k_radix_scatter(const uint32_t *__restrict__ kin,
+                                                               const uint32_t *__restrict__ vin, uint32_t *kout,
+                                                               uint32_t *vout, long long n, int shift,
+                                                               const uint32_t *__restrict__ offs, int nb)
+{
+    __shared__ uint32_t base[256];
+    __shared__ uint32_t wc[kSortThreads / 32][256];
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    base[tid] = offs[(long long)tid * nb + blockIdx.x];
+#pragma unroll
+    for (int w = 0; w < kSortThreads / 32; w++) wc[w][tid] = 0;
+    __syncthreads();
+    const long long start = (long long)blockIdx.x * kSortItems;
+    const unsigned lt = (1u << lane) - 1u;
+    for (int r = 0; r < kSortRounds; r++) {
+        long long i = start + r * kSortThreads + tid;
+        bool valid = i < n;
+        uint32_t k = valid ? kin[i] : 0u, v = valid ? vin[i] : 0u;
+        uint32_t dg = valid ? ((k >> shift) & 255u) : 256u;
+        unsigned peers = __match_any_sync(0xffffffffu, dg);
+        uint32_t rank = __popc(peers & lt);
+        if (valid && lane == __ffs(peers) - 1) wc[warp][dg] = __popc(peers);
+        __syncthreads();
+        uint32_t run = 0;
+#pragma unroll
+        for (int w = 0; w < kSortThreads / 32; w++) {
+            uint32_t t = wc[w][tid];
+            wc[w][tid] = run;
+            run += t;
+        }
+        __syncthreads();
+        if (valid) {
+            uint32_t pos = base[dg] + wc[warp][dg] + rank;
+            kout[pos] = k;
+            vout[pos] = v;
+        }
+        __syncthreads();
+        base[tid] += run;
+#pragma unroll
+        for (int w = 0; w < kSortThreads / 32; w++) wc[w][tid] = 0;
+        __syncthreads();
+    }
+}
+
+// ---------------------------------------------------------------------
+// device-wide exclusive scan of u32 (reduce, scan of block sums, downsweep)
+// ---------------------------------------------------------------------
+__device__ __forceinline__ uint32_t block_excl_scan_1024(uint32_t v, uint32_t *sh, uint32_t &total)
+{
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    uint32_t x = v;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        uint32_t y = __shfl_up_sync(0xffffffffu, x, o);
+        if (lane >= o) x += y;
+    }
+    if (lane == 31) sh[warp] = x;
+    __syncthreads();
+    if (warp == 0) {
+        uint32_t s = sh[lane];
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            uint32_t y = __shfl_up_sync(0xffffffffu, s, o);
+            if (lane >= o) s += y;
+        }
+        sh[lane] = s;
+    }
+    __syncthreads();
+    total = sh[31];
+    uint32_t before = warp ? sh[warp - 1] : 0u;
+    uint32_t r = before + x - v;
+    __syncthreads();
+    return r;
+}
+
+__global__ void __launch_bounds__(1024) k_scan_reduce(const uint32_t *__restrict__ in, long long m, uint32_t *sums)
+{
+    __shared__ uint32_t sh[32];
+    long long b0 = (long long)blockIdx.x * kScanItems + threadIdx.x * 4;
+    uint32_t s = 0;
+#pragma unroll
+    for (int q = 0; q < 4; q++)
+        if (b0 + q < m) s += in[b0 + q];
+    uint32_t tot;
+    block_excl_scan_1024(s, sh, tot);
+    if (threadIdx.x == 0) sums[blockIdx.x] = tot;
+}
+
+__global__ void __launch_bounds__(1024) k_scan_down(const uint32_t *__restrict__ in, long long m, uint32_t *out,
+                                                   const uint32_t *__restrict__ block_off)
+{
+    __shared__ uint32_t sh[32];
+    long long b0 = (long long)blockIdx.x * kScanItems + threadIdx.x * 4;
+    uint32_t v[4], s = 0;
+#pragma unroll
+    for (int q = 0; q < 4; q++) {
+        v[q] = b0 + q < m ? in[b0 + q] : 0u;
+        s += v[q];
+    }
+    uint32_t tot;
+    uint32_t run = block_excl_scan_1024(s, sh, tot) + (block_off ? block_off[blockIdx.x] : 0u);
+#pragma unroll
+    for (int q = 0; q < 4; q++) {
+        if (b0 + q < m) out[b0 + q] = run;
+        run += v[q];
+    }
+}
+
+size_t scan_scratch_words(long long m)
+{
+    size_t w = 0;
+    while (m > kScanItems) {
+        m = (m + kScanItems - 1) / kScanItems;
+        w += (size_t)m + 32;
+    }
+    return w + 32;
+}
+
+// exclusive scan of m words, in may equal out
+void scan_exclusive(const uint32_t *in, uint32_t *out, long long m, uint32_t *scratch, cudaStream_t st)
+{
+    if (m <= 0) return;
+    if (m <= kScanItems) {
+        note_launch();
+        k_scan_down<<<1, 1024, 0, st>>>(in, m, out, nullptr);
+        return;
+    }
+    long long nb = (m + kScanItems - 1) / kScanItems;
+    uint32_t *sums = scratch;
+    note_launch(2);
+    k_scan_reduce<<<(int)nb, 1024, 0, st>>>(in, m, sums);
+    scan_exclusive(sums, sums, nb, scratch + nb + 32, st);
+    k_scan_down<<<(int)nb, 1024, 0, st>>>(in, m, out, sums);
+}
+
+__global__ void k_tile_starts(const uint32_t *__restrict__ skey, long long n, long long ntiles, uint32_t *starts,
+                              long long *dcount)
+{
+    long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i > n) return;
+    long long lo = i == 0 ? 0 : (long long)skey[i - 1] + 1;
+    long long hi = i == n ? ntiles : (long long)skey[i];
+    for (long long t = lo; t <= hi && t <= ntiles; t++) {
+        starts[t] = (uint32_t)i;
+        if (t == ntiles) *dcount = i;
+    }
+}
+
+// ---------------------------------------------------------------------
+// host driver
+// ---------------------------------------------------------------------
+size_t sort_scratch_bytes(long long cap)
+{
+    long long nb = (cap + kSortItems - 1) / kSortItems;
+    size_t w = 4 * (size_t)cap + 256 * (size_t)nb + scan_scratch_words(256 * nb) + 256;
+    return w * sizeof(uint32_t);
+}
+
+int radix_passes(long long ntiles)
+{
+    int bits = 0;
+    while ((1ll << bits) <= ntiles) bits++;
+    return (bits + 7) / 8;
+}
+
+// sorts the first n entries (entries at or past *dcount count as dead);
+// returns the device pointer of the permutation (new -> old), the sorted
+// keys, and updates starts[0..ntiles] and *dcount (live particles)
+void sort_by_tile(const uint32_t *cell, long long n, const long long *dcount_in, const Grid &g, void *scratch,
+                  uint32_t *starts, long long *dcount_out, const uint32_t **perm, const uint32_t **skeys,
+                  cudaStream_t st)
+{
+    uint32_t *w = (uint32_t *)scratch;
+    long long cap_n = n;
+    uint32_t *kA = w, *kB = w + cap_n, *vA = w + 2 * cap_n, *vB = w + 3 * cap_n;
+    long long nb = (n + kSortItems - 1) / kSortItems;
+    uint32_t *counts = w + 4 * cap_n;
+    uint32_t *sscr = counts + 256 * nb + 64;
+    if (n > 0) {
+        note_launch(1 + 2 * radix_passes(g.ntiles));
+        k_make_keys<<<div_up(n, 256), 256, 0, st>>>(cell, dcount_in, n, g, kA, vA);
+        int passes = radix_passes(g.ntiles);
+        for (int p = 0; p < passes; p++) {
+            k_radix_hist<<<(int)nb, kSortThreads, 0, st>>>(kA, n, 8 * p, counts, (int)nb);
+            scan_exclusive(counts, counts, 256 * nb, sscr, st);
+            k_radix_scatter<<<(int)nb, kSortThreads, 0, st>>>(kA, vA, kB, vB, n, 8 * p, counts, (int)nb);
+            uint32_t *t = kA; kA = kB; kB = t;
+            t = vA; vA = vB; vB = t;
+        }
+    }
+    note_launch();
+    k_tile_starts<<<div_up(n + 1, 256), 256, 0, st>>>(kA, n, g.ntiles, starts, dcount_out);
+    *perm = vA;
+    *skeys = kA;
+}
+
+// ---------------------------------------------------------------------
+// apply the permutation to the particle arrays (new[i] = old[perm[i]])
+// ---------------------------------------------------------------------
+template <typename T>
+__device__ __forceinline__ void mv(const T *s, T *d, uint32_t from, long long to)
+{
+    if (s) d[to] = s[from];
+}
+
+__global__ void k_permute_f32(PartF32 src, PartF32 dst, const uint32_t *__restrict__ perm,
+                              const long long *__restrict__ dcount, int dim)
+{
+    long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= *dcount) return;
+    uint32_t a = perm[i];
+    dst.cell[i] = src.cell[a];
+    for (int d = 0; d < dim; d++) dst.off[d][i] = src.off[d][a];
+    dst.u[0][i] = src.u[0][a];
+    dst.u[1][i] = src.u[1][a];
+    dst.u[2][i] = src.u[2][a];
+}
+
+__global__ void k_permute_f64(PartF64 src, PartF64 dst, const uint32_t *__restrict__ perm,
+                              const long long *__restrict__ dcount, int dim)
+{
+    long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= *dcount) return;
+    uint32_t a = perm[i];
+    dst.cell[i] = src.cell[a];
+    for (int d = 0; d < dim; d++) dst.x[d][i] = src.x[d][a];
+    dst.u[0][i] = src.u[0][a];
+    dst.u[1][i] = src.u[1][a];
+    dst.u[2][i] = src.u[2][a];
+}
+
+void launch_permute_f32(const PartF32 &src, const PartF32 &dst, const uint32_t *perm, const long long *dcount,
+                        long long n, int dim, cudaStream_t st)
+{
+    if (n == 0) return;
+    note_launch();
+    k_permute_f32<<<div_up(n, 256), 256, 0, st>>>(src, dst, perm, dcount, dim);
+}
+
+void launch_permute_f64(const PartF64 &src, const PartF64 &dst, const uint32_t *perm, const long long *dcount,
+                        long long n, int dim, cudaStream_t st)
+{
+    if (n == 0) return;
+    note_launch();
+    k_permute_f64<<<div_up(n, 256), 256, 0, st>>>(src, dst, perm, dcount, dim);
+}
+
+}  // namespace pic

@@ -1,0 +1,19 @@
+// sort.cuh -- stable tile sort (sort.cu).
+#pragma once
+#include "pic_internal.cuh"
+#include "push.cuh"
+
+namespace pic {
+
+size_t sort_scratch_bytes(long long cap);
+size_t scan_scratch_words(long long m);
+void scan_exclusive(const uint32_t *in, uint32_t *out, long long m, uint32_t *scratch, cudaStream_t st);
+void sort_by_tile(const uint32_t *cell, long long n, const long long *dcount_in, const Grid &g, void *scratch,
+                  uint32_t *starts, long long *dcount_out, const uint32_t **perm, const uint32_t **skeys,
+                  cudaStream_t st);
+void launch_permute_f32(const PartF32 &src, const PartF32 &dst, const uint32_t *perm, const long long *dcount,
+                        long long n, int dim, cudaStream_t st);
+void launch_permute_f64(const PartF64 &src, const PartF64 &dst, const uint32_t *perm, const long long *dcount,
+                        long long n, int dim, cudaStream_t st);
+
+}  // namespace pic

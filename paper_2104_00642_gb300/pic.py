@@ -1,0 +1,280 @@
+"""Python binding of the C ABI in ``include/pic.h`` (argument marshalling only).
+
+Every step of the PIC method runs in the CUDA kernels of ``libpic.so``; this
+module only converts numpy arrays to pointers and error codes to exceptions.
+There is no CPU fallback: when the library is missing or no GPU is present,
+calls raise :class:`PicError`.
+
+Names follow the C ABI: :func:`pic_create`, :meth:`Sim.pic_load_particles`,
+:meth:`Sim.pic_step`, :meth:`Sim.pic_fields`, :meth:`Sim.pic_diagnostics` ...
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libpic.so")
+
+PIC_OK = 0
+ERRORS = {-1: "PIC_ERR_ARG", -2: "PIC_ERR_CFL", -3: "PIC_ERR_CUDA", -4: "PIC_ERR_CAPACITY",
+          -5: "PIC_ERR_NONFINITE", -6: "PIC_ERR_NOMEM", -7: "PIC_ERR_STATE"}
+PERIODIC, ABSORB = 0, 1
+FP32_CELLOFF, FP64_PLAIN = 0, 1
+EX, EY, EZ, BX, BY, BZ, JX, JY, JZ, RHO = range(10)
+MAX_SPECIES = 8
+
+# every symbol include/pic.h declares
+EXPORTS = ["pic_create", "pic_destroy", "pic_last_error", "pic_load_particles", "pic_set_laser",
+           "pic_set_field", "pic_step", "pic_fields", "pic_particle_count", "pic_get_particles",
+           "pic_get_cells", "pic_diagnostics", "pic_gather", "pic_sync", "pic_profile", "pic_profile_read"]
+PHASES = ("sort", "fields", "push", "fold")
+
+
+class PicError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__(f"{ERRORS.get(code, code)}: {msg}")
+        self.code = code
+
+
+class pic_grid(C.Structure):
+    _fields_ = [("dim", C.c_int), ("n", C.c_int64 * 3), ("dx", C.c_double * 3), ("bc", C.c_int * 3),
+                ("order", C.c_int)]
+
+
+class pic_species(C.Structure):
+    _fields_ = [("q", C.c_double), ("m", C.c_double), ("w", C.c_double), ("capacity", C.c_int64)]
+
+
+class pic_options(C.Structure):
+    _fields_ = [("precision", C.c_int), ("sort_interval", C.c_int), ("tile", C.c_int * 3),
+                ("rho_bg", C.c_double), ("stream", C.c_void_p)]
+
+
+class pic_laser(C.Structure):
+    _fields_ = [("a0", C.c_double), ("waist", C.c_double), ("fwhm", C.c_double), ("t_peak", C.c_double),
+                ("x_focus", C.c_double), ("yc", C.c_double), ("zc", C.c_double), ("pol", C.c_int)]
+
+
+class pic_diag(C.Structure):
+    _fields_ = [("step", C.c_int64), ("t", C.c_double), ("U_E", C.c_double), ("U_B", C.c_double),
+                ("U_kin", C.c_double * MAX_SPECIES), ("charge", C.c_double), ("gauss_max", C.c_double),
+                ("E_absorbed", C.c_double), ("n_alive", C.c_int64 * MAX_SPECIES)]
+
+
+_lib = None
+
+
+def load_library(path: str = LIB_PATH):
+    """Load libpic.so (it must have been built: see ``build.py``)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(path):
+        raise PicError(-3, f"{path} is not built (run paper_2104_00642_gb300/build.py)")
+    L = C.CDLL(path)
+    P, I, D, I64 = C.c_void_p, C.c_int, C.c_double, C.c_int64
+    L.pic_create.argtypes = [C.POINTER(pic_grid), D, C.POINTER(pic_species), I, C.POINTER(pic_options),
+                             C.POINTER(P)]
+    L.pic_create.restype = I
+    L.pic_destroy.argtypes = [P]
+    L.pic_destroy.restype = None
+    L.pic_last_error.argtypes = [P]
+    L.pic_last_error.restype = C.c_char_p
+    L.pic_load_particles.argtypes = [P, I, I64, P, P, P, P, P, P]
+    L.pic_load_particles.restype = I
+    L.pic_set_laser.argtypes = [P, C.POINTER(pic_laser)]
+    L.pic_set_laser.restype = I
+    L.pic_set_field.argtypes = [P, I, P]
+    L.pic_set_field.restype = I
+    L.pic_step.argtypes = [P, I64]
+    L.pic_step.restype = I
+    L.pic_fields.argtypes = [P, I, P]
+    L.pic_fields.restype = I
+    L.pic_particle_count.argtypes = [P, I]
+    L.pic_particle_count.restype = I64
+    L.pic_get_particles.argtypes = [P, I, I64, C.POINTER(I64), P, P, P, P, P, P, P]
+    L.pic_get_particles.restype = I
+    L.pic_get_cells.argtypes = [P, I, I64, P, P]
+    L.pic_get_cells.restype = I
+    L.pic_diagnostics.argtypes = [P, C.POINTER(pic_diag)]
+    L.pic_diagnostics.restype = I
+    L.pic_gather.argtypes = [P, I, I64, P]
+    L.pic_gather.restype = I
+    L.pic_sync.argtypes = [P]
+    L.pic_sync.restype = I
+    L.pic_profile.argtypes = [P, I]
+    L.pic_profile.restype = I
+    L.pic_profile_read.argtypes = [P, P, P, P]
+    L.pic_profile_read.restype = I
+    _lib = L
+    return L
+
+
+def _p(a):
+    return None if a is None else a.ctypes.data_as(C.c_void_p)
+
+
+def _f64(a):
+    return None if a is None else np.ascontiguousarray(a, dtype=np.float64)
+
+
+class Sim:
+    """One simulation (a ``pic_sim*``)."""
+
+    def __init__(self, dim, n, dx, dt, species, bc=(PERIODIC, PERIODIC, PERIODIC), precision=FP32_CELLOFF,
+                 sort_interval=0, tile=(0, 0, 0), rho_bg=0.0, stream=None):
+        L = load_library()
+        g = pic_grid()
+        g.dim = int(dim)
+        for d in range(3):
+            g.n[d] = int(n[d]) if d < len(n) else 1
+            g.dx[d] = float(dx[d]) if d < len(dx) else 1.0
+            g.bc[d] = int(bc[d]) if d < len(bc) else PERIODIC
+        g.order = 2
+        sp = (pic_species * max(1, len(species)))()
+        for i, s in enumerate(species):
+            sp[i].q, sp[i].m, sp[i].w, sp[i].capacity = float(s[0]), float(s[1]), float(s[2]), int(s[3])
+        o = pic_options()
+        o.precision = int(precision)
+        o.sort_interval = int(sort_interval)
+        for d in range(3):
+            o.tile[d] = int(tile[d]) if d < len(tile) else 0
+        o.rho_bg = float(rho_bg)
+        o.stream = stream
+        h = C.c_void_p()
+        rc = L.pic_create(C.byref(g), float(dt), sp, len(species), C.byref(o), C.byref(h))
+        if rc != PIC_OK:
+            raise PicError(rc, L.pic_last_error(None).decode())
+        self._h = h
+        self.dim = int(dim)
+        self.n = [int(g.n[d]) for d in range(3)]
+        self.bc = [int(g.bc[d]) for d in range(3)]
+        self.dt = float(dt)
+        self.nsp = len(species)
+        self.precision = precision
+
+    # -- lifetime ---------------------------------------------------------
+    def close(self):
+        h = getattr(self, "_h", None)
+        if h:
+            load_library().pic_destroy(h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+    def _check(self, rc):
+        if rc != PIC_OK:
+            raise PicError(rc, load_library().pic_last_error(self._h).decode())
+
+    # -- C ABI --------------------------------------------------------------
+    def box(self):
+        m = [1, 1, 1]
+        for d in range(self.dim):
+            m[d] = self.n[d] + (1 if self.bc[d] == ABSORB else 0)
+        return (m[2], m[1], m[0])
+
+    def pic_load_particles(self, sp, x, y, z, ux, uy, uz):
+        arrs = [_f64(a) for a in (x, y, z, ux, uy, uz)]
+        n = len(arrs[3])
+        self._check(load_library().pic_load_particles(self._h, int(sp), n, *[_p(a) for a in arrs]))
+
+    def pic_set_laser(self, a0, waist, fwhm, t_peak, x_focus, yc=0.0, zc=0.0, pol=0):
+        lz = pic_laser(a0, waist, fwhm, t_peak, x_focus, yc, zc, pol)
+        self._check(load_library().pic_set_laser(self._h, C.byref(lz)))
+
+    def pic_set_field(self, comp, arr):
+        a = _f64(np.broadcast_to(arr, self.box()))
+        self._check(load_library().pic_set_field(self._h, int(comp), _p(a)))
+
+    def pic_step(self, nsteps=1):
+        self._check(load_library().pic_step(self._h, int(nsteps)))
+
+    def pic_fields(self, comp):
+        out = np.zeros(self.box())
+        self._check(load_library().pic_fields(self._h, int(comp), _p(out)))
+        return out
+
+    def pic_particle_count(self, sp):
+        n = load_library().pic_particle_count(self._h, int(sp))
+        if n < 0:
+            self._check(-1)
+        return n
+
+    def pic_get_particles(self, sp):
+        n = self.pic_particle_count(sp)
+        out = {k: np.zeros(n) for k in ("x", "y", "z", "ux", "uy", "uz")}
+        alive = np.zeros(n, dtype=np.uint8)
+        nn = C.c_int64()
+        self._check(load_library().pic_get_particles(self._h, int(sp), n, C.byref(nn),
+                                                     *[_p(out[k]) for k in ("x", "y", "z", "ux", "uy", "uz")],
+                                                     _p(alive)))
+        out["alive"] = alive
+        return out
+
+    def pic_get_cells(self, sp):
+        n = self.pic_particle_count(sp)
+        cells = np.zeros(n, dtype=np.uint32)
+        bits = (C.c_int * 3)()
+        self._check(load_library().pic_get_cells(self._h, int(sp), n, _p(cells), bits))
+        return cells, tuple(bits)
+
+    def pic_gather(self, sp):
+        n = self.pic_particle_count(sp)
+        out = np.zeros((n, 6))
+        self._check(load_library().pic_gather(self._h, int(sp), n, _p(out)))
+        return out
+
+    def pic_diagnostics(self):
+        d = pic_diag()
+        self._check(load_library().pic_diagnostics(self._h, C.byref(d)))
+        return {"step": d.step, "t": d.t, "U_E": d.U_E, "U_B": d.U_B, "U_kin": list(d.U_kin[: self.nsp]),
+                "charge": d.charge, "gauss_max": d.gauss_max, "E_absorbed": d.E_absorbed,
+                "n_alive": list(d.n_alive[: self.nsp])}
+
+    def pic_sync(self):
+        self._check(load_library().pic_sync(self._h))
+
+    def pic_profile(self, enable=True):
+        self._check(load_library().pic_profile(self._h, int(bool(enable))))
+
+    def pic_profile_read(self):
+        ms = np.zeros(len(PHASES))
+        ln = np.zeros(len(PHASES), dtype=np.int64)
+        pl = C.c_int64()
+        self._check(load_library().pic_profile_read(self._h, _p(ms), _p(ln), C.byref(pl)))
+        return {"ms": dict(zip(PHASES, ms.tolist())), "launches": dict(zip(PHASES, ln.tolist())),
+                "push_launches": int(pl.value)}
+
+
+def pic_create(dim, n, dx, dt, species, **kw) -> Sim:
+    """pic_create(grid, dt, species): species is a list of (q, m, w, capacity)."""
+    return Sim(dim, n, dx, dt, species, **kw)
+
+
+def from_workload(w, precision=FP32_CELLOFF, sort_interval=0, capacity_scale=1.0, load=True, stream=None,
+                  tile=None) -> Sim:
+    """Create a simulation for a :class:`workloads.Workload` and load its particles."""
+    sp = [(s.q, s.m, s.w, max(1, int(s.capacity * capacity_scale))) for s in w.species]
+    t = tile if tile is not None else tuple(w.tile)
+    sim = Sim(w.dim, w.n, w.dx, w.dt, sp, bc=w.bc, precision=precision, sort_interval=sort_interval, tile=t,
+              rho_bg=w.rho_bg, stream=stream)
+    if w.laser is not None:
+        L = w.laser
+        sim.pic_set_laser(L.a0, L.waist, L.fwhm, L.t_peak, L.x_focus, L.yc, L.zc, L.pol)
+    if load:
+        for i, s in enumerate(w.species):
+            sim.pic_load_particles(i, s.x, s.y if w.dim > 1 else None, s.z if w.dim > 2 else None, s.ux, s.uy, s.uz)
+    return sim

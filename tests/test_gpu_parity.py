@@ -1,0 +1,242 @@
+"""Parity of the CUDA path (through the C ABI) with the FP64 CPU oracle.
+
+Tolerances (parity contract): single-step gathered fields, momenta and
+currents within 1e-5 relative in FP32 -- relative to the magnitude of the
+summed terms (sum W|F| for a gathered field, |u| for a momentum, |q w| dx/dt
+times the particles whose window covers a node for a current); cell indices
+and sort permutations bit-exact (cells: for particles not within 2^-18 of a
+face, whose FP32 and FP64 floors may legitimately differ); energy histories
+within 1e-3 of the run's maximum.  The FP64 plain form must agree to 1e-10.
+"""
+import math
+
+import numpy as np
+import pytest
+
+from oracle import oracle as O
+from paper_2104_00642_gb300 import pic, workloads as W
+from tests.helpers import boundary_ambiguous, oracle_from_workload, random_state, window_scale
+
+pytestmark = pytest.mark.gpu
+
+PRECS = [pic.FP32_CELLOFF, pic.FP64_PLAIN]
+TOL = {pic.FP32_CELLOFF: 1e-5, pic.FP64_PLAIN: 1e-10}
+GRIDS = {1: ((37,), (0.1,)), 2: ((20, 13), (0.1, 0.12)), 3: ((12, 10, 9), (0.1, 0.12, 0.11))}
+
+
+def _dt(dx, frac=0.9):
+    return frac / math.sqrt(sum(1.0 / d ** 2 for d in dx))
+
+
+def _make_pair(dim, prec, seed, nppc=3, fields=True, sort_interval=0, umax=0.5):
+    n, dx = GRIDS[dim]
+    w, F = random_state(dim, n, dx, _dt(dx), nppc, seed, umax=umax, fields=fields)
+    sim = pic.from_workload(w, precision=prec, sort_interval=sort_interval)
+    o = oracle_from_workload(w, sort_interval=sort_interval)
+    if F is not None:
+        for c in range(9):
+            sim.pic_set_field(c, F[c])
+            o.set_field(c, F[c])
+    return w, F, sim, o
+
+
+@pytest.mark.parametrize("prec", PRECS)
+@pytest.mark.parametrize("dim", [1, 2, 3])
+def test_gather_matches_oracle(dim, prec):
+    w, F, sim, o = _make_pair(dim, prec, seed=100 + dim)
+    got = sim.pic_gather(0)
+    s = w.species[0]
+    oabs = oracle_from_workload(w)
+    for c in range(6):
+        oabs.set_field(c, np.abs(F[c]))
+    for p in range(s.n):
+        x = (s.x[p], s.y[p], s.z[p])
+        ref = o.gather(x[:dim])
+        scale = oabs.gather(x[:dim])
+        assert np.all(np.abs(got[p] - ref) <= TOL[prec] * scale + 1e-300), (p, got[p], ref)
+
+
+@pytest.mark.parametrize("prec", PRECS)
+@pytest.mark.parametrize("dim", [1, 2, 3])
+def test_one_step_matches_oracle(dim, prec):
+    w, F, sim, o = _make_pair(dim, prec, seed=200 + dim)
+    sim.pic_step(1)
+    o.step(1)
+    tol = TOL[prec]
+    pg, po = sim.pic_get_particles(0), o.particles(0)
+    keys = ("x", "y", "z")
+    for d in range(dim):
+        assert np.max(np.abs(pg[keys[d]] - po[keys[d]])) <= 10 * tol * w.dx[d]
+    for k in ("ux", "uy", "uz"):
+        umag = np.sqrt(po["ux"] ** 2 + po["uy"] ** 2 + po["uz"] ** 2)
+        assert np.all(np.abs(pg[k] - po[k]) <= tol * umag + 1e-2 * tol)
+    # cell indices: bit-exact away from faces
+    cells, bits = sim.pic_get_cells(0)
+    amb = np.zeros(len(cells), dtype=bool)
+    for d in range(dim):
+        ref_c = np.floor(po[keys[d]] / w.dx[d]).astype(np.int64)
+        got_c = (cells.astype(np.int64) >> sum(bits[:d])) & ((1 << bits[d]) - 1)
+        a = boundary_ambiguous(po[keys[d]], w.dx[d])
+        amb |= a
+        assert np.array_equal(got_c[~a], ref_c[~a])
+    assert amb.sum() <= max(2, 1e-3 * len(cells))
+    # current: relative to the per-node scale of the summed terms
+    pre = o.particles(0)  # positions after the step: windows overlap the pre-step ones within 1 cell
+    for c, ax in ((pic.JX, 0), (pic.JY, 1), (pic.JZ, 2)):
+        scale = window_scale(pre, w, dim, ax)
+        dj = np.abs(sim.pic_fields(c) - o.field(c))
+        assert np.all(dj <= tol * scale + 1e-30), (c, dj.max(), scale.max())
+    jmax = max(window_scale(pre, w, dim, a).max() for a in range(3))
+    fmax = max(np.abs(o.field(c)).max() for c in range(6))
+    for c in range(6):
+        assert np.max(np.abs(sim.pic_fields(c) - o.field(c))) <= tol * (2 * fmax + w.dt * jmax)
+
+
+@pytest.mark.parametrize("prec", PRECS)
+@pytest.mark.parametrize("dim", [2, 3])
+def test_sort_permutation_bit_exact(dim, prec):
+    """Stable counting sort by tile: the order equals the oracle's (itself
+    pinned to numpy's stable argsort) on a ragged multi-tile grid."""
+    n = (40, 21, 1) if dim == 2 else (20, 12, 9)
+    dx = (0.1, 0.1, 0.1)
+    tile = (16, 8, 1) if dim == 2 else (8, 4, 4)
+    rng = np.random.default_rng(7 + dim)
+    N = 3000
+    xs = []
+    for d in range(3):
+        if d < dim:
+            c = rng.integers(0, n[d], N)
+            xs.append((c + rng.uniform(0.01, 0.99, N)) * dx[d])
+        else:
+            xs.append(np.zeros(N))
+    ux = np.arange(N) * 2.0 ** -20
+    uy = rng.uniform(-0.3, 0.3, N)
+    uz = rng.uniform(-0.3, 0.3, N)
+    sp = W.Species("e", -1.0, 1.0, 0.1, xs[0], xs[1], xs[2], ux, uy, uz, capacity=N)
+    w = W.Workload("sort", dim, n, dx, 0.03, (0, 0, 0), [sp], 1, tile=tile)
+    sim = pic.from_workload(w, precision=prec, sort_interval=1)
+    o = oracle_from_workload(w, sort_interval=1)
+    sim.pic_step(1)
+    o.step(1)
+    g_order = np.rint(sim.pic_get_particles(0)["ux"] * 2 ** 20).astype(np.int64)
+    o_order = np.rint(o.particles(0)["ux"] * 2 ** 20).astype(np.int64)
+    assert np.array_equal(g_order, o_order)
+    assert not np.array_equal(g_order, np.arange(N))
+
+
+@pytest.mark.parametrize("prec", PRECS)
+def test_absorbed_particles_are_dropped_in_order(prec):
+    """Absorbing faces: leaving particles die, their energy is tallied, and
+    the next sort drops them keeping the survivors' order."""
+    n, dx = (64,), (0.1,)
+    rng = np.random.default_rng(3)
+    N = 600
+    x = rng.uniform(0.0, 6.4, N)
+    ux = rng.uniform(-3.0, 3.0, N)
+    z = np.zeros(N)
+    sp = W.Species("e", -1.0, 1.0, 0.05, x, z, z, ux, rng.uniform(-1, 1, N), z.copy(), capacity=N)
+    w = W.Workload("absorb", 1, (64, 1, 1), (0.1, 1, 1), 0.09, (W.ABSORB, 0, 0), [sp], 1, tile=(16, 1, 1))
+    sim = pic.from_workload(w, precision=prec, sort_interval=4)
+    o = oracle_from_workload(w, sort_interval=4)
+    sim.pic_step(9)
+    o.step(9)
+    pg, po = sim.pic_get_particles(0), o.particles(0)
+    assert len(pg["x"]) == len(po["x"]) < N
+    assert np.array_equal(pg["alive"], po["alive"])
+    live = po["alive"] == 1
+    assert np.max(np.abs(pg["x"][live] - po["x"][live])) < 1e-4
+    assert np.max(np.abs(pg["ux"] - po["ux"])) < 1e-4
+    dg, do = sim.pic_diagnostics(), o.diagnostics()
+    assert abs(dg["E_absorbed"] - do["E_absorbed"]) <= 1e-5 * do["E_absorbed"]
+    assert do["E_absorbed"] > 0
+
+
+@pytest.fixture(scope="module")
+def langmuir_oracle():
+    w = W.langmuir_1d()
+    o = oracle_from_workload(w)
+    hist = []
+    for st in range(0, w.steps + 1, 50):
+        if st:
+            o.step(50)
+        d = o.diagnostics()
+        hist.append((d["U_E"], d["U_kin"][0]))
+        if st == 50:
+            ex = o.field(O.EX)[0, 0]
+            r50 = (ex - np.roll(ex, 1)) / w.dx[0] - o.rho()[0, 0] - w.rho_bg
+    ex = o.field(O.EX)[0, 0]
+    r_end = (ex - np.roll(ex, 1)) / w.dx[0] - o.rho()[0, 0] - w.rho_bg
+    return w, np.array(hist), r50, r_end
+
+
+@pytest.mark.parametrize("prec", PRECS)
+def test_langmuir_energy_history_and_continuity(langmuir_oracle, prec):
+    w, ref, r50_o, rend_o = langmuir_oracle
+    sim = pic.from_workload(w, precision=prec)
+    got = []
+    for st in range(0, w.steps + 1, 50):
+        if st:
+            sim.pic_step(50)
+        d = sim.pic_diagnostics()
+        got.append((d["U_E"], d["U_kin"][0]))
+        if st == 50:
+            ex = sim.pic_fields(pic.EX)[0, 0]
+            r50 = (ex - np.roll(ex, 1)) / w.dx[0] - sim.pic_fields(pic.RHO)[0, 0] - w.rho_bg
+    got = np.array(got)
+    for c in range(2):
+        assert np.max(np.abs(got[:, c] - ref[:, c])) <= 1e-3 * ref[:, c].max()
+    ex = sim.pic_fields(pic.EX)[0, 0]
+    rend = (ex - np.roll(ex, 1)) / w.dx[0] - sim.pic_fields(pic.RHO)[0, 0] - w.rho_bg
+    # Gauss residual stays at its value after the start-up step (charge conservation)
+    drift = np.max(np.abs(rend - r50))
+    assert drift <= (1e-11 if prec == pic.FP64_PLAIN else 2e-5), drift
+
+
+@pytest.mark.parametrize("prec", PRECS)
+def test_laser_vacuum_fields(prec):
+    wl = W.vacuum_pulse_1d(n_cells=512, steps=900)
+    sim = pic.from_workload(wl, precision=prec)
+    o = oracle_from_workload(wl)
+    for _ in range(3):
+        sim.pic_step(300)
+        o.step(300)
+        for c in (pic.EY, pic.BZ):
+            err = np.max(np.abs(sim.pic_fields(c) - o.field(c)))
+            assert err <= (1e-10 if prec == pic.FP64_PLAIN else 2e-4) * wl.laser.a0, (c, err)
+
+
+@pytest.mark.parametrize("prec", PRECS)
+def test_circular_laser_2d_vacuum(prec):
+    """CP Gaussian beam through a 2D absorbing/periodic box vs the oracle."""
+    dx = 2 * math.pi / 16
+    L = W.Laser(a0=2.0, waist=6.0, fwhm=12.0, t_peak=20.0, x_focus=40 * dx, yc=32 * dx, pol=1)
+    w = W.Workload("cp2d", 2, (96, 64, 1), (dx, dx, 1.0), 0.9 * dx / math.sqrt(2), (W.ABSORB, 0, 0), [], 1,
+                   laser=L, tile=(16, 16, 1))
+    sim = pic.from_workload(w, precision=prec)
+    o = oracle_from_workload(w)
+    sim.pic_step(200)
+    o.step(200)
+    for c in range(6):
+        err = np.max(np.abs(sim.pic_fields(c) - o.field(c)))
+        assert err <= (1e-10 if prec == pic.FP64_PLAIN else 1e-4) * L.a0, (c, err)
+    assert np.abs(o.field(O.EZ)).max() > 0.3 * L.a0
+
+
+def test_empty_species_and_errors():
+    sim = pic.pic_create(2, (16, 16), (0.1, 0.1), 0.05, [(-1.0, 1.0, 0.1, 100), (1.0, 1836.0, 0.1, 0)])
+    sim.pic_step(3)  # no particles at all
+    d = sim.pic_diagnostics()
+    assert d["n_alive"] == [0, 0] and d["U_E"] == 0.0
+    with pytest.raises(pic.PicError) as e:
+        sim.pic_load_particles(0, np.full(200, 0.5), np.full(200, 0.5), None, np.zeros(200), np.zeros(200),
+                               np.zeros(200))
+    assert "CAPACITY" in str(e.value)
+    with pytest.raises(pic.PicError) as e:
+        sim.pic_load_particles(0, np.array([1.7]), np.array([0.5]), None, np.zeros(1), np.zeros(1), np.zeros(1))
+    assert "ARG" in str(e.value)
+    with pytest.raises(pic.PicError):
+        sim.pic_load_particles(0, np.array([0.7]), np.array([0.5]), None, np.array([np.nan]), np.zeros(1),
+                               np.zeros(1))
+    sim.pic_load_particles(0, np.array([0.7]), np.array([0.5]), None, np.zeros(1), np.zeros(1), np.zeros(1))
+    sim.pic_step(2)
+    assert sim.pic_particle_count(0) == 1
