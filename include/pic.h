@@ -215,6 +215,35 @@ int pic_profile(pic_sim *sim, int enable);
  * Synchronises the stream and clears the accumulators. */
 int pic_profile_read(pic_sim *sim, double *ms, int64_t *launches, int64_t *push_launches);
 
+/* Field energy without any device allocation.  The paper has no
+ * counterpart: this entry point exists for callers that cannot call
+ * cudaMalloc (for example a plugin inside a host application that owns all
+ * device memory through its own pool, or a real-time loop that must not
+ * allocate), who therefore cannot create a pic_sim.
+ *
+ * dev_fields: host array of six device pointers (Ex, Ey, Ez, Bx, By, Bz),
+ * each to n caller-owned FP64 values (any layout, e.g. the exchange layout
+ * of pic_fields).  dev_out2: caller-owned device pointer to two doubles that
+ * receive dV/2 * sum(Ex^2+Ey^2+Ez^2) and dV/2 * sum(Bx^2+By^2+Bz^2), summed
+ * in FP64 in a fixed order.  stream: a cudaStream_t (NULL = legacy default);
+ * the call only enqueues work on it.
+ *
+ * Scratch: the per-block partial sums live in a static device array of
+ * 4096 x 2 doubles (64 KiB) that every GPU loading the library holds until
+ * the process exits; n may be at most 67,108,864 (4096 blocks x 16384
+ * elements), larger n returns PIC_ERR_ARG with a message.  The call makes no
+ * cudaMalloc/cudaFree and calls no allocating library routine.  Its first
+ * call on a device looks up the address of that array with
+ * cudaGetSymbolAddress (with the device current); make that first call
+ * before any stream capture.  Every call on a device shares the one array
+ * and overwrites it completely (no state carries over between calls), so
+ * calls that overlap on the GPU -- on two streams, or from two host threads
+ * -- race and must be serialised by the caller.
+ * Errors: PIC_ERR_ARG (null pointer, n out of range), PIC_ERR_CUDA; the
+ * message is returned by pic_last_error(NULL). */
+int pic_field_energy_noalloc(const double *const dev_fields[6], int64_t n, double dV, double *dev_out2,
+                             void *stream);
+
 #ifdef __cplusplus
 }
 #endif

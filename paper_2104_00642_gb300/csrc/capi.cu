@@ -43,6 +43,11 @@ std::string g_create_error;
 
 }  // namespace
 
+namespace pic {
+// message reported by pic_last_error(NULL) for calls that have no pic_sim
+void set_global_error(const std::string &msg) { g_create_error = msg; }
+}  // namespace pic
+
 struct pic_sim {
     Grid g{};
     int precision = PIC_PREC_FP32_CELLOFF;

@@ -29,7 +29,8 @@ MAX_SPECIES = 8
 # every symbol include/pic.h declares
 EXPORTS = ["pic_create", "pic_destroy", "pic_last_error", "pic_load_particles", "pic_set_laser",
            "pic_set_field", "pic_step", "pic_fields", "pic_particle_count", "pic_get_particles",
-           "pic_get_cells", "pic_diagnostics", "pic_gather", "pic_sync", "pic_profile", "pic_profile_read"]
+           "pic_get_cells", "pic_diagnostics", "pic_gather", "pic_sync", "pic_profile", "pic_profile_read",
+           "pic_field_energy_noalloc"]
 PHASES = ("sort", "fields", "push", "fold")
 
 
@@ -109,8 +110,23 @@ def load_library(path: str = LIB_PATH):
     L.pic_profile.restype = I
     L.pic_profile_read.argtypes = [P, P, P, P]
     L.pic_profile_read.restype = I
+    L.pic_field_energy_noalloc.argtypes = [C.POINTER(C.c_void_p), I64, D, P, P]
+    L.pic_field_energy_noalloc.restype = I
     _lib = L
     return L
+
+
+def pic_field_energy_noalloc(dev_fields, n, dV, dev_out2, stream=None):
+    """Field energy of six caller-owned device FP64 arrays (Ex..Bz) into two
+    device doubles, for callers that cannot allocate device memory: the
+    library allocates nothing for this call (its scratch is a static device
+    array).  Arguments are raw device addresses (ints)."""
+    L = load_library()
+    ptrs = (C.c_void_p * 6)(*[C.c_void_p(int(p)) for p in dev_fields])
+    rc = L.pic_field_energy_noalloc(ptrs, int(n), float(dV), C.c_void_p(int(dev_out2)),
+                                    None if stream is None else C.c_void_p(int(stream)))
+    if rc != PIC_OK:
+        raise PicError(rc, L.pic_last_error(None).decode())
 
 
 def _p(a):
