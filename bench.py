@@ -205,6 +205,7 @@ def main():
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU baseline leg")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-flush", action="store_true")
+    ap.add_argument("--no-fp64", action="store_true", help="skip the plain FP64 form")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
     if args.impl == "reference":
@@ -286,12 +287,16 @@ def main():
             "bytes_per_particle": bpp, "occupied_cells": occ}
 
     # ---- plain FP64 form on the same workload ------------------------------
-    sim64 = pic.from_workload(w, precision=pic.FP64_PLAIN, sort_interval=args.sort_interval,
-                              stream=stream.cuda_stream)
-    timed(sim64, 3)
-    ms64, _ = timed(sim64, args.fp64_steps)
-    v64 = npart * args.fp64_steps / (float(np.sum(ms64)) / 1e3)
-    sim64.close()
+    fp64 = None
+    if not args.no_fp64:
+        sim64 = pic.from_workload(w, precision=pic.FP64_PLAIN, sort_interval=args.sort_interval,
+                                  stream=stream.cuda_stream)
+        timed(sim64, 3)
+        ms64, _ = timed(sim64, args.fp64_steps)
+        v64 = npart * args.fp64_steps / (float(np.sum(ms64)) / 1e3)
+        sim64.close()
+        fp64 = {"value": v64, "unit": UNIT, "ms_per_step": float(np.mean(ms64)),
+                "fp32_over_fp64": value / world / v64}
 
     # ---- end to end through the C ABI from pinned host arrays --------------
     e2e = None
@@ -344,8 +349,7 @@ def main():
                           "replicas": world, "qed": "off (no QED in this workload)"},
                "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches,
                "clocks": clk.summary(),
-               "fp64_plain": {"value": v64, "unit": UNIT, "ms_per_step": float(np.mean(ms64)),
-                              "fp32_over_fp64": value / world / v64},
+               "fp64_plain": fp64,
                "phases_ms_per_step": {k: v / args.steps for k, v in prof["ms"].items()},
                "launches_per_step": {k: v / args.steps for k, v in prof["launches"].items()}}
         print(json.dumps(out))

@@ -19,6 +19,7 @@
 #include "diag.cuh"
 #include "fdtd.cuh"
 #include "push.cuh"
+#include "push_tile.cuh"
 #include "sort.cuh"
 
 using namespace pic;
@@ -37,6 +38,13 @@ struct SpeciesState {
     double *x[2][3] = {};
     double *ud[2][3] = {};
     uint32_t *tile_start = nullptr;  // ntiles + 1
+    // work items of the tiled push (rebuilt after every sort)
+    TileItem *items = nullptr;
+    uint32_t *nitems = nullptr;
+    uint32_t *item_cnt = nullptr;   // ntiles + 1
+    uint32_t *item_scan = nullptr;  // scan scratch
+    long long items_cap = 0;
+    bool items_valid = false;
 };
 
 std::string g_create_error;
@@ -51,6 +59,7 @@ void set_global_error(const std::string &msg) { g_create_error = msg; }
 struct pic_sim {
     Grid g{};
     int precision = PIC_PREC_FP32_CELLOFF;
+    int push_variant = PIC_PUSH_AUTO;
     int sort_interval = 0;
     double rho_bg = 0.0;
     cudaStream_t st = nullptr;
@@ -65,6 +74,8 @@ struct pic_sim {
     double *d_eabs = nullptr;
     long long step = 0;
     Laser laser{};
+    pic_laser lp{};             // laser parameters (host)
+    void *laser_prof = nullptr; // transverse profile arrays (device)
     std::vector<void *> allocs;
     std::string err;
     // profiling
@@ -164,6 +175,12 @@ PushConst push_const(const pic_sim *s, const SpeciesState &p)
         if (d < g.dim) dV *= g.dx[d];
     }
     pc.wmdV = p.w * p.m * dV;
+    pc.qmdt2_f = (float)pc.qmdt2;
+    pc.qw_f = (float)pc.qw;
+    for (int d = 0; d < 3; d++) {
+        pc.hdx_f[d] = (float)pc.hdx[d];
+        pc.cJ_f[d] = (float)pc.cJ[d];
+    }
     return pc;
 }
 
@@ -181,8 +198,19 @@ int sort_species(pic_sim *s, int i)
     else
         launch_permute_f32(view32(s, i, p.cur), view32(s, i, o), perm, p.d_count, p.n_hi, s->g.dim, s->st);
     p.cur = o;
+    if (p.items) {
+        build_tile_items(p.tile_start, s->g.ntiles, p.item_cnt, p.item_scan, p.items, p.nitems, s->st);
+        p.items_valid = true;
+    }
     CK(cudaGetLastError());
     return PIC_OK;
+}
+
+bool use_tile_push(const pic_sim *s, const SpeciesState &p)
+{
+    return s->push_variant == PIC_PUSH_AUTO && p.items_valid && s->precision == PIC_PREC_FP32_CELLOFF &&
+           s->g.dim == 2 && s->g.tile_log2[0] == s->g.tile_log2[1] &&
+           (s->g.tile_log2[0] == 3 || s->g.tile_log2[0] == 4);
 }
 
 int read_count(pic_sim *s, int i, long long *n)
@@ -277,6 +305,90 @@ void ph_end(pic_sim *s, int phase)
     s->prof_launch[phase] += g_launches - s->cur_l0;
 }
 
+// the laser view for a B update that ends at t_new (the Mur condition needs
+// B_inc(x, t) = E_L(t - x) at x = -/+ dx/2 and at the new and old B times)
+Laser laser_at(const pic_sim *s, double t_new)
+{
+    Laser L = s->laser;
+    if (!L.on) return L;
+    const double h = 0.5 * s->g.dt, hx = 0.5 * s->g.dx[0];
+    const double tau[4] = {t_new + hx, t_new - h + hx, t_new - hx, t_new - h - hx};
+    const double two_pi = 6.283185307179586476925286766559;
+    for (int q = 0; q < 4; q++) {
+        const double a = (tau[q] - s->lp.t_peak) / s->lp.fwhm;
+        L.env[q] = std::exp(-2.0 * 0.69314718055994530942 * a * a);
+        L.ph0[q] = std::fmod(tau[q] - s->lp.t_peak, two_pi);
+    }
+    return L;
+}
+
+void push_species(pic_sim *s, int i, float *F)
+{
+    SpeciesState &p = s->sp[i];
+    if (use_tile_push(s, p))
+        launch_push_tile2d(view32(s, i, p.cur), p.items, p.nitems, (long long)tile_items_capacity(p.n_hi, s->g.ntiles),
+                           F, s->g, push_const(s, p), s->d_err, s->d_eabs, s->st);
+    else
+        launch_push_f32(view32(s, i, p.cur), F, s->g, push_const(s, p), s->d_err, s->d_eabs, s->st);
+}
+
+void push_species(pic_sim *s, int i, double *F)
+{
+    SpeciesState &p = s->sp[i];
+    launch_push_f64(view64(s, i, p.cur), F, s->g, push_const(s, p), s->d_err, s->d_eabs, s->st);
+}
+
+// nsteps split steps (Sec. II.F).  The first half step of a call runs
+// alone; between steps the second E half step of step n and the first of
+// step n+1 are one fused launch (the same curl B and J^{n+1} applied twice);
+// the last step of a call ends with its own E half step, so fields and
+// particles are at the integer step when the call returns.
+template <typename R>
+int step_loop(pic_sim *s, int64_t nsteps)
+{
+    const Grid &g = s->g;
+    const double h = 0.5 * g.dt;
+    R *F = (R *)s->F;
+    for (int64_t it = 0; it < nsteps; it++) {
+        if (s->sort_interval > 0 && s->step % s->sort_interval == 0) {
+            ph_begin(s);
+            for (int i = 0; i < s->nsp; i++) {
+                int rc = sort_species(s, i);
+                if (rc) return rc;
+            }
+            ph_end(s, PIC_PHASE_SORT);
+        }
+        const double t0 = (double)s->step * g.dt;
+        if (it == 0) {
+            ph_begin(s);
+            launch_update_E<R>(F, g, h, false, true, s->st);  // E^{n+1/2}, then J := 0
+            launch_update_B<R>(F, g, h, t0 + h, laser_at(s, t0 + h), s->st);
+            ph_end(s, PIC_PHASE_FIELDS);
+        }
+        ph_begin(s);
+        for (int i = 0; i < s->nsp; i++) {
+            if (s->sp[i].n_hi) s->prof_push++;
+            push_species(s, i, F);
+        }
+        ph_end(s, PIC_PHASE_PUSH);
+        ph_begin(s);
+        launch_fold<R>(F, g, s->st);
+        ph_end(s, PIC_PHASE_FOLD);
+        ph_begin(s);
+        launch_update_B<R>(F, g, h, t0 + g.dt, laser_at(s, t0 + g.dt), s->st);  // B^{n+1}
+        if (it == nsteps - 1) {
+            launch_update_E<R>(F, g, h, false, false, s->st);  // E^{n+1}
+        } else {
+            launch_update_E<R>(F, g, h, true, true, s->st);  // E^{n+3/2}, then J := 0
+            launch_update_B<R>(F, g, h, t0 + g.dt + h, laser_at(s, t0 + g.dt + h), s->st);  // B^{n+3/2}
+        }
+        ph_end(s, PIC_PHASE_FIELDS);
+        CK(cudaGetLastError());
+        s->step++;
+    }
+    return PIC_OK;
+}
+
 int check_flags(pic_sim *s)
 {
     int h = 0;
@@ -328,6 +440,8 @@ int pic_create(const pic_grid *grid, double dt, const pic_species *species, int 
         }
         g.n[d] = act ? (int)grid->n[d] : 1;
         g.dx[d] = act ? grid->dx[d] : 1.0;
+        g.rdx_d[d] = 1.0 / g.dx[d];
+        g.rdx_f[d] = (float)g.rdx_d[d];
         g.bc[d] = act ? grid->bc[d] : PERIODIC;
         g.G[d] = act ? kGhost : 0;
         g.ext[d] = g.n[d] + 2 * g.G[d];
@@ -348,11 +462,14 @@ int pic_create(const pic_grid *grid, double dt, const pic_species *species, int 
     g.sz = pitch * g.ext[1];
     g.vol = ((g.sz * g.ext[2] + 63) / 64) * 64;
     g.origin = (long long)g.G[2] * g.sz + (long long)g.G[1] * g.sy + g.G[0];
+    if (g.vol >= (1ll << 31))  // kernels address one component with 32-bit offsets
+        return fail(s, PIC_ERR_ARG, "pic_create: padded grid of %lld cells exceeds 2^31", g.vol);
 
     s = new pic_sim();
     s->g = g;
     s->precision = prec;
     s->sort_interval = opt ? opt->sort_interval : 0;
+    s->push_variant = opt ? opt->push_variant : PIC_PUSH_AUTO;
     s->rho_bg = opt ? opt->rho_bg : 0.0;
     s->st = opt ? (cudaStream_t)opt->stream : nullptr;
     s->nsp = nsp;
@@ -382,6 +499,13 @@ int pic_create(const pic_grid *grid, double dt, const pic_species *species, int 
         maxcap = std::max(maxcap, p.cap);
         rc = rc ? rc : dalloc(s, (void **)&p.d_count, sizeof(long long));
         rc = rc ? rc : dalloc(s, (void **)&p.tile_start, (size_t)(g.ntiles + 1) * sizeof(uint32_t));
+        if (prec == PIC_PREC_FP32_CELLOFF && g.dim == 2) {
+            p.items_cap = (long long)tile_items_capacity(p.cap, g.ntiles);
+            rc = rc ? rc : dalloc(s, (void **)&p.items, (size_t)p.items_cap * sizeof(TileItem));
+            rc = rc ? rc : dalloc(s, (void **)&p.nitems, sizeof(uint32_t));
+            rc = rc ? rc : dalloc(s, (void **)&p.item_cnt, (size_t)(g.ntiles + 1) * sizeof(uint32_t));
+            rc = rc ? rc : dalloc(s, (void **)&p.item_scan, scan_scratch_words(g.ntiles + 1) * sizeof(uint32_t));
+        }
         for (int b = 0; b < 2 && !rc; b++) {
             rc = dalloc(s, (void **)&p.cell[b], (size_t)p.cap * 4);
             for (int d = 0; d < 3 && !rc; d++) {
@@ -484,6 +608,7 @@ int pic_load_particles(pic_sim *s, int sp, int64_t n, const double *x, const dou
     cudaFree(dtmp);
     if (e != cudaSuccess) return fail(s, PIC_ERR_CUDA, "pic_load_particles: %s", cudaGetErrorString(e));
     p.n_hi = newn;
+    p.items_valid = false;  // appended particles are in no tile's work item until the next sort
     return PIC_OK;
 }
 
@@ -493,15 +618,54 @@ int pic_set_laser(pic_sim *s, const pic_laser *L)
     if (s->g.bc[0] != ABSORB) return fail(s, PIC_ERR_ARG, "pic_set_laser: the x-min face must be absorbing");
     if (!(L->fwhm > 0.0) || (s->g.dim > 1 && !(L->waist > 0.0)) || (L->pol != 0 && L->pol != 1))
         return fail(s, PIC_ERR_ARG, "pic_set_laser: bad laser parameters");
+    // transverse profile of the paraxial Gaussian beam at the x-min face
+    // (focus at x_focus; 2D: sqrt(w0/w) amplitude and half the Gouy phase)
+    const Grid &g = s->g;
+    const int nty = g.dim >= 2 ? g.n[1] : 1, ntz = g.dim >= 3 ? g.n[2] : 1;
+    const size_t nt = (size_t)nty * ntz;
+    double amp = 1.0, wxi = 1.0, rinv = 0.0, gouy = 0.0;
+    if (g.dim >= 2) {
+        const double xr = 0.5 * L->waist * L->waist, xi = -L->x_focus;
+        wxi = L->waist * std::sqrt(1.0 + (xi / xr) * (xi / xr));
+        rinv = xi / (xi * xi + xr * xr);
+        gouy = std::atan(xi / xr);
+        amp = g.dim == 3 ? L->waist / wxi : std::sqrt(L->waist / wxi);
+        if (g.dim == 2) gouy *= 0.5;
+    }
+    std::vector<double> prof(4 * nt);  // A_Bz, PHI_Bz, A_By, PHI_By
+    for (int c = 0; c < 2; c++) {
+        const double sy = c == 0 ? 0.5 : 0.0, sz = c == 0 ? 0.0 : 0.5;  // B_z at (j+1/2, k), B_y at (j, k+1/2)
+        for (int k = 0; k < ntz; k++)
+            for (int j = 0; j < nty; j++) {
+                double r2 = 0.0;
+                if (g.dim >= 2) r2 += std::pow((j + sy) * g.dx[1] - L->yc, 2);
+                if (g.dim >= 3) r2 += std::pow((k + sz) * g.dx[2] - L->zc, 2);
+                const double trans = g.dim >= 2 ? std::exp(-r2 / (wxi * wxi)) : 1.0;
+                prof[(2 * c) * nt + (size_t)k * nty + j] = L->a0 * amp * trans;
+                prof[(2 * c + 1) * nt + (size_t)k * nty + j] = -0.5 * r2 * rinv + gouy;
+            }
+    }
+    if (!s->laser_prof) {
+        int rc = dalloc(s, &s->laser_prof, 4 * nt * rsize(s));
+        if (rc) return rc;
+    }
+    if (s->precision == PIC_PREC_FP64_PLAIN) {
+        CK(cudaMemcpyAsync(s->laser_prof, prof.data(), 4 * nt * 8, cudaMemcpyHostToDevice, s->st));
+    } else {
+        std::vector<float> pf(prof.begin(), prof.end());
+        CK(cudaMemcpyAsync(s->laser_prof, pf.data(), 4 * nt * 4, cudaMemcpyHostToDevice, s->st));
+    }
+    CK(cudaStreamSynchronize(s->st));
+    const size_t rb = rsize(s);
     s->laser.on = 1;
     s->laser.pol = L->pol;
-    s->laser.a0 = L->a0;
-    s->laser.waist = L->waist;
-    s->laser.fwhm = L->fwhm;
-    s->laser.t_peak = L->t_peak;
-    s->laser.x_focus = L->x_focus;
-    s->laser.yc = L->yc;
-    s->laser.zc = L->zc;
+    s->laser.nty = nty;
+    s->laser.ntz = ntz;
+    for (int c = 0; c < 2; c++) {
+        s->laser.A[c] = (const char *)s->laser_prof + (2 * c) * nt * rb;
+        s->laser.PHI[c] = (const char *)s->laser_prof + (2 * c + 1) * nt * rb;
+    }
+    s->lp = *L;
     return PIC_OK;
 }
 
@@ -518,63 +682,8 @@ int pic_step(pic_sim *s, int64_t nsteps)
 {
     if (!s) return PIC_ERR_ARG;
     if (nsteps < 0) return fail(s, PIC_ERR_ARG, "pic_step: negative step count");
-    const Grid &g = s->g;
-    const double h = 0.5 * g.dt;
-    const bool f64 = s->precision == PIC_PREC_FP64_PLAIN;
-    for (int64_t it = 0; it < nsteps; it++) {
-        if (s->sort_interval > 0 && s->step % s->sort_interval == 0) {
-            ph_begin(s);
-            for (int i = 0; i < s->nsp; i++) {
-                int rc = sort_species(s, i);
-                if (rc) return rc;
-            }
-            ph_end(s, PIC_PHASE_SORT);
-        }
-        double t0 = (double)s->step * g.dt;
-        if (f64) {
-            double *F = (double *)s->F;
-            ph_begin(s);
-            launch_update_E<double>(F, g, h, true, s->st);
-            launch_update_B<double>(F, g, h, t0 + h, s->laser, s->st);
-            ph_end(s, PIC_PHASE_FIELDS);
-            ph_begin(s);
-            for (int i = 0; i < s->nsp; i++) {
-                SpeciesState &p = s->sp[i];
-                if (p.n_hi) s->prof_push++;
-                launch_push_f64(view64(s, i, p.cur), F, g, push_const(s, p), s->d_err, s->d_eabs, s->st);
-            }
-            ph_end(s, PIC_PHASE_PUSH);
-            ph_begin(s);
-            launch_fold<double>(F, g, s->st);
-            ph_end(s, PIC_PHASE_FOLD);
-            ph_begin(s);
-            launch_update_B<double>(F, g, h, t0 + g.dt, s->laser, s->st);
-            launch_update_E<double>(F, g, h, false, s->st);
-            ph_end(s, PIC_PHASE_FIELDS);
-        } else {
-            float *F = (float *)s->F;
-            ph_begin(s);
-            launch_update_E<float>(F, g, h, true, s->st);
-            launch_update_B<float>(F, g, h, t0 + h, s->laser, s->st);
-            ph_end(s, PIC_PHASE_FIELDS);
-            ph_begin(s);
-            for (int i = 0; i < s->nsp; i++) {
-                SpeciesState &p = s->sp[i];
-                if (p.n_hi) s->prof_push++;
-                launch_push_f32(view32(s, i, p.cur), F, g, push_const(s, p), s->d_err, s->d_eabs, s->st);
-            }
-            ph_end(s, PIC_PHASE_PUSH);
-            ph_begin(s);
-            launch_fold<float>(F, g, s->st);
-            ph_end(s, PIC_PHASE_FOLD);
-            ph_begin(s);
-            launch_update_B<float>(F, g, h, t0 + g.dt, s->laser, s->st);
-            launch_update_E<float>(F, g, h, false, s->st);
-            ph_end(s, PIC_PHASE_FIELDS);
-        }
-        CK(cudaGetLastError());
-        s->step++;
-    }
+    int rc = s->precision == PIC_PREC_FP64_PLAIN ? step_loop<double>(s, nsteps) : step_loop<float>(s, nsteps);
+    if (rc) return rc;
     return check_flags(s);
 }
 

@@ -5,7 +5,7 @@
 namespace pic {
 
 template <typename R>
-void launch_update_E(R *F, const Grid &g, double h, bool zeroJ, cudaStream_t st);
+void launch_update_E(R *F, const Grid &g, double h, bool twice, bool zeroJ, cudaStream_t st);
 template <typename R>
 void launch_update_B(R *F, const Grid &g, double h, double t_new, const Laser &L, cudaStream_t st);
 template <typename R>

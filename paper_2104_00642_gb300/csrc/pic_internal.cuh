@@ -44,11 +44,33 @@ struct Grid {
     int tile_log2[3];  // log2 of tile edge per axis
     int ntile[3];      // tiles per axis
     long long ntiles;
+    // 1/dx precomputed on the host: FP64 arithmetic on GB300 runs at a small
+    // fraction of the FP32 rate, so kernels take their constants ready-made
+    float rdx_f[3];
+    double rdx_d[3];
 };
 
+template <typename R>
+__host__ __device__ inline R rdx(const Grid &g, int d);
+template <>
+__host__ __device__ inline float rdx<float>(const Grid &g, int d) { return g.rdx_f[d]; }
+template <>
+__host__ __device__ inline double rdx<double>(const Grid &g, int d) { return g.rdx_d[d]; }
+
+// Device view of the laser entering through x-min.  The transverse profile
+// is precomputed once (FP64 on the host, stored in the field precision):
+// for c = 0 (B_z, from E_y) and c = 1 (B_y, from E_z) and every transverse
+// node (j, k): amplitude A_c = a0 * amp * exp(-r^2/w^2) and phase offset
+// PHI_c = -r^2/(2R) + Gouy.  The temporal factors of the four time points a
+// Mur update needs are computed on the host per launch: tau_q = t -/+ dx/2
+// at the new and old B times, env_q = exp(-2 ln2 ((tau_q - t_peak)/fwhm)^2)
+// and ph0_q = (tau_q - t_peak) mod 2 pi, so a boundary thread evaluates
+// E_y = A env sin(ph0 + PHI) (and E_z with cos for circular polarisation).
 struct Laser {
     int on, pol;
-    double a0, waist, fwhm, t_peak, x_focus, yc, zc;
+    int nty, ntz;          // transverse profile size (n_y, n_z; 1 on inactive axes)
+    const void *A[2], *PHI[2];
+    double env[4], ph0[4];  // q = 0: t_new at -dx/2, 1: t_old at -dx/2, 2: t_new at +dx/2, 3: t_old at +dx/2
 };
 
 // staggering of component c along axis d: 1 = half node

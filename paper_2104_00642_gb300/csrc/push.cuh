@@ -29,6 +29,8 @@ struct PushConst {
     double hdt;    // dt / 2         (FP64 absolute drift)
     double cJ[3];  // -q w dx_d / dt (Esirkepov prefix coefficient)
     double wmdV;   // w * m * dV     (absorbed kinetic energy)
+    // FP32 copies for the FP32 form (converted once on the host)
+    float qmdt2_f, qw_f, hdx_f[3], cJ_f[3];
 };
 
 void launch_push_f32(const PartF32 &P, float *F, const Grid &g, const PushConst &pc, int *err, double *e_abs,

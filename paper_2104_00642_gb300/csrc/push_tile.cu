@@ -1,0 +1,337 @@
+// push_tile.cu -- tiled particle push for 2D grids (FP32 cell+offset form).
+//
+// Particles are counting-sorted by tile (T x T cells) every K steps.  Each
+// work item is a chunk of at most kChunk particles that sat in one tile at the
+// last sort.  A persistent CTA takes items in turn and, per item:
+//   1. stages the six field components of the tile box [t0-4, t0+T+8) x
+//      [t0-4, t0+T+5) into shared memory (rows are contiguous in HBM);
+//   2. zeroes a shared current box of the same shape;
+//   3. pushes every particle of the chunk (half drift, gather from shared
+//      memory, Boris, two half drifts, Esirkepov on the 4-node union window
+//      with shared-memory atomics);
+//   4. flushes the current box to HBM with vector atomics (float4), once.
+// A particle that drifted so far since the sort that its stencil leaves the
+// box is handled on the global path (gather from HBM, global atomics), so the
+// result does not depend on the sort interval.
+#include "push_dev.cuh"
+#include "push_tile.cuh"
+
+namespace pic {
+
+template <int T>
+struct Box2 {
+    static constexpr int WX = T + 12;  // x: [t0-4, t0+T+8), a multiple of 4 floats
+    static constexpr int WY = T + 9;   // y: [t0-4, t0+T+5)
+    static constexpr int N = WX * WY;
+    static constexpr int SMEM = 9 * N * (int)sizeof(float);
+};
+
+// Eq. (19) in 2D on a strided view: F_c(x, y) = P[c*cs + (y-oy)*rs + (x-ox)]
+__device__ __forceinline__ void gather2d(const float *__restrict__ P, long long cs, int rs, int ox, int oy,
+                                         const int *icn, const float (*wn)[3], const int *ich, const float (*wh)[3],
+                                         float *eb)
+{
+#pragma unroll
+    for (int c = 0; c < 6; c++) {
+        const int sx = stag(c, 0), sy = stag(c, 1);
+        const int ix = (sx ? ich[0] : icn[0]) - 1 - ox;
+        const int iy = (sy ? ich[1] : icn[1]) - 1 - oy;
+        const float *wx = sx ? wh[0] : wn[0];
+        const float *wy = sy ? wh[1] : wn[1];
+        const float *row = P + c * cs + (long long)iy * rs + ix;
+        float acc = 0.f;
+#pragma unroll
+        for (int b = 0; b < 3; b++) {
+            const float *r = row + (long long)b * rs;
+            float s = wx[0] * r[0];
+            s += wx[1] * r[1];
+            s += wx[2] * r[2];
+            acc += wy[b] * s;
+        }
+        eb[c] = acc;
+    }
+}
+
+// shapes of the start (i0, w0) and end (i1, w1) points on the 4-node union
+// window [u0, u0+3], u0 = min(i0, i1) - 1 (|i1 - i0| <= 1)
+__device__ __forceinline__ int union4(int i0, const float *w0, int i1, const float *w1, float *S0, float *dS)
+{
+    const int u0 = min(i0, i1) - 1;
+    const int o0 = i0 - 1 - u0, o1 = i1 - 1 - u0;  // each 0 or 1
+#pragma unroll
+    for (int k = 0; k < 4; k++) {
+        float s0 = o0 ? (k >= 1 ? w0[k - 1] : 0.f) : (k <= 2 ? w0[k] : 0.f);
+        float s1 = o1 ? (k >= 1 ? w1[k - 1] : 0.f) : (k <= 2 ? w1[k] : 0.f);
+        S0[k] = s0;
+        dS[k] = s1 - s0;
+    }
+    return u0;
+}
+
+// Esirkepov in 2D on the union window (Eqs. (20)-(22); W_x = dSx (S0y +
+// dSy/2), W_y = dSy (S0x + dSx/2); J_z = q w v_z times the time average of
+// the node-shape product) into a strided view J_c(x, y) = P[c*cs + ...]
+__device__ __forceinline__ void deposit2d(float *P, long long cs, int rs, int ox, int oy, int ux, int uy,
+                                          const float (*S0)[4], const float (*dS)[4], float cjx, float cjy,
+                                          float jvz)
+{
+    float *Jx = P + (long long)(uy - oy) * rs + (ux - ox);
+    float *Jy = Jx + cs;
+    float *Jz = Jx + 2 * cs;
+#pragma unroll
+    for (int b = 0; b < 4; b++) {
+        const float ty = S0[1][b] + 0.5f * dS[1][b];
+        float acc = 0.f;
+#pragma unroll
+        for (int a = 0; a < 3; a++) {
+            acc += cjx * (dS[0][a] * ty);
+            if (acc != 0.f) atomicAdd(Jx + (long long)b * rs + a, acc);
+        }
+    }
+#pragma unroll
+    for (int a = 0; a < 4; a++) {
+        const float tx = S0[0][a] + 0.5f * dS[0][a];
+        float acc = 0.f;
+#pragma unroll
+        for (int b = 0; b < 3; b++) {
+            acc += cjy * (dS[1][b] * tx);
+            if (acc != 0.f) atomicAdd(Jy + (long long)b * rs + a, acc);
+        }
+    }
+    const float third = 1.0f / 3.0f;
+#pragma unroll
+    for (int b = 0; b < 4; b++)
+#pragma unroll
+        for (int a = 0; a < 4; a++) {
+            float wz = S0[0][a] * S0[1][b] + 0.5f * dS[0][a] * S0[1][b] + 0.5f * S0[0][a] * dS[1][b] +
+                       third * dS[0][a] * dS[1][b];
+            if (wz != 0.f) atomicAdd(Jz + (long long)b * rs + a, jvz * wz);
+        }
+}
+
+template <int T>
+__global__ void __launch_bounds__(kTileThreads, 4)
+    k_push_tile2d(PartF32 P, const TileItem *__restrict__ items, const uint32_t *__restrict__ nitems,
+                  float *__restrict__ F, Grid g, PushConst pc, int *err, double *e_abs)
+{
+    using B = Box2<T>;
+    extern __shared__ float smem[];
+    float *sF = smem;           // 6 components
+    float *sJ = smem + 6 * B::N;  // 3 components
+    const int nit = (int)*nitems;
+    const long long V = g.vol;
+    const float hdx0 = pc.hdx_f[0], hdx1 = pc.hdx_f[1];
+    const float k = pc.qmdt2_f;
+    const float cjx = pc.cJ_f[0], cjy = pc.cJ_f[1], qw = pc.qw_f;
+    float *Fg = F + g.origin;  // interior origin
+    const int rs = (int)g.sy;
+    for (int it = blockIdx.x; it < nit; it += gridDim.x) {
+        const TileItem m = items[it];
+        const int tx = m.tile % g.ntile[0], ty = m.tile / g.ntile[0];
+        const int bx0 = tx * T - 4, by0 = ty * T - 4;
+        // 1-2. stage fields, zero the current box
+        for (int q = threadIdx.x; q < 6 * B::N; q += blockDim.x) {
+            const int c = q / B::N, r = q - c * B::N;
+            const int y = r / B::WX, x = r - y * B::WX;
+            const int gx = bx0 + x, gy = by0 + y;
+            float v = 0.f;
+            if (gx < g.n[0] + g.G[0] && gy < g.n[1] + g.G[1]) v = __ldg(Fg + c * V + (long long)gy * rs + gx);
+            sF[q] = v;
+        }
+        for (int q = threadIdx.x; q < 3 * B::N; q += blockDim.x) sJ[q] = 0.f;
+        __syncthreads();
+        // 3. particles
+        // Lane striding: the chunk is cut into 32 contiguous segments of S
+        // particles and lane l of every warp walks segment l.  Sorted
+        // particles of one cell are contiguous, so the 32 lanes of one
+        // shared-memory atomic target 32 different cells (different current
+        // addresses) instead of one, whatever the in-tile order.
+        const int S = (m.count + 31) >> 5;
+        const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+        for (int j = warp; j < S; j += kTileThreads / 32) {
+            const int li = lane * S + j;
+            if (li >= m.count) continue;
+            const long long p = (long long)m.start + li;
+            const uint32_t cp = P.cell[p];
+            if (cp == kDead) continue;
+            int c[2];
+            int dummy;
+            unpack_cell(g, cp, c[0], c[1], dummy);
+            float o[2] = {P.off[0][p], P.off[1][p]};
+            float ux = P.u[0][p], uy = P.u[1][p], uz = P.u[2][p];
+            float ig = inv_gamma(ux, uy, uz);
+            drift_f32(c[0], o[0], hdx0 * ux * ig);
+            drift_f32(c[1], o[1], hdx1 * uy * ig);
+            const int ch[2] = {c[0], c[1]};
+            const float oh[2] = {o[0], o[1]};
+            int icn[2], ich[2];
+            float wn[2][3], wh[2][3];
+            axis_w_f32(c[0], o[0], icn[0], wn[0], ich[0], wh[0]);
+            axis_w_f32(c[1], o[1], icn[1], wn[1], ich[1], wh[1]);
+            float eb[6];
+            const bool gin = ch[0] - 1 >= bx0 && ch[0] + 2 < bx0 + B::WX && ch[1] - 1 >= by0 && ch[1] + 2 < by0 + B::WY;
+            if (gin) gather2d(sF, B::N, B::WX, bx0, by0, icn, wn, ich, wh, eb);
+            else gather2d(Fg, V, rs, 0, 0, icn, wn, ich, wh, eb);
+            boris<float>(ux, uy, uz, k * eb[0], k * eb[1], k * eb[2], k * eb[3], k * eb[4], k * eb[5]);
+            const float ig1 = inv_gamma(ux, uy, uz);
+            const float d0 = hdx0 * ux * ig1, d1 = hdx1 * uy * ig1;
+            drift_f32(c[0], o[0], d0);
+            drift_f32(c[1], o[1], d1);
+            const int c1[2] = {c[0], c[1]};
+            const float o1[2] = {o[0], o[1]};
+            drift_f32(c[0], o[0], d0);
+            drift_f32(c[1], o[1], d1);
+            // Esirkepov on x^{n+1/2} -> x^{n+3/2}
+            float S0[2][4], dS[2][4];
+            int u0[2];
+            bool ok = true;
+#pragma unroll
+            for (int d = 0; d < 2; d++) {
+                int i0, i1;
+                float w0[3], w1[3];
+                axis_wn_f32(ch[d], oh[d], i0, w0);
+                axis_wn_f32(c[d], o[d], i1, w1);
+                ok &= (i1 - i0 >= -1 && i1 - i0 <= 1);
+                u0[d] = union4(i0, w0, i1, w1, S0[d], dS[d]);
+            }
+            if (!ok) {
+                atomicOr(err, ERR_CFL);
+                continue;
+            }
+            const float jvz = qw * uz * ig1;
+            const bool din = u0[0] >= bx0 && u0[0] + 3 < bx0 + B::WX && u0[1] >= by0 && u0[1] + 3 < by0 + B::WY;
+            if (din) deposit2d(sJ, B::N, B::WX, bx0, by0, u0[0], u0[1], S0, dS, cjx, cjy, jvz);
+            else deposit2d(Fg + JX * V, V, rs, 0, 0, u0[0], u0[1], S0, dS, cjx, cjy, jvz);
+            // boundaries
+            int cc[2] = {c1[0], c1[1]};
+            bool dead = false;
+#pragma unroll
+            for (int d = 0; d < 2; d++) {
+                if (g.bc[d] == PERIODIC) {
+                    if (cc[d] < 0) cc[d] += g.n[d];
+                    else if (cc[d] >= g.n[d]) cc[d] -= g.n[d];
+                } else if (cc[d] < 0 || cc[d] >= g.n[d]) {
+                    dead = true;
+                }
+            }
+            if (!isfinite(ux + uy + uz)) atomicOr(err, ERR_NONFINITE);
+            if (dead) {
+                P.cell[p] = kDead;
+                double uu = (double)ux * ux + (double)uy * uy + (double)uz * uz;
+                atomicAdd(e_abs, pc.wmdV * uu / (sqrt(1.0 + uu) + 1.0));
+            } else {
+                P.cell[p] = pack_cell(g, cc[0], cc[1], 0);
+            }
+            P.off[0][p] = o1[0];
+            P.off[1][p] = o1[1];
+            P.u[0][p] = ux;
+            P.u[1][p] = uy;
+            P.u[2][p] = uz;
+        }
+        __syncthreads();
+        // 4. flush the current box, four floats at a time
+        for (int q = threadIdx.x; q < 3 * B::N / 4; q += blockDim.x) {
+            const float4 v = reinterpret_cast<const float4 *>(sJ)[q];
+            if (v.x == 0.f && v.y == 0.f && v.z == 0.f && v.w == 0.f) continue;
+            const int e = 4 * q;
+            const int c = e / B::N, r = e - c * B::N;
+            const int y = r / B::WX, x = r - y * B::WX;
+            const int gx = bx0 + x, gy = by0 + y;
+            if (gx < -g.G[0] || gx + 3 >= g.n[0] + g.G[0] || gy < -g.G[1] || gy >= g.n[1] + g.G[1]) {
+                // partial vector at the edge of the padded box (holds zeros only
+                // for accepted particles; kept exact for safety)
+                float vv[4] = {v.x, v.y, v.z, v.w};
+                for (int l = 0; l < 4; l++)
+                    if (vv[l] != 0.f && gx + l >= -g.G[0] && gx + l < g.n[0] + g.G[0] && gy >= -g.G[1] &&
+                        gy < g.n[1] + g.G[1])
+                        atomicAdd(Fg + (JX + c) * V + (long long)gy * rs + gx + l, vv[l]);
+                continue;
+            }
+            atomicAdd(reinterpret_cast<float4 *>(Fg + (JX + c) * V + (long long)gy * rs + gx), v);
+        }
+        __syncthreads();
+    }
+}
+
+// ---------------------------------------------------------------------
+// work items: chunks of at most kChunk particles of one tile
+// ---------------------------------------------------------------------
+__global__ void k_item_counts(const uint32_t *__restrict__ starts, long long ntiles, uint32_t *cnt)
+{
+    long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t > ntiles) return;
+    if (t == ntiles) {
+        cnt[t] = 0;
+        return;
+    }
+    uint32_t n = starts[t + 1] - starts[t];
+    cnt[t] = (n + kChunk - 1) / kChunk;
+}
+
+__global__ void k_item_write(const uint32_t *__restrict__ starts, const uint32_t *__restrict__ off, long long ntiles,
+                             TileItem *items, uint32_t *nitems)
+{
+    long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= ntiles) {
+        if (t == ntiles) *nitems = off[ntiles];
+        return;
+    }
+    uint32_t s = starts[t], n = starts[t + 1] - s;
+    uint32_t o = off[t];
+    for (uint32_t q = 0; q * kChunk < n; q++) {
+        TileItem m;
+        m.tile = (int)t;
+        m.start = (int)(s + q * kChunk);
+        m.count = (int)min((uint32_t)kChunk, n - q * kChunk);
+        m.pad = 0;
+        items[o + q] = m;
+    }
+}
+
+size_t tile_items_capacity(long long cap, long long ntiles) { return (size_t)(ntiles + cap / kChunk + 2); }
+
+void build_tile_items(const uint32_t *starts, long long ntiles, uint32_t *cnt_scratch, uint32_t *scan_scratch,
+                      TileItem *items, uint32_t *nitems, cudaStream_t st)
+{
+    note_launch(2);
+    k_item_counts<<<div_up(ntiles + 1, 256), 256, 0, st>>>(starts, ntiles, cnt_scratch);
+    scan_exclusive(cnt_scratch, cnt_scratch, ntiles + 1, scan_scratch, st);
+    k_item_write<<<div_up(ntiles + 1, 256), 256, 0, st>>>(starts, cnt_scratch, ntiles, items, nitems);
+}
+
+bool tile_push_supported(const Grid &g, int tile_edge)
+{
+    return g.dim == 2 && (1 << g.tile_log2[0]) == tile_edge && (1 << g.tile_log2[1]) == tile_edge;
+}
+
+template <int T>
+static void launch_T(const PartF32 &P, const TileItem *items, const uint32_t *nitems, long long max_items, float *F,
+                     const Grid &g, const PushConst &pc, int *err, double *e_abs, cudaStream_t st)
+{
+    static bool attr = false;
+    if (!attr) {
+        cudaFuncSetAttribute(k_push_tile2d<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, Box2<T>::SMEM);
+        attr = true;
+    }
+    static int nsm = 0;
+    if (!nsm) {
+        int dev = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+    }
+    long long grid = std::min<long long>(max_items, (long long)nsm * 8);
+    if (grid < 1) grid = 1;
+    note_launch();
+    k_push_tile2d<T><<<(int)grid, kTileThreads, Box2<T>::SMEM, st>>>(P, items, nitems, F, g, pc, err, e_abs);
+}
+
+void launch_push_tile2d(const PartF32 &P, const TileItem *items, const uint32_t *nitems, long long max_items,
+                        float *F, const Grid &g, const PushConst &pc, int *err, double *e_abs, cudaStream_t st)
+{
+    if (P.n == 0) return;
+    int T = 1 << g.tile_log2[0];
+    if (T == 16) launch_T<16>(P, items, nitems, max_items, F, g, pc, err, e_abs, st);
+    else launch_T<8>(P, items, nitems, max_items, F, g, pc, err, e_abs, st);
+}
+
+}  // namespace pic

@@ -1,0 +1,22 @@
+// push_tile.cuh -- tiled 2D push (push_tile.cu) and its work items.
+#pragma once
+#include "push.cuh"
+#include "sort.cuh"
+
+namespace pic {
+
+constexpr int kChunk = 1024;       // particles per work item at most
+constexpr int kTileThreads = 128;  // threads per CTA of the tiled push
+
+struct TileItem {
+    int tile, start, count, pad;
+};
+
+size_t tile_items_capacity(long long cap, long long ntiles);
+void build_tile_items(const uint32_t *starts, long long ntiles, uint32_t *cnt_scratch, uint32_t *scan_scratch,
+                      TileItem *items, uint32_t *nitems, cudaStream_t st);
+bool tile_push_supported(const Grid &g, int tile_edge);
+void launch_push_tile2d(const PartF32 &P, const TileItem *items, const uint32_t *nitems, long long max_items,
+                        float *F, const Grid &g, const PushConst &pc, int *err, double *e_abs, cudaStream_t st);
+
+}  // namespace pic

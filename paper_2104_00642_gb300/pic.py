@@ -23,6 +23,7 @@ ERRORS = {-1: "PIC_ERR_ARG", -2: "PIC_ERR_CFL", -3: "PIC_ERR_CUDA", -4: "PIC_ERR
           -5: "PIC_ERR_NONFINITE", -6: "PIC_ERR_NOMEM", -7: "PIC_ERR_STATE"}
 PERIODIC, ABSORB = 0, 1
 FP32_CELLOFF, FP64_PLAIN = 0, 1
+PUSH_AUTO, PUSH_SIMPLE = 0, 1
 EX, EY, EZ, BX, BY, BZ, JX, JY, JZ, RHO = range(10)
 MAX_SPECIES = 8
 
@@ -51,7 +52,7 @@ class pic_species(C.Structure):
 
 class pic_options(C.Structure):
     _fields_ = [("precision", C.c_int), ("sort_interval", C.c_int), ("tile", C.c_int * 3),
-                ("rho_bg", C.c_double), ("stream", C.c_void_p)]
+                ("rho_bg", C.c_double), ("stream", C.c_void_p), ("push_variant", C.c_int)]
 
 
 class pic_laser(C.Structure):
@@ -141,7 +142,7 @@ class Sim:
     """One simulation (a ``pic_sim*``)."""
 
     def __init__(self, dim, n, dx, dt, species, bc=(PERIODIC, PERIODIC, PERIODIC), precision=FP32_CELLOFF,
-                 sort_interval=0, tile=(0, 0, 0), rho_bg=0.0, stream=None):
+                 sort_interval=0, tile=(0, 0, 0), rho_bg=0.0, stream=None, push_variant=0):
         L = load_library()
         g = pic_grid()
         g.dim = int(dim)
@@ -160,6 +161,7 @@ class Sim:
             o.tile[d] = int(tile[d]) if d < len(tile) else 0
         o.rho_bg = float(rho_bg)
         o.stream = stream
+        o.push_variant = int(push_variant)
         h = C.c_void_p()
         rc = L.pic_create(C.byref(g), float(dt), sp, len(species), C.byref(o), C.byref(h))
         if rc != PIC_OK:
@@ -281,12 +283,12 @@ def pic_create(dim, n, dx, dt, species, **kw) -> Sim:
 
 
 def from_workload(w, precision=FP32_CELLOFF, sort_interval=0, capacity_scale=1.0, load=True, stream=None,
-                  tile=None) -> Sim:
+                  tile=None, push_variant=0) -> Sim:
     """Create a simulation for a :class:`workloads.Workload` and load its particles."""
     sp = [(s.q, s.m, s.w, max(1, int(s.capacity * capacity_scale))) for s in w.species]
     t = tile if tile is not None else tuple(w.tile)
     sim = Sim(w.dim, w.n, w.dx, w.dt, sp, bc=w.bc, precision=precision, sort_interval=sort_interval, tile=t,
-              rho_bg=w.rho_bg, stream=stream)
+              rho_bg=w.rho_bg, stream=stream, push_variant=push_variant)
     if w.laser is not None:
         L = w.laser
         sim.pic_set_laser(L.a0, L.waist, L.fwhm, L.t_peak, L.x_focus, L.yc, L.zc, L.pol)

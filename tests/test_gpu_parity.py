@@ -240,3 +240,80 @@ def test_empty_species_and_errors():
     sim.pic_load_particles(0, np.array([0.7]), np.array([0.5]), None, np.zeros(1), np.zeros(1), np.zeros(1))
     sim.pic_step(2)
     assert sim.pic_particle_count(0) == 1
+
+
+# --------------------------------------------------------------------------
+# tiled 2D push (shared-memory staging and current box)
+# --------------------------------------------------------------------------
+
+@pytest.mark.parametrize("tile", [8, 16])
+def test_tile_push_one_step_matches_oracle(tile):
+    """Sort at step 0 (same order in both), one step through the tiled
+    kernel: ragged grid (tiles do not divide it), several tiles."""
+    n, dx = (40, 21), (0.1, 0.12)
+    w, F = random_state(2, n, dx, _dt(dx), 4, seed=301, umax=0.9)
+    sim = pic.from_workload(w, precision=pic.FP32_CELLOFF, sort_interval=1, tile=(tile, tile, 1))
+    o = oracle_from_workload(w, sort_interval=1, tile=(tile, tile, 1))
+    for c in range(9):
+        sim.pic_set_field(c, F[c])
+        o.set_field(c, F[c])
+    sim.pic_step(1)
+    o.step(1)
+    tol = TOL[pic.FP32_CELLOFF]
+    pg, po = sim.pic_get_particles(0), o.particles(0)
+    assert np.max(np.abs(pg["x"] - po["x"])) <= 10 * tol * dx[0]
+    assert np.max(np.abs(pg["y"] - po["y"])) <= 10 * tol * dx[1]
+    umag = np.sqrt(po["ux"] ** 2 + po["uy"] ** 2 + po["uz"] ** 2)
+    for k in ("ux", "uy", "uz"):
+        assert np.all(np.abs(pg[k] - po[k]) <= tol * umag + 1e-7)
+    for c, ax in ((pic.JX, 0), (pic.JY, 1), (pic.JZ, 2)):
+        scale = window_scale(po, w, 2, ax)
+        assert np.all(np.abs(sim.pic_fields(c) - o.field(c)) <= tol * scale + 1e-30)
+
+
+def test_tile_push_fallback_after_drift_matches_simple_kernel():
+    """Fast particles and a long sort interval: many leave their tile box and
+    take the global path.  The tiled and the simple kernel agree to FP32
+    round-off and both agree with the oracle."""
+    n, dx = (48, 32), (0.1, 0.1)
+    w, F = random_state(2, n, dx, _dt(dx), 4, seed=302, umax=3.0)
+    sims = [pic.from_workload(w, precision=pic.FP32_CELLOFF, sort_interval=50, tile=(8, 8, 1), push_variant=v)
+            for v in (pic.PUSH_AUTO, pic.PUSH_SIMPLE)]
+    o = oracle_from_workload(w, sort_interval=50, tile=(8, 8, 1))
+    for c in range(9):
+        for s in sims:
+            s.pic_set_field(c, F[c])
+        o.set_field(c, F[c])
+    for s in sims:
+        s.pic_step(12)
+    o.step(12)
+    pa, pb, po = sims[0].pic_get_particles(0), sims[1].pic_get_particles(0), o.particles(0)
+    for k in ("x", "y", "ux", "uy", "uz"):
+        assert np.max(np.abs(pa[k] - pb[k])) < 1e-4
+        assert np.max(np.abs(pa[k] - po[k])) < 1e-3
+    da, do = sims[0].pic_diagnostics(), o.diagnostics()
+    for k in ("U_E", "U_B"):
+        assert abs(da[k] - do[k]) <= 1e-3 * max(do["U_E"], do["U_B"])
+    assert abs(da["U_kin"][0] - do["U_kin"][0]) <= 1e-4 * do["U_kin"][0]
+
+
+@pytest.mark.parametrize("prec", PRECS)
+def test_laser_foil_small_energy_history(prec):
+    """The bench workload's physics at reduced size: LP laser a0 = 20 on a
+    10 n_c hydrogen slab (absorbing x, periodic y), energy histories within
+    1e-3 of their maximum."""
+    w = W.laser_foil_2d(nx=256, ny=64, slab=(128, 136), ppc=8, a0=20.0, fwhm_fs=5.0, steps=700)
+    w.laser.t_peak = 2.0 * w.laser.fwhm  # peak reaches the slab front near step 480
+    sim = pic.from_workload(w, precision=prec, sort_interval=8)
+    o = oracle_from_workload(w, sort_interval=8)
+    ref, got = [], []
+    for _ in range(7):
+        sim.pic_step(100)
+        o.step(100)
+        d, e = sim.pic_diagnostics(), o.diagnostics()
+        got.append([d["U_E"], d["U_B"], d["U_kin"][0], d["U_kin"][1], d["E_absorbed"]])
+        ref.append([e["U_E"], e["U_B"], e["U_kin"][0], e["U_kin"][1], e["E_absorbed"]])
+    got, ref = np.array(got), np.array(ref)
+    assert ref[:, 2].max() > 10 * ref[0, 2]  # the laser has heated the slab
+    for c in range(4):
+        assert np.max(np.abs(got[:, c] - ref[:, c])) <= 1e-3 * ref[:, c].max(), (c, got[:, c], ref[:, c])
