@@ -18,12 +18,17 @@
 
 namespace pic {
 
+// particle staging: slot (j, l) of particle i = l*S + j (lane l, segment
+// position j) sits at j*33 + l, so the 32 lanes of a read hit 32 banks
+constexpr int kPSlot = 33 * 32;
+
 template <int T>
 struct Box2 {
     static constexpr int WX = T + 12;  // x: [t0-4, t0+T+8), a multiple of 4 floats
     static constexpr int WY = T + 9;   // y: [t0-4, t0+T+5)
     static constexpr int N = WX * WY;
-    static constexpr int SMEM = 9 * N * (int)sizeof(float);
+    // fields (6) + current (3) boxes + staged particle state (6 arrays)
+    static constexpr int SMEM = (9 * N + 6 * kPSlot) * (int)sizeof(float);
 };
 
 // Eq. (19) in 2D on a strided view: F_c(x, y) = P[c*cs + (y-oy)*rs + (x-ox)]
@@ -68,45 +73,97 @@ __device__ __forceinline__ int union4(int i0, const float *w0, int i1, const flo
     return u0;
 }
 
-// Esirkepov in 2D on the union window (Eqs. (20)-(22); W_x = dSx (S0y +
-// dSy/2), W_y = dSy (S0x + dSx/2); J_z = q w v_z times the time average of
-// the node-shape product) into a strided view J_c(x, y) = P[c*cs + ...]
-__device__ __forceinline__ void deposit2d(float *P, long long cs, int rs, int ox, int oy, int ux, int uy,
-                                          const float (*S0)[4], const float (*dS)[4], float cjx, float cjy,
-                                          float jvz)
+// Esirkepov in 2D on the union window (Eqs. (20)-(22)): W_x = dSx (S0y +
+// dSy/2), W_y = dSy (S0x + dSx/2), and J_z = q w v_z times the time average
+// of the node-shape product, S0xS0y + (dSx S0y + S0x dSy)/2 + dSx dSy/3,
+// written as tx ty + dSx dSy/12 with tx = S0x + dSx/2, ty = S0y + dSy/2.
+// `Acc` adds one value at window offset (a, b) of component c.
+template <class Acc>
+__device__ __forceinline__ void esirkepov2d(const float (*S0)[4], const float (*dS)[4], float cjx, float cjy,
+                                            float jvz, Acc &acc)
 {
-    float *Jx = P + (long long)(uy - oy) * rs + (ux - ox);
-    float *Jy = Jx + cs;
-    float *Jz = Jx + 2 * cs;
+    float tx[4], ty[4], dx12[4];
 #pragma unroll
-    for (int b = 0; b < 4; b++) {
-        const float ty = S0[1][b] + 0.5f * dS[1][b];
-        float acc = 0.f;
-#pragma unroll
-        for (int a = 0; a < 3; a++) {
-            acc += cjx * (dS[0][a] * ty);
-            if (acc != 0.f) atomicAdd(Jx + (long long)b * rs + a, acc);
-        }
+    for (int k = 0; k < 4; k++) {
+        tx[k] = S0[0][k] + 0.5f * dS[0][k];
+        ty[k] = S0[1][k] + 0.5f * dS[1][k];
+        dx12[k] = dS[0][k] * (1.0f / 12.0f);
     }
+    float px[3], py[3];  // prefix sums of dS along x and y
+    px[0] = dS[0][0];
+    py[0] = dS[1][0];
 #pragma unroll
-    for (int a = 0; a < 4; a++) {
-        const float tx = S0[0][a] + 0.5f * dS[0][a];
-        float acc = 0.f;
-#pragma unroll
-        for (int b = 0; b < 3; b++) {
-            acc += cjy * (dS[1][b] * tx);
-            if (acc != 0.f) atomicAdd(Jy + (long long)b * rs + a, acc);
-        }
+    for (int k = 1; k < 3; k++) {
+        px[k] = px[k - 1] + dS[0][k];
+        py[k] = py[k - 1] + dS[1][k];
     }
-    const float third = 1.0f / 3.0f;
 #pragma unroll
     for (int b = 0; b < 4; b++)
 #pragma unroll
-        for (int a = 0; a < 4; a++) {
-            float wz = S0[0][a] * S0[1][b] + 0.5f * dS[0][a] * S0[1][b] + 0.5f * S0[0][a] * dS[1][b] +
-                       third * dS[0][a] * dS[1][b];
-            if (wz != 0.f) atomicAdd(Jz + (long long)b * rs + a, jvz * wz);
-        }
+        for (int a = 0; a < 3; a++) acc.add(0, a, b, cjx * px[a] * ty[b]);
+#pragma unroll
+    for (int b = 0; b < 3; b++)
+#pragma unroll
+        for (int a = 0; a < 4; a++) acc.add(1, a, b, cjy * py[b] * tx[a]);
+#pragma unroll
+    for (int b = 0; b < 4; b++)
+#pragma unroll
+        for (int a = 0; a < 4; a++) acc.add(2, a, b, jvz * (tx[a] * ty[b] + dx12[a] * dS[1][b]));
+}
+
+// current into the shared box as 32-bit fixed point (integer shared-memory
+// atomics are native; float ones are not).  A chunk has at most kChunk
+// particles and each adds at most C = |q w| max(dx_d/dt) in magnitude to a
+// node, so with 2^20/C units per C a node holds at most 2^30: no overflow.
+// Rounding each value to the unit costs at most 2^-21 C per particle and
+// node, below 1e-6 of the node's sum of |contributions| scale.
+struct AccShared {
+    int *base;  // component 0 at (ux, uy) of the window
+    int cs, rs;
+    float scale;
+    __device__ __forceinline__ void add(int c, int a, int b, float v)
+    {
+        int q = __float2int_rn(v * scale);
+        if (q != 0) atomicAdd(base + c * cs + b * rs + a, q);
+    }
+};
+
+// current straight into HBM (particles whose window left the box)
+struct AccGlobal {
+    float *base;
+    long long cs;
+    int rs;
+    __device__ __forceinline__ void add(int c, int a, int b, float v)
+    {
+        if (v != 0.f) atomicAdd(base + c * cs + (long long)b * rs + a, v);
+    }
+};
+
+// Boris (Eqs. (13)-(16)) with the FP32 reciprocal square root and divide
+// of the special-function unit (a few ulp, far inside the FP32 tolerance)
+__device__ __forceinline__ void boris_fast(float &ux, float &uy, float &uz, float ex, float ey, float ez, float bx,
+                                           float by, float bz)
+{
+    float umx = ux + ex, umy = uy + ey, umz = uz + ez;
+    float ginv = rsqrtf(1.0f + umx * umx + umy * umy + umz * umz);
+    float tx = bx * ginv, ty = by * ginv, tz = bz * ginv;
+    float t2 = tx * tx + ty * ty + tz * tz;
+    float upx = umx + (umy * tz - umz * ty);
+    float upy = umy + (umz * tx - umx * tz);
+    float upz = umz + (umx * ty - umy * tx);
+    float f = __fdividef(2.0f, 1.0f + t2);
+    float sx = tx * f, sy = ty * f, sz = tz * f;
+    ux = umx + (upy * sz - upz * sy) + ex;
+    uy = umy + (upz * sx - upx * sz) + ey;
+    uz = umz + (upx * sy - upy * sx) + ez;
+}
+
+__device__ __forceinline__ float inv_gamma_fast(float ux, float uy, float uz)
+{
+    float u2 = ux * ux + uy * uy + uz * uz;
+    if (u2 < 1e8f) return rsqrtf(1.0f + u2);
+    double d2 = (double)ux * ux + (double)uy * uy + (double)uz * uz;  // FP64 island above gamma ~ 1e4
+    return (float)(1.0 / sqrt(1.0 + d2));
 }
 
 template <int T>
@@ -117,12 +174,18 @@ __global__ void __launch_bounds__(kTileThreads, 4)
     using B = Box2<T>;
     extern __shared__ float smem[];
     float *sF = smem;           // 6 components
-    float *sJ = smem + 6 * B::N;  // 3 components
+    int *sJ = reinterpret_cast<int *>(smem + 6 * B::N);  // 3 components, fixed point
+    float *sP = smem + 9 * B::N;                          // off_x, off_y, u_x, u_y, u_z
+    uint32_t *sPc = reinterpret_cast<uint32_t *>(sP + 5 * kPSlot);  // packed cell
     const int nit = (int)*nitems;
     const long long V = g.vol;
     const float hdx0 = pc.hdx_f[0], hdx1 = pc.hdx_f[1];
     const float k = pc.qmdt2_f;
     const float cjx = pc.cJ_f[0], cjy = pc.cJ_f[1], qw = pc.qw_f;
+    // fixed-point unit of the shared current box: 2^20 units per C
+    const float cmax = fabsf(qw) * fmaxf(fmaxf(fabsf(cjx), fabsf(cjy)) / fmaxf(fabsf(qw), 1e-30f), 1.0f);
+    const float jscale = 1048576.0f / fmaxf(cmax, 1e-30f);
+    const float junit = 1.0f / jscale;
     float *Fg = F + g.origin;  // interior origin
     const int rs = (int)g.sy;
     for (int it = blockIdx.x; it < nit; it += gridDim.x) {
@@ -138,28 +201,42 @@ __global__ void __launch_bounds__(kTileThreads, 4)
             if (gx < g.n[0] + g.G[0] && gy < g.n[1] + g.G[1]) v = __ldg(Fg + c * V + (long long)gy * rs + gx);
             sF[q] = v;
         }
-        for (int q = threadIdx.x; q < 3 * B::N; q += blockDim.x) sJ[q] = 0.f;
-        __syncthreads();
-        // 3. particles
+        for (int q = threadIdx.x; q < 3 * B::N; q += blockDim.x) sJ[q] = 0;
         // Lane striding: the chunk is cut into 32 contiguous segments of S
         // particles and lane l of every warp walks segment l.  Sorted
         // particles of one cell are contiguous, so the 32 lanes of one
         // shared-memory atomic target 32 different cells (different current
         // addresses) instead of one, whatever the in-tile order.
         const int S = (m.count + 31) >> 5;
+        // stage the chunk's particle state: every thread issues all its loads
+        // at once (coalesced), stored transposed to (segment position, lane)
+        for (int i = threadIdx.x; i < m.count; i += blockDim.x) {
+            const int l = i / S, j = i - l * S;
+            const int pos = j * 33 + l;
+            const long long p = (long long)m.start + i;
+            sPc[pos] = P.cell[p];
+            sP[0 * kPSlot + pos] = P.off[0][p];
+            sP[1 * kPSlot + pos] = P.off[1][p];
+            sP[2 * kPSlot + pos] = P.u[0][p];
+            sP[3 * kPSlot + pos] = P.u[1][p];
+            sP[4 * kPSlot + pos] = P.u[2][p];
+        }
+        __syncthreads();
+        // 3. particles
         const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
         for (int j = warp; j < S; j += kTileThreads / 32) {
             const int li = lane * S + j;
             if (li >= m.count) continue;
             const long long p = (long long)m.start + li;
-            const uint32_t cp = P.cell[p];
+            const int pos = j * 33 + lane;
+            const uint32_t cp = sPc[pos];
             if (cp == kDead) continue;
             int c[2];
             int dummy;
             unpack_cell(g, cp, c[0], c[1], dummy);
-            float o[2] = {P.off[0][p], P.off[1][p]};
-            float ux = P.u[0][p], uy = P.u[1][p], uz = P.u[2][p];
-            float ig = inv_gamma(ux, uy, uz);
+            float o[2] = {sP[pos], sP[kPSlot + pos]};
+            float ux = sP[2 * kPSlot + pos], uy = sP[3 * kPSlot + pos], uz = sP[4 * kPSlot + pos];
+            float ig = inv_gamma_fast(ux, uy, uz);
             drift_f32(c[0], o[0], hdx0 * ux * ig);
             drift_f32(c[1], o[1], hdx1 * uy * ig);
             const int ch[2] = {c[0], c[1]};
@@ -172,8 +249,8 @@ __global__ void __launch_bounds__(kTileThreads, 4)
             const bool gin = ch[0] - 1 >= bx0 && ch[0] + 2 < bx0 + B::WX && ch[1] - 1 >= by0 && ch[1] + 2 < by0 + B::WY;
             if (gin) gather2d(sF, B::N, B::WX, bx0, by0, icn, wn, ich, wh, eb);
             else gather2d(Fg, V, rs, 0, 0, icn, wn, ich, wh, eb);
-            boris<float>(ux, uy, uz, k * eb[0], k * eb[1], k * eb[2], k * eb[3], k * eb[4], k * eb[5]);
-            const float ig1 = inv_gamma(ux, uy, uz);
+            boris_fast(ux, uy, uz, k * eb[0], k * eb[1], k * eb[2], k * eb[3], k * eb[4], k * eb[5]);
+            const float ig1 = inv_gamma_fast(ux, uy, uz);
             const float d0 = hdx0 * ux * ig1, d1 = hdx1 * uy * ig1;
             drift_f32(c[0], o[0], d0);
             drift_f32(c[1], o[1], d1);
@@ -200,8 +277,13 @@ __global__ void __launch_bounds__(kTileThreads, 4)
             }
             const float jvz = qw * uz * ig1;
             const bool din = u0[0] >= bx0 && u0[0] + 3 < bx0 + B::WX && u0[1] >= by0 && u0[1] + 3 < by0 + B::WY;
-            if (din) deposit2d(sJ, B::N, B::WX, bx0, by0, u0[0], u0[1], S0, dS, cjx, cjy, jvz);
-            else deposit2d(Fg + JX * V, V, rs, 0, 0, u0[0], u0[1], S0, dS, cjx, cjy, jvz);
+            if (din) {
+                AccShared acc{sJ + (u0[1] - by0) * B::WX + (u0[0] - bx0), B::N, B::WX, jscale};
+                esirkepov2d(S0, dS, cjx, cjy, jvz, acc);
+            } else {
+                AccGlobal acc{Fg + JX * V + (long long)u0[1] * rs + u0[0], V, rs};
+                esirkepov2d(S0, dS, cjx, cjy, jvz, acc);
+            }
             // boundaries
             int cc[2] = {c1[0], c1[1]};
             bool dead = false;
@@ -229,10 +311,11 @@ __global__ void __launch_bounds__(kTileThreads, 4)
             P.u[2][p] = uz;
         }
         __syncthreads();
-        // 4. flush the current box, four floats at a time
+        // 4. flush the current box, four values at a time
         for (int q = threadIdx.x; q < 3 * B::N / 4; q += blockDim.x) {
-            const float4 v = reinterpret_cast<const float4 *>(sJ)[q];
-            if (v.x == 0.f && v.y == 0.f && v.z == 0.f && v.w == 0.f) continue;
+            const int4 iv = reinterpret_cast<const int4 *>(sJ)[q];
+            if ((iv.x | iv.y | iv.z | iv.w) == 0) continue;
+            const float4 v = make_float4(iv.x * junit, iv.y * junit, iv.z * junit, iv.w * junit);
             const int e = 4 * q;
             const int c = e / B::N, r = e - c * B::N;
             const int y = r / B::WX, x = r - y * B::WX;
