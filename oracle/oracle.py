@@ -85,10 +85,16 @@ def _bind_extras(L):
     for name, argt, rt in [
         ("or_bessel_k", [D, D], D),
         ("or_int_k13", [D], D),
-        ("or_dWrad_du", [D, D, D], D),
-        ("or_dWpair_de", [D, D, D], D),
-        ("or_Wrad", [D, D, D], D),
-        ("or_Wpair", [D, D, D], D),
+        ("or_qed_Frad", [D, D], D),
+        ("or_qed_Fpair", [D, D], D),
+        ("or_qed_Grad", [D], D),
+        ("or_qed_Gpair", [D], D),
+        ("or_qed_Prad", [D], D),
+        ("or_qed_cdf_rad", [D, D], D),
+        ("or_qed_cdf_pair", [D, D], D),
+        ("or_qed_sample_rad", [D, D], D),
+        ("or_qed_sample_pair", [D, D], D),
+        ("or_qed_method2_rad", [D, D, D, D], D),
     ]:
         if hasattr(L, name):
             f = getattr(L, name)

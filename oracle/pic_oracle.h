@@ -37,4 +37,17 @@ long or_step_count(const osim *s);
 void or_philox4x32_10(const uint32_t *ctr, const uint32_t *key, uint32_t *out);
 double or_uniform24(uint32_t x);
 
+double or_bessel_k(double nu, double x);
+double or_int_k13(double y);
+double or_qed_Frad(double u, double chi);
+double or_qed_Fpair(double v, double chi);
+double or_qed_Grad(double chi);
+double or_qed_Gpair(double chi);
+double or_qed_Prad(double chi);
+double or_qed_cdf_rad(double u, double chi);
+double or_qed_cdf_pair(double v, double chi);
+double or_qed_sample_rad(double chi, double r);
+double or_qed_sample_pair(double chi, double r);
+double or_qed_method2_rad(double chi, double dwdt, double r1, double r2);
+
 #endif

@@ -1,0 +1,99 @@
+"""Pins of the oracle's QED functions (Sec. IV, Eqs. (23), (24)) to closed
+forms, library Bessel functions and known asymptotic expansions."""
+import math
+
+import numpy as np
+import pytest
+from scipy import integrate, special
+
+from oracle import oracle as O
+
+
+@pytest.fixture(scope="module")
+def L():
+    return O.lib()
+
+
+@pytest.mark.parametrize("nu", [1.0 / 3.0, 2.0 / 3.0])
+@pytest.mark.parametrize("x", [1e-5, 1e-2, 0.3, 2.0, 17.0, 80.0])
+def test_bessel_k_matches_library(L, nu, x):
+    assert abs(L.or_bessel_k(nu, x) / special.kv(nu, x) - 1.0) < 1e-12
+
+
+@pytest.mark.parametrize("y", [1e-3, 0.2, 1.5, 9.0])
+def test_int_k13_matches_quadrature_of_library(L, y):
+    ref, _ = integrate.quad(lambda x: special.kv(1.0 / 3.0, x), y, np.inf, epsabs=1e-14, epsrel=1e-12)
+    assert abs(L.or_int_k13(y) / ref - 1.0) < 1e-9
+
+
+def test_int_k13_total_is_pi_over_sqrt3(L):
+    # Int_0^inf K_1/3 = pi / (2 cos(pi/6)) = pi / sqrt(3); the remainder near 0 is O(y^{2/3})
+    assert abs(L.or_int_k13(1e-15) - math.pi / math.sqrt(3.0)) < 1e-8
+
+
+def test_emission_rate_classical_limit(L):
+    """gamma W_rad -> 5 alpha chi E_s / (2 sqrt 3): Int_0^1 Frad du -> 5 pi chi / 2,
+    with the first quantum correction 1 - (8 sqrt3 / 15) chi"""
+    for chi in (1e-4, 3e-4):
+        g = L.or_qed_Grad(chi) / chi
+        # the next term is +3.5 chi^2 (measured): allow 5 chi^2
+        assert abs(g / (2.5 * math.pi) - (1.0 - 8.0 * math.sqrt(3.0) / 15.0 * chi)) < 5.0 * chi * chi + 1e-9
+
+
+def test_radiated_power_larmor_limit(L):
+    """Int_0^1 u Frad du -> 2 pi chi^2 / sqrt 3 (Larmor), correction 1 - (55 sqrt3 / 16) chi"""
+    for chi in (1e-4, 3e-4):
+        p = L.or_qed_Prad(chi) / (chi * chi)
+        assert abs(p / (2.0 * math.pi / math.sqrt(3.0)) - (1.0 - 55.0 * math.sqrt(3.0) / 16.0 * chi)) < 60 * chi * chi
+
+
+def test_pair_spectrum_symmetric_and_positive(L):
+    for chi in (0.5, 5.0, 50.0):
+        for v in (0.05, 0.2, 0.37, 0.49):
+            a, b = L.or_qed_Fpair(v, chi), L.or_qed_Fpair(1.0 - v, chi)
+            assert a > 0 and abs(a - b) <= 1e-13 * a
+
+
+def test_cdfs_monotone_from_zero_to_one(L):
+    for chi in (0.49, 4.9, 49.0):
+        us = np.linspace(0.0, 1.0, 21)
+        c = [L.or_qed_cdf_rad(u, chi) for u in us]
+        assert c[0] == 0.0 and abs(c[-1] - 1.0) < 1e-15 and np.all(np.diff(c) > 0)
+        cp = [L.or_qed_cdf_pair(u, chi) for u in us]
+        assert cp[0] == 0.0 and abs(cp[-1] - 1.0) < 1e-15 and np.all(np.diff(cp) >= 0)
+        assert abs(L.or_qed_cdf_pair(0.5, chi) - 0.5) < 1e-10  # symmetry (quadrature accuracy)
+
+
+def test_inverse_cdf_sampler_inverts_the_cdf(L):
+    for chi, r in ((0.49, 0.1), (4.9, 0.6), (49.0, 0.93)):
+        u = L.or_qed_sample_rad(chi, r)
+        assert abs(L.or_qed_cdf_rad(u, chi) - r) < 1e-10
+        v = L.or_qed_sample_pair(chi, r)
+        assert abs(L.or_qed_cdf_pair(v, chi) - r) < 1e-10
+
+
+def test_method_two_reproduces_the_spectrum(L):
+    """Method II (u0 = r1^3 accepted when r2 < 3 r1^2 dW/du dt) draws from the
+    same normalised spectrum as Method I: chi-square against Eq. (23)."""
+    rng = np.random.default_rng(8)
+    chi = 4.9
+    # 3 r^2 Frad(r^3) -> 3 Gamma(2/3) (3 chi)^(2/3) as r -> 0; keep the
+    # acceptance probability below one
+    pmax = 3.0 * math.gamma(2.0 / 3.0) * (3.0 * chi) ** (2.0 / 3.0)
+    dwdt = 0.5 / pmax
+    acc = []
+    r1 = rng.random(120000)
+    r2 = rng.random(120000)
+    for a, b in zip(r1, r2):
+        u = L.or_qed_method2_rad(chi, dwdt, a, b)
+        assert u != -2.0
+        if u >= 0:
+            acc.append(u)
+    acc = np.array(acc)
+    edges = np.linspace(0.0, 1.0, 11) ** 3
+    counts, _ = np.histogram(acc, edges)
+    cdf = np.array([L.or_qed_cdf_rad(e, chi) for e in edges])
+    expect = np.diff(cdf) * len(acc)
+    stat = np.sum((counts - expect) ** 2 / expect)
+    assert len(acc) > 2000
+    assert stat < 35.0  # chi^2 with 9 dof: p ~ 1e-4
