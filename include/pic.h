@@ -74,11 +74,18 @@ typedef struct {
 
 /* Species.  q in e, m in m_e, w = density carried by one macro-particle (in
  * n_r, the same for all particles of the species; a uniform density n with
- * ppc particles per cell has w = n/ppc).  capacity = maximum particle count. */
+ * ppc particles per cell has w = n/ppc).  capacity = maximum particle count
+ * (created photons and pairs are appended up to it).  kind: PIC_KIND_MASSIVE
+ * or PIC_KIND_PHOTON (q = 0, m = 0: moves at c along u, deposits no current).
+ * qed: 1 if a massive species emits photons (nonlinear Compton, Sec. IV). */
 typedef struct {
     double q, m, w;
     int64_t capacity;
+    int kind;
+    int qed;
 } pic_species;
+
+enum { PIC_KIND_MASSIVE = 0, PIC_KIND_PHOTON = 1 };
 
 /* Options.  precision: PIC_PREC_FP32_CELLOFF (int cell + FP32 in-cell offset,
  * FP32 fields and push) or PIC_PREC_FP64_PLAIN (absolute FP64 positions and
@@ -94,6 +101,7 @@ typedef struct {
     double rho_bg;
     void *stream;
     int push_variant; /* PIC_PUSH_AUTO or PIC_PUSH_SIMPLE (one thread per particle, global atomics) */
+    uint64_t seed;    /* key of the Philox4x32-10 stream of the QED Monte Carlo */
 } pic_options;
 
 /* Push kernels: AUTO uses the tiled shared-memory kernel wherever it exists
@@ -125,12 +133,52 @@ typedef struct {
     int64_t step;
     double t;
     double U_E, U_B;
-    double U_kin[PIC_MAX_SPECIES];
+    double U_kin[PIC_MAX_SPECIES]; /* photons: sum_p w |k| dV */
     double charge;
     double gauss_max;
     double E_absorbed;
     int64_t n_alive[PIC_MAX_SPECIES];
+    double E_photon_lost; /* energy of emitted photons below photon_emin */
 } pic_diag;
+
+/* QED Monte Carlo (Sec. IV) in the optical-depth form of Method I: every
+ * emitting particle carries an optical depth tau (FP64) drawn as -ln r; each
+ * step tau -= W dt with W the total rate of Eq. (23) (or (24) for photons) at
+ * the particle's quantum parameter chi; when tau <= 0 the event happens, the
+ * energy fraction comes from the inverse CDF of the spectrum at a Philox
+ * draw, and tau restarts.  Draws: Philox4x32-10 with key = seed, counter =
+ * (id_lo, id_hi, step, purpose).  Emitted photons go to photon_sp (collinear,
+ * energy u gamma; the emitter recoils to gamma (1-u)); converting photons
+ * create an electron in electron_sp and a positron in positron_sp (fractions
+ * 1-v and v, collinear).  Particle identities: (species << 48) | load index.
+ * lambda_r_m: wavelength of the reference frequency (2 pi c / omega_r, in
+ * metres), which sets E_s = m c^2 / (hbar omega_r).  Only the FP32 form
+ * implements the Monte Carlo. */
+enum { PIC_QED_OFF = 0, PIC_QED_TABLE = 1 };
+enum { PIC_QED_EMISSION = 0, PIC_QED_PAIR = 1 };
+typedef struct {
+    int mode;
+    int photon_sp, electron_sp, positron_sp; /* -1 = none */
+    double lambda_r_m;
+    double photon_emin;
+} pic_qed;
+
+/* Configure the QED Monte Carlo (builds the rate and inverse-CDF tables on
+ * the first call).  Call before loading particles of QED species, so their
+ * identities and optical depths are initialised.  Errors: PIC_ERR_ARG. */
+int pic_set_qed(pic_sim *sim, const pic_qed *qed);
+
+/* Evaluate the device tables the Monte Carlo uses, for inspection: with
+ * r == NULL, rate[i] = G(chi[i]) = Int_0^1 F (the total rate is
+ * alpha E_s G / (sqrt3 pi gamma)); otherwise rate[i] = the energy fraction
+ * whose CDF is r[i].  process: PIC_QED_EMISSION or PIC_QED_PAIR.  Host
+ * arrays of n values.  Errors: PIC_ERR_ARG, PIC_ERR_STATE (no tables). */
+int pic_qed_eval(pic_sim *sim, int process, int64_t n, const double *chi, const double *r, double *out);
+
+/* Copy the identities and optical depths of a QED species (photon or
+ * emitting species) in the current array order to caller-sized host arrays
+ * (either may be NULL).  Errors: PIC_ERR_ARG, PIC_ERR_CAPACITY. */
+int pic_get_qed_state(pic_sim *sim, int sp, int64_t cap, uint64_t *id, double *tau);
 
 /* Create a simulation: validates the grid, the Courant condition
  * dt < 1/sqrt(sum_d 1/dx_d^2), species and options, allocates all device

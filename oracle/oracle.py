@@ -71,6 +71,15 @@ def lib():
         L.or_diagnostics.restype = I
         L.or_step_count.argtypes = [P]
         L.or_step_count.restype = LG
+        L.or_add_species2.argtypes = [P, D, D, D, LG, I, I]
+        L.or_add_species2.restype = I
+        L.or_set_qed.argtypes = [P, I, I, I, D, D, C.c_uint64]
+        L.or_Es.argtypes = [P]
+        L.or_Es.restype = D
+        L.or_photon_lost.argtypes = [P]
+        L.or_photon_lost.restype = D
+        L.or_get_qed_state.argtypes = [P, I, P, P]
+        L.or_get_qed_state.restype = LG
         L.or_philox4x32_10.argtypes = [P, P, P]
         L.or_uniform24.argtypes = [C.c_uint32]
         L.or_uniform24.restype = D
@@ -170,12 +179,30 @@ class OracleSim:
             m[d] = int(self.n[d]) + (1 if self.bc[d] == ABSORB else 0)
         return (m[2], m[1], m[0])
 
-    def add_species(self, q, m, w, cap):
-        i = lib().or_add_species(self._h, float(q), float(m), float(w), int(cap))
+    def add_species(self, q, m, w, cap, kind=0, qed=0):
+        i = lib().or_add_species2(self._h, float(q), float(m), float(w), int(cap), int(kind), int(qed))
         if i < 0:
             raise ValueError("oracle: too many species")
         self.nsp += 1
         return i
+
+    def set_qed(self, photon_sp=-1, electron_sp=-1, positron_sp=-1, lambda_r_m=1e-6, photon_emin=0.0, seed=0):
+        lib().or_set_qed(self._h, int(photon_sp), int(electron_sp), int(positron_sp), float(lambda_r_m),
+                         float(photon_emin), C.c_uint64(int(seed) & 0xFFFFFFFFFFFFFFFF))
+
+    @property
+    def Es(self):
+        return lib().or_Es(self._h)
+
+    def photon_lost(self):
+        return lib().or_photon_lost(self._h)
+
+    def qed_state(self, isp):
+        n = lib().or_get_qed_state(self._h, int(isp), None, None)
+        ids = np.zeros(max(n, 1), dtype=np.uint64)
+        tau = np.zeros(max(n, 1))
+        lib().or_get_qed_state(self._h, int(isp), _ptr(ids), _ptr(tau))
+        return ids[:n], tau[:n]
 
     def load(self, isp, x, y, z, ux, uy, uz):
         n = len(ux)

@@ -63,10 +63,20 @@ typedef struct {
     double q, m, w;     /* charge (e), mass (m_e), density weight per macro-particle (n_r) */
     long n, cap;
     double *x;          /* 3*n absolute positions (L_r) */
-    double *u;          /* 3*n momenta per mass, u = gamma v */
+    double *u;          /* 3*n momenta per mass, u = gamma v (photons: k in m c) */
     unsigned char *alive;
     uint64_t *id;
+    int kind;           /* 0 massive, 1 photon (moves at c along k, no charge) */
+    int qed;            /* massive species that emits photons */
+    double *tau;        /* optical depth left (Sec. IV, Method I in optical-depth form) */
 } osp;
+
+/* one QED event of the current step, kept for spawning in parent order */
+typedef struct {
+    long parent;
+    double k[3];        /* photon momentum (emission) or converting photon's k */
+    double frac;        /* pair: positron fraction v */
+} oevent;
 
 typedef struct {
     int on, pol;        /* pol 0: linear along y; 1: circular */
@@ -89,6 +99,12 @@ struct osim {
     int tile[3];
     olaser L;
     double e_absorbed;
+    /* QED */
+    int qed_on, photon_sp, electron_sp, positron_sp;
+    double Es, emin, e_lost;
+    uint32_t key[2];
+    oevent *ev[OR_MAX_SPECIES];
+    long nev[OR_MAX_SPECIES], evcap[OR_MAX_SPECIES];
 };
 
 static long imod(long a, long n) { long r = a % n; return r < 0 ? r + n : r; }
@@ -172,22 +188,54 @@ void or_destroy(osim *s)
     if (!s) return;
     for (int c = 0; c < NF; c++) free(s->F[c]);
     for (int i = 0; i < s->nsp; i++) {
-        free(s->sp[i].x); free(s->sp[i].u); free(s->sp[i].alive); free(s->sp[i].id);
+        free(s->sp[i].x); free(s->sp[i].u); free(s->sp[i].alive); free(s->sp[i].id); free(s->sp[i].tau);
+        free(s->ev[i]);
     }
     free(s);
 }
 
-int or_add_species(osim *s, double q, double m, double w, long cap)
+int or_add_species2(osim *s, double q, double m, double w, long cap, int kind, int qed)
 {
     if (s->nsp >= OR_MAX_SPECIES) return -1;
     osp *p = &s->sp[s->nsp];
     p->q = q; p->m = m; p->w = w; p->cap = cap; p->n = 0;
+    p->kind = kind; p->qed = qed;
     p->x = (double *)calloc((size_t)(3 * cap + 3), sizeof(double));
     p->u = (double *)calloc((size_t)(3 * cap + 3), sizeof(double));
     p->alive = (unsigned char *)calloc((size_t)cap + 1, 1);
     p->id = (uint64_t *)calloc((size_t)cap + 1, sizeof(uint64_t));
+    p->tau = (double *)calloc((size_t)cap + 1, sizeof(double));
+    s->ev[s->nsp] = (oevent *)calloc((size_t)cap + 1, sizeof(oevent));
+    s->evcap[s->nsp] = cap + 1;
     return s->nsp++;
 }
+
+int or_add_species(osim *s, double q, double m, double w, long cap) { return or_add_species2(s, q, m, w, cap, 0, 0); }
+
+/* -ln r of the Philox draw (id, step = 0xFFFFFFFF, purpose 2): the optical
+ * depth a particle starts with */
+static double initial_tau(const osim *s, uint64_t id)
+{
+    uint32_t c[4] = {(uint32_t)id, (uint32_t)(id >> 32), 0xFFFFFFFFu, 2u}, w[4];
+    or_philox4x32_10(c, s->key, w);
+    return -log(or_uniform24(w[0]));
+}
+
+void or_set_qed(osim *s, int photon_sp, int electron_sp, int positron_sp, double lambda_r_m, double emin,
+                uint64_t seed)
+{
+    s->qed_on = 1;
+    s->photon_sp = photon_sp;
+    s->electron_sp = electron_sp;
+    s->positron_sp = positron_sp;
+    /* E_s = m c^2 / (hbar omega_r) = m c^2 lambda_r / (h c) */
+    s->Es = 510998.95 * lambda_r_m / 1.239841984e-6;
+    s->emin = emin;
+    s->key[0] = (uint32_t)seed;
+    s->key[1] = (uint32_t)(seed >> 32);
+}
+
+double or_Es(const osim *s) { return s->Es; }
 
 int or_load(osim *s, int isp, long n, const double *x, const double *y, const double *z,
             const double *ux, const double *uy, const double *uz)
@@ -203,7 +251,8 @@ int or_load(osim *s, int isp, long n, const double *x, const double *y, const do
         p->u[3 * b + 1] = uy[a];
         p->u[3 * b + 2] = uz[a];
         p->alive[b] = 1;
-        p->id[b] = (uint64_t)b;
+        p->id[b] = ((uint64_t)isp << 48) | (uint64_t)b;
+        p->tau[b] = initial_tau(s, p->id[b]);
     }
     p->n += n;
     return 0;
@@ -662,18 +711,21 @@ static void sort_species(osim *s, osp *p, long *perm_out)
     double *x = (double *)malloc((size_t)(3 * p->n + 3) * sizeof(double));
     double *u = (double *)malloc((size_t)(3 * p->n + 3) * sizeof(double));
     uint64_t *id = (uint64_t *)malloc((size_t)p->n * sizeof(uint64_t) + 8);
+    double *tau = (double *)malloc((size_t)p->n * sizeof(double) + 8);
     for (long b = 0; b < nalive; b++) {
         long a = perm[b];
         for (int d = 0; d < 3; d++) { x[3 * b + d] = p->x[3 * a + d]; u[3 * b + d] = p->u[3 * a + d]; }
         id[b] = p->id[a];
+        tau[b] = p->tau[a];
         if (perm_out) perm_out[b] = a;
     }
     memcpy(p->x, x, (size_t)(3 * nalive) * sizeof(double));
     memcpy(p->u, u, (size_t)(3 * nalive) * sizeof(double));
     memcpy(p->id, id, (size_t)nalive * sizeof(uint64_t));
+    memcpy(p->tau, tau, (size_t)nalive * sizeof(double));
     for (long b = 0; b < nalive; b++) p->alive[b] = 1;
     p->n = nalive;
-    free(x); free(u); free(id); free(perm); free(key); free(cnt);
+    free(x); free(u); free(id); free(tau); free(perm); free(key); free(cnt);
 }
 
 long or_sort_species(osim *s, int isp, long *perm_out)
@@ -683,11 +735,39 @@ long or_sort_species(osim *s, int isp, long *perm_out)
     return s->sp[isp].n;
 }
 
+/* quantum parameter chi = sqrt((g E + u x B)^2 - (u.E)^2) / E_s (Sec. IV:
+ * |F_{mu nu} p^nu| over the Schwinger field in the units of Eq. (8)) */
+static double chi_of(const osim *s, double g, const double *u, const double *eb)
+{
+    double fx = g * eb[0] + (u[1] * eb[5] - u[2] * eb[4]);
+    double fy = g * eb[1] + (u[2] * eb[3] - u[0] * eb[5]);
+    double fz = g * eb[2] + (u[0] * eb[4] - u[1] * eb[3]);
+    double ue = u[0] * eb[0] + u[1] * eb[1] + u[2] * eb[2];
+    double q = fx * fx + fy * fy + fz * fz - ue * ue;
+    return q > 0.0 ? sqrt(q) / s->Es : 0.0;
+}
+
+/* the prefactor alpha E_s dt / (sqrt 3 pi) of W dt (alpha = 1/137.035999084) */
+static double qed_pref(const osim *s)
+{
+    return (1.0 / 137.035999084) * s->Es * s->dt / (sqrt(3.0) * 3.14159265358979323846);
+}
+
+static void record(osim *s, int isp, long parent, const double *k, double frac)
+{
+    oevent *e = &s->ev[isp][s->nev[isp]++];
+    e->parent = parent;
+    e->k[0] = k[0]; e->k[1] = k[1]; e->k[2] = k[2];
+    e->frac = frac;
+}
+
 static void push_species(osim *s, osp *p)
 {
     double qm = p->q / p->m, qw = p->q * p->w;
     double dV = 1.0;
     for (int d = 0; d < s->dim; d++) dV *= s->dx[d];
+    int isp = (int)(p - s->sp);
+    int mc = s->qed_on && p->qed && s->photon_sp >= 0;
     for (long a = 0; a < p->n; a++) {
         if (!p->alive[a]) continue;
         double *x = &p->x[3 * a], *u = &p->u[3 * a];
@@ -696,6 +776,32 @@ static void push_species(osim *s, osp *p)
         double eb[6];
         or_gather(s, xh, eb);                      /* E, B at x^{n+1/2} */
         or_boris(qm, s->dt, eb, eb + 3, u);        /* u^{n+1} */
+        int emitted = 0;
+        double kph[3] = {0, 0, 0};
+        if (mc) {
+            /* optical depth form of Method I: tau -= W_rad dt; at tau <= 0
+             * emit u gamma along u (u from the inverse CDF of Eq. (23)),
+             * recoil to gamma (1-u), restart tau from -ln r */
+            double gam = gamma_of(u);
+            double chi = chi_of(s, gam, u, eb);
+            p->tau[a] -= qed_pref(s) * or_qed_Grad(chi) / gam;
+            if (p->tau[a] <= 0.0) {
+                uint32_t c[4] = {(uint32_t)p->id[a], (uint32_t)(p->id[a] >> 32), (uint32_t)s->step, 0u}, w[4];
+                or_philox4x32_10(c, s->key, w);
+                double frac = or_qed_sample_rad(chi, or_uniform24(w[0]));
+                double eg = frac * gam, um = sqrt(u[0] * u[0] + u[1] * u[1] + u[2] * u[2]);
+                double g1 = gam * (1.0 - frac);
+                if (g1 < 1.0) g1 = 1.0;
+                double sc = um > 0.0 ? sqrt(g1 * g1 - 1.0) / um : 0.0;
+                for (int d = 0; d < 3; d++) {
+                    kph[d] = um > 0.0 ? eg * u[d] / um : 0.0;
+                    u[d] *= sc;
+                }
+                p->tau[a] = -log(or_uniform24(w[1]));
+                if (eg >= s->emin) emitted = 1;
+                else s->e_lost += eg * p->w * dV;
+            }
+        }
         double x1[3] = {xh[0], xh[1], xh[2]};
         half_drift(s, x1, u, 1.0);                 /* x^{n+1} */
         double x32[3] = {x1[0], x1[1], x1[2]};
@@ -718,8 +824,110 @@ static void push_species(osim *s, osp *p)
             double uu = u[0] * u[0] + u[1] * u[1] + u[2] * u[2];
             s->e_absorbed += p->w * p->m * (uu / (g + 1.0)) * dV;
             p->alive[a] = 0;
+        } else if (emitted) {
+            record(s, isp, a, kph, 0.0);  /* an emitter absorbed in the same step leaves no photon */
         }
     }
+}
+
+/* photons move at c along k; W_pair dt of Eq. (24) at chi_gamma of the
+ * fields at x^{n+1/2} drains tau; at tau <= 0 the photon converts (the
+ * positron fraction v from the inverse CDF) */
+static void push_photons(osim *s, osp *p)
+{
+    int isp = (int)(p - s->sp);
+    int mc = s->qed_on && s->electron_sp >= 0 && s->positron_sp >= 0;
+    for (long a = 0; a < p->n; a++) {
+        if (!p->alive[a]) continue;
+        double *x = &p->x[3 * a], *k = &p->u[3 * a];
+        double km = sqrt(k[0] * k[0] + k[1] * k[1] + k[2] * k[2]);
+        double v[3] = {km > 0 ? k[0] / km : 0, km > 0 ? k[1] / km : 0, km > 0 ? k[2] / km : 0};
+        double xh[3] = {x[0], x[1], x[2]};
+        for (int d = 0; d < s->dim; d++) xh[d] += 0.5 * s->dt * v[d];
+        int conv = 0;
+        double frac = 0.0;
+        if (mc && km > 0.0) {
+            double eb[6];
+            or_gather(s, xh, eb);
+            double chi = chi_of(s, km, k, eb);
+            p->tau[a] -= qed_pref(s) * or_qed_Gpair(chi) / km;
+            if (p->tau[a] <= 0.0) {
+                uint32_t c[4] = {(uint32_t)p->id[a], (uint32_t)(p->id[a] >> 32), (uint32_t)s->step, 1u}, w[4];
+                or_philox4x32_10(c, s->key, w);
+                frac = or_qed_sample_pair(chi, or_uniform24(w[0]));
+                p->tau[a] = -log(or_uniform24(w[1]));
+                conv = 1;
+            }
+        }
+        double x1[3] = {xh[0], xh[1], xh[2]};
+        for (int d = 0; d < s->dim; d++) x1[d] += 0.5 * s->dt * v[d];
+        int dead = 0;
+        for (int d = 0; d < s->dim; d++) {
+            double L = (double)s->n[d] * s->dx[d];
+            if (s->bc[d] == BC_PERIODIC) {
+                if (x1[d] < 0.0) x1[d] += L;
+                if (x1[d] >= L) x1[d] -= L;
+            } else if (x1[d] < 0.0 || x1[d] >= L) {
+                dead = 1;
+            }
+        }
+        for (int d = 0; d < s->dim; d++) x[d] = x1[d];
+        if (dead) p->alive[a] = 0;
+        else if (conv) record(s, isp, a, k, frac);
+    }
+}
+
+static void append(osim *s, int isp, const double *x, const double *u, uint64_t id)
+{
+    osp *p = &s->sp[isp];
+    if (p->n >= p->cap) return;
+    long b = p->n++;
+    for (int d = 0; d < 3; d++) { p->x[3 * b + d] = x[d]; p->u[3 * b + d] = u[d]; }
+    p->alive[b] = 1;
+    p->id[b] = id;
+    p->tau[b] = initial_tau(s, id);
+}
+
+/* children of this step's events: first the pairs of converted photons
+ * (electron, then positron, in photon order), then the photons of each
+ * emitting species in species and parent order */
+static void spawn(osim *s)
+{
+    int ph = s->photon_sp;
+    if (ph >= 0 && s->electron_sp >= 0 && s->positron_sp >= 0) {
+        osp *P = &s->sp[ph];
+        for (long e = 0; e < s->nev[ph]; e++) {
+            oevent *ev = &s->ev[ph][e];
+            long a = ev->parent;
+            uint32_t c[4] = {(uint32_t)P->id[a], (uint32_t)(P->id[a] >> 32), (uint32_t)s->step, 1u}, w[4];
+            or_philox4x32_10(c, s->key, w);
+            uint64_t eid = ((uint64_t)w[3] << 32) | w[2];
+            double km = sqrt(ev->k[0] * ev->k[0] + ev->k[1] * ev->k[1] + ev->k[2] * ev->k[2]);
+            double ep = ev->frac * km, em = (1.0 - ev->frac) * km;
+            double pm = em > 1.0 ? sqrt(em * em - 1.0) : 0.0, pp = ep > 1.0 ? sqrt(ep * ep - 1.0) : 0.0;
+            double ue[3], uq[3];
+            for (int d = 0; d < 3; d++) {
+                ue[d] = km > 0 ? pm * ev->k[d] / km : 0.0;
+                uq[d] = km > 0 ? pp * ev->k[d] / km : 0.0;
+            }
+            append(s, s->electron_sp, &P->x[3 * a], ue, eid);
+            append(s, s->positron_sp, &P->x[3 * a], uq, eid + 1);
+            P->alive[a] = 0;
+        }
+    }
+    if (ph >= 0)
+        for (int i = 0; i < s->nsp; i++) {
+            osp *p = &s->sp[i];
+            if (p->kind != 0 || !p->qed) continue;
+            for (long e = 0; e < s->nev[i]; e++) {
+                oevent *ev = &s->ev[i][e];
+                long a = ev->parent;
+                uint32_t c[4] = {(uint32_t)p->id[a], (uint32_t)(p->id[a] >> 32), (uint32_t)s->step, 0u}, w[4];
+                or_philox4x32_10(c, s->key, w);
+                append(s, ph, &p->x[3 * a], ev->k, ((uint64_t)w[3] << 32) | w[2]);
+            }
+        }
+    for (int i = 0; i < s->nsp; i++) s->nev[i] = 0;
 }
 
 int or_step(osim *s, long nsteps)
@@ -732,7 +940,11 @@ int or_step(osim *s, long nsteps)
         update_E(s, h);                       /* E^{n+1/2} with J^n */
         update_B(s, h, t0 + h);               /* B^{n+1/2} */
         for (int c = JX; c <= JZ; c++) memset(s->F[c], 0, (size_t)ncells_store(s) * sizeof(double));
-        for (int i = 0; i < s->nsp; i++) push_species(s, &s->sp[i]);
+        for (int i = 0; i < s->nsp; i++) {
+            if (s->sp[i].kind == 1) push_photons(s, &s->sp[i]);
+            else push_species(s, &s->sp[i]);
+        }
+        if (s->qed_on) spawn(s);
         update_B(s, h, t0 + s->dt);           /* B^{n+1} */
         update_E(s, h);                       /* E^{n+1} with J^{n+1} */
         s->step++;
@@ -840,7 +1052,8 @@ int or_diagnostics(const osim *s, double *out)
             if (!p->alive[a]) continue;
             const double *u = &p->u[3 * a];
             double uu = u[0] * u[0] + u[1] * u[1] + u[2] * u[2];
-            uk += p->w * p->m * uu / (gamma_of(u) + 1.0);
+            if (p->kind == 1) uk += p->w * sqrt(uu); /* photon energy |k| */
+            else uk += p->w * p->m * uu / (gamma_of(u) + 1.0);
             na++;
         }
         out[7 + isp] = uk * dV;
@@ -868,3 +1081,16 @@ int or_diagnostics(const osim *s, double *out)
 }
 
 long or_step_count(const osim *s) { return s->step; }
+
+double or_photon_lost(const osim *s) { return s->e_lost; }
+
+long or_get_qed_state(const osim *s, int isp, uint64_t *id, double *tau)
+{
+    if (isp < 0 || isp >= s->nsp) return -1;
+    const osp *p = &s->sp[isp];
+    for (long a = 0; a < p->n; a++) {
+        if (id) id[a] = p->id[a];
+        if (tau) tau[a] = p->tau[a];
+    }
+    return p->n;
+}

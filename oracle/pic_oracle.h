@@ -15,6 +15,12 @@ osim *or_create(int dim, const long *n, const double *dx, const int *bc, double 
                 double rho_bg, int sort_interval, const int *tile);
 void or_destroy(osim *s);
 int or_add_species(osim *s, double q, double m, double w, long cap);
+int or_add_species2(osim *s, double q, double m, double w, long cap, int kind, int qed);
+void or_set_qed(osim *s, int photon_sp, int electron_sp, int positron_sp, double lambda_r_m, double emin,
+                uint64_t seed);
+double or_Es(const osim *s);
+double or_photon_lost(const osim *s);
+long or_get_qed_state(const osim *s, int isp, uint64_t *id, double *tau);
 int or_load(osim *s, int isp, long n, const double *x, const double *y, const double *z,
             const double *ux, const double *uy, const double *uz);
 int or_get_field(const osim *s, int c, double *out);

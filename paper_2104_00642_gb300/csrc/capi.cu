@@ -20,6 +20,7 @@
 #include "fdtd.cuh"
 #include "push.cuh"
 #include "push_tile.cuh"
+#include "qed_host.cuh"
 #include "sort.cuh"
 
 using namespace pic;
@@ -45,6 +46,15 @@ struct SpeciesState {
     uint32_t *item_scan = nullptr;  // scan scratch
     long long items_cap = 0;
     bool items_valid = false;
+    // QED: kind, optical depth and identity (double-buffered with the
+    // particle arrays), event flags and data of the current step
+    int kind = PIC_KIND_MASSIVE;
+    int qed = 0;
+    double *tau[2] = {nullptr, nullptr};
+    uint64_t *id[2] = {nullptr, nullptr};
+    uint32_t *ev = nullptr;
+    float *evk = nullptr;
+    bool has_qed_arrays() const { return tau[0] != nullptr; }
 };
 
 std::string g_create_error;
@@ -60,6 +70,14 @@ struct pic_sim {
     Grid g{};
     int precision = PIC_PREC_FP32_CELLOFF;
     int push_variant = PIC_PUSH_AUTO;
+    // QED
+    uint64_t seed = 0;
+    pic_qed qed{};
+    bool qed_on = false;
+    void *qed_tables = nullptr;
+    QedTables T{};
+    double Es = 0.0;
+    double *d_elost = nullptr;
     int sort_interval = 0;
     double rho_bg = 0.0;
     cudaStream_t st = nullptr;
@@ -137,6 +155,8 @@ PartF32 view32(pic_sim *s, int i, int buf)
     }
     v.n = p.n_hi;
     v.dn = p.d_count;
+    v.tau = p.tau[buf];
+    v.id = p.id[buf];
     return v;
 }
 
@@ -209,6 +229,7 @@ int sort_species(pic_sim *s, int i)
 bool use_tile_push(const pic_sim *s, const SpeciesState &p)
 {
     return s->push_variant == PIC_PUSH_AUTO && p.items_valid && s->precision == PIC_PREC_FP32_CELLOFF &&
+           p.kind == PIC_KIND_MASSIVE && !(s->qed_on && p.qed) &&
            s->g.dim == 2 && s->g.tile_log2[0] == s->g.tile_log2[1] &&
            (s->g.tile_log2[0] == 3 || s->g.tile_log2[0] == 4);
 }
@@ -322,9 +343,43 @@ Laser laser_at(const pic_sim *s, double t_new)
     return L;
 }
 
+QedParams qed_params(pic_sim *s, int i)
+{
+    SpeciesState &p = s->sp[i];
+    QedParams q{};
+    const double alpha = 1.0 / 137.035999084;
+    q.on = s->qed_on && (p.kind == PIC_KIND_PHOTON ? (s->qed.electron_sp >= 0 && s->qed.positron_sp >= 0)
+                                                   : (p.qed && s->qed.photon_sp >= 0));
+    q.pref = alpha * s->Es * s->g.dt / (std::sqrt(3.0) * 3.14159265358979323846);
+    q.inv_Es = s->Es > 0.0 ? 1.0 / s->Es : 0.0;
+    q.emin = s->qed.photon_emin;
+    q.key[0] = (uint32_t)s->seed;
+    q.key[1] = (uint32_t)(s->seed >> 32);
+    q.step = (uint32_t)s->step;
+    q.T = s->T;
+    q.tau = p.tau[p.cur];
+    q.id = p.id[p.cur];
+    q.ev = p.ev;
+    q.evk = p.evk;
+    q.e_lost = s->d_elost;
+    double dV = 1.0;
+    for (int d = 0; d < s->g.dim; d++) dV *= s->g.dx[d];
+    q.wdV = p.w * dV;
+    return q;
+}
+
 void push_species(pic_sim *s, int i, float *F)
 {
     SpeciesState &p = s->sp[i];
+    if (p.kind == PIC_KIND_PHOTON) {
+        launch_push_photon_f32(view32(s, i, p.cur), F, s->g, push_const(s, p), qed_params(s, i), s->d_err, s->st);
+        return;
+    }
+    if (s->qed_on && p.qed) {
+        launch_push_qed_f32(view32(s, i, p.cur), F, s->g, push_const(s, p), qed_params(s, i), s->d_err, s->d_eabs,
+                            s->st);
+        return;
+    }
     if (use_tile_push(s, p))
         launch_push_tile2d(view32(s, i, p.cur), p.items, p.nitems, (long long)tile_items_capacity(p.n_hi, s->g.ntiles),
                            F, s->g, push_const(s, p), s->d_err, s->d_eabs, s->st);
@@ -336,6 +391,43 @@ void push_species(pic_sim *s, int i, double *F)
 {
     SpeciesState &p = s->sp[i];
     launch_push_f64(view64(s, i, p.cur), F, s->g, push_const(s, p), s->d_err, s->d_eabs, s->st);
+}
+
+// Append this step's QED children, in a fixed order: first the pairs of the
+// photons that converted (electrons, then positrons, in photon order), then
+// the photons emitted by each emitting species in species order (in parent
+// order).  The event flags are exclusive-scanned in array order.
+void qed_spawn(pic_sim *s)
+{
+    if (!s->qed_on) return;
+    uint32_t *off = (uint32_t *)s->sort_scratch;
+    const int ph = s->qed.photon_sp, el = s->qed.electron_sp, po = s->qed.positron_sp;
+    const int dim = s->g.dim;
+    auto scan = [&](const SpeciesState &p) {
+        scan_exclusive(p.ev, off, p.n_hi + 1, off + p.n_hi + 64, s->st);
+        return off + p.n_hi;  // total
+    };
+    if (ph >= 0 && el >= 0 && po >= 0 && s->sp[ph].n_hi > 0) {
+        SpeciesState &P = s->sp[ph], &E = s->sp[el], &O = s->sp[po];
+        const uint32_t *tot = scan(P);
+        launch_spawn_pairs(view32(s, ph, P.cur), off, tot, qed_params(s, ph), view32(s, el, E.cur), E.tau[E.cur],
+                           E.id[E.cur], E.ev, E.d_count, E.cap, view32(s, po, O.cur), O.tau[O.cur], O.id[O.cur], O.ev,
+                           O.d_count, O.cap, dim, s->d_err, s->st);
+        E.n_hi = std::min(E.cap, E.n_hi + P.n_hi);
+        O.n_hi = std::min(O.cap, O.n_hi + P.n_hi);
+        E.items_valid = O.items_valid = false;
+    }
+    if (ph < 0) return;
+    for (int i = 0; i < s->nsp; i++) {
+        SpeciesState &p = s->sp[i];
+        if (p.kind == PIC_KIND_PHOTON || !p.qed || p.n_hi == 0) continue;
+        SpeciesState &P = s->sp[ph];
+        const uint32_t *tot = scan(p);
+        launch_spawn_photons(view32(s, i, p.cur), off, tot, qed_params(s, i), view32(s, ph, P.cur), P.tau[P.cur],
+                             P.id[P.cur], P.ev, P.d_count, P.cap, dim, s->d_err, s->st);
+        P.n_hi = std::min(P.cap, P.n_hi + p.n_hi);
+        P.items_valid = false;
+    }
 }
 
 // nsteps split steps (Sec. II.F).  The first half step of a call runs
@@ -370,6 +462,7 @@ int step_loop(pic_sim *s, int64_t nsteps)
             if (s->sp[i].n_hi) s->prof_push++;
             push_species(s, i, F);
         }
+        qed_spawn(s);
         ph_end(s, PIC_PHASE_PUSH);
         ph_begin(s);
         launch_fold<R>(F, g, s->st);
@@ -470,6 +563,7 @@ int pic_create(const pic_grid *grid, double dt, const pic_species *species, int 
     s->precision = prec;
     s->sort_interval = opt ? opt->sort_interval : 0;
     s->push_variant = opt ? opt->push_variant : PIC_PUSH_AUTO;
+    s->seed = opt ? opt->seed : 0;
     s->rho_bg = opt ? opt->rho_bg : 0.0;
     s->st = opt ? (cudaStream_t)opt->stream : nullptr;
     s->nsp = nsp;
@@ -488,14 +582,30 @@ int pic_create(const pic_grid *grid, double dt, const pic_species *species, int 
     for (int i = 0; i < nsp && !rc; i++) {
         SpeciesState &p = s->sp[i];
         const pic_species &q = species[i];
-        if (!(q.m > 0.0) || q.capacity < 0 || q.capacity > 0x7FFFFFFFll) {
+        const bool photon = q.kind == PIC_KIND_PHOTON;
+        if ((q.kind != PIC_KIND_MASSIVE && !photon) || (!photon && !(q.m > 0.0)) ||
+            (photon && (q.q != 0.0 || q.m != 0.0 || q.qed)) || q.capacity < 0 || q.capacity > 0x7FFFFFFFll) {
             rc = fail(s, PIC_ERR_ARG, "pic_create: bad species %d", i);
+            break;
+        }
+        if ((photon || q.qed) && prec != PIC_PREC_FP32_CELLOFF) {
+            rc = fail(s, PIC_ERR_ARG, "pic_create: the QED Monte Carlo exists in the FP32 form only");
             break;
         }
         p.q = q.q;
         p.m = q.m;
         p.w = q.w;
         p.cap = q.capacity;
+        p.kind = q.kind;
+        p.qed = q.qed;
+        if (photon || q.qed) {
+            for (int b = 0; b < 2 && !rc; b++) {
+                rc = dalloc(s, (void **)&p.tau[b], (size_t)p.cap * 8);
+                rc = rc ? rc : dalloc(s, (void **)&p.id[b], (size_t)p.cap * 8);
+            }
+            rc = rc ? rc : dalloc(s, (void **)&p.ev, (size_t)(p.cap + 1) * 4);
+            rc = rc ? rc : dalloc(s, (void **)&p.evk, (size_t)(p.cap + 1) * 16);
+        }
         maxcap = std::max(maxcap, p.cap);
         rc = rc ? rc : dalloc(s, (void **)&p.d_count, sizeof(long long));
         rc = rc ? rc : dalloc(s, (void **)&p.tile_start, (size_t)(g.ntiles + 1) * sizeof(uint32_t));
@@ -524,10 +634,14 @@ int pic_create(const pic_grid *grid, double dt, const pic_species *species, int 
     rc = rc ? rc : dalloc(s, (void **)&s->diag_out, 16 * sizeof(double));
     rc = rc ? rc : dalloc(s, (void **)&s->d_err, sizeof(int));
     rc = rc ? rc : dalloc(s, (void **)&s->d_eabs, sizeof(double));
+    rc = rc ? rc : dalloc(s, (void **)&s->d_elost, sizeof(double));
     if (!rc) {
         cudaError_t z = cudaMemsetAsync(s->F, 0, (size_t)NCOMP * g.vol * R, s->st);
         if (z == cudaSuccess) z = cudaMemsetAsync(s->d_err, 0, sizeof(int), s->st);
         if (z == cudaSuccess) z = cudaMemsetAsync(s->d_eabs, 0, sizeof(double), s->st);
+        if (z == cudaSuccess) z = cudaMemsetAsync(s->d_elost, 0, sizeof(double), s->st);
+        for (int i = 0; i < nsp && z == cudaSuccess; i++)
+            if (s->sp[i].ev) z = cudaMemsetAsync(s->sp[i].ev, 0, (size_t)(s->sp[i].cap + 1) * 4, s->st);
         for (int i = 0; i < nsp && z == cudaSuccess; i++)
             z = cudaMemsetAsync(s->sp[i].d_count, 0, sizeof(long long), s->st);
         if (z == cudaSuccess) z = cudaStreamSynchronize(s->st);
@@ -609,6 +723,77 @@ int pic_load_particles(pic_sim *s, int sp, int64_t n, const double *x, const dou
     if (e != cudaSuccess) return fail(s, PIC_ERR_CUDA, "pic_load_particles: %s", cudaGetErrorString(e));
     p.n_hi = newn;
     p.items_valid = false;  // appended particles are in no tile's work item until the next sort
+    if (p.has_qed_arrays()) {
+        // identity (species << 48) | load index, optical depth -ln r of its Philox draw
+        const uint32_t key[2] = {(uint32_t)s->seed, (uint32_t)(s->seed >> 32)};
+        launch_init_qed(cnt, n, (uint64_t)sp << 48, p.id[p.cur], p.tau[p.cur], key, s->st);
+        CK(cudaGetLastError());
+        CK(cudaStreamSynchronize(s->st));
+    }
+    return PIC_OK;
+}
+
+int pic_set_qed(pic_sim *s, const pic_qed *Q)
+{
+    if (!s || !Q) return PIC_ERR_ARG;
+    if (Q->mode != PIC_QED_OFF && Q->mode != PIC_QED_TABLE) return fail(s, PIC_ERR_ARG, "pic_set_qed: bad mode");
+    auto kind_ok = [&](int i, int kind) { return i == -1 || (i >= 0 && i < s->nsp && s->sp[i].kind == kind); };
+    if (!kind_ok(Q->photon_sp, PIC_KIND_PHOTON) || !kind_ok(Q->electron_sp, PIC_KIND_MASSIVE) ||
+        !kind_ok(Q->positron_sp, PIC_KIND_MASSIVE) || !(Q->lambda_r_m > 0.0) || Q->photon_emin < 0.0)
+        return fail(s, PIC_ERR_ARG, "pic_set_qed: bad species index, kind or wavelength");
+    if (Q->electron_sp >= 0 && (s->sp[Q->electron_sp].q >= 0.0 || !s->sp[Q->electron_sp].has_qed_arrays()))
+        return fail(s, PIC_ERR_ARG, "pic_set_qed: the pair-electron species must be a negative QED species");
+    if (Q->positron_sp >= 0 && (s->sp[Q->positron_sp].q <= 0.0 || !s->sp[Q->positron_sp].has_qed_arrays()))
+        return fail(s, PIC_ERR_ARG, "pic_set_qed: the pair-positron species must be a positive QED species");
+    if (!s->qed_tables) {
+        int rc = dalloc(s, &s->qed_tables, qed_table_bytes());
+        if (rc) return rc;
+        if (qed_upload_tables(s->qed_tables, &s->T, s->st)) return fail(s, PIC_ERR_CUDA, "pic_set_qed: table upload");
+    }
+    // E_s = m c^2 / (hbar omega_r) = m c^2 lambda_r / (h c)
+    const double mc2_eV = 510998.95, hc_eVm = 1.239841984e-6;
+    s->Es = mc2_eV * Q->lambda_r_m / hc_eVm;
+    s->qed = *Q;
+    s->qed_on = Q->mode != PIC_QED_OFF;
+    return PIC_OK;
+}
+
+int pic_qed_eval(pic_sim *s, int process, int64_t n, const double *chi, const double *r, double *out)
+{
+    if (!s) return PIC_ERR_ARG;
+    if ((process != PIC_QED_EMISSION && process != PIC_QED_PAIR) || n < 0 || !chi || !out)
+        return fail(s, PIC_ERR_ARG, "pic_qed_eval: bad arguments");
+    if (!s->qed_tables) return fail(s, PIC_ERR_STATE, "pic_qed_eval: call pic_set_qed first");
+    if (n == 0) return PIC_OK;
+    double *d = nullptr;
+    CK(cudaMalloc(&d, (size_t)n * 3 * sizeof(double)));
+    cudaError_t e = cudaMemcpyAsync(d, chi, n * 8, cudaMemcpyHostToDevice, s->st);
+    if (e == cudaSuccess && r) e = cudaMemcpyAsync(d + n, r, n * 8, cudaMemcpyHostToDevice, s->st);
+    if (e == cudaSuccess) {
+        launch_qed_eval(s->T, s->precision == PIC_PREC_FP64_PLAIN, process, n, d, r ? d + n : nullptr, d + 2 * n,
+                        s->st);
+        e = cudaGetLastError();
+    }
+    if (e == cudaSuccess) e = cudaMemcpyAsync(out, d + 2 * n, n * 8, cudaMemcpyDeviceToHost, s->st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s->st);
+    cudaFree(d);
+    if (e != cudaSuccess) return fail(s, PIC_ERR_CUDA, "pic_qed_eval: %s", cudaGetErrorString(e));
+    return PIC_OK;
+}
+
+int pic_get_qed_state(pic_sim *s, int sp, int64_t cap, uint64_t *id, double *tau)
+{
+    if (!s) return PIC_ERR_ARG;
+    if (sp < 0 || sp >= s->nsp || !s->sp[sp].has_qed_arrays())
+        return fail(s, PIC_ERR_ARG, "pic_get_qed_state: not a QED species");
+    long long cnt = 0;
+    int rc = read_count(s, sp, &cnt);
+    if (rc) return rc;
+    if (cnt > cap) return fail(s, PIC_ERR_CAPACITY, "pic_get_qed_state: capacity");
+    SpeciesState &p = s->sp[sp];
+    if (cnt && id) CK(cudaMemcpyAsync(id, p.id[p.cur], cnt * 8, cudaMemcpyDeviceToHost, s->st));
+    if (cnt && tau) CK(cudaMemcpyAsync(tau, p.tau[p.cur], cnt * 8, cudaMemcpyDeviceToHost, s->st));
+    CK(cudaStreamSynchronize(s->st));
     return PIC_OK;
 }
 
@@ -849,10 +1034,11 @@ int pic_diagnostics(pic_sim *s, pic_diag *d)
     for (int i = 0; i < s->nsp; i++) {
         SpeciesState &p = s->sp[i];
         if (s->precision == PIC_PREC_FP64_PLAIN) diag_kinetic_f64(view64(s, i, p.cur), s->diag_scratch, s->diag_out, s->st);
-        else diag_kinetic_f32(view32(s, i, p.cur), s->diag_scratch, s->diag_out, s->st);
+        else
+            diag_kinetic_f32(view32(s, i, p.cur), p.kind == PIC_KIND_PHOTON, s->diag_scratch, s->diag_out, s->st);
         CK(cudaMemcpyAsync(h, s->diag_out, 2 * sizeof(double), cudaMemcpyDeviceToHost, s->st));
         CK(cudaStreamSynchronize(s->st));
-        d->U_kin[i] = h[0] * p.w * p.m * dV;
+        d->U_kin[i] = h[0] * p.w * (p.kind == PIC_KIND_PHOTON ? 1.0 : p.m) * dV;
         d->n_alive[i] = (int64_t)llround(h[1]);
         charge += p.q * p.w * h[1] * dV;
     }
@@ -869,6 +1055,7 @@ int pic_diagnostics(pic_sim *s, pic_diag *d)
     CK(cudaGetLastError());
     d->gauss_max = h[0];
     d->E_absorbed = h[1];
+    CK(cudaMemcpy(&d->E_photon_lost, s->d_elost, sizeof(double), cudaMemcpyDeviceToHost));
     d->step = s->step;
     d->t = (double)s->step * g.dt;
     bool finite = std::isfinite(d->U_E) && std::isfinite(d->U_B) && std::isfinite(d->gauss_max);

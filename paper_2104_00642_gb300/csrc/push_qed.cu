@@ -1,0 +1,231 @@
+// push_qed.cu -- particle push with the QED Monte Carlo (Sec. IV) fused in,
+// FP32 cell+offset form, one thread per particle.
+//
+// Leptons: half drift, gather, Boris (as in push.cu), then the optical-depth
+// form of Method I: tau -= W_rad(chi, gamma) dt in FP64 with chi from the
+// gathered E^{n+1/2}, B^{n+1/2} and u^{n+1}; when tau <= 0 a photon of
+// energy u gamma is emitted along u (u from the inverse CDF of Eq. (23) with
+// a Philox draw), the lepton recoils to gamma (1 - u) along its direction and
+// tau restarts from -ln r.  The recoiled momentum then drives both drifts
+// and the Esirkepov deposit.
+// Photons: move at c along k, gather E, B at x^{n+1/2}, tau -= W_pair dt with
+// chi_gamma from k; when tau <= 0 the photon converts (the pair fraction v
+// from the inverse CDF of Eq. (24)); no current.
+#include "push_dev.cuh"
+#include "qed_host.cuh"
+
+namespace pic {
+
+template <int DIM>
+__global__ void __launch_bounds__(256) k_push_qed_f32(PartF32 P, float *__restrict__ F, Grid g, PushConst pc,
+                                                      QedParams q, int *err, double *e_abs)
+{
+    const long long p = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (p >= *P.dn) {
+        if (p <= P.n) q.ev[p] = 0;  // slots past the live count (and the scan's end slot) carry no event
+        return;
+    }
+    const uint32_t pc0 = P.cell[p];
+    if (pc0 == kDead) {
+        q.ev[p] = 0;
+        return;
+    }
+    int c[3];
+    unpack_cell(g, pc0, c[0], c[1], c[2]);
+    float o[3] = {P.off[0][p], DIM >= 2 ? P.off[1][p] : 0.f, DIM >= 3 ? P.off[2][p] : 0.f};
+    float ux = P.u[0][p], uy = P.u[1][p], uz = P.u[2][p];
+    float u[3] = {ux, uy, uz};
+    float ig = inv_gamma(ux, uy, uz);
+#pragma unroll
+    for (int d = 0; d < DIM; d++) drift_f32(c[d], o[d], pc.hdx_f[d] * u[d] * ig);
+    const int ch[3] = {c[0], c[1], c[2]};
+    const float oh[3] = {o[0], o[1], o[2]};
+    int icn[3] = {0, 0, 0}, ich[3] = {0, 0, 0};
+    float wn[3][3], wh[3][3];
+#pragma unroll
+    for (int d = 0; d < DIM; d++) axis_w_f32(c[d], o[d], icn[d], wn[d], ich[d], wh[d]);
+    float eb[6];
+    gather<float, DIM>(F, g, icn, wn, ich, wh, eb);
+    const float k = pc.qmdt2_f;
+    boris<float>(ux, uy, uz, k * eb[0], k * eb[1], k * eb[2], k * eb[3], k * eb[4], k * eb[5]);
+    // --- QED: optical depth, emission, recoil ---
+    uint32_t event = 0;
+    float4 evd = make_float4(0.f, 0.f, 0.f, 0.f);
+    if (q.on) {
+        const double uu = (double)ux * ux + (double)uy * uy + (double)uz * uz;
+        const double gam = sqrt(1.0 + uu);
+        const double chi = chi_of<float>((float)gam, ux, uy, uz, eb[0], eb[1], eb[2], eb[3], eb[4], eb[5], q.inv_Es);
+        double tau = q.tau[p] - q.pref * qed_rate<float>(q.T, QED_RAD, chi) / gam;
+        if (tau <= 0.0) {
+            uint32_t w[4];
+            const uint64_t id = q.id[p];
+            philox4x32_10((uint32_t)id, (uint32_t)(id >> 32), q.step, QP_EMIT, q.key[0], q.key[1], w);
+            const double frac = qed_sample<float>(q.T, QED_RAD, chi, uniform24(w[0]));
+            const double eg = frac * gam;
+            const double umag = sqrt(uu);
+            const double g1 = fmax(gam * (1.0 - frac), 1.0);
+            const double s = umag > 0.0 ? sqrt(g1 * g1 - 1.0) / umag : 0.0;
+            const double kx = umag > 0.0 ? eg * ux / umag : 0.0, ky = umag > 0.0 ? eg * uy / umag : 0.0,
+                         kz = umag > 0.0 ? eg * uz / umag : 0.0;
+            ux = (float)(ux * s);
+            uy = (float)(uy * s);
+            uz = (float)(uz * s);
+            tau = -log(uniform24(w[1]));
+            if (eg >= q.emin) {
+                event = 1;
+                evd = make_float4((float)kx, (float)ky, (float)kz, 0.f);
+            } else {
+                atomicAdd(q.e_lost, eg * q.wdV);
+            }
+        }
+        q.tau[p] = tau;
+    }
+    const float ig1 = inv_gamma(ux, uy, uz);
+    u[0] = ux;
+    u[1] = uy;
+    u[2] = uz;
+#pragma unroll
+    for (int d = 0; d < DIM; d++) drift_f32(c[d], o[d], pc.hdx_f[d] * u[d] * ig1);
+    int c1[3] = {c[0], c[1], c[2]};
+    const float o1[3] = {o[0], o[1], o[2]};
+#pragma unroll
+    for (int d = 0; d < DIM; d++) drift_f32(c[d], o[d], pc.hdx_f[d] * u[d] * ig1);
+    float S0[3][5], dS[3][5];
+    int base[3] = {0, 0, 0};
+    bool ok = true;
+#pragma unroll
+    for (int d = 0; d < DIM; d++) {
+        int i0, i1;
+        float w0[3], w1[3];
+        axis_wn_f32(ch[d], oh[d], i0, w0);
+        axis_wn_f32(c[d], o[d], i1, w1);
+        ok &= window5<float>(i0, w0, i1, w1, S0[d], dS[d]);
+        base[d] = i0 - 2;
+    }
+    if (!ok) {
+        atomicOr(err, ERR_CFL);
+        q.ev[p] = 0;
+        return;
+    }
+    const float cJ[3] = {pc.cJ_f[0], pc.cJ_f[1], pc.cJ_f[2]};
+    deposit_global<float, DIM>(F, g, base, S0, dS, cJ, pc.qw_f * uy * ig1, pc.qw_f * uz * ig1);
+    bool dead = false;
+#pragma unroll
+    for (int d = 0; d < DIM; d++) {
+        if (g.bc[d] == PERIODIC) {
+            if (c1[d] < 0) c1[d] += g.n[d];
+            else if (c1[d] >= g.n[d]) c1[d] -= g.n[d];
+        } else if (c1[d] < 0 || c1[d] >= g.n[d]) {
+            dead = true;
+        }
+    }
+    if (!isfinite(ux + uy + uz)) atomicOr(err, ERR_NONFINITE);
+    if (dead) {
+        P.cell[p] = kDead;
+        const double uu = (double)ux * ux + (double)uy * uy + (double)uz * uz;
+        atomicAdd(e_abs, pc.wmdV * uu / (sqrt(1.0 + uu) + 1.0));
+        event = 0;  // an emitter absorbed in the same step records no photon
+    } else {
+        P.cell[p] = pack_cell(g, c1[0], DIM >= 2 ? c1[1] : 0, DIM >= 3 ? c1[2] : 0);
+    }
+#pragma unroll
+    for (int d = 0; d < DIM; d++) P.off[d][p] = o1[d];
+    P.u[0][p] = ux;
+    P.u[1][p] = uy;
+    P.u[2][p] = uz;
+    q.ev[p] = event;
+    if (event) reinterpret_cast<float4 *>(q.evk)[p] = evd;
+}
+
+template <int DIM>
+__global__ void __launch_bounds__(256) k_push_photon_f32(PartF32 P, const float *__restrict__ F, Grid g, PushConst pc,
+                                                         QedParams q, int *err)
+{
+    const long long p = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (p >= *P.dn) {
+        if (p <= P.n) q.ev[p] = 0;  // slots past the live count (and the scan's end slot) carry no event
+        return;
+    }
+    const uint32_t pc0 = P.cell[p];
+    if (pc0 == kDead) {
+        q.ev[p] = 0;
+        return;
+    }
+    int c[3];
+    unpack_cell(g, pc0, c[0], c[1], c[2]);
+    float o[3] = {P.off[0][p], DIM >= 2 ? P.off[1][p] : 0.f, DIM >= 3 ? P.off[2][p] : 0.f};
+    const float kx = P.u[0][p], ky = P.u[1][p], kz = P.u[2][p];
+    const float km = sqrtf(kx * kx + ky * ky + kz * kz);
+    const float ik = km > 0.f ? 1.0f / km : 0.f;
+    const float v[3] = {kx * ik, ky * ik, kz * ik};
+#pragma unroll
+    for (int d = 0; d < DIM; d++) drift_f32(c[d], o[d], pc.hdx_f[d] * v[d]);
+    uint32_t event = 0;
+    float4 evd = make_float4(0.f, 0.f, 0.f, 0.f);
+    if (q.on) {
+        int icn[3] = {0, 0, 0}, ich[3] = {0, 0, 0};
+        float wn[3][3], wh[3][3];
+#pragma unroll
+        for (int d = 0; d < DIM; d++) axis_w_f32(c[d], o[d], icn[d], wn[d], ich[d], wh[d]);
+        float eb[6];
+        gather<float, DIM>(F, g, icn, wn, ich, wh, eb);
+        const double chi = chi_of<float>(km, kx, ky, kz, eb[0], eb[1], eb[2], eb[3], eb[4], eb[5], q.inv_Es);
+        double tau = q.tau[p] - (km > 0.f ? q.pref * qed_rate<float>(q.T, QED_PAIR, chi) / km : 0.0);
+        if (tau <= 0.0) {
+            uint32_t w[4];
+            const uint64_t id = q.id[p];
+            philox4x32_10((uint32_t)id, (uint32_t)(id >> 32), q.step, QP_PAIR, q.key[0], q.key[1], w);
+            const double vf = qed_sample<float>(q.T, QED_PAIR, chi, uniform24(w[0]));
+            event = 1;
+            evd = make_float4(kx, ky, kz, (float)vf);
+            tau = -log(uniform24(w[1]));
+        }
+        q.tau[p] = tau;
+    }
+#pragma unroll
+    for (int d = 0; d < DIM; d++) drift_f32(c[d], o[d], pc.hdx_f[d] * v[d]);
+    bool dead = false;
+#pragma unroll
+    for (int d = 0; d < DIM; d++) {
+        if (g.bc[d] == PERIODIC) {
+            if (c[d] < 0) c[d] += g.n[d];
+            else if (c[d] >= g.n[d]) c[d] -= g.n[d];
+        } else if (c[d] < 0 || c[d] >= g.n[d]) {
+            dead = true;
+        }
+    }
+    if (dead) {
+        P.cell[p] = kDead;
+        event = 0;  // a photon leaving through an absorbing face does not convert
+    } else {
+        P.cell[p] = pack_cell(g, c[0], DIM >= 2 ? c[1] : 0, DIM >= 3 ? c[2] : 0);
+    }
+#pragma unroll
+    for (int d = 0; d < DIM; d++) P.off[d][p] = o[d];
+    q.ev[p] = event;
+    if (event) reinterpret_cast<float4 *>(q.evk)[p] = evd;
+}
+
+void launch_push_qed_f32(const PartF32 &P, float *F, const Grid &g, const PushConst &pc, const QedParams &q,
+                         int *err, double *e_abs, cudaStream_t st)
+{
+    if (P.n == 0) return;
+    note_launch();
+    const int nb = div_up(P.n + 1, 256);
+    if (g.dim == 1) k_push_qed_f32<1><<<nb, 256, 0, st>>>(P, F, g, pc, q, err, e_abs);
+    else if (g.dim == 2) k_push_qed_f32<2><<<nb, 256, 0, st>>>(P, F, g, pc, q, err, e_abs);
+    else k_push_qed_f32<3><<<nb, 256, 0, st>>>(P, F, g, pc, q, err, e_abs);
+}
+
+void launch_push_photon_f32(const PartF32 &P, const float *F, const Grid &g, const PushConst &pc,
+                            const QedParams &q, int *err, cudaStream_t st)
+{
+    if (P.n == 0) return;
+    note_launch();
+    const int nb = div_up(P.n + 1, 256);
+    if (g.dim == 1) k_push_photon_f32<1><<<nb, 256, 0, st>>>(P, F, g, pc, q, err);
+    else if (g.dim == 2) k_push_photon_f32<2><<<nb, 256, 0, st>>>(P, F, g, pc, q, err);
+    else k_push_photon_f32<3><<<nb, 256, 0, st>>>(P, F, g, pc, q, err);
+}
+
+}  // namespace pic

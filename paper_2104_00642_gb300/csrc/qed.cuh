@@ -1,0 +1,162 @@
+// qed.cuh -- device side of the QED Monte Carlo (Sec. IV): counter-based
+// random numbers, quantum parameters, tabulated rates and inverse CDFs of
+// nonlinear Compton emission (Eq. (23)) and Breit-Wheeler pair creation
+// (Eq. (24)).
+//
+// Normalised forms (units of Eq. (8); E_s = m c^2 / (hbar omega_r)):
+//   dW_rad/du  = alpha E_s / (sqrt3 pi gamma) Frad(u, chi),   u = eps_gamma / eps_e,
+//   dW_pair/dv = alpha E_s / (sqrt3 pi k)     Fpair(v, chi),  v = eps_+ / eps_gamma,
+// tabulated as G(chi) = Int_0^1 F and as the inverse of the normalised CDF.
+#pragma once
+#include <cstdint>
+
+#include "pic_internal.cuh"
+
+namespace pic {
+
+enum QedProcess { QED_RAD = 0, QED_PAIR = 1 };
+
+// tables: ln chi_i = lnchi0 + i dlnchi, i < nchi.  lnG[0][i] = ln G_rad(chi_i),
+// lnG[1][i] = ln G_pair(chi_i) + 8/(3 chi_i); inv[p][i*nr + j] = s with
+// CDF_p(s^3) = r_j, t_j = j/(nr-1): r_j = 1 - (1-t_j)^2 on [0,1] for emission,
+// r_j = t_j^2/2 on [0,1/2] for pairs (the pair spectrum is symmetric).
+struct QedTables {
+    int nchi, nr;
+    double lnchi0, dlnchi;
+    const float *lnG_f[2], *inv_f[2];
+    const double *lnG_d[2], *inv_d[2];
+};
+
+struct QedParams {
+    int on;           // this species takes part in the Monte Carlo
+    double pref;      // alpha E_s dt / (sqrt3 pi): W dt = pref G(chi) / (gamma or k)
+    double inv_Es;    // 1 / E_s
+    double emin;      // lightest photon kept as a macro-photon (m c^2)
+    uint32_t key[2];  // Philox key
+    uint32_t step;    // step index (counter word 2)
+    QedTables T;
+    double *tau;      // optical depth left, per particle
+    uint64_t *id;     // identity, per particle
+    uint32_t *ev;     // event flag per particle (1 = emitted / converted)
+    float *evk;       // event data, 4 floats per particle: photon momentum (and v for pairs)
+    double *e_lost;   // energy of photons below emin (tally)
+    double wdV;       // weight * cell volume of this species (energy tallies)
+};
+
+// ---------------------------------------------------------------------
+// Philox4x32-10 (Salmon et al., SC'11): ten rounds of two 32x32->64
+// multiplications (0xD2511F53, 0xCD9E8D57), key bumped by the Weyl
+// constants (0x9E3779B9, 0xBB67AE85)
+// ---------------------------------------------------------------------
+__host__ __device__ inline void philox4x32_10(uint32_t c0, uint32_t c1, uint32_t c2, uint32_t c3, uint32_t k0,
+                                              uint32_t k1, uint32_t *out)
+{
+#pragma unroll
+    for (int r = 0; r < 10; r++) {
+        const uint64_t p0 = (uint64_t)0xD2511F53u * c0;
+        const uint64_t p1 = (uint64_t)0xCD9E8D57u * c2;
+        const uint32_t hi0 = (uint32_t)(p0 >> 32), lo0 = (uint32_t)p0;
+        const uint32_t hi1 = (uint32_t)(p1 >> 32), lo1 = (uint32_t)p1;
+        const uint32_t n0 = hi1 ^ c1 ^ k0, n2 = hi0 ^ c3 ^ k1;
+        c0 = n0;
+        c1 = lo1;
+        c2 = n2;
+        c3 = lo0;
+        k0 += 0x9E3779B9u;
+        k1 += 0xBB67AE85u;
+    }
+    out[0] = c0;
+    out[1] = c1;
+    out[2] = c2;
+    out[3] = c3;
+}
+
+// uniform deviate in (0,1) from the top 24 bits, exact in FP32 and FP64
+__host__ __device__ inline double uniform24(uint32_t x) { return ((double)(x >> 8) + 0.5) * (1.0 / 16777216.0); }
+
+// counter words 2-3 of the draws: (step, purpose)
+enum QedPurpose : uint32_t { QP_EMIT = 0, QP_PAIR = 1, QP_INIT = 2 };
+constexpr uint32_t kInitStep = 0xFFFFFFFFu;
+
+// initial optical depth of a particle with identity id
+__host__ __device__ inline double initial_tau(uint64_t id, const uint32_t *key)
+{
+    uint32_t w[4];
+    philox4x32_10((uint32_t)id, (uint32_t)(id >> 32), kInitStep, QP_INIT, key[0], key[1], w);
+    return -log(uniform24(w[0]));
+}
+
+// quantum parameter chi = sqrt((g E + u x B)^2 - (u.E)^2) / E_s for a
+// particle of momentum u (or a photon of momentum k, g = |k|)
+template <typename R>
+__device__ __forceinline__ double chi_of(R g, R ux, R uy, R uz, R ex, R ey, R ez, R bx, R by, R bz, double inv_Es)
+{
+    const double fx = (double)g * ex + ((double)uy * bz - (double)uz * by);
+    const double fy = (double)g * ey + ((double)uz * bx - (double)ux * bz);
+    const double fz = (double)g * ez + ((double)ux * by - (double)uy * bx);
+    const double ue = (double)ux * ex + (double)uy * ey + (double)uz * ez;
+    const double s = fx * fx + fy * fy + fz * fz - ue * ue;
+    return s > 0.0 ? sqrt(s) * inv_Es : 0.0;
+}
+
+// G_p(chi): Catmull-Rom in ln chi on ln G (pairs: on ln G + 8/(3 chi), the
+// exponential small-chi factor removed); below the table the emission rate
+// follows its classical limit (ln G linear in ln chi) and the pair rate is
+// zero; above it both continue linearly in ln chi
+template <typename R>
+__host__ __device__ __forceinline__ double qed_rate(const QedTables &T, int p, double chi)
+{
+    if (!(chi > 0.0)) return 0.0;
+    const R *L = p == 0 ? (const R *)(sizeof(R) == 4 ? (const void *)T.lnG_f[0] : (const void *)T.lnG_d[0])
+                        : (const R *)(sizeof(R) == 4 ? (const void *)T.lnG_f[1] : (const void *)T.lnG_d[1]);
+    const double x = (log(chi) - T.lnchi0) / T.dlnchi;
+    const double sub = p == QED_PAIR ? 8.0 / (3.0 * chi) : 0.0;
+    if (x <= 0.0) {
+        if (p == QED_PAIR) return 0.0;
+        return exp((double)L[0] + x * ((double)L[1] - (double)L[0]));
+    }
+    if (x >= T.nchi - 1) {
+        const int n = T.nchi;
+        return exp((double)L[n - 1] + (x - (n - 1)) * ((double)L[n - 1] - (double)L[n - 2]) - sub);
+    }
+    int i = (int)x;
+    const double t = x - i;
+    const int i0 = max(i - 1, 0), i3 = min(i + 2, T.nchi - 1);
+    const double p0 = L[i0], p1 = L[i], p2 = L[i + 1], p3 = L[i3];
+    const double a = -0.5 * p0 + 1.5 * p1 - 1.5 * p2 + 0.5 * p3;
+    const double b = p0 - 2.5 * p1 + 2.0 * p2 - 0.5 * p3;
+    const double c = -0.5 * p0 + 0.5 * p2;
+    return exp(((a * t + b) * t + c) * t + p1 - sub);
+}
+
+// fraction (u for emission, v for pairs) with CDF = r: bilinear in
+// (ln chi, r) on s = fraction^(1/3), chi clamped to the table
+template <typename R>
+__host__ __device__ __forceinline__ double qed_sample(const QedTables &T, int p, double chi, double r)
+{
+    const R *I = (const R *)(sizeof(R) == 4 ? (const void *)T.inv_f[p] : (const void *)T.inv_d[p]);
+    double x = (log(fmax(chi, 1e-300)) - T.lnchi0) / T.dlnchi;
+    x = fmin(fmax(x, 0.0), (double)(T.nchi - 1) - 1e-9);
+    const int i = (int)x;
+    const double tx = x - i;
+    bool flip = false;
+    double rr = r;
+    if (p == QED_PAIR && rr > 0.5) {
+        rr = 1.0 - rr;
+        flip = true;
+    }
+    // r grids: emission r_j = 1 - (1 - t_j)^2, pairs r_j = t_j^2 / 2, t_j uniform
+    const double tj = p == QED_PAIR ? sqrt(2.0 * rr) : 1.0 - sqrt(fmax(1.0 - rr, 0.0));
+    double y = tj * (T.nr - 1);
+    y = fmin(fmax(y, 0.0), (double)(T.nr - 1) - 1e-9);
+    const int j = (int)y;
+    const double ty = y - j;
+    const R *a = I + (long long)i * T.nr + j, *b = a + T.nr;
+    const double s0 = (1.0 - ty) * (double)a[0] + ty * (double)a[1];
+    const double s1 = (1.0 - ty) * (double)b[0] + ty * (double)b[1];
+    const double s = (1.0 - tx) * s0 + tx * s1;
+    const double f = s * s * s;
+    return flip ? 1.0 - f : f;
+}
+
+}  // namespace pic

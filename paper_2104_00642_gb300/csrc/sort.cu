@@ -266,6 +266,10 @@ __global__ void k_permute_f32(PartF32 src, PartF32 dst, const uint32_t *__restri
     dst.u[0][i] = src.u[0][a];
     dst.u[1][i] = src.u[1][a];
     dst.u[2][i] = src.u[2][a];
+    if (src.tau) {
+        dst.tau[i] = src.tau[a];
+        dst.id[i] = src.id[a];
+    }
 }
 
 __global__ void k_permute_f64(PartF64 src, PartF64 dst, const uint32_t *__restrict__ perm,

@@ -31,7 +31,10 @@ MAX_SPECIES = 8
 EXPORTS = ["pic_create", "pic_destroy", "pic_last_error", "pic_load_particles", "pic_set_laser",
            "pic_set_field", "pic_step", "pic_fields", "pic_particle_count", "pic_get_particles",
            "pic_get_cells", "pic_diagnostics", "pic_gather", "pic_sync", "pic_profile", "pic_profile_read",
-           "pic_field_energy_noalloc"]
+           "pic_field_energy_noalloc", "pic_set_qed", "pic_qed_eval", "pic_get_qed_state"]
+KIND_MASSIVE, KIND_PHOTON = 0, 1
+QED_OFF, QED_TABLE = 0, 1
+QED_EMISSION, QED_PAIR = 0, 1
 PHASES = ("sort", "fields", "push", "fold")
 
 
@@ -47,12 +50,18 @@ class pic_grid(C.Structure):
 
 
 class pic_species(C.Structure):
-    _fields_ = [("q", C.c_double), ("m", C.c_double), ("w", C.c_double), ("capacity", C.c_int64)]
+    _fields_ = [("q", C.c_double), ("m", C.c_double), ("w", C.c_double), ("capacity", C.c_int64),
+                ("kind", C.c_int), ("qed", C.c_int)]
 
 
 class pic_options(C.Structure):
     _fields_ = [("precision", C.c_int), ("sort_interval", C.c_int), ("tile", C.c_int * 3),
-                ("rho_bg", C.c_double), ("stream", C.c_void_p), ("push_variant", C.c_int)]
+                ("rho_bg", C.c_double), ("stream", C.c_void_p), ("push_variant", C.c_int), ("seed", C.c_uint64)]
+
+
+class pic_qed(C.Structure):
+    _fields_ = [("mode", C.c_int), ("photon_sp", C.c_int), ("electron_sp", C.c_int), ("positron_sp", C.c_int),
+                ("lambda_r_m", C.c_double), ("photon_emin", C.c_double)]
 
 
 class pic_laser(C.Structure):
@@ -63,7 +72,7 @@ class pic_laser(C.Structure):
 class pic_diag(C.Structure):
     _fields_ = [("step", C.c_int64), ("t", C.c_double), ("U_E", C.c_double), ("U_B", C.c_double),
                 ("U_kin", C.c_double * MAX_SPECIES), ("charge", C.c_double), ("gauss_max", C.c_double),
-                ("E_absorbed", C.c_double), ("n_alive", C.c_int64 * MAX_SPECIES)]
+                ("E_absorbed", C.c_double), ("n_alive", C.c_int64 * MAX_SPECIES), ("E_photon_lost", C.c_double)]
 
 
 _lib = None
@@ -113,6 +122,12 @@ def load_library(path: str = LIB_PATH):
     L.pic_profile_read.restype = I
     L.pic_field_energy_noalloc.argtypes = [C.POINTER(C.c_void_p), I64, D, P, P]
     L.pic_field_energy_noalloc.restype = I
+    L.pic_set_qed.argtypes = [P, C.POINTER(pic_qed)]
+    L.pic_set_qed.restype = I
+    L.pic_qed_eval.argtypes = [P, I, I64, P, P, P]
+    L.pic_qed_eval.restype = I
+    L.pic_get_qed_state.argtypes = [P, I, I64, P, P]
+    L.pic_get_qed_state.restype = I
     _lib = L
     return L
 
@@ -142,7 +157,7 @@ class Sim:
     """One simulation (a ``pic_sim*``)."""
 
     def __init__(self, dim, n, dx, dt, species, bc=(PERIODIC, PERIODIC, PERIODIC), precision=FP32_CELLOFF,
-                 sort_interval=0, tile=(0, 0, 0), rho_bg=0.0, stream=None, push_variant=0):
+                 sort_interval=0, tile=(0, 0, 0), rho_bg=0.0, stream=None, push_variant=0, seed=0):
         L = load_library()
         g = pic_grid()
         g.dim = int(dim)
@@ -154,6 +169,8 @@ class Sim:
         sp = (pic_species * max(1, len(species)))()
         for i, s in enumerate(species):
             sp[i].q, sp[i].m, sp[i].w, sp[i].capacity = float(s[0]), float(s[1]), float(s[2]), int(s[3])
+            sp[i].kind = int(s[4]) if len(s) > 4 else KIND_MASSIVE
+            sp[i].qed = int(s[5]) if len(s) > 5 else 0
         o = pic_options()
         o.precision = int(precision)
         o.sort_interval = int(sort_interval)
@@ -162,6 +179,7 @@ class Sim:
         o.rho_bg = float(rho_bg)
         o.stream = stream
         o.push_variant = int(push_variant)
+        o.seed = int(seed) & 0xFFFFFFFFFFFFFFFF
         h = C.c_void_p()
         rc = L.pic_create(C.byref(g), float(dt), sp, len(species), C.byref(o), C.byref(h))
         if rc != PIC_OK:
@@ -260,7 +278,27 @@ class Sim:
         self._check(load_library().pic_diagnostics(self._h, C.byref(d)))
         return {"step": d.step, "t": d.t, "U_E": d.U_E, "U_B": d.U_B, "U_kin": list(d.U_kin[: self.nsp]),
                 "charge": d.charge, "gauss_max": d.gauss_max, "E_absorbed": d.E_absorbed,
-                "n_alive": list(d.n_alive[: self.nsp])}
+                "n_alive": list(d.n_alive[: self.nsp]), "E_photon_lost": d.E_photon_lost}
+
+    def pic_set_qed(self, photon_sp=-1, electron_sp=-1, positron_sp=-1, lambda_r_m=1e-6, photon_emin=0.0,
+                    mode=QED_TABLE):
+        q = pic_qed(int(mode), int(photon_sp), int(electron_sp), int(positron_sp), float(lambda_r_m),
+                    float(photon_emin))
+        self._check(load_library().pic_set_qed(self._h, C.byref(q)))
+
+    def pic_qed_eval(self, process, chi, r=None):
+        chi = _f64(np.atleast_1d(chi))
+        rr = None if r is None else _f64(np.atleast_1d(r))
+        out = np.zeros(len(chi))
+        self._check(load_library().pic_qed_eval(self._h, int(process), len(chi), _p(chi), _p(rr), _p(out)))
+        return out
+
+    def pic_get_qed_state(self, sp):
+        n = self.pic_particle_count(sp)
+        ids = np.zeros(max(n, 1), dtype=np.uint64)
+        tau = np.zeros(max(n, 1))
+        self._check(load_library().pic_get_qed_state(self._h, int(sp), n, _p(ids), _p(tau)))
+        return ids[:n], tau[:n]
 
     def pic_sync(self):
         self._check(load_library().pic_sync(self._h))

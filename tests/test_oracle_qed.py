@@ -97,3 +97,43 @@ def test_method_two_reproduces_the_spectrum(L):
     stat = np.sum((counts - expect) ** 2 / expect)
     assert len(acc) > 2000
     assert stat < 35.0  # chi^2 with 9 dof: p ~ 1e-4
+
+
+# --------------------------------------------------------------------------
+# the optical-depth Monte Carlo inside the oracle's step
+# --------------------------------------------------------------------------
+
+def test_qed_monte_carlo_conserves_energy_in_pure_B():
+    """Electrons gyrating in a uniform B emit photons that convert to pairs;
+    the magnetic field does no work, Boris keeps gamma, emission keeps
+    gamma_e + eps_gamma and pair creation keeps eps_+ + eps_- = k, so the
+    total energy is conserved to round-off.  The run must produce photons and
+    pairs (otherwise the check would be empty)."""
+    from tests import qed_setup as Q
+    o = Q.make_oracle()
+    e0 = Q.total_energy(o.particles(0), o.particles(1), o.particles(2))
+    o.step(25)
+    pe, pp, pg = o.particles(0), o.particles(1), o.particles(2)
+    e1 = Q.total_energy(pe, pp, pg)
+    assert len(pg["ux"]) > 30
+    assert len(pp["ux"]) >= 2 and len(pe["ux"]) == Q.N_E + len(pp["ux"])
+    assert abs(e1 - e0) <= 1e-12 * e0
+    # every photon carries an identity drawn from its parent's Philox stream
+    ids, tau = o.qed_state(2)
+    assert len(np.unique(ids)) == len(ids) and np.all(tau > 0)
+
+
+@pytest.mark.parametrize("chi", [0.01, 1.0, 50.0])
+def test_total_emission_rate_matches_library_quadrature(L, chi):
+    """Int_0^1 Frad du by scipy quad (with the Bessel functions of the
+    library), split at u = 1/2 into s = u^(1/3) and t = (1-u)^(1/3)."""
+    def F(u):
+        y = 2 * u / (3 * chi * (1 - u))
+        if y > 700:
+            return 0.0
+        ik = integrate.quad(lambda x: special.kv(1 / 3, x), y, np.inf, epsabs=0, epsrel=1e-12, limit=200)[0]
+        return ((1 - u) + 1 / (1 - u)) * special.kv(2 / 3, y) - ik
+    wh = 0.5 ** (1 / 3)
+    a = integrate.quad(lambda s: 3 * s * s * F(s ** 3), 0, wh, epsabs=0, epsrel=1e-10, limit=400)[0]
+    b = integrate.quad(lambda t: 3 * t * t * F(1 - t ** 3), 0, wh, epsabs=0, epsrel=1e-10, limit=400)[0]
+    assert abs(L.or_qed_Grad(chi) / (a + b) - 1.0) < 1e-7
