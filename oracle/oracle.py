@@ -80,6 +80,10 @@ def lib():
         L.or_photon_lost.restype = D
         L.or_get_qed_state.argtypes = [P, I, P, P]
         L.or_get_qed_state.restype = LG
+        L.or_mlp_nparams.restype = LG
+        L.or_mlp_forward.argtypes = [P, LG, P, P]
+        L.or_mlp_loss_grad.argtypes = [P, LG, P, P, P]
+        L.or_mlp_loss_grad.restype = D
         L.or_philox4x32_10.argtypes = [P, P, P]
         L.or_uniform24.argtypes = [C.c_uint32]
         L.or_uniform24.restype = D
@@ -275,3 +279,24 @@ class OracleSim:
     @property
     def step_count(self):
         return lib().or_step_count(self._h)
+
+
+def mlp_nparams() -> int:
+    return int(lib().or_mlp_nparams())
+
+
+def mlp_forward(params, x):
+    P = _f64(params)
+    X = _f64(np.asarray(x).reshape(-1, 2))
+    out = np.zeros((X.shape[0], 2))
+    lib().or_mlp_forward(_ptr(P), X.shape[0], _ptr(X), _ptr(out))
+    return out
+
+
+def mlp_loss_grad(params, x, t):
+    P = _f64(params)
+    X = _f64(np.asarray(x).reshape(-1, 2))
+    T = _f64(np.asarray(t).reshape(-1, 2))
+    G = np.zeros(mlp_nparams())
+    loss = lib().or_mlp_loss_grad(_ptr(P), X.shape[0], _ptr(X), _ptr(T), _ptr(G))
+    return loss, G

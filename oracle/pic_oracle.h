@@ -56,4 +56,8 @@ double or_qed_sample_rad(double chi, double r);
 double or_qed_sample_pair(double chi, double r);
 double or_qed_method2_rad(double chi, double dwdt, double r1, double r2);
 
+long or_mlp_nparams(void);
+void or_mlp_forward(const double *P, long n, const double *in, double *out);
+double or_mlp_loss_grad(const double *P, long n, const double *in, const double *tgt, double *G);
+
 #endif
