@@ -52,6 +52,8 @@ def make_workload(name, rank=0, sample=None):
         return W.thermal_3d(n=n, seed=W.SEED0 + 3 + 1000 * rank)
     if name == "langmuir_1d":
         return W.langmuir_1d()
+    if name == "qed_collision_2d":
+        return W.qed_collision_2d(seed=W.SEED0 + 7 + 1000 * rank)
     raise SystemExit(f"unknown workload {name}")
 
 
@@ -193,13 +195,103 @@ def run_reference(args):
     print(json.dumps(out))
 
 
+def photon_spectrum(sim, sp, edges):
+    p = sim.pic_get_particles(sp)
+    a = p["alive"] == 1
+    k = np.sqrt(p["ux"][a] ** 2 + p["uy"][a] ** 2 + p["uz"][a] ** 2)
+    return np.histogram(k, edges)[0]
+
+
+def run_qed(args, w, pic, torch, stream, timed, rank, world, dist, local):
+    """The strong-field QED collision: the same seeded beam through three
+    forms, each advanced untimed to the collision, then W warm-up and K timed
+    steps around the pulse peak: FP32 cell+offset with the surrogate networks
+    (trained on the device first, untimed), FP32 with the tables, and the
+    plain FP64 form with the tables.  Particle-steps count the live particles
+    of all species (trapezoid over the window).  Errors of the two FP32 forms
+    are stated against the FP64 run: energies and the photon spectrum."""
+    K = args.steps
+    pre = max(0, w.notes["steps_to_collision"] - K // 2 - args.warmup)
+    edges = np.logspace(np.log10(w.qed["photon_emin"]), np.log10(3000.0), 25)
+    runs = {}
+    for mode in ("surrogate", "table", "fp64"):
+        prec = pic.FP64_PLAIN if mode == "fp64" else pic.FP32_CELLOFF
+        sim = pic.from_workload(w, precision=prec, sort_interval=args.sort_interval, stream=stream.cuda_stream,
+                                seed=0x5EED + rank)
+        train = None
+        if mode == "surrogate":
+            train = {p: sim.pic_mlp_train(p, seed=17) for p in (pic.QED_EMISSION, pic.QED_PAIR)}
+            sim.pic_set_qed(mode=pic.QED_SURROGATE, **w.qed)
+        with torch.cuda.stream(stream):
+            sim.pic_step(pre)
+        timed(sim, args.warmup)
+        n0 = sum(sim.pic_diagnostics()["n_alive"])
+        if dist:
+            dist.barrier()
+        torch.cuda.synchronize()
+        with Clocks(local) as clk:
+            ms, prof = timed(sim, K, profile=True)
+        d = sim.pic_diagnostics()
+        n1 = sum(d["n_alive"])
+        t_local = float(np.sum(ms)) / 1e3
+        t = t_local
+        if dist:
+            tt = torch.tensor([t_local], device="cuda", dtype=torch.float64)
+            dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+            t = float(tt.item())
+        runs[mode] = {"value": world * 0.5 * (n0 + n1) * K / t, "ms_per_step": 1e3 * t / K, "n_alive": d["n_alive"],
+                      "U_kin": d["U_kin"], "U_EM": d["U_E"] + d["U_B"], "E_photon_lost": d["E_photon_lost"],
+                      "spectrum": photon_spectrum(sim, w.qed["photon_sp"], edges), "prof": prof, "clocks": clk.summary(),
+                      "train": train}
+        sim.close()
+    ref = runs["fp64"]
+
+    def errors(r):
+        e_tot = lambda x: sum(x["U_kin"]) + x["U_EM"] + x["E_photon_lost"]
+        big = ref["spectrum"] >= 1000
+        spec = np.abs(r["spectrum"][big] / ref["spectrum"][big] - 1.0)
+        return {"total_energy_rel": abs(e_tot(r) / e_tot(ref) - 1.0),
+                "photon_energy_rel": abs(r["U_kin"][2] / ref["U_kin"][2] - 1.0) if ref["U_kin"][2] else None,
+                "electron_energy_rel": abs(r["U_kin"][0] / ref["U_kin"][0] - 1.0),
+                "photon_count_rel": abs(r["n_alive"][2] / max(ref["n_alive"][2], 1) - 1.0),
+                "pairs": (int(r["n_alive"][1]), int(ref["n_alive"][1])),
+                "photon_spectrum_max_bin_rel": float(spec.max()) if big.any() else None,
+                "photon_spectrum_bins": int(big.sum())}
+
+    if rank == 0:
+        s = runs["surrogate"]
+        prof = s["prof"]
+        tr = s["train"]
+        out = {"metric": METRIC, "value": s["value"], "unit": UNIT, "n_gpus": world, "steps": K,
+               "warmup": args.warmup, "ms_per_step": s["ms_per_step"], "higher_is_better": True, "scaling": "weak",
+               "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+               "config": {"workload": describe(w), "precision": "fp32 cell+offset, QED by the surrogate networks "
+                          "inside their chi range (tables outside); FP64 islands: optical depth, diagnostics",
+                          "window": f"steps {pre + args.warmup}..{pre + args.warmup + K} around the collision "
+                                    f"(step {w.notes['steps_to_collision']})",
+                          "sort_interval": args.sort_interval, "replicas": world,
+                          "l2": "flushed (256 MiB write) before every timed step" if not args.no_flush else "not flushed"},
+               "fp32_table": {"value": runs["table"]["value"], "ms_per_step": runs["table"]["ms_per_step"],
+                              "error_vs_fp64": errors(runs["table"])},
+               "fp64_plain": {"value": runs["fp64"]["value"], "ms_per_step": runs["fp64"]["ms_per_step"],
+                              "fp32_surrogate_over_fp64": s["value"] / runs["fp64"]["value"]},
+               "surrogate_error_vs_fp64": errors(s),
+               "surrogate_training": {str(p): {k: v for k, v in r.items()} for p, r in tr.items()},
+               "n_alive_end": {m: [int(v) for v in r["n_alive"]] for m, r in runs.items()},
+               "gpu_launches": int(sum(prof["launches"].values())), "clocks": s["clocks"],
+               "phases_ms_per_step": {k: v / K for k, v in prof["ms"].items()},
+               "roofline": None, "cpu_baseline": None, "e2e": None}
+        print(json.dumps(out))
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=50)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="native", choices=["native", "reference"])
-    ap.add_argument("--workload", default="laser_foil_2d", choices=["laser_foil_2d", "thermal_3d", "langmuir_1d"])
+    ap.add_argument("--workload", default="laser_foil_2d",
+                    choices=["laser_foil_2d", "thermal_3d", "langmuir_1d", "qed_collision_2d"])
     ap.add_argument("--sort-interval", type=int, default=8)
     ap.add_argument("--fp64-steps", type=int, default=10)
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU baseline leg")
@@ -248,6 +340,13 @@ def main():
         if profile:
             sim.pic_profile(False)
         return ms, prof
+
+    if args.workload == "qed_collision_2d":
+        run_qed(args, w, pic, torch, stream, timed, rank, world, dist, local)
+        if dist:
+            dist.barrier()
+            dist.destroy_process_group()
+        return
 
     # ---- FP32 cell+offset: the headline ----------------------------------
     sim = pic.from_workload(w, precision=pic.FP32_CELLOFF, sort_interval=args.sort_interval,

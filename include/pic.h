@@ -152,9 +152,13 @@ typedef struct {
  * create an electron in electron_sp and a positron in positron_sp (fractions
  * 1-v and v, collinear).  Particle identities: (species << 48) | load index.
  * lambda_r_m: wavelength of the reference frequency (2 pi c / omega_r, in
- * metres), which sets E_s = m c^2 / (hbar omega_r).  Only the FP32 form
- * implements the Monte Carlo. */
-enum { PIC_QED_OFF = 0, PIC_QED_TABLE = 1 };
+ * metres), which sets E_s = m c^2 / (hbar omega_r).  The FP32 form reads
+ * the FP32 copy of the tables, the FP64 form the FP64 copy.
+ * PIC_QED_SURROGATE (FP32 form; the FP64 form keeps its tables): as
+ * PIC_QED_TABLE, but inside the chi range of a trained (or set) network the
+ * rate and the energy fraction come from that network (pic_mlp_train); a
+ * process without a network uses its tables. */
+enum { PIC_QED_OFF = 0, PIC_QED_TABLE = 1, PIC_QED_SURROGATE = 2 };
 enum { PIC_QED_EMISSION = 0, PIC_QED_PAIR = 1 };
 typedef struct {
     int mode;
@@ -168,12 +172,82 @@ typedef struct {
  * identities and optical depths are initialised.  Errors: PIC_ERR_ARG. */
 int pic_set_qed(pic_sim *sim, const pic_qed *qed);
 
-/* Evaluate the device tables the Monte Carlo uses, for inspection: with
- * r == NULL, rate[i] = G(chi[i]) = Int_0^1 F (the total rate is
+/* Evaluate what the Monte Carlo uses, for inspection: with r == NULL,
+ * rate[i] = G(chi[i]) = Int_0^1 F (the total rate is
  * alpha E_s G / (sqrt3 pi gamma)); otherwise rate[i] = the energy fraction
- * whose CDF is r[i].  process: PIC_QED_EMISSION or PIC_QED_PAIR.  Host
- * arrays of n values.  Errors: PIC_ERR_ARG, PIC_ERR_STATE (no tables). */
+ * whose CDF is r[i].  The device tables, or in PIC_QED_SURROGATE mode the
+ * ready network inside its chi range.  process: PIC_QED_EMISSION or
+ * PIC_QED_PAIR.  Host arrays of n values.  Errors: PIC_ERR_ARG,
+ * PIC_ERR_STATE (no tables). */
 int pic_qed_eval(pic_sim *sim, int process, int64_t n, const double *chi, const double *r, double *out);
+
+/* ---------------------------------------------------------------------
+ * Surrogate network for the QED Monte Carlo (the paper has none: its
+ * Method I and II use the spectra of Eqs. (23)/(24) directly).  One network
+ * per process, 2 -> 64 -> 64 -> 64 -> 2 with SiLU, BF16 weights and FP32
+ * accumulation.  Inputs x0 = 2 (ln chi - ln chi_min) / ln(chi_max/chi_min) - 1
+ * and x1 = 2 t - 1, with t = 1 - sqrt(1 - r) for emission and
+ * t = sqrt(2 min(r, 1 - r)) for pairs (r: the CDF value).  Outputs
+ * y0 = s = fraction^(1/3) at r (pairs: the fraction of min(r, 1 - r)) and
+ * y1 = (ln G (+ 8/(3 chi) for pairs) - mu) / sd.  Parameters (FP32, 8642):
+ *   W0[64][2] b0[64] W1[64][64] b1[64] W2[64][64] b2[64] W3[2][64] b3[2]
+ * with W[out][in]; the device holds them rounded to BF16 (biases FP32).
+ * --------------------------------------------------------------------- */
+#define PIC_MLP_NPARAMS 8642
+typedef struct {
+    int64_t iterations;      /* Adam steps (0: 20000) */
+    int64_t batch;           /* samples per step, a multiple of 128 (0: 16384) */
+    double lr, lr_final;     /* cosine schedule from lr to lr_final (0: 1e-2, 1e-4) */
+    double chi_min, chi_max; /* trained range (0: 1e-3..1e2 emission, 1e-2..1e2 pairs) */
+    double rate_weight;      /* loss weight of the rate output (0: 4) */
+    uint64_t seed;           /* Philox key of samples and initial weights */
+    int keep;                /* 1: continue from the present parameters */
+} pic_mlp_train_opts;
+
+typedef struct {
+    double loss;               /* loss of the last batch */
+    double max_err_lnG;        /* max |ln G_net - ln G_table| on the validation grid */
+    double max_err_s, rms_err_s; /* |s_net - s_table| on the validation grid */
+    double ms;                 /* device time of the training loop */
+    int64_t iterations;
+    int64_t table_bytes;       /* device bytes of one process's tables (FP32 + FP64) */
+    int64_t net_bytes;         /* device bytes of the network the push reads */
+} pic_mlp_report;
+
+typedef struct {
+    double chi_min, chi_max; /* trained range */
+    double mu, sd;           /* rate output normalisation */
+} pic_mlp_info;
+
+/* Train the network of `process` on the device with the library's own
+ * kernels (forward, backward, Adam; one CUDA graph per iteration): each step
+ * draws a fresh batch of (ln chi uniform in the range, r uniform) and takes
+ * the targets from the FP64 tables.  Then validates the network against the
+ * tables on a 256 x 256 grid of cell midpoints in (ln chi, r) and marks it
+ * ready.  Needs pic_set_qed first (the tables).  report may be NULL.
+ * Errors: PIC_ERR_ARG, PIC_ERR_STATE, PIC_ERR_NOMEM, PIC_ERR_CUDA. */
+int pic_mlp_train(pic_sim *sim, int process, const pic_mlp_train_opts *opt, pic_mlp_report *report);
+
+/* Validation of the present network only (report->loss, ms, iterations 0). */
+int pic_mlp_validate(pic_sim *sim, int process, pic_mlp_report *report);
+
+/* Read (params: PIC_MLP_NPARAMS floats, FP32 master copy) or replace the
+ * network of `process`; either pointer may be NULL on read.  pic_mlp_set
+ * marks the network ready.  Errors: PIC_ERR_ARG, PIC_ERR_STATE (get: no
+ * network), PIC_ERR_NOMEM, PIC_ERR_CUDA. */
+int pic_mlp_get(pic_sim *sim, int process, float *params, pic_mlp_info *info);
+int pic_mlp_set(pic_sim *sim, int process, const float *params, const pic_mlp_info *info);
+
+/* The raw network on n normalised input rows x[n][2] -> y[n][2] (host
+ * arrays), through the warp-level inference path the push uses. */
+int pic_mlp_eval(pic_sim *sim, int process, int64_t n, const float *x, float *y);
+
+/* Loss L = (1/n) sum_rows sum_o (y_o - t_o)^2 and its gradient with respect
+ * to every parameter (grad: PIC_MLP_NPARAMS floats) at the present
+ * parameters, by the training kernels (BF16 forward, backward on the tensor
+ * cores, FP32 weight gradients).  n a multiple of 32, at most 1048576.
+ * Errors: PIC_ERR_ARG, PIC_ERR_STATE, PIC_ERR_NOMEM, PIC_ERR_CUDA. */
+int pic_mlp_grad(pic_sim *sim, int process, int64_t n, const float *x, const float *t, float *grad, double *loss);
 
 /* Copy the identities and optical depths of a QED species (photon or
  * emitting species) in the current array order to caller-sized host arrays

@@ -7,17 +7,20 @@
 //   (with J^{n+1}).
 // Nothing inside a step waits for the host; the device error flags are read
 // once at the end of pic_step.
+#include <algorithm>
 #include <cmath>
 #include <cstdarg>
 #include <cstdio>
 #include <cstdlib>
 #include <cstring>
+#include <random>
 #include <string>
 #include <vector>
 
 #include "../../include/pic.h"
 #include "diag.cuh"
 #include "fdtd.cuh"
+#include "mlp_host.cuh"
 #include "push.cuh"
 #include "push_tile.cuh"
 #include "qed_host.cuh"
@@ -78,6 +81,8 @@ struct pic_sim {
     QedTables T{};
     double Es = 0.0;
     double *d_elost = nullptr;
+    MlpNet net[2];  // surrogate networks: emission, pairs
+    MlpScratch ms;  // their training scratch
     int sort_interval = 0;
     double rho_bg = 0.0;
     cudaStream_t st = nullptr;
@@ -171,6 +176,8 @@ PartF64 view64(pic_sim *s, int i, int buf)
     }
     v.n = p.n_hi;
     v.dn = p.d_count;
+    v.tau = p.tau[buf];
+    v.id = p.id[buf];
     return v;
 }
 
@@ -365,6 +372,10 @@ QedParams qed_params(pic_sim *s, int i)
     double dV = 1.0;
     for (int d = 0; d < s->g.dim; d++) dV *= s->g.dx[d];
     q.wdV = p.w * dV;
+    const MlpNet &net = s->net[p.kind == PIC_KIND_PHOTON ? QED_PAIR : QED_RAD];
+    const bool surr = s->qed.mode == PIC_QED_SURROGATE && net.ready && s->precision == PIC_PREC_FP32_CELLOFF;
+    q.net = surr ? net.img : nullptr;
+    q.nrm = net.nrm;
     return q;
 }
 
@@ -390,6 +401,15 @@ void push_species(pic_sim *s, int i, float *F)
 void push_species(pic_sim *s, int i, double *F)
 {
     SpeciesState &p = s->sp[i];
+    if (p.kind == PIC_KIND_PHOTON) {
+        launch_push_photon_f64(view64(s, i, p.cur), F, s->g, push_const(s, p), qed_params(s, i), s->d_err, s->st);
+        return;
+    }
+    if (s->qed_on && p.qed) {
+        launch_push_qed_f64(view64(s, i, p.cur), F, s->g, push_const(s, p), qed_params(s, i), s->d_err, s->d_eabs,
+                            s->st);
+        return;
+    }
     launch_push_f64(view64(s, i, p.cur), F, s->g, push_const(s, p), s->d_err, s->d_eabs, s->st);
 }
 
@@ -397,9 +417,13 @@ void push_species(pic_sim *s, int i, double *F)
 // photons that converted (electrons, then positrons, in photon order), then
 // the photons emitted by each emitting species in species order (in parent
 // order).  The event flags are exclusive-scanned in array order.
-void qed_spawn(pic_sim *s)
+template <typename R>
+void qed_spawn_views(pic_sim *s)
 {
-    if (!s->qed_on) return;
+    auto view = [&](int i) {
+        if constexpr (sizeof(R) == 8) return view64(s, i, s->sp[i].cur);
+        else return view32(s, i, s->sp[i].cur);
+    };
     uint32_t *off = (uint32_t *)s->sort_scratch;
     const int ph = s->qed.photon_sp, el = s->qed.electron_sp, po = s->qed.positron_sp;
     const int dim = s->g.dim;
@@ -410,9 +434,9 @@ void qed_spawn(pic_sim *s)
     if (ph >= 0 && el >= 0 && po >= 0 && s->sp[ph].n_hi > 0) {
         SpeciesState &P = s->sp[ph], &E = s->sp[el], &O = s->sp[po];
         const uint32_t *tot = scan(P);
-        launch_spawn_pairs(view32(s, ph, P.cur), off, tot, qed_params(s, ph), view32(s, el, E.cur), E.tau[E.cur],
-                           E.id[E.cur], E.ev, E.d_count, E.cap, view32(s, po, O.cur), O.tau[O.cur], O.id[O.cur], O.ev,
-                           O.d_count, O.cap, dim, s->d_err, s->st);
+        launch_spawn_pairs(view(ph), off, tot, qed_params(s, ph), view(el), E.tau[E.cur], E.id[E.cur], E.ev,
+                           E.d_count, E.cap, view(po), O.tau[O.cur], O.id[O.cur], O.ev, O.d_count, O.cap, dim,
+                           s->d_err, s->st);
         E.n_hi = std::min(E.cap, E.n_hi + P.n_hi);
         O.n_hi = std::min(O.cap, O.n_hi + P.n_hi);
         E.items_valid = O.items_valid = false;
@@ -423,11 +447,18 @@ void qed_spawn(pic_sim *s)
         if (p.kind == PIC_KIND_PHOTON || !p.qed || p.n_hi == 0) continue;
         SpeciesState &P = s->sp[ph];
         const uint32_t *tot = scan(p);
-        launch_spawn_photons(view32(s, i, p.cur), off, tot, qed_params(s, i), view32(s, ph, P.cur), P.tau[P.cur],
-                             P.id[P.cur], P.ev, P.d_count, P.cap, dim, s->d_err, s->st);
+        launch_spawn_photons(view(i), off, tot, qed_params(s, i), view(ph), P.tau[P.cur], P.id[P.cur], P.ev,
+                             P.d_count, P.cap, dim, s->d_err, s->st);
         P.n_hi = std::min(P.cap, P.n_hi + p.n_hi);
         P.items_valid = false;
     }
+}
+
+void qed_spawn(pic_sim *s)
+{
+    if (!s->qed_on) return;
+    if (s->precision == PIC_PREC_FP64_PLAIN) qed_spawn_views<double>(s);
+    else qed_spawn_views<float>(s);
 }
 
 // nsteps split steps (Sec. II.F).  The first half step of a call runs
@@ -588,10 +619,6 @@ int pic_create(const pic_grid *grid, double dt, const pic_species *species, int 
             rc = fail(s, PIC_ERR_ARG, "pic_create: bad species %d", i);
             break;
         }
-        if ((photon || q.qed) && prec != PIC_PREC_FP32_CELLOFF) {
-            rc = fail(s, PIC_ERR_ARG, "pic_create: the QED Monte Carlo exists in the FP32 form only");
-            break;
-        }
         p.q = q.q;
         p.m = q.m;
         p.w = q.w;
@@ -604,7 +631,8 @@ int pic_create(const pic_grid *grid, double dt, const pic_species *species, int 
                 rc = rc ? rc : dalloc(s, (void **)&p.id[b], (size_t)p.cap * 8);
             }
             rc = rc ? rc : dalloc(s, (void **)&p.ev, (size_t)(p.cap + 1) * 4);
-            rc = rc ? rc : dalloc(s, (void **)&p.evk, (size_t)(p.cap + 1) * 16);
+            // event data: 4 floats per particle, 4 doubles in the FP64 form
+            rc = rc ? rc : dalloc(s, (void **)&p.evk, (size_t)(p.cap + 1) * 4 * rsize(s));
         }
         maxcap = std::max(maxcap, p.cap);
         rc = rc ? rc : dalloc(s, (void **)&p.d_count, sizeof(long long));
@@ -736,7 +764,8 @@ int pic_load_particles(pic_sim *s, int sp, int64_t n, const double *x, const dou
 int pic_set_qed(pic_sim *s, const pic_qed *Q)
 {
     if (!s || !Q) return PIC_ERR_ARG;
-    if (Q->mode != PIC_QED_OFF && Q->mode != PIC_QED_TABLE) return fail(s, PIC_ERR_ARG, "pic_set_qed: bad mode");
+    if (Q->mode != PIC_QED_OFF && Q->mode != PIC_QED_TABLE && Q->mode != PIC_QED_SURROGATE)
+        return fail(s, PIC_ERR_ARG, "pic_set_qed: bad mode");
     auto kind_ok = [&](int i, int kind) { return i == -1 || (i >= 0 && i < s->nsp && s->sp[i].kind == kind); };
     if (!kind_ok(Q->photon_sp, PIC_KIND_PHOTON) || !kind_ok(Q->electron_sp, PIC_KIND_MASSIVE) ||
         !kind_ok(Q->positron_sp, PIC_KIND_MASSIVE) || !(Q->lambda_r_m > 0.0) || Q->photon_emin < 0.0)
@@ -770,8 +799,12 @@ int pic_qed_eval(pic_sim *s, int process, int64_t n, const double *chi, const do
     cudaError_t e = cudaMemcpyAsync(d, chi, n * 8, cudaMemcpyHostToDevice, s->st);
     if (e == cudaSuccess && r) e = cudaMemcpyAsync(d + n, r, n * 8, cudaMemcpyHostToDevice, s->st);
     if (e == cudaSuccess) {
-        launch_qed_eval(s->T, s->precision == PIC_PREC_FP64_PLAIN, process, n, d, r ? d + n : nullptr, d + 2 * n,
-                        s->st);
+        const MlpNet &net = s->net[process];
+        if (s->qed.mode == PIC_QED_SURROGATE && net.ready && s->precision == PIC_PREC_FP32_CELLOFF)
+            launch_qed_eval_surr(net.img, net.nrm, s->T, false, process, n, d, r ? d + n : nullptr, d + 2 * n, s->st);
+        else
+            launch_qed_eval(s->T, s->precision == PIC_PREC_FP64_PLAIN, process, n, d, r ? d + n : nullptr, d + 2 * n,
+                            s->st);
         e = cudaGetLastError();
     }
     if (e == cudaSuccess) e = cudaMemcpyAsync(out, d + 2 * n, n * 8, cudaMemcpyDeviceToHost, s->st);
@@ -1033,7 +1066,8 @@ int pic_diagnostics(pic_sim *s, pic_diag *d)
     double charge = 0.0;
     for (int i = 0; i < s->nsp; i++) {
         SpeciesState &p = s->sp[i];
-        if (s->precision == PIC_PREC_FP64_PLAIN) diag_kinetic_f64(view64(s, i, p.cur), s->diag_scratch, s->diag_out, s->st);
+        if (s->precision == PIC_PREC_FP64_PLAIN)
+            diag_kinetic_f64(view64(s, i, p.cur), p.kind == PIC_KIND_PHOTON, s->diag_scratch, s->diag_out, s->st);
         else
             diag_kinetic_f32(view32(s, i, p.cur), p.kind == PIC_KIND_PHOTON, s->diag_scratch, s->diag_out, s->st);
         CK(cudaMemcpyAsync(h, s->diag_out, 2 * sizeof(double), cudaMemcpyDeviceToHost, s->st));
@@ -1061,6 +1095,301 @@ int pic_diagnostics(pic_sim *s, pic_diag *d)
     bool finite = std::isfinite(d->U_E) && std::isfinite(d->U_B) && std::isfinite(d->gauss_max);
     for (int i = 0; i < s->nsp; i++) finite = finite && std::isfinite(d->U_kin[i]);
     if (!finite) return fail(s, PIC_ERR_NONFINITE, "pic_diagnostics: non-finite value");
+    return PIC_OK;
+}
+
+}  // extern "C"
+
+// ---------------------------------------------------------------------
+// surrogate network: device state and training orchestration
+// ---------------------------------------------------------------------
+namespace {
+
+static_assert(PIC_MLP_NPARAMS == kMlpNParams, "parameter count of the C ABI");
+
+int mlp_net_alloc(pic_sim *s, MlpNet &net)
+{
+    if (net.img) return PIC_OK;
+    const size_t pb = (size_t)kMlpNParams * sizeof(float);
+    void *img = nullptr, *buf = nullptr;
+    int rc = dalloc(s, &img, sizeof(MlpImage));
+    if (!rc) rc = dalloc(s, &buf, 4 * pb);
+    if (rc) return rc;
+    CK(cudaMemsetAsync(img, 0, sizeof(MlpImage), s->st));
+    CK(cudaMemsetAsync(buf, 0, 4 * pb, s->st));
+    net.img = (MlpImage *)img;
+    net.P = (float *)buf;
+    net.M = net.P + kMlpNParams;
+    net.V = net.M + kMlpNParams;
+    net.G = net.V + kMlpNParams;
+    return PIC_OK;
+}
+
+int mlp_scratch(pic_sim *s, long long B)
+{
+    MlpScratch &S = s->ms;
+    if (!S.it) {
+        void *small = nullptr;
+        int rc = dalloc(s, &small, 64);
+        if (rc) return rc;
+        S.acc = (double *)small;                  // 4 doubles
+        S.loss = (float *)((char *)small + 32);   // 2 floats
+        S.it = (int *)((char *)small + 48);
+    }
+    if (B <= S.B) return PIC_OK;
+    void *buf = nullptr;
+    const size_t per_row = (size_t)(3 * 2 + 6 * kMlpH) * sizeof(float);
+    int rc = dalloc(s, &buf, per_row * (size_t)B);
+    if (rc) return rc;
+    float *f = (float *)buf;
+    S.X = f;
+    S.T = f + 2 * B;
+    S.Y = f + 4 * B;
+    for (int l = 0; l < 3; l++) {
+        S.Z.z[l] = f + 6 * B + (size_t)l * kMlpH * B;
+        S.D.z[l] = f + 6 * B + (size_t)(3 + l) * kMlpH * B;
+    }
+    S.B = B;
+    return PIC_OK;
+}
+
+// ln G (+ 8/(3 chi) for pairs) from the FP64 tables at two values of chi
+int mlp_table_lnG(pic_sim *s, int p, const double chi[2], double out[2])
+{
+    double *d = nullptr;
+    CK(cudaMalloc(&d, 4 * sizeof(double)));
+    cudaError_t e = cudaMemcpyAsync(d, chi, 2 * sizeof(double), cudaMemcpyHostToDevice, s->st);
+    if (e == cudaSuccess) {
+        launch_qed_eval(s->T, true, p, 2, d, nullptr, d + 2, s->st);
+        e = cudaGetLastError();
+    }
+    double G[2] = {0, 0};
+    if (e == cudaSuccess) e = cudaMemcpyAsync(G, d + 2, 2 * sizeof(double), cudaMemcpyDeviceToHost, s->st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s->st);
+    cudaFree(d);
+    if (e != cudaSuccess) return fail(s, PIC_ERR_CUDA, "mlp: table evaluation: %s", cudaGetErrorString(e));
+    for (int i = 0; i < 2; i++) out[i] = std::log(G[i]) + (p == QED_PAIR ? 8.0 / (3.0 * chi[i]) : 0.0);
+    return PIC_OK;
+}
+
+void mlp_norm_set(MlpNorm &n, double chi_min, double chi_max, double mu, double sd)
+{
+    n.lnchi_lo = std::log(chi_min);
+    n.lnchi_hi = std::log(chi_max);
+    n.x0a = (float)(2.0 / (n.lnchi_hi - n.lnchi_lo));
+    n.x0b = (float)(-(n.lnchi_hi + n.lnchi_lo) / (n.lnchi_hi - n.lnchi_lo));
+    n.mu = (float)mu;
+    n.sd = (float)sd;
+}
+
+// initial parameters: W ~ N(0, 1/fan_in), biases 0
+void mlp_init_params(std::vector<float> &P, uint64_t seed)
+{
+    std::mt19937_64 rng(seed ^ 0x6d6c7020696e6974ull);
+    std::normal_distribution<double> nd(0.0, 1.0);
+    P.assign(kMlpNParams, 0.f);
+    auto fill = [&](int off, int n_out, int n_in) {
+        for (int i = 0; i < n_out * n_in; i++) P[off + i] = (float)(nd(rng) / std::sqrt((double)n_in));
+    };
+    fill(kOffW0, kMlpH, 2);
+    fill(kOffW1, kMlpH, kMlpH);
+    fill(kOffW2, kMlpH, kMlpH);
+    fill(kOffW3, 2, kMlpH);
+}
+
+int mlp_check(pic_sim *s, int process)
+{
+    if (process != PIC_QED_EMISSION && process != PIC_QED_PAIR) return fail(s, PIC_ERR_ARG, "mlp: bad process");
+    if (!s->qed_tables) return fail(s, PIC_ERR_STATE, "mlp: call pic_set_qed first (the tables)");
+    return PIC_OK;
+}
+
+int mlp_validate(pic_sim *s, int p, pic_mlp_report *rep)
+{
+    MlpNet &net = s->net[p];
+    int rc = mlp_scratch(s, 0);
+    if (rc) return rc;
+    CK(cudaMemsetAsync(s->ms.acc, 0, 4 * sizeof(double), s->st));
+    launch_mlp_validate(net.img, net.nrm, s->T, p, 256, 256, s->ms.acc, s->st);
+    CK(cudaGetLastError());
+    double acc[4];
+    CK(cudaMemcpyAsync(acc, s->ms.acc, sizeof acc, cudaMemcpyDeviceToHost, s->st));
+    CK(cudaStreamSynchronize(s->st));
+    rep->max_err_lnG = acc[0];
+    rep->max_err_s = acc[1];
+    rep->rms_err_s = std::sqrt(acc[2] / (256.0 * 256.0));
+    rep->table_bytes = (int64_t)(qed_table_bytes() / 2);
+    rep->net_bytes = kMlpStageBytes;
+    return PIC_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+int pic_mlp_train(pic_sim *s, int p, const pic_mlp_train_opts *o, pic_mlp_report *rep)
+{
+    if (!s || !o) return PIC_ERR_ARG;
+    int rc = mlp_check(s, p);
+    if (rc) return rc;
+    const long long iters = o->iterations > 0 ? o->iterations : 20000;
+    const long long B = o->batch > 0 ? o->batch : 16384;
+    const double chi_min = o->chi_min > 0 ? o->chi_min : (p == QED_PAIR ? 1e-2 : 1e-3);
+    const double chi_max = o->chi_max > 0 ? o->chi_max : 1e2;
+    if (B % 128 || B > (1ll << 22) || o->iterations < 0 || !(chi_max > chi_min) || chi_min < 1e-4 || chi_max > 1e3 ||
+        o->lr < 0 || o->lr_final < 0 || o->rate_weight < 0)
+        return fail(s, PIC_ERR_ARG, "pic_mlp_train: bad options (batch a multiple of 128, chi range in [1e-4, 1e3])");
+    MlpNet &net = s->net[p];
+    const bool fresh = !net.img || !o->keep;
+    if ((rc = mlp_net_alloc(s, net)) || (rc = mlp_scratch(s, B))) return rc;
+    double lg[2];
+    const double ends[2] = {chi_min, chi_max};
+    if ((rc = mlp_table_lnG(s, p, ends, lg))) return rc;
+    mlp_norm_set(net.nrm, chi_min, chi_max, 0.5 * (lg[0] + lg[1]), std::max(0.5 * std::fabs(lg[1] - lg[0]), 1.0));
+    if (fresh) {
+        std::vector<float> P0;
+        mlp_init_params(P0, o->seed + (uint64_t)p);
+        CK(cudaMemcpyAsync(net.P, P0.data(), P0.size() * sizeof(float), cudaMemcpyHostToDevice, s->st));
+        CK(cudaMemsetAsync(net.M, 0, 3 * (size_t)kMlpNParams * sizeof(float), s->st));  // M, V, G
+    }
+    launch_mlp_image(net.P, net.img, s->st);
+    CK(cudaMemsetAsync(s->ms.it, 0, sizeof(int), s->st));
+    CK(cudaMemsetAsync(s->ms.loss, 0, 2 * sizeof(float), s->st));
+    CK(cudaStreamSynchronize(s->st));
+    MlpAdam a{iters, o->lr > 0 ? o->lr : 1e-2, o->lr_final > 0 ? o->lr_final : 1e-4, 0.9f, 0.999f, 1e-8f};
+    const float w_rate = (float)(o->rate_weight > 0 ? o->rate_weight : 4.0);
+    const uint32_t key[2] = {(uint32_t)o->seed, (uint32_t)(o->seed >> 32)};
+    // one iteration captured as a graph on a private stream, replayed
+    cudaStream_t ts = nullptr;
+    cudaGraph_t gr = nullptr;
+    cudaGraphExec_t ge = nullptr;
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    cudaError_t e = cudaStreamCreateWithFlags(&ts, cudaStreamNonBlocking);
+    if (e == cudaSuccess) e = cudaStreamBeginCapture(ts, cudaStreamCaptureModeThreadLocal);
+    if (e == cudaSuccess) {
+        mlp_train_iteration(net, s->ms, s->T, p, key, a, w_rate, ts);
+        e = cudaStreamEndCapture(ts, &gr);
+    }
+    if (e == cudaSuccess) e = cudaGraphInstantiate(&ge, gr, 0);
+    if (e == cudaSuccess) e = cudaEventCreate(&e0);
+    if (e == cudaSuccess) e = cudaEventCreate(&e1);
+    if (e == cudaSuccess) e = cudaEventRecord(e0, ts);
+    for (long long i = 0; i < iters && e == cudaSuccess; i++) e = cudaGraphLaunch(ge, ts);
+    note_launch(6 * (iters - 1));  // the captured iteration counted its six launches once
+    if (e == cudaSuccess) e = cudaEventRecord(e1, ts);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(ts);
+    float ms = 0.f, loss[2] = {0.f, 0.f};
+    if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
+    if (e == cudaSuccess) e = cudaMemcpy(loss, s->ms.loss, sizeof loss, cudaMemcpyDeviceToHost);
+    if (ge) cudaGraphExecDestroy(ge);
+    if (gr) cudaGraphDestroy(gr);
+    if (e0) cudaEventDestroy(e0);
+    if (e1) cudaEventDestroy(e1);
+    if (ts) cudaStreamDestroy(ts);
+    if (e != cudaSuccess) return fail(s, PIC_ERR_CUDA, "pic_mlp_train: %s", cudaGetErrorString(e));
+    net.ready = true;
+    pic_mlp_report r{};
+    if ((rc = mlp_validate(s, p, &r))) return rc;
+    r.loss = loss[1];
+    r.ms = ms;
+    r.iterations = iters;
+    if (rep) *rep = r;
+    return PIC_OK;
+}
+
+int pic_mlp_validate(pic_sim *s, int p, pic_mlp_report *rep)
+{
+    if (!s || !rep) return PIC_ERR_ARG;
+    int rc = mlp_check(s, p);
+    if (rc) return rc;
+    if (!s->net[p].ready) return fail(s, PIC_ERR_STATE, "pic_mlp_validate: no network");
+    *rep = pic_mlp_report{};
+    return mlp_validate(s, p, rep);
+}
+
+int pic_mlp_get(pic_sim *s, int p, float *params, pic_mlp_info *info)
+{
+    if (!s) return PIC_ERR_ARG;
+    if (p != PIC_QED_EMISSION && p != PIC_QED_PAIR) return fail(s, PIC_ERR_ARG, "pic_mlp_get: bad process");
+    const MlpNet &net = s->net[p];
+    if (!net.ready) return fail(s, PIC_ERR_STATE, "pic_mlp_get: no network");
+    if (params) {
+        CK(cudaMemcpyAsync(params, net.P, (size_t)kMlpNParams * sizeof(float), cudaMemcpyDeviceToHost, s->st));
+        CK(cudaStreamSynchronize(s->st));
+    }
+    if (info) {
+        info->chi_min = std::exp(net.nrm.lnchi_lo);
+        info->chi_max = std::exp(net.nrm.lnchi_hi);
+        info->mu = net.nrm.mu;
+        info->sd = net.nrm.sd;
+    }
+    return PIC_OK;
+}
+
+int pic_mlp_set(pic_sim *s, int p, const float *params, const pic_mlp_info *info)
+{
+    if (!s || !params || !info) return PIC_ERR_ARG;
+    if (p != PIC_QED_EMISSION && p != PIC_QED_PAIR) return fail(s, PIC_ERR_ARG, "pic_mlp_set: bad process");
+    if (!(info->chi_max > info->chi_min) || !(info->chi_min > 0.0) || !(info->sd > 0.0))
+        return fail(s, PIC_ERR_ARG, "pic_mlp_set: bad range or normalisation");
+    MlpNet &net = s->net[p];
+    int rc = mlp_net_alloc(s, net);
+    if (rc) return rc;
+    mlp_norm_set(net.nrm, info->chi_min, info->chi_max, info->mu, info->sd);
+    CK(cudaMemcpyAsync(net.P, params, (size_t)kMlpNParams * sizeof(float), cudaMemcpyHostToDevice, s->st));
+    CK(cudaMemsetAsync(net.M, 0, 3 * (size_t)kMlpNParams * sizeof(float), s->st));
+    launch_mlp_image(net.P, net.img, s->st);
+    CK(cudaGetLastError());
+    CK(cudaStreamSynchronize(s->st));
+    net.ready = true;
+    return PIC_OK;
+}
+
+int pic_mlp_eval(pic_sim *s, int p, int64_t n, const float *x, float *y)
+{
+    if (!s) return PIC_ERR_ARG;
+    if ((p != PIC_QED_EMISSION && p != PIC_QED_PAIR) || n < 0 || (n && (!x || !y)))
+        return fail(s, PIC_ERR_ARG, "pic_mlp_eval: bad arguments");
+    const MlpNet &net = s->net[p];
+    if (!net.ready) return fail(s, PIC_ERR_STATE, "pic_mlp_eval: no network");
+    if (n == 0) return PIC_OK;
+    float *d = nullptr;
+    CK(cudaMalloc(&d, (size_t)n * 4 * sizeof(float)));
+    cudaError_t e = cudaMemcpyAsync(d, x, (size_t)n * 2 * sizeof(float), cudaMemcpyHostToDevice, s->st);
+    if (e == cudaSuccess) {
+        launch_mlp_eval(net.img, n, d, d + 2 * n, s->st);
+        e = cudaGetLastError();
+    }
+    if (e == cudaSuccess) e = cudaMemcpyAsync(y, d + 2 * n, (size_t)n * 2 * sizeof(float), cudaMemcpyDeviceToHost, s->st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s->st);
+    cudaFree(d);
+    if (e != cudaSuccess) return fail(s, PIC_ERR_CUDA, "pic_mlp_eval: %s", cudaGetErrorString(e));
+    return PIC_OK;
+}
+
+int pic_mlp_grad(pic_sim *s, int p, int64_t n, const float *x, const float *t, float *grad, double *loss)
+{
+    if (!s) return PIC_ERR_ARG;
+    if ((p != PIC_QED_EMISSION && p != PIC_QED_PAIR) || n <= 0 || n % 32 || n > (1 << 20) || !x || !t || !grad)
+        return fail(s, PIC_ERR_ARG, "pic_mlp_grad: bad arguments (n a positive multiple of 32)");
+    MlpNet &net = s->net[p];
+    if (!net.ready) return fail(s, PIC_ERR_STATE, "pic_mlp_grad: no network");
+    int rc = mlp_scratch(s, n);
+    if (rc) return rc;
+    MlpScratch &S = s->ms;
+    CK(cudaMemcpyAsync(S.X, x, (size_t)n * 2 * sizeof(float), cudaMemcpyHostToDevice, s->st));
+    CK(cudaMemcpyAsync(S.T, t, (size_t)n * 2 * sizeof(float), cudaMemcpyHostToDevice, s->st));
+    CK(cudaMemsetAsync(net.G, 0, (size_t)kMlpNParams * sizeof(float), s->st));
+    CK(cudaMemsetAsync(S.loss, 0, sizeof(float), s->st));
+    launch_mlp_forward(net.img, n, S.X, S.Z, S.Y, s->st);
+    launch_mlp_backward(net.img, n, S.X, S.T, S.Y, S.Z, S.D, net.G, 1.0f, S.loss, s->st);
+    CK(cudaGetLastError());
+    float l = 0.f;
+    CK(cudaMemcpyAsync(grad, net.G, (size_t)kMlpNParams * sizeof(float), cudaMemcpyDeviceToHost, s->st));
+    CK(cudaMemcpyAsync(&l, S.loss, sizeof(float), cudaMemcpyDeviceToHost, s->st));
+    CK(cudaMemsetAsync(net.G, 0, (size_t)kMlpNParams * sizeof(float), s->st));
+    CK(cudaStreamSynchronize(s->st));
+    if (loss) *loss = l;
     return PIC_OK;
 }
 

@@ -86,7 +86,7 @@ __global__ void __launch_bounds__(kRedThreads) k_kinetic_f32(PartF32 P, int phot
     block_reduce_store<2, false>(v, partial);
 }
 
-__global__ void __launch_bounds__(kRedThreads) k_kinetic_f64(PartF64 P, double *partial)
+__global__ void __launch_bounds__(kRedThreads) k_kinetic_f64(PartF64 P, int photon, double *partial)
 {
     double v[2] = {0.0, 0.0};
     long long n = *P.dn;
@@ -94,7 +94,7 @@ __global__ void __launch_bounds__(kRedThreads) k_kinetic_f64(PartF64 P, double *
         if (P.cell[p] == kDead) continue;
         double ux = P.u[0][p], uy = P.u[1][p], uz = P.u[2][p];
         double uu = ux * ux + uy * uy + uz * uz;
-        v[0] += uu / (sqrt(1.0 + uu) + 1.0);
+        v[0] += photon ? sqrt(uu) : uu / (sqrt(1.0 + uu) + 1.0);
         v[1] += 1.0;
     }
     block_reduce_store<2, false>(v, partial);
@@ -233,9 +233,9 @@ void diag_kinetic_f32(const PartF32 &P, bool photon, double *scratch, double *ou
     k_kinetic_f32<<<kRedBlocks, kRedThreads, 0, st>>>(P, photon ? 1 : 0, scratch);
     k_final<2, false><<<1, kRedThreads, 0, st>>>(scratch, kRedBlocks, out2);
 }
-void diag_kinetic_f64(const PartF64 &P, double *scratch, double *out2, cudaStream_t st)
+void diag_kinetic_f64(const PartF64 &P, bool photon, double *scratch, double *out2, cudaStream_t st)
 {
-    k_kinetic_f64<<<kRedBlocks, kRedThreads, 0, st>>>(P, scratch);
+    k_kinetic_f64<<<kRedBlocks, kRedThreads, 0, st>>>(P, photon ? 1 : 0, scratch);
     k_final<2, false><<<1, kRedThreads, 0, st>>>(scratch, kRedBlocks, out2);
 }
 

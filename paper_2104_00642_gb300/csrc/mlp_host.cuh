@@ -1,0 +1,49 @@
+// mlp_host.cuh -- host side of the surrogate network (mlp.cu).
+#pragma once
+#include <cuda_runtime.h>
+
+#include "mlp.cuh"
+#include "qed.cuh"
+
+namespace pic {
+
+// one network: FP32 master parameters with Adam moments and the gradient
+// (packed order), and the BF16 device image the kernels read
+struct MlpNet {
+    MlpImage *img = nullptr;
+    float *P = nullptr, *M = nullptr, *V = nullptr, *G = nullptr;
+    MlpNorm nrm{};
+    bool ready = false;
+};
+
+// training scratch for a batch of B rows (B a multiple of 128)
+struct MlpScratch {
+    long long B = 0;
+    float *X = nullptr, *T = nullptr, *Y = nullptr;  // [B][2]
+    MlpZ Z{}, D{};                                   // [B][64] each
+    float *loss = nullptr;                           // [0] running, [1] last iteration
+    int *it = nullptr;                               // iteration counter
+    double *acc = nullptr;                           // validation accumulators (4)
+};
+
+struct MlpAdam {
+    long long iters;
+    double lr0, lr_final;
+    float beta1, beta2, eps;
+};
+
+// (both staged images stay below the 48 KB default dynamic shared memory)
+static_assert(kMlpTrainStageBytes <= 48 * 1024, "no opt-in needed");
+void launch_mlp_image(const float *P, MlpImage *img, cudaStream_t st);
+void launch_mlp_forward(const MlpImage *img, long long B, const float *X, const MlpZ &Z, float *Y, cudaStream_t st);
+void launch_mlp_backward(const MlpImage *img, long long B, const float *X, const float *Tg, const float *Y,
+                         const MlpZ &Z, const MlpZ &D, float *grad, float w_rate, float *loss, cudaStream_t st);
+void mlp_train_iteration(MlpNet &net, MlpScratch &S, const QedTables &T, int p, const uint32_t *key,
+                         const MlpAdam &a, float w_rate, cudaStream_t st);
+void launch_mlp_eval(const MlpImage *img, long long n, const float *X, float *Y, cudaStream_t st);
+void launch_qed_eval_surr(const MlpImage *img, const MlpNorm &nrm, const QedTables &T, bool f64, int p, long long n,
+                          const double *chi, const double *r, double *out, cudaStream_t st);
+void launch_mlp_validate(const MlpImage *img, const MlpNorm &nrm, const QedTables &T, int p, int nc, int nr,
+                         double *acc, cudaStream_t st);
+
+}  // namespace pic

@@ -22,6 +22,8 @@ struct PartF64 {
     double *u[3];
     long long n;           // host-side upper bound of the count (grid sizing)
     const long long *dn;   // live count on the device (updated by sorts)
+    double *tau;           // QED optical depth (NULL when the species has none)
+    uint64_t *id;          // QED identity (NULL when the species has none)
 };
 
 struct PushConst {

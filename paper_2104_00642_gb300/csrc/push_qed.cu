@@ -16,24 +16,41 @@
 
 namespace pic {
 
-template <int DIM>
+// With SURR the surrogate network replaces the tables inside its chi range.
+// Its evaluation is warp-collective, so lanes without a live particle stay
+// in step (on a safe dummy particle in cell 0, storing nothing) until the
+// network has run; a live lane draws its emission numbers every step, so a
+// single evaluation yields both the rate and, if the event happens, the
+// energy fraction.
+template <int DIM, bool SURR>
 __global__ void __launch_bounds__(256) k_push_qed_f32(PartF32 P, float *__restrict__ F, Grid g, PushConst pc,
                                                       QedParams q, int *err, double *e_abs)
 {
+    extern __shared__ __align__(16) unsigned char smem[];
+    if constexpr (SURR) {
+        mlp_stage(smem, q.net, kMlpStageBytes);
+        __syncthreads();
+    }
     const long long p = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-    if (p >= *P.dn) {
-        if (p <= P.n) q.ev[p] = 0;  // slots past the live count (and the scan's end slot) carry no event
-        return;
+    const bool live = p < *P.dn && P.cell[p] != kDead;
+    if (!SURR || !__any_sync(0xffffffffu, live)) {
+        if (!live) {
+            if (p <= P.n) q.ev[p] = 0;  // dead slots and slots past the live count (and the scan's end slot)
+            return;
+        }
     }
-    const uint32_t pc0 = P.cell[p];
-    if (pc0 == kDead) {
-        q.ev[p] = 0;
-        return;
+    int c[3] = {0, 0, 0};
+    float o[3] = {0.f, 0.f, 0.f};
+    float ux = 0.f, uy = 0.f, uz = 0.f;
+    if (live) {
+        unpack_cell(g, P.cell[p], c[0], c[1], c[2]);
+        o[0] = P.off[0][p];
+        if (DIM >= 2) o[1] = P.off[1][p];
+        if (DIM >= 3) o[2] = P.off[2][p];
+        ux = P.u[0][p];
+        uy = P.u[1][p];
+        uz = P.u[2][p];
     }
-    int c[3];
-    unpack_cell(g, pc0, c[0], c[1], c[2]);
-    float o[3] = {P.off[0][p], DIM >= 2 ? P.off[1][p] : 0.f, DIM >= 3 ? P.off[2][p] : 0.f};
-    float ux = P.u[0][p], uy = P.u[1][p], uz = P.u[2][p];
     float u[3] = {ux, uy, uz};
     float ig = inv_gamma(ux, uy, uz);
 #pragma unroll
@@ -55,12 +72,36 @@ __global__ void __launch_bounds__(256) k_push_qed_f32(PartF32 P, float *__restri
         const double uu = (double)ux * ux + (double)uy * uy + (double)uz * uz;
         const double gam = sqrt(1.0 + uu);
         const double chi = chi_of<float>((float)gam, ux, uy, uz, eb[0], eb[1], eb[2], eb[3], eb[4], eb[5], q.inv_Es);
-        double tau = q.tau[p] - q.pref * qed_rate<float>(q.T, QED_RAD, chi) / gam;
+        uint32_t w[4];
+        bool use_net = false;
+        float y0 = 0.f, y1 = 0.f;
+        if constexpr (SURR) {
+            double lnchi;
+            const bool inr = live && mlp_in_range(q.nrm, chi, lnchi);
+            if (__any_sync(0xffffffffu, inr)) {
+                float x0 = 0.f, x1 = 0.f;
+                if (inr) {
+                    const uint64_t id = q.id[p];
+                    philox4x32_10((uint32_t)id, (uint32_t)(id >> 32), q.step, QP_EMIT, q.key[0], q.key[1], w);
+                    mlp_inputs(q.nrm, QED_RAD, lnchi, uniform24(w[0]), x0, x1);
+                }
+                mlp_eval_warp(*reinterpret_cast<const MlpImage *>(smem), x0, x1, y0, y1);
+                use_net = inr;
+            }
+            if (!live) {
+                if (p <= P.n) q.ev[p] = 0;
+                return;
+            }
+        }
+        const double G = use_net ? mlp_rate(q.nrm, QED_RAD, chi, y1) : qed_rate<float>(q.T, QED_RAD, chi);
+        double tau = q.tau[p] - q.pref * G / gam;
         if (tau <= 0.0) {
-            uint32_t w[4];
-            const uint64_t id = q.id[p];
-            philox4x32_10((uint32_t)id, (uint32_t)(id >> 32), q.step, QP_EMIT, q.key[0], q.key[1], w);
-            const double frac = qed_sample<float>(q.T, QED_RAD, chi, uniform24(w[0]));
+            if (!use_net) {
+                const uint64_t id = q.id[p];
+                philox4x32_10((uint32_t)id, (uint32_t)(id >> 32), q.step, QP_EMIT, q.key[0], q.key[1], w);
+            }
+            const double r0 = uniform24(w[0]);
+            const double frac = use_net ? mlp_fraction(QED_RAD, y0, r0) : qed_sample<float>(q.T, QED_RAD, chi, r0);
             const double eg = frac * gam;
             const double umag = sqrt(uu);
             const double g1 = fmax(gam * (1.0 - frac), 1.0);
@@ -79,6 +120,9 @@ __global__ void __launch_bounds__(256) k_push_qed_f32(PartF32 P, float *__restri
             }
         }
         q.tau[p] = tau;
+    } else if (SURR && !live) {
+        if (p <= P.n) q.ev[p] = 0;
+        return;
     }
     const float ig1 = inv_gamma(ux, uy, uz);
     u[0] = ux;
@@ -137,24 +181,36 @@ __global__ void __launch_bounds__(256) k_push_qed_f32(PartF32 P, float *__restri
     if (event) reinterpret_cast<float4 *>(q.evk)[p] = evd;
 }
 
-template <int DIM>
+// SURR: the pair network inside its chi range, as in k_push_qed_f32
+template <int DIM, bool SURR>
 __global__ void __launch_bounds__(256) k_push_photon_f32(PartF32 P, const float *__restrict__ F, Grid g, PushConst pc,
                                                          QedParams q, int *err)
 {
+    extern __shared__ __align__(16) unsigned char smem[];
+    if constexpr (SURR) {
+        mlp_stage(smem, q.net, kMlpStageBytes);
+        __syncthreads();
+    }
     const long long p = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-    if (p >= *P.dn) {
-        if (p <= P.n) q.ev[p] = 0;  // slots past the live count (and the scan's end slot) carry no event
-        return;
+    const bool live = p < *P.dn && P.cell[p] != kDead;
+    if (!SURR || !__any_sync(0xffffffffu, live)) {
+        if (!live) {
+            if (p <= P.n) q.ev[p] = 0;  // dead slots and slots past the live count (and the scan's end slot)
+            return;
+        }
     }
-    const uint32_t pc0 = P.cell[p];
-    if (pc0 == kDead) {
-        q.ev[p] = 0;
-        return;
+    int c[3] = {0, 0, 0};
+    float o[3] = {0.f, 0.f, 0.f};
+    float kx = 0.f, ky = 0.f, kz = 0.f;
+    if (live) {
+        unpack_cell(g, P.cell[p], c[0], c[1], c[2]);
+        o[0] = P.off[0][p];
+        if (DIM >= 2) o[1] = P.off[1][p];
+        if (DIM >= 3) o[2] = P.off[2][p];
+        kx = P.u[0][p];
+        ky = P.u[1][p];
+        kz = P.u[2][p];
     }
-    int c[3];
-    unpack_cell(g, pc0, c[0], c[1], c[2]);
-    float o[3] = {P.off[0][p], DIM >= 2 ? P.off[1][p] : 0.f, DIM >= 3 ? P.off[2][p] : 0.f};
-    const float kx = P.u[0][p], ky = P.u[1][p], kz = P.u[2][p];
     const float km = sqrtf(kx * kx + ky * ky + kz * kz);
     const float ik = km > 0.f ? 1.0f / km : 0.f;
     const float v[3] = {kx * ik, ky * ik, kz * ik};
@@ -170,17 +226,44 @@ __global__ void __launch_bounds__(256) k_push_photon_f32(PartF32 P, const float 
         float eb[6];
         gather<float, DIM>(F, g, icn, wn, ich, wh, eb);
         const double chi = chi_of<float>(km, kx, ky, kz, eb[0], eb[1], eb[2], eb[3], eb[4], eb[5], q.inv_Es);
-        double tau = q.tau[p] - (km > 0.f ? q.pref * qed_rate<float>(q.T, QED_PAIR, chi) / km : 0.0);
+        uint32_t w[4];
+        bool use_net = false;
+        float y0 = 0.f, y1 = 0.f;
+        if constexpr (SURR) {
+            double lnchi;
+            const bool inr = live && km > 0.f && mlp_in_range(q.nrm, chi, lnchi);
+            if (__any_sync(0xffffffffu, inr)) {
+                float x0 = 0.f, x1 = 0.f;
+                if (inr) {
+                    const uint64_t id = q.id[p];
+                    philox4x32_10((uint32_t)id, (uint32_t)(id >> 32), q.step, QP_PAIR, q.key[0], q.key[1], w);
+                    mlp_inputs(q.nrm, QED_PAIR, lnchi, uniform24(w[0]), x0, x1);
+                }
+                mlp_eval_warp(*reinterpret_cast<const MlpImage *>(smem), x0, x1, y0, y1);
+                use_net = inr;
+            }
+            if (!live) {
+                if (p <= P.n) q.ev[p] = 0;
+                return;
+            }
+        }
+        const double G = use_net ? mlp_rate(q.nrm, QED_PAIR, chi, y1) : qed_rate<float>(q.T, QED_PAIR, chi);
+        double tau = q.tau[p] - (km > 0.f ? q.pref * G / km : 0.0);
         if (tau <= 0.0) {
-            uint32_t w[4];
-            const uint64_t id = q.id[p];
-            philox4x32_10((uint32_t)id, (uint32_t)(id >> 32), q.step, QP_PAIR, q.key[0], q.key[1], w);
-            const double vf = qed_sample<float>(q.T, QED_PAIR, chi, uniform24(w[0]));
+            if (!use_net) {
+                const uint64_t id = q.id[p];
+                philox4x32_10((uint32_t)id, (uint32_t)(id >> 32), q.step, QP_PAIR, q.key[0], q.key[1], w);
+            }
+            const double r0 = uniform24(w[0]);
+            const double vf = use_net ? mlp_fraction(QED_PAIR, y0, r0) : qed_sample<float>(q.T, QED_PAIR, chi, r0);
             event = 1;
             evd = make_float4(kx, ky, kz, (float)vf);
             tau = -log(uniform24(w[1]));
         }
         q.tau[p] = tau;
+    } else if (SURR && !live) {
+        if (p <= P.n) q.ev[p] = 0;
+        return;
     }
 #pragma unroll
     for (int d = 0; d < DIM; d++) drift_f32(c[d], o[d], pc.hdx_f[d] * v[d]);
@@ -206,15 +289,226 @@ __global__ void __launch_bounds__(256) k_push_photon_f32(PartF32 P, const float 
     if (event) reinterpret_cast<float4 *>(q.evk)[p] = evd;
 }
 
+// ---------------------------------------------------------------------
+// FP64 plain form: absolute positions, everything in double precision,
+// the tables' FP64 copy (no surrogate).  Event data: 4 doubles per particle.
+// ---------------------------------------------------------------------
+template <int DIM>
+__global__ void __launch_bounds__(256) k_push_qed_f64(PartF64 P, double *__restrict__ F, Grid g, PushConst pc,
+                                                      QedParams q, int *err, double *e_abs)
+{
+    const long long p = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (p >= *P.dn || P.cell[p] == kDead) {
+        if (p <= P.n) q.ev[p] = 0;
+        return;
+    }
+    double x[3] = {P.x[0][p], DIM >= 2 ? P.x[1][p] : 0.0, DIM >= 3 ? P.x[2][p] : 0.0};
+    double ux = P.u[0][p], uy = P.u[1][p], uz = P.u[2][p];
+    const double ig = inv_gamma(ux, uy, uz);
+    double u[3] = {ux, uy, uz};
+#pragma unroll
+    for (int d = 0; d < DIM; d++) x[d] += pc.hdt * u[d] * ig;
+    const double xh[3] = {x[0], x[1], x[2]};
+    int icn[3] = {0, 0, 0}, ich[3] = {0, 0, 0};
+    double wn[3][3], wh[3][3];
+#pragma unroll
+    for (int d = 0; d < DIM; d++) axis_w_f64(x[d] / g.dx[d], icn[d], wn[d], ich[d], wh[d]);
+    double eb[6];
+    gather<double, DIM>(F, g, icn, wn, ich, wh, eb);
+    const double k = pc.qmdt2;
+    boris<double>(ux, uy, uz, k * eb[0], k * eb[1], k * eb[2], k * eb[3], k * eb[4], k * eb[5]);
+    uint32_t event = 0;
+    double4 evd = make_double4(0.0, 0.0, 0.0, 0.0);
+    if (q.on) {
+        const double uu = ux * ux + uy * uy + uz * uz;
+        const double gam = sqrt(1.0 + uu);
+        const double chi = chi_of<double>(gam, ux, uy, uz, eb[0], eb[1], eb[2], eb[3], eb[4], eb[5], q.inv_Es);
+        double tau = q.tau[p] - q.pref * qed_rate<double>(q.T, QED_RAD, chi) / gam;
+        if (tau <= 0.0) {
+            uint32_t w[4];
+            const uint64_t id = q.id[p];
+            philox4x32_10((uint32_t)id, (uint32_t)(id >> 32), q.step, QP_EMIT, q.key[0], q.key[1], w);
+            const double frac = qed_sample<double>(q.T, QED_RAD, chi, uniform24(w[0]));
+            const double eg = frac * gam, umag = sqrt(uu);
+            const double g1 = fmax(gam * (1.0 - frac), 1.0);
+            const double s = umag > 0.0 ? sqrt(g1 * g1 - 1.0) / umag : 0.0;
+            const double e = umag > 0.0 ? eg / umag : 0.0;
+            const double kx = e * ux, ky = e * uy, kz = e * uz;
+            ux *= s;
+            uy *= s;
+            uz *= s;
+            tau = -log(uniform24(w[1]));
+            if (eg >= q.emin) {
+                event = 1;
+                evd = make_double4(kx, ky, kz, 0.0);
+            } else {
+                atomicAdd(q.e_lost, eg * q.wdV);
+            }
+        }
+        q.tau[p] = tau;
+    }
+    const double ig1 = inv_gamma(ux, uy, uz);
+    u[0] = ux;
+    u[1] = uy;
+    u[2] = uz;
+#pragma unroll
+    for (int d = 0; d < DIM; d++) x[d] += pc.hdt * u[d] * ig1;
+    double x1[3] = {x[0], x[1], x[2]};
+#pragma unroll
+    for (int d = 0; d < DIM; d++) x[d] += pc.hdt * u[d] * ig1;
+    double S0[3][5], dS[3][5];
+    int base[3] = {0, 0, 0};
+    bool ok = true;
+#pragma unroll
+    for (int d = 0; d < DIM; d++) {
+        int i0, i1;
+        double w0[3], w1[3];
+        axis_wn_f64(xh[d] / g.dx[d], i0, w0);
+        axis_wn_f64(x[d] / g.dx[d], i1, w1);
+        ok &= window5<double>(i0, w0, i1, w1, S0[d], dS[d]);
+        base[d] = i0 - 2;
+    }
+    if (!ok) {
+        atomicOr(err, ERR_CFL);
+        q.ev[p] = 0;
+        return;
+    }
+    deposit_global<double, DIM>(F, g, base, S0, dS, pc.cJ, pc.qw * uy * ig1, pc.qw * uz * ig1);
+    bool dead = false;
+    int cc[3] = {0, 0, 0};
+#pragma unroll
+    for (int d = 0; d < DIM; d++) {
+        const double L = (double)g.n[d] * g.dx[d];
+        if (g.bc[d] == PERIODIC) {
+            if (x1[d] < 0.0) x1[d] += L;
+            if (x1[d] >= L) x1[d] -= L;
+        } else if (x1[d] < 0.0 || x1[d] >= L) {
+            dead = true;
+        }
+        const int ci = (int)floor(x1[d] / g.dx[d]);
+        cc[d] = ci < 0 ? 0 : (ci >= g.n[d] ? g.n[d] - 1 : ci);
+    }
+    if (!isfinite(ux + uy + uz)) atomicOr(err, ERR_NONFINITE);
+    if (dead) {
+        P.cell[p] = kDead;
+        const double uu = ux * ux + uy * uy + uz * uz;
+        atomicAdd(e_abs, pc.wmdV * uu / (sqrt(1.0 + uu) + 1.0));
+        event = 0;
+    } else {
+        P.cell[p] = pack_cell(g, cc[0], cc[1], cc[2]);
+    }
+#pragma unroll
+    for (int d = 0; d < DIM; d++) P.x[d][p] = x1[d];
+    P.u[0][p] = ux;
+    P.u[1][p] = uy;
+    P.u[2][p] = uz;
+    q.ev[p] = event;
+    if (event) reinterpret_cast<double4 *>(q.evk)[p] = evd;
+}
+
+template <int DIM>
+__global__ void __launch_bounds__(256) k_push_photon_f64(PartF64 P, const double *__restrict__ F, Grid g,
+                                                         PushConst pc, QedParams q, int *err)
+{
+    const long long p = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (p >= *P.dn || P.cell[p] == kDead) {
+        if (p <= P.n) q.ev[p] = 0;
+        return;
+    }
+    double x[3] = {P.x[0][p], DIM >= 2 ? P.x[1][p] : 0.0, DIM >= 3 ? P.x[2][p] : 0.0};
+    const double kx = P.u[0][p], ky = P.u[1][p], kz = P.u[2][p];
+    const double km = sqrt(kx * kx + ky * ky + kz * kz);
+    const double ik = km > 0.0 ? 1.0 / km : 0.0;
+    const double v[3] = {kx * ik, ky * ik, kz * ik};
+#pragma unroll
+    for (int d = 0; d < DIM; d++) x[d] += pc.hdt * v[d];
+    uint32_t event = 0;
+    double4 evd = make_double4(0.0, 0.0, 0.0, 0.0);
+    if (q.on) {
+        int icn[3] = {0, 0, 0}, ich[3] = {0, 0, 0};
+        double wn[3][3], wh[3][3];
+#pragma unroll
+        for (int d = 0; d < DIM; d++) axis_w_f64(x[d] / g.dx[d], icn[d], wn[d], ich[d], wh[d]);
+        double eb[6];
+        gather<double, DIM>(F, g, icn, wn, ich, wh, eb);
+        const double chi = chi_of<double>(km, kx, ky, kz, eb[0], eb[1], eb[2], eb[3], eb[4], eb[5], q.inv_Es);
+        double tau = q.tau[p] - (km > 0.0 ? q.pref * qed_rate<double>(q.T, QED_PAIR, chi) / km : 0.0);
+        if (tau <= 0.0) {
+            uint32_t w[4];
+            const uint64_t id = q.id[p];
+            philox4x32_10((uint32_t)id, (uint32_t)(id >> 32), q.step, QP_PAIR, q.key[0], q.key[1], w);
+            event = 1;
+            evd = make_double4(kx, ky, kz, qed_sample<double>(q.T, QED_PAIR, chi, uniform24(w[0])));
+            tau = -log(uniform24(w[1]));
+        }
+        q.tau[p] = tau;
+    }
+#pragma unroll
+    for (int d = 0; d < DIM; d++) x[d] += pc.hdt * v[d];
+    bool dead = false;
+    int cc[3] = {0, 0, 0};
+#pragma unroll
+    for (int d = 0; d < DIM; d++) {
+        const double L = (double)g.n[d] * g.dx[d];
+        if (g.bc[d] == PERIODIC) {
+            if (x[d] < 0.0) x[d] += L;
+            if (x[d] >= L) x[d] -= L;
+        } else if (x[d] < 0.0 || x[d] >= L) {
+            dead = true;
+        }
+        const int ci = (int)floor(x[d] / g.dx[d]);
+        cc[d] = ci < 0 ? 0 : (ci >= g.n[d] ? g.n[d] - 1 : ci);
+    }
+    if (dead) {
+        P.cell[p] = kDead;
+        event = 0;
+    } else {
+        P.cell[p] = pack_cell(g, cc[0], cc[1], cc[2]);
+    }
+#pragma unroll
+    for (int d = 0; d < DIM; d++) P.x[d][p] = x[d];
+    q.ev[p] = event;
+    if (event) reinterpret_cast<double4 *>(q.evk)[p] = evd;
+}
+
+void launch_push_qed_f64(const PartF64 &P, double *F, const Grid &g, const PushConst &pc, const QedParams &q,
+                         int *err, double *e_abs, cudaStream_t st)
+{
+    if (P.n == 0) return;
+    note_launch();
+    const int nb = div_up(P.n + 1, 256);
+    if (g.dim == 1) k_push_qed_f64<1><<<nb, 256, 0, st>>>(P, F, g, pc, q, err, e_abs);
+    else if (g.dim == 2) k_push_qed_f64<2><<<nb, 256, 0, st>>>(P, F, g, pc, q, err, e_abs);
+    else k_push_qed_f64<3><<<nb, 256, 0, st>>>(P, F, g, pc, q, err, e_abs);
+}
+
+void launch_push_photon_f64(const PartF64 &P, const double *F, const Grid &g, const PushConst &pc,
+                            const QedParams &q, int *err, cudaStream_t st)
+{
+    if (P.n == 0) return;
+    note_launch();
+    const int nb = div_up(P.n + 1, 256);
+    if (g.dim == 1) k_push_photon_f64<1><<<nb, 256, 0, st>>>(P, F, g, pc, q, err);
+    else if (g.dim == 2) k_push_photon_f64<2><<<nb, 256, 0, st>>>(P, F, g, pc, q, err);
+    else k_push_photon_f64<3><<<nb, 256, 0, st>>>(P, F, g, pc, q, err);
+}
+
 void launch_push_qed_f32(const PartF32 &P, float *F, const Grid &g, const PushConst &pc, const QedParams &q,
                          int *err, double *e_abs, cudaStream_t st)
 {
     if (P.n == 0) return;
     note_launch();
     const int nb = div_up(P.n + 1, 256);
-    if (g.dim == 1) k_push_qed_f32<1><<<nb, 256, 0, st>>>(P, F, g, pc, q, err, e_abs);
-    else if (g.dim == 2) k_push_qed_f32<2><<<nb, 256, 0, st>>>(P, F, g, pc, q, err, e_abs);
-    else k_push_qed_f32<3><<<nb, 256, 0, st>>>(P, F, g, pc, q, err, e_abs);
+    if (q.on && q.net) {
+        const int sm = kMlpStageBytes;
+        if (g.dim == 1) k_push_qed_f32<1, true><<<nb, 256, sm, st>>>(P, F, g, pc, q, err, e_abs);
+        else if (g.dim == 2) k_push_qed_f32<2, true><<<nb, 256, sm, st>>>(P, F, g, pc, q, err, e_abs);
+        else k_push_qed_f32<3, true><<<nb, 256, sm, st>>>(P, F, g, pc, q, err, e_abs);
+    } else {
+        if (g.dim == 1) k_push_qed_f32<1, false><<<nb, 256, 0, st>>>(P, F, g, pc, q, err, e_abs);
+        else if (g.dim == 2) k_push_qed_f32<2, false><<<nb, 256, 0, st>>>(P, F, g, pc, q, err, e_abs);
+        else k_push_qed_f32<3, false><<<nb, 256, 0, st>>>(P, F, g, pc, q, err, e_abs);
+    }
 }
 
 void launch_push_photon_f32(const PartF32 &P, const float *F, const Grid &g, const PushConst &pc,
@@ -223,9 +517,16 @@ void launch_push_photon_f32(const PartF32 &P, const float *F, const Grid &g, con
     if (P.n == 0) return;
     note_launch();
     const int nb = div_up(P.n + 1, 256);
-    if (g.dim == 1) k_push_photon_f32<1><<<nb, 256, 0, st>>>(P, F, g, pc, q, err);
-    else if (g.dim == 2) k_push_photon_f32<2><<<nb, 256, 0, st>>>(P, F, g, pc, q, err);
-    else k_push_photon_f32<3><<<nb, 256, 0, st>>>(P, F, g, pc, q, err);
+    if (q.on && q.net) {
+        const int sm = kMlpStageBytes;
+        if (g.dim == 1) k_push_photon_f32<1, true><<<nb, 256, sm, st>>>(P, F, g, pc, q, err);
+        else if (g.dim == 2) k_push_photon_f32<2, true><<<nb, 256, sm, st>>>(P, F, g, pc, q, err);
+        else k_push_photon_f32<3, true><<<nb, 256, sm, st>>>(P, F, g, pc, q, err);
+    } else {
+        if (g.dim == 1) k_push_photon_f32<1, false><<<nb, 256, 0, st>>>(P, F, g, pc, q, err);
+        else if (g.dim == 2) k_push_photon_f32<2, false><<<nb, 256, 0, st>>>(P, F, g, pc, q, err);
+        else k_push_photon_f32<3, false><<<nb, 256, 0, st>>>(P, F, g, pc, q, err);
+    }
 }
 
 }  // namespace pic

@@ -359,6 +359,77 @@ __global__ void k_spawn_pairs_f32(PartF32 phot, const uint32_t *__restrict__ off
     po_ev[dp] = 0;
 }
 
+// FP64 plain form: absolute positions, event data as 4 doubles per particle
+__global__ void k_spawn_photons_f64(PartF64 parent, const uint32_t *__restrict__ off,
+                                    const uint32_t *__restrict__ total, QedParams q, PartF64 ph, double *ph_tau,
+                                    uint64_t *ph_id, uint32_t *ph_ev, long long *ph_count, long long ph_cap, int dim,
+                                    int *err)
+{
+    const long long p = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    const long long n = *parent.dn;
+    const long long base = *ph_count;
+    if (p == 0 && base + *total > ph_cap) atomicOr(err, ERR_CAPACITY);
+    if (p >= n || !q.ev[p]) return;
+    const long long dst = base + off[p];
+    if (dst >= ph_cap) return;
+    uint32_t w[4];
+    const uint64_t pid = q.id[p];
+    philox4x32_10((uint32_t)pid, (uint32_t)(pid >> 32), q.step, QP_EMIT, q.key[0], q.key[1], w);
+    const uint64_t cid = ((uint64_t)w[3] << 32) | w[2];
+    const double4 e = reinterpret_cast<const double4 *>(q.evk)[p];
+    ph.cell[dst] = parent.cell[p];
+    for (int d = 0; d < dim; d++) ph.x[d][dst] = parent.x[d][p];
+    ph.u[0][dst] = e.x;
+    ph.u[1][dst] = e.y;
+    ph.u[2][dst] = e.z;
+    ph_id[dst] = cid;
+    ph_tau[dst] = initial_tau(cid, q.key);
+    ph_ev[dst] = 0;
+}
+
+__global__ void k_spawn_pairs_f64(PartF64 phot, const uint32_t *__restrict__ off, const uint32_t *__restrict__ total,
+                                  QedParams q, PartF64 el, double *el_tau, uint64_t *el_id, uint32_t *el_ev,
+                                  long long *el_count, long long el_cap, PartF64 po, double *po_tau, uint64_t *po_id,
+                                  uint32_t *po_ev, long long *po_count, long long po_cap, int dim, int *err)
+{
+    const long long p = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    const long long n = *phot.dn;
+    const long long be = *el_count, bp = *po_count;
+    if (p == 0 && (be + *total > el_cap || bp + *total > po_cap)) atomicOr(err, ERR_CAPACITY);
+    if (p >= n || !q.ev[p]) return;
+    const long long de = be + off[p], dp = bp + off[p];
+    if (de >= el_cap || dp >= po_cap) return;
+    uint32_t w[4];
+    const uint64_t pid = q.id[p];
+    philox4x32_10((uint32_t)pid, (uint32_t)(pid >> 32), q.step, QP_PAIR, q.key[0], q.key[1], w);
+    const uint64_t eid = ((uint64_t)w[3] << 32) | w[2], pid2 = eid + 1;
+    const double4 e = reinterpret_cast<const double4 *>(q.evk)[p];
+    const double k = sqrt(e.x * e.x + e.y * e.y + e.z * e.z);
+    const uint32_t cell = phot.cell[p];
+    for (int d = 0; d < dim; d++) {
+        el.x[d][de] = phot.x[d][p];
+        po.x[d][dp] = phot.x[d][p];
+    }
+    el.cell[de] = cell;
+    po.cell[dp] = cell;
+    phot.cell[p] = kDead;
+    const double ep = e.w * k, em = (1.0 - e.w) * k;
+    const double pm = sqrt(fmax(em * em - 1.0, 0.0)), pp = sqrt(fmax(ep * ep - 1.0, 0.0));
+    const double inv = k > 0.0 ? 1.0 / k : 0.0;
+    el.u[0][de] = pm * e.x * inv;
+    el.u[1][de] = pm * e.y * inv;
+    el.u[2][de] = pm * e.z * inv;
+    po.u[0][dp] = pp * e.x * inv;
+    po.u[1][dp] = pp * e.y * inv;
+    po.u[2][dp] = pp * e.z * inv;
+    el_id[de] = eid;
+    po_id[dp] = pid2;
+    el_tau[de] = initial_tau(eid, q.key);
+    po_tau[dp] = initial_tau(pid2, q.key);
+    el_ev[de] = 0;
+    po_ev[dp] = 0;
+}
+
 __global__ void k_add_count(long long *count, const uint32_t *total, long long cap)
 {
     const long long c = *count + *total;
@@ -403,6 +474,30 @@ void launch_spawn_pairs(const PartF32 &phot, const uint32_t *off, const uint32_t
     if (phot.n == 0) return;
     note_launch(3);
     k_spawn_pairs_f32<<<div_up(phot.n, 256), 256, 0, st>>>(phot, off, total, q, el, el_tau, el_id, el_ev, el_count,
+                                                          el_cap, po, po_tau, po_id, po_ev, po_count, po_cap, dim, err);
+    k_add_count<<<1, 1, 0, st>>>(el_count, total, el_cap);
+    k_add_count<<<1, 1, 0, st>>>(po_count, total, po_cap);
+}
+
+void launch_spawn_photons(const PartF64 &parent, const uint32_t *off, const uint32_t *total, const QedParams &q,
+                          const PartF64 &ph, double *ph_tau, uint64_t *ph_id, uint32_t *ph_ev, long long *ph_count,
+                          long long ph_cap, int dim, int *err, cudaStream_t st)
+{
+    if (parent.n == 0) return;
+    note_launch(2);
+    k_spawn_photons_f64<<<div_up(parent.n, 256), 256, 0, st>>>(parent, off, total, q, ph, ph_tau, ph_id, ph_ev,
+                                                              ph_count, ph_cap, dim, err);
+    k_add_count<<<1, 1, 0, st>>>(ph_count, total, ph_cap);
+}
+
+void launch_spawn_pairs(const PartF64 &phot, const uint32_t *off, const uint32_t *total, const QedParams &q,
+                        const PartF64 &el, double *el_tau, uint64_t *el_id, uint32_t *el_ev, long long *el_count,
+                        long long el_cap, const PartF64 &po, double *po_tau, uint64_t *po_id, uint32_t *po_ev,
+                        long long *po_count, long long po_cap, int dim, int *err, cudaStream_t st)
+{
+    if (phot.n == 0) return;
+    note_launch(3);
+    k_spawn_pairs_f64<<<div_up(phot.n, 256), 256, 0, st>>>(phot, off, total, q, el, el_tau, el_id, el_ev, el_count,
                                                           el_cap, po, po_tau, po_id, po_ev, po_count, po_cap, dim, err);
     k_add_count<<<1, 1, 0, st>>>(el_count, total, el_cap);
     k_add_count<<<1, 1, 0, st>>>(po_count, total, po_cap);

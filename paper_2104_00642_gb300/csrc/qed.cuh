@@ -10,6 +10,7 @@
 #pragma once
 #include <cstdint>
 
+#include "mlp.cuh"
 #include "pic_internal.cuh"
 
 namespace pic {
@@ -41,6 +42,8 @@ struct QedParams {
     float *evk;       // event data, 4 floats per particle: photon momentum (and v for pairs)
     double *e_lost;   // energy of photons below emin (tally)
     double wdV;       // weight * cell volume of this species (energy tallies)
+    const MlpImage *net;  // surrogate network of this species' process (nullptr: tables only)
+    MlpNorm nrm;          // its trained chi range and normalisation
 };
 
 // ---------------------------------------------------------------------
@@ -75,7 +78,9 @@ __host__ __device__ inline void philox4x32_10(uint32_t c0, uint32_t c1, uint32_t
 __host__ __device__ inline double uniform24(uint32_t x) { return ((double)(x >> 8) + 0.5) * (1.0 / 16777216.0); }
 
 // counter words 2-3 of the draws: (step, purpose)
-enum QedPurpose : uint32_t { QP_EMIT = 0, QP_PAIR = 1, QP_INIT = 2 };
+// (QP_TRAIN + process: training samples of the surrogate network, with the
+// sample index as counter words 0-1 and the training iteration as word 2)
+enum QedPurpose : uint32_t { QP_EMIT = 0, QP_PAIR = 1, QP_INIT = 2, QP_TRAIN = 3 };
 constexpr uint32_t kInitStep = 0xFFFFFFFFu;
 
 // initial optical depth of a particle with identity id
@@ -99,25 +104,23 @@ __device__ __forceinline__ double chi_of(R g, R ux, R uy, R uz, R ex, R ey, R ez
     return s > 0.0 ? sqrt(s) * inv_Es : 0.0;
 }
 
-// G_p(chi): Catmull-Rom in ln chi on ln G (pairs: on ln G + 8/(3 chi), the
-// exponential small-chi factor removed); below the table the emission rate
-// follows its classical limit (ln G linear in ln chi) and the pair rate is
-// zero; above it both continue linearly in ln chi
 template <typename R>
-__host__ __device__ __forceinline__ double qed_rate(const QedTables &T, int p, double chi)
+__host__ __device__ __forceinline__ const R *qed_lnG_nodes(const QedTables &T, int p)
 {
-    if (!(chi > 0.0)) return 0.0;
-    const R *L = p == 0 ? (const R *)(sizeof(R) == 4 ? (const void *)T.lnG_f[0] : (const void *)T.lnG_d[0])
-                        : (const R *)(sizeof(R) == 4 ? (const void *)T.lnG_f[1] : (const void *)T.lnG_d[1]);
-    const double x = (log(chi) - T.lnchi0) / T.dlnchi;
-    const double sub = p == QED_PAIR ? 8.0 / (3.0 * chi) : 0.0;
-    if (x <= 0.0) {
-        if (p == QED_PAIR) return 0.0;
-        return exp((double)L[0] + x * ((double)L[1] - (double)L[0]));
-    }
+    return p == 0 ? (const R *)(sizeof(R) == 4 ? (const void *)T.lnG_f[0] : (const void *)T.lnG_d[0])
+                  : (const R *)(sizeof(R) == 4 ? (const void *)T.lnG_f[1] : (const void *)T.lnG_d[1]);
+}
+
+// The tabulated ln G (pairs: ln G + 8/(3 chi)) at table coordinate
+// x = (ln chi - lnchi0) / dlnchi > 0: Catmull-Rom inside the table, linear
+// continuation above it
+template <typename R>
+__host__ __device__ __forceinline__ double qed_lnG_table(const QedTables &T, int p, double x)
+{
+    const R *L = qed_lnG_nodes<R>(T, p);
     if (x >= T.nchi - 1) {
         const int n = T.nchi;
-        return exp((double)L[n - 1] + (x - (n - 1)) * ((double)L[n - 1] - (double)L[n - 2]) - sub);
+        return (double)L[n - 1] + (x - (n - 1)) * ((double)L[n - 1] - (double)L[n - 2]);
     }
     int i = (int)x;
     const double t = x - i;
@@ -126,7 +129,25 @@ __host__ __device__ __forceinline__ double qed_rate(const QedTables &T, int p, d
     const double a = -0.5 * p0 + 1.5 * p1 - 1.5 * p2 + 0.5 * p3;
     const double b = p0 - 2.5 * p1 + 2.0 * p2 - 0.5 * p3;
     const double c = -0.5 * p0 + 0.5 * p2;
-    return exp(((a * t + b) * t + c) * t + p1 - sub);
+    return ((a * t + b) * t + c) * t + p1;
+}
+
+// G_p(chi): Catmull-Rom in ln chi on ln G (pairs: on ln G + 8/(3 chi), the
+// exponential small-chi factor removed); below the table the emission rate
+// follows its classical limit (ln G linear in ln chi) and the pair rate is
+// zero; above it both continue linearly in ln chi
+template <typename R>
+__host__ __device__ __forceinline__ double qed_rate(const QedTables &T, int p, double chi)
+{
+    if (!(chi > 0.0)) return 0.0;
+    const double x = (log(chi) - T.lnchi0) / T.dlnchi;
+    const double sub = p == QED_PAIR ? 8.0 / (3.0 * chi) : 0.0;
+    if (x <= 0.0) {
+        if (p == QED_PAIR) return 0.0;
+        const R *L = qed_lnG_nodes<R>(T, p);
+        return exp((double)L[0] + x * ((double)L[1] - (double)L[0]));
+    }
+    return exp(qed_lnG_table<R>(T, p, x) - sub);
 }
 
 // fraction (u for emission, v for pairs) with CDF = r: bilinear in
@@ -157,6 +178,31 @@ __host__ __device__ __forceinline__ double qed_sample(const QedTables &T, int p,
     const double s = (1.0 - tx) * s0 + tx * s1;
     const double f = s * s * s;
     return flip ? 1.0 - f : f;
+}
+
+// --- surrogate network in place of the tables (trained chi range) ---
+__device__ __forceinline__ bool mlp_in_range(const MlpNorm &n, double chi, double &lnchi)
+{
+    lnchi = chi > 0.0 ? log(chi) : -1e300;
+    return lnchi >= n.lnchi_lo && lnchi <= n.lnchi_hi;
+}
+// network inputs for (ln chi, r)
+__device__ __forceinline__ void mlp_inputs(const MlpNorm &n, int p, double lnchi, double r, float &x0, float &x1)
+{
+    x0 = fmaf(n.x0a, (float)lnchi, n.x0b);
+    x1 = (float)mlp_rcoord(p, r);
+}
+// G from the rate output y1
+__device__ __forceinline__ double mlp_rate(const MlpNorm &n, int p, double chi, float y1)
+{
+    return exp((double)fmaf(n.sd, y1, n.mu) - (p == QED_PAIR ? 8.0 / (3.0 * chi) : 0.0));
+}
+// energy fraction from the sample output y0 at CDF r
+__device__ __forceinline__ double mlp_fraction(int p, float y0, double r)
+{
+    // pairs: the network's v is that of min(r, 1 - r), at most 1/2
+    const double s = fmin(fmax((double)y0, 0.0), p == QED_PAIR ? 0.7937005259840998 : 1.0), f = s * s * s;
+    return p == QED_PAIR && r > 0.5 ? 1.0 - f : f;
 }
 
 }  // namespace pic

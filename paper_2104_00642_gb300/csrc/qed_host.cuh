@@ -19,6 +19,17 @@ void launch_spawn_pairs(const PartF32 &phot, const uint32_t *off, const uint32_t
                         const PartF32 &el, double *el_tau, uint64_t *el_id, uint32_t *el_ev, long long *el_count,
                         long long el_cap, const PartF32 &po, double *po_tau, uint64_t *po_id, uint32_t *po_ev,
                         long long *po_count, long long po_cap, int dim, int *err, cudaStream_t st);
+void launch_spawn_photons(const PartF64 &parent, const uint32_t *off, const uint32_t *total, const QedParams &q,
+                          const PartF64 &ph, double *ph_tau, uint64_t *ph_id, uint32_t *ph_ev, long long *ph_count,
+                          long long ph_cap, int dim, int *err, cudaStream_t st);
+void launch_spawn_pairs(const PartF64 &phot, const uint32_t *off, const uint32_t *total, const QedParams &q,
+                        const PartF64 &el, double *el_tau, uint64_t *el_id, uint32_t *el_ev, long long *el_count,
+                        long long el_cap, const PartF64 &po, double *po_tau, uint64_t *po_id, uint32_t *po_ev,
+                        long long *po_count, long long po_cap, int dim, int *err, cudaStream_t st);
+void launch_push_qed_f64(const PartF64 &P, double *F, const Grid &g, const PushConst &pc, const QedParams &q,
+                         int *err, double *e_abs, cudaStream_t st);
+void launch_push_photon_f64(const PartF64 &P, const double *F, const Grid &g, const PushConst &pc,
+                            const QedParams &q, int *err, cudaStream_t st);
 void launch_push_qed_f32(const PartF32 &P, float *F, const Grid &g, const PushConst &pc, const QedParams &q,
                          int *err, double *e_abs, cudaStream_t st);
 void launch_push_photon_f32(const PartF32 &P, const float *F, const Grid &g, const PushConst &pc,

@@ -283,6 +283,10 @@ __global__ void k_permute_f64(PartF64 src, PartF64 dst, const uint32_t *__restri
     dst.u[0][i] = src.u[0][a];
     dst.u[1][i] = src.u[1][a];
     dst.u[2][i] = src.u[2][a];
+    if (src.tau) {
+        dst.tau[i] = src.tau[a];
+        dst.id[i] = src.id[a];
+    }
 }
 
 void launch_permute_f32(const PartF32 &src, const PartF32 &dst, const uint32_t *perm, const long long *dcount,

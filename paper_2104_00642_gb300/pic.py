@@ -31,9 +31,11 @@ MAX_SPECIES = 8
 EXPORTS = ["pic_create", "pic_destroy", "pic_last_error", "pic_load_particles", "pic_set_laser",
            "pic_set_field", "pic_step", "pic_fields", "pic_particle_count", "pic_get_particles",
            "pic_get_cells", "pic_diagnostics", "pic_gather", "pic_sync", "pic_profile", "pic_profile_read",
-           "pic_field_energy_noalloc", "pic_set_qed", "pic_qed_eval", "pic_get_qed_state"]
+           "pic_field_energy_noalloc", "pic_set_qed", "pic_qed_eval", "pic_get_qed_state", "pic_mlp_train",
+           "pic_mlp_validate", "pic_mlp_get", "pic_mlp_set", "pic_mlp_eval", "pic_mlp_grad"]
 KIND_MASSIVE, KIND_PHOTON = 0, 1
-QED_OFF, QED_TABLE = 0, 1
+QED_OFF, QED_TABLE, QED_SURROGATE = 0, 1, 2
+MLP_NPARAMS = 8642
 QED_EMISSION, QED_PAIR = 0, 1
 PHASES = ("sort", "fields", "push", "fold")
 
@@ -73,6 +75,26 @@ class pic_diag(C.Structure):
     _fields_ = [("step", C.c_int64), ("t", C.c_double), ("U_E", C.c_double), ("U_B", C.c_double),
                 ("U_kin", C.c_double * MAX_SPECIES), ("charge", C.c_double), ("gauss_max", C.c_double),
                 ("E_absorbed", C.c_double), ("n_alive", C.c_int64 * MAX_SPECIES), ("E_photon_lost", C.c_double)]
+
+
+class pic_mlp_train_opts(C.Structure):
+    _fields_ = [("iterations", C.c_int64), ("batch", C.c_int64), ("lr", C.c_double), ("lr_final", C.c_double),
+                ("chi_min", C.c_double), ("chi_max", C.c_double), ("rate_weight", C.c_double),
+                ("seed", C.c_uint64), ("keep", C.c_int)]
+
+
+class pic_mlp_report(C.Structure):
+    _fields_ = [("loss", C.c_double), ("max_err_lnG", C.c_double), ("max_err_s", C.c_double),
+                ("rms_err_s", C.c_double), ("ms", C.c_double), ("iterations", C.c_int64),
+                ("table_bytes", C.c_int64), ("net_bytes", C.c_int64)]
+
+
+class pic_mlp_info(C.Structure):
+    _fields_ = [("chi_min", C.c_double), ("chi_max", C.c_double), ("mu", C.c_double), ("sd", C.c_double)]
+
+
+def _report(r):
+    return {k: getattr(r, k) for k, _ in pic_mlp_report._fields_}
 
 
 _lib = None
@@ -128,6 +150,14 @@ def load_library(path: str = LIB_PATH):
     L.pic_qed_eval.restype = I
     L.pic_get_qed_state.argtypes = [P, I, I64, P, P]
     L.pic_get_qed_state.restype = I
+    L.pic_mlp_train.argtypes = [P, I, C.POINTER(pic_mlp_train_opts), C.POINTER(pic_mlp_report)]
+    L.pic_mlp_validate.argtypes = [P, I, C.POINTER(pic_mlp_report)]
+    L.pic_mlp_get.argtypes = [P, I, P, C.POINTER(pic_mlp_info)]
+    L.pic_mlp_set.argtypes = [P, I, P, C.POINTER(pic_mlp_info)]
+    L.pic_mlp_eval.argtypes = [P, I, I64, P, P]
+    L.pic_mlp_grad.argtypes = [P, I, I64, P, P, P, C.POINTER(D)]
+    for name in ("pic_mlp_train", "pic_mlp_validate", "pic_mlp_get", "pic_mlp_set", "pic_mlp_eval", "pic_mlp_grad"):
+        getattr(L, name).restype = I
     _lib = L
     return L
 
@@ -293,6 +323,47 @@ class Sim:
         self._check(load_library().pic_qed_eval(self._h, int(process), len(chi), _p(chi), _p(rr), _p(out)))
         return out
 
+    def pic_mlp_train(self, process, iterations=0, batch=0, lr=0.0, lr_final=0.0, chi_min=0.0, chi_max=0.0,
+                      rate_weight=0.0, seed=0, keep=False):
+        o = pic_mlp_train_opts(int(iterations), int(batch), float(lr), float(lr_final), float(chi_min),
+                               float(chi_max), float(rate_weight), int(seed) & 0xFFFFFFFFFFFFFFFF, int(bool(keep)))
+        r = pic_mlp_report()
+        self._check(load_library().pic_mlp_train(self._h, int(process), C.byref(o), C.byref(r)))
+        return _report(r)
+
+    def pic_mlp_validate(self, process):
+        r = pic_mlp_report()
+        self._check(load_library().pic_mlp_validate(self._h, int(process), C.byref(r)))
+        return _report(r)
+
+    def pic_mlp_get(self, process):
+        P = np.zeros(MLP_NPARAMS, dtype=np.float32)
+        info = pic_mlp_info()
+        self._check(load_library().pic_mlp_get(self._h, int(process), _p(P), C.byref(info)))
+        return P, {k: getattr(info, k) for k, _ in pic_mlp_info._fields_}
+
+    def pic_mlp_set(self, process, params, chi_min, chi_max, mu, sd):
+        P = np.ascontiguousarray(params, dtype=np.float32)
+        if P.size != MLP_NPARAMS:
+            raise ValueError("pic_mlp_set: wrong parameter count")
+        info = pic_mlp_info(float(chi_min), float(chi_max), float(mu), float(sd))
+        self._check(load_library().pic_mlp_set(self._h, int(process), _p(P), C.byref(info)))
+
+    def pic_mlp_eval(self, process, x):
+        X = np.ascontiguousarray(np.asarray(x, dtype=np.float32).reshape(-1, 2))
+        Y = np.zeros_like(X)
+        self._check(load_library().pic_mlp_eval(self._h, int(process), X.shape[0], _p(X), _p(Y)))
+        return Y
+
+    def pic_mlp_grad(self, process, x, t):
+        X = np.ascontiguousarray(np.asarray(x, dtype=np.float32).reshape(-1, 2))
+        T = np.ascontiguousarray(np.asarray(t, dtype=np.float32).reshape(-1, 2))
+        G = np.zeros(MLP_NPARAMS, dtype=np.float32)
+        loss = C.c_double(0.0)
+        self._check(load_library().pic_mlp_grad(self._h, int(process), X.shape[0], _p(X), _p(T), _p(G),
+                                                C.byref(loss)))
+        return loss.value, G
+
     def pic_get_qed_state(self, sp):
         n = self.pic_particle_count(sp)
         ids = np.zeros(max(n, 1), dtype=np.uint64)
@@ -321,16 +392,21 @@ def pic_create(dim, n, dx, dt, species, **kw) -> Sim:
 
 
 def from_workload(w, precision=FP32_CELLOFF, sort_interval=0, capacity_scale=1.0, load=True, stream=None,
-                  tile=None, push_variant=0) -> Sim:
-    """Create a simulation for a :class:`workloads.Workload` and load its particles."""
-    sp = [(s.q, s.m, s.w, max(1, int(s.capacity * capacity_scale))) for s in w.species]
+                  tile=None, push_variant=0, seed=0) -> Sim:
+    """Create a simulation for a :class:`workloads.Workload` and load its particles
+    (QED workloads: the Monte Carlo is configured in table mode first)."""
+    sp = [(s.q, s.m, s.w, max(1, int(s.capacity * capacity_scale)), s.kind, s.qed) for s in w.species]
     t = tile if tile is not None else tuple(w.tile)
     sim = Sim(w.dim, w.n, w.dx, w.dt, sp, bc=w.bc, precision=precision, sort_interval=sort_interval, tile=t,
-              rho_bg=w.rho_bg, stream=stream, push_variant=push_variant)
+              rho_bg=w.rho_bg, stream=stream, push_variant=push_variant, seed=seed)
     if w.laser is not None:
         L = w.laser
         sim.pic_set_laser(L.a0, L.waist, L.fwhm, L.t_peak, L.x_focus, L.yc, L.zc, L.pol)
+    if w.qed is not None:
+        sim.pic_set_qed(mode=QED_TABLE, **w.qed)
     if load:
         for i, s in enumerate(w.species):
-            sim.pic_load_particles(i, s.x, s.y if w.dim > 1 else None, s.z if w.dim > 2 else None, s.ux, s.uy, s.uz)
+            if s.n:
+                sim.pic_load_particles(i, s.x, s.y if w.dim > 1 else None, s.z if w.dim > 2 else None, s.ux, s.uy,
+                                       s.uz)
     return sim

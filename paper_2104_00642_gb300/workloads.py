@@ -15,6 +15,8 @@ c/omega_r, density in n_r.  Workloads:
   entering from x-min; absorbing x, periodic y (omega_r = omega_L).
 * ``thermal_3d``: uniform Maxwellian electrons on a neutralising background,
   3D periodic (omega_r = omega_p).
+* ``qed_collision_2d``: a GeV electron beam against an a0 = 200 laser, with
+  photon emission and pair creation (Sec. IV; omega_r = omega_L).
 """
 from __future__ import annotations
 
@@ -42,6 +44,8 @@ class Species:
     uy: np.ndarray
     uz: np.ndarray
     capacity: int = 0
+    kind: int = 0  # 0 massive, 1 photon
+    qed: int = 0   # 1: takes part in the QED Monte Carlo
 
     @property
     def n(self) -> int:
@@ -74,6 +78,8 @@ class Workload:
     laser: Laser | None = None
     tile: tuple = (8, 8, 8)
     notes: dict = field(default_factory=dict)
+    # QED Monte Carlo: species indices, reference wavelength (m), photon_emin
+    qed: dict | None = None
 
     @property
     def n_particles(self) -> int:
@@ -186,6 +192,55 @@ def laser_foil_2d(nx=2048, ny=1024, cells_per_lambda=64, slab=(1024, 1088), n0=1
     return Workload("laser_foil_2d", 2, (nx, ny, 1), (dx, dx, 1.0), dt, (ABSORB, PERIODIC, PERIODIC),
                     species, steps, laser=laser, tile=tile,
                     notes={"theta": theta, "n0": n0, "ppc": ppc, "slab": slab})
+
+
+def qed_collision_2d(nx=2048, ny=512, cells_per_lambda=32, n_beam=10_000_000, gamma0=1957.0, spread=0.01,
+                     sigma_um=1.0, a0=200.0, waist_um=2.0, fwhm_fs=15.0, x_focus_um=6.5, n_peak=0.01,
+                     photon_cap=16.0, pair_cap=0.5, photon_emin=2.0, steps=3000, courant=0.95, seed=SEED0 + 7,
+                     tile=(16, 16, 1)):
+    """Strong-field QED collision (2D3V): a linearly polarised Gaussian laser
+    of amplitude a0 enters from x-min and focuses at x_focus; an electron beam
+    (Gaussian, sigma in x and y, gamma0 with a relative rms spread, moving
+    along -x) is placed so that its centre meets the pulse peak at the focus.
+    Species: electrons (beam, QED), positrons (QED), photons.  The beam's
+    peak density is n_peak (weight from the macro count); emitted photons
+    below photon_emin (m c^2) are tallied, not kept.  Lengths: lambda = 1 um."""
+    rng = _rng(seed)
+    dx = 2.0 * math.pi / cells_per_lambda
+    dt = courant * dx / math.sqrt(2.0)
+    lam = 2.0 * math.pi
+    sig = sigma_um * lam
+    omega_L = 2.0 * math.pi * 2.99792458e8 / 1.0e-6
+    fwhm = fwhm_fs * 1e-15 * omega_L
+    t_peak = 2.5 * fwhm
+    xf = x_focus_um * lam
+    yc = 0.5 * ny * dx
+    # the pulse peak reaches x_f at t_peak + x_f; the beam centre (speed ~ 1)
+    # starts at 2 x_f + t_peak to be there at that time
+    xb = 2.0 * xf + t_peak
+    x = rng.normal(xb, sig, n_beam)
+    y = rng.normal(yc, sig, n_beam)
+    x = np.clip(x, 0.5 * dx, (nx - 0.5) * dx)
+    y = np.mod(y, ny * dx)
+    g = gamma0 * (1.0 + spread * rng.standard_normal(n_beam))
+    ux = -np.sqrt(g * g - 1.0)
+    zero = np.zeros(n_beam)
+    core = n_beam * dx * dx / (2.0 * math.pi * sig * sig)  # macro-particles per cell at the peak
+    w = n_peak / core
+    e = Species("electron", -1.0, 1.0, w, x, y, zero, ux, zero.copy(), zero.copy(),
+                capacity=int(n_beam * (1.0 + pair_cap)), qed=1)
+    emp = np.zeros(0)
+    npair = int(n_beam * pair_cap)
+    po = Species("positron", 1.0, 1.0, w, emp, emp, emp, emp, emp, emp, capacity=max(npair, 1), qed=1)
+    ph = Species("photon", 0.0, 0.0, w, emp, emp, emp, emp, emp, emp, capacity=int(n_beam * photon_cap), kind=1)
+    laser = Laser(a0=a0, waist=waist_um * lam, fwhm=fwhm, t_peak=t_peak, x_focus=xf, yc=yc)
+    t_collide = t_peak + xf
+    return Workload("qed_collision_2d", 2, (nx, ny, 1), (dx, dx, 1.0), dt, (ABSORB, PERIODIC, PERIODIC),
+                    [e, po, ph], steps, laser=laser, tile=tile,
+                    notes={"t_collide": t_collide, "steps_to_collision": int(t_collide / dt), "w": w,
+                           "beam_x0": xb, "peak_macros_per_cell": core},
+                    qed={"photon_sp": 2, "electron_sp": 0, "positron_sp": 1, "lambda_r_m": 1e-6,
+                         "photon_emin": photon_emin})
 
 
 def vacuum_pulse_1d(n_cells=1024, cells_per_lambda=32, a0=1.0, fwhm=4.0 * 2.0 * math.pi, steps=1500,

@@ -97,3 +97,30 @@ def test_monte_carlo_matches_oracle_event_by_event():
     # energy conservation of the whole ensemble (FP32 particles)
     e1 = Q.total_energy(s.pic_get_particles(0), s.pic_get_particles(1), s.pic_get_particles(2))
     assert abs(e1 - e0) <= 2e-5 * e0
+
+
+def test_monte_carlo_fp64_form_matches_oracle():
+    """The plain FP64 form (absolute positions, FP64 tables) against the
+    oracle: the same events with the same photon energies, tighter than the
+    FP32 form, and energy conserved to FP64 round-off."""
+    o = Q.make_oracle()
+    s = pic.pic_create(1, (16,), (1.0,), Q.DT, Q.species_spec(), seed=Q.SEED, precision=pic.FP64_PLAIN)
+    s.pic_set_qed(photon_sp=2, electron_sp=0, positron_sp=1, lambda_r_m=Q.LAMBDA)
+    s.pic_set_field(pic.BZ, np.full(s.box(), Q.B0))
+    s.pic_load_particles(0, *Q.electrons())
+    e0 = Q.total_energy(s.pic_get_particles(0), s.pic_get_particles(1), s.pic_get_particles(2))
+    s.pic_step(25)
+    o.step(25)
+    gid, gtau = s.pic_get_qed_state(2)
+    oid, otau = o.qed_state(2)
+    common = np.intersect1d(gid, oid)
+    assert len(oid) > 30 and len(gid) - len(common) <= 2 and len(oid) - len(common) <= 2, (len(gid), len(oid))
+    gk, ok = s.pic_get_particles(2), o.particles(2)
+    ge = dict(zip(gid.tolist(), np.sqrt(gk["ux"] ** 2 + gk["uy"] ** 2 + gk["uz"] ** 2).tolist()))
+    oe = dict(zip(oid.tolist(), np.sqrt(ok["ux"] ** 2 + ok["uy"] ** 2 + ok["uz"] ** 2).tolist()))
+    rel = np.array([abs(ge[i] / oe[i] - 1.0) for i in common.tolist()])
+    assert np.median(rel) < 1e-4 and np.max(rel) < 5e-2, (np.median(rel), np.max(rel))
+    e1 = Q.total_energy(s.pic_get_particles(0), s.pic_get_particles(1), s.pic_get_particles(2))
+    assert abs(e1 - e0) <= 1e-9 * e0
+    d = s.pic_diagnostics()  # converted photons stay in the arrays, dead, until the next sort
+    assert d["n_alive"][2] == int(gk["alive"].sum()) and d["U_kin"][2] > 0.0
