@@ -174,16 +174,17 @@ __global__ void __launch_bounds__(128) k_mlp_bwd(const MlpImage *img, long long 
 #pragma unroll
     for (int sh = 16; sh > 0; sh >>= 1) lsum += __shfl_xor_sync(0xffffffffu, lsum, sh);
     if (lane == 0) atomicAdd(loss, lsum);
-    // D2 = (D3 W2) * silu'(z2), D1 = (D2 W1) * silu'(z1), on the tensor cores
-    uint32_t A[2][4][4];
-    float acc[2][8][4];
-    auto ident = [](float v, int, int) { return v; };
+    // D2 = (D3 W2) * silu'(z2), D1 = (D2 W1) * silu'(z1), on the tensor
+    // cores, one m-tile at a time
+    uint32_t A[4][4];
+    float acc[8][4];
+    auto ident = [](float v) { return v; };
 #pragma unroll
-    for (int l = 1; l >= 0; l--) {
-        mlp_repack(d, A, ident);
-        mlp_layer(l == 1 ? S.W2T : S.W1T, nullptr, A, acc);
+    for (int m = 0; m < 2; m++)
 #pragma unroll
-        for (int m = 0; m < 2; m++)
+        for (int l = 1; l >= 0; l--) {
+            mlp_repack(d[m], A, ident);
+            mlp_layer(l == 1 ? S.W2T : S.W1T, nullptr, A, acc);
 #pragma unroll
             for (int nt = 0; nt < 8; nt++)
 #pragma unroll
@@ -191,12 +192,12 @@ __global__ void __launch_bounds__(128) k_mlp_bwd(const MlpImage *img, long long 
                     const long long row = quad_row(row0, 2 * m + h, g);
                     const int c = 8 * nt + 2 * t;
                     const float2 z = *reinterpret_cast<const float2 *>(&Z.z[l][row * kMlpH + c]);
-                    d[m][nt][2 * h] = acc[m][nt][2 * h] * dsilu(z.x);
-                    d[m][nt][2 * h + 1] = acc[m][nt][2 * h + 1] * dsilu(z.y);
+                    d[m][nt][2 * h] = acc[nt][2 * h] * dsilu(z.x);
+                    d[m][nt][2 * h + 1] = acc[nt][2 * h + 1] * dsilu(z.y);
                     *reinterpret_cast<float2 *>(&D.z[l][row * kMlpH + c]) =
                         make_float2(d[m][nt][2 * h], d[m][nt][2 * h + 1]);
                 }
-    }
+        }
 }
 
 // dW_l[j][k] = sum_rows D_{l+1}[row][j] in_l[row][k], db_l[j] = sum_rows D;

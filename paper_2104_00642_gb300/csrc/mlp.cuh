@@ -98,35 +98,32 @@ __device__ __forceinline__ void mma_bf16(float (&d)[4], const uint32_t (&a)[4], 
         : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b0), "r"(b1));
 }
 
-// One 64 x 64 layer for the warp's 32 rows: acc[m][nt] = bias + A[m] . W^T
-// (W rows = output features, bf16 pairs at pitch kMlpPitch; b == nullptr:
-// no bias).
+// One 64 x 64 layer for one m-tile (16 rows) of the warp:
+// acc[nt] = bias + A . W^T (W rows = output features, bf16 pairs at pitch
+// kMlpPitch; b == nullptr: no bias).
 // Fragment layout (m16n8k16, g = lane/4, t = lane%4): A k-tile kt holds
 // rows g / g+8 at columns 16kt + 2t (+1) and 16kt + 8 + 2t (+1); the
 // accumulator of n-tile nt holds rows g / g+8 at columns 8nt + 2t (+1).
-__device__ __forceinline__ void mlp_layer(const uint32_t *W, const float *b, const uint32_t (&A)[2][4][4],
-                                          float (&acc)[2][8][4])
+// The warp's two m-tiles go through the network one after the other, so
+// that only one tile's fragments (48 registers) are live at a time.
+__device__ __forceinline__ void mlp_layer(const uint32_t *W, const float *b, const uint32_t (&A)[4][4],
+                                          float (&acc)[8][4])
 {
     const int lane = threadIdx.x & 31, g = lane >> 2, t = lane & 3;
 #pragma unroll
     for (int nt = 0; nt < 8; nt++) {
         const float c0 = b ? b[8 * nt + 2 * t] : 0.f, c1 = b ? b[8 * nt + 2 * t + 1] : 0.f;
-#pragma unroll
-        for (int m = 0; m < 2; m++) {
-            acc[m][nt][0] = c0;
-            acc[m][nt][1] = c1;
-            acc[m][nt][2] = c0;
-            acc[m][nt][3] = c1;
-        }
+        acc[nt][0] = c0;
+        acc[nt][1] = c1;
+        acc[nt][2] = c0;
+        acc[nt][3] = c1;
     }
 #pragma unroll
     for (int kt = 0; kt < 4; kt++) {
 #pragma unroll
         for (int nt = 0; nt < 8; nt++) {
             const uint32_t *w = W + (8 * nt + g) * kMlpPitch + 8 * kt + t;
-            const uint32_t b0 = w[0], b1 = w[4];
-            mma_bf16(acc[0][nt], A[0][kt], b0, b1);
-            mma_bf16(acc[1][nt], A[1][kt], b0, b1);
+            mma_bf16(acc[nt], A[kt], w[0], w[4]);
         }
     }
 }
@@ -134,18 +131,16 @@ __device__ __forceinline__ void mlp_layer(const uint32_t *W, const float *b, con
 // accumulator fragments of n-tiles 2kt, 2kt+1 -> A fragment of k-tile kt,
 // with f applied elementwise (SiLU, or the identity for deltas)
 template <typename Fn>
-__device__ __forceinline__ void mlp_repack(const float (&acc)[2][8][4], uint32_t (&A)[2][4][4], Fn f)
+__device__ __forceinline__ void mlp_repack(const float (&acc)[8][4], uint32_t (&A)[4][4], Fn f)
 {
 #pragma unroll
-    for (int m = 0; m < 2; m++)
-#pragma unroll
-        for (int kt = 0; kt < 4; kt++) {
-            const float *lo = acc[m][2 * kt], *hi = acc[m][2 * kt + 1];
-            A[m][kt][0] = pack_bf16(f(lo[0], 0, 2 * kt), f(lo[1], 1, 2 * kt));
-            A[m][kt][1] = pack_bf16(f(lo[2], 2, 2 * kt), f(lo[3], 3, 2 * kt));
-            A[m][kt][2] = pack_bf16(f(hi[0], 0, 2 * kt + 1), f(hi[1], 1, 2 * kt + 1));
-            A[m][kt][3] = pack_bf16(f(hi[2], 2, 2 * kt + 1), f(hi[3], 3, 2 * kt + 1));
-        }
+    for (int kt = 0; kt < 4; kt++) {
+        const float *lo = acc[2 * kt], *hi = acc[2 * kt + 1];
+        A[kt][0] = pack_bf16(f(lo[0]), f(lo[1]));
+        A[kt][1] = pack_bf16(f(lo[2]), f(lo[3]));
+        A[kt][2] = pack_bf16(f(hi[0]), f(hi[1]));
+        A[kt][3] = pack_bf16(f(hi[2]), f(hi[3]));
+    }
 }
 
 // Forward pass of the warp's 32 rows.  Row index within the warp:
@@ -158,60 +153,69 @@ __device__ __forceinline__ void mlp_forward_rows(const MlpImage &S, const float 
                                                  MlpZ Z = MlpZ{}, long long row0 = 0)
 {
     const int lane = threadIdx.x & 31, g = lane >> 2, t = lane & 3;
-    uint32_t A[2][4][4];
-    float acc[2][8][4];
-    // input layer in FP32 on the CUDA cores
+    float ps[4][2];
 #pragma unroll
-    for (int nt = 0; nt < 8; nt++) {
-        const int c = 8 * nt + 2 * t;
-        const float w00 = S.W0[2 * c], w01 = S.W0[2 * c + 1], w10 = S.W0[2 * c + 2], w11 = S.W0[2 * c + 3];
-        const float c0 = S.b0[c], c1 = S.b0[c + 1];
+    for (int r = 0; r < 4; r++) ps[r][0] = ps[r][1] = 0.f;
+#pragma unroll 1
+    for (int m = 0; m < 2; m++) {
+        uint32_t A[4][4];
+        float acc[8][4];
+        const float xm[2][2] = {{m ? x[2][0] : x[0][0], m ? x[2][1] : x[0][1]},
+                                {m ? x[3][0] : x[1][0], m ? x[3][1] : x[1][1]}};
+        // input layer in FP32 on the CUDA cores
 #pragma unroll
-        for (int m = 0; m < 2; m++)
+        for (int nt = 0; nt < 8; nt++) {
+            const int c = 8 * nt + 2 * t;
+            const float w00 = S.W0[2 * c], w01 = S.W0[2 * c + 1], w10 = S.W0[2 * c + 2], w11 = S.W0[2 * c + 3];
+            const float c0 = S.b0[c], c1 = S.b0[c + 1];
 #pragma unroll
             for (int h = 0; h < 2; h++) {
-                const float *xr = x[2 * m + h];
-                acc[m][nt][2 * h] = fmaf(w01, xr[1], fmaf(w00, xr[0], c0));
-                acc[m][nt][2 * h + 1] = fmaf(w11, xr[1], fmaf(w10, xr[0], c1));
+                acc[nt][2 * h] = fmaf(w01, xm[h][1], fmaf(w00, xm[h][0], c0));
+                acc[nt][2 * h + 1] = fmaf(w11, xm[h][1], fmaf(w10, xm[h][0], c1));
             }
-    }
-    auto store = [&](int l) {
-        if constexpr (STORE) {
-#pragma unroll
-            for (int m = 0; m < 2; m++)
+        }
+        auto store = [&](int l) {
+            if constexpr (STORE) {
 #pragma unroll
                 for (int nt = 0; nt < 8; nt++)
 #pragma unroll
                     for (int h = 0; h < 2; h++) {
                         const long long row = row0 + 16 * m + 8 * h + g;
                         *reinterpret_cast<float2 *>(&Z.z[l][row * kMlpH + 8 * nt + 2 * t]) =
-                            make_float2(acc[m][nt][2 * h], acc[m][nt][2 * h + 1]);
+                            make_float2(acc[nt][2 * h], acc[nt][2 * h + 1]);
                     }
-        }
-    };
-    auto act = [](float z, int, int) { return silu(z); };
-    store(0);
-    mlp_repack(acc, A, act);
-    mlp_layer(S.W1, S.b1, A, acc);
-    store(1);
-    mlp_repack(acc, A, act);
-    mlp_layer(S.W2, S.b2, A, acc);
-    store(2);
-    // head in FP32
-    float ps[4][2];
-#pragma unroll
-    for (int r = 0; r < 4; r++) ps[r][0] = ps[r][1] = 0.f;
-#pragma unroll
-    for (int m = 0; m < 2; m++)
+            }
+        };
+        auto act = [](float z) { return silu(z); };
+        store(0);
+        mlp_repack(acc, A, act);
+        mlp_layer(S.W1, S.b1, A, acc);
+        store(1);
+        mlp_repack(acc, A, act);
+        mlp_layer(S.W2, S.b2, A, acc);
+        store(2);
+        // head in FP32
+        float p[2][2] = {{0.f, 0.f}, {0.f, 0.f}};
 #pragma unroll
         for (int nt = 0; nt < 8; nt++)
 #pragma unroll
             for (int e = 0; e < 4; e++) {
-                const int c = 8 * nt + 2 * t + (e & 1), r = 2 * m + (e >> 1);
-                const float a = silu(acc[m][nt][e]);
-                ps[r][0] = fmaf(a, S.W3[c], ps[r][0]);
-                ps[r][1] = fmaf(a, S.W3[kMlpH + c], ps[r][1]);
+                const int c = 8 * nt + 2 * t + (e & 1), h = e >> 1;
+                const float a = silu(acc[nt][e]);
+                p[h][0] = fmaf(a, S.W3[c], p[h][0]);
+                p[h][1] = fmaf(a, S.W3[kMlpH + c], p[h][1]);
             }
+#pragma unroll
+        for (int h = 0; h < 2; h++) {
+            if (m) {
+                ps[2 + h][0] = p[h][0];
+                ps[2 + h][1] = p[h][1];
+            } else {
+                ps[h][0] = p[h][0];
+                ps[h][1] = p[h][1];
+            }
+        }
+    }
 #pragma unroll
     for (int r = 0; r < 4; r++)
 #pragma unroll

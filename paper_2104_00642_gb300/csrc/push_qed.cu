@@ -23,7 +23,7 @@ namespace pic {
 // single evaluation yields both the rate and, if the event happens, the
 // energy fraction.
 template <int DIM, bool SURR>
-__global__ void __launch_bounds__(256) k_push_qed_f32(PartF32 P, float *__restrict__ F, Grid g, PushConst pc,
+__global__ void __launch_bounds__(256, SURR ? 2 : 1) k_push_qed_f32(PartF32 P, float *__restrict__ F, Grid g, PushConst pc,
                                                       QedParams q, int *err, double *e_abs)
 {
     extern __shared__ __align__(16) unsigned char smem[];
@@ -69,21 +69,23 @@ __global__ void __launch_bounds__(256) k_push_qed_f32(PartF32 P, float *__restri
     uint32_t event = 0;
     float4 evd = make_float4(0.f, 0.f, 0.f, 0.f);
     if (q.on) {
+        // chi and the rate in FP32, gamma in FP64 above 1e4, tau in FP64
+        const float uuf = ux * ux + uy * uy + uz * uz;
         const double uu = (double)ux * ux + (double)uy * uy + (double)uz * uz;
-        const double gam = sqrt(1.0 + uu);
-        const double chi = chi_of<float>((float)gam, ux, uy, uz, eb[0], eb[1], eb[2], eb[3], eb[4], eb[5], q.inv_Es);
+        const double gam = uuf > 1e8f ? sqrt(1.0 + uu) : (double)sqrtf(1.0f + uuf);
+        const float chi = chi_f32((float)gam, ux, uy, uz, eb[0], eb[1], eb[2], eb[3], eb[4], eb[5], (float)q.inv_Es);
         uint32_t w[4];
         bool use_net = false;
         float y0 = 0.f, y1 = 0.f;
         if constexpr (SURR) {
-            double lnchi;
-            const bool inr = live && mlp_in_range(q.nrm, chi, lnchi);
+            float lnchi;
+            const bool inr = live && mlp_in_range_f32(q.nrm, chi, lnchi);
             if (__any_sync(0xffffffffu, inr)) {
                 float x0 = 0.f, x1 = 0.f;
                 if (inr) {
                     const uint64_t id = q.id[p];
                     philox4x32_10((uint32_t)id, (uint32_t)(id >> 32), q.step, QP_EMIT, q.key[0], q.key[1], w);
-                    mlp_inputs(q.nrm, QED_RAD, lnchi, uniform24(w[0]), x0, x1);
+                    mlp_inputs_f32(q.nrm, QED_RAD, lnchi, (float)uniform24(w[0]), x0, x1);
                 }
                 mlp_eval_warp(*reinterpret_cast<const MlpImage *>(smem), x0, x1, y0, y1);
                 use_net = inr;
@@ -93,8 +95,8 @@ __global__ void __launch_bounds__(256) k_push_qed_f32(PartF32 P, float *__restri
                 return;
             }
         }
-        const double G = use_net ? mlp_rate(q.nrm, QED_RAD, chi, y1) : qed_rate<float>(q.T, QED_RAD, chi);
-        double tau = q.tau[p] - q.pref * G / gam;
+        const float G = use_net ? mlp_rate_f32(q.nrm, QED_RAD, chi, y1) : qed_rate_f32(q.T, QED_RAD, chi);
+        double tau = q.tau[p] - (double)((float)q.pref * G / (float)gam);
         if (tau <= 0.0) {
             if (!use_net) {
                 const uint64_t id = q.id[p];
@@ -183,7 +185,7 @@ __global__ void __launch_bounds__(256) k_push_qed_f32(PartF32 P, float *__restri
 
 // SURR: the pair network inside its chi range, as in k_push_qed_f32
 template <int DIM, bool SURR>
-__global__ void __launch_bounds__(256) k_push_photon_f32(PartF32 P, const float *__restrict__ F, Grid g, PushConst pc,
+__global__ void __launch_bounds__(256, SURR ? 2 : 1) k_push_photon_f32(PartF32 P, const float *__restrict__ F, Grid g, PushConst pc,
                                                          QedParams q, int *err)
 {
     extern __shared__ __align__(16) unsigned char smem[];
@@ -225,19 +227,19 @@ __global__ void __launch_bounds__(256) k_push_photon_f32(PartF32 P, const float 
         for (int d = 0; d < DIM; d++) axis_w_f32(c[d], o[d], icn[d], wn[d], ich[d], wh[d]);
         float eb[6];
         gather<float, DIM>(F, g, icn, wn, ich, wh, eb);
-        const double chi = chi_of<float>(km, kx, ky, kz, eb[0], eb[1], eb[2], eb[3], eb[4], eb[5], q.inv_Es);
+        const float chi = chi_f32(km, kx, ky, kz, eb[0], eb[1], eb[2], eb[3], eb[4], eb[5], (float)q.inv_Es);
         uint32_t w[4];
         bool use_net = false;
         float y0 = 0.f, y1 = 0.f;
         if constexpr (SURR) {
-            double lnchi;
-            const bool inr = live && km > 0.f && mlp_in_range(q.nrm, chi, lnchi);
+            float lnchi;
+            const bool inr = live && km > 0.f && mlp_in_range_f32(q.nrm, chi, lnchi);
             if (__any_sync(0xffffffffu, inr)) {
                 float x0 = 0.f, x1 = 0.f;
                 if (inr) {
                     const uint64_t id = q.id[p];
                     philox4x32_10((uint32_t)id, (uint32_t)(id >> 32), q.step, QP_PAIR, q.key[0], q.key[1], w);
-                    mlp_inputs(q.nrm, QED_PAIR, lnchi, uniform24(w[0]), x0, x1);
+                    mlp_inputs_f32(q.nrm, QED_PAIR, lnchi, (float)uniform24(w[0]), x0, x1);
                 }
                 mlp_eval_warp(*reinterpret_cast<const MlpImage *>(smem), x0, x1, y0, y1);
                 use_net = inr;
@@ -247,8 +249,8 @@ __global__ void __launch_bounds__(256) k_push_photon_f32(PartF32 P, const float 
                 return;
             }
         }
-        const double G = use_net ? mlp_rate(q.nrm, QED_PAIR, chi, y1) : qed_rate<float>(q.T, QED_PAIR, chi);
-        double tau = q.tau[p] - (km > 0.f ? q.pref * G / km : 0.0);
+        const float G = use_net ? mlp_rate_f32(q.nrm, QED_PAIR, chi, y1) : qed_rate_f32(q.T, QED_PAIR, chi);
+        double tau = q.tau[p] - (km > 0.f ? (double)((float)q.pref * G / km) : 0.0);
         if (tau <= 0.0) {
             if (!use_net) {
                 const uint64_t id = q.id[p];

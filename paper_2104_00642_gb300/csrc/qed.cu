@@ -288,18 +288,24 @@ void launch_qed_eval(const QedTables &T, bool f64, int p, long long n, const dou
 // spawning: the events of a species are exclusive-scanned in array order and
 // the children appended at the end of their species (deterministic order)
 // ---------------------------------------------------------------------
+// the spawn kernels stride over the parents with a grid of a few waves: most
+// parents have no event, and a grid sized to the (host upper bound of the)
+// count would spend its time launching empty blocks
+inline int spawn_blocks(long long n) { return (int)std::min<long long>(div_up(n, 256), 152 * 8); }
+
 __global__ void k_spawn_photons_f32(PartF32 parent, const uint32_t *__restrict__ off,
                                     const uint32_t *__restrict__ total, QedParams q, PartF32 ph, double *ph_tau,
                                     uint64_t *ph_id, uint32_t *ph_ev, long long *ph_count, long long ph_cap, int dim,
                                     int *err)
 {
-    const long long p = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    const long long p0 = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     const long long n = *parent.dn;
     const long long base = *ph_count;
-    if (p == 0 && base + *total > ph_cap) atomicOr(err, ERR_CAPACITY);
-    if (p >= n || !q.ev[p]) return;
+    if (p0 == 0 && base + *total > ph_cap) atomicOr(err, ERR_CAPACITY);
+    for (long long p = p0; p < n; p += (long long)gridDim.x * blockDim.x) {
+    if (!q.ev[p]) continue;
     const long long dst = base + off[p];
-    if (dst >= ph_cap) return;
+    if (dst >= ph_cap) continue;
     uint32_t w[4];
     const uint64_t pid = q.id[p];
     philox4x32_10((uint32_t)pid, (uint32_t)(pid >> 32), q.step, QP_EMIT, q.key[0], q.key[1], w);
@@ -312,6 +318,7 @@ __global__ void k_spawn_photons_f32(PartF32 parent, const uint32_t *__restrict__
     ph_id[dst] = cid;
     ph_tau[dst] = initial_tau(cid, q.key);
     ph_ev[dst] = 0;
+    }
 }
 
 __global__ void k_spawn_pairs_f32(PartF32 phot, const uint32_t *__restrict__ off, const uint32_t *__restrict__ total,
@@ -319,13 +326,14 @@ __global__ void k_spawn_pairs_f32(PartF32 phot, const uint32_t *__restrict__ off
                                   long long *el_count, long long el_cap, PartF32 po, double *po_tau, uint64_t *po_id,
                                   uint32_t *po_ev, long long *po_count, long long po_cap, int dim, int *err)
 {
-    const long long p = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    const long long p0 = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     const long long n = *phot.dn;
     const long long be = *el_count, bp = *po_count;
-    if (p == 0 && (be + *total > el_cap || bp + *total > po_cap)) atomicOr(err, ERR_CAPACITY);
-    if (p >= n || !q.ev[p]) return;
+    if (p0 == 0 && (be + *total > el_cap || bp + *total > po_cap)) atomicOr(err, ERR_CAPACITY);
+    for (long long p = p0; p < n; p += (long long)gridDim.x * blockDim.x) {
+    if (!q.ev[p]) continue;
     const long long de = be + off[p], dp = bp + off[p];
-    if (de >= el_cap || dp >= po_cap) return;
+    if (de >= el_cap || dp >= po_cap) continue;
     uint32_t w[4];
     const uint64_t pid = q.id[p];
     philox4x32_10((uint32_t)pid, (uint32_t)(pid >> 32), q.step, QP_PAIR, q.key[0], q.key[1], w);
@@ -357,6 +365,7 @@ __global__ void k_spawn_pairs_f32(PartF32 phot, const uint32_t *__restrict__ off
     po_tau[dp] = initial_tau(pid2, q.key);
     el_ev[de] = 0;
     po_ev[dp] = 0;
+    }
 }
 
 // FP64 plain form: absolute positions, event data as 4 doubles per particle
@@ -365,13 +374,14 @@ __global__ void k_spawn_photons_f64(PartF64 parent, const uint32_t *__restrict__
                                     uint64_t *ph_id, uint32_t *ph_ev, long long *ph_count, long long ph_cap, int dim,
                                     int *err)
 {
-    const long long p = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    const long long p0 = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     const long long n = *parent.dn;
     const long long base = *ph_count;
-    if (p == 0 && base + *total > ph_cap) atomicOr(err, ERR_CAPACITY);
-    if (p >= n || !q.ev[p]) return;
+    if (p0 == 0 && base + *total > ph_cap) atomicOr(err, ERR_CAPACITY);
+    for (long long p = p0; p < n; p += (long long)gridDim.x * blockDim.x) {
+    if (!q.ev[p]) continue;
     const long long dst = base + off[p];
-    if (dst >= ph_cap) return;
+    if (dst >= ph_cap) continue;
     uint32_t w[4];
     const uint64_t pid = q.id[p];
     philox4x32_10((uint32_t)pid, (uint32_t)(pid >> 32), q.step, QP_EMIT, q.key[0], q.key[1], w);
@@ -385,6 +395,7 @@ __global__ void k_spawn_photons_f64(PartF64 parent, const uint32_t *__restrict__
     ph_id[dst] = cid;
     ph_tau[dst] = initial_tau(cid, q.key);
     ph_ev[dst] = 0;
+    }
 }
 
 __global__ void k_spawn_pairs_f64(PartF64 phot, const uint32_t *__restrict__ off, const uint32_t *__restrict__ total,
@@ -392,13 +403,14 @@ __global__ void k_spawn_pairs_f64(PartF64 phot, const uint32_t *__restrict__ off
                                   long long *el_count, long long el_cap, PartF64 po, double *po_tau, uint64_t *po_id,
                                   uint32_t *po_ev, long long *po_count, long long po_cap, int dim, int *err)
 {
-    const long long p = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    const long long p0 = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     const long long n = *phot.dn;
     const long long be = *el_count, bp = *po_count;
-    if (p == 0 && (be + *total > el_cap || bp + *total > po_cap)) atomicOr(err, ERR_CAPACITY);
-    if (p >= n || !q.ev[p]) return;
+    if (p0 == 0 && (be + *total > el_cap || bp + *total > po_cap)) atomicOr(err, ERR_CAPACITY);
+    for (long long p = p0; p < n; p += (long long)gridDim.x * blockDim.x) {
+    if (!q.ev[p]) continue;
     const long long de = be + off[p], dp = bp + off[p];
-    if (de >= el_cap || dp >= po_cap) return;
+    if (de >= el_cap || dp >= po_cap) continue;
     uint32_t w[4];
     const uint64_t pid = q.id[p];
     philox4x32_10((uint32_t)pid, (uint32_t)(pid >> 32), q.step, QP_PAIR, q.key[0], q.key[1], w);
@@ -428,6 +440,7 @@ __global__ void k_spawn_pairs_f64(PartF64 phot, const uint32_t *__restrict__ off
     po_tau[dp] = initial_tau(pid2, q.key);
     el_ev[de] = 0;
     po_ev[dp] = 0;
+    }
 }
 
 __global__ void k_add_count(long long *count, const uint32_t *total, long long cap)
@@ -461,7 +474,7 @@ void launch_spawn_photons(const PartF32 &parent, const uint32_t *off, const uint
 {
     if (parent.n == 0) return;
     note_launch(2);
-    k_spawn_photons_f32<<<div_up(parent.n, 256), 256, 0, st>>>(parent, off, total, q, ph, ph_tau, ph_id, ph_ev,
+    k_spawn_photons_f32<<<spawn_blocks(parent.n), 256, 0, st>>>(parent, off, total, q, ph, ph_tau, ph_id, ph_ev,
                                                               ph_count, ph_cap, dim, err);
     k_add_count<<<1, 1, 0, st>>>(ph_count, total, ph_cap);
 }
@@ -473,7 +486,7 @@ void launch_spawn_pairs(const PartF32 &phot, const uint32_t *off, const uint32_t
 {
     if (phot.n == 0) return;
     note_launch(3);
-    k_spawn_pairs_f32<<<div_up(phot.n, 256), 256, 0, st>>>(phot, off, total, q, el, el_tau, el_id, el_ev, el_count,
+    k_spawn_pairs_f32<<<spawn_blocks(phot.n), 256, 0, st>>>(phot, off, total, q, el, el_tau, el_id, el_ev, el_count,
                                                           el_cap, po, po_tau, po_id, po_ev, po_count, po_cap, dim, err);
     k_add_count<<<1, 1, 0, st>>>(el_count, total, el_cap);
     k_add_count<<<1, 1, 0, st>>>(po_count, total, po_cap);
@@ -485,7 +498,7 @@ void launch_spawn_photons(const PartF64 &parent, const uint32_t *off, const uint
 {
     if (parent.n == 0) return;
     note_launch(2);
-    k_spawn_photons_f64<<<div_up(parent.n, 256), 256, 0, st>>>(parent, off, total, q, ph, ph_tau, ph_id, ph_ev,
+    k_spawn_photons_f64<<<spawn_blocks(parent.n), 256, 0, st>>>(parent, off, total, q, ph, ph_tau, ph_id, ph_ev,
                                                               ph_count, ph_cap, dim, err);
     k_add_count<<<1, 1, 0, st>>>(ph_count, total, ph_cap);
 }
@@ -497,7 +510,7 @@ void launch_spawn_pairs(const PartF64 &phot, const uint32_t *off, const uint32_t
 {
     if (phot.n == 0) return;
     note_launch(3);
-    k_spawn_pairs_f64<<<div_up(phot.n, 256), 256, 0, st>>>(phot, off, total, q, el, el_tau, el_id, el_ev, el_count,
+    k_spawn_pairs_f64<<<spawn_blocks(phot.n), 256, 0, st>>>(phot, off, total, q, el, el_tau, el_id, el_ev, el_count,
                                                           el_cap, po, po_tau, po_id, po_ev, po_count, po_cap, dim, err);
     k_add_count<<<1, 1, 0, st>>>(el_count, total, el_cap);
     k_add_count<<<1, 1, 0, st>>>(po_count, total, po_cap);

@@ -180,6 +180,38 @@ __host__ __device__ __forceinline__ double qed_sample(const QedTables &T, int p,
     return flip ? 1.0 - f : f;
 }
 
+// --- FP32 form: chi and the rate in single precision (the optical depth
+// they decrement stays FP64) ---
+__device__ __forceinline__ float chi_f32(float g, float ux, float uy, float uz, float ex, float ey, float ez, float bx,
+                                         float by, float bz, float inv_Es)
+{
+    const float fx = fmaf(g, ex, uy * bz - uz * by);
+    const float fy = fmaf(g, ey, uz * bx - ux * bz);
+    const float fz = fmaf(g, ez, ux * by - uy * bx);
+    const float ue = ux * ex + uy * ey + uz * ez;
+    const float s = fx * fx + fy * fy + fz * fz - ue * ue;
+    return s > 0.f ? sqrtf(s) * inv_Es : 0.f;
+}
+
+// G_p(chi) from the FP32 tables, as qed_rate in single precision
+__device__ __forceinline__ float qed_rate_f32(const QedTables &T, int p, float chi)
+{
+    if (!(chi > 0.f)) return 0.f;
+    const float *L = T.lnG_f[p];
+    const float x = (logf(chi) - (float)T.lnchi0) * (float)(1.0 / T.dlnchi);
+    const float sub = p == QED_PAIR ? 8.0f / (3.0f * chi) : 0.f;
+    if (x <= 0.f) return p == QED_PAIR ? 0.f : expf(fmaf(x, L[1] - L[0], L[0]));
+    const int n = T.nchi;
+    if (x >= n - 1) return expf(fmaf(x - (n - 1), L[n - 1] - L[n - 2], L[n - 1]) - sub);
+    const int i = (int)x;
+    const float t = x - i;
+    const float p0 = L[max(i - 1, 0)], p1 = L[i], p2 = L[i + 1], p3 = L[min(i + 2, n - 1)];
+    const float a = -0.5f * p0 + 1.5f * p1 - 1.5f * p2 + 0.5f * p3;
+    const float b = p0 - 2.5f * p1 + 2.0f * p2 - 0.5f * p3;
+    const float c = -0.5f * p0 + 0.5f * p2;
+    return expf(fmaf(fmaf(fmaf(a, t, b), t, c), t, p1) - sub);
+}
+
 // --- surrogate network in place of the tables (trained chi range) ---
 __device__ __forceinline__ bool mlp_in_range(const MlpNorm &n, double chi, double &lnchi)
 {
@@ -192,10 +224,26 @@ __device__ __forceinline__ void mlp_inputs(const MlpNorm &n, int p, double lnchi
     x0 = fmaf(n.x0a, (float)lnchi, n.x0b);
     x1 = (float)mlp_rcoord(p, r);
 }
+// the same in FP32 (the push: r is a 24-bit uniform, exact in FP32)
+__device__ __forceinline__ void mlp_inputs_f32(const MlpNorm &n, int p, float lnchi, float r, float &x0, float &x1)
+{
+    x0 = fmaf(n.x0a, lnchi, n.x0b);
+    const float t = p == 0 ? 1.0f - sqrtf(fmaxf(1.0f - r, 0.f)) : sqrtf(2.0f * fminf(r, 1.0f - r));
+    x1 = 2.0f * t - 1.0f;
+}
 // G from the rate output y1
 __device__ __forceinline__ double mlp_rate(const MlpNorm &n, int p, double chi, float y1)
 {
     return exp((double)fmaf(n.sd, y1, n.mu) - (p == QED_PAIR ? 8.0 / (3.0 * chi) : 0.0));
+}
+__device__ __forceinline__ float mlp_rate_f32(const MlpNorm &n, int p, float chi, float y1)
+{
+    return expf(fmaf(n.sd, y1, n.mu) - (p == QED_PAIR ? 8.0f / (3.0f * chi) : 0.f));
+}
+__device__ __forceinline__ bool mlp_in_range_f32(const MlpNorm &n, float chi, float &lnchi)
+{
+    lnchi = chi > 0.f ? logf(chi) : -1e30f;
+    return lnchi >= (float)n.lnchi_lo && lnchi <= (float)n.lnchi_hi;
 }
 // energy fraction from the sample output y0 at CDF r
 __device__ __forceinline__ double mlp_fraction(int p, float y0, double r)
