@@ -397,7 +397,8 @@ def main():
     alg_bytes_launch = (npart * bpp + len(w.species) * grid_b) / len(w.species)
     achieved = alg_bytes_launch / per_launch_s / 1e9
     trec = traffic_record(["paper_2104_00642_gb300/csrc/push_tile.cu", "paper_2104_00642_gb300/csrc/push_dev.cuh",
-                           "paper_2104_00642_gb300/csrc/push.cuh", "paper_2104_00642_gb300/csrc/pic_internal.cuh"])
+                           "paper_2104_00642_gb300/csrc/push.cuh", "paper_2104_00642_gb300/csrc/pic_internal.cuh",
+                           "paper_2104_00642_gb300/csrc/push_tile.cuh"])
     roof = {"bound": "hbm", "kernel": "push (gather+Boris+drift+Esirkepov)", "achieved": achieved,
             "peak": peak, "unit": "GB/s", "frac": achieved / peak, "peak_kind": f"{peak_kind} hbm_gbs",
             "traffic": (trec["bytes_per_launch"] if trec else None),

@@ -19,8 +19,9 @@
 namespace pic {
 
 // particle staging: slot (j, l) of particle i = l*S + j (lane l, segment
-// position j) sits at j*33 + l, so the 32 lanes of a read hit 32 banks
-constexpr int kPSlot = 33 * 32;
+// position j < kChunk/32) sits at j*33 + l, so the 32 lanes of a read hit
+// 32 banks
+constexpr int kPSlot = 33 * (kChunk / 32);
 
 template <int T>
 struct Box2 {
@@ -123,8 +124,9 @@ struct AccShared {
     float scale;
     __device__ __forceinline__ void add(int c, int a, int b, float v)
     {
-        int q = __float2int_rn(v * scale);
-        if (q != 0) atomicAdd(base + c * cs + b * rs + a, q);
+        // no zero test: a branch per node costs more than the occasional
+        // zero add, and the warp issues the atomic for its other lanes anyway
+        atomicAdd(base + c * cs + b * rs + a, __float2int_rn(v * scale));
     }
 };
 
@@ -167,7 +169,7 @@ __device__ __forceinline__ float inv_gamma_fast(float ux, float uy, float uz)
 }
 
 template <int T>
-__global__ void __launch_bounds__(kTileThreads, 4)
+__global__ void __launch_bounds__(kTileThreads, kTileMinBlocks)
     k_push_tile2d(PartF32 P, const TileItem *__restrict__ items, const uint32_t *__restrict__ nitems,
                   float *__restrict__ F, Grid g, PushConst pc, int *err, double *e_abs)
 {
@@ -213,7 +215,7 @@ __global__ void __launch_bounds__(kTileThreads, 4)
         for (int i = threadIdx.x; i < m.count; i += blockDim.x) {
             const int l = i / S, j = i - l * S;
             const int pos = j * 33 + l;
-            const long long p = (long long)m.start + i;
+            const int p = m.start + i;  // capacities are below 2^31
             sPc[pos] = P.cell[p];
             sP[0 * kPSlot + pos] = P.off[0][p];
             sP[1 * kPSlot + pos] = P.off[1][p];
@@ -227,7 +229,7 @@ __global__ void __launch_bounds__(kTileThreads, 4)
         for (int j = warp; j < S; j += kTileThreads / 32) {
             const int li = lane * S + j;
             if (li >= m.count) continue;
-            const long long p = (long long)m.start + li;
+            const int p = m.start + li;
             const int pos = j * 33 + lane;
             const uint32_t cp = sPc[pos];
             if (cp == kDead) continue;
@@ -402,7 +404,7 @@ static void launch_T(const PartF32 &P, const TileItem *items, const uint32_t *ni
         cudaGetDevice(&dev);
         cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
     }
-    long long grid = std::min<long long>(max_items, (long long)nsm * 8);
+    long long grid = std::min<long long>(max_items, (long long)nsm * kTileMinBlocks);  // one resident wave
     if (grid < 1) grid = 1;
     note_launch();
     k_push_tile2d<T><<<(int)grid, kTileThreads, Box2<T>::SMEM, st>>>(P, items, nitems, F, g, pc, err, e_abs);

@@ -5,8 +5,9 @@
 
 namespace pic {
 
-constexpr int kChunk = 1024;       // particles per work item at most
+constexpr int kChunk = 384;        // particles per work item at most
 constexpr int kTileThreads = 128;  // threads per CTA of the tiled push
+constexpr int kTileMinBlocks = 6;  // CTAs per SM: 80 registers, 35 KB shared memory each (measured best)
 
 struct TileItem {
     int tile, start, count, pad;
