@@ -140,6 +140,10 @@ __device__ inline R incident_B(const Grid &g, const Laser &L, int c, int q, int 
     return R(0);
 }
 
+template <typename R, int DIM>
+__device__ __forceinline__ void mur_faces(R *const *B, const Grid &g, R h, const Laser &L, int i, int j, int k, int o,
+                                          const R *oldv);
+
 // B -= h curl E, then the Mur ghosts of the tangential B on absorbing
 // faces: for the scattered part s = B - B_inc of an outgoing wave,
 // s_ghost(new) = s_inner(old) + (a-1)/(a+1) (s_inner(new) - s_ghost(old)),
@@ -178,6 +182,15 @@ __global__ void __launch_bounds__(256) k_update_B(R *__restrict__ F, Grid g, R h
         oldv[c] = B[c][o];
         if (ph.comp(BX + c)) B[c][o] = oldv[c] - h * cur[c];
     }
+    mur_faces<R, DIM>(B, g, h, L, i, j, k, o, oldv);
+}
+
+// the Mur ghosts of cell (i, j, k) at offset o, after its B update (oldv:
+// its B before the update)
+template <typename R, int DIM>
+__device__ __forceinline__ void mur_faces(R *const *B, const Grid &g, R h, const Laser &L, int i, int j, int k, int o,
+                                          const R *oldv)
+{
     int p[3] = {i, j, k};
 #pragma unroll
     for (int d = 0; d < DIM; d++) {
@@ -211,6 +224,200 @@ __global__ void __launch_bounds__(256) k_update_B(R *__restrict__ F, Grid g, R h
                 const R si_new = B[c][o] - ii_new;
                 B[c][og] = ig_new + si_old + c1 * (si_new - sg_old);
             }
+        }
+    }
+}
+
+// ---------------------------------------------------------------------
+// FP32, four cells per thread along x (float4 loads and stores; the padded
+// rows start 16-byte aligned and hold a multiple of 4 cells when n_x is a
+// multiple of 4).  Same arithmetic, in the same order, as the one-cell
+// kernels above.  A component is stored as a vector when all four cells are
+// physical for it, else cell by cell (ghost cells on absorbing axes belong
+// to the Mur update).
+// ---------------------------------------------------------------------
+__device__ __forceinline__ float4 ld4(const float *p) { return *reinterpret_cast<const float4 *>(p); }
+__device__ __forceinline__ void st4(float *p, const float (&v)[4])
+{
+    *reinterpret_cast<float4 *>(p) = make_float4(v[0], v[1], v[2], v[3]);
+}
+__device__ __forceinline__ void unpack4(const float4 &a, float (&v)[4])
+{
+    v[0] = a.x;
+    v[1] = a.y;
+    v[2] = a.z;
+    v[3] = a.w;
+}
+
+__device__ __forceinline__ bool thread_cell4(const Grid &g, int &i, int &j, int &k)
+{
+    i = 4 * (blockIdx.x * blockDim.x + threadIdx.x);
+    j = blockIdx.y * blockDim.y + threadIdx.y;
+    k = blockIdx.z;
+    if (i >= g.ext[0] || j >= g.ext[1]) return false;
+    i -= g.G[0];
+    j -= g.G[1];
+    k -= g.G[2];
+    return true;
+}
+
+__device__ __forceinline__ void store_phys(float *A, int o, const float (&v)[4], const Phys (&ph)[4], int c)
+{
+    const bool all = ph[0].comp(c) && ph[1].comp(c) && ph[2].comp(c) && ph[3].comp(c);
+    if (all) {
+        st4(A + o, v);
+    } else {
+#pragma unroll
+        for (int e = 0; e < 4; e++)
+            if (ph[e].comp(c)) A[o + e] = v[e];
+    }
+}
+
+template <int DIM>
+__global__ void __launch_bounds__(256) k_update_E4(float *__restrict__ F, Grid g, float h, int twice, int zeroJ)
+{
+    int i, j, k;
+    if (!thread_cell4(g, i, j, k)) return;
+    const int o = loff(g, i, j, k);
+    const long long V = g.vol;
+    const float *__restrict__ Bx = F + BX * V;
+    const float *__restrict__ By = F + BY * V;
+    const float *__restrict__ Bz = F + BZ * V;
+    float *E[3] = {F + EX * V, F + EY * V, F + EZ * V};
+    float *J[3] = {F + JX * V, F + JY * V, F + JZ * V};
+    const float rdx = g.rdx_f[0], rdy = g.rdx_f[1], rdz = g.rdx_f[2];
+    float bz[4], by[4];
+    unpack4(ld4(Bz + o), bz);
+    unpack4(ld4(By + o), by);
+    const int mx = nb_off(g, 0, i, -1);
+    const float bzl = Bz[o + mx], byl = By[o + mx];
+    float cx[4] = {0.f, 0.f, 0.f, 0.f}, cy[4] = {0.f, 0.f, 0.f, 0.f}, cz[4] = {0.f, 0.f, 0.f, 0.f};
+#pragma unroll
+    for (int e = 0; e < 4; e++) {
+        cy[e] -= (bz[e] - (e ? bz[e - 1] : bzl)) * rdx;
+        cz[e] += (by[e] - (e ? by[e - 1] : byl)) * rdx;
+    }
+    float bx[4];
+    if (DIM >= 2) {
+        const int my = nb_off(g, 1, j, -1);
+        float bzm[4], bxm[4];
+        unpack4(ld4(Bx + o), bx);
+        unpack4(ld4(Bz + o + my), bzm);
+        unpack4(ld4(Bx + o + my), bxm);
+#pragma unroll
+        for (int e = 0; e < 4; e++) {
+            cx[e] += (bz[e] - bzm[e]) * rdy;
+            cz[e] -= (bx[e] - bxm[e]) * rdy;
+        }
+    }
+    if (DIM >= 3) {
+        const int mz = nb_off(g, 2, k, -1);
+        float bym[4], bxm[4];
+        unpack4(ld4(By + o + mz), bym);
+        unpack4(ld4(Bx + o + mz), bxm);
+#pragma unroll
+        for (int e = 0; e < 4; e++) {
+            cx[e] -= (by[e] - bym[e]) * rdz;
+            cy[e] += (bx[e] - bxm[e]) * rdz;
+        }
+    }
+    Phys ph[4];
+#pragma unroll
+    for (int e = 0; e < 4; e++) ph[e] = phys_of(g, i + e, j, k);
+    const float *cur[3] = {cx, cy, cz};
+#pragma unroll
+    for (int c = 0; c < 3; c++) {
+        float jv[4], ev[4];
+        unpack4(ld4(J[c] + o), jv);
+        unpack4(ld4(E[c] + o), ev);
+#pragma unroll
+        for (int e = 0; e < 4; e++) {
+            const float a = h * (cur[c][e] - jv[e]);
+            ev[e] += a;
+            if (twice) ev[e] += a;
+        }
+        store_phys(E[c], o, ev, ph, EX + c);
+    }
+    if (zeroJ) {
+        const float z[4] = {0.f, 0.f, 0.f, 0.f};
+#pragma unroll
+        for (int c = 0; c < 3; c++) st4(J[c] + o, z);
+    }
+}
+
+template <int DIM>
+__global__ void __launch_bounds__(256) k_update_B4(float *__restrict__ F, Grid g, float h, Laser L)
+{
+    int i, j, k;
+    if (!thread_cell4(g, i, j, k)) return;
+    const int o = loff(g, i, j, k);
+    const long long V = g.vol;
+    const float *__restrict__ Ex = F + EX * V;
+    const float *__restrict__ Ey = F + EY * V;
+    const float *__restrict__ Ez = F + EZ * V;
+    float *B[3] = {F + BX * V, F + BY * V, F + BZ * V};
+    const float rdx = g.rdx_f[0], rdy = g.rdx_f[1], rdz = g.rdx_f[2];
+    float ez[4], ey[4];
+    unpack4(ld4(Ez + o), ez);
+    unpack4(ld4(Ey + o), ey);
+    const int px = nb_off(g, 0, i + 3, +1);
+    const float ezr = Ez[o + 3 + px], eyr = Ey[o + 3 + px];
+    float cx[4] = {0.f, 0.f, 0.f, 0.f}, cy[4] = {0.f, 0.f, 0.f, 0.f}, cz[4] = {0.f, 0.f, 0.f, 0.f};
+#pragma unroll
+    for (int e = 0; e < 4; e++) {
+        cy[e] -= ((e < 3 ? ez[e + 1] : ezr) - ez[e]) * rdx;
+        cz[e] += ((e < 3 ? ey[e + 1] : eyr) - ey[e]) * rdx;
+    }
+    float ex[4];
+    if (DIM >= 2) {
+        const int py = nb_off(g, 1, j, +1);
+        float ezp[4], exp_[4];
+        unpack4(ld4(Ex + o), ex);
+        unpack4(ld4(Ez + o + py), ezp);
+        unpack4(ld4(Ex + o + py), exp_);
+#pragma unroll
+        for (int e = 0; e < 4; e++) {
+            cx[e] += (ezp[e] - ez[e]) * rdy;
+            cz[e] -= (exp_[e] - ex[e]) * rdy;
+        }
+    }
+    if (DIM >= 3) {
+        const int pz = nb_off(g, 2, k, +1);
+        float eyp[4], exp_[4];
+        unpack4(ld4(Ey + o + pz), eyp);
+        unpack4(ld4(Ex + o + pz), exp_);
+#pragma unroll
+        for (int e = 0; e < 4; e++) {
+            cx[e] -= (eyp[e] - ey[e]) * rdz;
+            cy[e] += (exp_[e] - ex[e]) * rdz;
+        }
+    }
+    Phys ph[4];
+#pragma unroll
+    for (int e = 0; e < 4; e++) ph[e] = phys_of(g, i + e, j, k);
+    const float *cur[3] = {cx, cy, cz};
+    float oldv[3][4];
+#pragma unroll
+    for (int c = 0; c < 3; c++) {
+        float nv[4];
+        unpack4(ld4(B[c] + o), oldv[c]);
+#pragma unroll
+        for (int e = 0; e < 4; e++) nv[e] = oldv[c][e] - h * cur[c][e];
+        store_phys(B[c], o, nv, ph, BX + c);
+    }
+    // Mur ghosts: only groups that touch an absorbing face
+    bool face = false;
+#pragma unroll
+    for (int d = 0; d < DIM; d++) {
+        if (g.bc[d] != ABSORB) continue;
+        const int lo = d == 0 ? i : (d == 1 ? j : k), hi = d == 0 ? i + 3 : lo;
+        face |= (lo <= 0 && hi >= 0) || (lo <= g.n[d] - 1 && hi >= g.n[d] - 1);
+    }
+    if (face) {
+#pragma unroll
+        for (int e = 0; e < 4; e++) {
+            const float ov[3] = {oldv[0][e], oldv[1][e], oldv[2][e]};
+            mur_faces<float, DIM>(B, g, h, L, i + e, j, k, o + e, ov);
         }
     }
 }
@@ -287,12 +494,23 @@ static void grid_dims(const Grid &g, int e0, int e1, int e2, dim3 &blk, dim3 &gr
     grd = dim3((unsigned)div_up(e0, blk.x), (unsigned)div_up(e1, blk.y), (unsigned)e2);
 }
 
+static bool vec4_ok(const Grid &g) { return g.n[0] % 4 == 0 && g.G[0] % 4 == 0; }
+
 template <typename R>
 void launch_update_E(R *F, const Grid &g, double h, bool twice, bool zeroJ, cudaStream_t st)
 {
     dim3 b, n;
-    grid_dims(g, g.ext[0], g.ext[1], g.ext[2], b, n);
     note_launch();
+    if constexpr (sizeof(R) == 4) {
+        if (vec4_ok(g)) {
+            grid_dims(g, g.ext[0] / 4, g.ext[1], g.ext[2], b, n);
+            if (g.dim == 1) k_update_E4<1><<<n, b, 0, st>>>(F, g, (float)h, twice, zeroJ);
+            else if (g.dim == 2) k_update_E4<2><<<n, b, 0, st>>>(F, g, (float)h, twice, zeroJ);
+            else k_update_E4<3><<<n, b, 0, st>>>(F, g, (float)h, twice, zeroJ);
+            return;
+        }
+    }
+    grid_dims(g, g.ext[0], g.ext[1], g.ext[2], b, n);
     if (g.dim == 1) k_update_E<R, 1><<<n, b, 0, st>>>(F, g, (R)h, twice, zeroJ);
     else if (g.dim == 2) k_update_E<R, 2><<<n, b, 0, st>>>(F, g, (R)h, twice, zeroJ);
     else k_update_E<R, 3><<<n, b, 0, st>>>(F, g, (R)h, twice, zeroJ);
@@ -302,8 +520,17 @@ template <typename R>
 void launch_update_B(R *F, const Grid &g, double h, double t_new, const Laser &L, cudaStream_t st)
 {
     dim3 b, n;
-    grid_dims(g, g.ext[0], g.ext[1], g.ext[2], b, n);
     note_launch();
+    if constexpr (sizeof(R) == 4) {
+        if (vec4_ok(g)) {
+            grid_dims(g, g.ext[0] / 4, g.ext[1], g.ext[2], b, n);
+            if (g.dim == 1) k_update_B4<1><<<n, b, 0, st>>>(F, g, (float)h, L);
+            else if (g.dim == 2) k_update_B4<2><<<n, b, 0, st>>>(F, g, (float)h, L);
+            else k_update_B4<3><<<n, b, 0, st>>>(F, g, (float)h, L);
+            return;
+        }
+    }
+    grid_dims(g, g.ext[0], g.ext[1], g.ext[2], b, n);
     if (g.dim == 1) k_update_B<R, 1><<<n, b, 0, st>>>(F, g, (R)h, t_new, L);
     else if (g.dim == 2) k_update_B<R, 2><<<n, b, 0, st>>>(F, g, (R)h, t_new, L);
     else k_update_B<R, 3><<<n, b, 0, st>>>(F, g, (R)h, t_new, L);
