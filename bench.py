@@ -306,6 +306,8 @@ def main():
     ap.add_argument("--no-flush", action="store_true")
     ap.add_argument("--no-fp64", action="store_true", help="skip the plain FP64 form")
     ap.add_argument("--qed-beam", type=int, default=10_000_000, help="beam macro-electrons (qed_collision_2d)")
+    ap.add_argument("--rows", type=int, default=None,
+                    help="smaller case for profiling: ny of laser_foil_2d, nz of thermal_3d (not a bench line)")
     ap.add_argument("--qed-modes", default="surrogate,table,fp64", help="forms run by qed_collision_2d")
     ap.add_argument("--qed-train-iters", type=int, default=0, help="surrogate training steps (0: library default)")
     args = ap.parse_args()
@@ -327,7 +329,7 @@ def main():
         import torch.distributed as dist
         dist.init_process_group("nccl", init_method="env://")
     stream = torch.cuda.Stream()
-    w = make_workload(args.workload, rank, beam=args.qed_beam)
+    w = make_workload(args.workload, rank, sample=args.rows, beam=args.qed_beam)
     npart = w.n_particles
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
 

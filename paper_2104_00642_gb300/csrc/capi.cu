@@ -47,6 +47,7 @@ struct SpeciesState {
     uint32_t *nitems = nullptr;
     uint32_t *item_cnt = nullptr;   // ntiles + 1
     uint32_t *item_scan = nullptr;  // scan scratch
+    uint32_t *defer = nullptr;      // 3D: particles the tiled push leaves to the global path ([0] = count)
     long long items_cap = 0;
     bool items_valid = false;
     // QED: kind, optical depth and identity (double-buffered with the
@@ -226,7 +227,7 @@ int sort_species(pic_sim *s, int i)
         launch_permute_f32(view32(s, i, p.cur), view32(s, i, o), perm, p.d_count, p.n_hi, s->g.dim, s->st);
     p.cur = o;
     if (p.items) {
-        build_tile_items(p.tile_start, s->g.ntiles, p.item_cnt, p.item_scan, p.items, p.nitems, s->st);
+        build_tile_items(p.tile_start, s->g.ntiles, s->g.dim, p.item_cnt, p.item_scan, p.items, p.nitems, s->st);
         p.items_valid = true;
     }
     CK(cudaGetLastError());
@@ -235,9 +236,11 @@ int sort_species(pic_sim *s, int i)
 
 bool use_tile_push(const pic_sim *s, const SpeciesState &p)
 {
-    return s->push_variant == PIC_PUSH_AUTO && p.items_valid && s->precision == PIC_PREC_FP32_CELLOFF &&
-           p.kind == PIC_KIND_MASSIVE && !(s->qed_on && p.qed) &&
-           s->g.dim == 2 && s->g.tile_log2[0] == s->g.tile_log2[1] &&
+    if (s->push_variant != PIC_PUSH_AUTO || !p.items_valid || s->precision != PIC_PREC_FP32_CELLOFF ||
+        p.kind != PIC_KIND_MASSIVE || (s->qed_on && p.qed))
+        return false;
+    if (s->g.dim == 3) return tile3d_push_supported(s->g);
+    return s->g.dim == 2 && s->g.tile_log2[0] == s->g.tile_log2[1] &&
            (s->g.tile_log2[0] == 3 || s->g.tile_log2[0] == 4);
 }
 
@@ -391,10 +394,15 @@ void push_species(pic_sim *s, int i, float *F)
                             s->st);
         return;
     }
-    if (use_tile_push(s, p))
-        launch_push_tile2d(view32(s, i, p.cur), p.items, p.nitems, (long long)tile_items_capacity(p.n_hi, s->g.ntiles),
-                           F, s->g, push_const(s, p), s->d_err, s->d_eabs, s->st);
-    else
+    if (use_tile_push(s, p)) {
+        const long long max_items = (long long)tile_items_capacity(p.n_hi, s->g.ntiles, s->g.dim);
+        if (s->g.dim == 3)
+            launch_push_tile3d(view32(s, i, p.cur), p.items, p.nitems, max_items, F, s->g, push_const(s, p), s->d_err,
+                               s->d_eabs, p.defer + 1, p.defer, s->st);
+        else
+            launch_push_tile2d(view32(s, i, p.cur), p.items, p.nitems, max_items, F, s->g, push_const(s, p), s->d_err,
+                               s->d_eabs, s->st);
+    } else
         launch_push_f32(view32(s, i, p.cur), F, s->g, push_const(s, p), s->d_err, s->d_eabs, s->st);
 }
 
@@ -637,12 +645,13 @@ int pic_create(const pic_grid *grid, double dt, const pic_species *species, int 
         maxcap = std::max(maxcap, p.cap);
         rc = rc ? rc : dalloc(s, (void **)&p.d_count, sizeof(long long));
         rc = rc ? rc : dalloc(s, (void **)&p.tile_start, (size_t)(g.ntiles + 1) * sizeof(uint32_t));
-        if (prec == PIC_PREC_FP32_CELLOFF && g.dim == 2) {
-            p.items_cap = (long long)tile_items_capacity(p.cap, g.ntiles);
+        if (prec == PIC_PREC_FP32_CELLOFF && (g.dim == 2 || (g.dim == 3 && tile3d_push_supported(g)))) {
+            p.items_cap = (long long)tile_items_capacity(p.cap, g.ntiles, g.dim);
             rc = rc ? rc : dalloc(s, (void **)&p.items, (size_t)p.items_cap * sizeof(TileItem));
             rc = rc ? rc : dalloc(s, (void **)&p.nitems, sizeof(uint32_t));
             rc = rc ? rc : dalloc(s, (void **)&p.item_cnt, (size_t)(g.ntiles + 1) * sizeof(uint32_t));
             rc = rc ? rc : dalloc(s, (void **)&p.item_scan, scan_scratch_words(g.ntiles + 1) * sizeof(uint32_t));
+            if (g.dim == 3) rc = rc ? rc : dalloc(s, (void **)&p.defer, (size_t)(p.cap + 1) * sizeof(uint32_t));
         }
         for (int b = 0; b < 2 && !rc; b++) {
             rc = dalloc(s, (void **)&p.cell[b], (size_t)p.cap * 4);

@@ -25,11 +25,35 @@ long long g_launches = 0;
 // FP32 cell+offset push
 // ---------------------------------------------------------------------
 template <int DIM>
+__device__ __forceinline__ void push_one_f32(const PartF32 &P, long long p, float *__restrict__ F, const Grid &g,
+                                             const PushConst &pc, int *err, double *e_abs);
+
+template <int DIM>
 __global__ void __launch_bounds__(256) k_push_f32(PartF32 P, float *__restrict__ F, Grid g, PushConst pc,
                                                   int *err, double *e_abs)
 {
     long long p = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     if (p >= *P.dn) return;
+    push_one_f32<DIM>(P, p, F, g, pc, err, e_abs);
+}
+
+// the particles of a list (the tiled push's deferred ones), grid-stride
+template <int DIM>
+__global__ void __launch_bounds__(256) k_push_list_f32(PartF32 P, const uint32_t *__restrict__ list,
+                                                       const uint32_t *__restrict__ count, float *__restrict__ F,
+                                                       Grid g, PushConst pc, int *err, double *e_abs)
+{
+    const uint32_t n = *count;
+    for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x)
+        push_one_f32<DIM>(P, list[i], F, g, pc, err, e_abs);
+}
+
+// one particle: half drift, gather (HBM), Boris, drifts, Esirkepov (global
+// atomics), boundaries
+template <int DIM>
+__device__ __forceinline__ void push_one_f32(const PartF32 &P, long long p, float *__restrict__ F, const Grid &g,
+                                             const PushConst &pc, int *err, double *e_abs)
+{
     uint32_t pc0 = P.cell[p];
     if (pc0 == kDead) return;
     int c[3];
@@ -329,6 +353,17 @@ void launch_push_f32(const PartF32 &P, float *F, const Grid &g, const PushConst 
     if (g.dim == 1) k_push_f32<1><<<nb, bs, 0, st>>>(P, F, g, pc, err, e_abs);
     else if (g.dim == 2) k_push_f32<2><<<nb, bs, 0, st>>>(P, F, g, pc, err, e_abs);
     else k_push_f32<3><<<nb, bs, 0, st>>>(P, F, g, pc, err, e_abs);
+}
+
+void launch_push_list_f32(const PartF32 &P, const uint32_t *list, const uint32_t *count, long long max_n, float *F,
+                          const Grid &g, const PushConst &pc, int *err, double *e_abs, cudaStream_t st)
+{
+    if (max_n <= 0) return;
+    note_launch();
+    const int nb = (int)std::min<long long>(div_up(max_n, 256), 152LL * 8);
+    if (g.dim == 1) k_push_list_f32<1><<<nb, 256, 0, st>>>(P, list, count, F, g, pc, err, e_abs);
+    else if (g.dim == 2) k_push_list_f32<2><<<nb, 256, 0, st>>>(P, list, count, F, g, pc, err, e_abs);
+    else k_push_list_f32<3><<<nb, 256, 0, st>>>(P, list, count, F, g, pc, err, e_abs);
 }
 
 void launch_push_f64(const PartF64 &P, double *F, const Grid &g, const PushConst &pc, int *err, double *e_abs,

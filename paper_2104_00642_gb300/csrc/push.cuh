@@ -39,6 +39,9 @@ struct PushConst {
 
 void launch_push_f32(const PartF32 &P, float *F, const Grid &g, const PushConst &pc, int *err, double *e_abs,
                      cudaStream_t st);
+// the particles listed in list[0 .. *count) (count on the device, at most max_n)
+void launch_push_list_f32(const PartF32 &P, const uint32_t *list, const uint32_t *count, long long max_n, float *F,
+                          const Grid &g, const PushConst &pc, int *err, double *e_abs, cudaStream_t st);
 void launch_push_f64(const PartF64 &P, double *F, const Grid &g, const PushConst &pc, int *err, double *e_abs,
                      cudaStream_t st);
 void launch_gather_f32(const PartF32 &P, const float *F, const Grid &g, double *out, cudaStream_t st);

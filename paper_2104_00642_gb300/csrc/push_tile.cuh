@@ -13,11 +13,22 @@ struct TileItem {
     int tile, start, count, pad;
 };
 
-size_t tile_items_capacity(long long cap, long long ntiles);
-void build_tile_items(const uint32_t *starts, long long ntiles, uint32_t *cnt_scratch, uint32_t *scan_scratch,
-                      TileItem *items, uint32_t *nitems, cudaStream_t st);
+// 3D items (the 3D push stages no particle state; 256 measured best among
+// 256-1024 on the 8-ppc thermal workload: smaller items balance the CTAs)
+constexpr int kChunk3 = 256;
+
+size_t tile_items_capacity(long long cap, long long ntiles, int dim);
+void build_tile_items(const uint32_t *starts, long long ntiles, int dim, uint32_t *cnt_scratch,
+                      uint32_t *scan_scratch, TileItem *items, uint32_t *nitems, cudaStream_t st);
 bool tile_push_supported(const Grid &g, int tile_edge);
 void launch_push_tile2d(const PartF32 &P, const TileItem *items, const uint32_t *nitems, long long max_items,
                         float *F, const Grid &g, const PushConst &pc, int *err, double *e_abs, cudaStream_t st);
+// 3D: tiles of 4^3 cells, every n_d a multiple of 4
+bool tile3d_push_supported(const Grid &g);
+// (defer: a list of capacity >= the particle count, ndefer its device count;
+// the particles the tiled kernel defers are pushed after it on the global path)
+void launch_push_tile3d(const PartF32 &P, const TileItem *items, const uint32_t *nitems, long long max_items,
+                        float *F, const Grid &g, const PushConst &pc, int *err, double *e_abs, uint32_t *defer,
+                        uint32_t *ndefer, cudaStream_t st);
 
 }  // namespace pic

@@ -127,7 +127,7 @@ def langmuir_1d(n_cells=256, dx=0.05, ppc=100, amp=0.01, steps=1000, courant=0.9
 
 
 def thermal_3d(n=(256, 256, 256), dx=0.1, ppc=8, T_keV=10.0, steps=200, courant=0.95,
-               seed=SEED0 + 3, tile=(8, 8, 8)):
+               seed=SEED0 + 3, tile=(4, 4, 4)):
     """Uniform Maxwellian electrons (u_i ~ N(0, T/mc^2)) at Philox-uniform
     positions on a neutralising background, periodic in all axes."""
     rng = _rng(seed)

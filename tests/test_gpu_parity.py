@@ -297,6 +297,54 @@ def test_tile_push_fallback_after_drift_matches_simple_kernel():
     assert abs(da["U_kin"][0] - do["U_kin"][0]) <= 1e-4 * do["U_kin"][0]
 
 
+# --------------------------------------------------------------------------
+# tiled 3D push (4^3 tiles, shared-memory field and current boxes)
+# --------------------------------------------------------------------------
+
+def test_tile3d_push_one_step_matches_oracle():
+    """Sort at step 0, one step through the 3D tiled kernel: several tiles,
+    tiles touching every periodic face."""
+    n, dx = (16, 12, 8), (0.1, 0.12, 0.11)
+    w, F = random_state(3, n, dx, _dt(dx), 3, seed=311, umax=0.9)
+    sim = pic.from_workload(w, precision=pic.FP32_CELLOFF, sort_interval=1, tile=(4, 4, 4))
+    o = oracle_from_workload(w, sort_interval=1, tile=(4, 4, 4))
+    for c in range(9):
+        sim.pic_set_field(c, F[c])
+        o.set_field(c, F[c])
+    sim.pic_step(1)
+    o.step(1)
+    tol = TOL[pic.FP32_CELLOFF]
+    pg, po = sim.pic_get_particles(0), o.particles(0)
+    for k, d in (("x", 0), ("y", 1), ("z", 2)):
+        assert np.max(np.abs(pg[k] - po[k])) <= 10 * tol * dx[d]
+    umag = np.sqrt(po["ux"] ** 2 + po["uy"] ** 2 + po["uz"] ** 2)
+    for k in ("ux", "uy", "uz"):
+        assert np.all(np.abs(pg[k] - po[k]) <= tol * umag + 1e-7)
+    for c, ax in ((pic.JX, 0), (pic.JY, 1), (pic.JZ, 2)):
+        scale = window_scale(po, w, 3, ax)
+        assert np.all(np.abs(sim.pic_fields(c) - o.field(c)) <= tol * scale + 1e-30)
+
+
+def test_tile3d_push_fallback_after_drift_matches_simple_kernel():
+    """Fast particles and a long sort interval in 3D: particles leave their
+    tile box and take the global path; tiled and simple kernels agree."""
+    n, dx = (16, 16, 12), (0.1, 0.1, 0.1)
+    w, F = random_state(3, n, dx, _dt(dx), 2, seed=312, umax=3.0)
+    sims = [pic.from_workload(w, precision=pic.FP32_CELLOFF, sort_interval=50, tile=(4, 4, 4), push_variant=v)
+            for v in (pic.PUSH_AUTO, pic.PUSH_SIMPLE)]
+    for c in range(9):
+        for s in sims:
+            s.pic_set_field(c, F[c])
+    for s in sims:
+        s.pic_step(10)
+    pa, pb = sims[0].pic_get_particles(0), sims[1].pic_get_particles(0)
+    for k in ("x", "y", "z", "ux", "uy", "uz"):
+        assert np.max(np.abs(pa[k] - pb[k])) < 1e-4
+    da, db = sims[0].pic_diagnostics(), sims[1].pic_diagnostics()
+    for k in ("U_E", "U_B"):
+        assert abs(da[k] - db[k]) <= 1e-4 * max(db["U_E"], db["U_B"])
+
+
 def _laser_foil_small(seed):
     w = W.laser_foil_2d(nx=256, ny=64, slab=(128, 136), ppc=8, a0=20.0, fwhm_fs=5.0, steps=700, seed=seed)
     w.laser.t_peak = 2.0 * w.laser.fwhm  # peak reaches the slab front near step 480
