@@ -132,17 +132,21 @@ class Clocks:
                 "reasons": reasons, "samples": len(rows)}
 
 
-def traffic_record(kernel_src_files):
-    """dram bytes per push launch from the committed ncu summary, if it was
-    taken on the current kernel source (else None)"""
+def source_sha256(files):
+    h = hashlib.sha256()
+    for f in files:
+        h.update(open(os.path.join(ROOT, f), "rb").read())
+    return h.hexdigest()
+
+
+def traffic_record(workload):
+    """dram bytes per push launch of this workload from the committed ncu
+    summary, if it was taken on the current kernel source (else None)"""
     path = os.path.join(ROOT, "profiles", "push_traffic.json")
     if not os.path.exists(path):
         return None
-    rec = json.load(open(path))
-    h = hashlib.sha256()
-    for f in kernel_src_files:
-        h.update(open(os.path.join(ROOT, f), "rb").read())
-    if rec.get("source_sha256") != h.hexdigest():
+    rec = json.load(open(path)).get(workload)
+    if not rec or rec.get("source_sha256") != source_sha256(rec["source_files"]):
         return None
     return rec
 
@@ -398,9 +402,7 @@ def main():
     grid_b = (24 + 12) * occ  # gather 6 comps + deposit 3 comps, once per occupied cell
     alg_bytes_launch = (npart * bpp + len(w.species) * grid_b) / len(w.species)
     achieved = alg_bytes_launch / per_launch_s / 1e9
-    trec = traffic_record(["paper_2104_00642_gb300/csrc/push_tile.cu", "paper_2104_00642_gb300/csrc/push_dev.cuh",
-                           "paper_2104_00642_gb300/csrc/push.cuh", "paper_2104_00642_gb300/csrc/pic_internal.cuh",
-                           "paper_2104_00642_gb300/csrc/push_tile.cuh"])
+    trec = traffic_record(w.name)
     roof = {"bound": "hbm", "kernel": "push (gather+Boris+drift+Esirkepov)", "achieved": achieved,
             "peak": peak, "unit": "GB/s", "frac": achieved / peak, "peak_kind": f"{peak_kind} hbm_gbs",
             "traffic": (trec["bytes_per_launch"] if trec else None),

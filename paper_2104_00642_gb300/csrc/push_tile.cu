@@ -13,8 +13,7 @@
 // A particle that drifted so far since the sort that its stencil leaves the
 // box is handled on the global path (gather from HBM, global atomics), so the
 // result does not depend on the sort interval.
-#include "push_dev.cuh"
-#include "push_tile.cuh"
+#include "push_tile_dev.cuh"
 
 namespace pic {
 
@@ -58,22 +57,6 @@ __device__ __forceinline__ void gather2d(const float *__restrict__ P, long long 
     }
 }
 
-// shapes of the start (i0, w0) and end (i1, w1) points on the 4-node union
-// window [u0, u0+3], u0 = min(i0, i1) - 1 (|i1 - i0| <= 1)
-__device__ __forceinline__ int union4(int i0, const float *w0, int i1, const float *w1, float *S0, float *dS)
-{
-    const int u0 = min(i0, i1) - 1;
-    const int o0 = i0 - 1 - u0, o1 = i1 - 1 - u0;  // each 0 or 1
-#pragma unroll
-    for (int k = 0; k < 4; k++) {
-        float s0 = o0 ? (k >= 1 ? w0[k - 1] : 0.f) : (k <= 2 ? w0[k] : 0.f);
-        float s1 = o1 ? (k >= 1 ? w1[k - 1] : 0.f) : (k <= 2 ? w1[k] : 0.f);
-        S0[k] = s0;
-        dS[k] = s1 - s0;
-    }
-    return u0;
-}
-
 // Esirkepov in 2D on the union window (Eqs. (20)-(22)): W_x = dSx (S0y +
 // dSy/2), W_y = dSy (S0x + dSx/2), and J_z = q w v_z times the time average
 // of the node-shape product, S0xS0y + (dSx S0y + S0x dSy)/2 + dSx dSy/3,
@@ -112,24 +95,6 @@ __device__ __forceinline__ void esirkepov2d(const float (*S0)[4], const float (*
         for (int a = 0; a < 4; a++) acc.add(2, a, b, jvz * (tx[a] * ty[b] + dx12[a] * dS[1][b]));
 }
 
-// current into the shared box as 32-bit fixed point (integer shared-memory
-// atomics are native; float ones are not).  A chunk has at most kChunk
-// particles and each adds at most C = |q w| max(dx_d/dt) in magnitude to a
-// node, so with 2^20/C units per C a node holds at most 2^30: no overflow.
-// Rounding each value to the unit costs at most 2^-21 C per particle and
-// node, below 1e-6 of the node's sum of |contributions| scale.
-struct AccShared {
-    int *base;  // component 0 at (ux, uy) of the window
-    int cs, rs;
-    float scale;
-    __device__ __forceinline__ void add(int c, int a, int b, float v)
-    {
-        // no zero test: a branch per node costs more than the occasional
-        // zero add, and the warp issues the atomic for its other lanes anyway
-        atomicAdd(base + c * cs + b * rs + a, __float2int_rn(v * scale));
-    }
-};
-
 // current straight into HBM (particles whose window left the box)
 struct AccGlobal {
     float *base;
@@ -140,33 +105,6 @@ struct AccGlobal {
         if (v != 0.f) atomicAdd(base + c * cs + (long long)b * rs + a, v);
     }
 };
-
-// Boris (Eqs. (13)-(16)) with the FP32 reciprocal square root and divide
-// of the special-function unit (a few ulp, far inside the FP32 tolerance)
-__device__ __forceinline__ void boris_fast(float &ux, float &uy, float &uz, float ex, float ey, float ez, float bx,
-                                           float by, float bz)
-{
-    float umx = ux + ex, umy = uy + ey, umz = uz + ez;
-    float ginv = rsqrtf(1.0f + umx * umx + umy * umy + umz * umz);
-    float tx = bx * ginv, ty = by * ginv, tz = bz * ginv;
-    float t2 = tx * tx + ty * ty + tz * tz;
-    float upx = umx + (umy * tz - umz * ty);
-    float upy = umy + (umz * tx - umx * tz);
-    float upz = umz + (umx * ty - umy * tx);
-    float f = __fdividef(2.0f, 1.0f + t2);
-    float sx = tx * f, sy = ty * f, sz = tz * f;
-    ux = umx + (upy * sz - upz * sy) + ex;
-    uy = umy + (upz * sx - upx * sz) + ey;
-    uz = umz + (upx * sy - upy * sx) + ez;
-}
-
-__device__ __forceinline__ float inv_gamma_fast(float ux, float uy, float uz)
-{
-    float u2 = ux * ux + uy * uy + uz * uz;
-    if (u2 < 1e8f) return rsqrtf(1.0f + u2);
-    double d2 = (double)ux * ux + (double)uy * uy + (double)uz * uz;  // FP64 island above gamma ~ 1e4
-    return (float)(1.0 / sqrt(1.0 + d2));
-}
 
 template <int T>
 __global__ void __launch_bounds__(kTileThreads, kTileMinBlocks)
@@ -339,262 +277,6 @@ __global__ void __launch_bounds__(kTileThreads, kTileMinBlocks)
 }
 
 // ---------------------------------------------------------------------
-// 3D: tiles of T^3 cells, the same scheme with a 3D box
-//   x: [t0-4, t0+T+4) (float4-aligned rows), y and z: [t0-3, t0+T+3);
-// the box of a tile that touches the domain edge stays inside the padded
-// field box (ghost layers of 4), so staging and flush need no edge tests.
-// Particles are taken in array order (a tile's particles sit in random
-// cells, so consecutive lanes rarely share a current node).
-// ---------------------------------------------------------------------
-template <int T>
-struct Box3 {
-    static constexpr int WX = T + 8, WY = T + 6, WZ = T + 6;
-    static constexpr int RS = WX, PS = WX * WY, N = WX * WY * WZ;
-    static constexpr int SMEM = 9 * N * (int)sizeof(float);  // fields (6) + current (3)
-};
-
-// element k of a small register array without dynamic indexing (selects)
-__device__ __forceinline__ float sel3(const float *v, int k) { return k == 0 ? v[0] : (k == 1 ? v[1] : v[2]); }
-__device__ __forceinline__ float sel4(const float *v, int k)
-{
-    return k == 0 ? v[0] : (k == 1 ? v[1] : (k == 2 ? v[2] : v[3]));
-}
-
-// Eq. (19) in 3D on the shared box.  The z loop is kept rolled: the 3D push
-// body is large, and a fully unrolled one stalls on instruction fetch.
-template <int T>
-__device__ __forceinline__ void gather3d_box(const float *__restrict__ P, const int *o0, const int *icn,
-                                             const float (*wn)[3], const int *ich, const float (*wh)[3], float *eb)
-{
-    using B = Box3<T>;
-#pragma unroll
-    for (int c = 0; c < 6; c++) {
-        const int sx = stag(c, 0), sy = stag(c, 1), sz = stag(c, 2);
-        const int ix = (sx ? ich[0] : icn[0]) - 1 - o0[0];
-        const int iy = (sy ? ich[1] : icn[1]) - 1 - o0[1];
-        const int iz = (sz ? ich[2] : icn[2]) - 1 - o0[2];
-        const float *wx = sx ? wh[0] : wn[0];
-        const float *wy = sy ? wh[1] : wn[1];
-        const float *wz = sz ? wh[2] : wn[2];
-        const float *q = P + c * B::N + iz * B::PS + iy * B::RS + ix;
-        float acc = 0.f;
-#pragma unroll 1
-        for (int cz = 0; cz < 3; cz++) {
-            float sb = 0.f;
-#pragma unroll
-            for (int b = 0; b < 3; b++) {
-                const float *r = q + cz * B::PS + b * B::RS;
-                float s = wx[0] * r[0];
-                s += wx[1] * r[1];
-                s += wx[2] * r[2];
-                sb += wy[b] * s;
-            }
-            acc += sel3(wz, cz) * sb;
-        }
-        eb[c] = acc;
-    }
-}
-
-// Esirkepov in 3D on the union window (Eqs. (20)-(22)): W_x = dSx (ty tz +
-// dSy dSz / 12) with t = S0 + dS/2 (= S0y S0z + (dSy S0z + S0y dSz)/2 +
-// dSy dSz/3), cyclic for y and z; J_d is cJ_d times the prefix sum of W_d
-// along d (three nonzero nodes of the four).  Shared int32 fixed point.
-template <int T>
-__device__ __forceinline__ void esirkepov3d_box(int *base, const float (*S0)[4], const float (*dS)[4], float cjx,
-                                                float cjy, float cjz, float scale)
-{
-    using B = Box3<T>;
-    float t[3][4], p[3][3];
-#pragma unroll
-    for (int d = 0; d < 3; d++) {
-#pragma unroll
-        for (int k = 0; k < 4; k++) t[d][k] = S0[d][k] + 0.5f * dS[d][k];
-        p[d][0] = dS[d][0];
-        p[d][1] = p[d][0] + dS[d][1];
-        p[d][2] = p[d][1] + dS[d][2];
-    }
-    const float cj[3] = {cjx * scale, cjy * scale, cjz * scale};
-    const float r12 = 1.0f / 12.0f;
-    // the outermost loop of each component stays rolled (code size, as in
-    // gather3d_box); its index picks the z (or y) shape by selects
-#pragma unroll 1
-    for (int c = 0; c < 4; c++) {
-        const float tzc = sel4(t[2], c), dzc = sel4(dS[2], c) * r12;
-        int *bc = base + c * B::PS;
-#pragma unroll
-        for (int b = 0; b < 4; b++) {
-            const float wx = fmaf(t[1][b], tzc, dS[1][b] * dzc) * cj[0];
-#pragma unroll
-            for (int a = 0; a < 3; a++) atomicAdd(bc + b * B::RS + a, __float2int_rn(p[0][a] * wx));
-        }
-#pragma unroll
-        for (int a = 0; a < 4; a++) {
-            const float wy = fmaf(t[0][a], tzc, dS[0][a] * dzc) * cj[1];
-#pragma unroll
-            for (int b = 0; b < 3; b++) atomicAdd(bc + B::N + b * B::RS + a, __float2int_rn(p[1][b] * wy));
-        }
-    }
-#pragma unroll 1
-    for (int b = 0; b < 4; b++) {
-        const float tyb = sel4(t[1], b), dyb = sel4(dS[1], b) * r12;
-        int *bb = base + 2 * B::N + b * B::RS;
-#pragma unroll
-        for (int a = 0; a < 4; a++) {
-            const float wz = fmaf(t[0][a], tyb, dS[0][a] * dyb) * cj[2];
-#pragma unroll
-            for (int c = 0; c < 3; c++) atomicAdd(bb + c * B::PS + a, __float2int_rn(p[2][c] * wz));
-        }
-    }
-}
-
-// A particle whose stencil leaves its tile's box (it drifted since the sort)
-// is not pushed here: its index goes to a list, and the list is pushed
-// afterwards on the global path (launch_push_list_f32).  Nothing of the
-// particle is written before that decision, and a warp never waits on one
-// lane's slow path.
-template <int T>
-__global__ void __launch_bounds__(kTileThreads, 5)
-    k_push_tile3d(PartF32 P, const TileItem *__restrict__ items, const uint32_t *__restrict__ nitems,
-                  float *__restrict__ F, Grid g, PushConst pc, int *err, double *e_abs, uint32_t *defer,
-                  uint32_t *ndefer)
-{
-    using B = Box3<T>;
-    extern __shared__ float smem[];
-    float *sF = smem;                                    // 6 components
-    int *sJ = reinterpret_cast<int *>(smem + 6 * B::N);  // 3 components, fixed point
-    const int nit = (int)*nitems;
-    const long long V = g.vol;
-    const float hdx[3] = {pc.hdx_f[0], pc.hdx_f[1], pc.hdx_f[2]};
-    const float k = pc.qmdt2_f;
-    const float cjx = pc.cJ_f[0], cjy = pc.cJ_f[1], cjz = pc.cJ_f[2];
-    // fixed-point unit of the shared current box: 2^20 units per C, C the
-    // largest value one particle adds to a node (see AccShared)
-    const float cmax = fmaxf(fmaxf(fabsf(cjx), fabsf(cjy)), fabsf(cjz));
-    const float jscale = 1048576.0f / fmaxf(cmax, 1e-30f);
-    const float junit = 1.0f / jscale;
-    float *Fg = F + g.origin;
-    const int rs = (int)g.sy, ps = (int)g.sz;
-    for (int it = blockIdx.x; it < nit; it += gridDim.x) {
-        const TileItem m = items[it];
-        const int tx = m.tile % g.ntile[0], ty = (m.tile / g.ntile[0]) % g.ntile[1],
-                  tz = m.tile / (g.ntile[0] * g.ntile[1]);
-        const int o0[3] = {tx * T - 4, ty * T - 3, tz * T - 3};
-        // 1-2. stage fields (float4 rows), zero the current box
-        for (int q = threadIdx.x; q < 6 * B::N / 4; q += blockDim.x) {
-            const int e = 4 * q;
-            const int c = e / B::N, r = e - c * B::N;
-            const int z = r / B::PS, y = (r - z * B::PS) / B::RS, x = r - z * B::PS - y * B::RS;
-            const float *src = Fg + c * V + (long long)(o0[2] + z) * ps + (long long)(o0[1] + y) * rs + o0[0] + x;
-            reinterpret_cast<float4 *>(sF)[q] = __ldg(reinterpret_cast<const float4 *>(src));
-        }
-        for (int q = threadIdx.x; q < 3 * B::N / 4; q += blockDim.x) reinterpret_cast<int4 *>(sJ)[q] = make_int4(0, 0, 0, 0);
-        __syncthreads();
-        // 3. particles
-        for (int li = threadIdx.x; li < m.count; li += blockDim.x) {
-            const int p = m.start + li;
-            const uint32_t cp = P.cell[p];
-            if (cp == kDead) continue;
-            int c[3];
-            unpack_cell(g, cp, c[0], c[1], c[2]);
-            float o[3] = {P.off[0][p], P.off[1][p], P.off[2][p]};
-            float ux = P.u[0][p], uy = P.u[1][p], uz = P.u[2][p];
-            const float ig = inv_gamma_fast(ux, uy, uz);
-            const float u[3] = {ux, uy, uz};
-#pragma unroll
-            for (int d = 0; d < 3; d++) drift_f32(c[d], o[d], hdx[d] * u[d] * ig);
-            const int ch[3] = {c[0], c[1], c[2]};
-            const float oh[3] = {o[0], o[1], o[2]};
-            int icn[3], ich[3];
-            float wn[3][3], wh[3][3];
-            bool gin = true;
-#pragma unroll
-            for (int d = 0; d < 3; d++) {
-                axis_w_f32(c[d], o[d], icn[d], wn[d], ich[d], wh[d]);
-                const int W = d == 0 ? B::WX : B::WY;
-                gin &= ch[d] - 1 >= o0[d] && ch[d] + 2 < o0[d] + W;
-            }
-            if (!gin) {
-                defer[atomicAdd(ndefer, 1u)] = (uint32_t)p;
-                continue;
-            }
-            float eb[6];
-            gather3d_box<T>(sF, o0, icn, wn, ich, wh, eb);
-            boris_fast(ux, uy, uz, k * eb[0], k * eb[1], k * eb[2], k * eb[3], k * eb[4], k * eb[5]);
-            const float ig1 = inv_gamma_fast(ux, uy, uz);
-            const float dd[3] = {hdx[0] * ux * ig1, hdx[1] * uy * ig1, hdx[2] * uz * ig1};
-#pragma unroll
-            for (int d = 0; d < 3; d++) drift_f32(c[d], o[d], dd[d]);
-            const int c1[3] = {c[0], c[1], c[2]};
-            const float o1[3] = {o[0], o[1], o[2]};
-#pragma unroll
-            for (int d = 0; d < 3; d++) drift_f32(c[d], o[d], dd[d]);
-            // Esirkepov on x^{n+1/2} -> x^{n+3/2}
-            int i0[3], i1[3];
-            float w0[3][3], w1[3][3];
-            bool ok = true, din = true;
-            float S0[3][4], dS[3][4];
-            int u0[3];
-#pragma unroll
-            for (int d = 0; d < 3; d++) {
-                axis_wn_f32(ch[d], oh[d], i0[d], w0[d]);
-                axis_wn_f32(c[d], o[d], i1[d], w1[d]);
-                ok &= (i1[d] - i0[d] >= -1 && i1[d] - i0[d] <= 1);
-                u0[d] = union4(i0[d], w0[d], i1[d], w1[d], S0[d], dS[d]);
-                const int W = d == 0 ? B::WX : B::WY;
-                din &= u0[d] >= o0[d] && u0[d] + 3 < o0[d] + W;
-            }
-            if (!ok) {
-                atomicOr(err, ERR_CFL);
-                continue;
-            }
-            if (!din) {
-                defer[atomicAdd(ndefer, 1u)] = (uint32_t)p;
-                continue;
-            }
-            esirkepov3d_box<T>(sJ + (u0[2] - o0[2]) * B::PS + (u0[1] - o0[1]) * B::RS + (u0[0] - o0[0]), S0, dS, cjx,
-                               cjy, cjz, jscale);
-            // boundaries
-            int cc[3] = {c1[0], c1[1], c1[2]};
-            bool dead = false;
-#pragma unroll
-            for (int d = 0; d < 3; d++) {
-                if (g.bc[d] == PERIODIC) {
-                    if (cc[d] < 0) cc[d] += g.n[d];
-                    else if (cc[d] >= g.n[d]) cc[d] -= g.n[d];
-                } else if (cc[d] < 0 || cc[d] >= g.n[d]) {
-                    dead = true;
-                }
-            }
-            if (!isfinite(ux + uy + uz)) atomicOr(err, ERR_NONFINITE);
-            if (dead) {
-                P.cell[p] = kDead;
-                double uu = (double)ux * ux + (double)uy * uy + (double)uz * uz;
-                atomicAdd(e_abs, pc.wmdV * uu / (sqrt(1.0 + uu) + 1.0));
-            } else {
-                P.cell[p] = pack_cell(g, cc[0], cc[1], cc[2]);
-            }
-#pragma unroll
-            for (int d = 0; d < 3; d++) P.off[d][p] = o1[d];
-            P.u[0][p] = ux;
-            P.u[1][p] = uy;
-            P.u[2][p] = uz;
-        }
-        __syncthreads();
-        // 4. flush the current box, four values at a time
-        for (int q = threadIdx.x; q < 3 * B::N / 4; q += blockDim.x) {
-            const int4 iv = reinterpret_cast<const int4 *>(sJ)[q];
-            if ((iv.x | iv.y | iv.z | iv.w) == 0) continue;
-            const int e = 4 * q;
-            const int c = e / B::N, r = e - c * B::N;
-            const int z = r / B::PS, y = (r - z * B::PS) / B::RS, x = r - z * B::PS - y * B::RS;
-            float *dst = Fg + (JX + c) * V + (long long)(o0[2] + z) * ps + (long long)(o0[1] + y) * rs + o0[0] + x;
-            atomicAdd(reinterpret_cast<float4 *>(dst), make_float4(iv.x * junit, iv.y * junit, iv.z * junit, iv.w * junit));
-        }
-        __syncthreads();
-    }
-}
-
-// ---------------------------------------------------------------------
 // work items: chunks of at most `chunk` particles of one tile
 // ---------------------------------------------------------------------
 __global__ void k_item_counts(const uint32_t *__restrict__ starts, long long ntiles, uint32_t chunk, uint32_t *cnt)
@@ -670,39 +352,6 @@ static void launch_T(const PartF32 &P, const TileItem *items, const uint32_t *ni
     if (grid < 1) grid = 1;
     note_launch();
     k_push_tile2d<T><<<(int)grid, kTileThreads, Box2<T>::SMEM, st>>>(P, items, nitems, F, g, pc, err, e_abs);
-}
-
-void launch_push_tile3d(const PartF32 &P, const TileItem *items, const uint32_t *nitems, long long max_items,
-                        float *F, const Grid &g, const PushConst &pc, int *err, double *e_abs, uint32_t *defer,
-                        uint32_t *ndefer, cudaStream_t st)
-{
-    if (P.n == 0) return;
-    cudaMemsetAsync(ndefer, 0, sizeof(uint32_t), st);
-    constexpr int T = 4;
-    static bool attr = false;
-    if (!attr) {
-        cudaFuncSetAttribute(k_push_tile3d<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, Box3<T>::SMEM);
-        attr = true;
-    }
-    static int nsm = 0;
-    if (!nsm) {
-        int dev = 0;
-        cudaGetDevice(&dev);
-        cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
-    }
-    long long grid = std::min<long long>(max_items, (long long)nsm * 5);  // 5 CTAs of 44 KB per SM
-    if (grid < 1) grid = 1;
-    note_launch();
-    k_push_tile3d<T><<<(int)grid, kTileThreads, Box3<T>::SMEM, st>>>(P, items, nitems, F, g, pc, err, e_abs, defer,
-                                                                      ndefer);
-    launch_push_list_f32(P, defer, ndefer, P.n, F, g, pc, err, e_abs, st);
-}
-
-bool tile3d_push_supported(const Grid &g)
-{
-    for (int d = 0; d < 3; d++)
-        if (g.tile_log2[d] != 2 || g.n[d] % 4 != 0 || g.G[d] != 4) return false;
-    return g.dim == 3;
 }
 
 void launch_push_tile2d(const PartF32 &P, const TileItem *items, const uint32_t *nitems, long long max_items,
