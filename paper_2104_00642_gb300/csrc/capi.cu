@@ -531,6 +531,7 @@ int check_flags(pic_sim *s)
         if (h & ERR_CFL) return fail(s, PIC_ERR_CFL, "a particle moved more than one cell in a step");
         if (h & ERR_NONFINITE) return fail(s, PIC_ERR_NONFINITE, "non-finite particle momentum");
         if (h & ERR_CAPACITY) return fail(s, PIC_ERR_CAPACITY, "species capacity exceeded");
+        if (h & ERR_TIMEOUT) return fail(s, PIC_ERR_CUDA, "a bulk copy into shared memory did not complete in time");
     }
     return PIC_OK;
 }

@@ -13,7 +13,10 @@
 // A particle that drifted so far since the sort that its stencil leaves the
 // box is handled on the global path (gather from HBM, global atomics), so the
 // result does not depend on the sort interval.
+#include <cstring>
+
 #include "push_tile_dev.cuh"
+#include "tma.cuh"
 
 namespace pic {
 
@@ -106,13 +109,20 @@ struct AccGlobal {
     }
 };
 
+// With use_tma the field box of an item is one TMA tile copy (tmap: the six
+// field components as a 3D tensor, x fastest), issued by one thread and
+// overlapping the zeroing of the current box and the particle staging.
 template <int T>
 __global__ void __launch_bounds__(kTileThreads, kTileMinBlocks)
     k_push_tile2d(PartF32 P, const TileItem *__restrict__ items, const uint32_t *__restrict__ nitems,
-                  float *__restrict__ F, Grid g, PushConst pc, int *err, double *e_abs)
+                  float *__restrict__ F, Grid g, PushConst pc, int *err, double *e_abs,
+                  const __grid_constant__ CUtensorMap tmap, int use_tma)
 {
     using B = Box2<T>;
-    extern __shared__ float smem[];
+    extern __shared__ float smem_raw[];
+    __shared__ uint64_t mbar;
+    // the TMA destination starts on a 128-byte boundary
+    float *smem = reinterpret_cast<float *>((reinterpret_cast<uintptr_t>(smem_raw) + 127) & ~uintptr_t(127));
     float *sF = smem;           // 6 components
     int *sJ = reinterpret_cast<int *>(smem + 6 * B::N);  // 3 components, fixed point
     float *sP = smem + 9 * B::N;                          // off_x, off_y, u_x, u_y, u_z
@@ -128,18 +138,31 @@ __global__ void __launch_bounds__(kTileThreads, kTileMinBlocks)
     const float junit = 1.0f / jscale;
     float *Fg = F + g.origin;  // interior origin
     const int rs = (int)g.sy;
+    if (use_tma && threadIdx.x == 0) mbar_init(&mbar, 1);
+    __syncthreads();
+    uint32_t phase = 0;
     for (int it = blockIdx.x; it < nit; it += gridDim.x) {
         const TileItem m = items[it];
         const int tx = m.tile % g.ntile[0], ty = m.tile / g.ntile[0];
         const int bx0 = tx * T - 4, by0 = ty * T - 4;
         // 1-2. stage fields, zero the current box
-        for (int q = threadIdx.x; q < 6 * B::N; q += blockDim.x) {
-            const int c = q / B::N, r = q - c * B::N;
-            const int y = r / B::WX, x = r - y * B::WX;
-            const int gx = bx0 + x, gy = by0 + y;
-            float v = 0.f;
-            if (gx < g.n[0] + g.G[0] && gy < g.n[1] + g.G[1]) v = __ldg(Fg + c * V + (long long)gy * rs + gx);
-            sF[q] = v;
+        if (use_tma) {
+            if (threadIdx.x == 0) {
+                // padded coordinates of the box corner; x = tx*T is a multiple
+                // of 4 floats (16 bytes) as the copy engine requires
+                fence_proxy_async_smem();
+                mbar_arrive_expect_tx(&mbar, 6 * B::N * (int)sizeof(float));
+                tma_load_3d(sF, &tmap, bx0 + g.G[0], by0 + g.G[1], 0, &mbar);
+            }
+        } else {
+            for (int q = threadIdx.x; q < 6 * B::N; q += blockDim.x) {
+                const int c = q / B::N, r = q - c * B::N;
+                const int y = r / B::WX, x = r - y * B::WX;
+                const int gx = bx0 + x, gy = by0 + y;
+                float v = 0.f;
+                if (gx < g.n[0] + g.G[0] && gy < g.n[1] + g.G[1]) v = __ldg(Fg + c * V + (long long)gy * rs + gx);
+                sF[q] = v;
+            }
         }
         for (int q = threadIdx.x; q < 3 * B::N; q += blockDim.x) sJ[q] = 0;
         // Lane striding: the chunk is cut into 32 contiguous segments of S
@@ -150,18 +173,30 @@ __global__ void __launch_bounds__(kTileThreads, kTileMinBlocks)
         const int S = (m.count + 31) >> 5;
         // stage the chunk's particle state: every thread issues all its loads
         // at once (coalesced), stored transposed to (segment position, lane)
+        // (asynchronous 4-byte copies: no register round trip)
         for (int i = threadIdx.x; i < m.count; i += blockDim.x) {
             const int l = i / S, j = i - l * S;
             const int pos = j * 33 + l;
             const int p = m.start + i;  // capacities are below 2^31
-            sPc[pos] = P.cell[p];
-            sP[0 * kPSlot + pos] = P.off[0][p];
-            sP[1 * kPSlot + pos] = P.off[1][p];
-            sP[2 * kPSlot + pos] = P.u[0][p];
-            sP[3 * kPSlot + pos] = P.u[1][p];
-            sP[4 * kPSlot + pos] = P.u[2][p];
+            cp_async4(sPc + pos, P.cell + p);
+            cp_async4(sP + 0 * kPSlot + pos, P.off[0] + p);
+            cp_async4(sP + 1 * kPSlot + pos, P.off[1] + p);
+            cp_async4(sP + 2 * kPSlot + pos, P.u[0] + p);
+            cp_async4(sP + 3 * kPSlot + pos, P.u[1] + p);
+            cp_async4(sP + 4 * kPSlot + pos, P.u[2] + p);
         }
-        __syncthreads();
+        cp_async_wait_all();
+        bool landed = true;
+        if (use_tma) {
+            // bounded wait: a copy that never lands sets an error flag and the
+            // CTA stops, all its threads together (the host reports the flag)
+            landed = mbar_wait(&mbar, phase, 1 << 22);
+            phase ^= 1u;
+        }
+        if (__syncthreads_or(!landed)) {
+            if (threadIdx.x == 0) atomicOr(err, ERR_TIMEOUT);
+            return;
+        }
         // 3. particles
         const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
         for (int j = warp; j < S; j += kTileThreads / 32) {
@@ -337,9 +372,10 @@ template <int T>
 static void launch_T(const PartF32 &P, const TileItem *items, const uint32_t *nitems, long long max_items, float *F,
                      const Grid &g, const PushConst &pc, int *err, double *e_abs, cudaStream_t st)
 {
+    constexpr int smem = Box2<T>::SMEM + 128;  // + alignment of the TMA destination
     static bool attr = false;
     if (!attr) {
-        cudaFuncSetAttribute(k_push_tile2d<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, Box2<T>::SMEM);
+        cudaFuncSetAttribute(k_push_tile2d<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
         attr = true;
     }
     static int nsm = 0;
@@ -348,10 +384,16 @@ static void launch_T(const PartF32 &P, const TileItem *items, const uint32_t *ni
         cudaGetDevice(&dev);
         cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
     }
+    // the six field components as one 3D tensor (x, y, component); tiles of
+    // the box shape.  Without a tensor map the kernel stages with loads.
+    CUtensorMap tmap;
+    const int box[3] = {Box2<T>::WX, Box2<T>::WY, 6};
+    const bool tma = tma_encode_field_map(&tmap, F, g.ext[0], g.ext[1], g.sy, g.vol, 6, box);
+    if (!tma) memset(&tmap, 0, sizeof tmap);
     long long grid = std::min<long long>(max_items, (long long)nsm * kTileMinBlocks);  // one resident wave
     if (grid < 1) grid = 1;
     note_launch();
-    k_push_tile2d<T><<<(int)grid, kTileThreads, Box2<T>::SMEM, st>>>(P, items, nitems, F, g, pc, err, e_abs);
+    k_push_tile2d<T><<<(int)grid, kTileThreads, smem, st>>>(P, items, nitems, F, g, pc, err, e_abs, tmap, tma ? 1 : 0);
 }
 
 void launch_push_tile2d(const PartF32 &P, const TileItem *items, const uint32_t *nitems, long long max_items,
