@@ -1,8 +1,10 @@
 // push_tile3d.cu -- tiled particle push for 3D grids (FP32 cell+offset
 // form): the scheme of push_tile.cu with a 3D box.
 #include <algorithm>
+#include <cstring>
 
 #include "push_tile_dev.cuh"
+#include "tma.cuh"
 
 namespace pic {
 
@@ -124,10 +126,13 @@ template <int T>
 __global__ void __launch_bounds__(kTileThreads, 5)
     k_push_tile3d(PartF32 P, const TileItem *__restrict__ items, const uint32_t *__restrict__ nitems,
                   float *__restrict__ F, Grid g, PushConst pc, int *err, double *e_abs, uint32_t *defer,
-                  uint32_t *ndefer)
+                  uint32_t *ndefer, const __grid_constant__ CUtensorMap tmap, int use_tma)
 {
     using B = Box3<T>;
-    extern __shared__ float smem[];
+    extern __shared__ float smem_raw[];
+    __shared__ uint64_t mbar;
+    // the TMA destination starts on a 128-byte boundary
+    float *smem = reinterpret_cast<float *>((reinterpret_cast<uintptr_t>(smem_raw) + 127) & ~uintptr_t(127));
     float *sF = smem;                                    // 6 components
     int *sJ = reinterpret_cast<int *>(smem + 6 * B::N);  // 3 components, fixed point
     const int nit = (int)*nitems;
@@ -142,21 +147,41 @@ __global__ void __launch_bounds__(kTileThreads, 5)
     const float junit = 1.0f / jscale;
     float *Fg = F + g.origin;
     const int rs = (int)g.sy, ps = (int)g.sz;
+    if (use_tma && threadIdx.x == 0) mbar_init(&mbar, 1);
+    __syncthreads();
+    uint32_t phase = 0;
     for (int it = blockIdx.x; it < nit; it += gridDim.x) {
         const TileItem m = items[it];
         const int tx = m.tile % g.ntile[0], ty = (m.tile / g.ntile[0]) % g.ntile[1],
                   tz = m.tile / (g.ntile[0] * g.ntile[1]);
         const int o0[3] = {tx * T - 4, ty * T - 3, tz * T - 3};
-        // 1-2. stage fields (float4 rows), zero the current box
-        for (int q = threadIdx.x; q < 6 * B::N / 4; q += blockDim.x) {
-            const int e = 4 * q;
-            const int c = e / B::N, r = e - c * B::N;
-            const int z = r / B::PS, y = (r - z * B::PS) / B::RS, x = r - z * B::PS - y * B::RS;
-            const float *src = Fg + c * V + (long long)(o0[2] + z) * ps + (long long)(o0[1] + y) * rs + o0[0] + x;
-            reinterpret_cast<float4 *>(sF)[q] = __ldg(reinterpret_cast<const float4 *>(src));
+        // 1-2. stage fields (one TMA tile: x padded coordinate tx*T, a
+        // multiple of 4 floats; else float4 rows), zero the current box
+        if (use_tma) {
+            if (threadIdx.x == 0) {
+                fence_proxy_async_smem();
+                mbar_arrive_expect_tx(&mbar, 6 * B::N * (int)sizeof(float));
+                tma_load_4d(sF, &tmap, o0[0] + g.G[0], o0[1] + g.G[1], o0[2] + g.G[2], 0, &mbar);
+            }
+        } else {
+            for (int q = threadIdx.x; q < 6 * B::N / 4; q += blockDim.x) {
+                const int e = 4 * q;
+                const int c = e / B::N, r = e - c * B::N;
+                const int z = r / B::PS, y = (r - z * B::PS) / B::RS, x = r - z * B::PS - y * B::RS;
+                const float *src = Fg + c * V + (long long)(o0[2] + z) * ps + (long long)(o0[1] + y) * rs + o0[0] + x;
+                reinterpret_cast<float4 *>(sF)[q] = __ldg(reinterpret_cast<const float4 *>(src));
+            }
         }
         for (int q = threadIdx.x; q < 3 * B::N / 4; q += blockDim.x) reinterpret_cast<int4 *>(sJ)[q] = make_int4(0, 0, 0, 0);
-        __syncthreads();
+        bool landed = true;
+        if (use_tma) {
+            landed = mbar_wait(&mbar, phase, 1 << 22);
+            phase ^= 1u;
+        }
+        if (__syncthreads_or(!landed)) {
+            if (threadIdx.x == 0) atomicOr(err, ERR_TIMEOUT);
+            return;
+        }
         // 3. particles
         for (int li = threadIdx.x; li < m.count; li += blockDim.x) {
             const int p = m.start + li;
@@ -269,9 +294,10 @@ void launch_push_tile3d(const PartF32 &P, const TileItem *items, const uint32_t 
     if (P.n == 0) return;
     cudaMemsetAsync(ndefer, 0, sizeof(uint32_t), st);
     constexpr int T = 4;
+    constexpr int smem = Box3<T>::SMEM + 128;  // + alignment of the TMA destination
     static bool attr = false;
     if (!attr) {
-        cudaFuncSetAttribute(k_push_tile3d<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, Box3<T>::SMEM);
+        cudaFuncSetAttribute(k_push_tile3d<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
         attr = true;
     }
     static int nsm = 0;
@@ -280,11 +306,16 @@ void launch_push_tile3d(const PartF32 &P, const TileItem *items, const uint32_t 
         cudaGetDevice(&dev);
         cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
     }
+    // the six field components as one 4D tensor (x, y, z, component)
+    CUtensorMap tmap;
+    const int box[4] = {Box3<T>::WX, Box3<T>::WY, Box3<T>::WZ, 6};
+    const bool tma = tma_encode_field_map3(&tmap, F, g.ext, g.sy, g.sz, g.vol, 6, box);
+    if (!tma) memset(&tmap, 0, sizeof tmap);
     long long grid = std::min<long long>(max_items, (long long)nsm * 5);  // 5 CTAs of 44 KB per SM
     if (grid < 1) grid = 1;
     note_launch();
-    k_push_tile3d<T><<<(int)grid, kTileThreads, Box3<T>::SMEM, st>>>(P, items, nitems, F, g, pc, err, e_abs, defer,
-                                                                      ndefer);
+    k_push_tile3d<T><<<(int)grid, kTileThreads, smem, st>>>(P, items, nitems, F, g, pc, err, e_abs, defer, ndefer,
+                                                             tmap, tma ? 1 : 0);
     launch_push_list_f32(P, defer, ndefer, P.n, F, g, pc, err, e_abs, st);
 }
 

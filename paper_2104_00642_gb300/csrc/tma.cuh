@@ -40,6 +40,17 @@ __device__ __forceinline__ void tma_load_3d(void *dst, const CUtensorMap *map, i
         : "memory");
 }
 
+// one tile of a 4D tensor (x fastest; x * element size a multiple of 16 bytes)
+__device__ __forceinline__ void tma_load_4d(void *dst, const CUtensorMap *map, int x, int y, int z, int w,
+                                            uint64_t *bar)
+{
+    asm volatile(
+        "cp.async.bulk.tensor.4d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4, %5}], "
+        "[%6];" ::"r"(smem_u32(dst)),
+        "l"(map), "r"(x), "r"(y), "r"(z), "r"(w), "r"(smem_u32(bar))
+        : "memory");
+}
+
 // wait for the barrier phase with the given parity; gives up after
 // max_tries polls (each poll may suspend the thread for a short while) and
 // returns false then
@@ -72,5 +83,9 @@ __device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wai
 // false when the driver refuses the description.
 bool tma_encode_field_map(CUtensorMap *map, const float *base, int ext0, int ext1, long long pitch, long long vol,
                           int ncomp, const int *box);
+// the same for 3D arrays: ext[3] (x fastest), strides sy, sz and vol in floats,
+// tiles box[0..3] (x, y, z, component)
+bool tma_encode_field_map3(CUtensorMap *map, const float *base, const int *ext, long long sy, long long sz,
+                           long long vol, int ncomp, const int *box);
 
 }  // namespace pic
