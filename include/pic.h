@@ -195,7 +195,7 @@ int pic_qed_eval(pic_sim *sim, int process, int64_t n, const double *chi, const 
  * --------------------------------------------------------------------- */
 #define PIC_MLP_NPARAMS 8642
 typedef struct {
-    int64_t iterations;      /* Adam steps (0: 20000) */
+    int64_t iterations;      /* Adam steps (0: 40000) */
     int64_t batch;           /* samples per step, a multiple of 128 (0: 16384) */
     double lr, lr_final;     /* cosine schedule from lr to lr_final (0: 1e-2, 1e-4) */
     double chi_min, chi_max; /* trained range (0: 1e-3..1e2 emission, 1e-2..1e2 pairs) */

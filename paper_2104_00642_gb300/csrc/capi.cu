@@ -1149,7 +1149,7 @@ int mlp_scratch(pic_sim *s, long long B)
     if (B <= S.B) return PIC_OK;
     void *buf = nullptr;
     const size_t per_row = (size_t)(3 * 2 + 6 * kMlpH) * sizeof(float);
-    int rc = dalloc(s, &buf, per_row * (size_t)B);
+    int rc = dalloc(s, &buf, per_row * (size_t)B + mlp_partial_floats(B) * sizeof(float));
     if (rc) return rc;
     float *f = (float *)buf;
     S.X = f;
@@ -1159,6 +1159,7 @@ int mlp_scratch(pic_sim *s, long long B)
         S.Z.z[l] = f + 6 * B + (size_t)l * kMlpH * B;
         S.D.z[l] = f + 6 * B + (size_t)(3 + l) * kMlpH * B;
     }
+    S.partials = f + 6 * B + (size_t)6 * kMlpH * B;
     S.B = B;
     return PIC_OK;
 }
@@ -1242,7 +1243,7 @@ int pic_mlp_train(pic_sim *s, int p, const pic_mlp_train_opts *o, pic_mlp_report
     if (!s || !o) return PIC_ERR_ARG;
     int rc = mlp_check(s, p);
     if (rc) return rc;
-    const long long iters = o->iterations > 0 ? o->iterations : 20000;
+    const long long iters = o->iterations > 0 ? o->iterations : 40000;
     const long long B = o->batch > 0 ? o->batch : 16384;
     const double chi_min = o->chi_min > 0 ? o->chi_min : (p == QED_PAIR ? 1e-2 : 1e-3);
     const double chi_max = o->chi_max > 0 ? o->chi_max : 1e2;
@@ -1285,7 +1286,7 @@ int pic_mlp_train(pic_sim *s, int p, const pic_mlp_train_opts *o, pic_mlp_report
     if (e == cudaSuccess) e = cudaEventCreate(&e1);
     if (e == cudaSuccess) e = cudaEventRecord(e0, ts);
     for (long long i = 0; i < iters && e == cudaSuccess; i++) e = cudaGraphLaunch(ge, ts);
-    note_launch(6 * (iters - 1));  // the captured iteration counted its six launches once
+    note_launch(7 * (iters - 1));  // the captured iteration counted its seven launches once
     if (e == cudaSuccess) e = cudaEventRecord(e1, ts);
     if (e == cudaSuccess) e = cudaStreamSynchronize(ts);
     float ms = 0.f, loss[2] = {0.f, 0.f};
@@ -1392,7 +1393,7 @@ int pic_mlp_grad(pic_sim *s, int p, int64_t n, const float *x, const float *t, f
     CK(cudaMemsetAsync(net.G, 0, (size_t)kMlpNParams * sizeof(float), s->st));
     CK(cudaMemsetAsync(S.loss, 0, sizeof(float), s->st));
     launch_mlp_forward(net.img, n, S.X, S.Z, S.Y, s->st);
-    launch_mlp_backward(net.img, n, S.X, S.T, S.Y, S.Z, S.D, net.G, 1.0f, S.loss, s->st);
+    launch_mlp_backward(net.img, n, S.X, S.T, S.Y, S.Z, S.D, S.partials, net.G, 1.0f, S.loss, s->st);
     CK(cudaGetLastError());
     float l = 0.f;
     CK(cudaMemcpyAsync(grad, net.G, (size_t)kMlpNParams * sizeof(float), cudaMemcpyDeviceToHost, s->st));

@@ -105,9 +105,12 @@ __global__ void __launch_bounds__(128) k_mlp_fwd(const MlpImage *img, long long 
         }
 }
 
+// head: per-warp partials of dW3 (128), db3 (2) and the loss (1)
+constexpr int kHeadPartial = 2 * kMlpH + 3;
+
 __global__ void __launch_bounds__(128) k_mlp_bwd(const MlpImage *img, long long B, const float *__restrict__ Tg,
-                                                 const float *__restrict__ Y, MlpZ Z, MlpZ D, float *__restrict__ grad,
-                                                 float w_rate, float *loss)
+                                                 const float *__restrict__ Y, MlpZ Z, MlpZ D, float *__restrict__ head,
+                                                 float w_rate)
 {
     extern __shared__ __align__(16) unsigned char smem[];
     mlp_stage(smem, img, kMlpTrainStageBytes);
@@ -152,6 +155,9 @@ __global__ void __launch_bounds__(128) k_mlp_bwd(const MlpImage *img, long long 
                 }
                 *reinterpret_cast<float2 *>(&D.z[2][row * kMlpH + c]) = make_float2(d[m][nt][2 * h], d[m][nt][2 * h + 1]);
             }
+    // this warp's partial sums of the head gradient and the loss (summed over
+    // warps in a fixed order by k_mlp_reduce: training is deterministic)
+    float *ph = head + (row0 / 32) * kHeadPartial;
 #pragma unroll
     for (int o = 0; o < 2; o++)
 #pragma unroll
@@ -160,7 +166,7 @@ __global__ void __launch_bounds__(128) k_mlp_bwd(const MlpImage *img, long long 
             v += __shfl_xor_sync(0xffffffffu, v, 4);
             v += __shfl_xor_sync(0xffffffffu, v, 8);
             v += __shfl_xor_sync(0xffffffffu, v, 16);
-            if (g == 0) atomicAdd(&grad[kOffW3 + o * kMlpH + 8 * (q >> 1) + 2 * t + (q & 1)], v);
+            if (g == 0) ph[o * kMlpH + 8 * (q >> 1) + 2 * t + (q & 1)] = v;
         }
     // db3 and the loss: the quad's lanes hold the same rows; count lane t == 0
 #pragma unroll
@@ -168,12 +174,12 @@ __global__ void __launch_bounds__(128) k_mlp_bwd(const MlpImage *img, long long 
         float v = t == 0 ? dy[0][o] + dy[1][o] + dy[2][o] + dy[3][o] : 0.f;
 #pragma unroll
         for (int sh = 16; sh > 0; sh >>= 1) v += __shfl_xor_sync(0xffffffffu, v, sh);
-        if (lane == 0) atomicAdd(&grad[kOffB3 + o], v);
+        if (lane == 0) ph[2 * kMlpH + o] = v;
     }
     lsum = t == 0 ? lsum : 0.f;
 #pragma unroll
     for (int sh = 16; sh > 0; sh >>= 1) lsum += __shfl_xor_sync(0xffffffffu, lsum, sh);
-    if (lane == 0) atomicAdd(loss, lsum);
+    if (lane == 0) ph[2 * kMlpH + 2] = lsum;
     // D2 = (D3 W2) * silu'(z2), D1 = (D2 W1) * silu'(z1), on the tensor
     // cores, one m-tile at a time
     uint32_t A[4][4];
@@ -204,10 +210,14 @@ __global__ void __launch_bounds__(128) k_mlp_bwd(const MlpImage *img, long long 
 // in_0 = X (K = 2), in_l = bf16(silu(Z_l)) as the forward fed the tensor
 // cores.  blockIdx.y = l; blocks stride over 64-row chunks staged in shared
 // memory; each thread owns a 4 x 4 tile of (j, k), two float4 loads per row.
+// Each block writes its partial sums (packed parameter order, layers 0-2)
+// to its own row of `part`; k_mlp_reduce adds the rows in a fixed order.
 constexpr int kWgRows = 64;
+constexpr int kWgBlocks = 64;
 __global__ void __launch_bounds__(256) k_mlp_wgrad(long long B, const float *__restrict__ X, MlpZ Z, MlpZ D,
-                                                   float *__restrict__ grad)
+                                                   float *__restrict__ part)
 {
+    float *grad = part + (size_t)blockIdx.x * kOffW3;
     __shared__ __align__(16) float Ds[kWgRows][kMlpH];
     __shared__ __align__(16) float As[kWgRows][kMlpH];
     const int l = blockIdx.y, kin = l == 0 ? 2 : kMlpH;
@@ -257,8 +267,27 @@ __global__ void __launch_bounds__(256) k_mlp_wgrad(long long B, const float *__r
     for (int p = 0; p < 4; p++) {
 #pragma unroll
         for (int q = 0; q < 4; q++)
-            if (k0 + q < kin) atomicAdd(&grad[offW + (j0 + p) * kin + k0 + q], acc[p][q]);
-        if (k0 == 0) atomicAdd(&grad[offB + j0 + p], bacc[p]);
+            if (k0 + q < kin) grad[offW + (j0 + p) * kin + k0 + q] = acc[p][q];
+        if (k0 == 0) grad[offB + j0 + p] = bacc[p];
+    }
+}
+
+// the gradient and the loss from the partial sums, in a fixed order:
+// layers 0-2 over the wgrad blocks, the head and the loss over the warps
+__global__ void k_mlp_reduce(const float *__restrict__ part, int nblk, const float *__restrict__ head, int nwarp,
+                             float *__restrict__ grad, float *loss)
+{
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < kOffW3) {
+        float s = 0.f;
+        for (int b = 0; b < nblk; b++) s += part[(size_t)b * kOffW3 + i];
+        grad[i] = s;
+    } else if (i < kMlpNParams + 1) {
+        const int q = i - kOffW3;  // 0..129: dW3, db3; 130: the loss
+        float s = 0.f;
+        for (int w = 0; w < nwarp; w++) s += head[(size_t)w * kHeadPartial + q];
+        if (i < kMlpNParams) grad[i] = s;
+        else *loss = s;
     }
 }
 
@@ -380,14 +409,18 @@ void launch_mlp_forward(const MlpImage *img, long long B, const float *X, const 
     k_mlp_fwd<<<div_up_i(B, 128), 128, kMlpStageBytes, st>>>(img, B, X, Z, Y);
 }
 
+size_t mlp_partial_floats(long long B) { return (size_t)kWgBlocks * kOffW3 + (size_t)(B / 32) * kHeadPartial; }
+
 void launch_mlp_backward(const MlpImage *img, long long B, const float *X, const float *Tg, const float *Y,
-                         const MlpZ &Z, const MlpZ &D, float *grad, float w_rate, float *loss, cudaStream_t st)
+                         const MlpZ &Z, const MlpZ &D, float *partials, float *grad, float w_rate, float *loss,
+                         cudaStream_t st)
 {
-    note_launch(2);
-    k_mlp_bwd<<<div_up_i(B, 128), 128, kMlpTrainStageBytes, st>>>(img, B, Tg, Y, Z, D, grad, w_rate, loss);
-    // each block flushes 4160 float atomics: about one block per SM per layer
-    const int nb = std::min(div_up_i(B, kWgRows), 64);
-    k_mlp_wgrad<<<dim3(nb, 3), 256, 0, st>>>(B, X, Z, D, grad);
+    float *part = partials, *head = partials + (size_t)kWgBlocks * kOffW3;
+    note_launch(3);
+    k_mlp_bwd<<<div_up_i(B, 128), 128, kMlpTrainStageBytes, st>>>(img, B, Tg, Y, Z, D, head, w_rate);
+    const int nb = std::min(div_up_i(B, kWgRows), kWgBlocks);
+    k_mlp_wgrad<<<dim3(nb, 3), 256, 0, st>>>(B, X, Z, D, part);
+    k_mlp_reduce<<<div_up_i(kMlpNParams + 1, 256), 256, 0, st>>>(part, nb, head, (int)(B / 32), grad, loss);
 }
 
 void mlp_train_iteration(MlpNet &net, MlpScratch &S, const QedTables &T, int p, const uint32_t *key,
@@ -396,7 +429,7 @@ void mlp_train_iteration(MlpNet &net, MlpScratch &S, const QedTables &T, int p, 
     note_launch();
     k_mlp_data<<<div_up_i(S.B, 256), 256, 0, st>>>(T, p, net.nrm, key[0], key[1], S.it, S.B, S.X, S.T);
     launch_mlp_forward(net.img, S.B, S.X, S.Z, S.Y, st);
-    launch_mlp_backward(net.img, S.B, S.X, S.T, S.Y, S.Z, S.D, net.G, w_rate, S.loss, st);
+    launch_mlp_backward(net.img, S.B, S.X, S.T, S.Y, S.Z, S.D, S.partials, net.G, w_rate, S.loss, st);
     note_launch(2);
     k_mlp_adam<<<div_up_i(kMlpNParams, 256), 256, 0, st>>>(net.P, net.M, net.V, net.G, net.img, S.it, a);
     k_mlp_tick<<<1, 1, 0, st>>>(S.it, S.loss, S.loss + 1);

@@ -21,10 +21,14 @@ struct MlpScratch {
     long long B = 0;
     float *X = nullptr, *T = nullptr, *Y = nullptr;  // [B][2]
     MlpZ Z{}, D{};                                   // [B][64] each
-    float *loss = nullptr;                           // [0] running, [1] last iteration
+    float *loss = nullptr;                           // [0] this iteration, [1] the last one
     int *it = nullptr;                               // iteration counter
     double *acc = nullptr;                           // validation accumulators (4)
+    float *partials = nullptr;                       // per-block / per-warp gradient partials
 };
+
+// floats of gradient partials a batch of B rows needs (mlp_partial_floats)
+size_t mlp_partial_floats(long long B);
 
 struct MlpAdam {
     long long iters;
@@ -36,8 +40,11 @@ struct MlpAdam {
 static_assert(kMlpTrainStageBytes <= 48 * 1024, "no opt-in needed");
 void launch_mlp_image(const float *P, MlpImage *img, cudaStream_t st);
 void launch_mlp_forward(const MlpImage *img, long long B, const float *X, const MlpZ &Z, float *Y, cudaStream_t st);
+// backward pass, weight gradients and their fixed-order reduction into grad
+// (overwritten) and *loss (overwritten); partials: mlp_partial_floats(B)
 void launch_mlp_backward(const MlpImage *img, long long B, const float *X, const float *Tg, const float *Y,
-                         const MlpZ &Z, const MlpZ &D, float *grad, float w_rate, float *loss, cudaStream_t st);
+                         const MlpZ &Z, const MlpZ &D, float *partials, float *grad, float w_rate, float *loss,
+                         cudaStream_t st);
 void mlp_train_iteration(MlpNet &net, MlpScratch &S, const QedTables &T, int p, const uint32_t *key,
                          const MlpAdam &a, float w_rate, cudaStream_t st);
 void launch_mlp_eval(const MlpImage *img, long long n, const float *X, float *Y, cudaStream_t st);
