@@ -8,8 +8,11 @@ A "step" is one full PIC step (both field half steps, gather + Boris + drift
 + Esirkepov deposit of every particle, current fold, tile sort every K steps).
 
 Prints one JSON line.  ``value`` is particle-steps/s measured with CUDA events
-on the simulation's stream over K timed steps (L2 flushed before each step),
-inputs resident in HBM.  ``e2e`` is the same metric through the public C ABI
+on the simulation's stream around one ``pic_step(K)`` call, inputs resident
+in HBM; every step touches more bytes than the 126 MiB L2 holds (the line's
+``config.l2`` states how many), else the K steps are single calls with the
+L2 flushed before each.  ``per_step_l2_flushed`` repeats the measurement one
+step per call with the L2 flushed before each step.  ``e2e`` is the same metric through the public C ABI
 from pinned host arrays (particle upload, K steps, diagnostics read back).
 ``--impl reference`` times the FP64 CPU oracle instead (host cores).
 """
@@ -68,6 +71,19 @@ def bytes_per_particle(dim, precision):
     if precision == 0:
         return 2 * (4 + 4 * dim + 12)
     return 2 * (4 + 8 * dim + 24)
+
+
+L2_BYTES = 126 * 1024 * 1024  # GB300 L2
+
+
+def step_bytes(w, precision=0):
+    """bytes one step touches at least: the particle state of every species
+    (read and written once) and the nine field components of the padded grid"""
+    ext = 1
+    for d in range(w.dim):
+        ext *= w.n[d] + 8
+    state = bytes_per_particle(w.dim, precision) // 2
+    return sum(s.n for s in w.species) * state + 9 * (8 if precision else 4) * ext
 
 
 def occupied_cells(w):
@@ -206,7 +222,7 @@ def photon_spectrum(sim, sp, edges):
     return np.histogram(k, edges)[0]
 
 
-def run_qed(args, w, pic, torch, stream, timed, rank, world, dist, local):
+def run_qed(args, w, pic, torch, stream, timed, rank, world, dist, local, l2_note):
     """The strong-field QED collision: the same seeded beam through three
     forms, each advanced untimed to the collision, then W warm-up and K timed
     steps around the pulse peak: FP32 cell+offset with the surrogate networks
@@ -281,7 +297,7 @@ def run_qed(args, w, pic, torch, stream, timed, rank, world, dist, local):
                           "window": f"steps {pre + args.warmup}..{pre + args.warmup + K} around the collision "
                                     f"(step {w.notes['steps_to_collision']})",
                           "sort_interval": args.sort_interval, "replicas": world,
-                          "l2": "flushed (256 MiB write) before every timed step" if not args.no_flush else "not flushed"},
+                          "l2": l2_note()},
                "fp32_table": tab and {"value": tab["value"], "ms_per_step": tab["ms_per_step"],
                                       "error_vs_fp64": errors(tab)},
                "fp64_plain": f64 and {"value": f64["value"], "ms_per_step": f64["ms_per_step"],
@@ -308,6 +324,8 @@ def main():
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU baseline leg")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-flush", action="store_true")
+    ap.add_argument("--per-step", action="store_true",
+                    help="time single-step calls with the L2 flushed before each, whatever the workload size")
     ap.add_argument("--no-fp64", action="store_true", help="skip the plain FP64 form")
     ap.add_argument("--qed-beam", type=int, default=10_000_000, help="beam macro-electrons (qed_collision_2d)")
     ap.add_argument("--rows", type=int, default=None,
@@ -337,25 +355,43 @@ def main():
     npart = w.n_particles
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
 
-    def timed(sim, K, profile=False):
-        """K steps, each bracketed by CUDA events on the simulation's stream.
+    continuous = not args.per_step and step_bytes(w) > L2_BYTES
+
+    def l2_note():
+        if continuous:
+            return (f"not flushed: inputs larger than L2 (each step touches {step_bytes(w) / 1e6:.0f} MB, "
+                    f"L2 {L2_BYTES / 1e6:.0f} MB); K steps in one pic_step call")
+        return "flushed (256 MiB write) before every timed step" if not args.no_flush else "not flushed"
+
+    def timed(sim, K, profile=False, per_step=None):
+        """K steps between CUDA events on the simulation's stream: one
+        pic_step(K) call when the workload outgrows the L2 (continuous),
+        else K single-step calls with the L2 flushed before each.
         profile: the timed region proper; per-phase events on, and the CUDA
         profiler range opened (an ncu run with --profile-from-start off
         captures these launches only)."""
+        one_call = continuous if per_step is None else not per_step
         if profile:
             sim.pic_profile(True)
             torch.cuda.synchronize()
             torch.cuda.profiler.start()
         evs = []
         with torch.cuda.stream(stream):
-            for _ in range(K):
-                if not args.no_flush:
-                    flush.fill_(1.0)  # evict L2 between steps
+            if one_call:
                 a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
                 a.record(stream)
-                sim.pic_step(1)
+                sim.pic_step(K)
                 b.record(stream)
                 evs.append((a, b))
+            else:
+                for _ in range(K):
+                    if not args.no_flush:
+                        flush.fill_(1.0)  # evict L2 between steps
+                    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                    a.record(stream)
+                    sim.pic_step(1)
+                    b.record(stream)
+                    evs.append((a, b))
         torch.cuda.synchronize()
         if profile:
             torch.cuda.profiler.stop()
@@ -366,7 +402,7 @@ def main():
         return ms, prof
 
     if args.workload == "qed_collision_2d":
-        run_qed(args, w, pic, torch, stream, timed, rank, world, dist, local)
+        run_qed(args, w, pic, torch, stream, timed, rank, world, dist, local, l2_note)
         if dist:
             dist.barrier()
             dist.destroy_process_group()
@@ -388,6 +424,11 @@ def main():
         dist.all_reduce(tt, op=dist.ReduceOp.MAX)
         t = float(tt.item())
     value = world * npart * args.steps / t
+    flushed = None
+    if continuous:
+        ms_f, _ = timed(sim, args.steps, per_step=True)
+        flushed = {"value": npart * args.steps / (float(np.sum(ms_f)) / 1e3), "unit": UNIT,
+                   "ms_per_step": float(np.mean(ms_f)), "note": "this rank, one step per call, L2 flushed before each"}
     diag = sim.pic_diagnostics()
     if not all(math.isfinite(v) for v in (diag["U_E"], diag["U_B"])):
         raise SystemExit("non-finite diagnostics")
@@ -418,7 +459,7 @@ def main():
         ms64, _ = timed(sim64, args.fp64_steps)
         v64 = npart * args.fp64_steps / (float(np.sum(ms64)) / 1e3)
         sim64.close()
-        fp64 = {"value": v64, "unit": UNIT, "ms_per_step": float(np.mean(ms64)),
+        fp64 = {"value": v64, "unit": UNIT, "ms_per_step": float(np.sum(ms64)) / args.fp64_steps,
                 "fp32_over_fp64": value / world / v64}
 
     # ---- end to end through the C ABI from pinned host arrays --------------
@@ -468,8 +509,8 @@ def main():
                "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
                "config": {"workload": describe(w), "precision": "fp32 cell+offset (FP64 islands: diagnostics)",
                           "sort_interval": args.sort_interval,
-                          "l2": "flushed (256 MiB write) before every timed step" if not args.no_flush else "not flushed",
-                          "replicas": world, "qed": "off (no QED in this workload)"},
+                          "l2": l2_note(), "replicas": world, "qed": "off (no QED in this workload)"},
+               "per_step_l2_flushed": flushed,
                "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches,
                "clocks": clk.summary(),
                "fp64_plain": fp64,

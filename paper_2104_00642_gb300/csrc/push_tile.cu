@@ -202,7 +202,6 @@ __global__ void __launch_bounds__(kTileThreads, kTileMinBlocks)
         for (int j = warp; j < S; j += kTileThreads / 32) {
             const int li = lane * S + j;
             if (li >= m.count) continue;
-            const int p = m.start + li;
             const int pos = j * 33 + lane;
             const uint32_t cp = sPc[pos];
             if (cp == kDead) continue;
@@ -273,20 +272,36 @@ __global__ void __launch_bounds__(kTileThreads, kTileMinBlocks)
             }
             if (!isfinite(ux + uy + uz)) atomicOr(err, ERR_NONFINITE);
             if (dead) {
-                P.cell[p] = kDead;
+                sPc[pos] = kDead;
                 double uu = (double)ux * ux + (double)uy * uy + (double)uz * uz;
                 atomicAdd(e_abs, pc.wmdV * uu / (sqrt(1.0 + uu) + 1.0));
             } else {
-                P.cell[p] = pack_cell(g, cc[0], cc[1], 0);
+                sPc[pos] = pack_cell(g, cc[0], cc[1], 0);
             }
-            P.off[0][p] = o1[0];
-            P.off[1][p] = o1[1];
-            P.u[0][p] = ux;
-            P.u[1][p] = uy;
-            P.u[2][p] = uz;
+            // the new state goes back to the particle's own staging slot and
+            // leaves in array order below: lane-strided global stores would
+            // touch 32 sectors per instruction
+            sP[pos] = o1[0];
+            sP[kPSlot + pos] = o1[1];
+            sP[2 * kPSlot + pos] = ux;
+            sP[3 * kPSlot + pos] = uy;
+            sP[4 * kPSlot + pos] = uz;
         }
         __syncthreads();
-        // 4. flush the current box, four values at a time
+        // 4a. write the chunk's state back, coalesced (particles skipped above
+        // keep their staged values)
+        for (int i = threadIdx.x; i < m.count; i += blockDim.x) {
+            const int l = i / S, j = i - l * S;
+            const int pos = j * 33 + l;
+            const int p = m.start + i;
+            P.cell[p] = sPc[pos];
+            P.off[0][p] = sP[pos];
+            P.off[1][p] = sP[kPSlot + pos];
+            P.u[0][p] = sP[2 * kPSlot + pos];
+            P.u[1][p] = sP[3 * kPSlot + pos];
+            P.u[2][p] = sP[4 * kPSlot + pos];
+        }
+        // 4b. flush the current box, four values at a time
         for (int q = threadIdx.x; q < 3 * B::N / 4; q += blockDim.x) {
             const int4 iv = reinterpret_cast<const int4 *>(sJ)[q];
             if ((iv.x | iv.y | iv.z | iv.w) == 0) continue;
