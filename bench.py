@@ -57,6 +57,8 @@ def make_workload(name, rank=0, sample=None, beam=10_000_000):
         return W.langmuir_1d()
     if name == "qed_collision_2d":
         return W.qed_collision_2d(seed=W.SEED0 + 7 + 1000 * rank, n_beam=beam)
+    if name == "qed_foil_3d":
+        return W.qed_foil_3d(seed=W.SEED0 + 8 + 1000 * rank)
     raise SystemExit(f"unknown workload {name}")
 
 
@@ -231,7 +233,13 @@ def run_qed(args, w, pic, torch, stream, timed, rank, world, dist, local, l2_not
     of all species (trapezoid over the window).  Errors of the two FP32 forms
     are stated against the FP64 run: energies and the photon spectrum."""
     K = args.steps
-    pre = max(0, w.notes["steps_to_collision"] - K // 2 - args.warmup)
+    if args.qed_pre is not None:
+        pre = args.qed_pre
+    elif "steps_to_collision" in w.notes:
+        pre = max(0, w.notes["steps_to_collision"] - K // 2 - args.warmup)
+    else:
+        pre = 0
+    iph, iel, ipo = w.qed["photon_sp"], w.qed["electron_sp"], w.qed["positron_sp"]
     edges = np.logspace(np.log10(w.qed["photon_emin"]), np.log10(3000.0), 25)
     runs = {}
     modes = [m for m in args.qed_modes.split(",") if m]
@@ -275,13 +283,18 @@ def run_qed(args, w, pic, torch, stream, timed, rank, world, dist, local, l2_not
         big = ref["spectrum"] >= 1000
         spec = np.abs(r["spectrum"][big] / ref["spectrum"][big] - 1.0)
         return {"total_energy_rel": abs(e_tot(r) / e_tot(ref) - 1.0),
-                "photon_energy_rel": abs(r["U_kin"][2] / ref["U_kin"][2] - 1.0) if ref["U_kin"][2] else None,
-                "electron_energy_rel": abs(r["U_kin"][0] / ref["U_kin"][0] - 1.0),
-                "photon_count_rel": abs(r["n_alive"][2] / max(ref["n_alive"][2], 1) - 1.0),
-                "pairs": (int(r["n_alive"][1]), int(ref["n_alive"][1])),
+                "photon_energy_rel": abs(r["U_kin"][iph] / ref["U_kin"][iph] - 1.0) if ref["U_kin"][iph] else None,
+                "electron_energy_rel": abs(r["U_kin"][iel] / ref["U_kin"][iel] - 1.0),
+                "photon_count_rel": abs(r["n_alive"][iph] / max(ref["n_alive"][iph], 1) - 1.0),
+                "pairs": (int(r["n_alive"][ipo]), int(ref["n_alive"][ipo])),
                 "photon_spectrum_max_bin_rel": float(spec.max()) if big.any() else None,
                 "photon_spectrum_bins": int(big.sum())}
 
+    if "steps_to_collision" in w.notes:
+        where = f"the collision is at step {w.notes['steps_to_collision']}"
+    else:
+        where = f"the pulse peak reaches the foil at step {w.notes['steps_to_peak_at_foil']}"
+    window = f"steps {pre + args.warmup}..{pre + args.warmup + K} ({where})"
     if rank == 0:
         s = runs[modes[0]]
         prof = s["prof"]
@@ -294,8 +307,7 @@ def run_qed(args, w, pic, torch, stream, timed, rank, world, dist, local, l2_not
                           "precision": "fp32 cell+offset, QED by the surrogate networks inside their chi range "
                           "(tables outside); FP64 islands: optical depth, diagnostics" if modes[0] == "surrogate"
                           else modes[0],
-                          "window": f"steps {pre + args.warmup}..{pre + args.warmup + K} around the collision "
-                                    f"(step {w.notes['steps_to_collision']})",
+                          "window": window,
                           "sort_interval": args.sort_interval, "replicas": world,
                           "l2": l2_note()},
                "fp32_table": tab and {"value": tab["value"], "ms_per_step": tab["ms_per_step"],
@@ -318,7 +330,7 @@ def main():
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="native", choices=["native", "reference"])
     ap.add_argument("--workload", default="laser_foil_2d",
-                    choices=["laser_foil_2d", "thermal_3d", "langmuir_1d", "qed_collision_2d"])
+                    choices=["laser_foil_2d", "thermal_3d", "langmuir_1d", "qed_collision_2d", "qed_foil_3d"])
     ap.add_argument("--sort-interval", type=int, default=8)
     ap.add_argument("--fp64-steps", type=int, default=10)
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU baseline leg")
@@ -330,7 +342,9 @@ def main():
     ap.add_argument("--qed-beam", type=int, default=10_000_000, help="beam macro-electrons (qed_collision_2d)")
     ap.add_argument("--rows", type=int, default=None,
                     help="smaller case for profiling: ny of laser_foil_2d, nz of thermal_3d (not a bench line)")
-    ap.add_argument("--qed-modes", default="surrogate,table,fp64", help="forms run by qed_collision_2d")
+    ap.add_argument("--qed-modes", default="surrogate,table,fp64", help="forms run by the QED workloads")
+    ap.add_argument("--qed-pre", type=int, default=None,
+                    help="untimed steps before the window (default: to the collision; 0 for qed_foil_3d)")
     ap.add_argument("--qed-train-iters", type=int, default=0, help="surrogate training steps (0: library default)")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
@@ -401,7 +415,7 @@ def main():
             sim.pic_profile(False)
         return ms, prof
 
-    if args.workload == "qed_collision_2d":
+    if args.workload in ("qed_collision_2d", "qed_foil_3d"):
         run_qed(args, w, pic, torch, stream, timed, rank, world, dist, local, l2_note)
         if dist:
             dist.barrier()

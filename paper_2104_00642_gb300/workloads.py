@@ -17,6 +17,9 @@ c/omega_r, density in n_r.  Workloads:
   3D periodic (omega_r = omega_p).
 * ``qed_collision_2d``: a GeV electron beam against an a0 = 200 laser, with
   photon emission and pair creation (Sec. IV; omega_r = omega_L).
+* ``qed_foil_3d``: a circularly polarised a0 = 300 laser on a 100 n_c
+  electron-proton foil in 3D, photon emission and pair creation on
+  (Sec. III-IV; omega_r = omega_L).
 """
 from __future__ import annotations
 
@@ -240,6 +243,59 @@ def qed_collision_2d(nx=2048, ny=512, cells_per_lambda=32, n_beam=10_000_000, ga
                     notes={"t_collide": t_collide, "steps_to_collision": int(t_collide / dt), "w": w,
                            "beam_x0": xb, "peak_macros_per_cell": core},
                     qed={"photon_sp": 2, "electron_sp": 0, "positron_sp": 1, "lambda_r_m": 1e-6,
+                         "photon_emin": photon_emin})
+
+
+def qed_foil_3d(n=(1024, 512, 512), cells_per_lambda=32, foil=(512, 576), n0=100.0, ppc=8, T_keV=1.0, a0=300.0,
+                waist_um=3.0, fwhm_fs=30.0, t_peak_fwhm=2.5, photon_cap=0.5, pair_cap=0.05, photon_emin=2.0,
+                steps=2000, courant=0.95, seed=SEED0 + 8, tile=(4, 4, 4)):
+    """3D laser-foil with QED: an electron-proton foil of density n0 n_c over
+    x-cells [foil), all y and z, ppc electrons and ppc protons per cell at
+    random positions in the cell (Maxwell-Juttner T), a circularly polarised
+    Gaussian laser of amplitude a0 per component entering from x-min and
+    focused on the foil front, absorbing x, periodic y and z.  Species:
+    electrons (QED), protons, positrons (QED, empty), photons (empty);
+    capacities for the QED children are fractions of the electron count.
+    Lengths: lambda = 1 um = 2 pi c/omega_L."""
+    rng = _rng(seed)
+    dx = 2.0 * math.pi / cells_per_lambda
+    dt = courant * dx / math.sqrt(3.0)
+    theta = T_keV / MEC2_KEV
+    nx, ny, nz = n
+    fx0, fx1 = foil
+    fw = fx1 - fx0
+    ncell = fw * ny * nz
+    N = ncell * ppc
+    ci = np.repeat(np.arange(ncell, dtype=np.int64), ppc)
+    cx = fx0 + ci % fw
+    cy = (ci // fw) % ny
+    cz = ci // (fw * ny)
+    del ci
+    species = []
+    for name, q, m, qed in (("electron", -1.0, 1.0, 1), ("proton", 1.0, M_PROTON, 0)):
+        x = (cx + rng.random(N)) * dx
+        y = (cy + rng.random(N)) * dx
+        z = (cz + rng.random(N)) * dx
+        ux, uy, uz = maxwell_juttner_u(rng, N, theta / m)
+        cap = int(N * (1.0 + pair_cap)) if qed else N
+        species.append(Species(name, q, m, n0 / ppc, x, y, z, ux, uy, uz, capacity=cap, qed=qed))
+    emp = np.zeros(0)
+    w = n0 / ppc
+    species.append(Species("positron", 1.0, 1.0, w, emp, emp, emp, emp, emp, emp,
+                           capacity=max(int(N * pair_cap), 1), qed=1))
+    species.append(Species("photon", 0.0, 0.0, w, emp, emp, emp, emp, emp, emp,
+                           capacity=max(int(N * photon_cap), 1), kind=1))
+    omega_L = 2.0 * math.pi * 2.99792458e8 / 1.0e-6
+    fwhm = fwhm_fs * 1e-15 * omega_L
+    lam = 2.0 * math.pi
+    laser = Laser(a0=a0, waist=waist_um * lam, fwhm=fwhm, t_peak=t_peak_fwhm * fwhm, x_focus=fx0 * dx,
+                  yc=0.5 * ny * dx, zc=0.5 * nz * dx, pol=1)
+    t_arrive = laser.t_peak + fx0 * dx
+    return Workload("qed_foil_3d", 3, tuple(n), (dx, dx, dx), dt, (ABSORB, PERIODIC, PERIODIC), species, steps,
+                    laser=laser, tile=tile,
+                    notes={"theta": theta, "n0": n0, "ppc": ppc, "foil": foil, "t_peak_at_foil": t_arrive,
+                           "steps_to_peak_at_foil": int(t_arrive / dt)},
+                    qed={"photon_sp": 3, "electron_sp": 0, "positron_sp": 2, "lambda_r_m": 1e-6,
                          "photon_emin": photon_emin})
 
 

@@ -392,3 +392,49 @@ def test_laser_foil_small_energy_history(prec, laser_foil_oracles):
         spread = np.max(np.abs(ref[:, c] - other[:, c]))
         tail = np.abs(got[5:, c] - ref[5:, c])
         assert np.max(tail) <= max(1e-3 * scale, 3.0 * spread), (c, got[:, c], ref[:, c], spread)
+
+
+def _qed_foil_small(seed):
+    """the 3D QED laser-foil geometry at reduced size, QED off: a CP a0 = 300
+    pulse (5 fs, 1 um waist) on a 100 n_c foil 8 cells thick, absorbing x,
+    periodic y and z; the pulse peak reaches the foil near step 190"""
+    w = W.qed_foil_3d(n=(32, 16, 16), foil=(8, 16), ppc=2, fwhm_fs=5.0, t_peak_fwhm=2.0, waist_um=1.0, seed=seed)
+    w.qed = None
+    return w
+
+
+@pytest.fixture(scope="module")
+def qed_foil_oracles():
+    hs = []
+    for seed in (W.SEED0 + 8, W.SEED0 + 98):
+        o = oracle_from_workload(_qed_foil_small(seed), sort_interval=8)
+        h = []
+        for _ in range(10):
+            o.step(25)
+            e = o.diagnostics()
+            h.append([e["U_E"], e["U_B"], e["U_kin"][0], e["U_kin"][1], e["E_absorbed"]])
+        hs.append(np.array(h))
+    return hs
+
+
+@pytest.mark.parametrize("prec", PRECS)
+def test_qed_foil_3d_small_energy_history(prec, qed_foil_oracles):
+    """3D circularly polarised laser on an overdense foil (tiled 3D push,
+    3D laser entry and absorbing faces): the energy histories agree within
+    1e-3 of their maximum while the pulse rises (to step 125); once the foil
+    breaks up the run is chaotic and they agree within three times the
+    spread of two oracle runs with independent particle draws (or 1e-3)."""
+    ref, other = qed_foil_oracles
+    sim = pic.from_workload(_qed_foil_small(W.SEED0 + 8), precision=prec, sort_interval=8)
+    got = []
+    for _ in range(10):
+        sim.pic_step(25)
+        d = sim.pic_diagnostics()
+        got.append([d["U_E"], d["U_B"], d["U_kin"][0], d["U_kin"][1], d["E_absorbed"]])
+    got = np.array(got)
+    assert ref[:, 3].max() > 1000 * ref[0, 3]  # the pulse has driven the ions
+    for c in range(5):
+        scale = ref[:, c].max()
+        assert np.max(np.abs(got[:5, c] - ref[:5, c])) <= 1e-3 * scale, (c, got[:, c], ref[:, c])
+        spread = np.max(np.abs(ref[:, c] - other[:, c]))
+        assert np.max(np.abs(got[5:, c] - ref[5:, c])) <= max(1e-3 * scale, 3.0 * spread), (c, got[:, c], ref[:, c])

@@ -124,3 +124,68 @@ def test_monte_carlo_fp64_form_matches_oracle():
     assert abs(e1 - e0) <= 1e-9 * e0
     d = s.pic_diagnostics()  # converted photons stay in the arrays, dead, until the next sort
     assert d["n_alive"][2] == int(gk["alive"].sum()) and d["U_kin"][2] > 0.0
+
+
+_N3, _DX3 = (8, 8, 8), (2.0, 2.0, 2.0)
+
+
+def _electrons_3d():
+    rng = np.random.default_rng(31)
+    x = [rng.uniform(0.0, _N3[d] * _DX3[d], Q.N_E) for d in range(3)]
+    u = np.sqrt(Q.GAMMA0 ** 2 - 1.0)
+    ang = rng.uniform(0.0, 2.0 * np.pi, Q.N_E)
+    return x[0], x[1], x[2], u * np.cos(ang), u * np.sin(ang), np.zeros(Q.N_E)
+
+
+@pytest.fixture(scope="module")
+def oracle_3d():
+    """the oracle's 25 steps of the 3D set-up (shared by both forms)"""
+    o = O.OracleSim(3, _N3, _DX3, Q.DT)
+    for sp in Q.species_spec():
+        o.add_species(sp[0], sp[1], sp[2], sp[3], kind=sp[4], qed=sp[5])
+    o.set_qed(photon_sp=2, electron_sp=0, positron_sp=1, lambda_r_m=Q.LAMBDA, photon_emin=0.0, seed=Q.SEED)
+    o.set_field(O.BZ, np.full(o.box(), Q.B0))
+    o.load(0, *_electrons_3d())
+    o.step(25)
+    return o
+
+
+@pytest.mark.parametrize("prec", [pic.FP32_CELLOFF, pic.FP64_PLAIN])
+def test_monte_carlo_3d_matches_oracle_event_by_event(prec, oracle_3d):
+    """The same set-up on a periodic 8^3 grid with the electrons spread in 3D
+    (the 3D QED push, photon push and spawn kernels): the photons and pairs
+    are the oracle's events, with the oracle's photon energies and emission
+    points, and the ensemble energy is conserved."""
+    o = oracle_3d
+    s = pic.pic_create(3, _N3, _DX3, Q.DT, Q.species_spec(), seed=Q.SEED, precision=prec)
+    s.pic_set_qed(photon_sp=2, electron_sp=0, positron_sp=1, lambda_r_m=Q.LAMBDA)
+    s.pic_set_field(pic.BZ, np.full(s.box(), Q.B0))
+    s.pic_load_particles(0, *_electrons_3d())
+    e0 = Q.total_energy(s.pic_get_particles(0), s.pic_get_particles(1), s.pic_get_particles(2))
+    s.pic_step(25)
+    gid, _ = s.pic_get_qed_state(2)
+    oid, _ = o.qed_state(2)
+    common = np.intersect1d(gid, oid)
+    flips = 2 if prec == pic.FP64_PLAIN else 3
+    assert len(oid) > 30 and len(gid) - len(common) <= flips and len(oid) - len(common) <= flips, (len(gid), len(oid))
+    gk, ok = s.pic_get_particles(2), o.particles(2)
+    ge = dict(zip(gid.tolist(), np.sqrt(gk["ux"] ** 2 + gk["uy"] ** 2 + gk["uz"] ** 2).tolist()))
+    oe = dict(zip(oid.tolist(), np.sqrt(ok["ux"] ** 2 + ok["uy"] ** 2 + ok["uz"] ** 2).tolist()))
+    rel = np.array([abs(ge[i] / oe[i] - 1.0) for i in common.tolist()])
+    assert np.median(rel) < (1e-4 if prec == pic.FP64_PLAIN else 1e-3) and np.max(rel) < 5e-2
+    # photons move at c along k from the parent's position (photons that
+    # converted to pairs stay in the arrays, dead, until the next sort)
+    gx = dict(zip(gid.tolist(), zip(gk["x"], gk["y"], gk["z"], gk["alive"])))
+    ox = dict(zip(oid.tolist(), zip(ok["x"], ok["y"], ok["z"], ok["alive"])))
+    L = np.array([_N3[d] * _DX3[d] for d in range(3)])
+    both = [i for i in common.tolist() if gx[i][3] and ox[i][3]]
+    assert len(both) >= 30
+    for i in both[:50]:
+        dd = np.abs(np.array(gx[i][:3]) - np.array(ox[i][:3]))
+        dd = np.minimum(dd, L - dd)
+        assert np.all(dd < 1e-3 * _DX3[0]), (i, gx[i], ox[i])
+    pid, _ = s.pic_get_qed_state(1)
+    opid, _ = o.qed_state(1)
+    assert abs(len(pid) - len(opid)) <= 2 and len(opid) >= 2
+    e1 = Q.total_energy(s.pic_get_particles(0), s.pic_get_particles(1), s.pic_get_particles(2))
+    assert abs(e1 - e0) <= (1e-9 if prec == pic.FP64_PLAIN else 2e-5) * e0
