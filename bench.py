@@ -77,6 +77,12 @@ def bytes_per_particle(dim, precision):
 
 L2_BYTES = 126 * 1024 * 1024  # GB300 L2
 
+# steps between tile sorts, chosen by measurement on a GB300 (ms per step):
+# laser_foil_2d at steps 0-64 / 1928-1992 / 3792-3856 (laser on the slab):
+# K = 8: 0.338 / 0.339 / 0.370, K = 16: 0.310 / 0.317 / 0.367, K = 32: 0.298 /
+# 0.306 / 0.410; thermal_3d: K = 4: 19.6, K = 8: 20.7
+SORT_INTERVAL = {"laser_foil_2d": 16, "thermal_3d": 4}
+
 
 def step_bytes(w, precision=0):
     """bytes one step touches at least: the particle state of every species
@@ -331,7 +337,8 @@ def main():
     ap.add_argument("--impl", default="native", choices=["native", "reference"])
     ap.add_argument("--workload", default="laser_foil_2d",
                     choices=["laser_foil_2d", "thermal_3d", "langmuir_1d", "qed_collision_2d", "qed_foil_3d"])
-    ap.add_argument("--sort-interval", type=int, default=8)
+    ap.add_argument("--sort-interval", type=int, default=None,
+                    help="steps between tile sorts (default: the measured best of the workload)")
     ap.add_argument("--fp64-steps", type=int, default=10)
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU baseline leg")
     ap.add_argument("--no-e2e", action="store_true")
@@ -348,6 +355,8 @@ def main():
     ap.add_argument("--qed-train-iters", type=int, default=0, help="surrogate training steps (0: library default)")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
+    if args.sort_interval is None:
+        args.sort_interval = SORT_INTERVAL.get(args.workload, 8)
     if args.impl == "reference":
         run_reference(args)
         return

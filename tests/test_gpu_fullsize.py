@@ -1,7 +1,7 @@
 """Parity at the full sizes of the throughput workloads, in the launch
-configuration the bench times (FP32 cell+offset, tiled push, sort every 8
-steps, so the first step sorts): one step of the whole workload on the GPU,
-against outputs the oracle computes one by one.
+configuration the bench times (FP32 cell+offset, tiled push, the bench's
+sort interval, so the first step sorts): one step of the whole workload on
+the GPU, against outputs the oracle computes one by one.
 
 The particles are loaded ordered by tile (numpy's stable argsort of the tile
 of the cell the O6 rule gives), so the GPU's stable sort at the first step
@@ -74,7 +74,7 @@ def _take(s, idx):
                      capacity=max(len(idx), 1))
 
 
-def _run(w, seed, n_random=2000, n_nodes=6):
+def _run(w, seed, sort_interval, n_random=2000, n_nodes=6):
     rng = np.random.default_rng(seed)
     # 1. particles ordered by tile, as the sort must leave them
     cells = []
@@ -84,7 +84,7 @@ def _run(w, seed, n_random=2000, n_nodes=6):
         w.species[i] = _take(s, order)
         w.species[i].capacity = s.capacity
         cells.append([a[order] for a in c])
-    sim = pic.from_workload(w, precision=pic.FP32_CELLOFF, sort_interval=8)
+    sim = pic.from_workload(w, precision=pic.FP32_CELLOFF, sort_interval=sort_interval)
     box = sim.box()
     F = _smooth_fields(box, rng)
     for c in range(6):
@@ -157,9 +157,9 @@ def _run(w, seed, n_random=2000, n_nodes=6):
 
 def test_laser_foil_2d_full_size_one_step():
     """2048 x 1024 cells, 4,194,304 electrons and protons (the bench's default workload)"""
-    _run(W.laser_foil_2d(), seed=11)
+    _run(W.laser_foil_2d(), seed=11, sort_interval=16)
 
 
 def test_thermal_3d_full_size_one_step():
     """256^3 cells, 134,217,728 electrons at 8 per cell (the 3D throughput workload)"""
-    _run(W.thermal_3d(), seed=12, n_random=1000, n_nodes=4)
+    _run(W.thermal_3d(), seed=12, sort_interval=4, n_random=1000, n_nodes=4)
