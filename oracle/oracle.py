@@ -53,6 +53,8 @@ def lib():
         L.or_add_species.restype = I
         L.or_load.argtypes = [P, I, LG, P, P, P, P, P, P]
         L.or_load.restype = I
+        L.or_set_ids.argtypes = [P, I, LG, LG, P]
+        L.or_set_ids.restype = I
         L.or_get_field.argtypes = [P, I, P]
         L.or_set_field.argtypes = [P, I, P]
         L.or_get_ghost.argtypes = [P, I, LG, LG, LG, P]
@@ -214,6 +216,14 @@ class OracleSim:
         rc = lib().or_load(self._h, int(isp), int(n), *[_ptr(a) for a in arrs])
         if rc != 0:
             raise ValueError(f"oracle: load failed ({rc})")
+
+    def set_ids(self, isp, ids, first=0):
+        """identities of particles [first, first + len(ids)) (their optical
+        depths restart from the identities' initial draws)"""
+        a = np.ascontiguousarray(ids, dtype=np.uint64)
+        rc = lib().or_set_ids(self._h, int(isp), int(first), len(a), _ptr(a))
+        if rc:
+            raise ValueError(f"or_set_ids failed ({rc})")
 
     def set_laser(self, a0, waist, fwhm, t_peak, x_focus, yc=0.0, zc=0.0, pol=0):
         lib().or_set_laser(self._h, int(pol), float(a0), float(waist), float(fwhm), float(t_peak),

@@ -258,6 +258,21 @@ int or_load(osim *s, int isp, long n, const double *x, const double *y, const do
     return 0;
 }
 
+/* identities given by the caller for particles [first, first + n) of a
+   species (a sample of a larger load keeps the identities of that load);
+   each optical depth restarts from its identity's initial draw */
+int or_set_ids(osim *s, int isp, long first, long n, const uint64_t *id)
+{
+    if (isp < 0 || isp >= s->nsp) return -1;
+    osp *p = &s->sp[isp];
+    if (first < 0 || n < 0 || first + n > p->n) return -2;
+    for (long a = 0; a < n; a++) {
+        p->id[first + a] = id[a];
+        p->tau[first + a] = initial_tau(s, id[a]);
+    }
+    return 0;
+}
+
 /* output box of a field: [0,N) on periodic axes, [0,N] on absorbing ones */
 static void out_box(const osim *s, long *m)
 {

@@ -23,6 +23,8 @@ double or_photon_lost(const osim *s);
 long or_get_qed_state(const osim *s, int isp, uint64_t *id, double *tau);
 int or_load(osim *s, int isp, long n, const double *x, const double *y, const double *z,
             const double *ux, const double *uy, const double *uz);
+/* caller-given identities (and their initial optical depths) for particles [first, first + n) */
+int or_set_ids(osim *s, int isp, long first, long n, const uint64_t *id);
 int or_get_field(const osim *s, int c, double *out);
 int or_set_field(osim *s, int c, const double *in);
 int or_get_ghost(const osim *s, int c, long i, long j, long k, double *v);

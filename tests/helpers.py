@@ -17,11 +17,12 @@ def oracle_from_workload(w: W.Workload, sort_interval=0, tile=None, seed=0):
     o = O.OracleSim(w.dim, w.n[: w.dim], w.dx[: w.dim], w.dt, bc=w.bc[: w.dim], rho_bg=w.rho_bg,
                     sort_interval=sort_interval, tile=t[: w.dim])
     for s in w.species:
-        i = o.add_species(s.q, s.m, s.w, s.capacity, kind=s.kind, qed=s.qed)
+        o.add_species(s.q, s.m, s.w, s.capacity, kind=s.kind, qed=s.qed)
+    if w.qed is not None:  # before the load: the initial optical depths draw from the seed
+        o.set_qed(seed=seed, **w.qed)
+    for i, s in enumerate(w.species):
         if s.n:
             o.load(i, s.x, s.y if w.dim > 1 else None, s.z if w.dim > 2 else None, s.ux, s.uy, s.uz)
-    if w.qed is not None:
-        o.set_qed(seed=seed, **w.qed)
     if w.laser is not None:
         L = w.laser
         o.set_laser(L.a0, L.waist, L.fwhm, L.t_peak, L.x_focus, L.yc, L.zc, L.pol)

@@ -163,3 +163,97 @@ def test_laser_foil_2d_full_size_one_step():
 def test_thermal_3d_full_size_one_step():
     """256^3 cells, 134,217,728 electrons at 8 per cell (the 3D throughput workload)"""
     _run(W.thermal_3d(), seed=12, sort_interval=4, n_random=1000, n_nodes=4)
+
+
+B_QED = 3000.0  # chi ~ 15 for the 1 GeV beam: most sampled electrons emit in one step
+
+
+@pytest.fixture(scope="module")
+def qed_collision_sample():
+    """the 10^7-electron beam of the QED collision workload in a strong,
+    smooth B_z; the oracle steps 300 of its electrons (with their full-load
+    identities, hence the same Philox streams) once"""
+    w = W.qed_collision_2d()
+    rng = np.random.default_rng(21)
+    e = w.species[0]
+    idx = np.sort(rng.choice(e.n, size=300, replace=False))
+    nz, ny, nx = 1, w.n[1], w.n[0] + 1
+    yy = np.arange(ny)[:, None] / ny
+    xx = np.arange(nx)[None, :] / nx
+    bz = B_QED * (1.0 + 0.1 * np.sin(2 * np.pi * (xx + 2 * yy)))[None, :, :]
+    sub = W.Workload(w.name, w.dim, w.n, w.dx, w.dt, w.bc,
+                     [_take(e, idx)] + [W.Species(s.name, s.q, s.m, s.w, s.x, s.y, s.z, s.ux, s.uy, s.uz,
+                                                  capacity=4 * len(idx), kind=s.kind, qed=s.qed)
+                                        for s in w.species[1:]],
+                     1, laser=w.laser, tile=w.tile, qed=w.qed)
+    sub.species[0].qed = 1
+    sub.species[0].capacity = 4 * len(idx)
+    o = oracle_from_workload(sub, sort_interval=0, seed=SEED_QED)
+    o.set_ids(0, idx.astype(np.uint64))
+    o.set_field(O.BZ, bz)
+    tau0 = o.qed_state(0)[1].copy()
+    o.step(1)
+    return w, idx, bz, o, tau0
+
+
+SEED_QED = 0x5EED0001
+
+
+@pytest.mark.parametrize("prec", [pic.FP32_CELLOFF, pic.FP64_PLAIN])
+def test_qed_collision_2d_full_size_events(prec, qed_collision_sample):
+    """The whole beam steps once on the GPU (tables, the bench's sort
+    interval, so the first step sorts): for the 300 sampled electrons the
+    emission events are the oracle's (photon identities derived from the
+    parent's Philox stream, at most two flips where the optical depth ends
+    within the table-vs-quadrature rate difference of zero), with the
+    oracle's photon energies, and the non-emitters' optical depths and
+    momenta agree."""
+    w, idx, bz, o, tau0 = qed_collision_sample
+    sim = pic.from_workload(w, precision=prec, sort_interval=8, seed=SEED_QED)
+    sim.pic_set_field(pic.BZ, bz)
+    sim.pic_step(1)
+    iph = w.qed["photon_sp"]
+    key = np.array([SEED_QED & 0xFFFFFFFF, SEED_QED >> 32], dtype=np.uint32)
+
+    def draw(pid):  # the parent's emission draw of step 0: photon identity, restarted depth
+        r = O.philox4x32_10(np.array([pid & 0xFFFFFFFF, pid >> 32, 0, 0], dtype=np.uint32), key)
+        return (int(r[3]) << 32) | int(r[2]), -np.log(O.uniform24(int(r[1])))
+
+    gid, gtau = sim.pic_get_qed_state(0)
+    ge = sim.pic_get_particles(0)
+    where = {int(v): k for k, v in enumerate(gid.tolist())}
+    gpos = np.array([where[int(i)] for i in idx])
+    oid, otau = o.qed_state(0)
+    assert np.array_equal(oid, idx.astype(np.uint64))
+    oe = o.particles(0)
+    gph_id, _ = sim.pic_get_qed_state(iph)
+    oph_id, _ = o.qed_state(iph)
+    gph, oph = set(gph_id.tolist()), set(oph_id.tolist())
+    cand, restart = zip(*[draw(int(i)) for i in idx])
+    restart = np.array(restart)
+    # an event (kept photon or one below photon_emin) restarts the optical depth
+    g_ev = np.abs(gtau[gpos] - restart) <= 1e-12 * restart
+    o_ev = np.abs(otau - restart) <= 1e-12 * restart
+    assert o_ev.sum() >= 60 and np.sum(g_ev != o_ev) <= 2, (g_ev.sum(), o_ev.sum())
+    g_em = np.array([c in gph for c in cand])
+    o_em = np.array([c in oph for c in cand])
+    assert np.all(o_em <= o_ev) and np.all(g_em <= g_ev)
+    assert o_em.sum() >= 30 and np.sum(g_em != o_em) <= 2, (g_em.sum(), o_em.sum())
+    # photon energies of the common events
+    gk, ok = sim.pic_get_particles(iph), o.particles(iph)
+    gmap = dict(zip(gph_id.tolist(), np.sqrt(gk["ux"] ** 2 + gk["uy"] ** 2 + gk["uz"] ** 2).tolist()))
+    omap = dict(zip(oph_id.tolist(), np.sqrt(ok["ux"] ** 2 + ok["uy"] ** 2 + ok["uz"] ** 2).tolist()))
+    both = [c for c, a, b in zip(cand, g_em, o_em) if a and b]
+    rel = np.array([abs(gmap[c] / omap[c] - 1.0) for c in both])
+    assert np.median(rel) < (1e-4 if prec == pic.FP64_PLAIN else 1e-3) and np.max(rel) < 5e-2
+    # electrons without an event on either side: momenta and depth decrements
+    quiet = (~g_ev) & (~o_ev)
+    assert quiet.sum() >= 10
+    q = np.nonzero(quiet)[0]
+    umag = np.sqrt(oe["ux"] ** 2 + oe["uy"] ** 2 + oe["uz"] ** 2)
+    tol = 1e-10 if prec == pic.FP64_PLAIN else TOL
+    for k in ("ux", "uy", "uz"):
+        assert np.all(np.abs(ge[k][gpos][q] - oe[k][q]) <= tol * umag[q] + 1e-7), k
+    dg, do = tau0[q] - gtau[gpos][q], tau0[q] - otau[q]
+    assert np.all(np.abs(dg - do) <= 1e-3 * do), np.max(np.abs(dg - do) / do)
+    sim.close()

@@ -137,3 +137,26 @@ def test_total_emission_rate_matches_library_quadrature(L, chi):
     a = integrate.quad(lambda s: 3 * s * s * F(s ** 3), 0, wh, epsabs=0, epsrel=1e-10, limit=400)[0]
     b = integrate.quad(lambda t: 3 * t * t * F(1 - t ** 3), 0, wh, epsabs=0, epsrel=1e-10, limit=400)[0]
     assert abs(L.or_qed_Grad(chi) / (a + b) - 1.0) < 1e-7
+
+
+def test_caller_given_identities_restart_their_optical_depths():
+    """A sample keeps the identities of its full load: set_ids gives a
+    particle the identity and the initial optical depth that a load at that
+    index draws."""
+    def make():
+        o = O.OracleSim(1, (16,), (1.0,), 0.02)
+        o.add_species(-1.0, 1.0, 1e-12, 16, qed=1)
+        o.set_qed(photon_sp=-1, electron_sp=0, lambda_r_m=1e-6, seed=99)
+        return o
+
+    full = make()
+    z = np.zeros(10)
+    full.load(0, np.linspace(0.5, 9.5, 10), None, None, z, z, z)
+    ids, tau = full.qed_state(0)
+    sub = make()
+    pick = np.array([7, 2, 9])
+    sub.load(0, np.linspace(0.5, 9.5, 10)[pick], None, None, z[:3], z[:3], z[:3])
+    sub.set_ids(0, ids[pick])
+    sids, stau = sub.qed_state(0)
+    assert np.array_equal(sids, ids[pick]) and np.array_equal(stau, tau[pick])
+    assert len(set(tau.tolist())) == 10
