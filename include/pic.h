@@ -212,6 +212,8 @@ typedef struct {
     int64_t iterations;
     int64_t table_bytes;       /* device bytes of one process's tables (FP32 + FP64) */
     int64_t net_bytes;         /* device bytes of the network the push reads */
+    double max_err_mean;       /* max over the grid's chi rows of |<f>_net / <f>_table - 1|, <f> the
+                                  mean energy fraction of an event (the energy an event carries) */
 } pic_mlp_report;
 
 typedef struct {
@@ -221,7 +223,9 @@ typedef struct {
 
 /* Train the network of `process` on the device with the library's own
  * kernels (forward, backward, Adam; one CUDA graph per iteration): each step
- * draws a fresh batch of (ln chi uniform in the range, r uniform) and takes
+ * draws a fresh batch of (ln chi uniform in the range, r uniform; for
+ * emission half the rows take r = 1 - (1 - t)^2 with t uniform instead, which
+ * samples the hard end of the spectrum as densely as the soft end) and takes
  * the targets from the FP64 tables.  Then validates the network against the
  * tables on a 256 x 256 grid of cell midpoints in (ln chi, r) and marks it
  * ready.  Needs pic_set_qed first (the tables).  report may be NULL.

@@ -1140,11 +1140,11 @@ int mlp_scratch(pic_sim *s, long long B)
     MlpScratch &S = s->ms;
     if (!S.it) {
         void *small = nullptr;
-        int rc = dalloc(s, &small, 64);
+        int rc = dalloc(s, &small, 64 + kMlpValAcc * sizeof(double));
         if (rc) return rc;
-        S.acc = (double *)small;                  // 4 doubles
-        S.loss = (float *)((char *)small + 32);   // 2 floats
-        S.it = (int *)((char *)small + 48);
+        S.loss = (float *)small;                  // 2 floats
+        S.it = (int *)((char *)small + 16);
+        S.acc = (double *)((char *)small + 64);   // kMlpValAcc doubles
     }
     if (B <= S.B) return PIC_OK;
     void *buf = nullptr;
@@ -1220,15 +1220,20 @@ int mlp_validate(pic_sim *s, int p, pic_mlp_report *rep)
     MlpNet &net = s->net[p];
     int rc = mlp_scratch(s, 0);
     if (rc) return rc;
-    CK(cudaMemsetAsync(s->ms.acc, 0, 4 * sizeof(double), s->st));
-    launch_mlp_validate(net.img, net.nrm, s->T, p, 256, 256, s->ms.acc, s->st);
+    CK(cudaMemsetAsync(s->ms.acc, 0, kMlpValAcc * sizeof(double), s->st));
+    launch_mlp_validate(net.img, net.nrm, s->T, p, kMlpValRows, kMlpValRows, s->ms.acc, s->st);
     CK(cudaGetLastError());
-    double acc[4];
+    double acc[kMlpValAcc];
     CK(cudaMemcpyAsync(acc, s->ms.acc, sizeof acc, cudaMemcpyDeviceToHost, s->st));
     CK(cudaStreamSynchronize(s->st));
     rep->max_err_lnG = acc[0];
     rep->max_err_s = acc[1];
-    rep->rms_err_s = std::sqrt(acc[2] / (256.0 * 256.0));
+    rep->rms_err_s = std::sqrt(acc[2] / ((double)kMlpValRows * kMlpValRows));
+    rep->max_err_mean = 0.0;
+    for (int r = 0; r < kMlpValRows; r++) {
+        const double fn = acc[4 + 2 * r], ft = acc[5 + 2 * r];
+        if (ft > 0.0) rep->max_err_mean = std::max(rep->max_err_mean, std::fabs(fn / ft - 1.0));
+    }
     rep->table_bytes = (int64_t)(qed_table_bytes() / 2);
     rep->net_bytes = kMlpStageBytes;
     return PIC_OK;

@@ -64,7 +64,12 @@ __global__ void k_mlp_data(QedTables T, int p, MlpNorm nrm, uint32_t k0, uint32_
     uint32_t w[4];
     philox4x32_10((uint32_t)i, (uint32_t)(i >> 32), (uint32_t)*it, QP_TRAIN + p, k0, k1, w);
     const float x0 = (float)(2.0 * uniform24(w[0]) - 1.0);
-    const double r = uniform24(w[1]);
+    // emission: half the rows take r uniform, half r = 1 - (1 - t)^2 with t
+    // uniform (uniform in the network's r coordinate), so that the hard end of
+    // the spectrum (r -> 1), which carries most of the emitted energy, is
+    // sampled as densely as the soft end
+    const double t = uniform24(w[1]);
+    const double r = p == QED_RAD && (w[2] & 1u) ? 1.0 - (1.0 - t) * (1.0 - t) : t;
     const double lnchi = ((double)x0 - nrm.x0b) / nrm.x0a, chi = exp(lnchi);
     const double rr = p == QED_PAIR ? fmin(r, 1.0 - r) : r;
     const double s = cbrt(qed_sample<double>(T, p, chi, rr));
@@ -391,6 +396,9 @@ __global__ void __launch_bounds__(128) k_mlp_validate(const MlpImage *img, MlpNo
     atomicMax(reinterpret_cast<unsigned long long *>(&acc[0]), (unsigned long long)__double_as_longlong(eg));
     atomicMax(reinterpret_cast<unsigned long long *>(&acc[1]), (unsigned long long)__double_as_longlong(es));
     atomicAdd(&acc[2], es * es);
+    const double ft = s_tab * s_tab * s_tab;
+    atomicAdd(&acc[4 + 2 * ic], mlp_fraction(p, y0, r));
+    atomicAdd(&acc[5 + 2 * ic], p == QED_PAIR && r > 0.5 ? 1.0 - ft : ft);
 }
 
 int div_up_i(long long a, int b) { return (int)((a + b - 1) / b); }

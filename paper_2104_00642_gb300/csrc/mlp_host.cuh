@@ -23,9 +23,15 @@ struct MlpScratch {
     MlpZ Z{}, D{};                                   // [B][64] each
     float *loss = nullptr;                           // [0] this iteration, [1] the last one
     int *it = nullptr;                               // iteration counter
-    double *acc = nullptr;                           // validation accumulators (4)
+    double *acc = nullptr;                           // validation accumulators (kMlpValAcc)
     float *partials = nullptr;                       // per-block / per-warp gradient partials
 };
+
+// validation grid: kMlpValRows x kMlpValRows cell midpoints in (ln chi, r);
+// accumulators: max |d ln G|, max |d s|, sum d s^2, (unused), then per chi
+// row the sums of the network's and the tables' energy fractions
+constexpr int kMlpValRows = 256;
+constexpr int kMlpValAcc = 4 + 2 * kMlpValRows;
 
 // floats of gradient partials a batch of B rows needs (mlp_partial_floats)
 size_t mlp_partial_floats(long long B);

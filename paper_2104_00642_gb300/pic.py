@@ -86,7 +86,7 @@ class pic_mlp_train_opts(C.Structure):
 class pic_mlp_report(C.Structure):
     _fields_ = [("loss", C.c_double), ("max_err_lnG", C.c_double), ("max_err_s", C.c_double),
                 ("rms_err_s", C.c_double), ("ms", C.c_double), ("iterations", C.c_int64),
-                ("table_bytes", C.c_int64), ("net_bytes", C.c_int64)]
+                ("table_bytes", C.c_int64), ("net_bytes", C.c_int64), ("max_err_mean", C.c_double)]
 
 
 class pic_mlp_info(C.Structure):

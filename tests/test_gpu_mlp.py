@@ -123,8 +123,10 @@ def test_training_reaches_the_tables(trained, process):
     s, reps = trained
     r = reps[process]
     print(process, r)
-    assert r["iterations"] == 40000 and r["loss"] < 1e-5, r
+    assert r["iterations"] == 40000 and r["loss"] < 5e-5, r
     assert r["max_err_lnG"] < 3e-2 and r["rms_err_s"] < 1.5e-3 and r["max_err_s"] < 2e-2, r
+    # the mean energy fraction of an event, per chi row (the energy the events carry)
+    assert r["max_err_mean"] < 3e-2, r
     # the report's validation agrees with a fresh one
     v = s.pic_mlp_validate(process)
     assert abs(v["rms_err_s"] - r["rms_err_s"]) < 1e-9
