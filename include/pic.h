@@ -246,6 +246,14 @@ int pic_mlp_set(pic_sim *sim, int process, const float *params, const pic_mlp_in
  * arrays), through the warp-level inference path the push uses. */
 int pic_mlp_eval(pic_sim *sim, int process, int64_t n, const float *x, float *y);
 
+/* The same evaluation batched on the fifth-generation tensor cores: CTAs of
+ * 128 threads, one row per thread, the two 64 x 64 hidden layers as tcgen05
+ * MMAs (M = 128, N = 64, K = 16 slices) with FP32 accumulators in tensor
+ * memory.  The input layer, SiLU, BF16 activations and head are those of
+ * pic_mlp_eval: the results differ only by the order of the FP32 sums.
+ * x, y as for pic_mlp_eval; PIC_ERR_CUDA if the tensor cores time out. */
+int pic_mlp_eval_tc(pic_sim *sim, int process, int64_t n, const float *x, float *y);
+
 /* Loss L = (1/n) sum_rows sum_o (y_o - t_o)^2 and its gradient with respect
  * to every parameter (grad: PIC_MLP_NPARAMS floats) at the present
  * parameters, by the training kernels (BF16 forward, backward on the tensor

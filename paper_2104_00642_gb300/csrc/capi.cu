@@ -1383,6 +1383,28 @@ int pic_mlp_eval(pic_sim *s, int p, int64_t n, const float *x, float *y)
     return PIC_OK;
 }
 
+int pic_mlp_eval_tc(pic_sim *s, int p, int64_t n, const float *x, float *y)
+{
+    if (!s) return PIC_ERR_ARG;
+    if ((p != PIC_QED_EMISSION && p != PIC_QED_PAIR) || n < 0 || (n && (!x || !y)))
+        return fail(s, PIC_ERR_ARG, "pic_mlp_eval_tc: bad arguments");
+    const MlpNet &net = s->net[p];
+    if (!net.ready) return fail(s, PIC_ERR_STATE, "pic_mlp_eval_tc: no network");
+    if (n == 0) return PIC_OK;
+    float *d = nullptr;
+    CK(cudaMalloc(&d, (size_t)n * 4 * sizeof(float)));
+    cudaError_t e = cudaMemcpyAsync(d, x, (size_t)n * 2 * sizeof(float), cudaMemcpyHostToDevice, s->st);
+    if (e == cudaSuccess) {
+        launch_mlp_eval_tc(net.img, n, d, d + 2 * n, s->d_err, s->st);
+        e = cudaGetLastError();
+    }
+    if (e == cudaSuccess) e = cudaMemcpyAsync(y, d + 2 * n, (size_t)n * 2 * sizeof(float), cudaMemcpyDeviceToHost, s->st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s->st);
+    cudaFree(d);
+    if (e != cudaSuccess) return fail(s, PIC_ERR_CUDA, "pic_mlp_eval_tc: %s", cudaGetErrorString(e));
+    return check_flags(s);
+}
+
 int pic_mlp_grad(pic_sim *s, int p, int64_t n, const float *x, const float *t, float *grad, double *loss)
 {
     if (!s) return PIC_ERR_ARG;

@@ -54,6 +54,10 @@ void launch_mlp_backward(const MlpImage *img, long long B, const float *X, const
 void mlp_train_iteration(MlpNet &net, MlpScratch &S, const QedTables &T, int p, const uint32_t *key,
                          const MlpAdam &a, float w_rate, cudaStream_t st);
 void launch_mlp_eval(const MlpImage *img, long long n, const float *X, float *Y, cudaStream_t st);
+// the same evaluation on the tcgen05 tensor cores (mlp_tc.cu); a timeout of
+// the tensor cores sets ERR_TIMEOUT in *err
+void launch_mlp_eval_tc(const MlpImage *img, long long n, const float *X, float *Y, int *err, cudaStream_t st);
+size_t mlp_tc_smem_bytes();
 void launch_qed_eval_surr(const MlpImage *img, const MlpNorm &nrm, const QedTables &T, bool f64, int p, long long n,
                           const double *chi, const double *r, double *out, cudaStream_t st);
 void launch_mlp_validate(const MlpImage *img, const MlpNorm &nrm, const QedTables &T, int p, int nc, int nr,

@@ -32,7 +32,7 @@ EXPORTS = ["pic_create", "pic_destroy", "pic_last_error", "pic_load_particles", 
            "pic_set_field", "pic_step", "pic_fields", "pic_particle_count", "pic_get_particles",
            "pic_get_cells", "pic_diagnostics", "pic_gather", "pic_sync", "pic_profile", "pic_profile_read",
            "pic_field_energy_noalloc", "pic_set_qed", "pic_qed_eval", "pic_get_qed_state", "pic_mlp_train",
-           "pic_mlp_validate", "pic_mlp_get", "pic_mlp_set", "pic_mlp_eval", "pic_mlp_grad"]
+           "pic_mlp_validate", "pic_mlp_get", "pic_mlp_set", "pic_mlp_eval", "pic_mlp_eval_tc", "pic_mlp_grad"]
 KIND_MASSIVE, KIND_PHOTON = 0, 1
 QED_OFF, QED_TABLE, QED_SURROGATE = 0, 1, 2
 MLP_NPARAMS = 8642
@@ -155,8 +155,10 @@ def load_library(path: str = LIB_PATH):
     L.pic_mlp_get.argtypes = [P, I, P, C.POINTER(pic_mlp_info)]
     L.pic_mlp_set.argtypes = [P, I, P, C.POINTER(pic_mlp_info)]
     L.pic_mlp_eval.argtypes = [P, I, I64, P, P]
+    L.pic_mlp_eval_tc.argtypes = [P, I, I64, P, P]
     L.pic_mlp_grad.argtypes = [P, I, I64, P, P, P, C.POINTER(D)]
-    for name in ("pic_mlp_train", "pic_mlp_validate", "pic_mlp_get", "pic_mlp_set", "pic_mlp_eval", "pic_mlp_grad"):
+    for name in ("pic_mlp_train", "pic_mlp_validate", "pic_mlp_get", "pic_mlp_set", "pic_mlp_eval", "pic_mlp_eval_tc",
+                 "pic_mlp_grad"):
         getattr(L, name).restype = I
     _lib = L
     return L
@@ -353,6 +355,12 @@ class Sim:
         X = np.ascontiguousarray(np.asarray(x, dtype=np.float32).reshape(-1, 2))
         Y = np.zeros_like(X)
         self._check(load_library().pic_mlp_eval(self._h, int(process), X.shape[0], _p(X), _p(Y)))
+        return Y
+
+    def pic_mlp_eval_tc(self, process, x):
+        X = np.ascontiguousarray(np.asarray(x, dtype=np.float32).reshape(-1, 2))
+        Y = np.zeros_like(X)
+        self._check(load_library().pic_mlp_eval_tc(self._h, int(process), X.shape[0], _p(X), _p(Y)))
         return Y
 
     def pic_mlp_grad(self, process, x, t):

@@ -67,6 +67,28 @@ def test_forward_matches_oracle(sim):
     assert err.max() < 2e-2 * scale and np.sqrt(np.mean(err ** 2)) < 4e-3 * scale, (err.max(), scale)
 
 
+@pytest.mark.parametrize("n", [1, 127, 128, 1000 + 17, 40000 + 3])
+def test_tensor_core_evaluation_matches(sim, n):
+    """The batched tcgen05 evaluation (128 rows per CTA, accumulators in
+    tensor memory) against the warp-level mma.sync one and the FP64 network,
+    over one, partial and many 128-row tiles: the same BF16 activations up to
+    the order of the FP32 sums, so nearly every output agrees to 1e-5 (a sum
+    that lands on the other side of a BF16 rounding boundary moves one
+    activation by one BF16 step)."""
+    P = random_params(3)
+    sim.pic_mlp_set(pic.QED_EMISSION, P, 1e-3, 1e2, 0.0, 1.0)
+    rng = np.random.default_rng(40 + n)
+    x = rng.uniform(-1.0, 1.0, (n, 2)).astype(np.float32)
+    y_tc = sim.pic_mlp_eval_tc(pic.QED_EMISSION, x)
+    y_mma = sim.pic_mlp_eval(pic.QED_EMISSION, x)
+    ref = O.mlp_forward(device_view(P), x.astype(np.float64))
+    scale = np.abs(ref).max()
+    d = np.abs(y_tc - y_mma)
+    assert np.mean(d <= 1e-5 * scale) > 0.99 and d.max() < 1e-2 * scale, (d.max(), np.mean(d <= 1e-5 * scale))
+    err = np.abs(y_tc - ref)
+    assert err.max() < 2e-2 * scale and np.sqrt(np.mean(err ** 2)) < 4e-3 * scale
+
+
 @pytest.mark.parametrize("n", [32, 256, 4096 + 32])
 def test_gradient_matches_oracle_backprop(sim, n):
     """Loss and every parameter gradient of the GPU backward pass (deltas
