@@ -255,7 +255,8 @@ def run_qed(args, w, pic, torch, stream, timed, rank, world, dist, local, l2_not
                                 seed=0x5EED + rank)
         train = None
         if mode == "surrogate":
-            train = {p: sim.pic_mlp_train(p, iterations=args.qed_train_iters, seed=17)
+            cmin = {pic.QED_EMISSION: 0.0, pic.QED_PAIR: args.qed_pair_chi_min}
+            train = {p: sim.pic_mlp_train(p, iterations=args.qed_train_iters, seed=17, chi_min=cmin[p])
                      for p in (pic.QED_EMISSION, pic.QED_PAIR)}
             sim.pic_set_qed(mode=pic.QED_SURROGATE, **w.qed)
         with torch.cuda.stream(stream):
@@ -329,6 +330,26 @@ def run_qed(args, w, pic, torch, stream, timed, rank, world, dist, local, l2_not
         print(json.dumps(out))
 
 
+def run_mlp_rows(n):
+    """the two evaluations of the surrogate network (warp-level mma.sync,
+    CTA-level tcgen05) on the same random network and inputs, twice each"""
+    from paper_2104_00642_gb300 import pic
+    sim = pic.pic_create(1, (16,), (1.0,), 0.02, [(-1.0, 1.0, 1e-12, 16, 0, 1), (0.0, 0.0, 1e-12, 16, 1, 0)])
+    sim.pic_set_qed(photon_sp=1, electron_sp=0, lambda_r_m=1e-6)
+    rng = np.random.default_rng(1)
+    sim.pic_mlp_set(0, (rng.standard_normal(pic.MLP_NPARAMS) * 0.2).astype(np.float32), 1e-3, 1e2, 0.0, 1.0)
+    x = rng.uniform(-1.0, 1.0, (n, 2)).astype(np.float32)
+    out = {}
+    for name in ("pic_mlp_eval", "pic_mlp_eval_tc") * 2:
+        t = time.perf_counter()
+        out[name] = getattr(sim, name)(0, x)
+        out[name + "_s"] = time.perf_counter() - t
+    d = np.abs(out["pic_mlp_eval"] - out["pic_mlp_eval_tc"])
+    print(json.dumps({"rows": n, "wall_s_mma_sync": out["pic_mlp_eval_s"], "wall_s_tcgen05": out["pic_mlp_eval_tc_s"],
+                      "max_abs_diff": float(d.max()), "frac_within_1e-5": float(np.mean(d <= 1e-5))}))
+    sim.close()
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -350,6 +371,11 @@ def main():
     ap.add_argument("--rows", type=int, default=None,
                     help="smaller case for profiling: ny of laser_foil_2d, nz of thermal_3d (not a bench line)")
     ap.add_argument("--qed-modes", default="surrogate,table,fp64", help="forms run by the QED workloads")
+    ap.add_argument("--mlp-rows", type=int, default=0,
+                    help="instead of a PIC workload: evaluate a random surrogate network on this many rows with "
+                         "the mma.sync and the tcgen05 kernels (profiling aid; kernel times come from ncu)")
+    ap.add_argument("--qed-pair-chi-min", type=float, default=0.0,
+                    help="lower end of the pair network's chi range (0: library default)")
     ap.add_argument("--qed-pre", type=int, default=None,
                     help="untimed steps before the window (default: to the collision; 0 for qed_foil_3d)")
     ap.add_argument("--qed-train-iters", type=int, default=0, help="surrogate training steps (0: library default)")
@@ -359,6 +385,9 @@ def main():
         args.sort_interval = SORT_INTERVAL.get(args.workload, 8)
     if args.impl == "reference":
         run_reference(args)
+        return
+    if args.mlp_rows:
+        run_mlp_rows(args.mlp_rows)
         return
 
     import torch
