@@ -723,26 +723,17 @@ int pic_load_particles(pic_sim *s, int sp, int64_t n, const double *x, const dou
     const double *us[3] = {ux, uy, uz};
     for (int d = 0; d < 3; d++)
         if (!us[d] || (d < g.dim && !xs[d])) return fail(s, PIC_ERR_ARG, "pic_load_particles: null array");
-    for (int d = 0; d < g.dim; d++) {
-        double L = g.n[d] * g.dx[d];
-        for (int64_t a = 0; a < n; a++)
-            if (!(xs[d][a] >= 0.0 && xs[d][a] < L))
-                return fail(s, PIC_ERR_ARG, "pic_load_particles: particle %lld outside the domain on axis %d",
-                            (long long)a, d);
-    }
-    for (int d = 0; d < 3; d++)
-        for (int64_t a = 0; a < n; a++)
-            if (!std::isfinite(us[d][a])) return fail(s, PIC_ERR_ARG, "pic_load_particles: non-finite u");
     SpeciesState &p = s->sp[sp];
     long long cnt = 0;
     int rc = read_count(s, sp, &cnt);
     if (rc) return rc;
     if (cnt + n > p.cap) return fail(s, PIC_ERR_CAPACITY, "pic_load_particles: capacity %lld exceeded", p.cap);
     double *dtmp = nullptr;
-    CK(cudaMalloc(&dtmp, (size_t)n * 6 * sizeof(double)));
+    CK(cudaMalloc(&dtmp, (size_t)n * 6 * sizeof(double) + sizeof(unsigned long long)));
     double *dx_[3] = {dtmp, dtmp + n, dtmp + 2 * n};
     double *du_[3] = {dtmp + 3 * n, dtmp + 4 * n, dtmp + 5 * n};
-    cudaError_t e = cudaSuccess;
+    unsigned long long *dbad = reinterpret_cast<unsigned long long *>(dtmp + 6 * n), hbad = ~0ull;
+    cudaError_t e = cudaMemsetAsync(dbad, 0xFF, sizeof(unsigned long long), s->st);
     for (int d = 0; d < 3 && e == cudaSuccess; d++) {
         if (d < g.dim) e = cudaMemcpyAsync(dx_[d], xs[d], n * sizeof(double), cudaMemcpyHostToDevice, s->st);
         if (e == cudaSuccess) e = cudaMemcpyAsync(du_[d], us[d], n * sizeof(double), cudaMemcpyHostToDevice, s->st);
@@ -750,9 +741,18 @@ int pic_load_particles(pic_sim *s, int sp, int64_t n, const double *x, const dou
     if (e == cudaSuccess) {
         const double *cx[3] = {dx_[0], dx_[1], dx_[2]};
         const double *cu[3] = {du_[0], du_[1], du_[2]};
-        if (s->precision == PIC_PREC_FP64_PLAIN) launch_load_f64(view64(s, sp, p.cur), cnt, n, cx, cu, g, s->st);
-        else launch_load_f32(view32(s, sp, p.cur), cnt, n, cx, cu, g, s->st);
+        if (s->precision == PIC_PREC_FP64_PLAIN) launch_load_f64(view64(s, sp, p.cur), cnt, n, cx, cu, g, dbad, s->st);
+        else launch_load_f32(view32(s, sp, p.cur), cnt, n, cx, cu, g, dbad, s->st);
         e = cudaGetLastError();
+    }
+    // the positions and momenta are checked on the device (a host loop over
+    // them cost more than the upload); the count moves only if all passed
+    if (e == cudaSuccess) e = cudaMemcpyAsync(&hbad, dbad, sizeof hbad, cudaMemcpyDeviceToHost, s->st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s->st);
+    if (e == cudaSuccess && hbad != ~0ull) {
+        cudaFree(dtmp);
+        return fail(s, PIC_ERR_ARG, "pic_load_particles: particle %llu outside the domain or with a non-finite u",
+                    hbad);
     }
     long long newn = cnt + n;
     if (e == cudaSuccess) e = cudaMemcpyAsync(p.d_count, &newn, sizeof(long long), cudaMemcpyHostToDevice, s->st);

@@ -256,13 +256,29 @@ __global__ void k_gather_f64(PartF64 P, const double *__restrict__ F, Grid g, do
 // ---------------------------------------------------------------------
 // load: FP64 absolute positions -> layout (positions already validated)
 // ---------------------------------------------------------------------
+// a particle outside [0, L) on an active axis, or with a non-finite
+// momentum, is not stored: the lowest such index goes to *bad
+__device__ __forceinline__ bool load_ok(const double *const *xs, const double *ux, const double *uy,
+                                        const double *uz, long long a, const Grid &g, unsigned long long *bad)
+{
+    bool ok = isfinite(ux[a]) && isfinite(uy[a]) && isfinite(uz[a]);
+    for (int d = 0; d < g.dim; d++) {
+        const double xv = xs[d][a];
+        ok &= xv >= 0.0 && xv < g.n[d] * g.dx[d];  // false for NaN
+    }
+    if (!ok) atomicMin(bad, (unsigned long long)a);
+    return ok;
+}
+
 __global__ void k_load_f32(PartF32 P, long long first, long long n, const double *x, const double *y,
-                           const double *z, const double *ux, const double *uy, const double *uz, Grid g)
+                           const double *z, const double *ux, const double *uy, const double *uz, Grid g,
+                           unsigned long long *bad)
 {
     long long a = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     if (a >= n) return;
     long long p = first + a;
     const double *xs[3] = {x, y, z};
+    if (!load_ok(xs, ux, uy, uz, a, g, bad)) return;
     int c[3] = {0, 0, 0};
     for (int d = 0; d < g.dim; d++) {
         double X = xs[d][a] / g.dx[d];
@@ -285,12 +301,14 @@ __global__ void k_load_f32(PartF32 P, long long first, long long n, const double
 }
 
 __global__ void k_load_f64(PartF64 P, long long first, long long n, const double *x, const double *y,
-                           const double *z, const double *ux, const double *uy, const double *uz, Grid g)
+                           const double *z, const double *ux, const double *uy, const double *uz, Grid g,
+                           unsigned long long *bad)
 {
     long long a = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     if (a >= n) return;
     long long p = first + a;
     const double *xs[3] = {x, y, z};
+    if (!load_ok(xs, ux, uy, uz, a, g, bad)) return;
     int c[3] = {0, 0, 0};
     for (int d = 0; d < g.dim; d++) {
         double xv = xs[d][a];
@@ -398,19 +416,19 @@ void launch_gather_f64(const PartF64 &P, const double *F, const Grid &g, double 
 }
 
 void launch_load_f32(const PartF32 &P, long long first, long long n, const double *const *xs,
-                     const double *const *us, const Grid &g, cudaStream_t st)
+                     const double *const *us, const Grid &g, unsigned long long *bad, cudaStream_t st)
 {
     if (n == 0) return;
     note_launch();
-    k_load_f32<<<div_up(n, 256), 256, 0, st>>>(P, first, n, xs[0], xs[1], xs[2], us[0], us[1], us[2], g);
+    k_load_f32<<<div_up(n, 256), 256, 0, st>>>(P, first, n, xs[0], xs[1], xs[2], us[0], us[1], us[2], g, bad);
 }
 
 void launch_load_f64(const PartF64 &P, long long first, long long n, const double *const *xs,
-                     const double *const *us, const Grid &g, cudaStream_t st)
+                     const double *const *us, const Grid &g, unsigned long long *bad, cudaStream_t st)
 {
     if (n == 0) return;
     note_launch();
-    k_load_f64<<<div_up(n, 256), 256, 0, st>>>(P, first, n, xs[0], xs[1], xs[2], us[0], us[1], us[2], g);
+    k_load_f64<<<div_up(n, 256), 256, 0, st>>>(P, first, n, xs[0], xs[1], xs[2], us[0], us[1], us[2], g, bad);
 }
 
 void launch_unload_f32(const PartF32 &P, const Grid &g, double *const *xs, double *const *us, uint8_t *alive,

@@ -46,10 +46,12 @@ void launch_push_f64(const PartF64 &P, double *F, const Grid &g, const PushConst
                      cudaStream_t st);
 void launch_gather_f32(const PartF32 &P, const float *F, const Grid &g, double *out, cudaStream_t st);
 void launch_gather_f64(const PartF64 &P, const double *F, const Grid &g, double *out, cudaStream_t st);
+// (bad: the lowest index of a particle outside the domain or with a
+// non-finite momentum; such particles are not stored; preset to all ones)
 void launch_load_f32(const PartF32 &P, long long first, long long n, const double *const *xs,
-                     const double *const *us, const Grid &g, cudaStream_t st);
+                     const double *const *us, const Grid &g, unsigned long long *bad, cudaStream_t st);
 void launch_load_f64(const PartF64 &P, long long first, long long n, const double *const *xs,
-                     const double *const *us, const Grid &g, cudaStream_t st);
+                     const double *const *us, const Grid &g, unsigned long long *bad, cudaStream_t st);
 void launch_unload_f32(const PartF32 &P, const Grid &g, double *const *xs, double *const *us, uint8_t *alive,
                        cudaStream_t st);
 void launch_unload_f64(const PartF64 &P, const Grid &g, double *const *xs, double *const *us, uint8_t *alive,
