@@ -25,6 +25,7 @@ import math
 import os
 import subprocess
 import sys
+import tempfile
 import time
 
 import numpy as np
@@ -43,6 +44,17 @@ def _peaks():
         return float(p["hbm_gbs"]), "measured"
     except Exception:
         return 6800.0, "fallback"
+
+
+def max_over_ranks(t_local, dist, device="cuda"):
+    """the slowest rank's time: the replicas run independently, and the job
+    takes as long as its slowest one"""
+    if not dist:
+        return t_local
+    import torch
+    tt = torch.tensor([t_local], device=device, dtype=torch.float64)
+    dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+    return float(tt.item())
 
 
 def make_workload(name, rank=0, sample=None, beam=10_000_000):
@@ -116,11 +128,11 @@ class Clocks:
     def __init__(self, dev):
         self.dev = dev
         self.p = None
-        self.path = os.path.join(ROOT, "gpurun_out", f"clocks_{os.getpid()}.csv")
+        fd, self.path = tempfile.mkstemp(prefix="clocks_", suffix=".csv")
+        os.close(fd)
 
     def __enter__(self):
         try:
-            os.makedirs(os.path.dirname(self.path), exist_ok=True)
             self.f = open(self.path, "w")
             self.p = subprocess.Popen(["nvidia-smi", f"--id={self.dev}", f"--query-gpu={self.Q}",
                                        "--format=csv,noheader,nounits", "-lms", "200"], stdout=self.f,
@@ -270,12 +282,7 @@ def run_qed(args, w, pic, torch, stream, timed, rank, world, dist, local, l2_not
             ms, prof = timed(sim, K, profile=True)
         d = sim.pic_diagnostics()
         n1 = sum(d["n_alive"])
-        t_local = float(np.sum(ms)) / 1e3
-        t = t_local
-        if dist:
-            tt = torch.tensor([t_local], device="cuda", dtype=torch.float64)
-            dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-            t = float(tt.item())
+        t = max_over_ranks(float(np.sum(ms)) / 1e3, dist)
         runs[mode] = {"value": world * 0.5 * (n0 + n1) * K / t, "ms_per_step": 1e3 * t / K, "n_alive": d["n_alive"],
                       "U_kin": d["U_kin"], "U_EM": d["U_E"] + d["U_B"], "E_photon_lost": d["E_photon_lost"],
                       "spectrum": photon_spectrum(sim, w.qed["photon_sp"], edges), "prof": prof, "clocks": clk.summary(),
@@ -469,12 +476,7 @@ def main():
     torch.cuda.synchronize()
     with Clocks(local) as clk:
         ms, prof = timed(sim, args.steps, profile=True)
-    t_local = float(np.sum(ms)) / 1e3
-    t = t_local
-    if dist:
-        tt = torch.tensor([t_local], device="cuda", dtype=torch.float64)
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        t = float(tt.item())
+    t = max_over_ranks(float(np.sum(ms)) / 1e3, dist)
     value = world * npart * args.steps / t
     flushed = None
     if continuous:

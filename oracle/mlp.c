@@ -1,7 +1,7 @@
 /*
  * mlp.c -- FP64 reference of the small network that can stand in for the
- * QED tables (test infrastructure: it is the judge of the GPU network's
- * gradients).  Architecture 2 -> 64 -> 64 -> 64 -> 2 with SiLU on the hidden
+ * QED tables (test infrastructure: the reference the GPU network's
+ * gradients are checked against).  Architecture 2 -> 64 -> 64 -> 64 -> 2 with SiLU on the hidden
  * layers, parameters packed as
  *   W0[64][2] b0[64] W1[64][64] b1[64] W2[64][64] b2[64] W3[2][64] b3[2]
  * Loss: L = (1/n) sum_i sum_o (y_io - t_io)^2.
