@@ -264,7 +264,7 @@ def run_qed(args, w, pic, torch, stream, timed, rank, world, dist, local, l2_not
     for mode in modes:
         prec = pic.FP64_PLAIN if mode == "fp64" else pic.FP32_CELLOFF
         sim = pic.from_workload(w, precision=prec, sort_interval=args.sort_interval, stream=stream.cuda_stream,
-                                seed=0x5EED + rank)
+                                seed=0x5EED + rank, push_variant=args.push_variant)
         train = None
         if mode == "surrogate":
             cmin = {pic.QED_EMISSION: 0.0, pic.QED_PAIR: args.qed_pair_chi_min}
@@ -378,6 +378,8 @@ def main():
     ap.add_argument("--rows", type=int, default=None,
                     help="smaller case for profiling: ny of laser_foil_2d, nz of thermal_3d (not a bench line)")
     ap.add_argument("--qed-modes", default="surrogate,table,fp64", help="forms run by the QED workloads")
+    ap.add_argument("--push-variant", type=int, default=0,
+                    help="0: default kernels, 2: surrogate of the photon push per CTA on tcgen05 (QED workloads)")
     ap.add_argument("--mlp-rows", type=int, default=0,
                     help="instead of a PIC workload: evaluate a random surrogate network on this many rows with "
                          "the mma.sync and the tcgen05 kernels (profiling aid; kernel times come from ncu)")

@@ -236,7 +236,7 @@ int sort_species(pic_sim *s, int i)
 
 bool use_tile_push(const pic_sim *s, const SpeciesState &p)
 {
-    if (s->push_variant != PIC_PUSH_AUTO || !p.items_valid || s->precision != PIC_PREC_FP32_CELLOFF ||
+    if (s->push_variant == PIC_PUSH_SIMPLE || !p.items_valid || s->precision != PIC_PREC_FP32_CELLOFF ||
         p.kind != PIC_KIND_MASSIVE || (s->qed_on && p.qed))
         return false;
     if (s->g.dim == 3) return tile3d_push_supported(s->g);
@@ -386,7 +386,8 @@ void push_species(pic_sim *s, int i, float *F)
 {
     SpeciesState &p = s->sp[i];
     if (p.kind == PIC_KIND_PHOTON) {
-        launch_push_photon_f32(view32(s, i, p.cur), F, s->g, push_const(s, p), qed_params(s, i), s->d_err, s->st);
+        launch_push_photon_f32(view32(s, i, p.cur), F, s->g, push_const(s, p), qed_params(s, i), s->d_err, s->st,
+                               s->push_variant == PIC_PUSH_MLP_TC);
         return;
     }
     if (s->qed_on && p.qed) {
@@ -555,6 +556,8 @@ int pic_create(const pic_grid *grid, double dt, const pic_species *species, int 
     int prec = opt ? opt->precision : PIC_PREC_FP32_CELLOFF;
     if (prec != PIC_PREC_FP32_CELLOFF && prec != PIC_PREC_FP64_PLAIN)
         return fail(s, PIC_ERR_ARG, "pic_create: unknown precision");
+    if (opt && (opt->push_variant < PIC_PUSH_AUTO || opt->push_variant > PIC_PUSH_MLP_TC))
+        return fail(s, PIC_ERR_ARG, "pic_create: unknown push variant");
     Grid g{};
     g.dim = grid->dim;
     g.dt = dt;

@@ -11,6 +11,10 @@
 // Photons: move at c along k, gather E, B at x^{n+1/2}, tau -= W_pair dt with
 // chi_gamma from k; when tau <= 0 the photon converts (the pair fraction v
 // from the inverse CDF of Eq. (24)); no current.
+#include <algorithm>
+
+#include "mlp_host.cuh"
+#include "mlp_tc.cuh"
 #include "push_dev.cuh"
 #include "qed_host.cuh"
 
@@ -291,6 +295,120 @@ __global__ void __launch_bounds__(256, SURR ? 2 : 1) k_push_photon_f32(PartF32 P
     if (event) reinterpret_cast<float4 *>(q.evk)[p] = evd;
 }
 
+// The photon push with the pair network on the tcgen05 tensor cores:
+// persistent CTAs of 128 threads walk tiles of 128 photon slots (slots up
+// to P.n, so that the scan's end slot and the dead slots get a zero flag);
+// the network is evaluated by the whole CTA (mlp_eval_cta: one row per
+// thread, accumulators in tensor memory) for every tile with a photon in
+// its chi range.  Everything else is k_push_photon_f32<DIM, true>.  (On the
+// QED collision it runs at the speed of the warp-level kernel, 2 % behind:
+// the network's cost is its per-row SiLU and FP32 work, which both share;
+// the push uses it when asked for, PIC_PUSH_MLP_TC.)
+template <int DIM>
+__global__ void __launch_bounds__(kMlpTcRows, 4) k_push_photon_tc(PartF32 P, const float *__restrict__ F, Grid g,
+                                                                PushConst pc, QedParams q, int *err)
+{
+    extern __shared__ unsigned char smem_raw[];
+    MlpTcSmem &S = *reinterpret_cast<MlpTcSmem *>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
+    mlp_tc_setup(S, q.net);
+    uint32_t phase = 0;
+    const long long nlive = *P.dn;
+    for (long long tile = blockIdx.x; tile * kMlpTcRows <= P.n; tile += gridDim.x) {
+        const long long p = tile * kMlpTcRows + threadIdx.x;
+        const bool live = p < nlive && P.cell[p] != kDead;
+        int c[3] = {0, 0, 0};
+        float o[3] = {0.f, 0.f, 0.f};
+        float kx = 0.f, ky = 0.f, kz = 0.f;
+        if (live) {
+            unpack_cell(g, P.cell[p], c[0], c[1], c[2]);
+            o[0] = P.off[0][p];
+            if (DIM >= 2) o[1] = P.off[1][p];
+            if (DIM >= 3) o[2] = P.off[2][p];
+            kx = P.u[0][p];
+            ky = P.u[1][p];
+            kz = P.u[2][p];
+        }
+        const float km = sqrtf(kx * kx + ky * ky + kz * kz);
+        const float ik = km > 0.f ? 1.0f / km : 0.f;
+        const float v[3] = {kx * ik, ky * ik, kz * ik};
+#pragma unroll
+        for (int d = 0; d < DIM; d++) drift_f32(c[d], o[d], pc.hdx_f[d] * v[d]);
+        float chi = 0.f, x0 = 0.f, x1 = 0.f, y0 = 0.f, y1 = 0.f;
+        uint32_t w[4] = {0u, 0u, 0u, 0u};
+        bool inr = false;
+        if (q.on && live) {
+            int icn[3] = {0, 0, 0}, ich[3] = {0, 0, 0};
+            float wn[3][3], wh[3][3];
+#pragma unroll
+            for (int d = 0; d < DIM; d++) axis_w_f32(c[d], o[d], icn[d], wn[d], ich[d], wh[d]);
+            float eb[6];
+            gather<float, DIM>(F, g, icn, wn, ich, wh, eb);
+            chi = chi_f32(km, kx, ky, kz, eb[0], eb[1], eb[2], eb[3], eb[4], eb[5], (float)q.inv_Es);
+            float lnchi;
+            inr = km > 0.f && mlp_in_range_f32(q.nrm, chi, lnchi);
+            if (inr) {
+                const uint64_t id = q.id[p];
+                philox4x32_10((uint32_t)id, (uint32_t)(id >> 32), q.step, QP_PAIR, q.key[0], q.key[1], w);
+                mlp_inputs_f32(q.nrm, QED_PAIR, lnchi, (float)uniform24(w[0]), x0, x1);
+            }
+        }
+        if (q.on && __syncthreads_or(inr)) {
+            if (!mlp_eval_cta(S, phase, x0, x1, y0, y1)) {
+                // the tensor cores did not answer: flag it, give the MMAs in
+                // flight a last bounded wait, free the tensor memory, stop
+                if (threadIdx.x == 0) atomicOr(err, ERR_TIMEOUT);
+                mbar_wait(&S.bar, phase, 1 << 20);
+                break;
+            }
+        }
+        if (!live) {
+            if (p <= P.n) q.ev[p] = 0;
+            continue;
+        }
+        uint32_t event = 0;
+        float4 evd = make_float4(0.f, 0.f, 0.f, 0.f);
+        if (q.on) {
+            const float G = inr ? mlp_rate_f32(q.nrm, QED_PAIR, chi, y1) : qed_rate_f32(q.T, QED_PAIR, chi);
+            double tau = q.tau[p] - (km > 0.f ? (double)((float)q.pref * G / km) : 0.0);
+            if (tau <= 0.0) {
+                if (!inr) {
+                    const uint64_t id = q.id[p];
+                    philox4x32_10((uint32_t)id, (uint32_t)(id >> 32), q.step, QP_PAIR, q.key[0], q.key[1], w);
+                }
+                const double r0 = uniform24(w[0]);
+                const double vf = inr ? mlp_fraction(QED_PAIR, y0, r0) : qed_sample<float>(q.T, QED_PAIR, chi, r0);
+                event = 1;
+                evd = make_float4(kx, ky, kz, (float)vf);
+                tau = -log(uniform24(w[1]));
+            }
+            q.tau[p] = tau;
+        }
+#pragma unroll
+        for (int d = 0; d < DIM; d++) drift_f32(c[d], o[d], pc.hdx_f[d] * v[d]);
+        bool dead = false;
+#pragma unroll
+        for (int d = 0; d < DIM; d++) {
+            if (g.bc[d] == PERIODIC) {
+                if (c[d] < 0) c[d] += g.n[d];
+                else if (c[d] >= g.n[d]) c[d] -= g.n[d];
+            } else if (c[d] < 0 || c[d] >= g.n[d]) {
+                dead = true;
+            }
+        }
+        if (dead) {
+            P.cell[p] = kDead;
+            event = 0;  // a photon leaving through an absorbing face does not convert
+        } else {
+            P.cell[p] = pack_cell(g, c[0], DIM >= 2 ? c[1] : 0, DIM >= 3 ? c[2] : 0);
+        }
+#pragma unroll
+        for (int d = 0; d < DIM; d++) P.off[d][p] = o[d];
+        q.ev[p] = event;
+        if (event) reinterpret_cast<float4 *>(q.evk)[p] = evd;
+    }
+    mlp_tc_teardown(S);
+}
+
 // ---------------------------------------------------------------------
 // FP64 plain form: absolute positions, everything in double precision,
 // the tables' FP64 copy (no surrogate).  Event data: 4 doubles per particle.
@@ -514,12 +632,32 @@ void launch_push_qed_f32(const PartF32 &P, float *F, const Grid &g, const PushCo
 }
 
 void launch_push_photon_f32(const PartF32 &P, const float *F, const Grid &g, const PushConst &pc,
-                            const QedParams &q, int *err, cudaStream_t st)
+                            const QedParams &q, int *err, cudaStream_t st, bool tc)
 {
     if (P.n == 0) return;
     note_launch();
     const int nb = div_up(P.n + 1, 256);
-    if (q.on && q.net) {
+    if (q.on && q.net && tc) {
+        const int sm = (int)mlp_tc_smem_bytes();
+        static bool attr = false;
+        if (!attr) {
+            cudaFuncSetAttribute(k_push_photon_tc<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
+            cudaFuncSetAttribute(k_push_photon_tc<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
+            cudaFuncSetAttribute(k_push_photon_tc<3>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
+            attr = true;
+        }
+        static int nsm = 0;
+        if (!nsm) {
+            int dev = 0;
+            cudaGetDevice(&dev);
+            cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+        }
+        const long long tiles = P.n / kMlpTcRows + 1;  // slots 0..P.n
+        const int grid = (int)std::min<long long>(tiles, 4ll * nsm);
+        if (g.dim == 1) k_push_photon_tc<1><<<grid, kMlpTcRows, sm, st>>>(P, F, g, pc, q, err);
+        else if (g.dim == 2) k_push_photon_tc<2><<<grid, kMlpTcRows, sm, st>>>(P, F, g, pc, q, err);
+        else k_push_photon_tc<3><<<grid, kMlpTcRows, sm, st>>>(P, F, g, pc, q, err);
+    } else if (q.on && q.net) {
         const int sm = kMlpStageBytes;
         if (g.dim == 1) k_push_photon_f32<1, true><<<nb, 256, sm, st>>>(P, F, g, pc, q, err);
         else if (g.dim == 2) k_push_photon_f32<2, true><<<nb, 256, sm, st>>>(P, F, g, pc, q, err);

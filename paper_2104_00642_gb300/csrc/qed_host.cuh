@@ -32,7 +32,9 @@ void launch_push_photon_f64(const PartF64 &P, const double *F, const Grid &g, co
                             const QedParams &q, int *err, cudaStream_t st);
 void launch_push_qed_f32(const PartF32 &P, float *F, const Grid &g, const PushConst &pc, const QedParams &q,
                          int *err, double *e_abs, cudaStream_t st);
+// (tc: with the surrogate, evaluate the pair network per CTA on the tcgen05
+// tensor cores instead of per warp with mma.sync)
 void launch_push_photon_f32(const PartF32 &P, const float *F, const Grid &g, const PushConst &pc,
-                            const QedParams &q, int *err, cudaStream_t st);
+                            const QedParams &q, int *err, cudaStream_t st, bool tc);
 
 }  // namespace pic

@@ -23,7 +23,7 @@ ERRORS = {-1: "PIC_ERR_ARG", -2: "PIC_ERR_CFL", -3: "PIC_ERR_CUDA", -4: "PIC_ERR
           -5: "PIC_ERR_NONFINITE", -6: "PIC_ERR_NOMEM", -7: "PIC_ERR_STATE"}
 PERIODIC, ABSORB = 0, 1
 FP32_CELLOFF, FP64_PLAIN = 0, 1
-PUSH_AUTO, PUSH_SIMPLE = 0, 1
+PUSH_AUTO, PUSH_SIMPLE, PUSH_MLP_TC = 0, 1, 2
 EX, EY, EZ, BX, BY, BZ, JX, JY, JZ, RHO = range(10)
 MAX_SPECIES = 8
 

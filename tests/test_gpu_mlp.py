@@ -255,6 +255,31 @@ def test_surrogate_monte_carlo_in_the_push(trained):
     assert ns > 30 and abs(ns - nt) <= 4.0 * np.sqrt(nt) + 0.05 * nt, counts
 
 
+def test_photon_push_tensor_core_network_matches_warp_network(trained):
+    """The photon push evaluates the pair network per warp with mma.sync (the
+    default) or per CTA on tcgen05 (PIC_PUSH_MLP_TC): the same seeded run
+    through both gives the same photons and pairs, and the photons' optical
+    depths (driven by the network's rate) agree to FP32 rounding."""
+    s0, _ = trained
+    params = {p: s0.pic_mlp_get(p) for p in (pic.QED_EMISSION, pic.QED_PAIR)}
+    runs = {}
+    for variant in (pic.PUSH_AUTO, pic.PUSH_MLP_TC):
+        s = pic.pic_create(1, (16,), (1.0,), Q.DT, Q.species_spec(), seed=Q.SEED, push_variant=variant)
+        s.pic_set_qed(photon_sp=2, electron_sp=0, positron_sp=1, lambda_r_m=Q.LAMBDA, mode=pic.QED_SURROGATE)
+        for p, (P, info) in params.items():
+            s.pic_mlp_set(p, P, info["chi_min"], info["chi_max"], info["mu"], info["sd"])
+        s.pic_set_field(pic.BZ, np.full(s.box(), Q.B0))
+        s.pic_load_particles(0, *Q.electrons())
+        s.pic_step(40)
+        gid, gtau = s.pic_get_qed_state(2)
+        runs[variant] = (dict(zip(gid.tolist(), gtau.tolist())), s.pic_particle_count(1))
+    (ta, na), (tb, nb) = runs[pic.PUSH_MLP_TC], runs[pic.PUSH_AUTO]
+    assert len(ta) > 256 and abs(len(ta) - len(tb)) <= 2 and abs(na - nb) <= 2, (len(ta), len(tb), na, nb)
+    common = [i for i in ta if i in tb]
+    d = np.array([abs(ta[i] - tb[i]) / max(abs(tb[i]), 1e-12) for i in common])
+    assert len(common) >= len(ta) - 2 and np.median(d) < 1e-5, (len(common), np.median(d), d.max())
+
+
 def test_what_the_network_gains(trained):
     """What the network buys against the tables: the device bytes the push
     reads for one process (network image vs rate + inverse-CDF tables), and
