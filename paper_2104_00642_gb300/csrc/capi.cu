@@ -715,6 +715,17 @@ int pic_sync(pic_sim *s)
     return PIC_OK;
 }
 
+// the device address of a page-locked, mapped host array, else nullptr
+static const double *mapped_device_ptr(const double *h)
+{
+    cudaPointerAttributes a{};
+    if (cudaPointerGetAttributes(&a, h) != cudaSuccess) {
+        cudaGetLastError();  // not a pointer the runtime knows: clear the error
+        return nullptr;
+    }
+    return a.type == cudaMemoryTypeHost && a.devicePointer ? static_cast<const double *>(a.devicePointer) : nullptr;
+}
+
 int pic_load_particles(pic_sim *s, int sp, int64_t n, const double *x, const double *y, const double *z,
                        const double *ux, const double *uy, const double *uz)
 {
@@ -731,19 +742,30 @@ int pic_load_particles(pic_sim *s, int sp, int64_t n, const double *x, const dou
     int rc = read_count(s, sp, &cnt);
     if (rc) return rc;
     if (cnt + n > p.cap) return fail(s, PIC_ERR_CAPACITY, "pic_load_particles: capacity %lld exceeded", p.cap);
+    // Page-locked host arrays mapped into the device's address space are read
+    // in place by the load kernel; any other host array goes through a device
+    // staging buffer first.
+    const double *cx[3] = {nullptr, nullptr, nullptr}, *cu[3] = {nullptr, nullptr, nullptr};
+    bool direct = true;
+    for (int d = 0; d < 3; d++) {
+        direct &= (cu[d] = mapped_device_ptr(us[d])) != nullptr;
+        if (d < g.dim) direct &= (cx[d] = mapped_device_ptr(xs[d])) != nullptr;
+    }
+    const size_t stage = direct ? 0 : (size_t)n * 6 * sizeof(double);
     double *dtmp = nullptr;
-    CK(cudaMalloc(&dtmp, (size_t)n * 6 * sizeof(double) + sizeof(unsigned long long)));
-    double *dx_[3] = {dtmp, dtmp + n, dtmp + 2 * n};
-    double *du_[3] = {dtmp + 3 * n, dtmp + 4 * n, dtmp + 5 * n};
-    unsigned long long *dbad = reinterpret_cast<unsigned long long *>(dtmp + 6 * n), hbad = ~0ull;
+    CK(cudaMalloc(&dtmp, stage + sizeof(unsigned long long)));
+    unsigned long long *dbad = reinterpret_cast<unsigned long long *>((char *)dtmp + stage), hbad = ~0ull;
     cudaError_t e = cudaMemsetAsync(dbad, 0xFF, sizeof(unsigned long long), s->st);
-    for (int d = 0; d < 3 && e == cudaSuccess; d++) {
-        if (d < g.dim) e = cudaMemcpyAsync(dx_[d], xs[d], n * sizeof(double), cudaMemcpyHostToDevice, s->st);
-        if (e == cudaSuccess) e = cudaMemcpyAsync(du_[d], us[d], n * sizeof(double), cudaMemcpyHostToDevice, s->st);
+    if (!direct) {
+        for (int d = 0; d < 3 && e == cudaSuccess; d++) {
+            double *dxd = dtmp + (size_t)d * n, *dud = dtmp + (size_t)(3 + d) * n;
+            if (d < g.dim) e = cudaMemcpyAsync(dxd, xs[d], n * sizeof(double), cudaMemcpyHostToDevice, s->st);
+            if (e == cudaSuccess) e = cudaMemcpyAsync(dud, us[d], n * sizeof(double), cudaMemcpyHostToDevice, s->st);
+            cx[d] = d < g.dim ? dxd : nullptr;
+            cu[d] = dud;
+        }
     }
     if (e == cudaSuccess) {
-        const double *cx[3] = {dx_[0], dx_[1], dx_[2]};
-        const double *cu[3] = {du_[0], du_[1], du_[2]};
         if (s->precision == PIC_PREC_FP64_PLAIN) launch_load_f64(view64(s, sp, p.cur), cnt, n, cx, cu, g, dbad, s->st);
         else launch_load_f32(view32(s, sp, p.cur), cnt, n, cx, cu, g, dbad, s->st);
         e = cudaGetLastError();

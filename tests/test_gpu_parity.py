@@ -438,3 +438,35 @@ def test_qed_foil_3d_small_energy_history(prec, qed_foil_oracles):
         assert np.max(np.abs(got[:5, c] - ref[:5, c])) <= 1e-3 * scale, (c, got[:, c], ref[:, c])
         spread = np.max(np.abs(ref[:, c] - other[:, c]))
         assert np.max(np.abs(got[5:, c] - ref[5:, c])) <= max(1e-3 * scale, 3.0 * spread), (c, got[:, c], ref[:, c])
+
+
+def test_load_from_page_locked_host_arrays():
+    """Page-locked (pinned) host arrays are read in place by the load kernel,
+    pageable ones through a device staging buffer: the same particles either
+    way, and out-of-domain particles are refused on both paths."""
+    import torch
+    w, F = random_state(2, (20, 13), (0.1, 0.12), 0.03, 3, seed=77)
+    s = w.species[0]
+    arrs = [s.x, s.y, s.ux, s.uy, s.uz]
+    pinned = []
+    for a in arrs:
+        t = torch.empty(len(a), dtype=torch.float64, pin_memory=True)
+        t.numpy()[:] = a
+        pinned.append(t)
+    got = []
+    for src in (arrs, [t.numpy() for t in pinned]):
+        sim = pic.from_workload(w, load=False, capacity_scale=2.0)
+        sim.pic_load_particles(0, src[0], src[1], None, src[2], src[3], src[4])
+        got.append(sim.pic_get_particles(0))
+        bad = [a.copy() for a in src]
+        bad[1][5] = 99.0  # outside the domain in y
+        if src is not arrs:
+            for t, b in zip(pinned, bad):
+                t.numpy()[:] = b
+            bad = [t.numpy() for t in pinned]
+        with pytest.raises(pic.PicError) as e:
+            sim.pic_load_particles(0, bad[0], bad[1], None, bad[2], bad[3], bad[4])
+        assert "ARG" in str(e.value) and "particle 5 " in str(e.value)
+        assert sim.pic_particle_count(0) == s.n
+    for k in ("x", "y", "ux", "uy", "uz"):
+        assert np.array_equal(got[0][k], got[1][k]), k
