@@ -62,6 +62,8 @@ def lib():
         L.or_weights2.argtypes = [D, P]
         L.or_gather.argtypes = [P, P, P]
         L.or_boris.argtypes = [D, D, P, P, P]
+        L.or_vay.argtypes = [D, D, P, P, P]
+        L.or_set_pusher.argtypes = [P, I]
         L.or_deposit_one.argtypes = [P, P, P, P, D]
         L.or_sort_species.argtypes = [P, I, P]
         L.or_sort_species.restype = LG
@@ -135,6 +137,13 @@ def boris(qm: float, dt: float, E, B, u) -> np.ndarray:
     E, B = _f64(E), _f64(B)
     uu = _f64(np.array(u, dtype=np.float64).copy())
     lib().or_boris(float(qm), float(dt), _ptr(E), _ptr(B), _ptr(uu))
+    return uu
+
+
+def vay(qm: float, dt: float, E, B, u) -> np.ndarray:
+    E, B = _f64(E), _f64(B)
+    uu = _f64(np.array(u, dtype=np.float64).copy())
+    lib().or_vay(float(qm), float(dt), _ptr(E), _ptr(B), _ptr(uu))
     return uu
 
 
@@ -224,6 +233,10 @@ class OracleSim:
         rc = lib().or_set_ids(self._h, int(isp), int(first), len(a), _ptr(a))
         if rc:
             raise ValueError(f"or_set_ids failed ({rc})")
+
+    def set_pusher(self, pusher):
+        """0: Boris, 1: Vay"""
+        lib().or_set_pusher(self._h, int(pusher))
 
     def set_laser(self, a0, waist, fwhm, t_peak, x_focus, yc=0.0, zc=0.0, pol=0):
         lib().or_set_laser(self._h, int(pol), float(a0), float(waist), float(fwhm), float(t_peak),

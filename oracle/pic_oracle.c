@@ -97,6 +97,7 @@ struct osim {
     long step;
     int sort_interval;
     int tile[3];
+    int pusher; /* 0: Boris, 1: Vay */
     olaser L;
     double e_absorbed;
     /* QED */
@@ -555,6 +556,40 @@ void or_boris(double qm, double dt, const double *E, const double *B, double *u)
 }
 
 /* ------------------------------------------------------------------ */
+/* Vay's pusher, the alternative Sec. II.C names for fields whose      */
+/* electric and magnetic forces nearly cancel (J.-L. Vay, Phys.        */
+/* Plasmas 15, 056701 (2008)): a first half kick with the full Lorentz */
+/* force at the old velocity, then the second half kick solved for the */
+/* new gamma in closed form, so that a particle moving at the E x B    */
+/* drift velocity (E + v x B = 0) keeps its momentum exactly.          */
+/* ------------------------------------------------------------------ */
+
+void or_vay(double qm, double dt, const double *E, const double *B, double *u)
+{
+    const double h = 0.5 * qm * dt;
+    double tau[3], up[3];
+    const double g0 = sqrt(1.0 + u[0] * u[0] + u[1] * u[1] + u[2] * u[2]);
+    for (int d = 0; d < 3; d++) tau[d] = h * B[d];
+    /* u' = u + (q dt / m) (E + v x B / 2), v = u / gamma */
+    up[0] = u[0] + 2.0 * h * E[0] + (u[1] * tau[2] - u[2] * tau[1]) / g0;
+    up[1] = u[1] + 2.0 * h * E[1] + (u[2] * tau[0] - u[0] * tau[2]) / g0;
+    up[2] = u[2] + 2.0 * h * E[2] + (u[0] * tau[1] - u[1] * tau[0]) / g0;
+    const double tau2 = tau[0] * tau[0] + tau[1] * tau[1] + tau[2] * tau[2];
+    const double ustar = up[0] * tau[0] + up[1] * tau[1] + up[2] * tau[2];
+    const double sigma = 1.0 + up[0] * up[0] + up[1] * up[1] + up[2] * up[2] - tau2;
+    const double g1 = sqrt(0.5 * (sigma + sqrt(sigma * sigma + 4.0 * (tau2 + ustar * ustar))));
+    double t[3];
+    for (int d = 0; d < 3; d++) t[d] = tau[d] / g1;
+    const double sinv = 1.0 / (1.0 + t[0] * t[0] + t[1] * t[1] + t[2] * t[2]);
+    const double ut = up[0] * t[0] + up[1] * t[1] + up[2] * t[2];
+    u[0] = sinv * (up[0] + ut * t[0] + (up[1] * t[2] - up[2] * t[1]));
+    u[1] = sinv * (up[1] + ut * t[1] + (up[2] * t[0] - up[0] * t[2]));
+    u[2] = sinv * (up[2] + ut * t[2] + (up[0] * t[1] - up[1] * t[0]));
+}
+
+void or_set_pusher(osim *s, int pusher) { s->pusher = pusher; }
+
+/* ------------------------------------------------------------------ */
 /* Esirkepov charge-conserving current, Eqs. (20)-(22)                 */
 /* ------------------------------------------------------------------ */
 
@@ -790,7 +825,8 @@ static void push_species(osim *s, osp *p)
         half_drift(s, xh, u, 1.0);                 /* x^{n+1/2} */
         double eb[6];
         or_gather(s, xh, eb);                      /* E, B at x^{n+1/2} */
-        or_boris(qm, s->dt, eb, eb + 3, u);        /* u^{n+1} */
+        if (s->pusher) or_vay(qm, s->dt, eb, eb + 3, u);  /* u^{n+1} */
+        else or_boris(qm, s->dt, eb, eb + 3, u);
         int emitted = 0;
         double kph[3] = {0, 0, 0};
         if (mc) {

@@ -33,6 +33,10 @@ void or_set_laser(osim *s, int pol, double a0, double waist, double fwhm, double
 void or_weights2(double delta, double *w);
 void or_gather(const osim *s, const double *x, double *eb);
 void or_boris(double qm, double dt, const double *E, const double *B, double *u);
+/* Vay's pusher (Sec. II.C's alternative to Boris), same arguments */
+void or_vay(double qm, double dt, const double *E, const double *B, double *u);
+/* 0: Boris (default), 1: Vay, for every massive species of the step */
+void or_set_pusher(osim *s, int pusher);
 void or_deposit_one(osim *s, const double *x0, const double *x1, const double *v, double qw);
 long or_sort_species(osim *s, int isp, long *perm_out);
 int or_step(osim *s, long nsteps);

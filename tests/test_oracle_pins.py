@@ -210,6 +210,64 @@ def test_boris_ExB_drift():
 
 
 # --------------------------------------------------------------------------
+# Vay's pusher (the alternative Sec. II.C names after Eq. (16))
+# --------------------------------------------------------------------------
+
+def _force_free(Ey=0.9, beta=None):
+    B = np.array([0.0, 0.0, 1.0])
+    E = np.array([0.0, Ey, 0.0])
+    v = np.cross(E, B) / (B @ B)  # E + v x B = 0
+    return E, B, v / math.sqrt(1.0 - v @ v)
+
+
+def test_vay_keeps_the_force_free_drift_and_boris_does_not():
+    """A particle moving at v = E x B / B^2 feels no force (E + v x B = 0):
+    Vay's momentum stays put to round-off over 100 steps at |E| = 0.9 |B|
+    (gamma 2.29); Boris, which rotates with the half-kicked momentum, drifts
+    off by more than 0.5 % (the case Sec. II.C warns about)."""
+    E, B, u0 = _force_free()
+    uv, ub = u0.copy(), u0.copy()
+    for _ in range(100):
+        uv = O.vay(-1.0, 0.2, E, B, uv)
+        ub = O.boris(-1.0, 0.2, E, B, ub)
+    assert np.max(np.abs(uv - u0)) < 1e-13 * np.linalg.norm(u0)
+    assert np.max(np.abs(ub - u0)) > 5e-3 * np.linalg.norm(u0)
+
+
+def test_vay_pure_fields_and_order():
+    """Pure B: |u| is conserved to round-off; pure E: Vay equals Boris
+    (both u + q_m dt E); in general fields the two schemes differ per step
+    by O(dt^3) (both second order): halving dt divides the difference by
+    about eight."""
+    u = np.array([3.0, 1.0, 0.5])
+    B = np.array([0.3, -0.2, 1.1])
+    E = np.array([0.2, -0.1, 0.3])
+    uv = O.vay(-1.0, 0.3, np.zeros(3), B, u)
+    assert abs(np.linalg.norm(uv) - np.linalg.norm(u)) < 1e-14 * np.linalg.norm(u)
+    assert np.max(np.abs(O.vay(-1.0, 0.3, E, np.zeros(3), u) - (u - 0.3 * E))) < 1e-14
+    d = [np.max(np.abs(O.vay(-1.0, dt, E, B, u) - O.boris(-1.0, dt, E, B, u))) for dt in (0.1, 0.05, 0.025)]
+    assert 6.0 < d[0] / d[1] < 10.0 and 6.0 < d[1] / d[2] < 10.0, d
+
+
+def test_vay_in_the_step_moves_at_the_drift_velocity():
+    """Whole split step with Vay (a periodic 2D box, uniform crossed fields,
+    negligible charge): a particle launched at the force-free momentum moves
+    at E x B / B^2, x advancing by v dt every step to round-off."""
+    E, B, u0 = _force_free(Ey=0.5)
+    o = O.OracleSim(2, (16, 8), (0.5, 0.5), 0.05)
+    o.add_species(-1.0, 1.0, 1e-15, 4)
+    o.set_pusher(1)
+    o.set_field(O.EY, np.full(o.box(), E[1]))
+    o.set_field(O.BZ, np.full(o.box(), B[2]))
+    o.load(0, np.array([1.3]), np.array([2.1]), None, np.array([u0[0]]), np.array([u0[1]]), np.array([u0[2]]))
+    o.step(40)
+    p = o.particles(0)
+    v = u0 / math.sqrt(1.0 + u0 @ u0)
+    assert abs(p["x"][0] - (1.3 + 40 * 0.05 * v[0])) < 1e-6 and abs(p["y"][0] - 2.1) < 1e-9
+    assert abs(p["ux"][0] - u0[0]) < 1e-6 * abs(u0[0])
+
+
+# --------------------------------------------------------------------------
 # Esirkepov deposit (Eqs. (20)-(22)): continuity to round-off, path average
 # --------------------------------------------------------------------------
 
