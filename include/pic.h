@@ -104,12 +104,15 @@ typedef struct {
                          PIC_PUSH_MLP_TC (as AUTO, but the surrogate of the photon push evaluated per
                          CTA on the tcgen05 tensor cores instead of per warp with mma.sync) */
     uint64_t seed;    /* key of the Philox4x32-10 stream of the QED Monte Carlo */
+    int pusher;       /* momentum update: PIC_PUSHER_BORIS (Eqs. 13-16) or PIC_PUSHER_VAY (the
+                         alternative Sec. II.C names after Eq. 16 for nearly cancelling E and v x B) */
 } pic_options;
 
 /* Push kernels: AUTO uses the tiled shared-memory kernel wherever it exists
  * (2D grids, FP32 form, 8x8 or 16x16 tiles, particles sorted at least once)
  * and the simple kernel elsewhere; SIMPLE always uses the simple kernel. */
 enum { PIC_PUSH_AUTO = 0, PIC_PUSH_SIMPLE = 1, PIC_PUSH_MLP_TC = 2 };
+enum { PIC_PUSHER_BORIS = 0, PIC_PUSHER_VAY = 1 };
 
 /* Laser entering through the x-min face (requires bc[0] == PIC_BC_ABSORB):
  * paraxial Gaussian beam of peak amplitude a0 (normalised field), waist

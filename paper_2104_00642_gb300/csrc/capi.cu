@@ -74,6 +74,7 @@ struct pic_sim {
     Grid g{};
     int precision = PIC_PREC_FP32_CELLOFF;
     int push_variant = PIC_PUSH_AUTO;
+    int pusher = PIC_PUSHER_BORIS;
     // QED
     uint64_t seed = 0;
     pic_qed qed{};
@@ -203,6 +204,7 @@ PushConst push_const(const pic_sim *s, const SpeciesState &p)
         if (d < g.dim) dV *= g.dx[d];
     }
     pc.wmdV = p.w * p.m * dV;
+    pc.pusher = s->pusher;
     pc.qmdt2_f = (float)pc.qmdt2;
     pc.qw_f = (float)pc.qw;
     for (int d = 0; d < 3; d++) {
@@ -558,6 +560,8 @@ int pic_create(const pic_grid *grid, double dt, const pic_species *species, int 
         return fail(s, PIC_ERR_ARG, "pic_create: unknown precision");
     if (opt && (opt->push_variant < PIC_PUSH_AUTO || opt->push_variant > PIC_PUSH_MLP_TC))
         return fail(s, PIC_ERR_ARG, "pic_create: unknown push variant");
+    if (opt && opt->pusher != PIC_PUSHER_BORIS && opt->pusher != PIC_PUSHER_VAY)
+        return fail(s, PIC_ERR_ARG, "pic_create: unknown pusher");
     Grid g{};
     g.dim = grid->dim;
     g.dt = dt;
@@ -606,6 +610,7 @@ int pic_create(const pic_grid *grid, double dt, const pic_species *species, int 
     s->precision = prec;
     s->sort_interval = opt ? opt->sort_interval : 0;
     s->push_variant = opt ? opt->push_variant : PIC_PUSH_AUTO;
+    s->pusher = opt ? opt->pusher : PIC_PUSHER_BORIS;
     s->seed = opt ? opt->seed : 0;
     s->rho_bg = opt ? opt->rho_bg : 0.0;
     s->st = opt ? (cudaStream_t)opt->stream : nullptr;

@@ -132,6 +132,39 @@ __device__ __forceinline__ void boris(R &ux, R &uy, R &uz, R ex, R ey, R ez, R b
     uz = umz + (upx * sy - upy * sx) + ez;
 }
 
+// Vay's pusher (J.-L. Vay, Phys. Plasmas 15, 056701 (2008)), the
+// alternative Sec. II.C names for fields whose electric and magnetic forces
+// nearly cancel; E, B already multiplied by q_m dt / 2.  A first half kick
+// with the full Lorentz force at the old velocity, then the second half kick
+// solved for the new gamma in closed form: a particle at the E x B drift
+// velocity (E + v x B = 0) keeps its momentum exactly.
+template <typename R>
+__device__ __forceinline__ void vay(R &ux, R &uy, R &uz, R ex, R ey, R ez, R bx, R by, R bz)
+{
+    const R g0inv = R(1) / sqrt(R(1) + ux * ux + uy * uy + uz * uz);
+    const R upx = ux + R(2) * ex + (uy * bz - uz * by) * g0inv;
+    const R upy = uy + R(2) * ey + (uz * bx - ux * bz) * g0inv;
+    const R upz = uz + R(2) * ez + (ux * by - uy * bx) * g0inv;
+    const R tau2 = bx * bx + by * by + bz * bz;
+    const R ust = upx * bx + upy * by + upz * bz;
+    const R sigma = R(1) + upx * upx + upy * upy + upz * upz - tau2;
+    const R g1 = sqrt(R(0.5) * (sigma + sqrt(sigma * sigma + R(4) * (tau2 + ust * ust))));
+    const R tx = bx / g1, ty = by / g1, tz = bz / g1;
+    const R sinv = R(1) / (R(1) + tx * tx + ty * ty + tz * tz);
+    const R ut = upx * tx + upy * ty + upz * tz;
+    ux = sinv * (upx + ut * tx + (upy * tz - upz * ty));
+    uy = sinv * (upy + ut * ty + (upz * tx - upx * tz));
+    uz = sinv * (upz + ut * tz + (upx * ty - upy * tx));
+}
+
+// the momentum update of a push: Boris (pusher 0) or Vay (pusher 1)
+template <typename R>
+__device__ __forceinline__ void lorentz(int pusher, R &ux, R &uy, R &uz, R ex, R ey, R ez, R bx, R by, R bz)
+{
+    if (pusher) vay<R>(ux, uy, uz, ex, ey, ez, bx, by, bz);
+    else boris<R>(ux, uy, uz, ex, ey, ez, bx, by, bz);
+}
+
 // 1/gamma: FP32 below u^2 = 1e8 (gamma ~ 1e4), FP64 above, where 1 + u^2
 // loses the 1 in FP32.
 __device__ __forceinline__ float inv_gamma(float ux, float uy, float uz)

@@ -77,7 +77,7 @@ __device__ __forceinline__ void push_one_f32(const PartF32 &P, long long p, floa
     gather<float, DIM>(F, g, icn, wn, ich, wh, eb);
     // Boris
     const float k = pc.qmdt2_f;
-    boris<float>(ux, uy, uz, k * eb[0], k * eb[1], k * eb[2], k * eb[3], k * eb[4], k * eb[5]);
+    lorentz<float>(pc.pusher, ux, uy, uz, k * eb[0], k * eb[1], k * eb[2], k * eb[3], k * eb[4], k * eb[5]);
     float ig1 = inv_gamma(ux, uy, uz);
     u[0] = ux; u[1] = uy; u[2] = uz;
     // x^{n+1}, then x^{n+3/2}
@@ -157,7 +157,7 @@ __global__ void __launch_bounds__(256) k_push_f64(PartF64 P, double *__restrict_
     double eb[6];
     gather<double, DIM>(F, g, icn, wn, ich, wh, eb);
     const double k = pc.qmdt2;
-    boris<double>(ux, uy, uz, k * eb[0], k * eb[1], k * eb[2], k * eb[3], k * eb[4], k * eb[5]);
+    lorentz<double>(pc.pusher, ux, uy, uz, k * eb[0], k * eb[1], k * eb[2], k * eb[3], k * eb[4], k * eb[5]);
     double ig1 = inv_gamma(ux, uy, uz);
     u[0] = ux; u[1] = uy; u[2] = uz;
 #pragma unroll

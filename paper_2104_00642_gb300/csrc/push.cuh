@@ -35,6 +35,7 @@ struct PushConst {
     double wmdV;   // w * m * dV     (absorbed kinetic energy)
     // FP32 copies for the FP32 form (converted once on the host)
     float qmdt2_f, qw_f, hdx_f[3], cJ_f[3];
+    int pusher;    // 0: Boris, 1: Vay
 };
 
 void launch_push_f32(const PartF32 &P, float *F, const Grid &g, const PushConst &pc, int *err, double *e_abs,

@@ -68,7 +68,7 @@ __global__ void __launch_bounds__(256, SURR ? 2 : 1) k_push_qed_f32(PartF32 P, f
     float eb[6];
     gather<float, DIM>(F, g, icn, wn, ich, wh, eb);
     const float k = pc.qmdt2_f;
-    boris<float>(ux, uy, uz, k * eb[0], k * eb[1], k * eb[2], k * eb[3], k * eb[4], k * eb[5]);
+    lorentz<float>(pc.pusher, ux, uy, uz, k * eb[0], k * eb[1], k * eb[2], k * eb[3], k * eb[4], k * eb[5]);
     // --- QED: optical depth, emission, recoil ---
     uint32_t event = 0;
     float4 evd = make_float4(0.f, 0.f, 0.f, 0.f);
@@ -436,7 +436,7 @@ __global__ void __launch_bounds__(256) k_push_qed_f64(PartF64 P, double *__restr
     double eb[6];
     gather<double, DIM>(F, g, icn, wn, ich, wh, eb);
     const double k = pc.qmdt2;
-    boris<double>(ux, uy, uz, k * eb[0], k * eb[1], k * eb[2], k * eb[3], k * eb[4], k * eb[5]);
+    lorentz<double>(pc.pusher, ux, uy, uz, k * eb[0], k * eb[1], k * eb[2], k * eb[3], k * eb[4], k * eb[5]);
     uint32_t event = 0;
     double4 evd = make_double4(0.0, 0.0, 0.0, 0.0);
     if (q.on) {

@@ -223,7 +223,8 @@ __global__ void __launch_bounds__(kTileThreads, kTileMinBlocks)
             const bool gin = ch[0] - 1 >= bx0 && ch[0] + 2 < bx0 + B::WX && ch[1] - 1 >= by0 && ch[1] + 2 < by0 + B::WY;
             if (gin) gather2d(sF, B::N, B::WX, bx0, by0, icn, wn, ich, wh, eb);
             else gather2d(Fg, V, rs, 0, 0, icn, wn, ich, wh, eb);
-            boris_fast(ux, uy, uz, k * eb[0], k * eb[1], k * eb[2], k * eb[3], k * eb[4], k * eb[5]);
+            if (pc.pusher) vay<float>(ux, uy, uz, k * eb[0], k * eb[1], k * eb[2], k * eb[3], k * eb[4], k * eb[5]);
+            else boris_fast(ux, uy, uz, k * eb[0], k * eb[1], k * eb[2], k * eb[3], k * eb[4], k * eb[5]);
             const float ig1 = inv_gamma_fast(ux, uy, uz);
             const float d0 = hdx0 * ux * ig1, d1 = hdx1 * uy * ig1;
             drift_f32(c[0], o[0], d0);

@@ -212,7 +212,8 @@ __global__ void __launch_bounds__(kTileThreads, 5)
             }
             float eb[6];
             gather3d_box<T>(sF, o0, icn, wn, ich, wh, eb);
-            boris_fast(ux, uy, uz, k * eb[0], k * eb[1], k * eb[2], k * eb[3], k * eb[4], k * eb[5]);
+            if (pc.pusher) vay<float>(ux, uy, uz, k * eb[0], k * eb[1], k * eb[2], k * eb[3], k * eb[4], k * eb[5]);
+            else boris_fast(ux, uy, uz, k * eb[0], k * eb[1], k * eb[2], k * eb[3], k * eb[4], k * eb[5]);
             const float ig1 = inv_gamma_fast(ux, uy, uz);
             const float dd[3] = {hdx[0] * ux * ig1, hdx[1] * uy * ig1, hdx[2] * uz * ig1};
 #pragma unroll

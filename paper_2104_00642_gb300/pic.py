@@ -24,6 +24,7 @@ ERRORS = {-1: "PIC_ERR_ARG", -2: "PIC_ERR_CFL", -3: "PIC_ERR_CUDA", -4: "PIC_ERR
 PERIODIC, ABSORB = 0, 1
 FP32_CELLOFF, FP64_PLAIN = 0, 1
 PUSH_AUTO, PUSH_SIMPLE, PUSH_MLP_TC = 0, 1, 2
+PUSHER_BORIS, PUSHER_VAY = 0, 1
 EX, EY, EZ, BX, BY, BZ, JX, JY, JZ, RHO = range(10)
 MAX_SPECIES = 8
 
@@ -58,7 +59,8 @@ class pic_species(C.Structure):
 
 class pic_options(C.Structure):
     _fields_ = [("precision", C.c_int), ("sort_interval", C.c_int), ("tile", C.c_int * 3),
-                ("rho_bg", C.c_double), ("stream", C.c_void_p), ("push_variant", C.c_int), ("seed", C.c_uint64)]
+                ("rho_bg", C.c_double), ("stream", C.c_void_p), ("push_variant", C.c_int), ("seed", C.c_uint64),
+                ("pusher", C.c_int)]
 
 
 class pic_qed(C.Structure):
@@ -189,7 +191,7 @@ class Sim:
     """One simulation (a ``pic_sim*``)."""
 
     def __init__(self, dim, n, dx, dt, species, bc=(PERIODIC, PERIODIC, PERIODIC), precision=FP32_CELLOFF,
-                 sort_interval=0, tile=(0, 0, 0), rho_bg=0.0, stream=None, push_variant=0, seed=0):
+                 sort_interval=0, tile=(0, 0, 0), rho_bg=0.0, stream=None, push_variant=0, seed=0, pusher=0):
         L = load_library()
         g = pic_grid()
         g.dim = int(dim)
@@ -212,6 +214,7 @@ class Sim:
         o.stream = stream
         o.push_variant = int(push_variant)
         o.seed = int(seed) & 0xFFFFFFFFFFFFFFFF
+        o.pusher = int(pusher)
         h = C.c_void_p()
         rc = L.pic_create(C.byref(g), float(dt), sp, len(species), C.byref(o), C.byref(h))
         if rc != PIC_OK:
@@ -400,13 +403,13 @@ def pic_create(dim, n, dx, dt, species, **kw) -> Sim:
 
 
 def from_workload(w, precision=FP32_CELLOFF, sort_interval=0, capacity_scale=1.0, load=True, stream=None,
-                  tile=None, push_variant=0, seed=0) -> Sim:
+                  tile=None, push_variant=0, seed=0, pusher=0) -> Sim:
     """Create a simulation for a :class:`workloads.Workload` and load its particles
     (QED workloads: the Monte Carlo is configured in table mode first)."""
     sp = [(s.q, s.m, s.w, max(1, int(s.capacity * capacity_scale)), s.kind, s.qed) for s in w.species]
     t = tile if tile is not None else tuple(w.tile)
     sim = Sim(w.dim, w.n, w.dx, w.dt, sp, bc=w.bc, precision=precision, sort_interval=sort_interval, tile=t,
-              rho_bg=w.rho_bg, stream=stream, push_variant=push_variant, seed=seed)
+              rho_bg=w.rho_bg, stream=stream, push_variant=push_variant, seed=seed, pusher=pusher)
     if w.laser is not None:
         L = w.laser
         sim.pic_set_laser(L.a0, L.waist, L.fwhm, L.t_peak, L.x_focus, L.yc, L.zc, L.pol)

@@ -28,11 +28,12 @@ def _dt(dx, frac=0.9):
     return frac / math.sqrt(sum(1.0 / d ** 2 for d in dx))
 
 
-def _make_pair(dim, prec, seed, nppc=3, fields=True, sort_interval=0, umax=0.5):
+def _make_pair(dim, prec, seed, nppc=3, fields=True, sort_interval=0, umax=0.5, pusher=0):
     n, dx = GRIDS[dim]
     w, F = random_state(dim, n, dx, _dt(dx), nppc, seed, umax=umax, fields=fields)
-    sim = pic.from_workload(w, precision=prec, sort_interval=sort_interval)
+    sim = pic.from_workload(w, precision=prec, sort_interval=sort_interval, pusher=pusher)
     o = oracle_from_workload(w, sort_interval=sort_interval)
+    o.set_pusher(pusher)
     if F is not None:
         for c in range(9):
             sim.pic_set_field(c, F[c])
@@ -56,10 +57,13 @@ def test_gather_matches_oracle(dim, prec):
         assert np.all(np.abs(got[p] - ref) <= TOL[prec] * scale + 1e-300), (p, got[p], ref)
 
 
+@pytest.mark.parametrize("pusher", [pic.PUSHER_BORIS, pic.PUSHER_VAY])
 @pytest.mark.parametrize("prec", PRECS)
 @pytest.mark.parametrize("dim", [1, 2, 3])
-def test_one_step_matches_oracle(dim, prec):
-    w, F, sim, o = _make_pair(dim, prec, seed=200 + dim)
+def test_one_step_matches_oracle(dim, prec, pusher):
+    """One whole step from random particles and fields, with Boris (Eqs.
+    13-16) or Vay's pusher (Sec. II.C's alternative)."""
+    w, F, sim, o = _make_pair(dim, prec, seed=200 + dim, pusher=pusher)
     sim.pic_step(1)
     o.step(1)
     tol = TOL[prec]
@@ -246,14 +250,16 @@ def test_empty_species_and_errors():
 # tiled 2D push (shared-memory staging and current box)
 # --------------------------------------------------------------------------
 
+@pytest.mark.parametrize("pusher", [pic.PUSHER_BORIS, pic.PUSHER_VAY])
 @pytest.mark.parametrize("tile", [8, 16])
-def test_tile_push_one_step_matches_oracle(tile):
+def test_tile_push_one_step_matches_oracle(tile, pusher):
     """Sort at step 0 (same order in both), one step through the tiled
     kernel: ragged grid (tiles do not divide it), several tiles."""
     n, dx = (40, 21), (0.1, 0.12)
     w, F = random_state(2, n, dx, _dt(dx), 4, seed=301, umax=0.9)
-    sim = pic.from_workload(w, precision=pic.FP32_CELLOFF, sort_interval=1, tile=(tile, tile, 1))
+    sim = pic.from_workload(w, precision=pic.FP32_CELLOFF, sort_interval=1, tile=(tile, tile, 1), pusher=pusher)
     o = oracle_from_workload(w, sort_interval=1, tile=(tile, tile, 1))
+    o.set_pusher(pusher)
     for c in range(9):
         sim.pic_set_field(c, F[c])
         o.set_field(c, F[c])
@@ -301,13 +307,15 @@ def test_tile_push_fallback_after_drift_matches_simple_kernel():
 # tiled 3D push (4^3 tiles, shared-memory field and current boxes)
 # --------------------------------------------------------------------------
 
-def test_tile3d_push_one_step_matches_oracle():
+@pytest.mark.parametrize("pusher", [pic.PUSHER_BORIS, pic.PUSHER_VAY])
+def test_tile3d_push_one_step_matches_oracle(pusher):
     """Sort at step 0, one step through the 3D tiled kernel: several tiles,
     tiles touching every periodic face."""
     n, dx = (16, 12, 8), (0.1, 0.12, 0.11)
     w, F = random_state(3, n, dx, _dt(dx), 3, seed=311, umax=0.9)
-    sim = pic.from_workload(w, precision=pic.FP32_CELLOFF, sort_interval=1, tile=(4, 4, 4))
+    sim = pic.from_workload(w, precision=pic.FP32_CELLOFF, sort_interval=1, tile=(4, 4, 4), pusher=pusher)
     o = oracle_from_workload(w, sort_interval=1, tile=(4, 4, 4))
+    o.set_pusher(pusher)
     for c in range(9):
         sim.pic_set_field(c, F[c])
         o.set_field(c, F[c])
@@ -470,3 +478,30 @@ def test_load_from_page_locked_host_arrays():
         assert sim.pic_particle_count(0) == s.n
     for k in ("x", "y", "ux", "uy", "uz"):
         assert np.array_equal(got[0][k], got[1][k]), k
+
+
+@pytest.mark.parametrize("prec", PRECS)
+def test_vay_keeps_the_force_free_drift_on_the_gpu(prec):
+    """Uniform crossed fields (E_y = 0.9, B_z = 1) on a periodic 2D grid,
+    light particles launched at the force-free momentum (v = E x B / B^2,
+    gamma 2.29): with Vay's pusher every momentum stays put over 40 steps of
+    dt = 0.2 (the tiled FP32 kernel and the FP64 form); Boris drifts off by
+    0.4 % (the FP64 oracle's figure)."""
+    n, dx = (32, 16), (0.5, 0.5)
+    vd = 0.9
+    u0 = vd / np.sqrt(1.0 - vd * vd)
+    N = 64
+    rng = np.random.default_rng(9)
+    x = [rng.uniform(0.0, n[d] * dx[d], N) for d in range(2)]
+    drift = {}
+    for pusher in (pic.PUSHER_VAY, pic.PUSHER_BORIS):
+        sim = pic.pic_create(2, n, dx, 0.2, [(-1.0, 1.0, 1e-15, N)], precision=prec, sort_interval=4,
+                             tile=(16, 16, 1), pusher=pusher)
+        sim.pic_set_field(pic.EY, np.full(sim.box(), vd))
+        sim.pic_set_field(pic.BZ, np.full(sim.box(), 1.0))
+        sim.pic_load_particles(0, x[0], x[1], None, np.full(N, u0), np.zeros(N), np.zeros(N))
+        sim.pic_step(40)
+        p = sim.pic_get_particles(0)
+        drift[pusher] = np.max(np.abs(np.array([p["ux"] - u0, p["uy"], p["uz"]])))
+    assert drift[pic.PUSHER_VAY] < (1e-5 if prec == pic.FP32_CELLOFF else 1e-11) * u0, drift
+    assert drift[pic.PUSHER_BORIS] > 2e-3 * u0, drift
