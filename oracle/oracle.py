@@ -80,6 +80,8 @@ def lib():
         L.or_set_qed.argtypes = [P, I, I, I, D, D, C.c_uint64]
         L.or_Es.argtypes = [P]
         L.or_Es.restype = D
+        L.or_chi.argtypes = [P, D, P, P]
+        L.or_chi.restype = D
         L.or_photon_lost.argtypes = [P]
         L.or_photon_lost.restype = D
         L.or_get_qed_state.argtypes = [P, I, P, P]
@@ -208,6 +210,12 @@ class OracleSim:
     @property
     def Es(self):
         return lib().or_Es(self._h)
+
+    def chi(self, gamma, u, eb):
+        """the quantum parameter the Monte Carlo uses for momentum u (or k) with
+        gamma (or |k|) in the fields eb = (Ex, Ey, Ez, Bx, By, Bz)"""
+        uu, e = _f64(np.asarray(u, dtype=np.float64)), _f64(np.asarray(eb, dtype=np.float64))
+        return lib().or_chi(self._h, float(gamma), _ptr(uu), _ptr(e))
 
     def photon_lost(self):
         return lib().or_photon_lost(self._h)

@@ -797,6 +797,10 @@ static double chi_of(const osim *s, double g, const double *u, const double *eb)
     return q > 0.0 ? sqrt(q) / s->Es : 0.0;
 }
 
+/* chi as the Monte Carlo evaluates it, for inspection: gamma (or |k|), u (or
+ * k) and the six fields E, B */
+double or_chi(const osim *s, double g, const double *u, const double *eb) { return chi_of(s, g, u, eb); }
+
 /* the prefactor alpha E_s dt / (sqrt 3 pi) of W dt (alpha = 1/137.035999084) */
 static double qed_pref(const osim *s)
 {
