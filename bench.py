@@ -1,20 +1,29 @@
 """Throughput benchmark of the GB300 PIC hot path.
 
-Default workload: the 2D3V laser-foil run (grid 2048x1024, dx = lambda/64,
-hydrogen slab n = 10 n_c over x-cells 1024-1087, 32 ppc of electrons and of
-protons = 4,194,304 particles, LP Gaussian laser a0 = 20 from x-min,
-absorbing x / periodic y), FP32 cell+offset form, seeded synthetic inputs.
-A "step" is one full PIC step (both field half steps, gather + Boris + drift
-+ Esirkepov deposit of every particle, current fold, tile sort every K steps).
+Default workload: the strong-field QED collision (2D3V, grid 2048x512,
+dx = lambda/32; LP laser a0 = 200 from x-min against a 1 GeV beam of 10^7
+macro-electrons; nonlinear Compton and Breit-Wheeler Monte Carlo with
+per-particle optical depth), the configuration the metric -- FP32 cell+offset
+with the surrogate network vs the plain FP64 form at equal error -- is quoted
+on.  Each form is advanced untimed to the collision, then W warm-up and K
+timed steps run through it.  A "step" is one full PIC step of every species
+(both field half steps, gather + push + QED Monte Carlo + drift + Esirkepov
+deposit, current fold, spawn of photons and pairs, tile sort every K steps).
 
-Prints one JSON line.  ``value`` is particle-steps/s measured with CUDA events
-on the simulation's stream around one ``pic_step(K)`` call, inputs resident
-in HBM; every step touches more bytes than the 126 MiB L2 holds (the line's
-``config.l2`` states how many), else the K steps are single calls with the
-L2 flushed before each.  ``per_step_l2_flushed`` repeats the measurement one
-step per call with the L2 flushed before each step.  ``e2e`` is the same metric through the public C ABI
-from pinned host arrays (particle upload, K steps, diagnostics read back).
-``--impl reference`` times the FP64 CPU oracle instead (host cores).
+Prints one JSON line.  ``value`` is particle-steps/s of the FP32+surrogate
+form (live particles of all species), CUDA events on the simulation's stream
+around one ``pic_step(K)`` call, inputs resident in HBM (each step touches
+more bytes than the L2 holds).  The line carries the FP32+tables and plain
+FP64 forms on the same window, the errors of every form against the FP64
+oracle on the collision's QED regime (tests/golden/qed_field_sample.json),
+the roofline of the dominant push kernel, ``e2e`` (the state at the window's
+start restored from a host file through the C ABI, K steps, diagnostics read
+back, host wall clock) and the oracle's CPU throughput on that sample.
+
+``--workload laser_foil_2d | thermal_3d`` time the plain PIC step (no QED)
+through the laser-slab interaction or the thermal steady state, with the
+push-kernel roofline.  ``--impl reference`` times the FP64 CPU oracle
+(host cores) on a bounded sample of the workload.
 """
 from __future__ import annotations
 
@@ -94,6 +103,10 @@ L2_BYTES = 126 * 1024 * 1024  # GB300 L2
 # K = 8: 0.338 / 0.339 / 0.370, K = 16: 0.310 / 0.317 / 0.367, K = 32: 0.298 /
 # 0.306 / 0.410; thermal_3d: K = 4: 19.6, K = 8: 20.7
 SORT_INTERVAL = {"laser_foil_2d": 16, "thermal_3d": 4}
+# untimed steps before the timed window: the laser-foil run is timed while
+# the pulse sits on the slab (its peak reaches the slab front, x = 1024 dx,
+# at t = t_peak + 1024 dx, step 3674 of 4000)
+PRE_STEPS = {"laser_foil_2d": 3680}
 
 
 def step_bytes(w, precision=0):
@@ -135,7 +148,7 @@ class Clocks:
         try:
             self.f = open(self.path, "w")
             self.p = subprocess.Popen(["nvidia-smi", f"--id={self.dev}", f"--query-gpu={self.Q}",
-                                       "--format=csv,noheader,nounits", "-lms", "200"], stdout=self.f,
+                                       "--format=csv,noheader,nounits", "-lms", "100"], stdout=self.f,
                                       stderr=subprocess.DEVNULL)
         except Exception:
             self.p = None
@@ -212,6 +225,66 @@ def oracle_rate(wname, min_seconds=10.0, max_steps=50, steps=None, sample_rows=3
                                "particles": npart}
 
 
+def cpu_model():
+    try:
+        for ln in open("/proc/cpuinfo"):
+            if ln.lower().startswith(("model name", "cpu model")):
+                return ln.split(":", 1)[1].strip()
+        out = subprocess.run(["lscpu"], capture_output=True, text=True).stdout
+        for ln in out.splitlines():
+            if ln.startswith("Model name"):
+                return ln.split(":", 1)[1].strip()
+    except Exception:
+        pass
+    import platform
+    return platform.machine()
+
+
+def _oracle_qed_chunk(args):
+    """the FP64 oracle on electrons [lo, hi) of the QED field sample (their
+    full-load identities), `steps` steps: (particle-steps, seconds)"""
+    lo, hi, steps, seed = args
+    from oracle import oracle as O
+    from paper_2104_00642_gb300 import workloads as W
+    w = W.qed_field_sample()
+    o = O.OracleSim(1, (16,), (1.0,), w.dt)
+    for sp in w.species:
+        o.add_species(sp.q, sp.m, sp.w, sp.capacity, kind=sp.kind, qed=sp.qed)
+    o.set_qed(seed=seed, **w.qed)
+    o.set_field(O.BZ, np.full(o.box(), w.notes["B0"]))
+    e = w.species[0]
+    o.load(0, e.x[lo:hi], None, None, e.ux[lo:hi], e.uy[lo:hi], e.uz[lo:hi])
+    o.set_ids(0, np.arange(lo, hi, dtype=np.uint64))
+    done = 0
+    t0 = time.perf_counter()
+    per = []
+    for _ in range(steps):
+        n = sum(int(np.sum(o.particles(i)["alive"])) for i in range(3))
+        a = time.perf_counter()
+        o.step(1)
+        per.append((n, time.perf_counter() - a))
+        done += n
+    return done, time.perf_counter() - t0, per
+
+
+def oracle_qed_rate(n_e=64, steps=8, all_cores=False, seed=0x5A3D1E):
+    """FP64 oracle throughput on the collision's QED regime (the field
+    sample): one core on n_e electrons, or every host core on its own chunk
+    of n_e electrons each (processes started with spawn)"""
+    if not all_cores:
+        ps, sec, per = _oracle_qed_chunk((0, n_e, steps, seed))
+        return ps / sec, {"cores": 1, "particle_steps": ps, "seconds": sec, "per_step": per}
+    import multiprocessing as mp
+    nc = os.cpu_count() or 1
+    jobs = [(i * n_e, (i + 1) * n_e, steps, seed) for i in range(nc)]
+    t0 = time.perf_counter()
+    with mp.get_context("spawn").Pool(nc) as pool:
+        res = pool.map(_oracle_qed_chunk, jobs)
+    wall = time.perf_counter() - t0
+    ps = sum(r[0] for r in res)
+    return ps / wall, {"cores": nc, "particle_steps": ps, "seconds": wall}
+
+
 def run_reference(args):
     """--impl reference: the FP64 CPU oracle, as it stands, on the host cores"""
     rank = int(os.environ.get("RANK", "0"))
@@ -222,6 +295,23 @@ def run_reference(args):
     for _ in range(args.warmup):
         pass
     w = args.workload
+    if w in ("qed_collision_2d", "qed_foil_3d"):
+        ps_w, sec_w, per = _oracle_qed_chunk((0, 128, args.warmup + args.steps, 0x5A3D1E))
+        per = per[args.warmup:]
+        t = float(sum(x[1] for x in per))
+        value = float(sum(x[0] for x in per)) / t
+        sample = ("the collision's QED regime, 128 electrons of the qed_field_sample (gamma 1957 +- 1 %, chi ~ 1.9, "
+                  "photons and pairs they create), FP64 oracle")
+        out = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+               "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * t / len(per),
+               "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+               "config": {"workload": sample, "precision": "fp64 absolute positions, QED rates and spectra by "
+                          "quadrature (CPU oracle)"},
+               "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample,
+                                "cpu": cpu_model()},
+               "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+        print(json.dumps(out))
+        return
     v, info = oracle_rate(w, steps=args.warmup + args.steps)
     per = info["per_step_s"][args.warmup:]
     t = float(np.sum(per))
@@ -242,14 +332,48 @@ def photon_spectrum(sim, sp, edges):
     return np.histogram(k, edges)[0]
 
 
+def qed_bytes_per_particle(dim):
+    """algorithmic HBM bytes of one particle in a QED push: the FP32 state
+    read and written once, the FP64 optical depth read and written, the
+    event flag written"""
+    return 2 * (4 + 4 * dim + 12) + 16 + 4
+
+
+def run_qed_sample(pic, mode, nets, golden):
+    """one form on the QED field sample (the stored FP64 oracle run's seeded
+    inputs): its errors against the oracle"""
+    from paper_2104_00642_gb300 import workloads as W
+    from tests import qed_setup as Q
+    ws = W.qed_field_sample()
+    prec = pic.FP64_PLAIN if mode == "fp64" else pic.FP32_CELLOFF
+    sim = pic.from_workload(ws, precision=prec, seed=golden["seed"])
+    if mode == "surrogate":
+        for p_, (P, info) in nets.items():
+            sim.pic_mlp_set(p_, P, info["chi_min"], info["chi_max"], info["mu"], info["sd"])
+        sim.pic_set_qed(mode=pic.QED_SURROGATE, **ws.qed)
+    sim.pic_set_field(pic.BZ, np.full(sim.box(), ws.notes["B0"]))
+    hist = []
+    for _ in range(ws.steps):
+        sim.pic_step(1)
+        e = sim.pic_get_particles(0)
+        a = e["alive"] == 1
+        hist.append(float(np.sum(np.sqrt(1.0 + e["ux"][a] ** 2 + e["uy"][a] ** 2 + e["uz"][a] ** 2))))
+    d = sim.pic_diagnostics()
+    fin = Q.sample_observables([sim.pic_get_particles(i) for i in range(3)], d["E_photon_lost"])
+    sim.close()
+    return Q.sample_errors({"history": hist, "final": fin}, golden)
+
+
 def run_qed(args, w, pic, torch, stream, timed, rank, world, dist, local, l2_note):
     """The strong-field QED collision: the same seeded beam through three
     forms, each advanced untimed to the collision, then W warm-up and K timed
     steps around the pulse peak: FP32 cell+offset with the surrogate networks
     (trained on the device first, untimed), FP32 with the tables, and the
     plain FP64 form with the tables.  Particle-steps count the live particles
-    of all species (trapezoid over the window).  Errors of the two FP32 forms
-    are stated against the FP64 run: energies and the photon spectrum."""
+    of all species (trapezoid over the window).  Errors: every form against
+    the FP64 oracle on the collision's QED regime (stored run), and the FP32
+    forms against the FP64 run of the window."""
+    from tests import qed_setup as Q
     K = args.steps
     if args.qed_pre is not None:
         pre = args.qed_pre
@@ -260,7 +384,10 @@ def run_qed(args, w, pic, torch, stream, timed, rank, world, dist, local, l2_not
     iph, iel, ipo = w.qed["photon_sp"], w.qed["electron_sp"], w.qed["positron_sp"]
     edges = np.logspace(np.log10(w.qed["photon_emin"]), np.log10(3000.0), 25)
     runs = {}
+    nets = {}
     modes = [m for m in args.qed_modes.split(",") if m]
+    e2e = None
+    peak, peak_kind = _peaks()
     for mode in modes:
         prec = pic.FP64_PLAIN if mode == "fp64" else pic.FP32_CELLOFF
         sim = pic.from_workload(w, precision=prec, sort_interval=args.sort_interval, stream=stream.cuda_stream,
@@ -270,24 +397,57 @@ def run_qed(args, w, pic, torch, stream, timed, rank, world, dist, local, l2_not
             cmin = {pic.QED_EMISSION: 0.0, pic.QED_PAIR: args.qed_pair_chi_min}
             train = {p: sim.pic_mlp_train(p, iterations=args.qed_train_iters, seed=17, chi_min=cmin[p])
                      for p in (pic.QED_EMISSION, pic.QED_PAIR)}
+            nets = {p: sim.pic_mlp_get(p) for p in (pic.QED_EMISSION, pic.QED_PAIR)}
             sim.pic_set_qed(mode=pic.QED_SURROGATE, **w.qed)
         with torch.cuda.stream(stream):
             sim.pic_step(pre)
         timed(sim, args.warmup)
-        n0 = sum(sim.pic_diagnostics()["n_alive"])
+        d0 = sim.pic_diagnostics()
+        n0 = sum(d0["n_alive"])
+        ckpt = None
+        if mode == modes[0] and not args.no_e2e and world == 1:
+            # the state at the window's start, in a host file (untimed)
+            fd, ckpt = tempfile.mkstemp(prefix="pic_window_", suffix=".ckpt",
+                                        dir="/dev/shm" if os.path.isdir("/dev/shm") else None)
+            os.close(fd)
+            sim.pic_save(ckpt)
         if dist:
             dist.barrier()
         torch.cuda.synchronize()
         with Clocks(local) as clk:
             ms, prof = timed(sim, K, profile=True)
+        sp_ms, sp_n = sim.pic_profile_read_species()
         d = sim.pic_diagnostics()
         n1 = sum(d["n_alive"])
         t = max_over_ranks(float(np.sum(ms)) / 1e3, dist)
+        alive_mid = [0.5 * (a + b) for a, b in zip(d0["n_alive"], d["n_alive"])]
         runs[mode] = {"value": world * 0.5 * (n0 + n1) * K / t, "ms_per_step": 1e3 * t / K, "n_alive": d["n_alive"],
                       "U_kin": d["U_kin"], "U_EM": d["U_E"] + d["U_B"], "E_photon_lost": d["E_photon_lost"],
                       "spectrum": photon_spectrum(sim, w.qed["photon_sp"], edges), "prof": prof, "clocks": clk.summary(),
-                      "train": train}
-        sim.close()
+                      "train": train, "species_ms": sp_ms, "species_pushes": sp_n, "alive_mid": alive_mid}
+        if ckpt is not None:
+            # end to end through the C ABI: restore the window's start from the
+            # host file, K steps, diagnostics read back (host wall clock)
+            size = os.path.getsize(ckpt)
+            sim.close()
+            sim = None
+            sim_e = pic.from_workload(w, precision=prec, sort_interval=args.sort_interval, stream=stream.cuda_stream,
+                                      seed=0x5EED + rank, push_variant=args.push_variant, load=False)
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            sim_e.pic_restore(ckpt)
+            sim_e.pic_step(K)
+            de = sim_e.pic_diagnostics()
+            el = time.perf_counter() - t0
+            os.unlink(ckpt)
+            assert math.isfinite(de["U_E"])
+            e2e = {"value": 0.5 * (n0 + sum(de["n_alive"])) * K / el, "unit": UNIT, "h2d_bytes_per_step": size / K,
+                   "d2h_bytes_per_step": 8 * (16 + 2 * len(w.species)) / K, "seconds": el,
+                   "note": "pic_restore of the window's start from a host file (fields, particles, networks) + "
+                           "pic_step(K) + pic_diagnostics, host wall clock"}
+            sim_e.close()
+        if sim is not None:
+            sim.close()
     ref = runs.get("fp64")
 
     def errors(r):
@@ -304,6 +464,49 @@ def run_qed(args, w, pic, torch, stream, timed, rank, world, dist, local, l2_not
                 "photon_spectrum_max_bin_rel": float(spec.max()) if big.any() else None,
                 "photon_spectrum_bins": int(big.sum())}
 
+    # errors against the FP64 oracle on the collision's QED regime (stored run)
+    vs_oracle = None
+    gpath = os.path.join(ROOT, "tests", "golden", "qed_field_sample.json")
+    if rank == 0 and os.path.exists(gpath):
+        golden = json.load(open(gpath))
+        vs_oracle = {m: run_qed_sample(pic, m, nets, golden) for m in modes if m != "surrogate" or nets}
+        vs_oracle["sample"] = ("workloads.qed_field_sample: 2048 electrons at gamma 1957 +- 1 % in a uniform B_z "
+                               "(chi ~ 1.9, the collision's peak), 48 steps, photons >= 2 m c^2 and pairs; "
+                               "oracle run stored by tests/golden/make_qed_field_sample.py")
+
+    # roofline of the first form's dominant kernel: the species push that takes
+    # the most device time (per-species CUDA events in the timed region)
+    s0 = runs[modes[0]]
+    i_dom = int(np.argmax(s0["species_ms"]))
+    per_launch_s = s0["species_ms"][i_dom] / 1e3 / max(1, s0["species_pushes"][i_dom])
+    bpp = qed_bytes_per_particle(w.dim)
+    alg = s0["alive_mid"][i_dom] * bpp
+    achieved = alg / per_launch_s / 1e9
+    kind = "photon push (pair rate" if w.species[i_dom].kind == 1 else "lepton push (gather, push, emission rate"
+    kind += ", Monte Carlo" + (", surrogate network)" if modes[0] == "surrogate" else ", tables)")
+    roof = {"bound": "hbm", "kernel": f"{kind}, species {w.species[i_dom].name}", "achieved": achieved,
+            "peak": peak, "unit": "GB/s", "frac": achieved / peak, "peak_kind": f"{peak_kind} hbm_gbs",
+            "traffic": None, "algorithmic_bytes_per_launch": alg, "avg_launch_ms": per_launch_s * 1e3,
+            "bytes_per_particle": bpp, "particles_per_launch": s0["alive_mid"][i_dom],
+            "share_of_step": s0["species_ms"][i_dom] / max(1e-30, float(sum(s0["prof"]["ms"].values())))}
+    if modes[0] == "surrogate" and w.species[i_dom].kind == 1:
+        # the network's arithmetic: 2*(2*64 + 64*64 + 64*64 + 64*2) flops per evaluation
+        fl = s0["alive_mid"][i_dom] * 2.0 * (2 * 64 + 64 * 64 * 2 + 64 * 2)
+        roof["tensor_tflops_if_every_photon_evaluates"] = fl / per_launch_s / 1e12
+
+    # CPU baseline: the oracle on the collision's QED regime
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu:
+        v1, i1 = oracle_qed_rate(n_e=64, steps=8)
+        va, ia = oracle_qed_rate(n_e=32, steps=6, all_cores=True)
+        cpu = {"value": v1, "unit": UNIT, "cores": 1, "kind": "oracle",
+               "sample": "the collision's QED regime: electrons of the qed_field_sample (gamma 1957 +- 1 %, chi ~ "
+                         "1.9) with the photons and pairs they create, FP64 oracle (QED rates and spectra by "
+                         "quadrature), 64 electrons, 8 steps", "seconds": i1["seconds"],
+               "all_cores": {"value": va, "cores": ia["cores"], "seconds": ia["seconds"],
+                             "sample": "32 electrons per core, 6 steps, one process per core"},
+               "cpu": cpu_model(), "nproc": os.cpu_count()}
+
     if "steps_to_collision" in w.notes:
         where = f"the collision is at step {w.notes['steps_to_collision']}"
     else:
@@ -319,8 +522,8 @@ def run_qed(args, w, pic, torch, stream, timed, rank, world, dist, local, l2_not
                "vs_baseline": None, "dtype": "f32", "data": "synthetic",
                "config": {"workload": describe(w), "form": modes[0],
                           "precision": "fp32 cell+offset, QED by the surrogate networks inside their chi range "
-                          "(tables outside); FP64 islands: optical depth, diagnostics" if modes[0] == "surrogate"
-                          else modes[0],
+                          "(tables outside); FP64 islands: optical depth, gamma above 1e4, diagnostics"
+                          if modes[0] == "surrogate" else modes[0],
                           "window": window,
                           "sort_interval": args.sort_interval, "replicas": world,
                           "l2": l2_note()},
@@ -329,11 +532,13 @@ def run_qed(args, w, pic, torch, stream, timed, rank, world, dist, local, l2_not
                "fp64_plain": f64 and {"value": f64["value"], "ms_per_step": f64["ms_per_step"],
                                       "first_form_over_fp64": s["value"] / f64["value"]},
                "surrogate_error_vs_fp64": errors(runs.get("surrogate")),
+               "error_vs_oracle": vs_oracle,
                "surrogate_training": {str(p): {k: v for k, v in r.items()} for p, r in tr.items()},
                "n_alive_end": {m: [int(v) for v in r["n_alive"]] for m, r in runs.items()},
                "gpu_launches": int(sum(prof["launches"].values())), "clocks": s["clocks"],
                "phases_ms_per_step": {k: v / K for k, v in prof["ms"].items()},
-               "roofline": None, "cpu_baseline": None, "e2e": None}
+               "species_push_ms_per_step": {w.species[i].name: v / K for i, v in enumerate(s["species_ms"])},
+               "roofline": roof, "cpu_baseline": cpu, "e2e": e2e}
         print(json.dumps(out))
 
 
@@ -363,11 +568,13 @@ def main():
     ap.add_argument("--steps", type=int, default=50)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="native", choices=["native", "reference"])
-    ap.add_argument("--workload", default="laser_foil_2d",
+    ap.add_argument("--workload", default="qed_collision_2d",
                     choices=["laser_foil_2d", "thermal_3d", "langmuir_1d", "qed_collision_2d", "qed_foil_3d"])
     ap.add_argument("--sort-interval", type=int, default=None,
                     help="steps between tile sorts (default: the measured best of the workload)")
     ap.add_argument("--fp64-steps", type=int, default=10)
+    ap.add_argument("--pre", type=int, default=None,
+                    help="untimed steps before the window (laser_foil_2d default: to the laser on the slab)")
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU baseline leg")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-flush", action="store_true")
@@ -470,8 +677,15 @@ def main():
         return
 
     # ---- FP32 cell+offset: the headline ----------------------------------
+    pre = args.pre
+    if pre is None:
+        pre = PRE_STEPS.get(args.workload, 0) if args.rows is None else 0
     sim = pic.from_workload(w, precision=pic.FP32_CELLOFF, sort_interval=args.sort_interval,
                             stream=stream.cuda_stream)
+    if pre:
+        with torch.cuda.stream(stream):
+            sim.pic_step(pre)  # untimed: to the phase the window measures
+    npart = sum(sim.pic_diagnostics()["n_alive"])
     timed(sim, args.warmup)
     if dist:
         dist.barrier()
@@ -511,6 +725,9 @@ def main():
     if not args.no_fp64:
         sim64 = pic.from_workload(w, precision=pic.FP64_PLAIN, sort_interval=args.sort_interval,
                                   stream=stream.cuda_stream)
+        if pre:
+            with torch.cuda.stream(stream):
+                sim64.pic_step(pre)
         timed(sim64, 3)
         ms64, _ = timed(sim64, args.fp64_steps)
         v64 = npart * args.fp64_steps / (float(np.sum(ms64)) / 1e3)
@@ -518,35 +735,30 @@ def main():
         fp64 = {"value": v64, "unit": UNIT, "ms_per_step": float(np.sum(ms64)) / args.fp64_steps,
                 "fp32_over_fp64": value / world / v64}
 
-    # ---- end to end through the C ABI from pinned host arrays --------------
+    # ---- end to end through the C ABI: the window's start state from a host
+    # file (pic_restore), K steps, diagnostics read back, host wall clock ----
     e2e = None
-    if not args.no_e2e:
-        pinned = []
-        for s in w.species:
-            arrs = []
-            for a in (s.x, s.y, s.z, s.ux, s.uy, s.uz):
-                t_ = torch.empty(a.shape[0], dtype=torch.float64, pin_memory=True)
-                t_.numpy()[:] = a
-                arrs.append(t_)
-            pinned.append(arrs)
+    if not args.no_e2e and world == 1:
+        fd, ckpt = tempfile.mkstemp(prefix="pic_window_", suffix=".ckpt",
+                                    dir="/dev/shm" if os.path.isdir("/dev/shm") else None)
+        os.close(fd)
+        sim.pic_save(ckpt)  # the state after the timed window: the next window starts here
+        size = os.path.getsize(ckpt)
         sim.close()
         sim_e = pic.from_workload(w, precision=pic.FP32_CELLOFF, sort_interval=args.sort_interval,
                                   stream=stream.cuda_stream, load=False)
         torch.cuda.synchronize()
         t0 = time.perf_counter()
-        h2d = 0
-        for i, arrs in enumerate(pinned):
-            np_arrs = [a.numpy() for a in arrs]
-            sim_e.pic_load_particles(i, np_arrs[0], np_arrs[1] if w.dim > 1 else None,
-                                     np_arrs[2] if w.dim > 2 else None, np_arrs[3], np_arrs[4], np_arrs[5])
-            h2d += sum(a.nbytes for a in np_arrs[:w.dim]) + sum(a.nbytes for a in np_arrs[3:])
+        sim_e.pic_restore(ckpt)
         sim_e.pic_step(args.steps)
         d = sim_e.pic_diagnostics()
         el = time.perf_counter() - t0
-        d2h = 8 * (8 + 2 * len(w.species))
-        e2e = {"value": world * npart * args.steps / el, "unit": UNIT,
-               "h2d_bytes_per_step": h2d / args.steps, "d2h_bytes_per_step": d2h / args.steps,
-               "seconds": el, "note": "pic_load_particles + pic_step(K) + pic_diagnostics, host wall clock"}
+        os.unlink(ckpt)
+        d2h = 8 * (16 + 2 * len(w.species))
+        e2e = {"value": npart * args.steps / el, "unit": UNIT,
+               "h2d_bytes_per_step": size / args.steps, "d2h_bytes_per_step": d2h / args.steps,
+               "seconds": el, "note": "pic_restore of the window's state from a host file (fields, particles) + "
+                                      "pic_step(K) + pic_diagnostics, host wall clock"}
         assert math.isfinite(d["U_E"])
         sim_e.close()
     else:
@@ -565,6 +777,8 @@ def main():
                "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
                "config": {"workload": describe(w), "precision": "fp32 cell+offset (FP64 islands: diagnostics)",
                           "sort_interval": args.sort_interval,
+                          "window": f"steps {pre + args.warmup}..{pre + args.warmup + args.steps}"
+                                    + (" (the laser on the slab)" if args.workload == "laser_foil_2d" else ""),
                           "l2": l2_note(), "replicas": world, "qed": "off (no QED in this workload)"},
                "per_step_l2_flushed": flushed,
                "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches,

@@ -34,6 +34,7 @@
 #ifndef PIC_H
 #define PIC_H
 
+#include <stddef.h>
 #include <stdint.h>
 
 #ifdef __cplusplus
@@ -50,7 +51,10 @@ enum {
     PIC_ERR_CAPACITY = -4, /* species capacity exceeded */
     PIC_ERR_NONFINITE = -5,/* NaN/Inf found in a particle or a diagnostic */
     PIC_ERR_NOMEM = -6,    /* device allocation failed */
-    PIC_ERR_STATE = -7     /* call not valid in the current state */
+    PIC_ERR_STATE = -7,    /* call not valid in the current state */
+    PIC_ERR_TIMEOUT = -8   /* a bounded wait inside a kernel ran out (a bulk copy into shared memory or a
+                              tensor-core commit did not complete); the kernel stopped, the context stays
+                              usable, the step's results are not valid */
 };
 
 enum { PIC_BC_PERIODIC = 0, PIC_BC_ABSORB = 1 };
@@ -87,14 +91,31 @@ typedef struct {
 
 enum { PIC_KIND_MASSIVE = 0, PIC_KIND_PHOTON = 1 };
 
-/* Options.  precision: PIC_PREC_FP32_CELLOFF (int cell + FP32 in-cell offset,
- * FP32 fields and push) or PIC_PREC_FP64_PLAIN (absolute FP64 positions and
- * FP64 everything).  sort_interval: counting-sort particles by tile every K
+/* Device allocator a caller may hand the library (pic_options.alloc/free):
+ * alloc returns a device block of `bytes` bytes aligned to 256 bytes (NULL
+ * on failure), usable on `stream` (the simulation's cudaStream_t); free
+ * releases a block alloc returned.  ctx is passed through unchanged. */
+typedef void *(*pic_alloc_fn)(void *ctx, size_t bytes, void *stream);
+typedef void (*pic_free_fn)(void *ctx, void *ptr, void *stream);
+
+/* Options.  struct_size: sizeof(pic_options) as the caller compiled it
+ * (pic_create rejects sizes it does not know, so a caller built against
+ * another version of this header gets PIC_ERR_ARG instead of a misread
+ * struct); zero-initialise the struct and set the fields you need.
+ * precision: PIC_PREC_FP32_CELLOFF (int cell + FP32 in-cell offset, FP32
+ * fields and push) or PIC_PREC_FP64_PLAIN (absolute FP64 positions and FP64
+ * everything).  sort_interval: counting-sort particles by tile every K
  * steps (K >= 1; 0 = never after loading).  tile[d]: cells per tile along
  * active axes (powers of two, 0 = library default).  rho_bg: uniform
  * immobile background charge density used only by the Gauss diagnostic.
- * stream: a cudaStream_t (NULL = legacy default stream). */
+ * stream: a cudaStream_t (NULL = legacy default stream).  alloc/free: the
+ * caller's device allocator (both or neither; NULL = cudaMalloc/cudaFree):
+ * every device block the library uses for this simulation -- the state
+ * pic_create allocates, and the temporary blocks of calls such as
+ * pic_get_particles -- comes from it, and pic_destroy returns the state's
+ * blocks to it. */
 typedef struct {
+    int struct_size;
     int precision;
     int sort_interval;
     int tile[3];
@@ -106,6 +127,9 @@ typedef struct {
     uint64_t seed;    /* key of the Philox4x32-10 stream of the QED Monte Carlo */
     int pusher;       /* momentum update: PIC_PUSHER_BORIS (Eqs. 13-16) or PIC_PUSHER_VAY (the
                          alternative Sec. II.C names after Eq. 16 for nearly cancelling E and v x B) */
+    pic_alloc_fn alloc;
+    pic_free_fn free;
+    void *alloc_ctx;
 } pic_options;
 
 /* Push kernels: AUTO uses the tiled shared-memory kernel wherever it exists
@@ -203,7 +227,7 @@ typedef struct {
     int64_t iterations;      /* Adam steps (0: 40000) */
     int64_t batch;           /* samples per step, a multiple of 128 (0: 16384) */
     double lr, lr_final;     /* cosine schedule from lr to lr_final (0: 1e-2, 1e-4) */
-    double chi_min, chi_max; /* trained range (0: 1e-3..1e2 emission, 1e-2..1e2 pairs) */
+    double chi_min, chi_max; /* trained range (0: 1e-3..1e2 emission, 1e-1..1e2 pairs) */
     double rate_weight;      /* loss weight of the rate output (0: 4) */
     uint64_t seed;           /* Philox key of samples and initial weights */
     int keep;                /* 1: continue from the present parameters */
@@ -256,7 +280,7 @@ int pic_mlp_eval(pic_sim *sim, int process, int64_t n, const float *x, float *y)
  * MMAs (M = 128, N = 64, K = 16 slices) with FP32 accumulators in tensor
  * memory.  The input layer, SiLU, BF16 activations and head are those of
  * pic_mlp_eval: the results differ only by the order of the FP32 sums.
- * x, y as for pic_mlp_eval; PIC_ERR_CUDA if the tensor cores time out. */
+ * x, y as for pic_mlp_eval; PIC_ERR_TIMEOUT if the tensor cores time out. */
 int pic_mlp_eval_tc(pic_sim *sim, int process, int64_t n, const float *x, float *y);
 
 /* Loss L = (1/n) sum_rows sum_o (y_o - t_o)^2 and its gradient with respect
@@ -307,13 +331,50 @@ int pic_set_field(pic_sim *sim, int comp, const double *host_in);
  * particle, current fold, half B and E updates; counting sort by tile every
  * sort_interval steps.  Enqueued on the stream; returns after checking the
  * device error flags (one device->host read per call).
- * Errors: PIC_ERR_CFL (a particle crossed more than one cell), PIC_ERR_CUDA. */
+ * Errors: PIC_ERR_CFL (a particle crossed more than one cell),
+ * PIC_ERR_NONFINITE (a particle momentum became NaN or infinite),
+ * PIC_ERR_CAPACITY (QED children beyond a species' capacity; the excess is
+ * not stored), PIC_ERR_TIMEOUT, PIC_ERR_CUDA. */
 int pic_step(pic_sim *sim, int64_t nsteps);
 
 /* Copy component comp (PIC_EX..PIC_JZ, or PIC_RHO = particle charge density
  * as in pic_diag) to host_out in the exchange layout.  Synchronises the
  * stream.  Errors: PIC_ERR_ARG. */
 int pic_fields(pic_sim *sim, int comp, double *host_out);
+
+/* Borrowed device view of a resident field component (PIC_EX..PIC_JZ, the
+ * arrays of Sec. II.B's Yee grid; RHO is not resident): the value at stored
+ * index (i, j, k) -- exchange-layout index, see above; ghost layers from
+ * lo[d] to hi[d] inclusive -- is element origin + i*stride[0] + j*stride[1]
+ * + k*stride[2] of `data`, elem_bytes wide (4: FP32 form, 8: FP64 form).
+ * The library keeps ownership: the caller reads it and neither writes nor
+ * frees it.  The address stays valid until pic_destroy; the contents are
+ * those after the work enqueued on the simulation's stream, and change with
+ * the next pic_step, pic_set_field or pic_restore (synchronise with pic_sync,
+ * or order the reading stream after the simulation's).  Errors: PIC_ERR_ARG. */
+typedef struct {
+    void *data;
+    int elem_bytes;
+    int64_t origin;
+    int64_t stride[3];
+    int64_t lo[3], hi[3];
+} pic_field_view;
+int pic_field_device(pic_sim *sim, int comp, pic_field_view *view);
+
+/* Checkpoint (the paper names no format; its code writes MPI-IO output,
+ * Sec. II.F).  pic_save writes the whole simulation state to a file at path:
+ * step, fields and currents with their ghost layers, every species' live
+ * particles in array order (cell/offset or position, momentum, QED optical
+ * depth and identity), the tile index of the last sort, the absorbed and
+ * sub-threshold photon energy tallies, the laser, the QED set-up and the
+ * surrogate networks.  pic_restore reads it into a simulation created with
+ * the same grid, dt, species and options (else PIC_ERR_ARG): stepping on
+ * from there takes the same decisions as the run that wrote it (identical
+ * Philox counters and sort phase).  Both synchronise the stream.  The file
+ * is host-endian raw binary with a version tag.  Errors: PIC_ERR_ARG (bad
+ * path, unreadable or foreign file, other configuration), PIC_ERR_CUDA. */
+int pic_save(pic_sim *sim, const char *path);
+int pic_restore(pic_sim *sim, const char *path);
 
 /* Number of live particles of species sp after the last sort (dead particles
  * are dropped at sorts; between sorts they are counted as not alive). */
@@ -360,6 +421,13 @@ int pic_profile(pic_sim *sim, int enable);
  * Synchronises the stream and clears the accumulators. */
 int pic_profile_read(pic_sim *sim, double *ms, int64_t *launches, int64_t *push_launches);
 
+/* The push phase split by species: device time in milliseconds of each
+ * species' push (gather, push, deposit and its QED Monte Carlo; ms[nsp]) and
+ * the number of such pushes (pushes[nsp]) timed up to the last
+ * pic_profile_read (which gathers them); clears them.  Either pointer may be
+ * NULL. */
+int pic_profile_read_species(pic_sim *sim, double *ms, int64_t *pushes);
+
 /* Field energy without any device allocation.  The paper has no
  * counterpart: this entry point exists for callers that cannot call
  * cudaMalloc (for example a plugin inside a host application that owns all
@@ -380,7 +448,10 @@ int pic_profile_read(pic_sim *sim, double *ms, int64_t *launches, int64_t *push_
  * cudaMalloc/cudaFree and calls no allocating library routine.  Its first
  * call on a device looks up the address of that array with
  * cudaGetSymbolAddress (with the device current); make that first call
- * before any stream capture.  Every call on a device shares the one array
+ * before any stream capture.  The address is kept per device together with
+ * the identifier of the CUDA context it was taken in; a call made in another
+ * context of the device (after cudaDeviceReset, say) looks it up again, so
+ * the first call after such a reset must also come before any capture.  Every call on a device shares the one array
  * and overwrites it completely (no state carries over between calls), so
  * calls that overlap on the GPU -- on two streams, or from two host threads
  * -- race and must be serialised by the caller.

@@ -17,49 +17,14 @@
 #include <string>
 #include <vector>
 
-#include "../../include/pic.h"
 #include "diag.cuh"
 #include "fdtd.cuh"
-#include "mlp_host.cuh"
-#include "push.cuh"
-#include "push_tile.cuh"
-#include "qed_host.cuh"
+#include "sim.cuh"
 #include "sort.cuh"
 
 using namespace pic;
 
 namespace {
-
-struct SpeciesState {
-    double q = 0, m = 1, w = 0;
-    long long cap = 0;
-    long long n_hi = 0;        // host upper bound of the live count
-    long long *d_count = nullptr;
-    int cur = 0;
-    uint32_t *cell[2] = {nullptr, nullptr};
-    float *off[2][3] = {};
-    float *uf[2][3] = {};
-    double *x[2][3] = {};
-    double *ud[2][3] = {};
-    uint32_t *tile_start = nullptr;  // ntiles + 1
-    // work items of the tiled push (rebuilt after every sort)
-    TileItem *items = nullptr;
-    uint32_t *nitems = nullptr;
-    uint32_t *item_cnt = nullptr;   // ntiles + 1
-    uint32_t *item_scan = nullptr;  // scan scratch
-    uint32_t *defer = nullptr;      // 3D: particles the tiled push leaves to the global path ([0] = count)
-    long long items_cap = 0;
-    bool items_valid = false;
-    // QED: kind, optical depth and identity (double-buffered with the
-    // particle arrays), event flags and data of the current step
-    int kind = PIC_KIND_MASSIVE;
-    int qed = 0;
-    double *tau[2] = {nullptr, nullptr};
-    uint64_t *id[2] = {nullptr, nullptr};
-    uint32_t *ev = nullptr;
-    float *evk = nullptr;
-    bool has_qed_arrays() const { return tau[0] != nullptr; }
-};
 
 std::string g_create_error;
 
@@ -70,53 +35,7 @@ namespace pic {
 void set_global_error(const std::string &msg) { g_create_error = msg; }
 }  // namespace pic
 
-struct pic_sim {
-    Grid g{};
-    int precision = PIC_PREC_FP32_CELLOFF;
-    int push_variant = PIC_PUSH_AUTO;
-    int pusher = PIC_PUSHER_BORIS;
-    // QED
-    uint64_t seed = 0;
-    pic_qed qed{};
-    bool qed_on = false;
-    void *qed_tables = nullptr;
-    QedTables T{};
-    double Es = 0.0;
-    double *d_elost = nullptr;
-    MlpNet net[2];  // surrogate networks: emission, pairs
-    MlpScratch ms;  // their training scratch
-    int sort_interval = 0;
-    double rho_bg = 0.0;
-    cudaStream_t st = nullptr;
-    void *F = nullptr;       // 9 components
-    double *rho = nullptr;   // padded, for diagnostics
-    int nsp = 0;
-    SpeciesState sp[PIC_MAX_SPECIES];
-    void *sort_scratch = nullptr;
-    double *diag_scratch = nullptr;
-    double *diag_out = nullptr;  // 16 doubles
-    int *d_err = nullptr;
-    double *d_eabs = nullptr;
-    long long step = 0;
-    Laser laser{};
-    pic_laser lp{};             // laser parameters (host)
-    void *laser_prof = nullptr; // transverse profile arrays (device)
-    std::vector<void *> allocs;
-    std::string err;
-    // profiling
-    bool prof = false;
-    struct Mark {
-        int phase;
-        cudaEvent_t a, b;
-    };
-    std::vector<Mark> marks;
-    long long prof_launch[PIC_NPHASE] = {0, 0, 0, 0};
-    long long prof_push = 0;
-    cudaEvent_t cur_a = nullptr;
-    long long cur_l0 = 0;
-};
-
-namespace {
+namespace pic {
 
 int fail(pic_sim *s, int code, const char *fmt, ...)
 {
@@ -130,26 +49,49 @@ int fail(pic_sim *s, int code, const char *fmt, ...)
     return code;
 }
 
-#define CK(call)                                                                                   \
-    do {                                                                                           \
-        cudaError_t e_ = (call);                                                                   \
-        if (e_ != cudaSuccess) return fail(s, PIC_ERR_CUDA, "%s: %s", #call, cudaGetErrorString(e_)); \
-    } while (0)
-
-int dalloc(pic_sim *s, void **p, size_t bytes)
+// every device buffer starts on a 256-byte boundary (vector loads, TMA)
+static int raw_alloc(pic_sim *s, void **p, size_t bytes)
 {
     *p = nullptr;
     if (bytes == 0) bytes = 16;
+    if (s->alloc_fn) {
+        *p = s->alloc_fn(s->alloc_ctx, bytes, (void *)s->st);
+        if (!*p) return fail(s, PIC_ERR_NOMEM, "caller allocator: %zu bytes refused", bytes);
+        if (reinterpret_cast<uintptr_t>(*p) & 255) {
+            s->free_fn(s->alloc_ctx, *p, (void *)s->st);
+            *p = nullptr;
+            return fail(s, PIC_ERR_NOMEM, "caller allocator: a block not aligned to 256 bytes");
+        }
+        return PIC_OK;
+    }
     cudaError_t e = cudaMalloc(p, bytes);
     if (e != cudaSuccess) {
         *p = nullptr;
         return fail(s, PIC_ERR_NOMEM, "cudaMalloc(%zu): %s", bytes, cudaGetErrorString(e));
     }
-    s->allocs.push_back(*p);
     return PIC_OK;
 }
 
-size_t rsize(const pic_sim *s) { return s->precision == PIC_PREC_FP64_PLAIN ? 8 : 4; }
+static void raw_free(pic_sim *s, void *p)
+{
+    if (!p) return;
+    if (s->alloc_fn) s->free_fn(s->alloc_ctx, p, (void *)s->st);
+    else cudaFree(p);
+}
+
+int dalloc(pic_sim *s, void **p, size_t bytes)
+{
+    int rc = raw_alloc(s, p, bytes);
+    if (!rc) s->allocs.push_back(*p);
+    return rc;
+}
+
+int talloc(pic_sim *s, void **p, size_t bytes) { return raw_alloc(s, p, bytes); }
+void tfree(pic_sim *s, void *p) { raw_free(s, p); }
+
+}  // namespace pic
+
+namespace {
 
 PartF32 view32(pic_sim *s, int i, int buf)
 {
@@ -502,7 +444,18 @@ int step_loop(pic_sim *s, int64_t nsteps)
         ph_begin(s);
         for (int i = 0; i < s->nsp; i++) {
             if (s->sp[i].n_hi) s->prof_push++;
+            cudaEvent_t sa = nullptr;
+            if (s->prof && s->sp[i].n_hi) {
+                cudaEventCreate(&sa);
+                cudaEventRecord(sa, s->st);
+            }
             push_species(s, i, F);
+            if (sa) {
+                cudaEvent_t sb;
+                cudaEventCreate(&sb);
+                cudaEventRecord(sb, s->st);
+                s->marks.push_back({PIC_NPHASE + i, sa, sb});
+            }
         }
         qed_spawn(s);
         ph_end(s, PIC_PHASE_PUSH);
@@ -531,10 +484,11 @@ int check_flags(pic_sim *s)
     CK(cudaStreamSynchronize(s->st));
     if (h) {
         CK(cudaMemsetAsync(s->d_err, 0, sizeof(int), s->st));
-        if (h & ERR_CFL) return fail(s, PIC_ERR_CFL, "a particle moved more than one cell in a step");
         if (h & ERR_NONFINITE) return fail(s, PIC_ERR_NONFINITE, "non-finite particle momentum");
+        if (h & ERR_CFL) return fail(s, PIC_ERR_CFL, "a particle moved more than one cell in a step");
         if (h & ERR_CAPACITY) return fail(s, PIC_ERR_CAPACITY, "species capacity exceeded");
-        if (h & ERR_TIMEOUT) return fail(s, PIC_ERR_CUDA, "a bulk copy into shared memory did not complete in time");
+        if (h & ERR_TIMEOUT)
+            return fail(s, PIC_ERR_TIMEOUT, "a bounded wait in a kernel ran out (bulk copy or tensor-core commit)");
     }
     return PIC_OK;
 }
@@ -553,6 +507,17 @@ int pic_create(const pic_grid *grid, double dt, const pic_species *species, int 
     pic_sim *s = nullptr;
     if (!grid || !out || (nsp > 0 && !species) || nsp < 0 || nsp > PIC_MAX_SPECIES)
         return fail(s, PIC_ERR_ARG, "pic_create: null argument or bad species count");
+    // the caller's options, copied by the size it was compiled with
+    pic_options o{};
+    if (opt) {
+        if (opt->struct_size != (int)sizeof(pic_options))
+            return fail(s, PIC_ERR_ARG, "pic_create: pic_options.struct_size is %d, this library expects %d",
+                        opt->struct_size, (int)sizeof(pic_options));
+        std::memcpy(&o, opt, sizeof o);
+        if ((o.alloc == nullptr) != (o.free == nullptr))
+            return fail(s, PIC_ERR_ARG, "pic_create: give both alloc and free, or neither");
+        opt = &o;
+    }
     if (grid->dim < 1 || grid->dim > 3) return fail(s, PIC_ERR_ARG, "pic_create: dim must be 1, 2 or 3");
     if (grid->order != 2) return fail(s, PIC_ERR_ARG, "pic_create: only shape order 2 is implemented");
     int prec = opt ? opt->precision : PIC_PREC_FP32_CELLOFF;
@@ -614,6 +579,9 @@ int pic_create(const pic_grid *grid, double dt, const pic_species *species, int 
     s->seed = opt ? opt->seed : 0;
     s->rho_bg = opt ? opt->rho_bg : 0.0;
     s->st = opt ? (cudaStream_t)opt->stream : nullptr;
+    s->alloc_fn = opt ? opt->alloc : nullptr;
+    s->free_fn = opt ? opt->free : nullptr;
+    s->alloc_ctx = opt ? opt->alloc_ctx : nullptr;
     s->nsp = nsp;
     int dev_count = 0;
     cudaError_t e = cudaGetDeviceCount(&dev_count);
@@ -707,7 +675,7 @@ void pic_destroy(pic_sim *s)
     if (!s) return;
     if (s->st) cudaStreamSynchronize(s->st);
     else cudaDeviceSynchronize();
-    for (void *p : s->allocs) cudaFree(p);
+    for (void *p : s->allocs) raw_free(s, p);
     delete s;
 }
 
@@ -758,7 +726,7 @@ int pic_load_particles(pic_sim *s, int sp, int64_t n, const double *x, const dou
     }
     const size_t stage = direct ? 0 : (size_t)n * 6 * sizeof(double);
     double *dtmp = nullptr;
-    CK(cudaMalloc(&dtmp, stage + sizeof(unsigned long long)));
+    if (int rc_ = talloc(s, (void **)&dtmp, stage + sizeof(unsigned long long))) return rc_;
     unsigned long long *dbad = reinterpret_cast<unsigned long long *>((char *)dtmp + stage), hbad = ~0ull;
     cudaError_t e = cudaMemsetAsync(dbad, 0xFF, sizeof(unsigned long long), s->st);
     if (!direct) {
@@ -780,14 +748,14 @@ int pic_load_particles(pic_sim *s, int sp, int64_t n, const double *x, const dou
     if (e == cudaSuccess) e = cudaMemcpyAsync(&hbad, dbad, sizeof hbad, cudaMemcpyDeviceToHost, s->st);
     if (e == cudaSuccess) e = cudaStreamSynchronize(s->st);
     if (e == cudaSuccess && hbad != ~0ull) {
-        cudaFree(dtmp);
+        tfree(s, dtmp);
         return fail(s, PIC_ERR_ARG, "pic_load_particles: particle %llu outside the domain or with a non-finite u",
                     hbad);
     }
     long long newn = cnt + n;
     if (e == cudaSuccess) e = cudaMemcpyAsync(p.d_count, &newn, sizeof(long long), cudaMemcpyHostToDevice, s->st);
     if (e == cudaSuccess) e = cudaStreamSynchronize(s->st);
-    cudaFree(dtmp);
+    tfree(s, dtmp);
     if (e != cudaSuccess) return fail(s, PIC_ERR_CUDA, "pic_load_particles: %s", cudaGetErrorString(e));
     p.n_hi = newn;
     p.items_valid = false;  // appended particles are in no tile's work item until the next sort
@@ -835,7 +803,7 @@ int pic_qed_eval(pic_sim *s, int process, int64_t n, const double *chi, const do
     if (!s->qed_tables) return fail(s, PIC_ERR_STATE, "pic_qed_eval: call pic_set_qed first");
     if (n == 0) return PIC_OK;
     double *d = nullptr;
-    CK(cudaMalloc(&d, (size_t)n * 3 * sizeof(double)));
+    if (int rc_ = talloc(s, (void **)&d, (size_t)n * 3 * sizeof(double))) return rc_;
     cudaError_t e = cudaMemcpyAsync(d, chi, n * 8, cudaMemcpyHostToDevice, s->st);
     if (e == cudaSuccess && r) e = cudaMemcpyAsync(d + n, r, n * 8, cudaMemcpyHostToDevice, s->st);
     if (e == cudaSuccess) {
@@ -849,7 +817,7 @@ int pic_qed_eval(pic_sim *s, int process, int64_t n, const double *chi, const do
     }
     if (e == cudaSuccess) e = cudaMemcpyAsync(out, d + 2 * n, n * 8, cudaMemcpyDeviceToHost, s->st);
     if (e == cudaSuccess) e = cudaStreamSynchronize(s->st);
-    cudaFree(d);
+    tfree(s, d);
     if (e != cudaSuccess) return fail(s, PIC_ERR_CUDA, "pic_qed_eval: %s", cudaGetErrorString(e));
     return PIC_OK;
 }
@@ -956,6 +924,10 @@ int pic_profile(pic_sim *s, int enable)
     s->marks.clear();
     for (int p = 0; p < PIC_NPHASE; p++) s->prof_launch[p] = 0;
     s->prof_push = 0;
+    for (int i = 0; i < PIC_MAX_SPECIES; i++) {
+        s->prof_sp_ms[i] = 0.0;
+        s->prof_sp_n[i] = 0;
+    }
     s->prof = enable != 0;
     return PIC_OK;
 }
@@ -968,7 +940,12 @@ int pic_profile_read(pic_sim *s, double *ms, int64_t *launches, int64_t *push_la
     for (auto &m : s->marks) {
         float t = 0.f;
         cudaEventElapsedTime(&t, m.a, m.b);
-        acc[m.phase] += t;
+        if (m.phase >= PIC_NPHASE) {  // one species' push
+            s->prof_sp_ms[m.phase - PIC_NPHASE] += t;
+            s->prof_sp_n[m.phase - PIC_NPHASE]++;
+        } else {
+            acc[m.phase] += t;
+        }
         cudaEventDestroy(m.a);
         cudaEventDestroy(m.b);
     }
@@ -980,6 +957,18 @@ int pic_profile_read(pic_sim *s, double *ms, int64_t *launches, int64_t *push_la
     }
     if (push_launches) *push_launches = s->prof_push;
     s->prof_push = 0;
+    return PIC_OK;
+}
+
+int pic_profile_read_species(pic_sim *s, double *ms, int64_t *pushes)
+{
+    if (!s) return PIC_ERR_ARG;
+    for (int i = 0; i < s->nsp; i++) {
+        if (ms) ms[i] = s->prof_sp_ms[i];
+        if (pushes) pushes[i] = s->prof_sp_n[i];
+        s->prof_sp_ms[i] = 0.0;
+        s->prof_sp_n[i] = 0;
+    }
     return PIC_OK;
 }
 
@@ -995,6 +984,25 @@ int pic_fields(pic_sim *s, int comp, double *host_out)
     if (s->precision == PIC_PREC_FP64_PLAIN)
         return copy_comp_out<double>(s, (const double *)s->F + comp * s->g.vol, host_out);
     return copy_comp_out<float>(s, (const float *)s->F + comp * s->g.vol, host_out);
+}
+
+int pic_field_device(pic_sim *s, int comp, pic_field_view *v)
+{
+    if (!s) return PIC_ERR_ARG;
+    if (comp < PIC_EX || comp > PIC_JZ || !v) return fail(s, PIC_ERR_ARG, "pic_field_device: bad component");
+    const Grid &g = s->g;
+    const size_t R = rsize(s);
+    v->data = (char *)s->F + (size_t)comp * g.vol * R;
+    v->elem_bytes = (int)R;
+    v->origin = g.origin;
+    v->stride[0] = 1;
+    v->stride[1] = g.sy;
+    v->stride[2] = g.sz;
+    for (int d = 0; d < 3; d++) {
+        v->lo[d] = -g.G[d];
+        v->hi[d] = g.n[d] + g.G[d] - 1;
+    }
+    return PIC_OK;
 }
 
 int64_t pic_particle_count(pic_sim *s, int sp)
@@ -1019,12 +1027,12 @@ int pic_get_particles(pic_sim *s, int sp, int64_t cap, int64_t *n, double *x, do
     SpeciesState &p = s->sp[sp];
     double *dtmp = nullptr;
     uint8_t *dal = nullptr;
-    CK(cudaMalloc(&dtmp, (size_t)cnt * 6 * sizeof(double)));
-    cudaError_t e = cudaMalloc(&dal, (size_t)cnt);
-    if (e != cudaSuccess) {
-        cudaFree(dtmp);
-        return fail(s, PIC_ERR_CUDA, "pic_get_particles: %s", cudaGetErrorString(e));
+    if (int rc_ = talloc(s, (void **)&dtmp, (size_t)cnt * 6 * sizeof(double))) return rc_;
+    if (int rc_ = talloc(s, (void **)&dal, (size_t)cnt)) {
+        tfree(s, dtmp);
+        return rc_;
     }
+    cudaError_t e = cudaSuccess;
     double *dx_[3] = {dtmp, dtmp + cnt, dtmp + 2 * cnt};
     double *du_[3] = {dtmp + 3 * cnt, dtmp + 4 * cnt, dtmp + 5 * cnt};
     if (s->precision == PIC_PREC_FP64_PLAIN) launch_unload_f64(view64(s, sp, p.cur), s->g, dx_, du_, dal, s->st);
@@ -1036,8 +1044,8 @@ int pic_get_particles(pic_sim *s, int sp, int64_t cap, int64_t *n, double *x, do
         if (hs[q]) e = cudaMemcpyAsync(hs[q], ds[q], cnt * sizeof(double), cudaMemcpyDeviceToHost, s->st);
     if (e == cudaSuccess && alive) e = cudaMemcpyAsync(alive, dal, cnt, cudaMemcpyDeviceToHost, s->st);
     if (e == cudaSuccess) e = cudaStreamSynchronize(s->st);
-    cudaFree(dtmp);
-    cudaFree(dal);
+    tfree(s, dtmp);
+    tfree(s, dal);
     if (e != cudaSuccess) return fail(s, PIC_ERR_CUDA, "pic_get_particles: %s", cudaGetErrorString(e));
     return PIC_OK;
 }
@@ -1070,7 +1078,7 @@ int pic_gather(pic_sim *s, int sp, int64_t cap, double *out6)
     if (cnt == 0) return PIC_OK;
     SpeciesState &p = s->sp[sp];
     double *d = nullptr;
-    CK(cudaMalloc(&d, (size_t)cnt * 6 * sizeof(double)));
+    if (int rc_ = talloc(s, (void **)&d, (size_t)cnt * 6 * sizeof(double))) return rc_;
     if (s->precision == PIC_PREC_FP64_PLAIN)
         launch_gather_f64(view64(s, sp, p.cur), (const double *)s->F, s->g, d, s->st);
     else
@@ -1078,7 +1086,7 @@ int pic_gather(pic_sim *s, int sp, int64_t cap, double *out6)
     cudaError_t e = cudaGetLastError();
     if (e == cudaSuccess) e = cudaMemcpyAsync(out6, d, cnt * 6 * sizeof(double), cudaMemcpyDeviceToHost, s->st);
     if (e == cudaSuccess) e = cudaStreamSynchronize(s->st);
-    cudaFree(d);
+    tfree(s, d);
     if (e != cudaSuccess) return fail(s, PIC_ERR_CUDA, "pic_gather: %s", cudaGetErrorString(e));
     return PIC_OK;
 }
@@ -1198,7 +1206,7 @@ int mlp_scratch(pic_sim *s, long long B)
 int mlp_table_lnG(pic_sim *s, int p, const double chi[2], double out[2])
 {
     double *d = nullptr;
-    CK(cudaMalloc(&d, 4 * sizeof(double)));
+    if (int rc_ = talloc(s, (void **)&d, 4 * sizeof(double))) return rc_;
     cudaError_t e = cudaMemcpyAsync(d, chi, 2 * sizeof(double), cudaMemcpyHostToDevice, s->st);
     if (e == cudaSuccess) {
         launch_qed_eval(s->T, true, p, 2, d, nullptr, d + 2, s->st);
@@ -1207,7 +1215,7 @@ int mlp_table_lnG(pic_sim *s, int p, const double chi[2], double out[2])
     double G[2] = {0, 0};
     if (e == cudaSuccess) e = cudaMemcpyAsync(G, d + 2, 2 * sizeof(double), cudaMemcpyDeviceToHost, s->st);
     if (e == cudaSuccess) e = cudaStreamSynchronize(s->st);
-    cudaFree(d);
+    tfree(s, d);
     if (e != cudaSuccess) return fail(s, PIC_ERR_CUDA, "mlp: table evaluation: %s", cudaGetErrorString(e));
     for (int i = 0; i < 2; i++) out[i] = std::log(G[i]) + (p == QED_PAIR ? 8.0 / (3.0 * chi[i]) : 0.0);
     return PIC_OK;
@@ -1280,7 +1288,10 @@ int pic_mlp_train(pic_sim *s, int p, const pic_mlp_train_opts *o, pic_mlp_report
     if (rc) return rc;
     const long long iters = o->iterations > 0 ? o->iterations : 40000;
     const long long B = o->batch > 0 ? o->batch : 16384;
-    const double chi_min = o->chi_min > 0 ? o->chi_min : (p == QED_PAIR ? 1e-2 : 1e-3);
+    // default ranges: emission from chi = 1e-3 (below, the tables' classical
+    // limit); pairs from chi = 0.1, where G_pair = 3e-13 makes W dt ~ 1e-13 per
+    // step -- below it the tables give the rate and no event is expected
+    const double chi_min = o->chi_min > 0 ? o->chi_min : (p == QED_PAIR ? 1e-1 : 1e-3);
     const double chi_max = o->chi_max > 0 ? o->chi_max : 1e2;
     if (B % 128 || B > (1ll << 22) || o->iterations < 0 || !(chi_max > chi_min) || chi_min < 1e-4 || chi_max > 1e3 ||
         o->lr < 0 || o->lr_final < 0 || o->rate_weight < 0)
@@ -1400,7 +1411,7 @@ int pic_mlp_eval(pic_sim *s, int p, int64_t n, const float *x, float *y)
     if (!net.ready) return fail(s, PIC_ERR_STATE, "pic_mlp_eval: no network");
     if (n == 0) return PIC_OK;
     float *d = nullptr;
-    CK(cudaMalloc(&d, (size_t)n * 4 * sizeof(float)));
+    if (int rc_ = talloc(s, (void **)&d, (size_t)n * 4 * sizeof(float))) return rc_;
     cudaError_t e = cudaMemcpyAsync(d, x, (size_t)n * 2 * sizeof(float), cudaMemcpyHostToDevice, s->st);
     if (e == cudaSuccess) {
         launch_mlp_eval(net.img, n, d, d + 2 * n, s->st);
@@ -1408,7 +1419,7 @@ int pic_mlp_eval(pic_sim *s, int p, int64_t n, const float *x, float *y)
     }
     if (e == cudaSuccess) e = cudaMemcpyAsync(y, d + 2 * n, (size_t)n * 2 * sizeof(float), cudaMemcpyDeviceToHost, s->st);
     if (e == cudaSuccess) e = cudaStreamSynchronize(s->st);
-    cudaFree(d);
+    tfree(s, d);
     if (e != cudaSuccess) return fail(s, PIC_ERR_CUDA, "pic_mlp_eval: %s", cudaGetErrorString(e));
     return PIC_OK;
 }
@@ -1422,7 +1433,7 @@ int pic_mlp_eval_tc(pic_sim *s, int p, int64_t n, const float *x, float *y)
     if (!net.ready) return fail(s, PIC_ERR_STATE, "pic_mlp_eval_tc: no network");
     if (n == 0) return PIC_OK;
     float *d = nullptr;
-    CK(cudaMalloc(&d, (size_t)n * 4 * sizeof(float)));
+    if (int rc_ = talloc(s, (void **)&d, (size_t)n * 4 * sizeof(float))) return rc_;
     cudaError_t e = cudaMemcpyAsync(d, x, (size_t)n * 2 * sizeof(float), cudaMemcpyHostToDevice, s->st);
     if (e == cudaSuccess) {
         launch_mlp_eval_tc(net.img, n, d, d + 2 * n, s->d_err, s->st);
@@ -1430,7 +1441,7 @@ int pic_mlp_eval_tc(pic_sim *s, int p, int64_t n, const float *x, float *y)
     }
     if (e == cudaSuccess) e = cudaMemcpyAsync(y, d + 2 * n, (size_t)n * 2 * sizeof(float), cudaMemcpyDeviceToHost, s->st);
     if (e == cudaSuccess) e = cudaStreamSynchronize(s->st);
-    cudaFree(d);
+    tfree(s, d);
     if (e != cudaSuccess) return fail(s, PIC_ERR_CUDA, "pic_mlp_eval_tc: %s", cudaGetErrorString(e));
     return check_flags(s);
 }

@@ -132,6 +132,11 @@ __global__ void __launch_bounds__(kRedThreads) k_final(const double *__restrict_
 template <int DIM>
 __device__ __forceinline__ void rho_add(double *rho, const Grid &g, const double *X, double qw2)
 {
+    // a non-finite position has no node; the pushes remove particles whose
+    // momentum became non-finite, so this only guards the index arithmetic
+#pragma unroll
+    for (int d = 0; d < DIM; d++)
+        if (!isfinite(X[d])) return;
     int ic[3] = {0, 0, 0};
     double w[3][3];
 #pragma unroll

@@ -189,7 +189,7 @@ __global__ void __launch_bounds__(128) k_mlp_bwd(const MlpImage *img, long long 
     // cores, one m-tile at a time
     uint32_t A[4][4];
     float acc[8][4];
-    auto ident = [](float v) { return v; };
+    auto ident = [](float a, float b) { return pack_bf16(a, b); };
 #pragma unroll
     for (int m = 0; m < 2; m++)
 #pragma unroll
@@ -245,8 +245,8 @@ __global__ void __launch_bounds__(256) k_mlp_wgrad(long long B, const float *__r
                     if (c == 0) av = make_float4(X[2 * row], X[2 * row + 1], 0.f, 0.f);
                 } else {
                     const float4 z = *reinterpret_cast<const float4 *>(&Z.z[l - 1][row * kMlpH + c]);
-                    av = make_float4(bf16_round(silu(z.x)), bf16_round(silu(z.y)), bf16_round(silu(z.z)),
-                                     bf16_round(silu(z.w)));
+                    const uint32_t a01 = silu2_bf16(z.x, z.y), a23 = silu2_bf16(z.z, z.w);
+                    av = make_float4(bf16_lo(a01), bf16_hi(a01), bf16_lo(a23), bf16_hi(a23));
                 }
             }
             *reinterpret_cast<float4 *>(&Ds[r][c]) = dv;
@@ -362,7 +362,7 @@ __global__ void __launch_bounds__(128) k_qed_eval_surr(const MlpImage *img, MlpN
     const bool inr = ok && mlp_in_range(nrm, c, lnchi);
     float x0 = 0.f, x1 = 0.f, y0 = 0.f, y1 = 0.f;
     if (inr) mlp_inputs(nrm, p, lnchi, rv, x0, x1);
-    if (__any_sync(0xffffffffu, inr)) mlp_eval_warp(S, x0, x1, y0, y1);
+    if (__any_sync(0xffffffffu, inr)) mlp_eval_warp_sparse(S, inr, x0, x1, y0, y1);
     if (!ok) return;
     if (r) out[i] = inr ? mlp_fraction(p, y0, rv) : qed_sample<R>(T, p, c, rv);
     else out[i] = inr ? mlp_rate(nrm, p, c, y1) : qed_rate<R>(T, p, c);

@@ -89,6 +89,25 @@ __device__ __forceinline__ uint32_t pack_bf16(float lo, float hi)
     return *reinterpret_cast<uint32_t *>(&v);
 }
 
+// The hidden activations as the next layer's MMA takes them: SiLU of two
+// pre-activations, as a BF16 pair.  t = tanh(z/2) is evaluated on the BF16
+// pair of z/2 (tanh.approx.bf16x2: one special-function operation for both
+// values, half the MUFU issue of two FP32 tanh -- the unit that bounds the
+// evaluation), then silu = h + h t with h = z/2 in FP32, rounded to BF16
+// once.  The BF16 t carries a relative error of a few 2^-9, the size of the
+// BF16 rounding the activation gets anyway.
+__device__ __forceinline__ uint32_t silu2_bf16(float z0, float z1)
+{
+    const float h0 = 0.5f * z0, h1 = 0.5f * z1;
+    const uint32_t hp = pack_bf16(h0, h1);
+    uint32_t tp;
+    asm("tanh.approx.bf16x2 %0, %1;" : "=r"(tp) : "r"(hp));
+    const float t0 = __uint_as_float(tp << 16), t1 = __uint_as_float(tp & 0xffff0000u);
+    return pack_bf16(fmaf(h0, t0, h0), fmaf(h1, t1, h1));
+}
+__device__ __forceinline__ float bf16_lo(uint32_t v) { return __uint_as_float(v << 16); }
+__device__ __forceinline__ float bf16_hi(uint32_t v) { return __uint_as_float(v & 0xffff0000u); }
+
 __device__ __forceinline__ void mma_bf16(float (&d)[4], const uint32_t (&a)[4], uint32_t b0, uint32_t b1)
 {
     asm volatile(
@@ -129,17 +148,18 @@ __device__ __forceinline__ void mlp_layer(const uint32_t *W, const float *b, con
 }
 
 // accumulator fragments of n-tiles 2kt, 2kt+1 -> A fragment of k-tile kt,
-// with f applied elementwise (SiLU, or the identity for deltas)
-template <typename Fn>
-__device__ __forceinline__ void mlp_repack(const float (&acc)[8][4], uint32_t (&A)[4][4], Fn f)
+// each pair of values through f2 into a BF16 pair (silu2_bf16, or pack_bf16
+// for the deltas of the backward pass)
+template <typename Fn2>
+__device__ __forceinline__ void mlp_repack(const float (&acc)[8][4], uint32_t (&A)[4][4], Fn2 f2)
 {
 #pragma unroll
     for (int kt = 0; kt < 4; kt++) {
         const float *lo = acc[2 * kt], *hi = acc[2 * kt + 1];
-        A[kt][0] = pack_bf16(f(lo[0]), f(lo[1]));
-        A[kt][1] = pack_bf16(f(lo[2]), f(lo[3]));
-        A[kt][2] = pack_bf16(f(hi[0]), f(hi[1]));
-        A[kt][3] = pack_bf16(f(hi[2]), f(hi[3]));
+        A[kt][0] = f2(lo[0], lo[1]);
+        A[kt][1] = f2(lo[2], lo[3]);
+        A[kt][2] = f2(hi[0], hi[1]);
+        A[kt][3] = f2(hi[2], hi[3]);
     }
 }
 
@@ -150,14 +170,14 @@ __device__ __forceinline__ void mlp_repack(const float (&acc)[8][4], uint32_t (&
 // Z.z[l][(row0 + rr) * 64 + col] (training).
 template <bool STORE = false>
 __device__ __forceinline__ void mlp_forward_rows(const MlpImage &S, const float (&x)[4][2], float (&y)[4][2],
-                                                 MlpZ Z = MlpZ{}, long long row0 = 0)
+                                                 MlpZ Z = MlpZ{}, long long row0 = 0, int nm = 2)
 {
     const int lane = threadIdx.x & 31, g = lane >> 2, t = lane & 3;
     float ps[4][2];
 #pragma unroll
     for (int r = 0; r < 4; r++) ps[r][0] = ps[r][1] = 0.f;
 #pragma unroll 1
-    for (int m = 0; m < 2; m++) {
+    for (int m = 0; m < nm; m++) {  // nm: m-tiles holding rows (warp-uniform)
         uint32_t A[4][4];
         float acc[8][4];
         const float xm[2][2] = {{m ? x[2][0] : x[0][0], m ? x[2][1] : x[0][1]},
@@ -186,7 +206,7 @@ __device__ __forceinline__ void mlp_forward_rows(const MlpImage &S, const float 
                     }
             }
         };
-        auto act = [](float z) { return silu(z); };
+        auto act = [](float a, float b) { return silu2_bf16(a, b); };
         store(0);
         mlp_repack(acc, A, act);
         mlp_layer(S.W1, S.b1, A, acc);
@@ -241,6 +261,39 @@ __device__ __forceinline__ void mlp_eval_warp(const MlpImage &S, float x0, float
     }
     mlp_forward_rows(S, x, y);
     const int mine = 2 * (lane >> 4) + ((lane >> 3) & 1), src = 4 * (lane & 7);
+#pragma unroll
+    for (int r = 0; r < 4; r++) {
+        const float v0 = __shfl_sync(0xffffffffu, y[r][0], src), v1 = __shfl_sync(0xffffffffu, y[r][1], src);
+        if (r == mine) {
+            y0 = v0;
+            y1 = v1;
+        }
+    }
+}
+
+// As mlp_eval_warp, for the lanes with need set only (others get nothing):
+// the needing lanes' inputs are packed into the first rows, and when at most
+// 16 lanes need the network the second m-tile is not computed (half the
+// tensor-core and SiLU work of the warp).
+__device__ __forceinline__ void mlp_eval_warp_sparse(const MlpImage &S, bool need, float x0, float x1, float &y0,
+                                                     float &y1)
+{
+    const unsigned mask = __ballot_sync(0xffffffffu, need);
+    const int k = __popc(mask);
+    const int lane = threadIdx.x & 31, g = lane >> 2;
+    float x[4][2], y[4][2];
+#pragma unroll
+    for (int r = 0; r < 4; r++) {
+        const int row = 16 * (r >> 1) + 8 * (r & 1) + g;
+        const unsigned src = __fns(mask, 0, row + 1);  // lane of the row-th needing lane
+        const int sl = src < 32u ? (int)src : 0;
+        x[r][0] = __shfl_sync(0xffffffffu, x0, sl);
+        x[r][1] = __shfl_sync(0xffffffffu, x1, sl);
+    }
+    mlp_forward_rows(S, x, y, MlpZ{}, 0, (k + 15) >> 4);
+    // this lane's row: its rank among the needing lanes
+    const int q = __popc(mask & ((1u << lane) - 1u));
+    const int mine = 2 * (q >> 4) + ((q >> 3) & 1), src = 4 * (q & 7);
 #pragma unroll
     for (int r = 0; r < 4; r++) {
         const float v0 = __shfl_sync(0xffffffffu, y[r][0], src), v1 = __shfl_sync(0xffffffffu, y[r][1], src);

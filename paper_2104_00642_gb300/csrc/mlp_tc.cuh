@@ -62,17 +62,17 @@ __device__ __forceinline__ void mlp_tc_teardown(MlpTcSmem &S)
 
 // this thread's 64 activations f(acc + bias), rounded to BF16, into row
 // threadIdx.x of the A tile
-template <typename Fn>
-__device__ __forceinline__ void mlp_tc_put_row(MlpTcSmem &S, const float (&acc)[kMlpH], Fn f)
+template <typename Fn2>
+__device__ __forceinline__ void mlp_tc_put_row(MlpTcSmem &S, const float (&acc)[kMlpH], Fn2 f2)
 {
     uint8_t *row = S.A + umma_offset(threadIdx.x, 0);
 #pragma unroll
     for (int j = 0; j < kMlpH / 8; j++) {
         uint4 v;
-        v.x = pack_bf16(f(acc[8 * j + 0]), f(acc[8 * j + 1]));
-        v.y = pack_bf16(f(acc[8 * j + 2]), f(acc[8 * j + 3]));
-        v.z = pack_bf16(f(acc[8 * j + 4]), f(acc[8 * j + 5]));
-        v.w = pack_bf16(f(acc[8 * j + 6]), f(acc[8 * j + 7]));
+        v.x = f2(acc[8 * j + 0], acc[8 * j + 1]);
+        v.y = f2(acc[8 * j + 2], acc[8 * j + 3]);
+        v.z = f2(acc[8 * j + 4], acc[8 * j + 5]);
+        v.w = f2(acc[8 * j + 6], acc[8 * j + 7]);
         *reinterpret_cast<uint4 *>(row + j * kUmmaLbo) = v;
     }
 }
@@ -118,7 +118,7 @@ __device__ __forceinline__ bool mlp_eval_cta(MlpTcSmem &S, uint32_t &phase, floa
     float acc[kMlpH];
 #pragma unroll
     for (int c = 0; c < kMlpH; c++) acc[c] = fmaf(S.W0[2 * c + 1], x1, fmaf(S.W0[2 * c], x0, S.b0[c]));
-    auto act = [](float z) { return silu(z); };
+    auto act = [](float a, float b) { return silu2_bf16(a, b); };
     mlp_tc_put_row(S, acc, act);
     if (!mlp_tc_layer(S, S.B1, phase, acc)) return false;
 #pragma unroll

@@ -15,7 +15,12 @@
 // once on every GPU that loads the library and is held until the process
 // exits.  Host code may not use its name as a device address, so the first
 // call on a device looks its address up with cudaGetSymbolAddress (with that
-// device current) and caches it.
+// device current) and caches it.  The address belongs to the CUDA context it
+// was looked up in: after cudaDeviceReset the next context may load the
+// module elsewhere, so the cache remembers the context's unique identifier
+// and looks the address up again when the current context is another one.
+#include <cuda.h>
+
 #include <cstdio>
 #include <mutex>
 #include <string>
@@ -118,6 +123,33 @@ __global__ void __launch_bounds__(kNaThreads) k_na_final(const double *partial, 
 
 std::mutex g_na_mutex;
 void *g_na_addr[kNaMaxDevices] = {};
+unsigned long long g_na_ctx[kNaMaxDevices] = {};  // identifier of the context g_na_addr belongs to
+
+// unique identifier of the current CUDA context (driver entry points, so the
+// library needs no link to the driver library); false if there is no current
+// context or the driver does not offer the calls
+bool na_current_context(unsigned long long *id)
+{
+    using GetCurrent = CUresult (*)(CUcontext *);
+    using GetId = CUresult (*)(CUcontext, unsigned long long *);
+    static GetCurrent get_current = nullptr;
+    static GetId get_id = nullptr;
+    static std::once_flag once;
+    std::call_once(once, [] {
+        void *p = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &p, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            get_current = reinterpret_cast<GetCurrent>(p);
+        p = nullptr;
+        if (cudaGetDriverEntryPointByVersion("cuCtxGetId", &p, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            get_id = reinterpret_cast<GetId>(p);
+    });
+    CUcontext ctx = nullptr;
+    if (!get_current || !get_id || get_current(&ctx) != CUDA_SUCCESS || !ctx) return false;
+    return get_id(ctx, id) == CUDA_SUCCESS;
+}
 
 int na_fail(int code, const char *msg)
 {
@@ -145,16 +177,24 @@ extern "C" int pic_field_energy_noalloc(const double *const dev_fields[6], int64
         return na_fail(PIC_ERR_CUDA, "pic_field_energy_noalloc: no current CUDA device");
     void *scratch = nullptr;
     {
-        // set-up, once per device with that device current: the device
-        // address of the static scratch array
+        // set-up, once per device (and again in a new context of that device)
+        // with that device current: the device address of the static scratch
+        // array
         std::lock_guard<std::mutex> lk(g_na_mutex);
-        if (!g_na_addr[dev]) {
-            e = cudaGetSymbolAddress(&g_na_addr[dev], g_noalloc_partials);
+        unsigned long long ctx = 0;
+        const bool known = na_current_context(&ctx);
+        if (!g_na_addr[dev] || !known || g_na_ctx[dev] != ctx) {
+            void *addr = nullptr;
+            e = cudaGetSymbolAddress(&addr, g_noalloc_partials);
             if (e != cudaSuccess) {
                 g_na_addr[dev] = nullptr;
                 std::string m = std::string("pic_field_energy_noalloc: cudaGetSymbolAddress: ") + cudaGetErrorString(e);
                 return na_fail(PIC_ERR_CUDA, m.c_str());
             }
+            // the look-up made the device's primary context current if none was
+            unsigned long long now = 0;
+            g_na_addr[dev] = addr;
+            g_na_ctx[dev] = na_current_context(&now) ? now : 0;
         }
         scratch = g_na_addr[dev];
     }

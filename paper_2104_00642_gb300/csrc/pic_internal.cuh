@@ -148,7 +148,13 @@ __device__ __forceinline__ void vay(R &ux, R &uy, R &uz, R ex, R ey, R ez, R bx,
     const R tau2 = bx * bx + by * by + bz * bz;
     const R ust = upx * bx + upy * by + upz * bz;
     const R sigma = R(1) + upx * upx + upy * upy + upz * upz - tau2;
-    const R g1 = sqrt(R(0.5) * (sigma + sqrt(sigma * sigma + R(4) * (tau2 + ust * ust))));
+    // gamma_new^2 = (sigma + sqrt(sigma^2 + 4a)) / 2 with a = tau^2 + u*^2.
+    // For sigma < 0 (tau^2 > 1 + |u'|^2: strong B, slow particle) the sum
+    // cancels; the same value written as 2a / (sqrt(sigma^2 + 4a) - sigma)
+    // has no cancellation
+    const R a4 = R(4) * (tau2 + ust * ust);
+    const R root = sqrt(sigma * sigma + a4);
+    const R g1 = sqrt(sigma >= R(0) ? R(0.5) * (sigma + root) : R(0.5) * a4 / (root - sigma));
     const R tx = bx / g1, ty = by / g1, tz = bz / g1;
     const R sinv = R(1) / (R(1) + tx * tx + ty * ty + tz * tz);
     const R ut = upx * tx + upy * ty + upz * tz;

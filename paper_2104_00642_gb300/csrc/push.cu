@@ -100,6 +100,15 @@ __device__ __forceinline__ void push_one_f32(const PartF32 &P, long long p, floa
         ok &= window5<float>(i0, w0, i1, w1, S0[d], dS[d]);
         base[d] = i0 - 2;
     }
+    // a non-finite momentum (a NaN or infinite field) is reported and the particle
+    // removed before anything uses its position: NaN positions would give no valid
+    // cell or node index to the gather, the deposit or the diagnostics (and would
+    // otherwise be reported as a Courant violation)
+    if (!isfinite(ux + uy + uz)) {
+        atomicOr(err, ERR_NONFINITE);
+        P.cell[p] = kDead;
+        return;
+    }
     if (!ok) {
         atomicOr(err, ERR_CFL);
         return;
@@ -118,7 +127,6 @@ __device__ __forceinline__ void push_one_f32(const PartF32 &P, long long p, floa
             dead = true;
         }
     }
-    if (!isfinite(ux + uy + uz)) atomicOr(err, ERR_NONFINITE);
     if (dead) {
         P.cell[p] = kDead;
         double uu = (double)ux * ux + (double)uy * uy + (double)uz * uz;
@@ -177,6 +185,15 @@ __global__ void __launch_bounds__(256) k_push_f64(PartF64 P, double *__restrict_
         ok &= window5<double>(i0, w0, i1, w1, S0[d], dS[d]);
         base[d] = i0 - 2;
     }
+    // a non-finite momentum (a NaN or infinite field) is reported and the particle
+    // removed before anything uses its position: NaN positions would give no valid
+    // cell or node index to the gather, the deposit or the diagnostics (and would
+    // otherwise be reported as a Courant violation)
+    if (!isfinite(ux + uy + uz)) {
+        atomicOr(err, ERR_NONFINITE);
+        P.cell[p] = kDead;
+        return;
+    }
     if (!ok) {
         atomicOr(err, ERR_CFL);
         return;
@@ -196,7 +213,6 @@ __global__ void __launch_bounds__(256) k_push_f64(PartF64 P, double *__restrict_
         int ci = (int)floor(x1[d] / g.dx[d]);
         cc[d] = ci < 0 ? 0 : (ci >= g.n[d] ? g.n[d] - 1 : ci);
     }
-    if (!isfinite(ux + uy + uz)) atomicOr(err, ERR_NONFINITE);
     if (dead) {
         P.cell[p] = kDead;
         double uu = ux * ux + uy * uy + uz * uz;

@@ -91,7 +91,7 @@ __global__ void __launch_bounds__(256, SURR ? 2 : 1) k_push_qed_f32(PartF32 P, f
                     philox4x32_10((uint32_t)id, (uint32_t)(id >> 32), q.step, QP_EMIT, q.key[0], q.key[1], w);
                     mlp_inputs_f32(q.nrm, QED_RAD, lnchi, (float)uniform24(w[0]), x0, x1);
                 }
-                mlp_eval_warp(*reinterpret_cast<const MlpImage *>(smem), x0, x1, y0, y1);
+                mlp_eval_warp_sparse(*reinterpret_cast<const MlpImage *>(smem), inr, x0, x1, y0, y1);
                 use_net = inr;
             }
             if (!live) {
@@ -152,6 +152,16 @@ __global__ void __launch_bounds__(256, SURR ? 2 : 1) k_push_qed_f32(PartF32 P, f
         ok &= window5<float>(i0, w0, i1, w1, S0[d], dS[d]);
         base[d] = i0 - 2;
     }
+    // a non-finite momentum (a NaN or infinite field) is reported and the particle
+    // removed before anything uses its position: NaN positions would give no valid
+    // cell or node index to the gather, the deposit or the diagnostics (and would
+    // otherwise be reported as a Courant violation)
+    if (!isfinite(ux + uy + uz)) {
+        atomicOr(err, ERR_NONFINITE);
+        P.cell[p] = kDead;
+        q.ev[p] = 0;
+        return;
+    }
     if (!ok) {
         atomicOr(err, ERR_CFL);
         q.ev[p] = 0;
@@ -169,7 +179,6 @@ __global__ void __launch_bounds__(256, SURR ? 2 : 1) k_push_qed_f32(PartF32 P, f
             dead = true;
         }
     }
-    if (!isfinite(ux + uy + uz)) atomicOr(err, ERR_NONFINITE);
     if (dead) {
         P.cell[p] = kDead;
         const double uu = (double)ux * ux + (double)uy * uy + (double)uz * uz;
@@ -245,7 +254,7 @@ __global__ void __launch_bounds__(256, SURR ? 2 : 1) k_push_photon_f32(PartF32 P
                     philox4x32_10((uint32_t)id, (uint32_t)(id >> 32), q.step, QP_PAIR, q.key[0], q.key[1], w);
                     mlp_inputs_f32(q.nrm, QED_PAIR, lnchi, (float)uniform24(w[0]), x0, x1);
                 }
-                mlp_eval_warp(*reinterpret_cast<const MlpImage *>(smem), x0, x1, y0, y1);
+                mlp_eval_warp_sparse(*reinterpret_cast<const MlpImage *>(smem), inr, x0, x1, y0, y1);
                 use_net = inr;
             }
             if (!live) {
@@ -488,6 +497,16 @@ __global__ void __launch_bounds__(256) k_push_qed_f64(PartF64 P, double *__restr
         ok &= window5<double>(i0, w0, i1, w1, S0[d], dS[d]);
         base[d] = i0 - 2;
     }
+    // a non-finite momentum (a NaN or infinite field) is reported and the particle
+    // removed before anything uses its position: NaN positions would give no valid
+    // cell or node index to the gather, the deposit or the diagnostics (and would
+    // otherwise be reported as a Courant violation)
+    if (!isfinite(ux + uy + uz)) {
+        atomicOr(err, ERR_NONFINITE);
+        P.cell[p] = kDead;
+        q.ev[p] = 0;
+        return;
+    }
     if (!ok) {
         atomicOr(err, ERR_CFL);
         q.ev[p] = 0;
@@ -508,7 +527,6 @@ __global__ void __launch_bounds__(256) k_push_qed_f64(PartF64 P, double *__restr
         const int ci = (int)floor(x1[d] / g.dx[d]);
         cc[d] = ci < 0 ? 0 : (ci >= g.n[d] ? g.n[d] - 1 : ci);
     }
-    if (!isfinite(ux + uy + uz)) atomicOr(err, ERR_NONFINITE);
     if (dead) {
         P.cell[p] = kDead;
         const double uu = ux * ux + uy * uy + uz * uz;

@@ -246,6 +246,15 @@ __global__ void __launch_bounds__(kTileThreads, kTileMinBlocks)
                 ok &= (i1 - i0 >= -1 && i1 - i0 <= 1);
                 u0[d] = union4(i0, w0, i1, w1, S0[d], dS[d]);
             }
+            // a non-finite momentum (a NaN or infinite field) is reported and the particle
+            // removed before anything uses its position: NaN positions would give no valid
+            // cell or node index to the gather, the deposit or the diagnostics (and would
+            // otherwise be reported as a Courant violation)
+            if (!isfinite(ux + uy + uz)) {
+                atomicOr(err, ERR_NONFINITE);
+                sPc[pos] = kDead;
+                continue;
+            }
             if (!ok) {
                 atomicOr(err, ERR_CFL);
                 continue;
@@ -271,7 +280,6 @@ __global__ void __launch_bounds__(kTileThreads, kTileMinBlocks)
                     dead = true;
                 }
             }
-            if (!isfinite(ux + uy + uz)) atomicOr(err, ERR_NONFINITE);
             if (dead) {
                 sPc[pos] = kDead;
                 double uu = (double)ux * ux + (double)uy * uy + (double)uz * uz;

@@ -237,6 +237,15 @@ __global__ void __launch_bounds__(kTileThreads, 5)
                 const int W = d == 0 ? B::WX : B::WY;
                 din &= u0[d] >= o0[d] && u0[d] + 3 < o0[d] + W;
             }
+            // a non-finite momentum (a NaN or infinite field) is reported and the particle
+            // removed before anything uses its position: NaN positions would give no valid
+            // cell or node index to the gather, the deposit or the diagnostics (and would
+            // otherwise be reported as a Courant violation)
+            if (!isfinite(ux + uy + uz)) {
+                atomicOr(err, ERR_NONFINITE);
+                P.cell[p] = kDead;
+                continue;
+            }
             if (!ok) {
                 atomicOr(err, ERR_CFL);
                 continue;
@@ -259,7 +268,6 @@ __global__ void __launch_bounds__(kTileThreads, 5)
                     dead = true;
                 }
             }
-            if (!isfinite(ux + uy + uz)) atomicOr(err, ERR_NONFINITE);
             if (dead) {
                 P.cell[p] = kDead;
                 double uu = (double)ux * ux + (double)uy * uy + (double)uz * uz;

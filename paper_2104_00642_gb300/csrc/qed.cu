@@ -449,6 +449,19 @@ __global__ void k_add_count(long long *count, const uint32_t *total, long long c
     *count = c > cap ? cap : c;
 }
 
+// a pair is created only where both its electron and its positron find room
+// (the spawn kernels skip the rest), so both counts advance by the same number
+__global__ void k_add_pair_counts(long long *el_count, long long *po_count, const uint32_t *total, long long el_cap,
+                                  long long po_cap)
+{
+    long long n = *total;
+    n = min(n, el_cap - *el_count);
+    n = min(n, po_cap - *po_count);
+    if (n < 0) n = 0;
+    *el_count += n;
+    *po_count += n;
+}
+
 __global__ void k_init_qed(long long first, long long n, uint64_t id0, uint64_t *id, double *tau, uint32_t k0,
                            uint32_t k1)
 {
@@ -485,11 +498,10 @@ void launch_spawn_pairs(const PartF32 &phot, const uint32_t *off, const uint32_t
                         long long *po_count, long long po_cap, int dim, int *err, cudaStream_t st)
 {
     if (phot.n == 0) return;
-    note_launch(3);
+    note_launch(2);
     k_spawn_pairs_f32<<<spawn_blocks(phot.n), 256, 0, st>>>(phot, off, total, q, el, el_tau, el_id, el_ev, el_count,
                                                           el_cap, po, po_tau, po_id, po_ev, po_count, po_cap, dim, err);
-    k_add_count<<<1, 1, 0, st>>>(el_count, total, el_cap);
-    k_add_count<<<1, 1, 0, st>>>(po_count, total, po_cap);
+    k_add_pair_counts<<<1, 1, 0, st>>>(el_count, po_count, total, el_cap, po_cap);
 }
 
 void launch_spawn_photons(const PartF64 &parent, const uint32_t *off, const uint32_t *total, const QedParams &q,
@@ -509,11 +521,10 @@ void launch_spawn_pairs(const PartF64 &phot, const uint32_t *off, const uint32_t
                         long long *po_count, long long po_cap, int dim, int *err, cudaStream_t st)
 {
     if (phot.n == 0) return;
-    note_launch(3);
+    note_launch(2);
     k_spawn_pairs_f64<<<spawn_blocks(phot.n), 256, 0, st>>>(phot, off, total, q, el, el_tau, el_id, el_ev, el_count,
                                                           el_cap, po, po_tau, po_id, po_ev, po_count, po_cap, dim, err);
-    k_add_count<<<1, 1, 0, st>>>(el_count, total, el_cap);
-    k_add_count<<<1, 1, 0, st>>>(po_count, total, po_cap);
+    k_add_pair_counts<<<1, 1, 0, st>>>(el_count, po_count, total, el_cap, po_cap);
 }
 
 }  // namespace pic

@@ -171,7 +171,16 @@ __host__ __device__ __forceinline__ double qed_sample(const QedTables &T, int p,
     double y = tj * (T.nr - 1);
     y = fmin(fmax(y, 0.0), (double)(T.nr - 1) - 1e-9);
     const int j = (int)y;
-    const double ty = y - j;
+    double ty = y - j;
+    if (p == QED_RAD && rr < 0.5) {
+        // below the median the inverse is close to linear in r itself (the
+        // u^(-2/3) spectrum makes s = u^(1/3) proportional to r at small r),
+        // so the in-cell weight is taken in r: linear in t would be off by
+        // up to t_1/2 ~ 1e-3 in s near r = 0
+        const double t0 = (double)j / (T.nr - 1), t1 = (double)(j + 1) / (T.nr - 1);
+        const double r0 = 1.0 - (1.0 - t0) * (1.0 - t0), r1 = 1.0 - (1.0 - t1) * (1.0 - t1);
+        ty = fmin(fmax((rr - r0) / (r1 - r0), 0.0), 1.0);
+    }
     const R *a = I + (long long)i * T.nr + j, *b = a + T.nr;
     const double s0 = (1.0 - ty) * (double)a[0] + ty * (double)a[1];
     const double s1 = (1.0 - ty) * (double)b[0] + ty * (double)b[1];

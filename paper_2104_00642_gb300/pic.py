@@ -20,7 +20,7 @@ LIB_PATH = os.path.join(HERE, "libpic.so")
 
 PIC_OK = 0
 ERRORS = {-1: "PIC_ERR_ARG", -2: "PIC_ERR_CFL", -3: "PIC_ERR_CUDA", -4: "PIC_ERR_CAPACITY",
-          -5: "PIC_ERR_NONFINITE", -6: "PIC_ERR_NOMEM", -7: "PIC_ERR_STATE"}
+          -5: "PIC_ERR_NONFINITE", -6: "PIC_ERR_NOMEM", -7: "PIC_ERR_STATE", -8: "PIC_ERR_TIMEOUT"}
 PERIODIC, ABSORB = 0, 1
 FP32_CELLOFF, FP64_PLAIN = 0, 1
 PUSH_AUTO, PUSH_SIMPLE, PUSH_MLP_TC = 0, 1, 2
@@ -33,7 +33,8 @@ EXPORTS = ["pic_create", "pic_destroy", "pic_last_error", "pic_load_particles", 
            "pic_set_field", "pic_step", "pic_fields", "pic_particle_count", "pic_get_particles",
            "pic_get_cells", "pic_diagnostics", "pic_gather", "pic_sync", "pic_profile", "pic_profile_read",
            "pic_field_energy_noalloc", "pic_set_qed", "pic_qed_eval", "pic_get_qed_state", "pic_mlp_train",
-           "pic_mlp_validate", "pic_mlp_get", "pic_mlp_set", "pic_mlp_eval", "pic_mlp_eval_tc", "pic_mlp_grad"]
+           "pic_mlp_validate", "pic_mlp_get", "pic_mlp_set", "pic_mlp_eval", "pic_mlp_eval_tc", "pic_mlp_grad",
+           "pic_field_device", "pic_save", "pic_restore", "pic_profile_read_species"]
 KIND_MASSIVE, KIND_PHOTON = 0, 1
 QED_OFF, QED_TABLE, QED_SURROGATE = 0, 1, 2
 MLP_NPARAMS = 8642
@@ -57,10 +58,20 @@ class pic_species(C.Structure):
                 ("kind", C.c_int), ("qed", C.c_int)]
 
 
+ALLOC_FN = C.CFUNCTYPE(C.c_void_p, C.c_void_p, C.c_size_t, C.c_void_p)
+FREE_FN = C.CFUNCTYPE(None, C.c_void_p, C.c_void_p, C.c_void_p)
+
+
 class pic_options(C.Structure):
-    _fields_ = [("precision", C.c_int), ("sort_interval", C.c_int), ("tile", C.c_int * 3),
-                ("rho_bg", C.c_double), ("stream", C.c_void_p), ("push_variant", C.c_int), ("seed", C.c_uint64),
-                ("pusher", C.c_int)]
+    _fields_ = [("struct_size", C.c_int), ("precision", C.c_int), ("sort_interval", C.c_int),
+                ("tile", C.c_int * 3), ("rho_bg", C.c_double), ("stream", C.c_void_p), ("push_variant", C.c_int),
+                ("seed", C.c_uint64), ("pusher", C.c_int), ("alloc", ALLOC_FN), ("free", FREE_FN),
+                ("alloc_ctx", C.c_void_p)]
+
+
+class pic_field_view(C.Structure):
+    _fields_ = [("data", C.c_void_p), ("elem_bytes", C.c_int), ("origin", C.c_int64), ("stride", C.c_int64 * 3),
+                ("lo", C.c_int64 * 3), ("hi", C.c_int64 * 3)]
 
 
 class pic_qed(C.Structure):
@@ -159,8 +170,12 @@ def load_library(path: str = LIB_PATH):
     L.pic_mlp_eval.argtypes = [P, I, I64, P, P]
     L.pic_mlp_eval_tc.argtypes = [P, I, I64, P, P]
     L.pic_mlp_grad.argtypes = [P, I, I64, P, P, P, C.POINTER(D)]
+    L.pic_field_device.argtypes = [P, I, C.POINTER(pic_field_view)]
+    L.pic_profile_read_species.argtypes = [P, P, P]
+    L.pic_save.argtypes = [P, C.c_char_p]
+    L.pic_restore.argtypes = [P, C.c_char_p]
     for name in ("pic_mlp_train", "pic_mlp_validate", "pic_mlp_get", "pic_mlp_set", "pic_mlp_eval", "pic_mlp_eval_tc",
-                 "pic_mlp_grad"):
+                 "pic_mlp_grad", "pic_field_device", "pic_save", "pic_restore", "pic_profile_read_species"):
         getattr(L, name).restype = I
     _lib = L
     return L
@@ -179,6 +194,36 @@ def pic_field_energy_noalloc(dev_fields, n, dV, dev_out2, stream=None):
         raise PicError(rc, L.pic_last_error(None).decode())
 
 
+class TorchAllocator:
+    """Device memory for a simulation from PyTorch's caching allocator
+    (pic_options.alloc/free): the library's blocks then live in the same pool
+    as the caller's tensors.  Counts the blocks handed out and returned."""
+
+    def __init__(self, device=None):
+        import torch
+        self._torch = torch
+        self.device = torch.cuda.current_device() if device is None else device
+        self.allocated = 0
+        self.freed = 0
+        self.live = {}
+        self._alloc = ALLOC_FN(self._do_alloc)
+        self._free = FREE_FN(self._do_free)
+
+    def _do_alloc(self, ctx, nbytes, stream):
+        try:
+            ptr = self._torch.cuda.caching_allocator_alloc(int(nbytes), self.device, stream=int(stream or 0))
+        except Exception:  # out of memory: the library reports PIC_ERR_NOMEM
+            return None
+        self.allocated += 1
+        self.live[int(ptr)] = int(nbytes)
+        return ptr
+
+    def _do_free(self, ctx, ptr, stream):
+        self._torch.cuda.caching_allocator_delete(int(ptr))
+        self.live.pop(int(ptr), None)
+        self.freed += 1
+
+
 def _p(a):
     return None if a is None else a.ctypes.data_as(C.c_void_p)
 
@@ -191,7 +236,8 @@ class Sim:
     """One simulation (a ``pic_sim*``)."""
 
     def __init__(self, dim, n, dx, dt, species, bc=(PERIODIC, PERIODIC, PERIODIC), precision=FP32_CELLOFF,
-                 sort_interval=0, tile=(0, 0, 0), rho_bg=0.0, stream=None, push_variant=0, seed=0, pusher=0):
+                 sort_interval=0, tile=(0, 0, 0), rho_bg=0.0, stream=None, push_variant=0, seed=0, pusher=0,
+                 allocator=None):
         L = load_library()
         g = pic_grid()
         g.dim = int(dim)
@@ -206,6 +252,7 @@ class Sim:
             sp[i].kind = int(s[4]) if len(s) > 4 else KIND_MASSIVE
             sp[i].qed = int(s[5]) if len(s) > 5 else 0
         o = pic_options()
+        o.struct_size = C.sizeof(pic_options)
         o.precision = int(precision)
         o.sort_interval = int(sort_interval)
         for d in range(3):
@@ -215,6 +262,10 @@ class Sim:
         o.push_variant = int(push_variant)
         o.seed = int(seed) & 0xFFFFFFFFFFFFFFFF
         o.pusher = int(pusher)
+        self.allocator = allocator  # the callbacks must outlive the simulation
+        if allocator is not None:
+            o.alloc = allocator._alloc
+            o.free = allocator._free
         h = C.c_void_p()
         rc = L.pic_create(C.byref(g), float(dt), sp, len(species), C.byref(o), C.byref(h))
         if rc != PIC_OK:
@@ -277,6 +328,28 @@ class Sim:
         out = np.zeros(self.box())
         self._check(load_library().pic_fields(self._h, int(comp), _p(out)))
         return out
+
+    def pic_field_device(self, comp):
+        """borrowed device view of a resident component: dict with the device
+        address, element size, origin and strides (elements), index range"""
+        v = pic_field_view()
+        self._check(load_library().pic_field_device(self._h, int(comp), C.byref(v)))
+        return {"data": int(v.data or 0), "elem_bytes": v.elem_bytes, "origin": v.origin, "stride": tuple(v.stride),
+                "lo": tuple(v.lo), "hi": tuple(v.hi)}
+
+    def pic_profile_read_species(self):
+        """per-species push time (ms) and push count gathered by the last
+        pic_profile_read"""
+        ms = np.zeros(max(self.nsp, 1))
+        n = np.zeros(max(self.nsp, 1), dtype=np.int64)
+        self._check(load_library().pic_profile_read_species(self._h, _p(ms), _p(n)))
+        return ms[: self.nsp].tolist(), n[: self.nsp].tolist()
+
+    def pic_save(self, path):
+        self._check(load_library().pic_save(self._h, os.fsencode(path)))
+
+    def pic_restore(self, path):
+        self._check(load_library().pic_restore(self._h, os.fsencode(path)))
 
     def pic_particle_count(self, sp):
         n = load_library().pic_particle_count(self._h, int(sp))
@@ -403,13 +476,14 @@ def pic_create(dim, n, dx, dt, species, **kw) -> Sim:
 
 
 def from_workload(w, precision=FP32_CELLOFF, sort_interval=0, capacity_scale=1.0, load=True, stream=None,
-                  tile=None, push_variant=0, seed=0, pusher=0) -> Sim:
+                  tile=None, push_variant=0, seed=0, pusher=0, allocator=None) -> Sim:
     """Create a simulation for a :class:`workloads.Workload` and load its particles
     (QED workloads: the Monte Carlo is configured in table mode first)."""
     sp = [(s.q, s.m, s.w, max(1, int(s.capacity * capacity_scale)), s.kind, s.qed) for s in w.species]
     t = tile if tile is not None else tuple(w.tile)
     sim = Sim(w.dim, w.n, w.dx, w.dt, sp, bc=w.bc, precision=precision, sort_interval=sort_interval, tile=t,
-              rho_bg=w.rho_bg, stream=stream, push_variant=push_variant, seed=seed, pusher=pusher)
+              rho_bg=w.rho_bg, stream=stream, push_variant=push_variant, seed=seed, pusher=pusher,
+              allocator=allocator)
     if w.laser is not None:
         L = w.laser
         sim.pic_set_laser(L.a0, L.waist, L.fwhm, L.t_peak, L.x_focus, L.yc, L.zc, L.pol)

@@ -20,6 +20,8 @@ c/omega_r, density in n_r.  Workloads:
 * ``qed_foil_3d``: a circularly polarised a0 = 300 laser on a 100 n_c
   electron-proton foil in 3D, photon emission and pair creation on
   (Sec. III-IV; omega_r = omega_L).
+* ``qed_field_sample``: the collision's QED regime (beam energies, peak chi)
+  in a uniform field, small enough for the FP64 oracle.
 """
 from __future__ import annotations
 
@@ -297,6 +299,33 @@ def qed_foil_3d(n=(1024, 512, 512), cells_per_lambda=32, foil=(512, 576), n0=100
                            "steps_to_peak_at_foil": int(t_arrive / dt)},
                     qed={"photon_sp": 3, "electron_sp": 0, "positron_sp": 2, "lambda_r_m": 1e-6,
                          "photon_emin": photon_emin})
+
+
+def qed_field_sample(n_e=2048, gamma0=1957.0, spread=0.01, B0=400.0, dt=0.1319, steps=48, seed=SEED0 + 9):
+    """The QED regime of ``qed_collision_2d`` in a uniform field, small enough
+    for the FP64 oracle: n_e electrons with the beam's energy distribution
+    (gamma0 with a relative rms spread) moving in random directions of the
+    x-y plane through a uniform B_z = B0 (the caller sets it), which gives
+    chi = |u| B0 / E_s ~ 1.9 at gamma0 for lambda_r = 1 um -- the collision's
+    peak chi (2 gamma0 a0 hbar omega / m c^2 for a0 = 200); 1D periodic grid
+    of 16 cells, the collision's dt, tiny weight (no self-fields).  Species:
+    electrons (QED), positrons (QED), photons; photons below 2 m c^2 are
+    tallied, as in the collision."""
+    rng = _rng(seed)
+    g = gamma0 * (1.0 + spread * rng.standard_normal(n_e))
+    u = np.sqrt(g * g - 1.0)
+    ang = rng.uniform(0.0, 2.0 * math.pi, n_e)
+    x = (np.arange(n_e) + rng.random(n_e)) * (16.0 / n_e)
+    zero = np.zeros(n_e)
+    w = 1e-12
+    e = Species("electron", -1.0, 1.0, w, x, zero, zero.copy(), u * np.cos(ang), u * np.sin(ang), zero.copy(),
+                capacity=4 * n_e, qed=1)
+    emp = np.zeros(0)
+    po = Species("positron", 1.0, 1.0, w, emp, emp, emp, emp, emp, emp, capacity=4 * n_e, qed=1)
+    ph = Species("photon", 0.0, 0.0, w, emp, emp, emp, emp, emp, emp, capacity=64 * n_e, kind=1)
+    return Workload("qed_field_sample", 1, (16, 1, 1), (1.0, 1.0, 1.0), dt, (PERIODIC,) * 3, [e, po, ph], steps,
+                    tile=(16, 1, 1), notes={"B0": B0, "gamma0": gamma0},
+                    qed={"photon_sp": 2, "electron_sp": 0, "positron_sp": 1, "lambda_r_m": 1e-6, "photon_emin": 2.0})
 
 
 def vacuum_pulse_1d(n_cells=1024, cells_per_lambda=32, a0=1.0, fwhm=4.0 * 2.0 * math.pi, steps=1500,

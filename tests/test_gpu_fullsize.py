@@ -204,10 +204,10 @@ def test_qed_collision_2d_full_size_events(prec, qed_collision_sample):
     """The whole beam steps once on the GPU (tables, the bench's sort
     interval, so the first step sorts): for the 300 sampled electrons the
     emission events are the oracle's (photon identities derived from the
-    parent's Philox stream, at most two flips where the optical depth ends
-    within the table-vs-quadrature rate difference of zero), with the
-    oracle's photon energies, and the non-emitters' optical depths and
-    momenta agree."""
+    parent's Philox stream; a decision may differ only where the optical
+    depth ended the step within the table-vs-quadrature rate difference of
+    zero), with the oracle's photon energies (1e-3), and the non-emitters'
+    optical depths (the rate difference) and momenta agree."""
     w, idx, bz, o, tau0 = qed_collision_sample
     sim = pic.from_workload(w, precision=prec, sort_interval=8, seed=SEED_QED)
     sim.pic_set_field(pic.BZ, bz)
@@ -234,18 +234,24 @@ def test_qed_collision_2d_full_size_events(prec, qed_collision_sample):
     # an event (kept photon or one below photon_emin) restarts the optical depth
     g_ev = np.abs(gtau[gpos] - restart) <= 1e-12 * restart
     o_ev = np.abs(otau - restart) <= 1e-12 * restart
-    assert o_ev.sum() >= 60 and np.sum(g_ev != o_ev) <= 2, (g_ev.sum(), o_ev.sum())
+    assert o_ev.sum() >= 60, (g_ev.sum(), o_ev.sum())
+    # decisions differ only where the depth ended the step within the band the
+    # rate difference explains (tables vs quadrature, FP32 chi and rate)
+    delta = 3e-5 if prec == pic.FP64_PLAIN else 5e-5
+    for k in np.nonzero(g_ev != o_ev)[0]:
+        left, dec = (otau[k], tau0[k] - otau[k]) if g_ev[k] else (gtau[gpos][k], tau0[k] - gtau[gpos][k])
+        assert 0.0 < left <= 2.0 * delta * dec + 1e-12, (k, g_ev[k], left, dec)
     g_em = np.array([c in gph for c in cand])
     o_em = np.array([c in oph for c in cand])
     assert np.all(o_em <= o_ev) and np.all(g_em <= g_ev)
-    assert o_em.sum() >= 30 and np.sum(g_em != o_em) <= 2, (g_em.sum(), o_em.sum())
+    assert o_em.sum() >= 30 and np.all((g_em != o_em) <= (g_ev != o_ev)), (g_em.sum(), o_em.sum())
     # photon energies of the common events
     gk, ok = sim.pic_get_particles(iph), o.particles(iph)
     gmap = dict(zip(gph_id.tolist(), np.sqrt(gk["ux"] ** 2 + gk["uy"] ** 2 + gk["uz"] ** 2).tolist()))
     omap = dict(zip(oph_id.tolist(), np.sqrt(ok["ux"] ** 2 + ok["uy"] ** 2 + ok["uz"] ** 2).tolist()))
     both = [c for c, a, b in zip(cand, g_em, o_em) if a and b]
     rel = np.array([abs(gmap[c] / omap[c] - 1.0) for c in both])
-    assert np.median(rel) < (1e-4 if prec == pic.FP64_PLAIN else 1e-3) and np.max(rel) < 5e-2
+    assert np.max(rel) <= 1e-3, np.max(rel)
     # electrons without an event on either side: momenta and depth decrements
     quiet = (~g_ev) & (~o_ev)
     assert quiet.sum() >= 10
@@ -255,5 +261,5 @@ def test_qed_collision_2d_full_size_events(prec, qed_collision_sample):
     for k in ("ux", "uy", "uz"):
         assert np.all(np.abs(ge[k][gpos][q] - oe[k][q]) <= tol * umag[q] + 1e-7), k
     dg, do = tau0[q] - gtau[gpos][q], tau0[q] - otau[q]
-    assert np.all(np.abs(dg - do) <= 1e-3 * do), np.max(np.abs(dg - do) / do)
+    assert np.all(np.abs(dg - do) <= delta * do), np.max(np.abs(dg - do) / do)
     sim.close()
