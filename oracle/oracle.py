@@ -64,6 +64,9 @@ def lib():
         L.or_boris.argtypes = [D, D, P, P, P]
         L.or_vay.argtypes = [D, D, P, P, P]
         L.or_set_pusher.argtypes = [P, I]
+        L.or_set_order.argtypes = [P, I]
+        L.or_set_order.restype = I
+        L.or_weights4.argtypes = [D, P]
         L.or_deposit_one.argtypes = [P, P, P, P, D]
         L.or_sort_species.argtypes = [P, I, P]
         L.or_sort_species.restype = LG
@@ -132,6 +135,12 @@ def _f64(a):
 def weights2(delta: float) -> np.ndarray:
     w = np.zeros(3)
     lib().or_weights2(float(delta), _ptr(w))
+    return w
+
+
+def weights4(delta: float) -> np.ndarray:
+    w = np.zeros(5)
+    lib().or_weights4(float(delta), _ptr(w))
     return w
 
 
@@ -241,6 +250,11 @@ class OracleSim:
         rc = lib().or_set_ids(self._h, int(isp), int(first), len(a), _ptr(a))
         if rc:
             raise ValueError(f"or_set_ids failed ({rc})")
+
+    def set_order(self, order):
+        """shape order of gather, deposit and charge density: 2 or 4"""
+        if lib().or_set_order(self._h, int(order)):
+            raise ValueError("oracle: order must be 2 or 4")
 
     def set_pusher(self, pusher):
         """0: Boris, 1: Vay"""

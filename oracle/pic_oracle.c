@@ -98,6 +98,7 @@ struct osim {
     int sort_interval;
     int tile[3];
     int pusher; /* 0: Boris, 1: Vay */
+    int order;  /* shape order of Sec. II.D: 2 (W_2, three nodes) or 4 (W_4, five nodes) */
     olaser L;
     double e_absorbed;
     /* QED */
@@ -170,6 +171,7 @@ osim *or_create(int dim, const long *n, const double *dx, const int *bc, double 
     s->dt = dt;
     s->rho_bg = rho_bg;
     s->sort_interval = sort_interval;
+    s->order = 2;
     for (int d = 0; d < 3; d++) {
         int active = d < dim;
         s->n[d] = active ? n[d] : 1;
@@ -494,15 +496,48 @@ void or_weights2(double delta, double *w)
     w[2] = 0.5 * (0.5 + delta) * (0.5 + delta);
 }
 
+/* Antiderivative of the order-4 shape S_4 of Eq. (18) (the cubic B-spline:
+ * 2/3 - xi^2 + |xi|^3/2 for |xi| <= 1, (4/3)(1 - |xi|/2)^3 for 1 < |xi| <= 2),
+ * P(x) = Int_{-2}^{x} S_4: piecewise quartic, 0 below -2, 1 above 2, and
+ * P(x) = 1 - P(-x). */
+static double prim_s4(double x)
+{
+    if (x <= -2.0) return 0.0;
+    if (x >= 2.0) return 1.0;
+    if (x > 0.0) return 1.0 - prim_s4(-x);
+    if (x <= -1.0) {
+        double t = 2.0 + x;
+        return t * t * t * t / 24.0;
+    }
+    /* Int_{-2}^{-1} = 1/24, then Int_{-1}^{x} (2/3 - xi^2 - xi^3/2) */
+    return 1.0 / 24.0 + (2.0 / 3.0) * (x + 1.0) - (x * x * x + 1.0) / 3.0 - (x * x * x * x - 1.0) / 8.0;
+}
+
+/* W_4 for the five nodes i_c-2 .. i_c+2 of a particle at delta = X - i_c in
+ * [-1/2, 1/2): the integral of S_4(xi - delta) over each node's cell
+ * [m - 1/2, m + 1/2] (Sec. II.D, the weight definition after Eq. (18)). */
+void or_weights4(double delta, double *w)
+{
+    for (int m = -2; m <= 2; m++) w[m + 2] = prim_s4(m + 0.5 - delta) - prim_s4(m - 0.5 - delta);
+}
+
+/* the weights of the simulation's order: 3 (order 2) or 5 (order 4) values
+ * for the nodes i_c - order/2 .. i_c + order/2 */
+static void weights(const osim *s, double delta, double *w)
+{
+    if (s->order == 4) or_weights4(delta, w);
+    else or_weights2(delta, w);
+}
+
 /* nearest (half-)node and weights of a coordinate X = x/dx for a component
  * that is node-centred (half = 0) or half-node-centred (half = 1) */
-static long nearest(double X, int half, double *w)
+static long nearest(const osim *s, double X, int half, double *w)
 {
     long ic;
     double delta;
     if (half) { ic = (long)floor(X); delta = X - ((double)ic + 0.5); }
     else { ic = (long)floor(X + 0.5); delta = X - (double)ic; }
-    or_weights2(delta, w);
+    weights(s, delta, w);
     return ic;
 }
 
@@ -510,20 +545,21 @@ static long nearest(double X, int half, double *w)
  * component with its own staggered nearest node */
 static double gather1(const osim *s, int c, const double *x)
 {
-    double w[3][3];
+    const int P = s->order + 1, h = s->order / 2;
+    double w[3][5];
     long ic[3];
     for (int d = 0; d < 3; d++) {
-        if (d < s->dim) ic[d] = nearest(x[d] / s->dx[d], stag(c, d), w[d]);
-        else { ic[d] = 0; w[d][0] = 0.0; w[d][1] = 1.0; w[d][2] = 0.0; }
+        if (d < s->dim) ic[d] = nearest(s, x[d] / s->dx[d], stag(c, d), w[d]);
+        else { ic[d] = 0; for (int a = 0; a < P; a++) w[d][a] = a == h ? 1.0 : 0.0; }
     }
     double acc = 0.0;
-    for (int c3 = 0; c3 < 3; c3++) {
-        if (2 >= s->dim && c3 != 1) continue;
-        for (int b = 0; b < 3; b++) {
-            if (1 >= s->dim && b != 1) continue;
-            for (int a = 0; a < 3; a++)
+    for (int c3 = 0; c3 < P; c3++) {
+        if (2 >= s->dim && c3 != h) continue;
+        for (int b = 0; b < P; b++) {
+            if (1 >= s->dim && b != h) continue;
+            for (int a = 0; a < P; a++)
                 acc += w[0][a] * w[1][b] * w[2][c3] *
-                       getF(s, c, ic[0] + a - 1, ic[1] + b - 1, ic[2] + c3 - 1);
+                       getF(s, c, ic[0] + a - h, ic[1] + b - h, ic[2] + c3 - h);
         }
     }
     return acc;
@@ -589,25 +625,35 @@ void or_vay(double qm, double dt, const double *E, const double *B, double *u)
 
 void or_set_pusher(osim *s, int pusher) { s->pusher = pusher; }
 
+/* shape order of gather, deposit and charge density: 2 or 4 (Sec. II.D) */
+int or_set_order(osim *s, int order)
+{
+    if (order != 2 && order != 4) return -1;
+    s->order = order;
+    return 0;
+}
+
 /* ------------------------------------------------------------------ */
 /* Esirkepov charge-conserving current, Eqs. (20)-(22)                 */
 /* ------------------------------------------------------------------ */
 
-/* node-centred W_2 of a particle at X0 and at X1 on the 5-node window that
- * starts at node ic0-2 (ic0 the node nearest X0). Returns the window base. */
-static long window5(double X0, double X1, double *S0, double *S1)
+/* node-centred shapes (W_2 or W_4) of a particle at X0 and at X1 on the
+ * window of order + 3 nodes that starts at node ic0 - order/2 - 1 (ic0 the
+ * node nearest X0).  Returns the window base. */
+static long window(const osim *s, double X0, double X1, double *S0, double *S1)
 {
-    double w0[3], w1[3];
-    long ic0 = nearest(X0, 0, w0);
-    long ic1 = nearest(X1, 0, w1);
+    const int P = s->order + 1, h = s->order / 2, Wn = P + 2;
+    double w0[5], w1[5];
+    long ic0 = nearest(s, X0, 0, w0);
+    long ic1 = nearest(s, X1, 0, w1);
     long sh = ic1 - ic0; /* |sh| <= 1 under the Courant condition */
-    for (int a = 0; a < 5; a++) { S0[a] = 0.0; S1[a] = 0.0; }
-    for (int a = 0; a < 3; a++) {
+    for (int a = 0; a < Wn; a++) { S0[a] = 0.0; S1[a] = 0.0; }
+    for (int a = 0; a < P; a++) {
         S0[a + 1] = w0[a];
         long b = a + 1 + sh;
-        if (b >= 0 && b < 5) S1[b] = w1[a];
+        if (b >= 0 && b < Wn) S1[b] = w1[a];
     }
-    return ic0 - 2;
+    return ic0 - h - 1;
 }
 
 /* deposit of one particle moving on a straight line from x0 to x1 with
@@ -616,24 +662,26 @@ static long window5(double X0, double X1, double *S0, double *S1)
  * J_d(i+1/2) - J_d(i-1/2) = -q w (dx_d/dt) W_d(i) is summed from zero left of
  * the window; W_d is Esirkepov's decomposition (his Eq. 31) of the change of
  * the density shape. Along an inactive axis the current is q w v_d times the
- * shape product averaged along the path. */
+ * shape product averaged along the path.  The same shape as the gather
+ * (Sec. II.E after Eq. (22)): W_2 on a 5-node window, W_4 on 7 nodes. */
 static void deposit(osim *s, const double *x0, const double *x1, const double *v, double qw)
 {
-    double S0[3][5], S1[3][5], dS[3][5];
+    const int Wn = s->order + 3;
+    double S0[3][7], S1[3][7], dS[3][7];
     long base[3] = {0, 0, 0};
     for (int d = 0; d < s->dim; d++) {
-        base[d] = window5(x0[d] / s->dx[d], x1[d] / s->dx[d], S0[d], S1[d]);
-        for (int a = 0; a < 5; a++) dS[d][a] = S1[d][a] - S0[d][a];
+        base[d] = window(s, x0[d] / s->dx[d], x1[d] / s->dx[d], S0[d], S1[d]);
+        for (int a = 0; a < Wn; a++) dS[d][a] = S1[d][a] - S0[d][a];
     }
     double dt = s->dt;
     if (s->dim == 1) {
         double cx = -qw * s->dx[0] / dt, acc = 0.0;
-        /* the fifth partial sum is sum(dS) = 0 exactly: both shapes sum to one */
-        for (int a = 0; a < 4; a++) {
+        /* the last partial sum is sum(dS) = 0 exactly: both shapes sum to one */
+        for (int a = 0; a < Wn - 1; a++) {
             acc += cx * dS[0][a];
             addF(s, JX, base[0] + a, 0, 0, acc);
         }
-        for (int a = 0; a < 5; a++) {
+        for (int a = 0; a < Wn; a++) {
             double f = 0.5 * (S0[0][a] + S1[0][a]);
             addF(s, JY, base[0] + a, 0, 0, qw * v[1] * f);
             addF(s, JZ, base[0] + a, 0, 0, qw * v[2] * f);
@@ -642,24 +690,24 @@ static void deposit(osim *s, const double *x0, const double *x1, const double *v
     }
     if (s->dim == 2) {
         double cx = -qw * s->dx[0] / dt, cy = -qw * s->dx[1] / dt;
-        for (int b = 0; b < 5; b++) {
+        for (int b = 0; b < Wn; b++) {
             double acc = 0.0;
-            for (int a = 0; a < 4; a++) {
+            for (int a = 0; a < Wn - 1; a++) {
                 double Wx = dS[0][a] * (S0[1][b] + 0.5 * dS[1][b]);
                 acc += cx * Wx;
                 addF(s, JX, base[0] + a, base[1] + b, 0, acc);
             }
         }
-        for (int a = 0; a < 5; a++) {
+        for (int a = 0; a < Wn; a++) {
             double acc = 0.0;
-            for (int b = 0; b < 4; b++) {
+            for (int b = 0; b < Wn - 1; b++) {
                 double Wy = dS[1][b] * (S0[0][a] + 0.5 * dS[0][a]);
                 acc += cy * Wy;
                 addF(s, JY, base[0] + a, base[1] + b, 0, acc);
             }
         }
-        for (int b = 0; b < 5; b++)
-            for (int a = 0; a < 5; a++) {
+        for (int b = 0; b < Wn; b++)
+            for (int a = 0; a < Wn; a++) {
                 double Wz = S0[0][a] * S0[1][b] + 0.5 * dS[0][a] * S0[1][b] +
                             0.5 * S0[0][a] * dS[1][b] + (1.0 / 3.0) * dS[0][a] * dS[1][b];
                 addF(s, JZ, base[0] + a, base[1] + b, 0, qw * v[2] * Wz);
@@ -667,30 +715,30 @@ static void deposit(osim *s, const double *x0, const double *x1, const double *v
         return;
     }
     double cx = -qw * s->dx[0] / dt, cy = -qw * s->dx[1] / dt, cz = -qw * s->dx[2] / dt;
-    for (int c = 0; c < 5; c++)
-        for (int b = 0; b < 5; b++) {
+    for (int c = 0; c < Wn; c++)
+        for (int b = 0; b < Wn; b++) {
             double acc = 0.0;
-            for (int a = 0; a < 4; a++) {
+            for (int a = 0; a < Wn - 1; a++) {
                 double Wx = dS[0][a] * (S0[1][b] * S0[2][c] + 0.5 * dS[1][b] * S0[2][c] +
                                         0.5 * S0[1][b] * dS[2][c] + (1.0 / 3.0) * dS[1][b] * dS[2][c]);
                 acc += cx * Wx;
                 addF(s, JX, base[0] + a, base[1] + b, base[2] + c, acc);
             }
         }
-    for (int c = 0; c < 5; c++)
-        for (int a = 0; a < 5; a++) {
+    for (int c = 0; c < Wn; c++)
+        for (int a = 0; a < Wn; a++) {
             double acc = 0.0;
-            for (int b = 0; b < 4; b++) {
+            for (int b = 0; b < Wn - 1; b++) {
                 double Wy = dS[1][b] * (S0[0][a] * S0[2][c] + 0.5 * dS[0][a] * S0[2][c] +
                                         0.5 * S0[0][a] * dS[2][c] + (1.0 / 3.0) * dS[0][a] * dS[2][c]);
                 acc += cy * Wy;
                 addF(s, JY, base[0] + a, base[1] + b, base[2] + c, acc);
             }
         }
-    for (int b = 0; b < 5; b++)
-        for (int a = 0; a < 5; a++) {
+    for (int b = 0; b < Wn; b++)
+        for (int a = 0; a < Wn; a++) {
             double acc = 0.0;
-            for (int c = 0; c < 4; c++) {
+            for (int c = 0; c < Wn - 1; c++) {
                 double Wz = dS[2][c] * (S0[0][a] * S0[1][b] + 0.5 * dS[0][a] * S0[1][b] +
                                         0.5 * S0[0][a] * dS[1][b] + (1.0 / 3.0) * dS[0][a] * dS[1][b]);
                 acc += cz * Wz;
@@ -1044,18 +1092,19 @@ static void deposit_rho(const osim *s, double *rho)
             for (int side = 0; side < 2; side++) {
                 double xs[3] = {p->x[3 * a], p->x[3 * a + 1], p->x[3 * a + 2]};
                 half_drift(s, xs, &p->u[3 * a], side == 0 ? -1.0 : 1.0);
-                double w[3][3];
+                const int P = s->order + 1, h = s->order / 2;
+                double w[3][5];
                 long ic[3];
                 for (int d = 0; d < 3; d++) {
-                    if (d < s->dim) ic[d] = nearest(xs[d] / s->dx[d], 0, w[d]);
-                    else { ic[d] = 0; w[d][0] = 0; w[d][1] = 1; w[d][2] = 0; }
+                    if (d < s->dim) ic[d] = nearest(s, xs[d] / s->dx[d], 0, w[d]);
+                    else { ic[d] = 0; for (int a = 0; a < P; a++) w[d][a] = a == h ? 1.0 : 0.0; }
                 }
-                for (int c = 0; c < 3; c++)
-                    for (int b = 0; b < 3; b++)
-                        for (int aa = 0; aa < 3; aa++) {
+                for (int c = 0; c < P; c++)
+                    for (int b = 0; b < P; b++)
+                        for (int aa = 0; aa < P; aa++) {
                             double wt = w[0][aa] * w[1][b] * w[2][c];
                             if (wt == 0.0) continue;
-                            long idx[3] = {ic[0] + aa - 1, ic[1] + b - 1, ic[2] + c - 1};
+                            long idx[3] = {ic[0] + aa - h, ic[1] + b - h, ic[2] + c - h};
                             int ok = 1;
                             for (int d = 0; d < 3; d++) {
                                 if (d >= s->dim) { idx[d] = 0; continue; }

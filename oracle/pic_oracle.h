@@ -38,6 +38,9 @@ void or_boris(double qm, double dt, const double *E, const double *B, double *u)
 void or_vay(double qm, double dt, const double *E, const double *B, double *u);
 /* 0: Boris (default), 1: Vay, for every massive species of the step */
 void or_set_pusher(osim *s, int pusher);
+/* shape order 2 (default) or 4; returns -1 for others */
+int or_set_order(osim *s, int order);
+void or_weights4(double delta, double *w);
 void or_deposit_one(osim *s, const double *x0, const double *x1, const double *v, double qw);
 long or_sort_species(osim *s, int isp, long *perm_out);
 int or_step(osim *s, long nsteps);
