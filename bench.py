@@ -132,53 +132,117 @@ def occupied_cells(w):
 
 
 class Clocks:
-    """nvidia-smi sampling of SM clock and throttle reasons during the timed region"""
+    """SM clock and throttle reasons sampled DURING the timed region: a
+    thread polls NVML (read-only queries through ctypes) every ~2 ms, so a
+    window of a few milliseconds still has samples; without NVML it falls
+    back to nvidia-smi at 100 ms."""
 
-    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
-         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
-         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+    # clocks-event reason bits of NVML
+    REASONS = {0x4: "sw_power_cap", 0x8: "hw_slowdown", 0x20: "sw_thermal_slowdown", 0x40: "hw_thermal_slowdown",
+               0x80: "hw_power_brake_slowdown"}
 
     def __init__(self, dev):
         self.dev = dev
-        self.p = None
-        fd, self.path = tempfile.mkstemp(prefix="clocks_", suffix=".csv")
-        os.close(fd)
+        self.rows = []
+        self.nvml = None
+        self.thread = None
+        self.stop = False
+        self.smi = None
+
+    def _nvml_open(self):
+        import ctypes as C
+        for name in ("libnvidia-ml.so.1", "libnvidia-ml.so"):
+            try:
+                L = C.CDLL(name)
+                break
+            except OSError:
+                L = None
+        if L is None or L.nvmlInit_v2() != 0:
+            return None
+        h = C.c_void_p()
+        n = C.c_uint()
+        L.nvmlDeviceGetCount_v2(C.byref(n))
+        idx = self.dev if n.value > self.dev else 0
+        if n.value > 1:
+            try:  # the CUDA device's own NVML handle, by PCI bus id
+                import torch
+                pr = torch.cuda.get_device_properties(self.dev)
+                bus = f"{pr.pci_domain_id:08x}:{pr.pci_bus_id:02x}:{pr.pci_device_id:02x}.0".encode()
+                if L.nvmlDeviceGetHandleByPciBusId_v2(bus, C.byref(h)) == 0:
+                    return L, h
+            except Exception:
+                pass
+        if L.nvmlDeviceGetHandleByIndex_v2(idx, C.byref(h)) != 0:
+            return None
+        return L, h
+
+    def _poll(self):
+        import ctypes as C
+        L, h = self.nvml
+        sm, mx, rs = C.c_uint(), C.c_uint(), C.c_ulonglong()
+        L.nvmlDeviceGetMaxClockInfo(h, 1, C.byref(mx))
+        get_reasons = getattr(L, "nvmlDeviceGetCurrentClocksEventReasons", None) or \
+            L.nvmlDeviceGetCurrentClocksThrottleReasons
+        while not self.stop:
+            if L.nvmlDeviceGetClockInfo(h, 1, C.byref(sm)) == 0 and get_reasons(h, C.byref(rs)) == 0:
+                self.rows.append((sm.value, mx.value, rs.value))
+            time.sleep(0.002)
 
     def __enter__(self):
         try:
-            self.f = open(self.path, "w")
-            self.p = subprocess.Popen(["nvidia-smi", f"--id={self.dev}", f"--query-gpu={self.Q}",
-                                       "--format=csv,noheader,nounits", "-lms", "100"], stdout=self.f,
-                                      stderr=subprocess.DEVNULL)
+            self.nvml = self._nvml_open()
         except Exception:
-            self.p = None
+            self.nvml = None
+        if self.nvml is not None:
+            import threading
+            self.thread = threading.Thread(target=self._poll, daemon=True)
+            self.thread.start()
+            return self
+        try:
+            fd, self.path = tempfile.mkstemp(prefix="clocks_", suffix=".csv")
+            os.close(fd)
+            self.f = open(self.path, "w")
+            q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+                 "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+                 "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+            self.smi = subprocess.Popen(["nvidia-smi", f"--id={self.dev}", f"--query-gpu={q}",
+                                         "--format=csv,noheader,nounits", "-lms", "100"], stdout=self.f,
+                                        stderr=subprocess.DEVNULL)
+        except Exception:
+            self.smi = None
         return self
 
     def __exit__(self, *a):
-        if self.p is not None:
-            self.p.terminate()
+        if self.thread is not None:
+            self.stop = True
+            self.thread.join(timeout=5)
+        if self.smi is not None:
+            self.smi.terminate()
             try:
-                self.p.wait(timeout=5)
+                self.smi.wait(timeout=5)
             except Exception:
-                self.p.kill()
+                self.smi.kill()
             self.f.close()
+            names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+            for ln in open(self.path):
+                t = [x.strip() for x in ln.split(",")]
+                if len(t) >= 9 and t[1].replace(".", "").isdigit():
+                    bits = 0
+                    for i, nm in enumerate(names):
+                        if t[5 + i].lower() == "active":
+                            bits |= {"hw_slowdown": 0x8, "hw_thermal_slowdown": 0x40, "sw_thermal_slowdown": 0x20,
+                                     "sw_power_cap": 0x4}[nm]
+                    self.rows.append((float(t[1]), float(t[2]) if t[2].replace(".", "").isdigit() else 0.0, bits))
 
     def summary(self):
-        if self.p is None:
-            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
-        rows = []
-        for ln in open(self.path):
-            t = [x.strip() for x in ln.split(",")]
-            if len(t) >= 9:
-                rows.append(t)
-        if not rows:
-            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
-        sm = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
-        mx = [float(r[2]) for r in rows if r[2].replace(".", "").isdigit()]
-        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
-        reasons = sorted({names[i] for r in rows for i in range(4) if r[5 + i].lower() == "active"})
-        return {"sm_mhz": float(np.median(sm)) if sm else None, "sm_max_mhz": max(mx) if mx else None,
-                "reasons": reasons, "samples": len(rows)}
+        if not self.rows:
+            return {"sm_mhz": None, "sm_max_mhz": None,
+                    "reasons": ["no samples" if (self.nvml or self.smi) else "no NVML and no nvidia-smi"]}
+        sm = [r[0] for r in self.rows]
+        reasons = sorted({nm for r in self.rows for bit, nm in self.REASONS.items() if r[2] & bit})
+        return {"sm_mhz": float(np.median(sm)), "sm_max_mhz": float(max(r[1] for r in self.rows)),
+                "reasons": reasons, "samples": len(self.rows),
+                "source": "nvml (2 ms polling)" if self.nvml else "nvidia-smi (100 ms)"}
 
 
 def source_sha256(files):

@@ -66,8 +66,10 @@ enum { PIC_LASER_LINEAR_Y = 0, PIC_LASER_CIRCULAR = 1 };
 
 /* Grid.  dim in {1,2,3}; n[d] cells and dx[d] spacing along active axes
  * (entries for inactive axes are ignored).  bc[d] applies to both faces of
- * axis d.  order is the shape order of Sec. II.D; only 2 (the three-node
- * W_2 weights) is implemented.  Periodic axes need n[d] >= 8. */
+ * axis d.  order is the shape order of Sec. II.D (Eqs. (17), (18)): 2 (the
+ * three-node W_2 weights) or 4 (the five-node W_4, a 7-node Esirkepov
+ * window; the push runs on the one-thread-per-particle kernels, and the QED
+ * Monte Carlo needs order 2).  Periodic axes need n[d] >= 8. */
 typedef struct {
     int dim;
     int64_t n[3];

@@ -180,7 +180,9 @@ int sort_species(pic_sim *s, int i)
 
 bool use_tile_push(const pic_sim *s, const SpeciesState &p)
 {
+    // the tiled kernels stage order-2 stencils; order 4 runs on the simple kernels
     if (s->push_variant == PIC_PUSH_SIMPLE || !p.items_valid || s->precision != PIC_PREC_FP32_CELLOFF ||
+        s->g.order != 2 ||
         p.kind != PIC_KIND_MASSIVE || (s->qed_on && p.qed))
         return false;
     if (s->g.dim == 3) return tile3d_push_supported(s->g);
@@ -519,7 +521,7 @@ int pic_create(const pic_grid *grid, double dt, const pic_species *species, int 
         opt = &o;
     }
     if (grid->dim < 1 || grid->dim > 3) return fail(s, PIC_ERR_ARG, "pic_create: dim must be 1, 2 or 3");
-    if (grid->order != 2) return fail(s, PIC_ERR_ARG, "pic_create: only shape order 2 is implemented");
+    if (grid->order != 2 && grid->order != 4) return fail(s, PIC_ERR_ARG, "pic_create: shape order must be 2 or 4");
     int prec = opt ? opt->precision : PIC_PREC_FP32_CELLOFF;
     if (prec != PIC_PREC_FP32_CELLOFF && prec != PIC_PREC_FP64_PLAIN)
         return fail(s, PIC_ERR_ARG, "pic_create: unknown precision");
@@ -529,6 +531,7 @@ int pic_create(const pic_grid *grid, double dt, const pic_species *species, int 
         return fail(s, PIC_ERR_ARG, "pic_create: unknown pusher");
     Grid g{};
     g.dim = grid->dim;
+    g.order = grid->order;
     g.dt = dt;
     double cfl = 0.0;
     int bitsum = 0;
@@ -774,6 +777,8 @@ int pic_set_qed(pic_sim *s, const pic_qed *Q)
     if (!s || !Q) return PIC_ERR_ARG;
     if (Q->mode != PIC_QED_OFF && Q->mode != PIC_QED_TABLE && Q->mode != PIC_QED_SURROGATE)
         return fail(s, PIC_ERR_ARG, "pic_set_qed: bad mode");
+    if (Q->mode != PIC_QED_OFF && s->g.order != 2)
+        return fail(s, PIC_ERR_ARG, "pic_set_qed: the QED push kernels use the order-2 shape");
     auto kind_ok = [&](int i, int kind) { return i == -1 || (i >= 0 && i < s->nsp && s->sp[i].kind == kind); };
     if (!kind_ok(Q->photon_sp, PIC_KIND_PHOTON) || !kind_ok(Q->electron_sp, PIC_KIND_MASSIVE) ||
         !kind_ok(Q->positron_sp, PIC_KIND_MASSIVE) || !(Q->lambda_r_m > 0.0) || Q->photon_emin < 0.0)
@@ -924,9 +929,11 @@ int pic_profile(pic_sim *s, int enable)
     s->marks.clear();
     for (int p = 0; p < PIC_NPHASE; p++) s->prof_launch[p] = 0;
     s->prof_push = 0;
-    for (int i = 0; i < PIC_MAX_SPECIES; i++) {
-        s->prof_sp_ms[i] = 0.0;
-        s->prof_sp_n[i] = 0;
+    if (enable) {  // the per-species times gathered so far stay readable after disabling
+        for (int i = 0; i < PIC_MAX_SPECIES; i++) {
+            s->prof_sp_ms[i] = 0.0;
+            s->prof_sp_n[i] = 0;
+        }
     }
     s->prof = enable != 0;
     return PIC_OK;

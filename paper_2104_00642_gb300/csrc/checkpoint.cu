@@ -26,7 +26,7 @@ constexpr uint32_t kVersion = 1;
 
 // configuration the state depends on: restore only into an equal one
 struct Signature {
-    int dim, precision, nsp, sort_interval, pusher, pad;
+    int dim, precision, nsp, sort_interval, pusher, order;
     int n[3], bc[3], tile_log2[3];
     double dx[3], dt;
     uint64_t seed;
@@ -44,6 +44,7 @@ Signature signature(const pic_sim *s)
     z.nsp = s->nsp;
     z.sort_interval = s->sort_interval;
     z.pusher = s->pusher;
+    z.order = s->g.order;
     for (int d = 0; d < 3; d++) {
         z.n[d] = s->g.n[d];
         z.bc[d] = s->g.bc[d];

@@ -8,6 +8,7 @@
 // then one block summing the partials in index order, so results do not
 // depend on scheduling.
 #include "diag.cuh"
+#include "push_dev.cuh"
 
 namespace pic {
 
@@ -128,40 +129,44 @@ __global__ void __launch_bounds__(kRedThreads) k_final(const double *__restrict_
     }
 }
 
-// charge density of one species: q w W_2 at x -/+ (dt/2) v, half each
-template <int DIM>
+// charge density of one species: q w W (W_2 or W_4, the shape the deposit
+// uses) at x -/+ (dt/2) v, half each
+template <int DIM, int ORDER>
 __device__ __forceinline__ void rho_add(double *rho, const Grid &g, const double *X, double qw2)
 {
+    constexpr int P = ORDER + 1, H = ORDER / 2;
     // a non-finite position has no node; the pushes remove particles whose
     // momentum became non-finite, so this only guards the index arithmetic
 #pragma unroll
     for (int d = 0; d < DIM; d++)
         if (!isfinite(X[d])) return;
     int ic[3] = {0, 0, 0};
-    double w[3][3];
+    double w[3][P];
 #pragma unroll
     for (int d = 0; d < 3; d++) {
         if (d < DIM) {
             ic[d] = (int)floor(X[d] + 0.5);
-            w2<double>(X[d] - (double)ic[d], w[d]);
+            if constexpr (ORDER == 4) w4<double>(X[d] - (double)ic[d], w[d]);
+            else w2<double>(X[d] - (double)ic[d], w[d]);
         } else {
-            w[d][0] = 0.0; w[d][1] = 1.0; w[d][2] = 0.0;
+#pragma unroll
+            for (int a = 0; a < P; a++) w[d][a] = a == H ? 1.0 : 0.0;
         }
     }
 #pragma unroll
-    for (int c = 0; c < (DIM > 2 ? 3 : 1); c++)
+    for (int c = 0; c < (DIM > 2 ? P : 1); c++)
 #pragma unroll
-        for (int b = 0; b < (DIM > 1 ? 3 : 1); b++)
+        for (int b = 0; b < (DIM > 1 ? P : 1); b++)
 #pragma unroll
-            for (int a = 0; a < 3; a++) {
-                int jb = DIM > 1 ? b : 1, kc = DIM > 2 ? c : 1;
+            for (int a = 0; a < P; a++) {
+                int jb = DIM > 1 ? b : H, kc = DIM > 2 ? c : H;
                 double wt = w[0][a] * w[1][jb] * w[2][kc];
-                atomicAdd(rho + goff(g, ic[0] + a - 1, DIM > 1 ? ic[1] + b - 1 : 0, DIM > 2 ? ic[2] + c - 1 : 0),
+                atomicAdd(rho + goff(g, ic[0] + a - H, DIM > 1 ? ic[1] + b - H : 0, DIM > 2 ? ic[2] + c - H : 0),
                           qw2 * wt);
             }
 }
 
-template <int DIM>
+template <int DIM, int ORDER>
 __global__ void k_rho_f32(PartF32 P, Grid g, double hdt, double qw2, double *rho)
 {
     long long p = (long long)blockIdx.x * blockDim.x + threadIdx.x;
@@ -176,11 +181,11 @@ __global__ void k_rho_f32(PartF32 P, Grid g, double hdt, double qw2, double *rho
     for (int side = -1; side <= 1; side += 2) {
         double X[3] = {0, 0, 0};
         for (int d = 0; d < DIM; d++) X[d] = (double)c[d] + (double)P.off[d][p] + side * hdt * u[d] * ig / g.dx[d];
-        rho_add<DIM>(rho, g, X, qw2);
+        rho_add<DIM, ORDER>(rho, g, X, qw2);
     }
 }
 
-template <int DIM>
+template <int DIM, int ORDER>
 __global__ void k_rho_f64(PartF64 P, Grid g, double hdt, double qw2, double *rho)
 {
     long long p = (long long)blockIdx.x * blockDim.x + threadIdx.x;
@@ -192,7 +197,7 @@ __global__ void k_rho_f64(PartF64 P, Grid g, double hdt, double qw2, double *rho
     for (int side = -1; side <= 1; side += 2) {
         double X[3] = {0, 0, 0};
         for (int d = 0; d < DIM; d++) X[d] = (P.x[d][p] + side * hdt * u[d] * ig) / g.dx[d];
-        rho_add<DIM>(rho, g, X, qw2);
+        rho_add<DIM, ORDER>(rho, g, X, qw2);
     }
 }
 
@@ -249,18 +254,30 @@ void diag_rho_f32(const PartF32 &P, const Grid &g, double qw, double *rho, cudaS
     if (P.n == 0) return;
     int nb = div_up(P.n, 256);
     double h = 0.5 * g.dt;
-    if (g.dim == 1) k_rho_f32<1><<<nb, 256, 0, st>>>(P, g, h, 0.5 * qw, rho);
-    else if (g.dim == 2) k_rho_f32<2><<<nb, 256, 0, st>>>(P, g, h, 0.5 * qw, rho);
-    else k_rho_f32<3><<<nb, 256, 0, st>>>(P, g, h, 0.5 * qw, rho);
+    if (g.order == 4) {
+        if (g.dim == 1) k_rho_f32<1, 4><<<nb, 256, 0, st>>>(P, g, h, 0.5 * qw, rho);
+        else if (g.dim == 2) k_rho_f32<2, 4><<<nb, 256, 0, st>>>(P, g, h, 0.5 * qw, rho);
+        else k_rho_f32<3, 4><<<nb, 256, 0, st>>>(P, g, h, 0.5 * qw, rho);
+        return;
+    }
+    if (g.dim == 1) k_rho_f32<1, 2><<<nb, 256, 0, st>>>(P, g, h, 0.5 * qw, rho);
+    else if (g.dim == 2) k_rho_f32<2, 2><<<nb, 256, 0, st>>>(P, g, h, 0.5 * qw, rho);
+    else k_rho_f32<3, 2><<<nb, 256, 0, st>>>(P, g, h, 0.5 * qw, rho);
 }
 void diag_rho_f64(const PartF64 &P, const Grid &g, double qw, double *rho, cudaStream_t st)
 {
     if (P.n == 0) return;
     int nb = div_up(P.n, 256);
     double h = 0.5 * g.dt;
-    if (g.dim == 1) k_rho_f64<1><<<nb, 256, 0, st>>>(P, g, h, 0.5 * qw, rho);
-    else if (g.dim == 2) k_rho_f64<2><<<nb, 256, 0, st>>>(P, g, h, 0.5 * qw, rho);
-    else k_rho_f64<3><<<nb, 256, 0, st>>>(P, g, h, 0.5 * qw, rho);
+    if (g.order == 4) {
+        if (g.dim == 1) k_rho_f64<1, 4><<<nb, 256, 0, st>>>(P, g, h, 0.5 * qw, rho);
+        else if (g.dim == 2) k_rho_f64<2, 4><<<nb, 256, 0, st>>>(P, g, h, 0.5 * qw, rho);
+        else k_rho_f64<3, 4><<<nb, 256, 0, st>>>(P, g, h, 0.5 * qw, rho);
+        return;
+    }
+    if (g.dim == 1) k_rho_f64<1, 2><<<nb, 256, 0, st>>>(P, g, h, 0.5 * qw, rho);
+    else if (g.dim == 2) k_rho_f64<2, 2><<<nb, 256, 0, st>>>(P, g, h, 0.5 * qw, rho);
+    else k_rho_f64<3, 2><<<nb, 256, 0, st>>>(P, g, h, 0.5 * qw, rho);
 }
 
 template <typename R>

@@ -31,6 +31,7 @@ enum ErrFlag : int { ERR_CFL = 1, ERR_NONFINITE = 2, ERR_CAPACITY = 4, ERR_TIMEO
 
 struct Grid {
     int dim;
+    int order;         // shape order of Sec. II.D: 2 (W_2, three nodes) or 4 (W_4, five nodes)
     int n[3];          // cells per axis (1 on inactive axes)
     int G[3];          // ghost layers per side (kGhost on active axes, 0 otherwise)
     int ext[3];        // n + 2G

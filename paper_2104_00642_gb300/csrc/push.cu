@@ -24,17 +24,17 @@ long long g_launches = 0;
 // ---------------------------------------------------------------------
 // FP32 cell+offset push
 // ---------------------------------------------------------------------
-template <int DIM>
+template <int DIM, int ORDER = 2>
 __device__ __forceinline__ void push_one_f32(const PartF32 &P, long long p, float *__restrict__ F, const Grid &g,
                                              const PushConst &pc, int *err, double *e_abs);
 
-template <int DIM>
+template <int DIM, int ORDER>
 __global__ void __launch_bounds__(256) k_push_f32(PartF32 P, float *__restrict__ F, Grid g, PushConst pc,
                                                   int *err, double *e_abs)
 {
     long long p = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     if (p >= *P.dn) return;
-    push_one_f32<DIM>(P, p, F, g, pc, err, e_abs);
+    push_one_f32<DIM, ORDER>(P, p, F, g, pc, err, e_abs);
 }
 
 // the particles of a list (the tiled push's deferred ones), grid-stride
@@ -49,8 +49,8 @@ __global__ void __launch_bounds__(256) k_push_list_f32(PartF32 P, const uint32_t
 }
 
 // one particle: half drift, gather (HBM), Boris, drifts, Esirkepov (global
-// atomics), boundaries
-template <int DIM>
+// atomics), boundaries; shape order ORDER (W_2 or W_4 of Sec. II.D)
+template <int DIM, int ORDER>
 __device__ __forceinline__ void push_one_f32(const PartF32 &P, long long p, float *__restrict__ F, const Grid &g,
                                              const PushConst &pc, int *err, double *e_abs)
 {
@@ -70,11 +70,11 @@ __device__ __forceinline__ void push_one_f32(const PartF32 &P, long long p, floa
     float oh[3] = {o[0], o[1], o[2]};
     // gather
     int icn[3] = {0, 0, 0}, ich[3] = {0, 0, 0};
-    float wn[3][3], wh[3][3];
+    float wn[3][ORDER + 1], wh[3][ORDER + 1];
 #pragma unroll
-    for (int d = 0; d < DIM; d++) axis_w_f32(c[d], o[d], icn[d], wn[d], ich[d], wh[d]);
+    for (int d = 0; d < DIM; d++) axis_w_f32<ORDER>(c[d], o[d], icn[d], wn[d], ich[d], wh[d]);
     float eb[6];
-    gather<float, DIM>(F, g, icn, wn, ich, wh, eb);
+    gather<float, DIM, ORDER>(F, g, icn, wn, ich, wh, eb);
     // Boris
     const float k = pc.qmdt2_f;
     lorentz<float>(pc.pusher, ux, uy, uz, k * eb[0], k * eb[1], k * eb[2], k * eb[3], k * eb[4], k * eb[5]);
@@ -88,17 +88,17 @@ __device__ __forceinline__ void push_one_f32(const PartF32 &P, long long p, floa
 #pragma unroll
     for (int d = 0; d < DIM; d++) drift_f32(c[d], o[d], pc.hdx_f[d] * u[d] * ig1);
     // Esirkepov on x^{n+1/2} -> x^{n+3/2}
-    float S0[3][5], dS[3][5];
+    float S0[3][ORDER + 3], dS[3][ORDER + 3];
     int base[3] = {0, 0, 0};
     bool ok = true;
 #pragma unroll
     for (int d = 0; d < DIM; d++) {
         int i0, i1;
-        float w0[3], w1[3];
-        axis_wn_f32(ch[d], oh[d], i0, w0);
-        axis_wn_f32(c[d], o[d], i1, w1);
-        ok &= window5<float>(i0, w0, i1, w1, S0[d], dS[d]);
-        base[d] = i0 - 2;
+        float w0[ORDER + 1], w1[ORDER + 1];
+        axis_wn_f32<ORDER>(ch[d], oh[d], i0, w0);
+        axis_wn_f32<ORDER>(c[d], o[d], i1, w1);
+        ok &= window_n<float, ORDER>(i0, w0, i1, w1, S0[d], dS[d]);
+        base[d] = i0 - ORDER / 2 - 1;
     }
     // a non-finite momentum (a NaN or infinite field) is reported and the particle
     // removed before anything uses its position: NaN positions would give no valid
@@ -115,7 +115,7 @@ __device__ __forceinline__ void push_one_f32(const PartF32 &P, long long p, floa
     }
     const float cJ[3] = {pc.cJ_f[0], pc.cJ_f[1], pc.cJ_f[2]};
     const float qw = pc.qw_f;
-    deposit_global<float, DIM>(F, g, base, S0, dS, cJ, qw * uy * ig1, qw * uz * ig1);
+    deposit_global<float, DIM, ORDER>(F, g, base, S0, dS, cJ, qw * uy * ig1, qw * uz * ig1);
     // boundaries
     bool dead = false;
 #pragma unroll
@@ -144,7 +144,7 @@ __device__ __forceinline__ void push_one_f32(const PartF32 &P, long long p, floa
 // ---------------------------------------------------------------------
 // FP64 plain push (absolute positions)
 // ---------------------------------------------------------------------
-template <int DIM>
+template <int DIM, int ORDER>
 __global__ void __launch_bounds__(256) k_push_f64(PartF64 P, double *__restrict__ F, Grid g, PushConst pc,
                                                   int *err, double *e_abs)
 {
@@ -159,11 +159,11 @@ __global__ void __launch_bounds__(256) k_push_f64(PartF64 P, double *__restrict_
     for (int d = 0; d < DIM; d++) x[d] += pc.hdt * u[d] * ig;
     double xh[3] = {x[0], x[1], x[2]};
     int icn[3] = {0, 0, 0}, ich[3] = {0, 0, 0};
-    double wn[3][3], wh[3][3];
+    double wn[3][ORDER + 1], wh[3][ORDER + 1];
 #pragma unroll
-    for (int d = 0; d < DIM; d++) axis_w_f64(x[d] / g.dx[d], icn[d], wn[d], ich[d], wh[d]);
+    for (int d = 0; d < DIM; d++) axis_w_f64<ORDER>(x[d] / g.dx[d], icn[d], wn[d], ich[d], wh[d]);
     double eb[6];
-    gather<double, DIM>(F, g, icn, wn, ich, wh, eb);
+    gather<double, DIM, ORDER>(F, g, icn, wn, ich, wh, eb);
     const double k = pc.qmdt2;
     lorentz<double>(pc.pusher, ux, uy, uz, k * eb[0], k * eb[1], k * eb[2], k * eb[3], k * eb[4], k * eb[5]);
     double ig1 = inv_gamma(ux, uy, uz);
@@ -173,17 +173,17 @@ __global__ void __launch_bounds__(256) k_push_f64(PartF64 P, double *__restrict_
     double x1[3] = {x[0], x[1], x[2]};
 #pragma unroll
     for (int d = 0; d < DIM; d++) x[d] += pc.hdt * u[d] * ig1;
-    double S0[3][5], dS[3][5];
+    double S0[3][ORDER + 3], dS[3][ORDER + 3];
     int base[3] = {0, 0, 0};
     bool ok = true;
 #pragma unroll
     for (int d = 0; d < DIM; d++) {
         int i0, i1;
-        double w0[3], w1[3];
-        axis_wn_f64(xh[d] / g.dx[d], i0, w0);
-        axis_wn_f64(x[d] / g.dx[d], i1, w1);
-        ok &= window5<double>(i0, w0, i1, w1, S0[d], dS[d]);
-        base[d] = i0 - 2;
+        double w0[ORDER + 1], w1[ORDER + 1];
+        axis_wn_f64<ORDER>(xh[d] / g.dx[d], i0, w0);
+        axis_wn_f64<ORDER>(x[d] / g.dx[d], i1, w1);
+        ok &= window_n<double, ORDER>(i0, w0, i1, w1, S0[d], dS[d]);
+        base[d] = i0 - ORDER / 2 - 1;
     }
     // a non-finite momentum (a NaN or infinite field) is reported and the particle
     // removed before anything uses its position: NaN positions would give no valid
@@ -198,7 +198,7 @@ __global__ void __launch_bounds__(256) k_push_f64(PartF64 P, double *__restrict_
         atomicOr(err, ERR_CFL);
         return;
     }
-    deposit_global<double, DIM>(F, g, base, S0, dS, pc.cJ, pc.qw * uy * ig1, pc.qw * uz * ig1);
+    deposit_global<double, DIM, ORDER>(F, g, base, S0, dS, pc.cJ, pc.qw * uy * ig1, pc.qw * uz * ig1);
     bool dead = false;
     int cc[3] = {0, 0, 0};
 #pragma unroll
@@ -230,7 +230,7 @@ __global__ void __launch_bounds__(256) k_push_f64(PartF64 P, double *__restrict_
 // ---------------------------------------------------------------------
 // gather at the stored positions (inspection)
 // ---------------------------------------------------------------------
-template <int DIM>
+template <int DIM, int ORDER>
 __global__ void k_gather_f32(PartF32 P, const float *__restrict__ F, Grid g, double *out)
 {
     long long p = (long long)blockIdx.x * blockDim.x + threadIdx.x;
@@ -243,15 +243,15 @@ __global__ void k_gather_f32(PartF32 P, const float *__restrict__ F, Grid g, dou
     int c[3];
     unpack_cell(g, cp, c[0], c[1], c[2]);
     int icn[3] = {0, 0, 0}, ich[3] = {0, 0, 0};
-    float wn[3][3], wh[3][3];
+    float wn[3][ORDER + 1], wh[3][ORDER + 1];
 #pragma unroll
-    for (int d = 0; d < DIM; d++) axis_w_f32(c[d], P.off[d][p], icn[d], wn[d], ich[d], wh[d]);
+    for (int d = 0; d < DIM; d++) axis_w_f32<ORDER>(c[d], P.off[d][p], icn[d], wn[d], ich[d], wh[d]);
     float eb[6];
-    gather<float, DIM>(F, g, icn, wn, ich, wh, eb);
+    gather<float, DIM, ORDER>(F, g, icn, wn, ich, wh, eb);
     for (int q = 0; q < 6; q++) out[6 * p + q] = eb[q];
 }
 
-template <int DIM>
+template <int DIM, int ORDER>
 __global__ void k_gather_f64(PartF64 P, const double *__restrict__ F, Grid g, double *out)
 {
     long long p = (long long)blockIdx.x * blockDim.x + threadIdx.x;
@@ -261,11 +261,11 @@ __global__ void k_gather_f64(PartF64 P, const double *__restrict__ F, Grid g, do
         return;
     }
     int icn[3] = {0, 0, 0}, ich[3] = {0, 0, 0};
-    double wn[3][3], wh[3][3];
+    double wn[3][ORDER + 1], wh[3][ORDER + 1];
 #pragma unroll
-    for (int d = 0; d < DIM; d++) axis_w_f64(P.x[d][p] / g.dx[d], icn[d], wn[d], ich[d], wh[d]);
+    for (int d = 0; d < DIM; d++) axis_w_f64<ORDER>(P.x[d][p] / g.dx[d], icn[d], wn[d], ich[d], wh[d]);
     double eb[6];
-    gather<double, DIM>(F, g, icn, wn, ich, wh, eb);
+    gather<double, DIM, ORDER>(F, g, icn, wn, ich, wh, eb);
     for (int q = 0; q < 6; q++) out[6 * p + q] = eb[q];
 }
 
@@ -384,9 +384,15 @@ void launch_push_f32(const PartF32 &P, float *F, const Grid &g, const PushConst 
     if (P.n == 0) return;
     note_launch();
     int bs = 256, nb = div_up(P.n, bs);
-    if (g.dim == 1) k_push_f32<1><<<nb, bs, 0, st>>>(P, F, g, pc, err, e_abs);
-    else if (g.dim == 2) k_push_f32<2><<<nb, bs, 0, st>>>(P, F, g, pc, err, e_abs);
-    else k_push_f32<3><<<nb, bs, 0, st>>>(P, F, g, pc, err, e_abs);
+    if (g.order == 4) {
+        if (g.dim == 1) k_push_f32<1, 4><<<nb, bs, 0, st>>>(P, F, g, pc, err, e_abs);
+        else if (g.dim == 2) k_push_f32<2, 4><<<nb, bs, 0, st>>>(P, F, g, pc, err, e_abs);
+        else k_push_f32<3, 4><<<nb, bs, 0, st>>>(P, F, g, pc, err, e_abs);
+        return;
+    }
+    if (g.dim == 1) k_push_f32<1, 2><<<nb, bs, 0, st>>>(P, F, g, pc, err, e_abs);
+    else if (g.dim == 2) k_push_f32<2, 2><<<nb, bs, 0, st>>>(P, F, g, pc, err, e_abs);
+    else k_push_f32<3, 2><<<nb, bs, 0, st>>>(P, F, g, pc, err, e_abs);
 }
 
 void launch_push_list_f32(const PartF32 &P, const uint32_t *list, const uint32_t *count, long long max_n, float *F,
@@ -406,9 +412,15 @@ void launch_push_f64(const PartF64 &P, double *F, const Grid &g, const PushConst
     if (P.n == 0) return;
     note_launch();
     int bs = 256, nb = div_up(P.n, bs);
-    if (g.dim == 1) k_push_f64<1><<<nb, bs, 0, st>>>(P, F, g, pc, err, e_abs);
-    else if (g.dim == 2) k_push_f64<2><<<nb, bs, 0, st>>>(P, F, g, pc, err, e_abs);
-    else k_push_f64<3><<<nb, bs, 0, st>>>(P, F, g, pc, err, e_abs);
+    if (g.order == 4) {
+        if (g.dim == 1) k_push_f64<1, 4><<<nb, bs, 0, st>>>(P, F, g, pc, err, e_abs);
+        else if (g.dim == 2) k_push_f64<2, 4><<<nb, bs, 0, st>>>(P, F, g, pc, err, e_abs);
+        else k_push_f64<3, 4><<<nb, bs, 0, st>>>(P, F, g, pc, err, e_abs);
+        return;
+    }
+    if (g.dim == 1) k_push_f64<1, 2><<<nb, bs, 0, st>>>(P, F, g, pc, err, e_abs);
+    else if (g.dim == 2) k_push_f64<2, 2><<<nb, bs, 0, st>>>(P, F, g, pc, err, e_abs);
+    else k_push_f64<3, 2><<<nb, bs, 0, st>>>(P, F, g, pc, err, e_abs);
 }
 
 void launch_gather_f32(const PartF32 &P, const float *F, const Grid &g, double *out, cudaStream_t st)
@@ -416,9 +428,15 @@ void launch_gather_f32(const PartF32 &P, const float *F, const Grid &g, double *
     if (P.n == 0) return;
     note_launch();
     int bs = 256, nb = div_up(P.n, bs);
-    if (g.dim == 1) k_gather_f32<1><<<nb, bs, 0, st>>>(P, F, g, out);
-    else if (g.dim == 2) k_gather_f32<2><<<nb, bs, 0, st>>>(P, F, g, out);
-    else k_gather_f32<3><<<nb, bs, 0, st>>>(P, F, g, out);
+    if (g.order == 4) {
+        if (g.dim == 1) k_gather_f32<1, 4><<<nb, bs, 0, st>>>(P, F, g, out);
+        else if (g.dim == 2) k_gather_f32<2, 4><<<nb, bs, 0, st>>>(P, F, g, out);
+        else k_gather_f32<3, 4><<<nb, bs, 0, st>>>(P, F, g, out);
+        return;
+    }
+    if (g.dim == 1) k_gather_f32<1, 2><<<nb, bs, 0, st>>>(P, F, g, out);
+    else if (g.dim == 2) k_gather_f32<2, 2><<<nb, bs, 0, st>>>(P, F, g, out);
+    else k_gather_f32<3, 2><<<nb, bs, 0, st>>>(P, F, g, out);
 }
 
 void launch_gather_f64(const PartF64 &P, const double *F, const Grid &g, double *out, cudaStream_t st)
@@ -426,9 +444,15 @@ void launch_gather_f64(const PartF64 &P, const double *F, const Grid &g, double 
     if (P.n == 0) return;
     note_launch();
     int bs = 256, nb = div_up(P.n, bs);
-    if (g.dim == 1) k_gather_f64<1><<<nb, bs, 0, st>>>(P, F, g, out);
-    else if (g.dim == 2) k_gather_f64<2><<<nb, bs, 0, st>>>(P, F, g, out);
-    else k_gather_f64<3><<<nb, bs, 0, st>>>(P, F, g, out);
+    if (g.order == 4) {
+        if (g.dim == 1) k_gather_f64<1, 4><<<nb, bs, 0, st>>>(P, F, g, out);
+        else if (g.dim == 2) k_gather_f64<2, 4><<<nb, bs, 0, st>>>(P, F, g, out);
+        else k_gather_f64<3, 4><<<nb, bs, 0, st>>>(P, F, g, out);
+        return;
+    }
+    if (g.dim == 1) k_gather_f64<1, 2><<<nb, bs, 0, st>>>(P, F, g, out);
+    else if (g.dim == 2) k_gather_f64<2, 2><<<nb, bs, 0, st>>>(P, F, g, out);
+    else k_gather_f64<3, 2><<<nb, bs, 0, st>>>(P, F, g, out);
 }
 
 void launch_load_f32(const PartF32 &P, long long first, long long n, const double *const *xs,

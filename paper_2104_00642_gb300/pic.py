@@ -237,7 +237,7 @@ class Sim:
 
     def __init__(self, dim, n, dx, dt, species, bc=(PERIODIC, PERIODIC, PERIODIC), precision=FP32_CELLOFF,
                  sort_interval=0, tile=(0, 0, 0), rho_bg=0.0, stream=None, push_variant=0, seed=0, pusher=0,
-                 allocator=None):
+                 allocator=None, order=2):
         L = load_library()
         g = pic_grid()
         g.dim = int(dim)
@@ -245,7 +245,7 @@ class Sim:
             g.n[d] = int(n[d]) if d < len(n) else 1
             g.dx[d] = float(dx[d]) if d < len(dx) else 1.0
             g.bc[d] = int(bc[d]) if d < len(bc) else PERIODIC
-        g.order = 2
+        g.order = int(order)
         sp = (pic_species * max(1, len(species)))()
         for i, s in enumerate(species):
             sp[i].q, sp[i].m, sp[i].w, sp[i].capacity = float(s[0]), float(s[1]), float(s[2]), int(s[3])
@@ -476,14 +476,14 @@ def pic_create(dim, n, dx, dt, species, **kw) -> Sim:
 
 
 def from_workload(w, precision=FP32_CELLOFF, sort_interval=0, capacity_scale=1.0, load=True, stream=None,
-                  tile=None, push_variant=0, seed=0, pusher=0, allocator=None) -> Sim:
+                  tile=None, push_variant=0, seed=0, pusher=0, allocator=None, order=2) -> Sim:
     """Create a simulation for a :class:`workloads.Workload` and load its particles
     (QED workloads: the Monte Carlo is configured in table mode first)."""
     sp = [(s.q, s.m, s.w, max(1, int(s.capacity * capacity_scale)), s.kind, s.qed) for s in w.species]
     t = tile if tile is not None else tuple(w.tile)
     sim = Sim(w.dim, w.n, w.dx, w.dt, sp, bc=w.bc, precision=precision, sort_interval=sort_interval, tile=t,
               rho_bg=w.rho_bg, stream=stream, push_variant=push_variant, seed=seed, pusher=pusher,
-              allocator=allocator)
+              allocator=allocator, order=order)
     if w.laser is not None:
         L = w.laser
         sim.pic_set_laser(L.a0, L.waist, L.fwhm, L.t_peak, L.x_focus, L.yc, L.zc, L.pol)

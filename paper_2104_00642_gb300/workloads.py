@@ -167,6 +167,29 @@ def thermal_2d(n=(256, 256), dx=0.1, ppc=16, T_keV=10.0, steps=100, courant=0.95
                     rho_bg=1.0, tile=tile, notes={"theta": theta, "ppc": ppc})
 
 
+def self_heating_2d(n=(128, 128), ppc=16, T_keV=1.0, cells_per_lambda_p=320, steps=4000, courant=0.95,
+                    seed=SEED0 + 10, tile=(16, 16, 1)):
+    """The self-heating test of Sec. III(b) (Fig. 6): a uniform thermal
+    plasma, T = 1 keV, periodic, 320 cells per plasma wavelength (the
+    paper's n = 100 n_c sets only the unit: lengths here in c/omega_p, so
+    dx = 2 pi / 320 and n = 1); electrons at Philox-uniform positions with
+    u ~ N(0, T/mc^2) per component on a fixed neutralising background.  The
+    figure reports the relative growth of the total energy against shape
+    order and ppc."""
+    rng = _rng(seed)
+    dx = 2.0 * math.pi / cells_per_lambda_p
+    N = n[0] * n[1] * ppc
+    theta = T_keV / MEC2_KEV
+    x = rng.random(N) * (n[0] * dx)
+    y = rng.random(N) * (n[1] * dx)
+    s = math.sqrt(theta)
+    ux, uy, uz = (rng.standard_normal(N) * s for _ in range(3))
+    e = Species("electron", -1.0, 1.0, 1.0 / ppc, x, y, np.zeros(N), ux, uy, uz, capacity=N)
+    dt = courant * dx / math.sqrt(2.0)
+    return Workload("self_heating_2d", 2, (n[0], n[1], 1), (dx, dx, 1.0), dt, (PERIODIC,) * 3, [e], steps,
+                    rho_bg=1.0, tile=tile, notes={"theta": theta, "ppc": ppc, "debye_over_dx": math.sqrt(theta) / dx})
+
+
 def laser_foil_2d(nx=2048, ny=1024, cells_per_lambda=64, slab=(1024, 1088), n0=10.0, ppc=32,
                   T_keV=1.0, a0=20.0, waist_um=3.0, fwhm_fs=30.0, steps=4000, courant=0.95,
                   seed=SEED0 + 2, tile=(16, 16, 1), x_focus_cell=None):

@@ -57,9 +57,10 @@ def boundary_ambiguous(x, dx, tol=2.0 ** -18):
     return (f < tol) | (f > 1 - tol)
 
 
-def window_scale(o_parts, w, dim, comp_axis):
+def window_scale(o_parts, w, dim, comp_axis, reach=3):
     """per-node scale of the summed current terms: |q w| dx_d/dt times the
-    number of particles whose deposit window (7 cells) covers the node"""
+    number of particles whose deposit window (2 reach + 1 cells around the
+    particle's cell; 3 covers the order-2 window) covers the node"""
     s = w.species[0]
     shape = [1, 1, 1]
     for d in range(dim):
@@ -73,9 +74,9 @@ def window_scale(o_parts, w, dim, comp_axis):
             idx.append(c)
         else:
             idx.append(np.zeros_like(o_parts["ux"], dtype=np.int64))
-    for d0 in range(-3, 4):
-        for d1 in (range(-3, 4) if dim > 1 else [0]):
-            for d2 in (range(-3, 4) if dim > 2 else [0]):
+    for d0 in range(-reach, reach + 1):
+        for d1 in (range(-reach, reach + 1) if dim > 1 else [0]):
+            for d2 in (range(-reach, reach + 1) if dim > 2 else [0]):
                 ii = np.mod(idx[0] + d0, shape[2])
                 jj = np.mod(idx[1] + d1, shape[1])
                 kk = np.mod(idx[2] + d2, shape[0])
