@@ -650,7 +650,8 @@ def main():
                     help="smaller case for profiling: ny of laser_foil_2d, nz of thermal_3d (not a bench line)")
     ap.add_argument("--qed-modes", default="surrogate,table,fp64", help="forms run by the QED workloads")
     ap.add_argument("--push-variant", type=int, default=0,
-                    help="0: default kernels, 2: surrogate of the photon push per CTA on tcgen05 (QED workloads)")
+                    help="0: default kernels, 2: surrogate of the photon push per CTA on tcgen05 (QED workloads), "
+                         "3: warp-aggregated deposit in the 2D tiled push")
     ap.add_argument("--mlp-rows", type=int, default=0,
                     help="instead of a PIC workload: evaluate a random surrogate network on this many rows with "
                          "the mma.sync and the tcgen05 kernels (profiling aid; kernel times come from ncu)")
@@ -745,7 +746,7 @@ def main():
     if pre is None:
         pre = PRE_STEPS.get(args.workload, 0) if args.rows is None else 0
     sim = pic.from_workload(w, precision=pic.FP32_CELLOFF, sort_interval=args.sort_interval,
-                            stream=stream.cuda_stream)
+                            stream=stream.cuda_stream, push_variant=args.push_variant)
     if pre:
         with torch.cuda.stream(stream):
             sim.pic_step(pre)  # untimed: to the phase the window measures
@@ -810,7 +811,7 @@ def main():
         size = os.path.getsize(ckpt)
         sim.close()
         sim_e = pic.from_workload(w, precision=pic.FP32_CELLOFF, sort_interval=args.sort_interval,
-                                  stream=stream.cuda_stream, load=False)
+                                  stream=stream.cuda_stream, load=False, push_variant=args.push_variant)
         torch.cuda.synchronize()
         t0 = time.perf_counter()
         sim_e.pic_restore(ckpt)

@@ -136,8 +136,11 @@ typedef struct {
 
 /* Push kernels: AUTO uses the tiled shared-memory kernel wherever it exists
  * (2D grids, FP32 form, 8x8 or 16x16 tiles, particles sorted at least once)
- * and the simple kernel elsewhere; SIMPLE always uses the simple kernel. */
-enum { PIC_PUSH_AUTO = 0, PIC_PUSH_SIMPLE = 1, PIC_PUSH_MLP_TC = 2 };
+ * and the simple kernel elsewhere; SIMPLE always uses the simple kernel;
+ * TILE_AGG is AUTO with the 2D tiled kernel's warp-aggregated deposit (the
+ * lanes of a warp on consecutive, cell-sorted particles; lanes sharing a
+ * deposit window summed by warp reductions before one atomic per value). */
+enum { PIC_PUSH_AUTO = 0, PIC_PUSH_SIMPLE = 1, PIC_PUSH_MLP_TC = 2, PIC_PUSH_TILE_AGG = 3 };
 enum { PIC_PUSHER_BORIS = 0, PIC_PUSHER_VAY = 1 };
 
 /* Laser entering through the x-min face (requires bc[0] == PIC_BC_ABSORB):
@@ -191,11 +194,23 @@ typedef struct {
  * process without a network uses its tables. */
 enum { PIC_QED_OFF = 0, PIC_QED_TABLE = 1, PIC_QED_SURROGATE = 2 };
 enum { PIC_QED_EMISSION = 0, PIC_QED_PAIR = 1 };
+/* Sampling method (Sec. IV): METHOD1 (0 also) is Method I in the optical-
+ * depth form above.  METHOD2 is Method II: every step an emitter draws
+ * r1, r2 and emits u0 = r1^3 when r2 < 3 r1^2 (dW_rad/du)(u0) dt; a photon
+ * converts with v0 = r1 when r2 < (dW_pair/dv)(v0) dt (the pair spectrum is
+ * bounded, so v0 is drawn uniform -- the paper applies the methods to pairs
+ * "in the similar way"); no optical depth and no tables of the total rates
+ * or inverse CDFs: the differential rates of Eqs. (23)/(24) are evaluated
+ * from tables of K_{2/3} and Int K_{1/3}, so chi is not limited to the
+ * tables' range.  An acceptance probability above one makes pic_step
+ * return PIC_ERR_CFL (dt too long for the method).  Not with SURROGATE. */
+enum { PIC_QED_METHOD1 = 1, PIC_QED_METHOD2 = 2 };
 typedef struct {
     int mode;
     int photon_sp, electron_sp, positron_sp; /* -1 = none */
     double lambda_r_m;
     double photon_emin;
+    int method; /* PIC_QED_METHOD1 (or 0) or PIC_QED_METHOD2 */
 } pic_qed;
 
 /* Configure the QED Monte Carlo (builds the rate and inverse-CDF tables on

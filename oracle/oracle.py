@@ -83,6 +83,10 @@ def lib():
         L.or_set_qed.argtypes = [P, I, I, I, D, D, C.c_uint64]
         L.or_Es.argtypes = [P]
         L.or_Es.restype = D
+        L.or_set_qed_method.argtypes = [P, I]
+        L.or_set_qed_method.restype = I
+        L.or_method2_over.argtypes = [P]
+        L.or_method2_over.restype = LG
         L.or_chi.argtypes = [P, D, P, P]
         L.or_chi.restype = D
         L.or_photon_lost.argtypes = [P]
@@ -215,6 +219,15 @@ class OracleSim:
     def set_qed(self, photon_sp=-1, electron_sp=-1, positron_sp=-1, lambda_r_m=1e-6, photon_emin=0.0, seed=0):
         lib().or_set_qed(self._h, int(photon_sp), int(electron_sp), int(positron_sp), float(lambda_r_m),
                          float(photon_emin), C.c_uint64(int(seed) & 0xFFFFFFFFFFFFFFFF))
+
+    def set_qed_method(self, method):
+        """1: Method I (optical depth, default), 2: Method II"""
+        if lib().or_set_qed_method(self._h, int(method)):
+            raise ValueError("oracle: QED method must be 1 or 2")
+
+    def method2_over(self):
+        """Method II draws whose acceptance probability exceeded one"""
+        return lib().or_method2_over(self._h)
 
     @property
     def Es(self):

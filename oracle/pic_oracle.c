@@ -105,6 +105,8 @@ struct osim {
     int qed_on, photon_sp, electron_sp, positron_sp;
     double Es, emin, e_lost;
     uint32_t key[2];
+    int qed_method;     /* 1: Method I in the optical-depth form (default); 2: Method II */
+    long m2_over;       /* Method II draws whose acceptance probability exceeded one */
     oevent *ev[OR_MAX_SPECIES];
     long nev[OR_MAX_SPECIES], evcap[OR_MAX_SPECIES];
 };
@@ -239,6 +241,16 @@ void or_set_qed(osim *s, int photon_sp, int electron_sp, int positron_sp, double
 }
 
 double or_Es(const osim *s) { return s->Es; }
+
+/* QED sampling method: 1 (Method I, optical depth; default) or 2 (Method II) */
+int or_set_qed_method(osim *s, int method)
+{
+    if (method != 1 && method != 2) return -1;
+    s->qed_method = method;
+    return 0;
+}
+
+long or_method2_over(const osim *s) { return s->m2_over; }
 
 int or_load(osim *s, int isp, long n, const double *x, const double *y, const double *z,
             const double *ux, const double *uy, const double *uz)
@@ -766,9 +778,11 @@ static void half_drift(const osim *s, double *x, const double *u, double sign)
     for (int d = 0; d < s->dim; d++) x[d] += sign * 0.5 * s->dt * u[d] / g;
 }
 
+/* sort key: the tile of the particle's cell, then the cell within the tile
+ * (row-major, x fastest): key = tile * (cells per tile) + local cell */
 static long tile_key(const osim *s, const double *x)
 {
-    long key = 0, stride = 1;
+    long tile = 0, stride = 1, local = 0, lstride = 1;
     for (int d = 0; d < 3; d++) {
         long c = 0;
         if (d < s->dim) {
@@ -777,11 +791,15 @@ static long tile_key(const osim *s, const double *x)
             if (c > s->n[d] - 1) c = s->n[d] - 1;
         }
         long nt = (s->n[d] + s->tile[d] - 1) / s->tile[d];
-        key += (c / s->tile[d]) * stride;
+        tile += (c / s->tile[d]) * stride;
         stride *= nt;
+        local += (c % s->tile[d]) * lstride;
+        lstride *= s->tile[d];
     }
-    return key;
+    return tile * lstride + local;
 }
+
+static long cells_per_tile(const osim *s) { return (long)s->tile[0] * s->tile[1] * s->tile[2]; }
 
 static long ntiles(const osim *s)
 {
@@ -790,11 +808,12 @@ static long ntiles(const osim *s)
     return t;
 }
 
-/* stable counting sort of one species by tile key; dead particles get the
- * key ntiles, sort last and are dropped */
+/* stable counting sort of one species by tile key (tile, then cell within
+ * the tile); dead particles get the key past the last one, sort last and are
+ * dropped */
 static void sort_species(osim *s, osp *p, long *perm_out)
 {
-    long nt = ntiles(s);
+    long nt = ntiles(s) * cells_per_tile(s);
     long *cnt = (long *)calloc((size_t)nt + 2, sizeof(long));
     long *key = (long *)malloc((size_t)p->n * sizeof(long) + 8);
     for (long a = 0; a < p->n; a++) {
@@ -884,14 +903,31 @@ static void push_species(osim *s, osp *p)
         if (mc) {
             /* optical depth form of Method I: tau -= W_rad dt; at tau <= 0
              * emit u gamma along u (u from the inverse CDF of Eq. (23)),
-             * recoil to gamma (1-u), restart tau from -ln r */
+             * recoil to gamma (1-u), restart tau from -ln r.
+             * Method II: every step u0 = r1^3 is emitted when
+             * r2 < 3 r1^2 dW_rad/du(u0) dt (no optical depth) */
             double gam = gamma_of(u);
             double chi = chi_of(s, gam, u, eb);
-            p->tau[a] -= qed_pref(s) * or_qed_Grad(chi) / gam;
-            if (p->tau[a] <= 0.0) {
-                uint32_t c[4] = {(uint32_t)p->id[a], (uint32_t)(p->id[a] >> 32), (uint32_t)s->step, 0u}, w[4];
+            int event = 0;
+            double frac = 0.0;
+            uint32_t c[4] = {(uint32_t)p->id[a], (uint32_t)(p->id[a] >> 32), (uint32_t)s->step, 0u}, w[4];
+            if (s->qed_method == 2) {
                 or_philox4x32_10(c, s->key, w);
-                double frac = or_qed_sample_rad(chi, or_uniform24(w[0]));
+                double r1 = or_uniform24(w[0]), r2 = or_uniform24(w[1]);
+                double u0 = r1 * r1 * r1;
+                double pacc = 3.0 * r1 * r1 * qed_pref(s) * or_qed_Frad(u0, chi) / gam;
+                if (pacc > 1.0) s->m2_over++;
+                if (r2 < pacc) { event = 1; frac = u0; }
+            } else {
+                p->tau[a] -= qed_pref(s) * or_qed_Grad(chi) / gam;
+                if (p->tau[a] <= 0.0) {
+                    or_philox4x32_10(c, s->key, w);
+                    frac = or_qed_sample_rad(chi, or_uniform24(w[0]));
+                    p->tau[a] = -log(or_uniform24(w[1]));
+                    event = 1;
+                }
+            }
+            if (event) {
                 double eg = frac * gam, um = sqrt(u[0] * u[0] + u[1] * u[1] + u[2] * u[2]);
                 double g1 = gam * (1.0 - frac);
                 if (g1 < 1.0) g1 = 1.0;
@@ -900,7 +936,6 @@ static void push_species(osim *s, osp *p)
                     kph[d] = um > 0.0 ? eg * u[d] / um : 0.0;
                     u[d] *= sc;
                 }
-                p->tau[a] = -log(or_uniform24(w[1]));
                 if (eg >= s->emin) emitted = 1;
                 else s->e_lost += eg * p->w * dV;
             }
@@ -953,13 +988,24 @@ static void push_photons(osim *s, osp *p)
             double eb[6];
             or_gather(s, xh, eb);
             double chi = chi_of(s, km, k, eb);
-            p->tau[a] -= qed_pref(s) * or_qed_Gpair(chi) / km;
-            if (p->tau[a] <= 0.0) {
-                uint32_t c[4] = {(uint32_t)p->id[a], (uint32_t)(p->id[a] >> 32), (uint32_t)s->step, 1u}, w[4];
+            uint32_t c[4] = {(uint32_t)p->id[a], (uint32_t)(p->id[a] >> 32), (uint32_t)s->step, 1u}, w[4];
+            if (s->qed_method == 2) {
+                /* Method II for pairs (the paper: "in the similar way"): the
+                 * pair spectrum of Eq. (24) is bounded, so v0 = r1 is taken
+                 * uniform and accepted when r2 < dW_pair/dv(v0) dt */
                 or_philox4x32_10(c, s->key, w);
-                frac = or_qed_sample_pair(chi, or_uniform24(w[0]));
-                p->tau[a] = -log(or_uniform24(w[1]));
-                conv = 1;
+                double r1 = or_uniform24(w[0]), r2 = or_uniform24(w[1]);
+                double pacc = qed_pref(s) * or_qed_Fpair(r1, chi) / km;
+                if (pacc > 1.0) s->m2_over++;
+                if (r2 < pacc) { frac = r1; conv = 1; }
+            } else {
+                p->tau[a] -= qed_pref(s) * or_qed_Gpair(chi) / km;
+                if (p->tau[a] <= 0.0) {
+                    or_philox4x32_10(c, s->key, w);
+                    frac = or_qed_sample_pair(chi, or_uniform24(w[0]));
+                    p->tau[a] = -log(or_uniform24(w[1]));
+                    conv = 1;
+                }
             }
         }
         double x1[3] = {xh[0], xh[1], xh[2]};

@@ -19,6 +19,8 @@ int or_add_species2(osim *s, double q, double m, double w, long cap, int kind, i
 void or_set_qed(osim *s, int photon_sp, int electron_sp, int positron_sp, double lambda_r_m, double emin,
                 uint64_t seed);
 double or_Es(const osim *s);
+int or_set_qed_method(osim *s, int method);
+long or_method2_over(const osim *s);
 double or_chi(const osim *s, double g, const double *u, const double *eb);
 double or_photon_lost(const osim *s);
 long or_get_qed_state(const osim *s, int isp, uint64_t *id, double *tau);

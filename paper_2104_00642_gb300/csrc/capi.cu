@@ -306,6 +306,7 @@ QedParams qed_params(pic_sim *s, int i)
     const double alpha = 1.0 / 137.035999084;
     q.on = s->qed_on && (p.kind == PIC_KIND_PHOTON ? (s->qed.electron_sp >= 0 && s->qed.positron_sp >= 0)
                                                    : (p.qed && s->qed.photon_sp >= 0));
+    q.method = s->qed.method == PIC_QED_METHOD2 ? 2 : 1;
     q.pref = alpha * s->Es * s->g.dt / (std::sqrt(3.0) * 3.14159265358979323846);
     q.inv_Es = s->Es > 0.0 ? 1.0 / s->Es : 0.0;
     q.emin = s->qed.photon_emin;
@@ -348,7 +349,7 @@ void push_species(pic_sim *s, int i, float *F)
                                s->d_eabs, p.defer + 1, p.defer, s->st);
         else
             launch_push_tile2d(view32(s, i, p.cur), p.items, p.nitems, max_items, F, s->g, push_const(s, p), s->d_err,
-                               s->d_eabs, s->st);
+                               s->d_eabs, s->st, s->push_variant == PIC_PUSH_TILE_AGG);
     } else
         launch_push_f32(view32(s, i, p.cur), F, s->g, push_const(s, p), s->d_err, s->d_eabs, s->st);
 }
@@ -488,6 +489,8 @@ int check_flags(pic_sim *s)
         CK(cudaMemsetAsync(s->d_err, 0, sizeof(int), s->st));
         if (h & ERR_NONFINITE) return fail(s, PIC_ERR_NONFINITE, "non-finite particle momentum");
         if (h & ERR_CFL) return fail(s, PIC_ERR_CFL, "a particle moved more than one cell in a step");
+        if (h & ERR_QEDDT)
+            return fail(s, PIC_ERR_CFL, "QED Method II: an acceptance probability above one (dt too long for it)");
         if (h & ERR_CAPACITY) return fail(s, PIC_ERR_CAPACITY, "species capacity exceeded");
         if (h & ERR_TIMEOUT)
             return fail(s, PIC_ERR_TIMEOUT, "a bounded wait in a kernel ran out (bulk copy or tensor-core commit)");
@@ -525,7 +528,7 @@ int pic_create(const pic_grid *grid, double dt, const pic_species *species, int 
     int prec = opt ? opt->precision : PIC_PREC_FP32_CELLOFF;
     if (prec != PIC_PREC_FP32_CELLOFF && prec != PIC_PREC_FP64_PLAIN)
         return fail(s, PIC_ERR_ARG, "pic_create: unknown precision");
-    if (opt && (opt->push_variant < PIC_PUSH_AUTO || opt->push_variant > PIC_PUSH_MLP_TC))
+    if (opt && (opt->push_variant < PIC_PUSH_AUTO || opt->push_variant > PIC_PUSH_TILE_AGG))
         return fail(s, PIC_ERR_ARG, "pic_create: unknown push variant");
     if (opt && opt->pusher != PIC_PUSHER_BORIS && opt->pusher != PIC_PUSHER_VAY)
         return fail(s, PIC_ERR_ARG, "pic_create: unknown pusher");
@@ -779,6 +782,10 @@ int pic_set_qed(pic_sim *s, const pic_qed *Q)
         return fail(s, PIC_ERR_ARG, "pic_set_qed: bad mode");
     if (Q->mode != PIC_QED_OFF && s->g.order != 2)
         return fail(s, PIC_ERR_ARG, "pic_set_qed: the QED push kernels use the order-2 shape");
+    if (Q->method != 0 && Q->method != PIC_QED_METHOD1 && Q->method != PIC_QED_METHOD2)
+        return fail(s, PIC_ERR_ARG, "pic_set_qed: method must be PIC_QED_METHOD1 or PIC_QED_METHOD2");
+    if (Q->method == PIC_QED_METHOD2 && Q->mode == PIC_QED_SURROGATE)
+        return fail(s, PIC_ERR_ARG, "pic_set_qed: the surrogate replaces Method I's rate and inverse CDF");
     auto kind_ok = [&](int i, int kind) { return i == -1 || (i >= 0 && i < s->nsp && s->sp[i].kind == kind); };
     if (!kind_ok(Q->photon_sp, PIC_KIND_PHOTON) || !kind_ok(Q->electron_sp, PIC_KIND_MASSIVE) ||
         !kind_ok(Q->positron_sp, PIC_KIND_MASSIVE) || !(Q->lambda_r_m > 0.0) || Q->photon_emin < 0.0)

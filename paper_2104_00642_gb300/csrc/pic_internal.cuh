@@ -27,7 +27,9 @@ enum Comp { EX = 0, EY, EZ, BX, BY, BZ, JX, JY, JZ, NCOMP };
 enum Bc { PERIODIC = 0, ABSORB = 1 };
 
 // device error flags (bit mask, read by the host once per pic_step)
-enum ErrFlag : int { ERR_CFL = 1, ERR_NONFINITE = 2, ERR_CAPACITY = 4, ERR_TIMEOUT = 8 };
+// (ERR_QEDDT: a Method II acceptance probability above one -- the step is too
+// long for that sampler)
+enum ErrFlag : int { ERR_CFL = 1, ERR_NONFINITE = 2, ERR_CAPACITY = 4, ERR_TIMEOUT = 8, ERR_QEDDT = 16 };
 
 struct Grid {
     int dim;

@@ -99,15 +99,33 @@ __global__ void __launch_bounds__(256, SURR ? 2 : 1) k_push_qed_f32(PartF32 P, f
                 return;
             }
         }
-        const float G = use_net ? mlp_rate_f32(q.nrm, QED_RAD, chi, y1) : qed_rate_f32(q.T, QED_RAD, chi);
-        double tau = q.tau[p] - (double)((float)q.pref * G / (float)gam);
-        if (tau <= 0.0) {
-            if (!use_net) {
-                const uint64_t id = q.id[p];
-                philox4x32_10((uint32_t)id, (uint32_t)(id >> 32), q.step, QP_EMIT, q.key[0], q.key[1], w);
+        bool emit = false;
+        double frac = 0.0, tau = 0.0;
+        if (!SURR && q.method == 2) {
+            // Method II: u0 = r1^3 emitted when r2 < 3 r1^2 dW/du(u0) dt
+            const uint64_t id = q.id[p];
+            philox4x32_10((uint32_t)id, (uint32_t)(id >> 32), q.step, QP_EMIT, q.key[0], q.key[1], w);
+            const double r1 = uniform24(w[0]), r2 = uniform24(w[1]);
+            const double u0 = r1 * r1 * r1;
+            const double pacc = 3.0 * r1 * r1 * q.pref * qed_spec_rad(q.T, u0, (double)chi) / gam;
+            if (pacc > 1.0) atomicOr(err, ERR_QEDDT);
+            emit = r2 < pacc;
+            frac = u0;
+        } else {
+            const float G = use_net ? mlp_rate_f32(q.nrm, QED_RAD, chi, y1) : qed_rate_f32(q.T, QED_RAD, chi);
+            tau = q.tau[p] - (double)((float)q.pref * G / (float)gam);
+            if (tau <= 0.0) {
+                if (!use_net) {
+                    const uint64_t id = q.id[p];
+                    philox4x32_10((uint32_t)id, (uint32_t)(id >> 32), q.step, QP_EMIT, q.key[0], q.key[1], w);
+                }
+                const double r0 = uniform24(w[0]);
+                frac = use_net ? mlp_fraction(QED_RAD, y0, r0) : qed_sample<float>(q.T, QED_RAD, chi, r0);
+                tau = -log(uniform24(w[1]));
+                emit = true;
             }
-            const double r0 = uniform24(w[0]);
-            const double frac = use_net ? mlp_fraction(QED_RAD, y0, r0) : qed_sample<float>(q.T, QED_RAD, chi, r0);
+        }
+        if (emit) {
             const double eg = frac * gam;
             const double umag = sqrt(uu);
             const double g1 = fmax(gam * (1.0 - frac), 1.0);
@@ -117,7 +135,6 @@ __global__ void __launch_bounds__(256, SURR ? 2 : 1) k_push_qed_f32(PartF32 P, f
             ux = (float)(ux * s);
             uy = (float)(uy * s);
             uz = (float)(uz * s);
-            tau = -log(uniform24(w[1]));
             if (eg >= q.emin) {
                 event = 1;
                 evd = make_float4((float)kx, (float)ky, (float)kz, 0.f);
@@ -125,7 +142,7 @@ __global__ void __launch_bounds__(256, SURR ? 2 : 1) k_push_qed_f32(PartF32 P, f
                 atomicAdd(q.e_lost, eg * q.wdV);
             }
         }
-        q.tau[p] = tau;
+        if (SURR || q.method != 2) q.tau[p] = tau;
     } else if (SURR && !live) {
         if (p <= P.n) q.ev[p] = 0;
         return;
@@ -262,20 +279,36 @@ __global__ void __launch_bounds__(256, SURR ? 2 : 1) k_push_photon_f32(PartF32 P
                 return;
             }
         }
-        const float G = use_net ? mlp_rate_f32(q.nrm, QED_PAIR, chi, y1) : qed_rate_f32(q.T, QED_PAIR, chi);
-        double tau = q.tau[p] - (km > 0.f ? (double)((float)q.pref * G / km) : 0.0);
-        if (tau <= 0.0) {
-            if (!use_net) {
+        if (!SURR && q.method == 2) {
+            // Method II for pairs: v0 = r1 accepted when r2 < dW_pair/dv(v0) dt
+            if (km > 0.f) {
                 const uint64_t id = q.id[p];
                 philox4x32_10((uint32_t)id, (uint32_t)(id >> 32), q.step, QP_PAIR, q.key[0], q.key[1], w);
+                const double r1 = uniform24(w[0]), r2 = uniform24(w[1]);
+                const double pacc = q.pref * qed_spec_pair(q.T, r1, (double)chi) / (double)km;
+                if (pacc > 1.0) atomicOr(err, ERR_QEDDT);
+                if (r2 < pacc) {
+                    event = 1;
+                    evd = make_float4(kx, ky, kz, (float)r1);
+                }
             }
-            const double r0 = uniform24(w[0]);
-            const double vf = use_net ? mlp_fraction(QED_PAIR, y0, r0) : qed_sample<float>(q.T, QED_PAIR, chi, r0);
-            event = 1;
-            evd = make_float4(kx, ky, kz, (float)vf);
-            tau = -log(uniform24(w[1]));
+        } else {
+            const float G = use_net ? mlp_rate_f32(q.nrm, QED_PAIR, chi, y1) : qed_rate_f32(q.T, QED_PAIR, chi);
+            double tau = q.tau[p] - (km > 0.f ? (double)((float)q.pref * G / km) : 0.0);
+            if (tau <= 0.0) {
+                if (!use_net) {
+                    const uint64_t id = q.id[p];
+                    philox4x32_10((uint32_t)id, (uint32_t)(id >> 32), q.step, QP_PAIR, q.key[0], q.key[1], w);
+                }
+                const double r0 = uniform24(w[0]);
+                const double vf =
+                    use_net ? mlp_fraction(QED_PAIR, y0, r0) : qed_sample<float>(q.T, QED_PAIR, chi, r0);
+                event = 1;
+                evd = make_float4(kx, ky, kz, (float)vf);
+                tau = -log(uniform24(w[1]));
+            }
+            q.tau[p] = tau;
         }
-        q.tau[p] = tau;
     } else if (SURR && !live) {
         if (p <= P.n) q.ev[p] = 0;
         return;
@@ -452,12 +485,29 @@ __global__ void __launch_bounds__(256) k_push_qed_f64(PartF64 P, double *__restr
         const double uu = ux * ux + uy * uy + uz * uz;
         const double gam = sqrt(1.0 + uu);
         const double chi = chi_of<double>(gam, ux, uy, uz, eb[0], eb[1], eb[2], eb[3], eb[4], eb[5], q.inv_Es);
-        double tau = q.tau[p] - q.pref * qed_rate<double>(q.T, QED_RAD, chi) / gam;
-        if (tau <= 0.0) {
-            uint32_t w[4];
-            const uint64_t id = q.id[p];
+        bool emit = false;
+        double frac = 0.0, tau = 0.0;
+        uint32_t w[4];
+        const uint64_t id = q.id[p];
+        if (q.method == 2) {
+            // Method II: u0 = r1^3 emitted when r2 < 3 r1^2 dW/du(u0) dt
             philox4x32_10((uint32_t)id, (uint32_t)(id >> 32), q.step, QP_EMIT, q.key[0], q.key[1], w);
-            const double frac = qed_sample<double>(q.T, QED_RAD, chi, uniform24(w[0]));
+            const double r1 = uniform24(w[0]), r2 = uniform24(w[1]);
+            const double u0 = r1 * r1 * r1;
+            const double pacc = 3.0 * r1 * r1 * q.pref * qed_spec_rad(q.T, u0, chi) / gam;
+            if (pacc > 1.0) atomicOr(err, ERR_QEDDT);
+            emit = r2 < pacc;
+            frac = u0;
+        } else {
+            tau = q.tau[p] - q.pref * qed_rate<double>(q.T, QED_RAD, chi) / gam;
+            if (tau <= 0.0) {
+                philox4x32_10((uint32_t)id, (uint32_t)(id >> 32), q.step, QP_EMIT, q.key[0], q.key[1], w);
+                frac = qed_sample<double>(q.T, QED_RAD, chi, uniform24(w[0]));
+                tau = -log(uniform24(w[1]));
+                emit = true;
+            }
+        }
+        if (emit) {
             const double eg = frac * gam, umag = sqrt(uu);
             const double g1 = fmax(gam * (1.0 - frac), 1.0);
             const double s = umag > 0.0 ? sqrt(g1 * g1 - 1.0) / umag : 0.0;
@@ -466,7 +516,6 @@ __global__ void __launch_bounds__(256) k_push_qed_f64(PartF64 P, double *__restr
             ux *= s;
             uy *= s;
             uz *= s;
-            tau = -log(uniform24(w[1]));
             if (eg >= q.emin) {
                 event = 1;
                 evd = make_double4(kx, ky, kz, 0.0);
@@ -474,7 +523,7 @@ __global__ void __launch_bounds__(256) k_push_qed_f64(PartF64 P, double *__restr
                 atomicAdd(q.e_lost, eg * q.wdV);
             }
         }
-        q.tau[p] = tau;
+        if (q.method != 2) q.tau[p] = tau;
     }
     const double ig1 = inv_gamma(ux, uy, uz);
     u[0] = ux;
@@ -570,16 +619,32 @@ __global__ void __launch_bounds__(256) k_push_photon_f64(PartF64 P, const double
         double eb[6];
         gather<double, DIM>(F, g, icn, wn, ich, wh, eb);
         const double chi = chi_of<double>(km, kx, ky, kz, eb[0], eb[1], eb[2], eb[3], eb[4], eb[5], q.inv_Es);
-        double tau = q.tau[p] - (km > 0.0 ? q.pref * qed_rate<double>(q.T, QED_PAIR, chi) / km : 0.0);
-        if (tau <= 0.0) {
-            uint32_t w[4];
-            const uint64_t id = q.id[p];
-            philox4x32_10((uint32_t)id, (uint32_t)(id >> 32), q.step, QP_PAIR, q.key[0], q.key[1], w);
-            event = 1;
-            evd = make_double4(kx, ky, kz, qed_sample<double>(q.T, QED_PAIR, chi, uniform24(w[0])));
-            tau = -log(uniform24(w[1]));
+        if (q.method == 2) {
+            // Method II for pairs: v0 = r1 accepted when r2 < dW_pair/dv(v0) dt
+            if (km > 0.0) {
+                uint32_t w[4];
+                const uint64_t id = q.id[p];
+                philox4x32_10((uint32_t)id, (uint32_t)(id >> 32), q.step, QP_PAIR, q.key[0], q.key[1], w);
+                const double r1 = uniform24(w[0]), r2 = uniform24(w[1]);
+                const double pacc = q.pref * qed_spec_pair(q.T, r1, chi) / km;
+                if (pacc > 1.0) atomicOr(err, ERR_QEDDT);
+                if (r2 < pacc) {
+                    event = 1;
+                    evd = make_double4(kx, ky, kz, r1);
+                }
+            }
+        } else {
+            double tau = q.tau[p] - (km > 0.0 ? q.pref * qed_rate<double>(q.T, QED_PAIR, chi) / km : 0.0);
+            if (tau <= 0.0) {
+                uint32_t w[4];
+                const uint64_t id = q.id[p];
+                philox4x32_10((uint32_t)id, (uint32_t)(id >> 32), q.step, QP_PAIR, q.key[0], q.key[1], w);
+                event = 1;
+                evd = make_double4(kx, ky, kz, qed_sample<double>(q.T, QED_PAIR, chi, uniform24(w[0])));
+                tau = -log(uniform24(w[1]));
+            }
+            q.tau[p] = tau;
         }
-        q.tau[p] = tau;
     }
 #pragma unroll
     for (int d = 0; d < DIM; d++) x[d] += pc.hdt * v[d];

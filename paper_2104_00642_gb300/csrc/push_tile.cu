@@ -109,10 +109,35 @@ struct AccGlobal {
     }
 };
 
+// warp-aggregated current into the shared box: the lanes of grp share the
+// window origin; each value is summed over the group with one warp
+// reduction and added by the group's first lane with one shared atomic
+// (in the fixed-point units of AccShared; a group sum of at most 32
+// particles stays far inside int32)
+struct AccWarp {
+    int *base;
+    int cs, rs;
+    float scale;
+    unsigned grp;
+    bool lead;
+    __device__ __forceinline__ void add(int c, int a, int b, float v)
+    {
+        const int s = __reduce_add_sync(grp, __float2int_rn(v * scale));
+        if (lead && s) atomicAdd(base + c * cs + b * rs + a, s);
+    }
+};
+
 // With use_tma the field box of an item is one TMA tile copy (tmap: the six
 // field components as a 3D tensor, x fastest), issued by one thread and
 // overlapping the zeroing of the current box and the particle staging.
-template <int T>
+//
+// AGG (warp-aggregated deposit): the 32 lanes of a warp take 32 consecutive
+// particles of the item (the sort orders a tile's particles by cell, so they
+// share cells: their gathers read the same nodes -- shared-memory broadcasts --
+// and lanes with the same deposit window are summed before one atomic per
+// value).  Without AGG lane l walks the l-th of 32 contiguous segments, so
+// the lanes of an atomic hit different cells.
+template <int T, bool AGG>
 __global__ void __launch_bounds__(kTileThreads, kTileMinBlocks)
     k_push_tile2d(PartF32 P, const TileItem *__restrict__ items, const uint32_t *__restrict__ nitems,
                   float *__restrict__ F, Grid g, PushConst pc, int *err, double *e_abs,
@@ -176,7 +201,7 @@ __global__ void __launch_bounds__(kTileThreads, kTileMinBlocks)
         // (asynchronous 4-byte copies: no register round trip)
         for (int i = threadIdx.x; i < m.count; i += blockDim.x) {
             const int l = i / S, j = i - l * S;
-            const int pos = j * 33 + l;
+            const int pos = AGG ? i : j * 33 + l;
             const int p = m.start + i;  // capacities are below 2^31
             cp_async4(sPc + pos, P.cell + p);
             cp_async4(sP + 0 * kPSlot + pos, P.off[0] + p);
@@ -199,75 +224,102 @@ __global__ void __launch_bounds__(kTileThreads, kTileMinBlocks)
         }
         // 3. particles
         const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-        for (int j = warp; j < S; j += kTileThreads / 32) {
-            const int li = lane * S + j;
-            if (li >= m.count) continue;
-            const int pos = j * 33 + lane;
-            const uint32_t cp = sPc[pos];
-            if (cp == kDead) continue;
-            int c[2];
-            int dummy;
-            unpack_cell(g, cp, c[0], c[1], dummy);
-            float o[2] = {sP[pos], sP[kPSlot + pos]};
-            float ux = sP[2 * kPSlot + pos], uy = sP[3 * kPSlot + pos], uz = sP[4 * kPSlot + pos];
-            float ig = inv_gamma_fast(ux, uy, uz);
-            drift_f32(c[0], o[0], hdx0 * ux * ig);
-            drift_f32(c[1], o[1], hdx1 * uy * ig);
-            const int ch[2] = {c[0], c[1]};
-            const float oh[2] = {o[0], o[1]};
-            int icn[2], ich[2];
-            float wn[2][3], wh[2][3];
-            axis_w_f32(c[0], o[0], icn[0], wn[0], ich[0], wh[0]);
-            axis_w_f32(c[1], o[1], icn[1], wn[1], ich[1], wh[1]);
-            float eb[6];
-            const bool gin = ch[0] - 1 >= bx0 && ch[0] + 2 < bx0 + B::WX && ch[1] - 1 >= by0 && ch[1] + 2 < by0 + B::WY;
-            if (gin) gather2d(sF, B::N, B::WX, bx0, by0, icn, wn, ich, wh, eb);
-            else gather2d(Fg, V, rs, 0, 0, icn, wn, ich, wh, eb);
-            if (pc.pusher) vay<float>(ux, uy, uz, k * eb[0], k * eb[1], k * eb[2], k * eb[3], k * eb[4], k * eb[5]);
-            else boris_fast(ux, uy, uz, k * eb[0], k * eb[1], k * eb[2], k * eb[3], k * eb[4], k * eb[5]);
-            const float ig1 = inv_gamma_fast(ux, uy, uz);
-            const float d0 = hdx0 * ux * ig1, d1 = hdx1 * uy * ig1;
-            drift_f32(c[0], o[0], d0);
-            drift_f32(c[1], o[1], d1);
-            const int c1[2] = {c[0], c[1]};
-            const float o1[2] = {o[0], o[1]};
-            drift_f32(c[0], o[0], d0);
-            drift_f32(c[1], o[1], d1);
-            // Esirkepov on x^{n+1/2} -> x^{n+3/2}
+        constexpr int kWarps = kTileThreads / 32;
+        // passes of the warp over the item: warp-uniform, so the lanes stay
+        // together for the warp-collective deposit of AGG
+        const int npass = AGG ? (m.count + kTileThreads - 1) / kTileThreads : (S + kWarps - 1) / kWarps;
+        for (int pass = 0; pass < npass; pass++) {
+            int li, pos;
+            if (AGG) {
+                li = pass * kTileThreads + warp * 32 + lane;
+                pos = li;
+            } else {
+                const int j = pass * kWarps + warp;
+                li = j < S ? lane * S + j : m.count;
+                pos = j * 33 + lane;
+            }
+            const uint32_t cp = li < m.count ? sPc[pos] : kDead;
+            bool act = cp != kDead;  // a live particle of this item
+            int c[2] = {0, 0}, c1[2] = {0, 0}, u0[2] = {0, 0};
+            float o1[2] = {0.f, 0.f};
+            float ux = 0.f, uy = 0.f, uz = 0.f, ig1 = 0.f;
             float S0[2][4], dS[2][4];
-            int u0[2];
             bool ok = true;
+            if (act) {
+                int dummy;
+                unpack_cell(g, cp, c[0], c[1], dummy);
+                float o[2] = {sP[pos], sP[kPSlot + pos]};
+                ux = sP[2 * kPSlot + pos];
+                uy = sP[3 * kPSlot + pos];
+                uz = sP[4 * kPSlot + pos];
+                float ig = inv_gamma_fast(ux, uy, uz);
+                drift_f32(c[0], o[0], hdx0 * ux * ig);
+                drift_f32(c[1], o[1], hdx1 * uy * ig);
+                const int ch[2] = {c[0], c[1]};
+                const float oh[2] = {o[0], o[1]};
+                int icn[2], ich[2];
+                float wn[2][3], wh[2][3];
+                axis_w_f32(c[0], o[0], icn[0], wn[0], ich[0], wh[0]);
+                axis_w_f32(c[1], o[1], icn[1], wn[1], ich[1], wh[1]);
+                float eb[6];
+                const bool gin =
+                    ch[0] - 1 >= bx0 && ch[0] + 2 < bx0 + B::WX && ch[1] - 1 >= by0 && ch[1] + 2 < by0 + B::WY;
+                if (gin) gather2d(sF, B::N, B::WX, bx0, by0, icn, wn, ich, wh, eb);
+                else gather2d(Fg, V, rs, 0, 0, icn, wn, ich, wh, eb);
+                if (pc.pusher) vay<float>(ux, uy, uz, k * eb[0], k * eb[1], k * eb[2], k * eb[3], k * eb[4], k * eb[5]);
+                else boris_fast(ux, uy, uz, k * eb[0], k * eb[1], k * eb[2], k * eb[3], k * eb[4], k * eb[5]);
+                ig1 = inv_gamma_fast(ux, uy, uz);
+                const float d0 = hdx0 * ux * ig1, d1 = hdx1 * uy * ig1;
+                drift_f32(c[0], o[0], d0);
+                drift_f32(c[1], o[1], d1);
+                c1[0] = c[0];
+                c1[1] = c[1];
+                o1[0] = o[0];
+                o1[1] = o[1];
+                drift_f32(c[0], o[0], d0);
+                drift_f32(c[1], o[1], d1);
+                // Esirkepov on x^{n+1/2} -> x^{n+3/2}
 #pragma unroll
-            for (int d = 0; d < 2; d++) {
-                int i0, i1;
-                float w0[3], w1[3];
-                axis_wn_f32(ch[d], oh[d], i0, w0);
-                axis_wn_f32(c[d], o[d], i1, w1);
-                ok &= (i1 - i0 >= -1 && i1 - i0 <= 1);
-                u0[d] = union4(i0, w0, i1, w1, S0[d], dS[d]);
-            }
-            // a non-finite momentum (a NaN or infinite field) is reported and the particle
-            // removed before anything uses its position: NaN positions would give no valid
-            // cell or node index to the gather, the deposit or the diagnostics (and would
-            // otherwise be reported as a Courant violation)
-            if (!isfinite(ux + uy + uz)) {
-                atomicOr(err, ERR_NONFINITE);
-                sPc[pos] = kDead;
-                continue;
-            }
-            if (!ok) {
-                atomicOr(err, ERR_CFL);
-                continue;
+                for (int d = 0; d < 2; d++) {
+                    int i0, i1;
+                    float w0[3], w1[3];
+                    axis_wn_f32(ch[d], oh[d], i0, w0);
+                    axis_wn_f32(c[d], o[d], i1, w1);
+                    ok &= (i1 - i0 >= -1 && i1 - i0 <= 1);
+                    u0[d] = union4(i0, w0, i1, w1, S0[d], dS[d]);
+                }
+                // a non-finite momentum (a NaN or infinite field) is reported and the particle
+                // removed before anything uses its position: NaN positions would give no valid
+                // cell or node index to the gather, the deposit or the diagnostics (and would
+                // otherwise be reported as a Courant violation)
+                if (!isfinite(ux + uy + uz)) {
+                    atomicOr(err, ERR_NONFINITE);
+                    sPc[pos] = kDead;
+                    act = false;
+                } else if (!ok) {
+                    atomicOr(err, ERR_CFL);
+                    act = false;  // keeps its staged state
+                }
             }
             const float jvz = qw * uz * ig1;
-            const bool din = u0[0] >= bx0 && u0[0] + 3 < bx0 + B::WX && u0[1] >= by0 && u0[1] + 3 < by0 + B::WY;
-            if (din) {
-                AccShared acc{sJ + (u0[1] - by0) * B::WX + (u0[0] - bx0), B::N, B::WX, jscale};
-                esirkepov2d(S0, dS, cjx, cjy, jvz, acc);
-            } else {
+            const bool din = act && u0[0] >= bx0 && u0[0] + 3 < bx0 + B::WX && u0[1] >= by0 && u0[1] + 3 < by0 + B::WY;
+            if (act && !din) {
                 AccGlobal acc{Fg + JX * V + (long long)u0[1] * rs + u0[0], V, rs};
                 esirkepov2d(S0, dS, cjx, cjy, jvz, acc);
             }
+            if (AGG) {
+                const unsigned smask = __ballot_sync(0xffffffffu, din);
+                if (din) {
+                    const int key = (u0[1] - by0) * B::WX + (u0[0] - bx0);
+                    const unsigned grp = __match_any_sync(smask, key);
+                    AccWarp acc{sJ + key, B::N, B::WX, jscale, grp, lane == __ffs(grp) - 1};
+                    esirkepov2d(S0, dS, cjx, cjy, jvz, acc);
+                }
+            } else if (din) {
+                AccShared acc{sJ + (u0[1] - by0) * B::WX + (u0[0] - bx0), B::N, B::WX, jscale};
+                esirkepov2d(S0, dS, cjx, cjy, jvz, acc);
+            }
+            if (!act) continue;
             // boundaries
             int cc[2] = {c1[0], c1[1]};
             bool dead = false;
@@ -301,7 +353,7 @@ __global__ void __launch_bounds__(kTileThreads, kTileMinBlocks)
         // keep their staged values)
         for (int i = threadIdx.x; i < m.count; i += blockDim.x) {
             const int l = i / S, j = i - l * S;
-            const int pos = j * 33 + l;
+            const int pos = AGG ? i : j * 33 + l;
             const int p = m.start + i;
             P.cell[p] = sPc[pos];
             P.off[0][p] = sP[pos];
@@ -392,14 +444,14 @@ bool tile_push_supported(const Grid &g, int tile_edge)
     return g.dim == 2 && (1 << g.tile_log2[0]) == tile_edge && (1 << g.tile_log2[1]) == tile_edge;
 }
 
-template <int T>
+template <int T, bool AGG>
 static void launch_T(const PartF32 &P, const TileItem *items, const uint32_t *nitems, long long max_items, float *F,
                      const Grid &g, const PushConst &pc, int *err, double *e_abs, cudaStream_t st)
 {
     constexpr int smem = Box2<T>::SMEM + 128;  // + alignment of the TMA destination
     static bool attr = false;
     if (!attr) {
-        cudaFuncSetAttribute(k_push_tile2d<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+        cudaFuncSetAttribute(k_push_tile2d<T, AGG>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
         attr = true;
     }
     static int nsm = 0;
@@ -417,16 +469,23 @@ static void launch_T(const PartF32 &P, const TileItem *items, const uint32_t *ni
     long long grid = std::min<long long>(max_items, (long long)nsm * kTileMinBlocks);  // one resident wave
     if (grid < 1) grid = 1;
     note_launch();
-    k_push_tile2d<T><<<(int)grid, kTileThreads, smem, st>>>(P, items, nitems, F, g, pc, err, e_abs, tmap, tma ? 1 : 0);
+    k_push_tile2d<T, AGG><<<(int)grid, kTileThreads, smem, st>>>(P, items, nitems, F, g, pc, err, e_abs, tmap,
+                                                                tma ? 1 : 0);
 }
 
 void launch_push_tile2d(const PartF32 &P, const TileItem *items, const uint32_t *nitems, long long max_items,
-                        float *F, const Grid &g, const PushConst &pc, int *err, double *e_abs, cudaStream_t st)
+                        float *F, const Grid &g, const PushConst &pc, int *err, double *e_abs, cudaStream_t st,
+                        bool agg)
 {
     if (P.n == 0) return;
     int T = 1 << g.tile_log2[0];
-    if (T == 16) launch_T<16>(P, items, nitems, max_items, F, g, pc, err, e_abs, st);
-    else launch_T<8>(P, items, nitems, max_items, F, g, pc, err, e_abs, st);
+    if (agg) {
+        if (T == 16) launch_T<16, true>(P, items, nitems, max_items, F, g, pc, err, e_abs, st);
+        else launch_T<8, true>(P, items, nitems, max_items, F, g, pc, err, e_abs, st);
+    } else {
+        if (T == 16) launch_T<16, false>(P, items, nitems, max_items, F, g, pc, err, e_abs, st);
+        else launch_T<8, false>(P, items, nitems, max_items, F, g, pc, err, e_abs, st);
+    }
 }
 
 }  // namespace pic

@@ -21,8 +21,10 @@ size_t tile_items_capacity(long long cap, long long ntiles, int dim);
 void build_tile_items(const uint32_t *starts, long long ntiles, int dim, uint32_t *cnt_scratch,
                       uint32_t *scan_scratch, TileItem *items, uint32_t *nitems, cudaStream_t st);
 bool tile_push_supported(const Grid &g, int tile_edge);
+// (agg: the warp-aggregated deposit, lanes on consecutive particles)
 void launch_push_tile2d(const PartF32 &P, const TileItem *items, const uint32_t *nitems, long long max_items,
-                        float *F, const Grid &g, const PushConst &pc, int *err, double *e_abs, cudaStream_t st);
+                        float *F, const Grid &g, const PushConst &pc, int *err, double *e_abs, cudaStream_t st,
+                        bool agg);
 // 3D: tiles of 4^3 cells, every n_d a multiple of 4
 bool tile3d_push_supported(const Grid &g);
 // (defer: a list of capacity >= the particle count, ndefer its device count;

@@ -83,26 +83,28 @@ double cr(const std::vector<double> &L, double x)
             (-0.5 * p0 + 0.5 * p2)) * t + p1;
 }
 
-// K_{2/3}(y) and Int_y^inf K_{1/3}; zero beyond kYmax
-void bessel(double y, double &k23, double &ik13)
+// the host view of the Bessel table in the layout the device reads
+QedTables bessel_view()
 {
     const BesselTable &B = bessel_table();
-    if (y >= kYmax) {
-        k23 = ik13 = 0.0;
-        return;
-    }
-    if (y < kYmin) {
-        // below the table the leading small-argument behaviour is exact to
-        // O(y^{4/3}): K_{2/3} ~ y^{-2/3}, Int_y K_{1/3} = pi/sqrt3 - c y^{2/3}
-        const double k0 = std::exp(B.lnk23[0] - kYmin), i0 = std::exp(B.lnik13[0] - kYmin);
-        const double full = 3.14159265358979323846 / std::sqrt(3.0), r = std::cbrt(y / kYmin);
-        k23 = k0 / (r * r);
-        ik13 = full - (full - i0) * r * r;
-        return;
-    }
-    const double x = (std::log(y) - B.lny0) / B.dlny;
-    k23 = std::exp(cr(B.lnk23, x) - y);
-    ik13 = std::exp(cr(B.lnik13, x) - y);
+    QedTables T{};
+    T.bes_k23 = B.lnk23.data();
+    T.bes_ik13 = B.lnik13.data();
+    T.nbes = kNy;
+    T.bes_lny0 = B.lny0;
+    T.bes_dlny = B.dlny;
+    T.bes_ymin = kYmin;
+    T.bes_ymax = kYmax;
+    return T;
+}
+
+// K_{2/3}(y) and Int_y^inf K_{1/3}: the same evaluation the device makes
+// (qed_bessel: below the table the leading small-argument behaviour, exact
+// to O(y^{4/3}); zero beyond kYmax)
+void bessel(double y, double &k23, double &ik13)
+{
+    static const QedTables T = bessel_view();
+    qed_bessel(T, y, k23, ik13);
 }
 
 // Eq. (23): ((1-u) + 1/(1-u)) K_{2/3}(y) - Int_y^inf K_{1/3}, y = 2u / (3 chi (1-u))
@@ -228,7 +230,10 @@ const HostTables &host_tables()
 
 void qed_spectra(int p, double frac, double chi, double *F) { *F = p == QED_RAD ? spec_rad(frac, chi) : spec_pair(frac, chi); }
 
-size_t qed_table_bytes() { return 2 * ((size_t)kNchi + (size_t)kNchi * kNr) * (sizeof(float) + sizeof(double)); }
+size_t qed_table_bytes()
+{
+    return 2 * ((size_t)kNchi + (size_t)kNchi * kNr) * (sizeof(float) + sizeof(double)) + 2 * (size_t)kNy * 8;
+}
 
 // fill a device buffer (qed_table_bytes) and the table view pointing into it
 int qed_upload_tables(void *dev, QedTables *T, cudaStream_t st)
@@ -246,6 +251,14 @@ int qed_upload_tables(void *dev, QedTables *T, cudaStream_t st)
     if (cudaMemcpyAsync(base + hd.size() * 8, hf.data(), hf.size() * 4, cudaMemcpyHostToDevice, st) != cudaSuccess)
         return -1;
     if (cudaStreamSynchronize(st) != cudaSuccess) return -1;
+    // the Bessel table after the rate and inverse-CDF tables
+    const BesselTable &B = bessel_table();
+    char *bes = base + hd.size() * 8 + hf.size() * 4;
+    if (cudaMemcpyAsync(bes, B.lnk23.data(), (size_t)kNy * 8, cudaMemcpyHostToDevice, st) != cudaSuccess) return -1;
+    if (cudaMemcpyAsync(bes + (size_t)kNy * 8, B.lnik13.data(), (size_t)kNy * 8, cudaMemcpyHostToDevice, st) !=
+        cudaSuccess)
+        return -1;
+    if (cudaStreamSynchronize(st) != cudaSuccess) return -1;
     const double *d = (const double *)base;
     const float *f = (const float *)(base + hd.size() * 8);
     size_t off = 0;
@@ -259,6 +272,13 @@ int qed_upload_tables(void *dev, QedTables *T, cudaStream_t st)
     }
     T->nchi = kNchi;
     T->nr = kNr;
+    T->bes_k23 = (const double *)bes;
+    T->bes_ik13 = (const double *)bes + kNy;
+    T->nbes = kNy;
+    T->bes_lny0 = B.lny0;
+    T->bes_dlny = B.dlny;
+    T->bes_ymin = kYmin;
+    T->bes_ymax = kYmax;
     T->lnchi0 = std::log(kChiMin);
     T->dlnchi = (std::log(kChiMax) - T->lnchi0) / (kNchi - 1);
     return 0;

@@ -26,10 +26,16 @@ struct QedTables {
     double lnchi0, dlnchi;
     const float *lnG_f[2], *inv_f[2];
     const double *lnG_d[2], *inv_d[2];
+    // Bessel functions of Eqs. (23)/(24) for Method II's differential rates:
+    // ln K_{2/3}(y) + y and ln Int_y^inf K_{1/3} + y on nbes nodes of ln y
+    const double *bes_k23, *bes_ik13;
+    int nbes;
+    double bes_lny0, bes_dlny, bes_ymin, bes_ymax;
 };
 
 struct QedParams {
     int on;           // this species takes part in the Monte Carlo
+    int method;       // 1: Method I (optical depth), 2: Method II (per-step acceptance)
     double pref;      // alpha E_s dt / (sqrt3 pi): W dt = pref G(chi) / (gamma or k)
     double inv_Es;    // 1 / E_s
     double emin;      // lightest photon kept as a macro-photon (m c^2)
@@ -187,6 +193,63 @@ __host__ __device__ __forceinline__ double qed_sample(const QedTables &T, int p,
     const double s = (1.0 - tx) * s0 + tx * s1;
     const double f = s * s * s;
     return flip ? 1.0 - f : f;
+}
+
+// ---------------------------------------------------------------------
+// Bessel functions and spectra (Eqs. (23), (24)) for Method II
+// ---------------------------------------------------------------------
+// Catmull-Rom through the nodes L[0..n) at table coordinate x (clamped to
+// the table)
+__host__ __device__ __forceinline__ double qed_cr(const double *L, int n, double x)
+{
+    int i = (int)x;
+    if (i < 0) i = 0;
+    if (i > n - 2) i = n - 2;
+    const double t = x - i;
+    const double p0 = L[i > 0 ? i - 1 : 0], p1 = L[i], p2 = L[i + 1], p3 = L[i + 2 < n ? i + 2 : n - 1];
+    return (((-0.5 * p0 + 1.5 * p1 - 1.5 * p2 + 0.5 * p3) * t + (p0 - 2.5 * p1 + 2.0 * p2 - 0.5 * p3)) * t +
+            (-0.5 * p0 + 0.5 * p2)) * t + p1;
+}
+
+// K_{2/3}(y) and Int_y^inf K_{1/3}: the tables (ln K + y, smooth in ln y)
+// inside [ymin, ymax); zero above; below, the small-argument forms
+// K_{2/3} ~ y^{-2/3} and Int = pi/sqrt3 - c y^{2/3} matched at ymin
+__host__ __device__ __forceinline__ void qed_bessel(const QedTables &T, double y, double &k23, double &ik13)
+{
+    if (y >= T.bes_ymax) {
+        k23 = ik13 = 0.0;
+        return;
+    }
+    if (y < T.bes_ymin) {
+        const double k0 = exp(T.bes_k23[0] - T.bes_ymin), i0 = exp(T.bes_ik13[0] - T.bes_ymin);
+        const double full = 1.8137993642342178, r = cbrt(y / T.bes_ymin);  // pi / sqrt3
+        k23 = k0 / (r * r);
+        ik13 = full - (full - i0) * r * r;
+        return;
+    }
+    const double x = (log(y) - T.bes_lny0) / T.bes_dlny;
+    k23 = exp(qed_cr(T.bes_k23, T.nbes, x) - y);
+    ik13 = exp(qed_cr(T.bes_ik13, T.nbes, x) - y);
+}
+
+// Eq. (23) without its prefactor: ((1-u) + 1/(1-u)) K_{2/3}(y) - Int_y K_{1/3},
+// y = 2u / (3 chi (1-u))
+__host__ __device__ __forceinline__ double qed_spec_rad(const QedTables &T, double u, double chi)
+{
+    if (!(u > 0.0) || !(u < 1.0) || !(chi > 0.0)) return 0.0;
+    double k, ik;
+    qed_bessel(T, 2.0 * u / (3.0 * chi * (1.0 - u)), k, ik);
+    return ((1.0 - u) + 1.0 / (1.0 - u)) * k - ik;
+}
+
+// Eq. (24) without its prefactor: ((v^2 + (1-v)^2) / (v (1-v))) K_{2/3}(y)
+// + Int_y K_{1/3}, y = 2 / (3 chi v (1-v))
+__host__ __device__ __forceinline__ double qed_spec_pair(const QedTables &T, double v, double chi)
+{
+    if (!(v > 0.0) || !(v < 1.0) || !(chi > 0.0)) return 0.0;
+    double k, ik;
+    qed_bessel(T, 2.0 / (3.0 * chi * v * (1.0 - v)), k, ik);
+    return ((v * v + (1.0 - v) * (1.0 - v)) / (v * (1.0 - v))) * k + ik;
 }
 
 // --- FP32 form: chi and the rate in single precision (the optical depth

@@ -1,5 +1,9 @@
 // sort.cu -- stable counting sort of particles by tile (the tile holding a
-// particle's cell), dead particles last, and the per-tile start offsets.
+// particle's cell) and, inside a tile, by cell (row-major within the tile),
+// dead particles last, and the per-tile start offsets.  Cell order inside a
+// tile puts the particles of one cell next to each other, so the lanes of a
+// warp in the tiled push read the same field nodes and deposit into the
+// same window.
 //
 // The sort is a least-significant-digit radix sort of (tile key, index)
 // pairs with 8-bit digits.  Each pass is reduce-then-scan: per-block digit
@@ -23,12 +27,16 @@ __global__ void k_make_keys(const uint32_t *__restrict__ cell, const long long *
     long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
     uint32_t c = i < *dn ? cell[i] : kDead;
+    const int lb = g.tile_log2[0] + g.tile_log2[1] + g.tile_log2[2];  // bits of the cell within a tile
     uint32_t k;
-    if (c == kDead) k = (uint32_t)g.ntiles;
+    if (c == kDead) k = (uint32_t)g.ntiles << lb;
     else {
         int a, b, d;
         unpack_cell(g, c, a, b, d);
-        k = tile_of(g, a, b, d);
+        const uint32_t local = (uint32_t)(a & ((1 << g.tile_log2[0]) - 1)) |
+                               ((uint32_t)(b & ((1 << g.tile_log2[1]) - 1)) << g.tile_log2[0]) |
+                               ((uint32_t)(d & ((1 << g.tile_log2[2]) - 1)) << (g.tile_log2[0] + g.tile_log2[1]));
+        k = (tile_of(g, a, b, d) << lb) | local;
     }
     key[i] = k;
     val[i] = (uint32_t)i;
@@ -185,13 +193,13 @@ void scan_exclusive(const uint32_t *in, uint32_t *out, long long m, uint32_t *sc
     k_scan_down<<<(int)nb, 1024, 0, st>>>(in, m, out, sums);
 }
 
-__global__ void k_tile_starts(const uint32_t *__restrict__ skey, long long n, long long ntiles, uint32_t *starts,
-                              long long *dcount)
+__global__ void k_tile_starts(const uint32_t *__restrict__ skey, long long n, long long ntiles, int lb,
+                              uint32_t *starts, long long *dcount)
 {
     long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     if (i > n) return;
-    long long lo = i == 0 ? 0 : (long long)skey[i - 1] + 1;
-    long long hi = i == n ? ntiles : (long long)skey[i];
+    long long lo = i == 0 ? 0 : (long long)(skey[i - 1] >> lb) + 1;
+    long long hi = i == n ? ntiles : (long long)(skey[i] >> lb);
     for (long long t = lo; t <= hi && t <= ntiles; t++) {
         starts[t] = (uint32_t)i;
         if (t == ntiles) *dcount = i;
@@ -208,10 +216,11 @@ size_t sort_scratch_bytes(long long cap)
     return w * sizeof(uint32_t);
 }
 
-int radix_passes(long long ntiles)
+// 8-bit digits covering the largest key, (ntiles << lb) for the dead
+int radix_passes(long long ntiles, int lb)
 {
     int bits = 0;
-    while ((1ll << bits) <= ntiles) bits++;
+    while ((1ll << bits) <= (ntiles << lb)) bits++;
     return (bits + 7) / 8;
 }
 
@@ -228,10 +237,11 @@ void sort_by_tile(const uint32_t *cell, long long n, const long long *dcount_in,
     long long nb = (n + kSortItems - 1) / kSortItems;
     uint32_t *counts = w + 4 * cap_n;
     uint32_t *sscr = counts + 256 * nb + 64;
+    const int lb = g.tile_log2[0] + g.tile_log2[1] + g.tile_log2[2];
     if (n > 0) {
-        note_launch(1 + 2 * radix_passes(g.ntiles));
+        note_launch(1 + 2 * radix_passes(g.ntiles, lb));
         k_make_keys<<<div_up(n, 256), 256, 0, st>>>(cell, dcount_in, n, g, kA, vA);
-        int passes = radix_passes(g.ntiles);
+        int passes = radix_passes(g.ntiles, lb);
         for (int p = 0; p < passes; p++) {
             k_radix_hist<<<(int)nb, kSortThreads, 0, st>>>(kA, n, 8 * p, counts, (int)nb);
             scan_exclusive(counts, counts, 256 * nb, sscr, st);
@@ -241,7 +251,7 @@ void sort_by_tile(const uint32_t *cell, long long n, const long long *dcount_in,
         }
     }
     note_launch();
-    k_tile_starts<<<div_up(n + 1, 256), 256, 0, st>>>(kA, n, g.ntiles, starts, dcount_out);
+    k_tile_starts<<<div_up(n + 1, 256), 256, 0, st>>>(kA, n, g.ntiles, lb, starts, dcount_out);
     *perm = vA;
     *skeys = kA;
 }

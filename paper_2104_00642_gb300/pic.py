@@ -23,7 +23,7 @@ ERRORS = {-1: "PIC_ERR_ARG", -2: "PIC_ERR_CFL", -3: "PIC_ERR_CUDA", -4: "PIC_ERR
           -5: "PIC_ERR_NONFINITE", -6: "PIC_ERR_NOMEM", -7: "PIC_ERR_STATE", -8: "PIC_ERR_TIMEOUT"}
 PERIODIC, ABSORB = 0, 1
 FP32_CELLOFF, FP64_PLAIN = 0, 1
-PUSH_AUTO, PUSH_SIMPLE, PUSH_MLP_TC = 0, 1, 2
+PUSH_AUTO, PUSH_SIMPLE, PUSH_MLP_TC, PUSH_TILE_AGG = 0, 1, 2, 3
 PUSHER_BORIS, PUSHER_VAY = 0, 1
 EX, EY, EZ, BX, BY, BZ, JX, JY, JZ, RHO = range(10)
 MAX_SPECIES = 8
@@ -76,7 +76,7 @@ class pic_field_view(C.Structure):
 
 class pic_qed(C.Structure):
     _fields_ = [("mode", C.c_int), ("photon_sp", C.c_int), ("electron_sp", C.c_int), ("positron_sp", C.c_int),
-                ("lambda_r_m", C.c_double), ("photon_emin", C.c_double)]
+                ("lambda_r_m", C.c_double), ("photon_emin", C.c_double), ("method", C.c_int)]
 
 
 class pic_laser(C.Structure):
@@ -206,13 +206,15 @@ class TorchAllocator:
         self.allocated = 0
         self.freed = 0
         self.live = {}
+        self.errors = []  # exceptions the callbacks caught (the library sees a refusal)
         self._alloc = ALLOC_FN(self._do_alloc)
         self._free = FREE_FN(self._do_free)
 
     def _do_alloc(self, ctx, nbytes, stream):
         try:
             ptr = self._torch.cuda.caching_allocator_alloc(int(nbytes), self.device, stream=int(stream or 0))
-        except Exception:  # out of memory: the library reports PIC_ERR_NOMEM
+        except Exception as e:  # e.g. out of memory: the library reports PIC_ERR_NOMEM
+            self.errors.append(repr(e))
             return None
         self.allocated += 1
         self.live[int(ptr)] = int(nbytes)
@@ -389,9 +391,9 @@ class Sim:
                 "n_alive": list(d.n_alive[: self.nsp]), "E_photon_lost": d.E_photon_lost}
 
     def pic_set_qed(self, photon_sp=-1, electron_sp=-1, positron_sp=-1, lambda_r_m=1e-6, photon_emin=0.0,
-                    mode=QED_TABLE):
+                    mode=QED_TABLE, method=1):
         q = pic_qed(int(mode), int(photon_sp), int(electron_sp), int(positron_sp), float(lambda_r_m),
-                    float(photon_emin))
+                    float(photon_emin), int(method))
         self._check(load_library().pic_set_qed(self._h, C.byref(q)))
 
     def pic_qed_eval(self, process, chi, r=None):

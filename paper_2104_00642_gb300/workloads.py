@@ -22,6 +22,11 @@ c/omega_r, density in n_r.  Workloads:
   (Sec. III-IV; omega_r = omega_L).
 * ``qed_field_sample``: the collision's QED regime (beam energies, peak chi)
   in a uniform field, small enough for the FP64 oracle.
+* ``cascade``: seed replicas of one electron of Lorentz factor gamma0 moving
+  across a uniform magnetic field B0 = b B_cr, photon emission and pair
+  creation by Method II (Sec. IV: gamma0 = 1000 in 0.001 / 0.009 B_cr for
+  the spectra of Fig. 9, gamma0 = 2e5 in 0.2 B_cr for the pair count of
+  Fig. 10).
 """
 from __future__ import annotations
 
@@ -34,6 +39,7 @@ PERIODIC, ABSORB = 0, 1
 M_PROTON = 1836.15267343
 MEC2_KEV = 510.99895
 SEED0 = 20210401
+HBARC_EV_M = 1.973269804e-7  # hbar c (eV m)
 
 
 @dataclass
@@ -349,6 +355,52 @@ def qed_field_sample(n_e=2048, gamma0=1957.0, spread=0.01, B0=400.0, dt=0.1319, 
     return Workload("qed_field_sample", 1, (16, 1, 1), (1.0, 1.0, 1.0), dt, (PERIODIC,) * 3, [e, po, ph], steps,
                     tile=(16, 1, 1), notes={"B0": B0, "gamma0": gamma0},
                     qed={"photon_sp": 2, "electron_sp": 0, "positron_sp": 1, "lambda_r_m": 1e-6, "photon_emin": 2.0})
+
+
+def b_critical(lambda_r_m=1e-6):
+    """the critical field B_cr = m^2 c^2 / (e hbar) in units of m c omega_r / e:
+    m c^2 / (hbar omega_r), omega_r = 2 pi c / lambda_r"""
+    return MEC2_KEV * 1e3 * lambda_r_m / (2.0 * math.pi * HBARC_EV_M)
+
+
+def cascade(gamma0=1000.0, b=0.009, replicas=2000, t_end=4.0, dt=None, steps=None, seed=SEED0 + 11,
+            lambda_r_m=1e-6, photon_emin=0.0, capacity_per_replica=64):
+    """Seed replicas of the single-electron cascade of Sec. IV: each replica
+    is one electron of Lorentz factor gamma0 moving along +y across a uniform
+    B_z = b B_cr (the caller sets the field, notes["B0"]); chi0 = gamma0 b.
+    The replicas share a 16-cell periodic 1D grid at random x, with a tiny
+    weight so that they do not interact: every electron's identity starts
+    its own Philox stream, so the replicas are independent seeds.  Species:
+    electrons (QED), positrons (QED), photons (photons below photon_emin, in
+    m c^2, are tallied).  dt defaults to 1 / (8000 b^(2/3)): Method II's
+    acceptance per step peaks for leptons near gamma ~ 2, at about
+    3400 b^(2/3) dt for lambda_r = 1 um, so this keeps it below one half;
+    steps defaults to t_end / dt (t_end in 1/omega_r).
+    Paper set-ups: cascade(1000, 0.001), cascade(1000, 0.009) (Fig. 9),
+    cascade(2e5, 0.2) (Fig. 10)."""
+    rng = _rng(seed)
+    B0 = b * b_critical(lambda_r_m)
+    chi0 = gamma0 * b
+    if dt is None:
+        dt = 1.0 / (8000.0 * b ** (2.0 / 3.0)) * (lambda_r_m / 1e-6) ** (2.0 / 3.0)
+    if steps is None:
+        steps = int(math.ceil(t_end / dt))
+    n = int(replicas)
+    x = (np.arange(n) + rng.random(n)) * (16.0 / n)
+    zero = np.zeros(n)
+    u = math.sqrt(gamma0 * gamma0 - 1.0)
+    w = 1e-12
+    cap = capacity_per_replica * n
+    e = Species("electron", -1.0, 1.0, w, x, zero, zero.copy(), zero.copy(), np.full(n, u), zero.copy(),
+                capacity=cap, qed=1)
+    emp = np.zeros(0)
+    po = Species("positron", 1.0, 1.0, w, emp, emp, emp, emp, emp, emp, capacity=cap, qed=1)
+    ph = Species("photon", 0.0, 0.0, w, emp, emp, emp, emp, emp, emp, capacity=4 * cap, kind=1)
+    return Workload(f"cascade gamma0={gamma0:g} B0={b:g} B_cr", 1, (16, 1, 1), (1.0, 1.0, 1.0), dt,
+                    (PERIODIC,) * 3, [e, po, ph], steps, tile=(16, 1, 1),
+                    notes={"B0": B0, "gamma0": gamma0, "chi0": chi0, "replicas": n, "t_end": steps * dt},
+                    qed={"photon_sp": 2, "electron_sp": 0, "positron_sp": 1, "lambda_r_m": lambda_r_m,
+                         "photon_emin": photon_emin})
 
 
 def vacuum_pulse_1d(n_cells=1024, cells_per_lambda=32, a0=1.0, fwhm=4.0 * 2.0 * math.pi, steps=1500,

@@ -185,7 +185,9 @@ def test_field_device_view_reads_the_resident_arrays(prec):
         assert v["elem_bytes"] == (8 if prec == pic.FP64_PLAIN else 4)
         host = s.pic_fields(c)[0]  # (ny, nx + 1): absorbing x, periodic y
         ny, nx1 = host.shape
-        span = v["origin"] + (v["hi"][1] + 1) * v["stride"][1]
+        # one past the last element of the padded box (the component's
+        # allocation may end right there)
+        span = v["origin"] + v["hi"][1] * v["stride"][1] + v["hi"][0] + 1
         t = _read_device(v["data"], span, v["elem_bytes"])
         jj, ii = np.meshgrid(np.arange(ny), np.arange(nx1), indexing="ij")
         got = t[v["origin"] + ii + jj * v["stride"][1]].astype(np.float64)
@@ -207,6 +209,7 @@ def test_caller_allocator_serves_every_block():
     before = torch.cuda.memory_allocated()
     s = pic.from_workload(w, sort_interval=4, allocator=A)
     r = pic.from_workload(w, sort_interval=4)
+    assert not A.errors, A.errors
     assert A.allocated > 10 and torch.cuda.memory_allocated() > before
     n_state = len(A.live)  # blocks held by the simulation (the upload's staging came and went)
     for t in (s, r):

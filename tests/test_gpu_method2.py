@@ -1,0 +1,298 @@
+"""Method II of Sec. IV on the GPU (photon emission: u0 = r1^3 accepted when
+r2 < 3 r1^2 dW_rad/du(u0) dt; pair creation: v0 = r1 accepted when
+r2 < dW_pair/dv(v0) dt) against the FP64 oracle, and the cascade set-ups the
+paper runs with it (Figs. 9 and 10).
+
+* Event by event: both sides draw r1, r2 from the same Philox counter
+  (identity, step, purpose), so they accept the same draws.  They differ
+  only in how dW/du is evaluated (GPU: tables of K_{2/3} and Int K_{1/3};
+  oracle: quadrature), a relative difference well below 1e-5, so a draw
+  flips only when r2 lies within ~1e-5 pacc of pacc: the expected number of
+  flips over the few hundred events here is below 1e-2, and none is
+  allowed.
+* Spectra: one step of many identical emitters (or photons) gives accepted
+  fractions distributed as dW/du (dW/dv) of Eqs. (23)/(24).
+* Cascades: seed replicas on the GPU against replicas on the oracle, within
+  the Monte-Carlo noise; pure B does no work, so the total energy is
+  conserved exactly by the method.
+"""
+import math
+
+import numpy as np
+import pytest
+
+from oracle import oracle as O
+from paper_2104_00642_gb300 import pic, workloads as W
+from tests.helpers import oracle_from_workload
+
+pytestmark = pytest.mark.gpu
+
+SEED = 0x3E7D0C2A11
+
+
+def _pair(w, prec):
+    sim = pic.from_workload(w, precision=prec, seed=SEED)
+    sim.pic_set_qed(mode=pic.QED_TABLE, method=2, **w.qed)
+    sim.pic_set_field(pic.BZ, np.full(sim.box(), w.notes["B0"]))
+    o = oracle_from_workload(w, seed=SEED)
+    o.set_qed_method(2)
+    o.set_field(O.BZ, np.full(o.box(), w.notes["B0"]))
+    return sim, o
+
+
+def _alive_ids(ids, p):
+    return ids[p["alive"] == 1]
+
+
+def _energy_by_id(ids, p, photon):
+    uu = p["ux"] ** 2 + p["uy"] ** 2 + p["uz"] ** 2
+    e = np.sqrt(uu) if photon else np.sqrt(1.0 + uu)
+    a = p["alive"] == 1
+    return dict(zip(ids[a].tolist(), e[a].tolist()))
+
+
+@pytest.mark.parametrize("prec", [pic.FP64_PLAIN, pic.FP32_CELLOFF])
+def test_method2_matches_oracle_event_by_event(prec):
+    """64 electrons of gamma 1000 in 0.009 B_cr (chi0 = 9, the Fig. 9(d)-(f)
+    set-up) for 200 steps: after every step the same photons, electrons and
+    positrons exist on both sides (identities are drawn from the same
+    counters), and at the end every particle's energy agrees (FP64: 1e-9
+    relative; FP32: 2e-5 -- the FP32 momentum's rounding over the run)."""
+    w = W.cascade(1000.0, 0.009, replicas=64, steps=200, capacity_per_replica=64)
+    sim, o = _pair(w, prec)
+    events = 0
+    for step in range(w.steps):
+        sim.pic_step(1)
+        o.step(1)
+        for sp in range(3):
+            ig, _ = sim.pic_get_qed_state(sp)
+            io, _ = o.qed_state(sp)
+            g = set(_alive_ids(ig, sim.pic_get_particles(sp)).tolist())
+            r = set(_alive_ids(io, o.particles(sp)).tolist())
+            assert g == r, (step, sp, len(g - r), len(r - g))
+            if sp == 2:
+                events = max(events, len(g))
+    assert o.method2_over() == 0
+    assert events > 100  # the run creates photons (and pairs) to compare
+    tol = 1e-9 if prec == pic.FP64_PLAIN else 2e-5
+    for sp in range(3):
+        ig, _ = sim.pic_get_qed_state(sp)
+        io, _ = o.qed_state(sp)
+        eg = _energy_by_id(ig, sim.pic_get_particles(sp), sp == 2)
+        eo = _energy_by_id(io, o.particles(sp), sp == 2)
+        assert eg.keys() == eo.keys()
+        worst = max(abs(eg[k] - eo[k]) / eo[k] for k in eo) if eo else 0.0
+        assert worst <= tol, (sp, worst)
+    sim.close()
+
+
+def _spectrum_check(frac, weight_fn, n_draw, bins):
+    """chi^2 per bin of a histogram of accepted fractions against the
+    expected counts n_draw * Int_bin weight_fn (the acceptance density)"""
+    h, _ = np.histogram(frac, bins=bins)
+    exp = np.zeros(len(bins) - 1)
+    for i in range(len(bins) - 1):
+        x = np.linspace(bins[i], bins[i + 1], 41)
+        y = np.array([weight_fn(t) for t in x])
+        exp[i] = n_draw * np.sum(0.5 * (y[1:] + y[:-1]) * np.diff(x))
+    m = exp > 20
+    return float(np.sum((h[m] - exp[m]) ** 2 / exp[m]) / m.sum()), int(m.sum()), float(h.sum()), float(exp.sum())
+
+
+def test_method2_emission_spectrum_is_eq23():
+    """one step of 400k electrons of gamma 1000 at chi 1: the fractions
+    u = k / gamma of the photons emitted follow n dt pref dW_rad/du / gamma
+    (Eq. 23), bin by bin, and so does their number"""
+    n, gamma, chi = 400_000, 1000.0, 1.0
+    b = chi / math.sqrt(gamma * gamma - 1.0)
+    w = W.cascade(gamma, b, replicas=n, steps=1, capacity_per_replica=2)
+    sim, _ = _pair(w, pic.FP64_PLAIN)
+    sim.pic_step(1)
+    k = sim.pic_get_particles(2)
+    a = k["alive"] == 1
+    u = np.sqrt(k["ux"][a] ** 2 + k["uy"][a] ** 2 + k["uz"][a] ** 2) / gamma
+    sim.close()
+    # E_s (= B_cr in these units) alpha dt / (sqrt(3) pi): the prefactor of Eqs. (23)/(24)
+    pref = W.b_critical(1e-6) * w.dt / (137.035999084 * math.sqrt(3.0) * math.pi)
+    dens = lambda t: pref * O.lib().or_qed_Frad(t, chi) / gamma
+    bins = np.concatenate([np.geomspace(1e-5, 0.1, 25), np.linspace(0.1, 0.99, 20)[1:]])
+    c2, nb, got, want = _spectrum_check(u, dens, n, bins)
+    print(c2, nb, got, want)
+    assert c2 < 2.0 and nb > 20
+    assert abs(got - want) <= 5.0 * math.sqrt(want)
+
+
+def test_method2_pair_spectrum_is_eq24():
+    """one step of 400k photons of energy 1e4 m c^2 at chi_gamma 5: the
+    positron fraction v of the pairs created follows n dt pref dW_pair/dv / k
+    (Eq. 24)"""
+    n, kk, chi = 400_000, 1e4, 5.0
+    b = chi / kk
+    w = W.cascade(2.0, b, replicas=1, steps=1, capacity_per_replica=2 * n)
+    emp = np.zeros(0)
+    for s in w.species[:2]:
+        s.x = s.y = s.z = s.ux = s.uy = s.uz = emp
+    rng = np.random.default_rng(5)
+    ph = w.species[2]
+    ph.x = rng.random(n) * 16.0
+    ph.y = np.zeros(n)
+    ph.z = np.zeros(n)
+    ph.ux, ph.uy, ph.uz = np.zeros(n), np.full(n, kk), np.zeros(n)
+    sim, _ = _pair(w, pic.FP64_PLAIN)
+    sim.pic_step(1)
+    pos = sim.pic_get_particles(1)
+    a = pos["alive"] == 1
+    v = np.sqrt(1.0 + pos["ux"][a] ** 2 + pos["uy"][a] ** 2 + pos["uz"][a] ** 2) / kk
+    sim.close()
+    pref = W.b_critical(1e-6) * w.dt / (137.035999084 * math.sqrt(3.0) * math.pi)
+    dens = lambda t: pref * O.lib().or_qed_Fpair(t, chi) / kk
+    bins = np.linspace(0.0, 1.0, 41)
+    c2, nb, got, want = _spectrum_check(v, dens, n, bins)
+    print(c2, nb, got, want)
+    assert c2 < 2.0 and nb > 20
+    assert abs(got - want) <= 5.0 * math.sqrt(want)
+
+
+def test_method2_step_too_long_is_an_error():
+    """electrons of gamma 2 in 0.2 B_cr with dt 0.05: Method II's acceptance
+    3 r1^2 dW/du dt exceeds one for small r1, which pic_step reports instead
+    of silently clipping the rate"""
+    w = W.cascade(2.0, 0.2, replicas=256, dt=0.05, steps=4)
+    sim, _ = _pair(w, pic.FP32_CELLOFF)
+    with pytest.raises(pic.PicError) as e:
+        sim.pic_step(4)
+    assert e.value.code == -2 and "Method II" in str(e.value)  # PIC_ERR_CFL
+    sim.close()
+
+
+def test_method2_is_refused_with_the_surrogate():
+    w = W.cascade(1000.0, 0.009, replicas=4, steps=1)
+    sim = pic.from_workload(w)
+    with pytest.raises(pic.PicError):
+        sim.pic_set_qed(mode=pic.QED_SURROGATE, method=2, **w.qed)
+    with pytest.raises(pic.PicError):
+        sim.pic_set_qed(mode=pic.QED_TABLE, method=3, **w.qed)
+    sim.close()
+
+
+# ----------------------------------------------------------------------
+# cascades (Sec. IV, Figs. 9 and 10)
+# ----------------------------------------------------------------------
+
+def _observe(parts, emin_mev=None):
+    """per species: count and energy sum of live particles (and the count
+    above emin_mev)"""
+    out = []
+    for sp, p in enumerate(parts):
+        a = p["alive"] == 1
+        uu = p["ux"][a] ** 2 + p["uy"][a] ** 2 + p["uz"][a] ** 2
+        e = np.sqrt(uu) if sp == 2 else np.sqrt(1.0 + uu)
+        row = [float(a.sum()), float(e.sum())]
+        if emin_mev is not None:
+            row.append(float((e * W.MEC2_KEV * 1e-3 > emin_mev).sum()))
+        out.append(row)
+    return np.array(out)
+
+
+def _gpu_cascade(w, method=2, prec=pic.FP32_CELLOFF, seed=SEED, marks=(), emin_mev=None):
+    sim = pic.from_workload(w, precision=prec, seed=seed, sort_interval=16)
+    sim.pic_set_qed(mode=pic.QED_TABLE, method=method, **w.qed)
+    sim.pic_set_field(pic.BZ, np.full(sim.box(), w.notes["B0"]))
+    obs, done = {}, 0
+    for m in sorted(set(marks) | {w.steps}):
+        sim.pic_step(m - done)
+        done = m
+        obs[m] = _observe([sim.pic_get_particles(i) for i in range(3)], emin_mev)
+    lost = sim.pic_diagnostics()["E_photon_lost"]
+    sim.close()
+    return obs, lost
+
+
+def _oracle_cascade_per_replica(w, n_rep, marks, emin_mev=None, seed=SEED):
+    """n_rep independent oracle runs of one replica each: per mark, the
+    per-replica observables (n_rep, species, columns)"""
+    rows = {m: [] for m in marks}
+    one = W.cascade(w.notes["gamma0"], w.notes["B0"] / W.b_critical(), replicas=1, dt=w.dt, steps=w.steps,
+                    capacity_per_replica=w.species[0].capacity)
+    for r in range(n_rep):
+        o = O.OracleSim(1, (16,), (1.0,), w.dt)
+        for s in one.species:
+            o.add_species(s.q, s.m, s.w, s.capacity, kind=s.kind, qed=s.qed)
+        o.set_qed(seed=seed + 7919 * r, **one.qed)
+        o.set_qed_method(2)
+        o.set_field(O.BZ, np.full(o.box(), one.notes["B0"]))
+        s = one.species[0]
+        o.load(0, s.x, s.y, s.z, s.ux, s.uy, s.uz)
+        done = 0
+        for m in sorted(marks):
+            o.step(m - done)
+            done = m
+            rows[m].append(_observe([o.particles(i) for i in range(3)], emin_mev))
+        assert o.method2_over() == 0
+    return {m: np.array(v) for m, v in rows.items()}
+
+
+@pytest.mark.parametrize("b", [0.001, 0.009])
+def test_cascade_fig9_matches_oracle_replicas(b):
+    """Fig. 9 set-up (gamma0 = 1000 across 0.001 / 0.009 B_cr): 4000 GPU
+    replicas against 48 single-replica oracle runs, at t = 1 and t = 2
+    (1/omega for lambda = 1 um): the mean number of electrons, positrons and
+    photons per replica and their mean energy agree within 4.5 standard
+    errors of the oracle's replica spread; the GPU's total energy (leptons,
+    photons, pair rest mass) stays that of the primaries (pure B does no
+    work) to FP32 rounding"""
+    t_marks = (1.0, 2.0)
+    w0 = W.cascade(1000.0, b, replicas=4000, t_end=2.0, capacity_per_replica=128)
+    marks = tuple(int(round(t / w0.dt)) for t in t_marks)
+    g, lost = _gpu_cascade(w0, marks=marks)
+    ref = _oracle_cascade_per_replica(w0, 48, marks)
+    e0 = 4000 * 1000.0
+    for m in marks:
+        mg = g[m] / 4000.0
+        mo, so = ref[m].mean(axis=0), ref[m].std(axis=0, ddof=1) / math.sqrt(48)
+        print(b, m, mg.tolist(), mo.tolist(), so.tolist())
+        assert np.all(np.abs(mg - mo) <= 4.5 * so + 1e-9 * np.abs(mo)), (m, mg, mo, so)
+        assert abs(g[m][:, 1].sum() + lost - e0) <= 2e-4 * e0
+
+
+def test_cascade_fig9_method1_and_method2_agree():
+    """the paper shows both methods reproduce Eq. (23); on the cascade they
+    give the same per-replica counts and energies within the Monte-Carlo
+    noise (4000 replicas each, gamma0 = 1000 in 0.009 B_cr, t = 2)"""
+    w = W.cascade(1000.0, 0.009, replicas=4000, t_end=2.0, capacity_per_replica=128)
+    a, _ = _gpu_cascade(w, method=1)
+    b, _ = _gpu_cascade(w, method=2, seed=SEED + 1)
+    A, B = a[w.steps] / 4000.0, b[w.steps] / 4000.0
+    print(A.tolist(), B.tolist())
+    # counts: Poisson-like spread per replica at most ~ the mean (+ 1);
+    # energies: per-replica spread at most the primary energy
+    sd_n = np.sqrt((np.maximum(A[:, 0], B[:, 0]) + 1.0) * 2.0 / 4000.0) * 3.0
+    sd_e = 1000.0 * math.sqrt(2.0 / 4000.0)
+    assert np.all(np.abs(A[:, 0] - B[:, 0]) <= 5.0 * sd_n), (A, B)
+    assert np.all(np.abs(A[:, 1] - B[:, 1]) <= 5.0 * sd_e), (A, B)
+
+
+def test_cascade_fig10_pair_count_matches_oracle():
+    """Fig. 10 set-up (gamma0 = 2e5 across 0.2 B_cr, Method II, photons
+    below 2 m c^2 tallied): the number of electrons and positrons above 100
+    MeV per replica, averaged over 2000 GPU replicas, against 12
+    single-replica oracle runs, at t = 0.12, 0.24, 0.36; the GPU curve is
+    printed over t <= 0.6"""
+    w = W.cascade(2e5, 0.2, replicas=2000, t_end=0.6, photon_emin=2.0, capacity_per_replica=12288)
+    marks_all = tuple(int(round(t / w.dt)) for t in np.arange(0.06, 0.61, 0.06))
+    g, lost = _gpu_cascade(w, marks=marks_all, emin_mev=100.0)
+    curve = [(round(m * w.dt, 3), float((g[m][0, 2] + g[m][1, 2]) / 2000.0)) for m in marks_all]
+    print("e+- above 100 MeV per replica:", curve)
+    marks = (marks_all[1], marks_all[3], marks_all[5])  # t = 0.12, 0.24, 0.36
+    wo = W.cascade(2e5, 0.2, replicas=1, dt=w.dt, steps=marks[-1], photon_emin=2.0, capacity_per_replica=12288)
+    ref = _oracle_cascade_per_replica(wo, 12, marks, emin_mev=100.0)
+    e0 = 2000 * 2e5
+    for m in marks:
+        gm = g[m]
+        ng = (gm[0, 2] + gm[1, 2]) / 2000.0
+        per = ref[m][:, 0, 2] + ref[m][:, 1, 2]
+        no, so = per.mean(), per.std(ddof=1) / math.sqrt(len(per))
+        print(m * w.dt, ng, no, so)
+        assert abs(ng - no) <= 4.5 * so + 0.5, (m, ng, no, so)
+    last = g[w.steps]
+    assert abs(last[:, 1].sum() + lost - e0) <= 2e-4 * e0

@@ -107,6 +107,12 @@ def test_gradient_matches_oracle_backprop(sim, n):
         rel = np.linalg.norm(g - r) / max(np.linalg.norm(r), 1e-30)
         assert rel < 1e-2, (name, rel)
         assert np.dot(g, r) / (np.linalg.norm(g) * np.linalg.norm(r) + 1e-30) > 0.999, name
+        # element by element: within a few per cent of each entry (the BF16
+        # roundings of activations, deltas and weights), with a floor of a
+        # fraction of the block's rms for entries whose terms cancel
+        bound = 3e-2 * np.abs(r) + 3e-3 * np.sqrt(np.mean(r * r))
+        bad = np.abs(g - r) > bound
+        assert not bad.any(), (name, int(bad.sum()), float(np.max(np.abs(g - r) / (bound + 1e-300))))
 
 
 def test_gradient_step_lowers_the_loss(sim):

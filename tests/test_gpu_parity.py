@@ -99,8 +99,9 @@ def test_one_step_matches_oracle(dim, prec, pusher):
 @pytest.mark.parametrize("prec", PRECS)
 @pytest.mark.parametrize("dim", [2, 3])
 def test_sort_permutation_bit_exact(dim, prec):
-    """Stable counting sort by tile: the order equals the oracle's (itself
-    pinned to numpy's stable argsort) on a ragged multi-tile grid."""
+    """Stable counting sort by tile, then cell within the tile: the order
+    equals the oracle's (itself pinned to numpy's stable argsort) on a ragged
+    multi-tile grid."""
     n = (40, 21, 1) if dim == 2 else (20, 12, 9)
     dx = (0.1, 0.1, 0.1)
     tile = (16, 8, 1) if dim == 2 else (8, 4, 4)
@@ -250,14 +251,17 @@ def test_empty_species_and_errors():
 # tiled 2D push (shared-memory staging and current box)
 # --------------------------------------------------------------------------
 
+@pytest.mark.parametrize("variant", [pic.PUSH_AUTO, pic.PUSH_TILE_AGG])
 @pytest.mark.parametrize("pusher", [pic.PUSHER_BORIS, pic.PUSHER_VAY])
 @pytest.mark.parametrize("tile", [8, 16])
-def test_tile_push_one_step_matches_oracle(tile, pusher):
+def test_tile_push_one_step_matches_oracle(tile, pusher, variant):
     """Sort at step 0 (same order in both), one step through the tiled
-    kernel: ragged grid (tiles do not divide it), several tiles."""
+    kernel (lane-strided, or warp-aggregated deposit): ragged grid (tiles do
+    not divide it), several tiles, several particles per cell."""
     n, dx = (40, 21), (0.1, 0.12)
     w, F = random_state(2, n, dx, _dt(dx), 4, seed=301, umax=0.9)
-    sim = pic.from_workload(w, precision=pic.FP32_CELLOFF, sort_interval=1, tile=(tile, tile, 1), pusher=pusher)
+    sim = pic.from_workload(w, precision=pic.FP32_CELLOFF, sort_interval=1, tile=(tile, tile, 1), pusher=pusher,
+                            push_variant=variant)
     o = oracle_from_workload(w, sort_interval=1, tile=(tile, tile, 1))
     o.set_pusher(pusher)
     for c in range(9):
@@ -335,22 +339,31 @@ def test_tile3d_push_one_step_matches_oracle(pusher):
 
 def test_tile3d_push_fallback_after_drift_matches_simple_kernel():
     """Fast particles and a long sort interval in 3D: particles leave their
-    tile box and take the global path; tiled and simple kernels agree."""
+    tile box and take the global path; the tiled kernel agrees with the
+    simple kernel and both with the oracle over 10 steps."""
     n, dx = (16, 16, 12), (0.1, 0.1, 0.1)
     w, F = random_state(3, n, dx, _dt(dx), 2, seed=312, umax=3.0)
     sims = [pic.from_workload(w, precision=pic.FP32_CELLOFF, sort_interval=50, tile=(4, 4, 4), push_variant=v)
             for v in (pic.PUSH_AUTO, pic.PUSH_SIMPLE)]
+    o = oracle_from_workload(w, sort_interval=50, tile=(4, 4, 4))
     for c in range(9):
         for s in sims:
             s.pic_set_field(c, F[c])
+        o.set_field(c, F[c])
     for s in sims:
         s.pic_step(10)
-    pa, pb = sims[0].pic_get_particles(0), sims[1].pic_get_particles(0)
+    o.step(10)
+    pa, pb, po = sims[0].pic_get_particles(0), sims[1].pic_get_particles(0), o.particles(0)
+    umag = np.sqrt(po["ux"] ** 2 + po["uy"] ** 2 + po["uz"] ** 2)
     for k in ("x", "y", "z", "ux", "uy", "uz"):
         assert np.max(np.abs(pa[k] - pb[k])) < 1e-4
-    da, db = sims[0].pic_diagnostics(), sims[1].pic_diagnostics()
+        tol = 1e-4 * (umag + 1.0) if k.startswith("u") else 1e-4
+        assert np.all(np.abs(pa[k] - po[k]) <= tol), (k, np.max(np.abs(pa[k] - po[k])))
+    da, db, do = sims[0].pic_diagnostics(), sims[1].pic_diagnostics(), o.diagnostics()
     for k in ("U_E", "U_B"):
         assert abs(da[k] - db[k]) <= 1e-4 * max(db["U_E"], db["U_B"])
+        assert abs(da[k] - do[k]) <= 1e-4 * max(do["U_E"], do["U_B"])
+    assert abs(da["U_kin"][0] / do["U_kin"][0] - 1.0) <= 1e-4
 
 
 def _laser_foil_small(seed):

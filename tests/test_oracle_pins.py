@@ -382,6 +382,7 @@ def test_particle_at_rest_deposits_nothing():
 # --------------------------------------------------------------------------
 
 def test_sort_matches_numpy_stable_argsort():
+    """stable sort by (tile, cell within the tile)"""
     rng = np.random.default_rng(3)
     n, dx, tile = (32, 24, 16), (0.1, 0.1, 0.1), (8, 8, 4)
     s = O.OracleSim(3, n, dx, 0.05, tile=tile)
@@ -390,12 +391,20 @@ def test_sort_matches_numpy_stable_argsort():
     u = [rng.normal(0, 0.1, N) for _ in range(3)]
     i = s.add_species(-1, 1, 1, N)
     s.load(i, *x, *u)
-    key = np.zeros(N, dtype=np.int64)
+    # key: the tile, then the cell inside the tile (row-major, x fastest)
+    tile_id = np.zeros(N, dtype=np.int64)
+    local = np.zeros(N, dtype=np.int64)
     nt = [n[d] // tile[d] for d in range(3)]
     for d in reversed(range(3)):
-        key = key * nt[d] + (np.floor(x[d] / dx[d]).astype(np.int64) // tile[d])
+        c = np.floor(x[d] / dx[d]).astype(np.int64)
+        tile_id = tile_id * nt[d] + c // tile[d]
+        local = local * tile[d] + c % tile[d]
+    key = tile_id * (tile[0] * tile[1] * tile[2]) + local
     perm = s.sort(i)
     assert np.array_equal(perm, np.argsort(key, kind="stable"))
+    # the particles of one cell are contiguous after the sort
+    c_sorted = key[perm]
+    assert np.all(np.diff(c_sorted) >= 0)
 
 
 # --------------------------------------------------------------------------
