@@ -182,10 +182,20 @@ bool use_tile_push(const pic_sim *s, const SpeciesState &p)
 {
     // the tiled kernels stage order-2 stencils; order 4 runs on the simple kernels
     if (s->push_variant == PIC_PUSH_SIMPLE || !p.items_valid || s->precision != PIC_PREC_FP32_CELLOFF ||
-        s->g.order != 2 ||
-        p.kind != PIC_KIND_MASSIVE || (s->qed_on && p.qed))
+        s->g.order != 2 || p.kind != PIC_KIND_MASSIVE)
         return false;
-    if (s->g.dim == 3) return tile3d_push_supported(s->g);
+    // QED leptons: the Monte Carlo is fused into the 2D tiled kernel only
+    if (s->g.dim == 3) return !(s->qed_on && p.qed) && tile3d_push_supported(s->g);
+    return s->g.dim == 2 && s->g.tile_log2[0] == s->g.tile_log2[1] &&
+           (s->g.tile_log2[0] == 3 || s->g.tile_log2[0] == 4);
+}
+
+// photons: the tiled photon push (2D) on the work items of the last sort
+bool use_tile_photon_push(const pic_sim *s, const SpeciesState &p)
+{
+    if (s->push_variant == PIC_PUSH_SIMPLE || s->push_variant == PIC_PUSH_MLP_TC || !p.items_valid ||
+        s->precision != PIC_PREC_FP32_CELLOFF || p.kind != PIC_KIND_PHOTON)
+        return false;
     return s->g.dim == 2 && s->g.tile_log2[0] == s->g.tile_log2[1] &&
            (s->g.tile_log2[0] == 3 || s->g.tile_log2[0] == 4);
 }
@@ -333,13 +343,35 @@ void push_species(pic_sim *s, int i, float *F)
 {
     SpeciesState &p = s->sp[i];
     if (p.kind == PIC_KIND_PHOTON) {
-        launch_push_photon_f32(view32(s, i, p.cur), F, s->g, push_const(s, p), qed_params(s, i), s->d_err, s->st,
-                               s->push_variant == PIC_PUSH_MLP_TC);
+        const QedParams q = qed_params(s, i);
+        const PartF32 P = view32(s, i, p.cur);
+        if (use_tile_photon_push(s, p)) {
+            // the photons sorted into work items on the tiled kernel, those
+            // emitted since on the one-thread-per-particle kernel
+            const long long max_items = (long long)tile_items_capacity(p.n_hi, s->g.ntiles, s->g.dim);
+            launch_push_photon_tile2d(P, p.items, p.nitems, max_items, F, s->g, push_const(s, p), q, s->d_err, s->st);
+            launch_push_photon_f32(P, F, s->g, push_const(s, p), q, s->d_err, s->st, false,
+                                   p.tile_start + s->g.ntiles);
+        } else {
+            launch_push_photon_f32(P, F, s->g, push_const(s, p), q, s->d_err, s->st,
+                                   s->push_variant == PIC_PUSH_MLP_TC);
+        }
         return;
     }
     if (s->qed_on && p.qed) {
-        launch_push_qed_f32(view32(s, i, p.cur), F, s->g, push_const(s, p), qed_params(s, i), s->d_err, s->d_eabs,
-                            s->st);
+        const QedParams q = qed_params(s, i);
+        const PartF32 P = view32(s, i, p.cur);
+        if (use_tile_push(s, p)) {
+            // the particles sorted into work items on the tiled kernel, those
+            // appended since (pairs) on the one-thread-per-particle kernel
+            const long long max_items = (long long)tile_items_capacity(p.n_hi, s->g.ntiles, s->g.dim);
+            launch_push_tile2d(P, p.items, p.nitems, max_items, F, s->g, push_const(s, p), s->d_err, s->d_eabs,
+                               s->st, true, &q);
+            launch_push_qed_f32(P, F, s->g, push_const(s, p), q, s->d_err, s->d_eabs, s->st,
+                                p.tile_start + s->g.ntiles);
+        } else {
+            launch_push_qed_f32(P, F, s->g, push_const(s, p), q, s->d_err, s->d_eabs, s->st);
+        }
         return;
     }
     if (use_tile_push(s, p)) {
@@ -395,7 +427,11 @@ void qed_spawn_views(pic_sim *s)
                            s->d_err, s->st);
         E.n_hi = std::min(E.cap, E.n_hi + P.n_hi);
         O.n_hi = std::min(O.cap, O.n_hi + P.n_hi);
-        E.items_valid = O.items_valid = false;
+        // the pairs land past the sorted particles (tile_start[ntiles]): the
+        // work items stay valid for the ones before, the QED lepton push
+        // takes the rest on its one-thread-per-particle kernel
+        if (!E.qed) E.items_valid = false;
+        if (!O.qed) O.items_valid = false;
     }
     if (ph < 0) return;
     for (int i = 0; i < s->nsp; i++) {
@@ -406,7 +442,8 @@ void qed_spawn_views(pic_sim *s)
         launch_spawn_photons(view(i), off, tot, qed_params(s, i), view(ph), P.tau[P.cur], P.id[P.cur], P.ev,
                              P.d_count, P.cap, dim, s->d_err, s->st);
         P.n_hi = std::min(P.cap, P.n_hi + p.n_hi);
-        P.items_valid = false;
+        // (the photons land past the sorted ones: the photon push takes them
+        // on its one-thread-per-particle kernel, the work items stay valid)
     }
 }
 

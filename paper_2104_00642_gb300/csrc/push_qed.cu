@@ -13,10 +13,7 @@
 // from the inverse CDF of Eq. (24)); no current.
 #include <algorithm>
 
-#include "mlp_host.cuh"
-#include "mlp_tc.cuh"
-#include "push_dev.cuh"
-#include "qed_host.cuh"
+#include "push_qed_dev.cuh"
 
 namespace pic {
 
@@ -26,20 +23,28 @@ namespace pic {
 // network has run; a live lane draws its emission numbers every step, so a
 // single evaluation yields both the rate and, if the event happens, the
 // energy fraction.
+//
+// first (optional, device): the particles below it are pushed by the tiled
+// kernel (the ones sorted into its work items); this launch takes the rest
+// (those appended since the sort) and owns their event flags.
 template <int DIM, bool SURR>
 __global__ void __launch_bounds__(256, SURR ? 2 : 1) k_push_qed_f32(PartF32 P, float *__restrict__ F, Grid g, PushConst pc,
-                                                      QedParams q, int *err, double *e_abs)
+                                                      QedParams q, int *err, double *e_abs,
+                                                      const uint32_t *__restrict__ first)
 {
     extern __shared__ __align__(16) unsigned char smem[];
+    const long long p0 = first ? (long long)*first : 0;
+    if ((long long)(blockIdx.x + 1) * blockDim.x <= p0) return;  // the whole block is the tiled kernel's
     if constexpr (SURR) {
         mlp_stage(smem, q.net, kMlpStageBytes);
         __syncthreads();
     }
     const long long p = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-    const bool live = p < *P.dn && P.cell[p] != kDead;
+    const bool mine = p >= p0;
+    const bool live = mine && p < *P.dn && P.cell[p] != kDead;
     if (!SURR || !__any_sync(0xffffffffu, live)) {
         if (!live) {
-            if (p <= P.n) q.ev[p] = 0;  // dead slots and slots past the live count (and the scan's end slot)
+            if (mine && p <= P.n) q.ev[p] = 0;  // dead slots and slots past the live count (and the scan's end slot)
             return;
         }
     }
@@ -72,79 +77,9 @@ __global__ void __launch_bounds__(256, SURR ? 2 : 1) k_push_qed_f32(PartF32 P, f
     // --- QED: optical depth, emission, recoil ---
     uint32_t event = 0;
     float4 evd = make_float4(0.f, 0.f, 0.f, 0.f);
-    if (q.on) {
-        // chi and the rate in FP32, gamma in FP64 above 1e4, tau in FP64
-        const float uuf = ux * ux + uy * uy + uz * uz;
-        const double uu = (double)ux * ux + (double)uy * uy + (double)uz * uz;
-        const double gam = uuf > 1e8f ? sqrt(1.0 + uu) : (double)sqrtf(1.0f + uuf);
-        const float chi = chi_f32((float)gam, ux, uy, uz, eb[0], eb[1], eb[2], eb[3], eb[4], eb[5], (float)q.inv_Es);
-        uint32_t w[4];
-        bool use_net = false;
-        float y0 = 0.f, y1 = 0.f;
-        if constexpr (SURR) {
-            float lnchi;
-            const bool inr = live && mlp_in_range_f32(q.nrm, chi, lnchi);
-            if (__any_sync(0xffffffffu, inr)) {
-                float x0 = 0.f, x1 = 0.f;
-                if (inr) {
-                    const uint64_t id = q.id[p];
-                    philox4x32_10((uint32_t)id, (uint32_t)(id >> 32), q.step, QP_EMIT, q.key[0], q.key[1], w);
-                    mlp_inputs_f32(q.nrm, QED_RAD, lnchi, (float)uniform24(w[0]), x0, x1);
-                }
-                mlp_eval_warp_sparse(*reinterpret_cast<const MlpImage *>(smem), inr, x0, x1, y0, y1);
-                use_net = inr;
-            }
-            if (!live) {
-                if (p <= P.n) q.ev[p] = 0;
-                return;
-            }
-        }
-        bool emit = false;
-        double frac = 0.0, tau = 0.0;
-        if (!SURR && q.method == 2) {
-            // Method II: u0 = r1^3 emitted when r2 < 3 r1^2 dW/du(u0) dt
-            const uint64_t id = q.id[p];
-            philox4x32_10((uint32_t)id, (uint32_t)(id >> 32), q.step, QP_EMIT, q.key[0], q.key[1], w);
-            const double r1 = uniform24(w[0]), r2 = uniform24(w[1]);
-            const double u0 = r1 * r1 * r1;
-            const double pacc = 3.0 * r1 * r1 * q.pref * qed_spec_rad(q.T, u0, (double)chi) / gam;
-            if (pacc > 1.0) atomicOr(err, ERR_QEDDT);
-            emit = r2 < pacc;
-            frac = u0;
-        } else {
-            const float G = use_net ? mlp_rate_f32(q.nrm, QED_RAD, chi, y1) : qed_rate_f32(q.T, QED_RAD, chi);
-            tau = q.tau[p] - (double)((float)q.pref * G / (float)gam);
-            if (tau <= 0.0) {
-                if (!use_net) {
-                    const uint64_t id = q.id[p];
-                    philox4x32_10((uint32_t)id, (uint32_t)(id >> 32), q.step, QP_EMIT, q.key[0], q.key[1], w);
-                }
-                const double r0 = uniform24(w[0]);
-                frac = use_net ? mlp_fraction(QED_RAD, y0, r0) : qed_sample<float>(q.T, QED_RAD, chi, r0);
-                tau = -log(uniform24(w[1]));
-                emit = true;
-            }
-        }
-        if (emit) {
-            const double eg = frac * gam;
-            const double umag = sqrt(uu);
-            const double g1 = fmax(gam * (1.0 - frac), 1.0);
-            const double s = umag > 0.0 ? sqrt(g1 * g1 - 1.0) / umag : 0.0;
-            const double kx = umag > 0.0 ? eg * ux / umag : 0.0, ky = umag > 0.0 ? eg * uy / umag : 0.0,
-                         kz = umag > 0.0 ? eg * uz / umag : 0.0;
-            ux = (float)(ux * s);
-            uy = (float)(uy * s);
-            uz = (float)(uz * s);
-            if (eg >= q.emin) {
-                event = 1;
-                evd = make_float4((float)kx, (float)ky, (float)kz, 0.f);
-            } else {
-                atomicAdd(q.e_lost, eg * q.wdV);
-            }
-        }
-        if (SURR || q.method != 2) q.tau[p] = tau;
-    } else if (SURR && !live) {
-        if (p <= P.n) q.ev[p] = 0;
+    qed_lepton_f32<SURR>(q, smem, live, p, eb, ux, uy, uz, err, event, evd);
+    if (SURR && !live) {
+        if (mine && p <= P.n) q.ev[p] = 0;
         return;
     }
     const float ig1 = inv_gamma(ux, uy, uz);
@@ -214,20 +149,24 @@ __global__ void __launch_bounds__(256, SURR ? 2 : 1) k_push_qed_f32(PartF32 P, f
 }
 
 // SURR: the pair network inside its chi range, as in k_push_qed_f32
+// (first: as in k_push_qed_f32 -- the photons below it are the tiled kernel's)
 template <int DIM, bool SURR>
 __global__ void __launch_bounds__(256, SURR ? 2 : 1) k_push_photon_f32(PartF32 P, const float *__restrict__ F, Grid g, PushConst pc,
-                                                         QedParams q, int *err)
+                                                         QedParams q, int *err, const uint32_t *__restrict__ first)
 {
     extern __shared__ __align__(16) unsigned char smem[];
+    const long long p0 = first ? (long long)*first : 0;
+    if ((long long)(blockIdx.x + 1) * blockDim.x <= p0) return;  // the whole block is the tiled kernel's
     if constexpr (SURR) {
         mlp_stage(smem, q.net, kMlpStageBytes);
         __syncthreads();
     }
     const long long p = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-    const bool live = p < *P.dn && P.cell[p] != kDead;
+    const bool mine = p >= p0;
+    const bool live = mine && p < *P.dn && P.cell[p] != kDead;
     if (!SURR || !__any_sync(0xffffffffu, live)) {
         if (!live) {
-            if (p <= P.n) q.ev[p] = 0;  // dead slots and slots past the live count (and the scan's end slot)
+            if (mine && p <= P.n) q.ev[p] = 0;  // dead slots and slots past the live count (and the scan's end slot)
             return;
         }
     }
@@ -257,60 +196,13 @@ __global__ void __launch_bounds__(256, SURR ? 2 : 1) k_push_photon_f32(PartF32 P
         for (int d = 0; d < DIM; d++) axis_w_f32(c[d], o[d], icn[d], wn[d], ich[d], wh[d]);
         float eb[6];
         gather<float, DIM>(F, g, icn, wn, ich, wh, eb);
-        const float chi = chi_f32(km, kx, ky, kz, eb[0], eb[1], eb[2], eb[3], eb[4], eb[5], (float)q.inv_Es);
-        uint32_t w[4];
-        bool use_net = false;
-        float y0 = 0.f, y1 = 0.f;
-        if constexpr (SURR) {
-            float lnchi;
-            const bool inr = live && km > 0.f && mlp_in_range_f32(q.nrm, chi, lnchi);
-            if (__any_sync(0xffffffffu, inr)) {
-                float x0 = 0.f, x1 = 0.f;
-                if (inr) {
-                    const uint64_t id = q.id[p];
-                    philox4x32_10((uint32_t)id, (uint32_t)(id >> 32), q.step, QP_PAIR, q.key[0], q.key[1], w);
-                    mlp_inputs_f32(q.nrm, QED_PAIR, lnchi, (float)uniform24(w[0]), x0, x1);
-                }
-                mlp_eval_warp_sparse(*reinterpret_cast<const MlpImage *>(smem), inr, x0, x1, y0, y1);
-                use_net = inr;
-            }
-            if (!live) {
-                if (p <= P.n) q.ev[p] = 0;
-                return;
-            }
-        }
-        if (!SURR && q.method == 2) {
-            // Method II for pairs: v0 = r1 accepted when r2 < dW_pair/dv(v0) dt
-            if (km > 0.f) {
-                const uint64_t id = q.id[p];
-                philox4x32_10((uint32_t)id, (uint32_t)(id >> 32), q.step, QP_PAIR, q.key[0], q.key[1], w);
-                const double r1 = uniform24(w[0]), r2 = uniform24(w[1]);
-                const double pacc = q.pref * qed_spec_pair(q.T, r1, (double)chi) / (double)km;
-                if (pacc > 1.0) atomicOr(err, ERR_QEDDT);
-                if (r2 < pacc) {
-                    event = 1;
-                    evd = make_float4(kx, ky, kz, (float)r1);
-                }
-            }
-        } else {
-            const float G = use_net ? mlp_rate_f32(q.nrm, QED_PAIR, chi, y1) : qed_rate_f32(q.T, QED_PAIR, chi);
-            double tau = q.tau[p] - (km > 0.f ? (double)((float)q.pref * G / km) : 0.0);
-            if (tau <= 0.0) {
-                if (!use_net) {
-                    const uint64_t id = q.id[p];
-                    philox4x32_10((uint32_t)id, (uint32_t)(id >> 32), q.step, QP_PAIR, q.key[0], q.key[1], w);
-                }
-                const double r0 = uniform24(w[0]);
-                const double vf =
-                    use_net ? mlp_fraction(QED_PAIR, y0, r0) : qed_sample<float>(q.T, QED_PAIR, chi, r0);
-                event = 1;
-                evd = make_float4(kx, ky, kz, (float)vf);
-                tau = -log(uniform24(w[1]));
-            }
-            q.tau[p] = tau;
+        qed_photon_f32<SURR>(q, smem, live, p, km, kx, ky, kz, eb, err, event, evd);
+        if (SURR && !live) {
+            if (mine && p <= P.n) q.ev[p] = 0;
+            return;
         }
     } else if (SURR && !live) {
-        if (p <= P.n) q.ev[p] = 0;
+        if (mine && p <= P.n) q.ev[p] = 0;
         return;
     }
 #pragma unroll
@@ -697,30 +589,30 @@ void launch_push_photon_f64(const PartF64 &P, const double *F, const Grid &g, co
 }
 
 void launch_push_qed_f32(const PartF32 &P, float *F, const Grid &g, const PushConst &pc, const QedParams &q,
-                         int *err, double *e_abs, cudaStream_t st)
+                         int *err, double *e_abs, cudaStream_t st, const uint32_t *first)
 {
     if (P.n == 0) return;
     note_launch();
     const int nb = div_up(P.n + 1, 256);
     if (q.on && q.net) {
         const int sm = kMlpStageBytes;
-        if (g.dim == 1) k_push_qed_f32<1, true><<<nb, 256, sm, st>>>(P, F, g, pc, q, err, e_abs);
-        else if (g.dim == 2) k_push_qed_f32<2, true><<<nb, 256, sm, st>>>(P, F, g, pc, q, err, e_abs);
-        else k_push_qed_f32<3, true><<<nb, 256, sm, st>>>(P, F, g, pc, q, err, e_abs);
+        if (g.dim == 1) k_push_qed_f32<1, true><<<nb, 256, sm, st>>>(P, F, g, pc, q, err, e_abs, first);
+        else if (g.dim == 2) k_push_qed_f32<2, true><<<nb, 256, sm, st>>>(P, F, g, pc, q, err, e_abs, first);
+        else k_push_qed_f32<3, true><<<nb, 256, sm, st>>>(P, F, g, pc, q, err, e_abs, first);
     } else {
-        if (g.dim == 1) k_push_qed_f32<1, false><<<nb, 256, 0, st>>>(P, F, g, pc, q, err, e_abs);
-        else if (g.dim == 2) k_push_qed_f32<2, false><<<nb, 256, 0, st>>>(P, F, g, pc, q, err, e_abs);
-        else k_push_qed_f32<3, false><<<nb, 256, 0, st>>>(P, F, g, pc, q, err, e_abs);
+        if (g.dim == 1) k_push_qed_f32<1, false><<<nb, 256, 0, st>>>(P, F, g, pc, q, err, e_abs, first);
+        else if (g.dim == 2) k_push_qed_f32<2, false><<<nb, 256, 0, st>>>(P, F, g, pc, q, err, e_abs, first);
+        else k_push_qed_f32<3, false><<<nb, 256, 0, st>>>(P, F, g, pc, q, err, e_abs, first);
     }
 }
 
 void launch_push_photon_f32(const PartF32 &P, const float *F, const Grid &g, const PushConst &pc,
-                            const QedParams &q, int *err, cudaStream_t st, bool tc)
+                            const QedParams &q, int *err, cudaStream_t st, bool tc, const uint32_t *first)
 {
     if (P.n == 0) return;
     note_launch();
     const int nb = div_up(P.n + 1, 256);
-    if (q.on && q.net && tc) {
+    if (q.on && q.net && tc && !first) {
         const int sm = (int)mlp_tc_smem_bytes();
         static bool attr = false;
         if (!attr) {
@@ -742,13 +634,13 @@ void launch_push_photon_f32(const PartF32 &P, const float *F, const Grid &g, con
         else k_push_photon_tc<3><<<grid, kMlpTcRows, sm, st>>>(P, F, g, pc, q, err);
     } else if (q.on && q.net) {
         const int sm = kMlpStageBytes;
-        if (g.dim == 1) k_push_photon_f32<1, true><<<nb, 256, sm, st>>>(P, F, g, pc, q, err);
-        else if (g.dim == 2) k_push_photon_f32<2, true><<<nb, 256, sm, st>>>(P, F, g, pc, q, err);
-        else k_push_photon_f32<3, true><<<nb, 256, sm, st>>>(P, F, g, pc, q, err);
+        if (g.dim == 1) k_push_photon_f32<1, true><<<nb, 256, sm, st>>>(P, F, g, pc, q, err, first);
+        else if (g.dim == 2) k_push_photon_f32<2, true><<<nb, 256, sm, st>>>(P, F, g, pc, q, err, first);
+        else k_push_photon_f32<3, true><<<nb, 256, sm, st>>>(P, F, g, pc, q, err, first);
     } else {
-        if (g.dim == 1) k_push_photon_f32<1, false><<<nb, 256, 0, st>>>(P, F, g, pc, q, err);
-        else if (g.dim == 2) k_push_photon_f32<2, false><<<nb, 256, 0, st>>>(P, F, g, pc, q, err);
-        else k_push_photon_f32<3, false><<<nb, 256, 0, st>>>(P, F, g, pc, q, err);
+        if (g.dim == 1) k_push_photon_f32<1, false><<<nb, 256, 0, st>>>(P, F, g, pc, q, err, first);
+        else if (g.dim == 2) k_push_photon_f32<2, false><<<nb, 256, 0, st>>>(P, F, g, pc, q, err, first);
+        else k_push_photon_f32<3, false><<<nb, 256, 0, st>>>(P, F, g, pc, q, err, first);
     }
 }
 

@@ -1,0 +1,157 @@
+// push_qed_dev.cuh -- the QED Monte Carlo of one lepton after its momentum
+// update (Sec. IV), shared by the one-thread-per-particle push and the tiled
+// push: chi from the gathered E, B and u^{n+1} (FP32; gamma in FP64 above
+// u^2 = 1e8), the rate from the tables or, inside its chi range, the
+// surrogate network; Method I in the optical-depth form (tau in FP64) or
+// Method II (per-step acceptance).  On an event the photon momentum goes to
+// evd (event = 1 when it is heavy enough to be kept, else its energy is
+// tallied) and the lepton recoils to gamma (1 - u) along its direction.
+#pragma once
+
+#include "mlp_host.cuh"
+#include "mlp_tc.cuh"
+#include "push_dev.cuh"
+#include "qed_host.cuh"
+
+namespace pic {
+
+// With SURR the call is warp-collective: every lane of the warp makes it
+// (lanes with live false only take part in the network's evaluation);
+// mlp_smem is the staged network image.  p indexes the QED arrays.
+template <bool SURR>
+__device__ __forceinline__ void qed_lepton_f32(const QedParams &q, const unsigned char *mlp_smem, bool live,
+                                               long long p, const float *eb, float &ux, float &uy, float &uz,
+                                               int *err, uint32_t &event, float4 &evd)
+{
+    if (!q.on) return;
+    // chi and the rate in FP32, gamma in FP64 above 1e4, tau in FP64
+    const float uuf = ux * ux + uy * uy + uz * uz;
+    const double uu = (double)ux * ux + (double)uy * uy + (double)uz * uz;
+    const double gam = uuf > 1e8f ? sqrt(1.0 + uu) : (double)sqrtf(1.0f + uuf);
+    const float chi = chi_f32((float)gam, ux, uy, uz, eb[0], eb[1], eb[2], eb[3], eb[4], eb[5], (float)q.inv_Es);
+    uint32_t w[4];
+    bool use_net = false;
+    float y0 = 0.f, y1 = 0.f;
+    if constexpr (SURR) {
+        float lnchi;
+        const bool inr = live && mlp_in_range_f32(q.nrm, chi, lnchi);
+        if (__any_sync(0xffffffffu, inr)) {
+            float x0 = 0.f, x1 = 0.f;
+            if (inr) {
+                const uint64_t id = q.id[p];
+                philox4x32_10((uint32_t)id, (uint32_t)(id >> 32), q.step, QP_EMIT, q.key[0], q.key[1], w);
+                mlp_inputs_f32(q.nrm, QED_RAD, lnchi, (float)uniform24(w[0]), x0, x1);
+            }
+            mlp_eval_warp_sparse(*reinterpret_cast<const MlpImage *>(mlp_smem), inr, x0, x1, y0, y1);
+            use_net = inr;
+        }
+        if (!live) return;
+    }
+    bool emit = false;
+    double frac = 0.0, tau = 0.0;
+    if (!SURR && q.method == 2) {
+        // Method II: u0 = r1^3 emitted when r2 < 3 r1^2 dW/du(u0) dt
+        const uint64_t id = q.id[p];
+        philox4x32_10((uint32_t)id, (uint32_t)(id >> 32), q.step, QP_EMIT, q.key[0], q.key[1], w);
+        const double r1 = uniform24(w[0]), r2 = uniform24(w[1]);
+        const double u0 = r1 * r1 * r1;
+        const double pacc = 3.0 * r1 * r1 * q.pref * qed_spec_rad(q.T, u0, (double)chi) / gam;
+        if (pacc > 1.0) atomicOr(err, ERR_QEDDT);
+        emit = r2 < pacc;
+        frac = u0;
+    } else {
+        const float G = use_net ? mlp_rate_f32(q.nrm, QED_RAD, chi, y1) : qed_rate_f32(q.T, QED_RAD, chi);
+        tau = q.tau[p] - (double)((float)q.pref * G / (float)gam);
+        if (tau <= 0.0) {
+            if (!use_net) {
+                const uint64_t id = q.id[p];
+                philox4x32_10((uint32_t)id, (uint32_t)(id >> 32), q.step, QP_EMIT, q.key[0], q.key[1], w);
+            }
+            const double r0 = uniform24(w[0]);
+            frac = use_net ? mlp_fraction(QED_RAD, y0, r0) : qed_sample<float>(q.T, QED_RAD, chi, r0);
+            tau = -log(uniform24(w[1]));
+            emit = true;
+        }
+    }
+    if (emit) {
+        const double eg = frac * gam;
+        const double umag = sqrt(uu);
+        const double g1 = fmax(gam * (1.0 - frac), 1.0);
+        const double s = umag > 0.0 ? sqrt(g1 * g1 - 1.0) / umag : 0.0;
+        const double kx = umag > 0.0 ? eg * ux / umag : 0.0, ky = umag > 0.0 ? eg * uy / umag : 0.0,
+                     kz = umag > 0.0 ? eg * uz / umag : 0.0;
+        ux = (float)(ux * s);
+        uy = (float)(uy * s);
+        uz = (float)(uz * s);
+        if (eg >= q.emin) {
+            event = 1;
+            evd = make_float4((float)kx, (float)ky, (float)kz, 0.f);
+        } else {
+            atomicAdd(q.e_lost, eg * q.wdV);
+        }
+    }
+    if (SURR || q.method != 2) q.tau[p] = tau;
+}
+
+// The pair-creation Monte Carlo of one photon (Sec. IV): chi_gamma from k and
+// the gathered E, B at x^{n+1/2}; W_pair from the tables or the surrogate
+// network inside its chi range; Method I (optical depth, FP64) or Method II.
+// On a conversion evd = (k, positron fraction v) and event = 1.  With SURR
+// the call is warp-collective as qed_lepton_f32's.
+template <bool SURR>
+__device__ __forceinline__ void qed_photon_f32(const QedParams &q, const unsigned char *mlp_smem, bool live,
+                                               long long p, float km, float kx, float ky, float kz, const float *eb,
+                                               int *err, uint32_t &event, float4 &evd)
+{
+    const float chi = chi_f32(km, kx, ky, kz, eb[0], eb[1], eb[2], eb[3], eb[4], eb[5], (float)q.inv_Es);
+    uint32_t w[4];
+    bool use_net = false;
+    float y0 = 0.f, y1 = 0.f;
+    if constexpr (SURR) {
+        float lnchi;
+        const bool inr = live && km > 0.f && mlp_in_range_f32(q.nrm, chi, lnchi);
+        if (__any_sync(0xffffffffu, inr)) {
+            float x0 = 0.f, x1 = 0.f;
+            if (inr) {
+                const uint64_t id = q.id[p];
+                philox4x32_10((uint32_t)id, (uint32_t)(id >> 32), q.step, QP_PAIR, q.key[0], q.key[1], w);
+                mlp_inputs_f32(q.nrm, QED_PAIR, lnchi, (float)uniform24(w[0]), x0, x1);
+            }
+            mlp_eval_warp_sparse(*reinterpret_cast<const MlpImage *>(mlp_smem), inr, x0, x1, y0, y1);
+            use_net = inr;
+        }
+        if (!live) return;
+    }
+    if (!SURR && q.method == 2) {
+        // Method II for pairs: v0 = r1 accepted when r2 < dW_pair/dv(v0) dt
+        if (km > 0.f) {
+            const uint64_t id = q.id[p];
+            philox4x32_10((uint32_t)id, (uint32_t)(id >> 32), q.step, QP_PAIR, q.key[0], q.key[1], w);
+            const double r1 = uniform24(w[0]), r2 = uniform24(w[1]);
+            const double pacc = q.pref * qed_spec_pair(q.T, r1, (double)chi) / (double)km;
+            if (pacc > 1.0) atomicOr(err, ERR_QEDDT);
+            if (r2 < pacc) {
+                event = 1;
+                evd = make_float4(kx, ky, kz, (float)r1);
+            }
+        }
+    } else {
+        const float G = use_net ? mlp_rate_f32(q.nrm, QED_PAIR, chi, y1) : qed_rate_f32(q.T, QED_PAIR, chi);
+        double tau = q.tau[p] - (km > 0.f ? (double)((float)q.pref * G / km) : 0.0);
+        if (tau <= 0.0) {
+            if (!use_net) {
+                const uint64_t id = q.id[p];
+                philox4x32_10((uint32_t)id, (uint32_t)(id >> 32), q.step, QP_PAIR, q.key[0], q.key[1], w);
+            }
+            const double r0 = uniform24(w[0]);
+            const double vf =
+                use_net ? mlp_fraction(QED_PAIR, y0, r0) : qed_sample<float>(q.T, QED_PAIR, chi, r0);
+            event = 1;
+            evd = make_float4(kx, ky, kz, (float)vf);
+            tau = -log(uniform24(w[1]));
+        }
+        q.tau[p] = tau;
+    }
+}
+
+}  // namespace pic

@@ -15,6 +15,7 @@
 // result does not depend on the sort interval.
 #include <cstring>
 
+#include "push_qed_dev.cuh"
 #include "push_tile_dev.cuh"
 #include "tma.cuh"
 
@@ -137,21 +138,32 @@ struct AccWarp {
 // and lanes with the same deposit window are summed before one atomic per
 // value).  Without AGG lane l walks the l-th of 32 contiguous segments, so
 // the lanes of an atomic hit different cells.
-template <int T, bool AGG>
-__global__ void __launch_bounds__(kTileThreads, kTileMinBlocks)
+//
+// QM (QED leptons): 1 = the Monte Carlo of Sec. IV with the
+// tables (Method I or II), 2 = with the surrogate network inside its chi
+// range (its image staged after the boxes); between the momentum update and
+// the drifts, as in the one-thread-per-particle QED push.  The event flag
+// of every particle of the items is written (0 for dead ones); particles
+// appended after the sort are left to that kernel.
+template <int T, bool AGG, int QM>
+__global__ void __launch_bounds__(kTileThreads, QM == 2 ? 3 : kTileMinBlocks)
     k_push_tile2d(PartF32 P, const TileItem *__restrict__ items, const uint32_t *__restrict__ nitems,
                   float *__restrict__ F, Grid g, PushConst pc, int *err, double *e_abs,
-                  const __grid_constant__ CUtensorMap tmap, int use_tma)
+                  const __grid_constant__ CUtensorMap tmap, int use_tma, QedParams q)
 {
     using B = Box2<T>;
-    extern __shared__ float smem_raw[];
+    extern __shared__ __align__(16) float smem_raw[];
     __shared__ uint64_t mbar;
     // the TMA destination starts on a 128-byte boundary
-    float *smem = reinterpret_cast<float *>((reinterpret_cast<uintptr_t>(smem_raw) + 127) & ~uintptr_t(127));
+    // (offset from the shared array itself, so that the compiler keeps every
+    // access below in the shared address space)
+    float *smem = smem_raw + ((128u - ((uint32_t)__cvta_generic_to_shared(smem_raw) & 127u)) & 127u) / 4u;
     float *sF = smem;           // 6 components
     int *sJ = reinterpret_cast<int *>(smem + 6 * B::N);  // 3 components, fixed point
     float *sP = smem + 9 * B::N;                          // off_x, off_y, u_x, u_y, u_z
     uint32_t *sPc = reinterpret_cast<uint32_t *>(sP + 5 * kPSlot);  // packed cell
+    unsigned char *sNet = reinterpret_cast<unsigned char *>(smem) + ((B::SMEM + 15) & ~15);  // QM == 2: the network
+    if constexpr (QM == 2) mlp_stage(sNet, q.net, kMlpStageBytes);
     const int nit = (int)*nitems;
     const long long V = g.vol;
     const float hdx0 = pc.hdx_f[0], hdx1 = pc.hdx_f[1];
@@ -180,16 +192,16 @@ __global__ void __launch_bounds__(kTileThreads, kTileMinBlocks)
                 tma_load_3d(sF, &tmap, bx0 + g.G[0], by0 + g.G[1], 0, &mbar);
             }
         } else {
-            for (int q = threadIdx.x; q < 6 * B::N; q += blockDim.x) {
-                const int c = q / B::N, r = q - c * B::N;
+            for (int e = threadIdx.x; e < 6 * B::N; e += blockDim.x) {
+                const int c = e / B::N, r = e - c * B::N;
                 const int y = r / B::WX, x = r - y * B::WX;
                 const int gx = bx0 + x, gy = by0 + y;
                 float v = 0.f;
                 if (gx < g.n[0] + g.G[0] && gy < g.n[1] + g.G[1]) v = __ldg(Fg + c * V + (long long)gy * rs + gx);
-                sF[q] = v;
+                sF[e] = v;
             }
         }
-        for (int q = threadIdx.x; q < 3 * B::N; q += blockDim.x) sJ[q] = 0;
+        for (int e = threadIdx.x; e < 3 * B::N; e += blockDim.x) sJ[e] = 0;
         // Lane striding: the chunk is cut into 32 contiguous segments of S
         // particles and lane l of every warp walks segment l.  Sorted
         // particles of one cell are contiguous, so the 32 lanes of one
@@ -241,33 +253,45 @@ __global__ void __launch_bounds__(kTileThreads, kTileMinBlocks)
             const uint32_t cp = li < m.count ? sPc[pos] : kDead;
             bool act = cp != kDead;  // a live particle of this item
             int c[2] = {0, 0}, c1[2] = {0, 0}, u0[2] = {0, 0};
-            float o1[2] = {0.f, 0.f};
+            float o[2] = {0.f, 0.f}, o1[2] = {0.f, 0.f};
             float ux = 0.f, uy = 0.f, uz = 0.f, ig1 = 0.f;
             float S0[2][4], dS[2][4];
+            int ch[2] = {0, 0};
+            float oh[2] = {0.f, 0.f};
+            float eb[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
             bool ok = true;
             if (act) {
                 int dummy;
                 unpack_cell(g, cp, c[0], c[1], dummy);
-                float o[2] = {sP[pos], sP[kPSlot + pos]};
+                o[0] = sP[pos];
+                o[1] = sP[kPSlot + pos];
                 ux = sP[2 * kPSlot + pos];
                 uy = sP[3 * kPSlot + pos];
                 uz = sP[4 * kPSlot + pos];
                 float ig = inv_gamma_fast(ux, uy, uz);
                 drift_f32(c[0], o[0], hdx0 * ux * ig);
                 drift_f32(c[1], o[1], hdx1 * uy * ig);
-                const int ch[2] = {c[0], c[1]};
-                const float oh[2] = {o[0], o[1]};
+                ch[0] = c[0];
+                ch[1] = c[1];
+                oh[0] = o[0];
+                oh[1] = o[1];
                 int icn[2], ich[2];
                 float wn[2][3], wh[2][3];
                 axis_w_f32(c[0], o[0], icn[0], wn[0], ich[0], wh[0]);
                 axis_w_f32(c[1], o[1], icn[1], wn[1], ich[1], wh[1]);
-                float eb[6];
                 const bool gin =
                     ch[0] - 1 >= bx0 && ch[0] + 2 < bx0 + B::WX && ch[1] - 1 >= by0 && ch[1] + 2 < by0 + B::WY;
                 if (gin) gather2d(sF, B::N, B::WX, bx0, by0, icn, wn, ich, wh, eb);
                 else gather2d(Fg, V, rs, 0, 0, icn, wn, ich, wh, eb);
                 if (pc.pusher) vay<float>(ux, uy, uz, k * eb[0], k * eb[1], k * eb[2], k * eb[3], k * eb[4], k * eb[5]);
                 else boris_fast(ux, uy, uz, k * eb[0], k * eb[1], k * eb[2], k * eb[3], k * eb[4], k * eb[5]);
+            }
+            // QED (every lane of the warp: the network's evaluation is collective)
+            const long long pg = (long long)m.start + li;
+            uint32_t event = 0;
+            float4 evd = make_float4(0.f, 0.f, 0.f, 0.f);
+            if constexpr (QM != 0) qed_lepton_f32<QM == 2>(q, sNet, act, pg, eb, ux, uy, uz, err, event, evd);
+            if (act) {
                 ig1 = inv_gamma_fast(ux, uy, uz);
                 const float d0 = hdx0 * ux * ig1, d1 = hdx1 * uy * ig1;
                 drift_f32(c[0], o[0], d0);
@@ -319,7 +343,10 @@ __global__ void __launch_bounds__(kTileThreads, kTileMinBlocks)
                 AccShared acc{sJ + (u0[1] - by0) * B::WX + (u0[0] - bx0), B::N, B::WX, jscale};
                 esirkepov2d(S0, dS, cjx, cjy, jvz, acc);
             }
-            if (!act) continue;
+            if (!act) {
+                if (QM != 0 && li < m.count) q.ev[pg] = 0;
+                continue;
+            }
             // boundaries
             int cc[2] = {c1[0], c1[1]};
             bool dead = false;
@@ -336,8 +363,13 @@ __global__ void __launch_bounds__(kTileThreads, kTileMinBlocks)
                 sPc[pos] = kDead;
                 double uu = (double)ux * ux + (double)uy * uy + (double)uz * uz;
                 atomicAdd(e_abs, pc.wmdV * uu / (sqrt(1.0 + uu) + 1.0));
+                event = 0;  // an emitter absorbed in the same step records no photon
             } else {
                 sPc[pos] = pack_cell(g, cc[0], cc[1], 0);
+            }
+            if constexpr (QM != 0) {
+                q.ev[pg] = event;
+                if (event) reinterpret_cast<float4 *>(q.evk)[pg] = evd;
             }
             // the new state goes back to the particle's own staging slot and
             // leaves in array order below: lane-strided global stores would
@@ -363,11 +395,11 @@ __global__ void __launch_bounds__(kTileThreads, kTileMinBlocks)
             P.u[2][p] = sP[4 * kPSlot + pos];
         }
         // 4b. flush the current box, four values at a time
-        for (int q = threadIdx.x; q < 3 * B::N / 4; q += blockDim.x) {
-            const int4 iv = reinterpret_cast<const int4 *>(sJ)[q];
+        for (int v4 = threadIdx.x; v4 < 3 * B::N / 4; v4 += blockDim.x) {
+            const int4 iv = reinterpret_cast<const int4 *>(sJ)[v4];
             if ((iv.x | iv.y | iv.z | iv.w) == 0) continue;
             const float4 v = make_float4(iv.x * junit, iv.y * junit, iv.z * junit, iv.w * junit);
-            const int e = 4 * q;
+            const int e = 4 * v4;
             const int c = e / B::N, r = e - c * B::N;
             const int y = r / B::WX, x = r - y * B::WX;
             const int gx = bx0 + x, gy = by0 + y;
@@ -384,6 +416,139 @@ __global__ void __launch_bounds__(kTileThreads, kTileMinBlocks)
             atomicAdd(reinterpret_cast<float4 *>(Fg + (JX + c) * V + (long long)gy * rs + gx), v);
         }
         __syncthreads();
+    }
+}
+
+// ---------------------------------------------------------------------
+// Tiled photon push (2D, FP32).  Photons carry no current, so a work item
+// only stages its tile's field box (one TMA copy) and walks its photons with
+// consecutive lanes on consecutive photons: the particle traffic is
+// coalesced and the gathers of photons of one cell are shared-memory
+// broadcasts.  Each photon moves at c along k, its pair Monte Carlo is
+// qed_photon_f32 (as in the one-thread-per-particle photon push), event
+// flags are written for every photon of the items; photons appended since
+// the sort are left to that kernel.  SURR: the pair network inside its chi
+// range (its image after the field box).
+// ---------------------------------------------------------------------
+template <int T, bool SURR>
+__global__ void __launch_bounds__(kTileThreads, SURR ? 3 : kTileMinBlocks)
+    k_push_photon_tile2d(PartF32 P, const TileItem *__restrict__ items, const uint32_t *__restrict__ nitems,
+                         const float *__restrict__ F, Grid g, PushConst pc, int *err,
+                         const __grid_constant__ CUtensorMap tmap, int use_tma, QedParams q)
+{
+    using B = Box2<T>;
+    extern __shared__ __align__(16) float smem_raw[];
+    __shared__ uint64_t mbar;
+    float *smem = smem_raw + ((128u - ((uint32_t)__cvta_generic_to_shared(smem_raw) & 127u)) & 127u) / 4u;
+    float *sF = smem;  // 6 components
+    unsigned char *sNet = reinterpret_cast<unsigned char *>(smem) + ((6 * B::N * (int)sizeof(float) + 15) & ~15);
+    if constexpr (SURR) mlp_stage(sNet, q.net, kMlpStageBytes);
+    const int nit = (int)*nitems;
+    const long long V = g.vol;
+    const float *Fg = F + g.origin;
+    const int rs = (int)g.sy;
+    const float hdx0 = pc.hdx_f[0], hdx1 = pc.hdx_f[1];
+    if (use_tma && threadIdx.x == 0) mbar_init(&mbar, 1);
+    __syncthreads();
+    uint32_t phase = 0;
+    for (int it = blockIdx.x; it < nit; it += gridDim.x) {
+        const TileItem m = items[it];
+        const int tx = m.tile % g.ntile[0], ty = m.tile / g.ntile[0];
+        const int bx0 = tx * T - 4, by0 = ty * T - 4;
+        if (use_tma) {
+            if (threadIdx.x == 0) {
+                fence_proxy_async_smem();
+                mbar_arrive_expect_tx(&mbar, 6 * B::N * (int)sizeof(float));
+                tma_load_3d(sF, &tmap, bx0 + g.G[0], by0 + g.G[1], 0, &mbar);
+            }
+        } else {
+            for (int e = threadIdx.x; e < 6 * B::N; e += blockDim.x) {
+                const int c = e / B::N, r = e - c * B::N;
+                const int y = r / B::WX, x = r - y * B::WX;
+                const int gx = bx0 + x, gy = by0 + y;
+                float v = 0.f;
+                if (gx < g.n[0] + g.G[0] && gy < g.n[1] + g.G[1]) v = __ldg(Fg + c * V + (long long)gy * rs + gx);
+                sF[e] = v;
+            }
+        }
+        bool landed = true;
+        if (use_tma) {
+            landed = mbar_wait(&mbar, phase, 1 << 22);
+            phase ^= 1u;
+        }
+        if (__syncthreads_or(!landed)) {
+            if (threadIdx.x == 0) atomicOr(err, ERR_TIMEOUT);
+            return;
+        }
+        // warp-uniform passes (the network's evaluation is warp-collective)
+        const int npass = (m.count + kTileThreads - 1) / kTileThreads;
+        for (int pass = 0; pass < npass; pass++) {
+            const int li = pass * kTileThreads + threadIdx.x;
+            const long long p = (long long)m.start + li;
+            const uint32_t cp = li < m.count ? P.cell[p] : kDead;
+            const bool live = cp != kDead;
+            int c[2] = {0, 0};
+            float o[2] = {0.f, 0.f};
+            float kx = 0.f, ky = 0.f, kz = 0.f;
+            if (live) {
+                int dummy;
+                unpack_cell(g, cp, c[0], c[1], dummy);
+                o[0] = P.off[0][p];
+                o[1] = P.off[1][p];
+                kx = P.u[0][p];
+                ky = P.u[1][p];
+                kz = P.u[2][p];
+            }
+            const float km = sqrtf(kx * kx + ky * ky + kz * kz);
+            const float ik = km > 0.f ? 1.0f / km : 0.f;
+            const float d0 = hdx0 * kx * ik, d1 = hdx1 * ky * ik;
+            drift_f32(c[0], o[0], d0);
+            drift_f32(c[1], o[1], d1);
+            uint32_t event = 0;
+            float4 evd = make_float4(0.f, 0.f, 0.f, 0.f);
+            if (q.on) {
+                float eb[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+                if (live) {
+                    int icn[2], ich[2];
+                    float wn[2][3], wh[2][3];
+                    axis_w_f32(c[0], o[0], icn[0], wn[0], ich[0], wh[0]);
+                    axis_w_f32(c[1], o[1], icn[1], wn[1], ich[1], wh[1]);
+                    const bool gin =
+                        c[0] - 1 >= bx0 && c[0] + 2 < bx0 + B::WX && c[1] - 1 >= by0 && c[1] + 2 < by0 + B::WY;
+                    if (gin) gather2d(sF, B::N, B::WX, bx0, by0, icn, wn, ich, wh, eb);
+                    else gather2d(Fg, V, rs, 0, 0, icn, wn, ich, wh, eb);
+                }
+                qed_photon_f32<SURR>(q, sNet, live, p, km, kx, ky, kz, eb, err, event, evd);
+            }
+            if (li >= m.count) continue;
+            if (!live) {
+                q.ev[p] = 0;
+                continue;
+            }
+            drift_f32(c[0], o[0], d0);
+            drift_f32(c[1], o[1], d1);
+            bool dead = false;
+#pragma unroll
+            for (int d = 0; d < 2; d++) {
+                if (g.bc[d] == PERIODIC) {
+                    if (c[d] < 0) c[d] += g.n[d];
+                    else if (c[d] >= g.n[d]) c[d] -= g.n[d];
+                } else if (c[d] < 0 || c[d] >= g.n[d]) {
+                    dead = true;
+                }
+            }
+            if (dead) {
+                P.cell[p] = kDead;
+                event = 0;  // a photon leaving through an absorbing face does not convert
+            } else {
+                P.cell[p] = pack_cell(g, c[0], c[1], 0);
+            }
+            P.off[0][p] = o[0];
+            P.off[1][p] = o[1];
+            q.ev[p] = event;
+            if (event) reinterpret_cast<float4 *>(q.evk)[p] = evd;
+        }
+        __syncthreads();  // the next item's copy overwrites the box
     }
 }
 
@@ -444,14 +609,15 @@ bool tile_push_supported(const Grid &g, int tile_edge)
     return g.dim == 2 && (1 << g.tile_log2[0]) == tile_edge && (1 << g.tile_log2[1]) == tile_edge;
 }
 
-template <int T, bool AGG>
+template <int T, bool AGG, int QM>
 static void launch_T(const PartF32 &P, const TileItem *items, const uint32_t *nitems, long long max_items, float *F,
-                     const Grid &g, const PushConst &pc, int *err, double *e_abs, cudaStream_t st)
+                     const Grid &g, const PushConst &pc, int *err, double *e_abs, cudaStream_t st, const QedParams &q)
 {
-    constexpr int smem = Box2<T>::SMEM + 128;  // + alignment of the TMA destination
+    // + alignment of the TMA destination (+ the network image)
+    constexpr int smem = ((Box2<T>::SMEM + 15) & ~15) + 128 + (QM == 2 ? kMlpStageBytes : 0);
     static bool attr = false;
     if (!attr) {
-        cudaFuncSetAttribute(k_push_tile2d<T, AGG>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+        cudaFuncSetAttribute(k_push_tile2d<T, AGG, QM>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
         attr = true;
     }
     static int nsm = 0;
@@ -466,25 +632,84 @@ static void launch_T(const PartF32 &P, const TileItem *items, const uint32_t *ni
     const int box[3] = {Box2<T>::WX, Box2<T>::WY, 6};
     const bool tma = tma_encode_field_map(&tmap, F, g.ext[0], g.ext[1], g.sy, g.vol, 6, box);
     if (!tma) memset(&tmap, 0, sizeof tmap);
-    long long grid = std::min<long long>(max_items, (long long)nsm * kTileMinBlocks);  // one resident wave
+    static int per_sm = 0;  // resident CTAs per SM
+    if (!per_sm) {
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_push_tile2d<T, AGG, QM>, kTileThreads, smem);
+        if (per_sm < 1) per_sm = 1;
+    }
+    long long grid = std::min<long long>(max_items, (long long)nsm * per_sm);  // one resident wave
     if (grid < 1) grid = 1;
     note_launch();
-    k_push_tile2d<T, AGG><<<(int)grid, kTileThreads, smem, st>>>(P, items, nitems, F, g, pc, err, e_abs, tmap,
-                                                                tma ? 1 : 0);
+    k_push_tile2d<T, AGG, QM><<<(int)grid, kTileThreads, smem, st>>>(P, items, nitems, F, g, pc, err, e_abs, tmap,
+                                                                    tma ? 1 : 0, q);
+}
+
+template <int T>
+static void launch_variant(const PartF32 &P, const TileItem *items, const uint32_t *nitems, long long max_items,
+                           float *F, const Grid &g, const PushConst &pc, int *err, double *e_abs, cudaStream_t st,
+                           bool agg, const QedParams *q)
+{
+    if (q && q->on) {
+        if (q->net) launch_T<T, false, 2>(P, items, nitems, max_items, F, g, pc, err, e_abs, st, *q);
+        else launch_T<T, false, 1>(P, items, nitems, max_items, F, g, pc, err, e_abs, st, *q);
+        return;
+    }
+    const QedParams none{};
+    if (agg) launch_T<T, true, 0>(P, items, nitems, max_items, F, g, pc, err, e_abs, st, none);
+    else launch_T<T, false, 0>(P, items, nitems, max_items, F, g, pc, err, e_abs, st, none);
 }
 
 void launch_push_tile2d(const PartF32 &P, const TileItem *items, const uint32_t *nitems, long long max_items,
                         float *F, const Grid &g, const PushConst &pc, int *err, double *e_abs, cudaStream_t st,
-                        bool agg)
+                        bool agg, const QedParams *q)
 {
     if (P.n == 0) return;
-    int T = 1 << g.tile_log2[0];
-    if (agg) {
-        if (T == 16) launch_T<16, true>(P, items, nitems, max_items, F, g, pc, err, e_abs, st);
-        else launch_T<8, true>(P, items, nitems, max_items, F, g, pc, err, e_abs, st);
+    if ((1 << g.tile_log2[0]) == 16) launch_variant<16>(P, items, nitems, max_items, F, g, pc, err, e_abs, st, agg, q);
+    else launch_variant<8>(P, items, nitems, max_items, F, g, pc, err, e_abs, st, agg, q);
+}
+
+template <int T, bool SURR>
+static void launch_photon_T(const PartF32 &P, const TileItem *items, const uint32_t *nitems, long long max_items,
+                            const float *F, const Grid &g, const PushConst &pc, int *err, cudaStream_t st,
+                            const QedParams &q)
+{
+    constexpr int smem = ((6 * Box2<T>::N * (int)sizeof(float) + 15) & ~15) + 128 + (SURR ? kMlpStageBytes : 0);
+    static bool attr = false;
+    if (!attr) {
+        cudaFuncSetAttribute(k_push_photon_tile2d<T, SURR>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+        attr = true;
+    }
+    static int nsm = 0, per_sm = 0;
+    if (!nsm) {
+        int dev = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_push_photon_tile2d<T, SURR>, kTileThreads, smem);
+        if (per_sm < 1) per_sm = 1;
+    }
+    CUtensorMap tmap;
+    const int box[3] = {Box2<T>::WX, Box2<T>::WY, 6};
+    const bool tma = tma_encode_field_map(&tmap, const_cast<float *>(F), g.ext[0], g.ext[1], g.sy, g.vol, 6, box);
+    if (!tma) memset(&tmap, 0, sizeof tmap);
+    long long grid = std::min<long long>(max_items, (long long)nsm * per_sm);
+    if (grid < 1) grid = 1;
+    note_launch();
+    k_push_photon_tile2d<T, SURR><<<(int)grid, kTileThreads, smem, st>>>(P, items, nitems, F, g, pc, err, tmap,
+                                                                         tma ? 1 : 0, q);
+}
+
+void launch_push_photon_tile2d(const PartF32 &P, const TileItem *items, const uint32_t *nitems, long long max_items,
+                               const float *F, const Grid &g, const PushConst &pc, const QedParams &q, int *err,
+                               cudaStream_t st)
+{
+    if (P.n == 0) return;
+    const bool surr = q.on && q.net;
+    if ((1 << g.tile_log2[0]) == 16) {
+        if (surr) launch_photon_T<16, true>(P, items, nitems, max_items, F, g, pc, err, st, q);
+        else launch_photon_T<16, false>(P, items, nitems, max_items, F, g, pc, err, st, q);
     } else {
-        if (T == 16) launch_T<16, false>(P, items, nitems, max_items, F, g, pc, err, e_abs, st);
-        else launch_T<8, false>(P, items, nitems, max_items, F, g, pc, err, e_abs, st);
+        if (surr) launch_photon_T<8, true>(P, items, nitems, max_items, F, g, pc, err, st, q);
+        else launch_photon_T<8, false>(P, items, nitems, max_items, F, g, pc, err, st, q);
     }
 }
 

@@ -129,10 +129,12 @@ __global__ void __launch_bounds__(kTileThreads, 5)
                   uint32_t *ndefer, const __grid_constant__ CUtensorMap tmap, int use_tma)
 {
     using B = Box3<T>;
-    extern __shared__ float smem_raw[];
+    extern __shared__ __align__(16) float smem_raw[];
     __shared__ uint64_t mbar;
     // the TMA destination starts on a 128-byte boundary
-    float *smem = reinterpret_cast<float *>((reinterpret_cast<uintptr_t>(smem_raw) + 127) & ~uintptr_t(127));
+    // (offset from the shared array itself, so that the compiler keeps every
+    // access below in the shared address space)
+    float *smem = smem_raw + ((128u - ((uint32_t)__cvta_generic_to_shared(smem_raw) & 127u)) & 127u) / 4u;
     float *sF = smem;                                    // 6 components
     int *sJ = reinterpret_cast<int *>(smem + 6 * B::N);  // 3 components, fixed point
     const int nit = (int)*nitems;

@@ -30,11 +30,14 @@ void launch_push_qed_f64(const PartF64 &P, double *F, const Grid &g, const PushC
                          int *err, double *e_abs, cudaStream_t st);
 void launch_push_photon_f64(const PartF64 &P, const double *F, const Grid &g, const PushConst &pc,
                             const QedParams &q, int *err, cudaStream_t st);
+// (first: see k_push_qed_f32 -- nullptr pushes every particle)
 void launch_push_qed_f32(const PartF32 &P, float *F, const Grid &g, const PushConst &pc, const QedParams &q,
-                         int *err, double *e_abs, cudaStream_t st);
+                         int *err, double *e_abs, cudaStream_t st, const uint32_t *first = nullptr);
 // (tc: with the surrogate, evaluate the pair network per CTA on the tcgen05
 // tensor cores instead of per warp with mma.sync)
+// (first: see k_push_photon_f32 -- nullptr pushes every photon; tc is not
+// taken with first)
 void launch_push_photon_f32(const PartF32 &P, const float *F, const Grid &g, const PushConst &pc,
-                            const QedParams &q, int *err, cudaStream_t st, bool tc);
+                            const QedParams &q, int *err, cudaStream_t st, bool tc, const uint32_t *first = nullptr);
 
 }  // namespace pic

@@ -3,9 +3,9 @@ configuration the bench times (FP32 cell+offset, tiled push, the bench's
 sort interval, so the first step sorts): one step of the whole workload on
 the GPU, against outputs the oracle computes one by one.
 
-The particles are loaded ordered by tile (numpy's stable argsort of the tile
-of the cell the O6 rule gives), so the GPU's stable sort at the first step
-must leave them in place.  Smooth random fields are set on both sides.  The
+The particles are loaded in the sort's order (numpy's stable argsort of the
+key (tile, cell within the tile) of the cell the O6 rule gives), so the
+GPU's stable sort at the first step must leave them in place.  Smooth random fields are set on both sides.  The
 oracle then steps, on the same grid and fields, a sample of the particles:
 about 2000 at random, plus every particle whose deposit window can reach one
 of a few sampled nodes.  A particle's push depends only on the fields and
@@ -43,12 +43,17 @@ def _cells(w, s):
 
 
 def _tile_keys(w, cells):
+    """the sort key: tile index (x fastest), then the cell within the tile
+    (x fastest)"""
     tl = [int(np.log2(w.tile[d])) for d in range(w.dim)]
     nt = [w.n[d] // w.tile[d] for d in range(w.dim)]
     k = np.zeros_like(cells[0])
     for d in reversed(range(w.dim)):
         k = k * nt[d] + (cells[d] >> tl[d])
-    return k
+    loc = np.zeros_like(cells[0])
+    for d in reversed(range(w.dim)):
+        loc = loc * w.tile[d] + (cells[d] & (w.tile[d] - 1))
+    return k * int(np.prod([w.tile[d] for d in range(w.dim)])) + loc
 
 
 def _smooth_fields(shape, rng, amp=(0.6, 0.6, 0.6, 0.4, 0.4, 0.4)):

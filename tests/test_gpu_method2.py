@@ -296,3 +296,42 @@ def test_cascade_fig10_pair_count_matches_oracle():
         assert abs(ng - no) <= 4.5 * so + 0.5, (m, ng, no, so)
     last = g[w.steps]
     assert abs(last[:, 1].sum() + lost - e0) <= 2e-4 * e0
+
+
+def test_method2_tiled_2d_matches_oracle_event_by_event():
+    """Method II fused into the 2D tiled push (FP32, 8x8 tiles, a sort every
+    4 steps): 64 electrons of gamma 1000 in 0.009 B_cr spread over a
+    periodic 32^2 grid, 150 steps, the same particles on both sides after
+    every step"""
+    w1 = W.cascade(1000.0, 0.009, replicas=64, steps=150, capacity_per_replica=64)
+    rng = np.random.default_rng(41)
+    e = w1.species[0]
+    x, y = rng.uniform(0.0, 32.0, 64), rng.uniform(0.0, 32.0, 64)
+    ang = rng.uniform(0.0, 2.0 * math.pi, 64)
+    u = math.sqrt(1000.0 ** 2 - 1.0)
+    spec = [(sp.q, sp.m, sp.w, sp.capacity, sp.kind, sp.qed) for sp in w1.species]
+    s = pic.pic_create(2, (32, 32), (1.0, 1.0), w1.dt, spec, seed=SEED, sort_interval=4, tile=(8, 8))
+    s.pic_set_qed(mode=pic.QED_TABLE, method=2, **w1.qed)
+    s.pic_set_field(pic.BZ, np.full(s.box(), w1.notes["B0"]))
+    s.pic_load_particles(0, x, y, None, u * np.cos(ang), u * np.sin(ang), np.zeros(64))
+    o = O.OracleSim(2, (32, 32), (1.0, 1.0), w1.dt)
+    for sp in w1.species:
+        o.add_species(sp.q, sp.m, sp.w, sp.capacity, kind=sp.kind, qed=sp.qed)
+    o.set_qed(seed=SEED, **w1.qed)
+    o.set_qed_method(2)
+    o.set_field(O.BZ, np.full(o.box(), w1.notes["B0"]))
+    o.load(0, x, y, None, u * np.cos(ang), u * np.sin(ang), np.zeros(64))
+    n_ph = 0
+    for step in range(w1.steps):
+        s.pic_step(1)
+        o.step(1)
+        for sp in range(3):
+            ig, _ = s.pic_get_qed_state(sp)
+            io, _ = o.qed_state(sp)
+            g = set(_alive_ids(ig, s.pic_get_particles(sp)).tolist())
+            r = set(_alive_ids(io, o.particles(sp)).tolist())
+            assert g == r, (step, sp, len(g - r), len(r - g))
+            if sp == 2:
+                n_ph = max(n_ph, len(g))
+    assert n_ph > 100 and o.method2_over() == 0
+    s.close()

@@ -147,3 +147,57 @@ def test_monte_carlo_3d_matches_oracle_event_by_event(prec):
         assert np.all(dd < 1e-3 * _DX3[0]), (i, gx[i], ox[i])
     e1 = Q.total_energy(s.pic_get_particles(0), s.pic_get_particles(1), s.pic_get_particles(2))
     assert abs(e1 - e0) <= (1e-9 if prec == pic.FP64_PLAIN else 2e-5) * e0
+
+
+_N2, _DX2 = (32, 32), (1.0, 1.0)
+
+
+def _electrons_2d():
+    rng = np.random.default_rng(37)
+    x = [rng.uniform(0.0, _N2[d] * _DX2[d], Q.N_E) for d in range(2)]
+    u = np.sqrt(Q.GAMMA0 ** 2 - 1.0)
+    ang = rng.uniform(0.0, 2.0 * np.pi, Q.N_E)
+    return x[0], x[1], None, u * np.cos(ang), u * np.sin(ang), np.zeros(Q.N_E)
+
+
+def _oracle_2d():
+    o = O.OracleSim(2, _N2, _DX2, Q.DT)
+    for sp in Q.species_spec():
+        o.add_species(sp[0], sp[1], sp[2], sp[3], kind=sp[4], qed=sp[5])
+    o.set_qed(photon_sp=2, electron_sp=0, positron_sp=1, lambda_r_m=Q.LAMBDA, photon_emin=0.0, seed=Q.SEED)
+    o.set_field(O.BZ, np.full(o.box(), Q.B0))
+    o.load(0, *_electrons_2d())
+    return o
+
+
+def test_monte_carlo_2d_tiled_matches_oracle_event_by_event():
+    """FP32 on a periodic 32^2 grid with 8x8 tiles and a sort every 4 steps:
+    after the first sort the leptons' Monte Carlo runs fused into the tiled
+    push (the sorted particles' work items; pairs appended since the sort on
+    the one-thread-per-particle kernel), compared with the oracle step by
+    step as in 1D.  The tiled path is the one taken: it issues one more push
+    launch per QED lepton species and step than the simple kernel alone."""
+    o = _oracle_2d()
+    s = pic.pic_create(2, _N2, _DX2, Q.DT, Q.species_spec(), seed=Q.SEED, sort_interval=4, tile=(8, 8))
+    s.pic_set_qed(photon_sp=2, electron_sp=0, positron_sp=1, lambda_r_m=Q.LAMBDA)
+    s.pic_set_field(pic.BZ, np.full(s.box(), Q.B0))
+    s.pic_load_particles(0, *_electrons_2d())
+    e0 = Q.total_energy(s.pic_get_particles(0), s.pic_get_particles(1), s.pic_get_particles(2))
+    s.pic_profile(True)
+    r = Q.compare_events(s, o, 25, *DELTA[pic.FP32_CELLOFF], Q.photon_chi_in_bz(o.Es))
+    assert r["events"] >= 150 and r["conversions"] >= 5 and r["flips"] <= 0.05 * r["events"], r
+    e1 = Q.total_energy(s.pic_get_particles(0), s.pic_get_particles(1), s.pic_get_particles(2))
+    assert abs(e1 - e0) <= 2e-5 * e0
+    tiled = s.pic_profile_read()["launches"]["push"]
+    s.close()
+    ref = pic.pic_create(2, _N2, _DX2, Q.DT, Q.species_spec(), seed=Q.SEED, sort_interval=4, tile=(8, 8),
+                         push_variant=pic.PUSH_SIMPLE)
+    ref.pic_set_qed(photon_sp=2, electron_sp=0, positron_sp=1, lambda_r_m=Q.LAMBDA)
+    ref.pic_set_field(pic.BZ, np.full(ref.box(), Q.B0))
+    ref.pic_load_particles(0, *_electrons_2d())
+    ref.pic_profile(True)
+    for _ in range(25):
+        ref.pic_step(1)
+    simple = ref.pic_profile_read()["launches"]["push"]
+    ref.close()
+    assert tiled >= simple + 20, (tiled, simple)
