@@ -18,7 +18,7 @@ LIB_PATH = os.path.join(_HERE, "liboracle.so")
 SOURCES = ["pic_oracle.c", "philox.c", "qed.c", "mlp.c"]
 
 EX, EY, EZ, BX, BY, BZ, JX, JY, JZ = range(9)
-PERIODIC, ABSORB = 0, 1
+PERIODIC, ABSORB, SLAB = 0, 1, 2  # SLAB: a slab of a larger periodic grid (domain-decomposition tests)
 
 
 def build(force: bool = False) -> str:
@@ -71,6 +71,16 @@ def lib():
         L.or_sort_species.argtypes = [P, I, P]
         L.or_sort_species.restype = LG
         L.or_step.argtypes = [P, LG]
+        L.or_step_phase.argtypes = [P, I]
+        L.or_step_phase.restype = I
+        L.or_field_raw_size.argtypes = [P, P]
+        L.or_field_raw_size.restype = LG
+        L.or_get_field_raw.argtypes = [P, I, P]
+        L.or_set_field_raw.argtypes = [P, I, P]
+        L.or_take_outbox.argtypes = [P, I, P, P, P, P]
+        L.or_take_outbox.restype = LG
+        L.or_load_state.argtypes = [P, I, LG, P, P, P, P]
+        L.or_load_state.restype = I
         L.or_get_particles.argtypes = [P, I, P, P, P, P, P, P, P]
         L.or_get_particles.restype = LG
         L.or_get_rho.argtypes = [P, P]
@@ -312,6 +322,49 @@ class OracleSim:
 
     def step(self, n=1):
         lib().or_step(self._h, int(n))
+
+    def step_phase(self, phase):
+        """one of the split step's five phases (0: E half, 1: B half, 2: push,
+        3: B half, 4: E half and n -> n+1)"""
+        if lib().or_step_phase(self._h, int(phase)):
+            raise ValueError("oracle: bad phase")
+
+    # --- slab sub-domains (bc SLAB along x): raw arrays with ghost layers ---
+    def field_raw(self, c):
+        """component c with its ghost layers, shape (len_z, len_y, len_x)
+        (along a SLAB axis index i sits at i + 4)"""
+        ln = np.zeros(3, dtype=np.int64)
+        L = lib()
+        n = L.or_field_raw_size(self._h, _ptr(ln))
+        out = np.zeros(n)
+        L.or_get_field_raw(self._h, int(c), _ptr(out))
+        return out.reshape(ln[2], ln[1], ln[0])
+
+    def set_field_raw(self, c, a):
+        a = _f64(np.asarray(a, dtype=np.float64))
+        lib().or_set_field_raw(self._h, int(c), _ptr(a))
+
+    def take_outbox(self, isp):
+        """particles of species isp that left the slab since the last call:
+        (x (n, 3), u (n, 3), id, tau)"""
+        L = lib()
+        n = L.or_take_outbox(self._h, int(isp), None, None, None, None)
+        x, u = np.zeros((n, 3)), np.zeros((n, 3))
+        ids, tau = np.zeros(n, dtype=np.uint64), np.zeros(n)
+        if n:
+            L.or_take_outbox(self._h, int(isp), _ptr(x), _ptr(u), _ptr(ids), _ptr(tau))
+        return x, u, ids, tau
+
+    def load_state(self, isp, x, u, ids, tau):
+        """append particles with their identities and optical depths"""
+        n = len(ids)
+        if n == 0:
+            return
+        xa, ua = _f64(np.asarray(x, dtype=np.float64).reshape(n, 3)), _f64(np.asarray(u, dtype=np.float64).reshape(n, 3))
+        ia, ta = np.ascontiguousarray(ids, dtype=np.uint64), _f64(np.asarray(tau, dtype=np.float64))
+        rc = lib().or_load_state(self._h, int(isp), n, _ptr(xa), _ptr(ua), _ptr(ia), _ptr(ta))
+        if rc:
+            raise ValueError(f"oracle: load_state failed ({rc})")
 
     def particles(self, isp):
         L = lib()

@@ -53,7 +53,15 @@
 #include "pic_oracle.h"
 
 enum { EX = 0, EY, EZ, BX, BY, BZ, JX, JY, JZ, NF };
-enum { BC_PERIODIC = 0, BC_ABSORB = 1 };
+/* BC_SLAB (test infrastructure for the domain decomposition of Sec. II.F):
+ * the axis is one slab of a larger periodic grid; its SLAB_G ghost layers on
+ * each side are stored and filled by the caller (neighbours' values), the
+ * solver updates the slab's own nodes [0, N) only, deposits may land in the
+ * ghosts (the caller sums them into the neighbours), and a particle whose
+ * position leaves [0, L) is moved to its species' outbox (the caller hands
+ * it to the neighbour) instead of being wrapped or absorbed. */
+enum { BC_PERIODIC = 0, BC_ABSORB = 1, BC_SLAB = 2 };
+#define SLAB_G 4
 
 /* ------------------------------------------------------------------ */
 /* Sim state                                                           */
@@ -69,6 +77,10 @@ typedef struct {
     int kind;           /* 0 massive, 1 photon (moves at c along k, no charge) */
     int qed;            /* massive species that emits photons */
     double *tau;        /* optical depth left (Sec. IV, Method I in optical-depth form) */
+    /* BC_SLAB: particles that left the slab this step (x as computed, u, id, tau) */
+    long nout, outcap;
+    double *ox, *ou, *otau;
+    uint64_t *oid;
 } osp;
 
 /* one QED event of the current step, kept for spawning in parent order */
@@ -182,6 +194,7 @@ osim *or_create(int dim, const long *n, const double *dx, const int *bc, double 
         s->tile[d] = active ? (tile ? tile[d] : 8) : 1;
         if (!active) { s->lo[d] = 0; s->len[d] = 1; }
         else if (s->bc[d] == BC_PERIODIC) { s->lo[d] = 0; s->len[d] = s->n[d]; }
+        else if (s->bc[d] == BC_SLAB) { s->lo[d] = -SLAB_G; s->len[d] = s->n[d] + 2 * SLAB_G; }
         else { s->lo[d] = -1; s->len[d] = s->n[d] + 2; }
     }
     for (int c = 0; c < NF; c++) s->F[c] = (double *)calloc((size_t)ncells_store(s), sizeof(double));
@@ -194,6 +207,7 @@ void or_destroy(osim *s)
     for (int c = 0; c < NF; c++) free(s->F[c]);
     for (int i = 0; i < s->nsp; i++) {
         free(s->sp[i].x); free(s->sp[i].u); free(s->sp[i].alive); free(s->sp[i].id); free(s->sp[i].tau);
+        free(s->sp[i].ox); free(s->sp[i].ou); free(s->sp[i].otau); free(s->sp[i].oid);
         free(s->ev[i]);
     }
     free(s);
@@ -882,6 +896,26 @@ static void record(osim *s, int isp, long parent, const double *k, double frac)
     e->frac = frac;
 }
 
+/* BC_SLAB: move particle a to its species' outbox (it leaves the slab) */
+static void to_outbox(osp *p, long a)
+{
+    if (p->nout == p->outcap) {
+        p->outcap = p->outcap ? 2 * p->outcap : 64;
+        p->ox = (double *)realloc(p->ox, (size_t)p->outcap * 3 * sizeof(double));
+        p->ou = (double *)realloc(p->ou, (size_t)p->outcap * 3 * sizeof(double));
+        p->otau = (double *)realloc(p->otau, (size_t)p->outcap * sizeof(double));
+        p->oid = (uint64_t *)realloc(p->oid, (size_t)p->outcap * sizeof(uint64_t));
+    }
+    long b = p->nout++;
+    for (int d = 0; d < 3; d++) {
+        p->ox[3 * b + d] = p->x[3 * a + d];
+        p->ou[3 * b + d] = p->u[3 * a + d];
+    }
+    p->otau[b] = p->tau[a];
+    p->oid[b] = p->id[a];
+    p->alive[a] = 0;
+}
+
 static void push_species(osim *s, osp *p)
 {
     double qm = p->q / p->m, qw = p->q * p->w;
@@ -947,14 +981,15 @@ static void push_species(osim *s, osp *p)
         double g = gamma_of(u);
         double v[3] = {u[0] / g, u[1] / g, u[2] / g};
         deposit(s, xh, x32, v, qw);                /* J^{n+1} */
-        int dead = 0;
+        int dead = 0, leaves = 0;
         for (int d = 0; d < s->dim; d++) {
             double L = (double)s->n[d] * s->dx[d];
             if (s->bc[d] == BC_PERIODIC) {
                 if (x1[d] < 0.0) x1[d] += L;
                 if (x1[d] >= L) x1[d] -= L;
             } else if (x1[d] < 0.0 || x1[d] >= L) {
-                dead = 1;
+                if (s->bc[d] == BC_SLAB) leaves = 1;
+                else dead = 1;
             }
         }
         for (int d = 0; d < s->dim; d++) x[d] = x1[d];
@@ -962,6 +997,8 @@ static void push_species(osim *s, osp *p)
             double uu = u[0] * u[0] + u[1] * u[1] + u[2] * u[2];
             s->e_absorbed += p->w * p->m * (uu / (g + 1.0)) * dV;
             p->alive[a] = 0;
+        } else if (leaves) {
+            to_outbox(p, a);
         } else if (emitted) {
             record(s, isp, a, kph, 0.0);  /* an emitter absorbed in the same step leaves no photon */
         }
@@ -1010,18 +1047,20 @@ static void push_photons(osim *s, osp *p)
         }
         double x1[3] = {xh[0], xh[1], xh[2]};
         for (int d = 0; d < s->dim; d++) x1[d] += 0.5 * s->dt * v[d];
-        int dead = 0;
+        int dead = 0, leaves = 0;
         for (int d = 0; d < s->dim; d++) {
             double L = (double)s->n[d] * s->dx[d];
             if (s->bc[d] == BC_PERIODIC) {
                 if (x1[d] < 0.0) x1[d] += L;
                 if (x1[d] >= L) x1[d] -= L;
             } else if (x1[d] < 0.0 || x1[d] >= L) {
-                dead = 1;
+                if (s->bc[d] == BC_SLAB) leaves = 1;
+                else dead = 1;
             }
         }
         for (int d = 0; d < s->dim; d++) x[d] = x1[d];
         if (dead) p->alive[a] = 0;
+        else if (leaves) to_outbox(p, a);
         else if (conv) record(s, isp, a, k, frac);
     }
 }
@@ -1079,25 +1118,107 @@ static void spawn(osim *s)
     for (int i = 0; i < s->nsp; i++) s->nev[i] = 0;
 }
 
-int or_step(osim *s, long nsteps)
+/* The split step of Sec. II.F in five phases (a slab's caller exchanges
+ * ghost layers, currents and particles between them):
+ *   0: (sort) E^{n+1/2} with J^n;   1: B^{n+1/2};
+ *   2: push every species (J^{n+1}), QED spawn;
+ *   3: B^{n+1};                     4: E^{n+1} with J^{n+1}, n -> n+1. */
+int or_step_phase(osim *s, int phase)
 {
     double h = 0.5 * s->dt;
-    for (long it = 0; it < nsteps; it++) {
+    double t0 = (double)s->step * s->dt;
+    switch (phase) {
+    case 0:
         if (s->sort_interval > 0 && s->step % s->sort_interval == 0)
             for (int i = 0; i < s->nsp; i++) sort_species(s, &s->sp[i], NULL);
-        double t0 = (double)s->step * s->dt;
         update_E(s, h);                       /* E^{n+1/2} with J^n */
+        return 0;
+    case 1:
         update_B(s, h, t0 + h);               /* B^{n+1/2} */
+        return 0;
+    case 2:
         for (int c = JX; c <= JZ; c++) memset(s->F[c], 0, (size_t)ncells_store(s) * sizeof(double));
         for (int i = 0; i < s->nsp; i++) {
             if (s->sp[i].kind == 1) push_photons(s, &s->sp[i]);
             else push_species(s, &s->sp[i]);
         }
         if (s->qed_on) spawn(s);
+        return 0;
+    case 3:
         update_B(s, h, t0 + s->dt);           /* B^{n+1} */
+        return 0;
+    case 4:
         update_E(s, h);                       /* E^{n+1} with J^{n+1} */
         s->step++;
+        return 0;
     }
+    return -1;
+}
+
+int or_step(osim *s, long nsteps)
+{
+    for (long it = 0; it < nsteps; it++)
+        for (int ph = 0; ph < 5; ph++) or_step_phase(s, ph);
+    return 0;
+}
+
+/* BC_SLAB: the whole stored array of component c (ghost layers included),
+ * x fastest, len[0] x len[1] x len[2] */
+long or_field_raw_size(const osim *s, long *len)
+{
+    for (int d = 0; d < 3; d++) len[d] = s->len[d];
+    return ncells_store(s);
+}
+
+int or_get_field_raw(const osim *s, int c, double *out)
+{
+    if (c < 0 || c >= NF) return -1;
+    memcpy(out, s->F[c], (size_t)ncells_store(s) * sizeof(double));
+    return 0;
+}
+
+int or_set_field_raw(osim *s, int c, const double *in)
+{
+    if (c < 0 || c >= NF) return -1;
+    memcpy(s->F[c], in, (size_t)ncells_store(s) * sizeof(double));
+    return 0;
+}
+
+/* BC_SLAB: the particles of species isp that left the slab since the last
+ * call (positions as computed, momenta, identities, optical depths); with
+ * x == NULL only the count; a call with arrays empties the outbox */
+long or_take_outbox(osim *s, int isp, double *x, double *u, uint64_t *id, double *tau)
+{
+    if (isp < 0 || isp >= s->nsp) return -1;
+    osp *p = &s->sp[isp];
+    long n = p->nout;
+    if (!x) return n;
+    memcpy(x, p->ox, (size_t)n * 3 * sizeof(double));
+    memcpy(u, p->ou, (size_t)n * 3 * sizeof(double));
+    memcpy(id, p->oid, (size_t)n * sizeof(uint64_t));
+    memcpy(tau, p->otau, (size_t)n * sizeof(double));
+    p->nout = 0;
+    return n;
+}
+
+/* append particles with their identities and optical depths (migration) */
+int or_load_state(osim *s, int isp, long n, const double *x, const double *u, const uint64_t *id,
+                  const double *tau)
+{
+    if (isp < 0 || isp >= s->nsp) return -1;
+    osp *p = &s->sp[isp];
+    if (p->n + n > p->cap) return -2;
+    for (long a = 0; a < n; a++) {
+        long b = p->n + a;
+        for (int d = 0; d < 3; d++) {
+            p->x[3 * b + d] = d < s->dim ? x[3 * a + d] : 0.0;
+            p->u[3 * b + d] = u[3 * a + d];
+        }
+        p->alive[b] = 1;
+        p->id[b] = id[a];
+        p->tau[b] = tau[a];
+    }
+    p->n += n;
     return 0;
 }
 

@@ -46,6 +46,15 @@ void or_weights4(double delta, double *w);
 void or_deposit_one(osim *s, const double *x0, const double *x1, const double *v, double qw);
 long or_sort_species(osim *s, int isp, long *perm_out);
 int or_step(osim *s, long nsteps);
+/* the split step in its five phases (BC_SLAB callers exchange between them) */
+int or_step_phase(osim *s, int phase);
+/* BC_SLAB = 2: a slab of a larger periodic grid (ghost layers set by the caller) */
+long or_field_raw_size(const osim *s, long *len);
+int or_get_field_raw(const osim *s, int c, double *out);
+int or_set_field_raw(osim *s, int c, const double *in);
+long or_take_outbox(osim *s, int isp, double *x, double *u, uint64_t *id, double *tau);
+int or_load_state(osim *s, int isp, long n, const double *x, const double *u, const uint64_t *id,
+                  const double *tau);
 long or_get_particles(const osim *s, int isp, double *x, double *y, double *z, double *ux,
                       double *uy, double *uz, unsigned char *alive);
 int or_get_rho(const osim *s, double *rho);
