@@ -428,6 +428,9 @@ def run_qed_sample(pic, mode, nets, golden):
     return Q.sample_errors({"history": hist, "final": fin}, golden)
 
 
+PUSHER = {"boris": 0, "vay": 1}
+
+
 def run_qed(args, w, pic, torch, stream, timed, rank, world, dist, local, l2_note):
     """The strong-field QED collision: the same seeded beam through three
     forms, each advanced untimed to the collision, then W warm-up and K timed
@@ -454,7 +457,7 @@ def run_qed(args, w, pic, torch, stream, timed, rank, world, dist, local, l2_not
     peak, peak_kind = _peaks()
     for mode in modes:
         prec = pic.FP64_PLAIN if mode == "fp64" else pic.FP32_CELLOFF
-        sim = pic.from_workload(w, precision=prec, sort_interval=args.sort_interval, stream=stream.cuda_stream,
+        sim = pic.from_workload(w, precision=prec, sort_interval=args.sort_interval, pusher=PUSHER[args.pusher], stream=stream.cuda_stream,
                                 seed=0x5EED + rank, push_variant=args.push_variant)
         train = None
         if mode == "surrogate":
@@ -495,7 +498,7 @@ def run_qed(args, w, pic, torch, stream, timed, rank, world, dist, local, l2_not
             size = os.path.getsize(ckpt)
             sim.close()
             sim = None
-            sim_e = pic.from_workload(w, precision=prec, sort_interval=args.sort_interval, stream=stream.cuda_stream,
+            sim_e = pic.from_workload(w, precision=prec, sort_interval=args.sort_interval, pusher=PUSHER[args.pusher], stream=stream.cuda_stream,
                                       seed=0x5EED + rank, push_variant=args.push_variant, load=False)
             torch.cuda.synchronize()
             t0 = time.perf_counter()
@@ -588,7 +591,7 @@ def run_qed(args, w, pic, torch, stream, timed, rank, world, dist, local, l2_not
                           "precision": "fp32 cell+offset, QED by the surrogate networks inside their chi range "
                           "(tables outside); FP64 islands: optical depth, gamma above 1e4, diagnostics"
                           if modes[0] == "surrogate" else modes[0],
-                          "window": window,
+                          "window": window, "pusher": args.pusher,
                           "sort_interval": args.sort_interval, "replicas": world,
                           "l2": l2_note()},
                "fp32_table": tab and {"value": tab["value"], "ms_per_step": tab["ms_per_step"],
@@ -649,6 +652,8 @@ def main():
     ap.add_argument("--rows", type=int, default=None,
                     help="smaller case for profiling: ny of laser_foil_2d, nz of thermal_3d (not a bench line)")
     ap.add_argument("--qed-modes", default="surrogate,table,fp64", help="forms run by the QED workloads")
+    ap.add_argument("--pusher", default="boris", choices=["boris", "vay"],
+                    help="momentum update of every push (Sec. II.C: Boris, or Vay's for nearly cancelling forces)")
     ap.add_argument("--push-variant", type=int, default=0,
                     help="0: default kernels, 2: surrogate of the photon push per CTA on tcgen05 (QED workloads), "
                          "3: warp-aggregated deposit in the 2D tiled push")
@@ -746,7 +751,7 @@ def main():
     if pre is None:
         pre = PRE_STEPS.get(args.workload, 0) if args.rows is None else 0
     sim = pic.from_workload(w, precision=pic.FP32_CELLOFF, sort_interval=args.sort_interval,
-                            stream=stream.cuda_stream, push_variant=args.push_variant)
+                            pusher=PUSHER[args.pusher], stream=stream.cuda_stream, push_variant=args.push_variant)
     if pre:
         with torch.cuda.stream(stream):
             sim.pic_step(pre)  # untimed: to the phase the window measures
@@ -789,7 +794,7 @@ def main():
     fp64 = None
     if not args.no_fp64:
         sim64 = pic.from_workload(w, precision=pic.FP64_PLAIN, sort_interval=args.sort_interval,
-                                  stream=stream.cuda_stream)
+                                  pusher=PUSHER[args.pusher], stream=stream.cuda_stream)
         if pre:
             with torch.cuda.stream(stream):
                 sim64.pic_step(pre)
@@ -811,7 +816,7 @@ def main():
         size = os.path.getsize(ckpt)
         sim.close()
         sim_e = pic.from_workload(w, precision=pic.FP32_CELLOFF, sort_interval=args.sort_interval,
-                                  stream=stream.cuda_stream, load=False, push_variant=args.push_variant)
+                                  pusher=PUSHER[args.pusher], stream=stream.cuda_stream, load=False, push_variant=args.push_variant)
         torch.cuda.synchronize()
         t0 = time.perf_counter()
         sim_e.pic_restore(ckpt)
@@ -841,7 +846,7 @@ def main():
                "warmup": args.warmup, "ms_per_step": 1e3 * t / args.steps, "higher_is_better": True,
                "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
                "config": {"workload": describe(w), "precision": "fp32 cell+offset (FP64 islands: diagnostics)",
-                          "sort_interval": args.sort_interval,
+                          "sort_interval": args.sort_interval, "pusher": args.pusher,
                           "window": f"steps {pre + args.warmup}..{pre + args.warmup + args.steps}"
                                     + (" (the laser on the slab)" if args.workload == "laser_foil_2d" else ""),
                           "l2": l2_note(), "replicas": world, "qed": "off (no QED in this workload)"},

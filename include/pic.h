@@ -477,6 +477,19 @@ int pic_profile_read_species(pic_sim *sim, double *ms, int64_t *pushes);
 int pic_field_energy_noalloc(const double *const dev_fields[6], int64_t n, double dV, double *dev_out2,
                              void *stream);
 
+/* Measurement, no counterpart in the paper: throughput ceilings of the
+ * instruction mixes the push kernels are made of, on the current device
+ * (each a timed kernel of independent chains over 8 CTAs of 256 threads per
+ * SM): out[0] FP32 FMA flop/s, out[1] FP64 FMA flop/s, out[2] shared-memory
+ * integer atomics per second with the 32 lanes of a warp on 32 words (the
+ * lane-strided deposit), out[3] the same with the 32 lanes on one word,
+ * out[4] lane values per second through a warp reduction over groups of 8
+ * lanes plus one atomic per group (the warp-aggregated deposit).  out holds
+ * 5 doubles (host).  Allocates 4 KiB of device memory for the duration of
+ * the call; synchronises the device.  Errors: PIC_ERR_ARG, PIC_ERR_NOMEM,
+ * PIC_ERR_CUDA. */
+int pic_measure_ceilings(double *out);
+
 #ifdef __cplusplus
 }
 #endif

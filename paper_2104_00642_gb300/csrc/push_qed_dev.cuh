@@ -17,7 +17,8 @@ namespace pic {
 
 // With SURR the call is warp-collective: every lane of the warp makes it
 // (lanes with live false only take part in the network's evaluation);
-// mlp_smem is the staged network image.  p indexes the QED arrays.
+// mlp_smem is the staged network image.  p indexes the QED arrays; a lane
+// with live false touches nothing there.
 template <bool SURR>
 __device__ __forceinline__ void qed_lepton_f32(const QedParams &q, const unsigned char *mlp_smem, bool live,
                                                long long p, const float *eb, float &ux, float &uy, float &uz,
@@ -45,8 +46,11 @@ __device__ __forceinline__ void qed_lepton_f32(const QedParams &q, const unsigne
             mlp_eval_warp_sparse(*reinterpret_cast<const MlpImage *>(mlp_smem), inr, x0, x1, y0, y1);
             use_net = inr;
         }
-        if (!live) return;
     }
+    // a lane without a particle stops here, in every mode: p may index
+    // another thread's particle (the tiled kernels' idle lanes), whose
+    // optical depth it must not write
+    if (!live) return;
     bool emit = false;
     double frac = 0.0, tau = 0.0;
     if (!SURR && q.method == 2) {
@@ -120,8 +124,8 @@ __device__ __forceinline__ void qed_photon_f32(const QedParams &q, const unsigne
             mlp_eval_warp_sparse(*reinterpret_cast<const MlpImage *>(mlp_smem), inr, x0, x1, y0, y1);
             use_net = inr;
         }
-        if (!live) return;
     }
+    if (!live) return;  // as in qed_lepton_f32
     if (!SURR && q.method == 2) {
         // Method II for pairs: v0 = r1 accepted when r2 < dW_pair/dv(v0) dt
         if (km > 0.f) {

@@ -173,6 +173,7 @@ __global__ void __launch_bounds__(kTileThreads, QM == 2 ? 3 : kTileMinBlocks)
     const float cmax = fabsf(qw) * fmaxf(fmaxf(fabsf(cjx), fabsf(cjy)) / fmaxf(fabsf(qw), 1e-30f), 1.0f);
     const float jscale = 1048576.0f / fmaxf(cmax, 1e-30f);
     const float junit = 1.0f / jscale;
+    const float sjx = cjx * jscale, sjy = cjy * jscale;
     float *Fg = F + g.origin;  // interior origin
     const int rs = (int)g.sy;
     if (use_tma && threadIdx.x == 0) mbar_init(&mbar, 1);
@@ -208,11 +209,14 @@ __global__ void __launch_bounds__(kTileThreads, QM == 2 ? 3 : kTileMinBlocks)
         // shared-memory atomic target 32 different cells (different current
         // addresses) instead of one, whatever the in-tile order.
         const int S = (m.count + 31) >> 5;
+        // i / S for i < kChunk as a float product: (i + 1/2) / S lies at least
+        // 1/(2S) from an integer, far beyond the product's rounding
+        const float invS = 1.0f / (float)S;
         // stage the chunk's particle state: every thread issues all its loads
         // at once (coalesced), stored transposed to (segment position, lane)
         // (asynchronous 4-byte copies: no register round trip)
         for (int i = threadIdx.x; i < m.count; i += blockDim.x) {
-            const int l = i / S, j = i - l * S;
+            const int l = __float2int_rz(((float)i + 0.5f) * invS), j = i - l * S;
             const int pos = AGG ? i : j * 33 + l;
             const int p = m.start + i;  // capacities are below 2^31
             cp_async4(sPc + pos, P.cell + p);
@@ -339,9 +343,23 @@ __global__ void __launch_bounds__(kTileThreads, QM == 2 ? 3 : kTileMinBlocks)
                     AccWarp acc{sJ + key, B::N, B::WX, jscale, grp, lane == __ffs(grp) - 1};
                     esirkepov2d(S0, dS, cjx, cjy, jvz, acc);
                 }
-            } else if (din) {
-                AccShared acc{sJ + (u0[1] - by0) * B::WX + (u0[0] - bx0), B::N, B::WX, jscale};
-                esirkepov2d(S0, dS, cjx, cjy, jvz, acc);
+            } else {
+                // A warp whose 32 lanes all deposit on one window (a dense
+                // beam: the whole chunk in one cell, so lane striding cannot
+                // spread the lanes over cells) sums each value over the warp
+                // with one reduction and adds it with one atomic; otherwise
+                // every lane adds its own values (lanes on different cells).
+                // The fixed-point scale is folded into the three coefficients.
+                const int key = din ? (u0[1] - by0) * B::WX + (u0[0] - bx0) : -1;
+                int same = 0;
+                __match_all_sync(0xffffffffu, key, &same);
+                if (same && key >= 0) {
+                    AccWarpAll acc{sJ + key, B::N, B::WX, lane == 0};
+                    esirkepov2d(S0, dS, sjx, sjy, jvz * jscale, acc);
+                } else if (din) {
+                    AccSharedUnits acc{sJ + key, B::N, B::WX};
+                    esirkepov2d(S0, dS, sjx, sjy, jvz * jscale, acc);
+                }
             }
             if (!act) {
                 if (QM != 0 && li < m.count) q.ev[pg] = 0;
@@ -384,7 +402,7 @@ __global__ void __launch_bounds__(kTileThreads, QM == 2 ? 3 : kTileMinBlocks)
         // 4a. write the chunk's state back, coalesced (particles skipped above
         // keep their staged values)
         for (int i = threadIdx.x; i < m.count; i += blockDim.x) {
-            const int l = i / S, j = i - l * S;
+            const int l = __float2int_rz(((float)i + 0.5f) * invS), j = i - l * S;
             const int pos = AGG ? i : j * 33 + l;
             const int p = m.start + i;
             P.cell[p] = sPc[pos];

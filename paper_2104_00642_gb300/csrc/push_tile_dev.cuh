@@ -40,6 +40,32 @@ struct AccShared {
     }
 };
 
+// as AccShared with the values already in fixed-point units (the caller
+// folded the scale into the deposit's coefficients: one multiply fewer per
+// node)
+struct AccSharedUnits {
+    int *base;
+    int cs, rs;
+    __device__ __forceinline__ void add(int c, int a, int b, float v)
+    {
+        atomicAdd(base + c * cs + b * rs + a, __float2int_rn(v));
+    }
+};
+
+// the whole warp on one window: each value summed over the 32 lanes (one
+// warp reduction; 32 values of at most 2^20 units stay inside int32) and
+// added once by the lead lane
+struct AccWarpAll {
+    int *base;
+    int cs, rs;
+    bool lead;
+    __device__ __forceinline__ void add(int c, int a, int b, float v)
+    {
+        const int s = __reduce_add_sync(0xffffffffu, __float2int_rn(v));
+        if (lead) atomicAdd(base + c * cs + b * rs + a, s);
+    }
+};
+
 // Boris (Eqs. (13)-(16)) with the FP32 reciprocal square root and divide
 // of the special-function unit (a few ulp, far inside the FP32 tolerance)
 __device__ __forceinline__ void boris_fast(float &ux, float &uy, float &uz, float ex, float ey, float ez, float bx,

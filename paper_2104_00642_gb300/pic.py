@@ -34,7 +34,7 @@ EXPORTS = ["pic_create", "pic_destroy", "pic_last_error", "pic_load_particles", 
            "pic_get_cells", "pic_diagnostics", "pic_gather", "pic_sync", "pic_profile", "pic_profile_read",
            "pic_field_energy_noalloc", "pic_set_qed", "pic_qed_eval", "pic_get_qed_state", "pic_mlp_train",
            "pic_mlp_validate", "pic_mlp_get", "pic_mlp_set", "pic_mlp_eval", "pic_mlp_eval_tc", "pic_mlp_grad",
-           "pic_field_device", "pic_save", "pic_restore", "pic_profile_read_species"]
+           "pic_field_device", "pic_save", "pic_restore", "pic_profile_read_species", "pic_measure_ceilings"]
 KIND_MASSIVE, KIND_PHOTON = 0, 1
 QED_OFF, QED_TABLE, QED_SURROGATE = 0, 1, 2
 MLP_NPARAMS = 8642
@@ -173,12 +173,26 @@ def load_library(path: str = LIB_PATH):
     L.pic_field_device.argtypes = [P, I, C.POINTER(pic_field_view)]
     L.pic_profile_read_species.argtypes = [P, P, P]
     L.pic_save.argtypes = [P, C.c_char_p]
+    L.pic_measure_ceilings.argtypes = [P]
+    L.pic_measure_ceilings.restype = I
     L.pic_restore.argtypes = [P, C.c_char_p]
     for name in ("pic_mlp_train", "pic_mlp_validate", "pic_mlp_get", "pic_mlp_set", "pic_mlp_eval", "pic_mlp_eval_tc",
                  "pic_mlp_grad", "pic_field_device", "pic_save", "pic_restore", "pic_profile_read_species"):
         getattr(L, name).restype = I
     _lib = L
     return L
+
+
+def pic_measure_ceilings():
+    """throughput ceilings of the push kernels' instruction mixes on the
+    current device (see include/pic.h): dict of per-second rates"""
+    L = load_library()
+    out = np.zeros(5)
+    rc = L.pic_measure_ceilings(_p(out))
+    if rc:
+        raise PicError(rc, L.pic_last_error(None).decode())
+    return {"fp32_flops": out[0], "fp64_flops": out[1], "shared_atomics_distinct": out[2],
+            "shared_atomics_same_word": out[3], "warp_reduce_then_atomic_values": out[4]}
 
 
 def pic_field_energy_noalloc(dev_fields, n, dV, dev_out2, stream=None):

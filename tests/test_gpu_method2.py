@@ -250,26 +250,46 @@ def test_cascade_fig9_matches_oracle_replicas(b):
     for m in marks:
         mg = g[m] / 4000.0
         mo, so = ref[m].mean(axis=0), ref[m].std(axis=0, ddof=1) / math.sqrt(48)
+        # rare species (pairs at 0.001 B_cr: a few in 4000 replicas) may be
+        # absent from all 48 oracle runs: the standard error of a count is
+        # then at least its Poisson value for one event in 48 runs, and that
+        # of an energy sum that count times the primary energy
+        floor_n = np.sqrt(np.maximum(np.maximum(mo[:, 0], mg[:, 0]), 1.0 / 48) / 48)
+        so = np.stack([np.maximum(so[:, 0], floor_n), np.maximum(so[:, 1], floor_n * 1000.0)], axis=1)
         print(b, m, mg.tolist(), mo.tolist(), so.tolist())
-        assert np.all(np.abs(mg - mo) <= 4.5 * so + 1e-9 * np.abs(mo)), (m, mg, mo, so)
-        assert abs(g[m][:, 1].sum() + lost - e0) <= 2e-4 * e0
+        assert np.all(np.abs(mg - mo) <= 4.5 * so), (m, mg, mo, so)
+        assert abs(g[m][:, 1].sum() - e0) <= 2e-4 * e0  # no photon is tallied here (photon_emin 0)
 
 
 def test_cascade_fig9_method1_and_method2_agree():
-    """the paper shows both methods reproduce Eq. (23); on the cascade they
-    give the same per-replica counts and energies within the Monte-Carlo
-    noise (4000 replicas each, gamma0 = 1000 in 0.009 B_cr, t = 2)"""
-    w = W.cascade(1000.0, 0.009, replicas=4000, t_end=2.0, capacity_per_replica=128)
-    a, _ = _gpu_cascade(w, method=1)
-    b, _ = _gpu_cascade(w, method=2, seed=SEED + 1)
-    A, B = a[w.steps] / 4000.0, b[w.steps] / 4000.0
-    print(A.tolist(), B.tolist())
-    # counts: Poisson-like spread per replica at most ~ the mean (+ 1);
-    # energies: per-replica spread at most the primary energy
-    sd_n = np.sqrt((np.maximum(A[:, 0], B[:, 0]) + 1.0) * 2.0 / 4000.0) * 3.0
-    sd_e = 1000.0 * math.sqrt(2.0 / 4000.0)
-    assert np.all(np.abs(A[:, 0] - B[:, 0]) <= 5.0 * sd_n), (A, B)
-    assert np.all(np.abs(A[:, 1] - B[:, 1]) <= 5.0 * sd_e), (A, B)
+    """the paper shows both methods reproduce Eq. (23).  On the cascade
+    (gamma0 = 1000 in 0.009 B_cr, t = 1, 4000 replicas) they differ by the
+    step error of the optical-depth form: it takes at most one event per step
+    (after an event tau restarts from a fresh draw), so its event rate is
+    W / (1 + W dt / 2) where Method II's is W.  That difference must be
+    first order in dt: with dt / 4 the photon counts of the two methods
+    come at least three times closer (and agree within the noise there);
+    the lepton counts and energies agree within the noise at both steps."""
+    res = {}
+    for div in (1, 4):
+        w0 = W.cascade(1000.0, 0.009, replicas=4000, t_end=1.0, capacity_per_replica=128)
+        w = W.cascade(1000.0, 0.009, replicas=4000, dt=w0.dt / div, t_end=1.0, capacity_per_replica=128)
+        a, _ = _gpu_cascade(w, method=1)
+        b, _ = _gpu_cascade(w, method=2, seed=SEED + 1)
+        res[div] = (a[w.steps] / 4000.0, b[w.steps] / 4000.0)
+        print(div, res[div][0].tolist(), res[div][1].tolist())
+    n = 4000.0
+    for div in (1, 4):
+        A, B = res[div]
+        # leptons: counts with a Poisson-like spread per replica of at most
+        # the mean + 1, energies with a spread at most the primary energy
+        sd_n = np.sqrt((np.maximum(A[:2, 0], B[:2, 0]) + 1.0) * 2.0 / n)
+        assert np.all(np.abs(A[:2, 0] - B[:2, 0]) <= 5.0 * sd_n), (div, A, B)
+        assert np.all(np.abs(A[:2, 1] - B[:2, 1]) <= 5.0 * 1000.0 * math.sqrt(2.0 / n)), (div, A, B)
+    d1 = res[1][1][2, 0] - res[1][0][2, 0]  # photons: Method II minus Method I
+    d4 = res[4][1][2, 0] - res[4][0][2, 0]
+    sd_ph = math.sqrt(2.0 * (res[4][0][2, 0] + 1.0) * 3.0 / n)  # photon counts: spread ~ 3 x Poisson per replica
+    assert d1 > 0.0 and abs(d4) <= max(d1 / 3.0, 5.0 * sd_ph), (d1, d4, sd_ph)
 
 
 def test_cascade_fig10_pair_count_matches_oracle():
@@ -295,7 +315,17 @@ def test_cascade_fig10_pair_count_matches_oracle():
         print(m * w.dt, ng, no, so)
         assert abs(ng - no) <= 4.5 * so + 0.5, (m, ng, no, so)
     last = g[w.steps]
-    assert abs(last[:, 1].sum() + lost - e0) <= 2e-4 * e0
+    # energy: pure B does no work, and the kinematics of Sec. IV conserve it
+    # except where they put a lepton left below its rest energy at rest (an
+    # emission recoil to gamma (1 - u) < 1, a pair share v k < 1), which only
+    # adds energy -- a few 1e-3 here, where the cascade ends in ~1e4 soft
+    # pairs per replica.  The tally of the photons below 2 m c^2 carries the
+    # weight and the cell volume (diagnostics' units): lost / (w dx) per
+    # macro-particle.
+    lost_gamma = lost / (w.species[2].w * w.dx[0])
+    gain = (last[:, 1].sum() + lost_gamma) / e0 - 1.0
+    print("energy gain", gain)
+    assert 0.0 <= gain <= 1e-2, (last[:, 1].sum(), lost_gamma, e0)
 
 
 def test_method2_tiled_2d_matches_oracle_event_by_event():
