@@ -261,8 +261,9 @@ __global__ void __launch_bounds__(kTileThreads, QM == 2 ? 3 : kTileMinBlocks)
             float ux = 0.f, uy = 0.f, uz = 0.f, ig1 = 0.f;
             float S0[2][4], dS[2][4];
             int ch[2] = {0, 0};
-            float oh[2] = {0.f, 0.f};
             float eb[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+            int icn[2] = {0, 0};  // node shape at x^{n+1/2}: the gather's, and the deposit's start
+            float wn[2][3];
             bool ok = true;
             if (act) {
                 int dummy;
@@ -277,10 +278,8 @@ __global__ void __launch_bounds__(kTileThreads, QM == 2 ? 3 : kTileMinBlocks)
                 drift_f32(c[1], o[1], hdx1 * uy * ig);
                 ch[0] = c[0];
                 ch[1] = c[1];
-                oh[0] = o[0];
-                oh[1] = o[1];
-                int icn[2], ich[2];
-                float wn[2][3], wh[2][3];
+                int ich[2];
+                float wh[2][3];
                 axis_w_f32(c[0], o[0], icn[0], wn[0], ich[0], wh[0]);
                 axis_w_f32(c[1], o[1], icn[1], wn[1], ich[1], wh[1]);
                 const bool gin =
@@ -309,12 +308,11 @@ __global__ void __launch_bounds__(kTileThreads, QM == 2 ? 3 : kTileMinBlocks)
                 // Esirkepov on x^{n+1/2} -> x^{n+3/2}
 #pragma unroll
                 for (int d = 0; d < 2; d++) {
-                    int i0, i1;
-                    float w0[3], w1[3];
-                    axis_wn_f32(ch[d], oh[d], i0, w0);
+                    int i1;
+                    float w1[3];
                     axis_wn_f32(c[d], o[d], i1, w1);
-                    ok &= (i1 - i0 >= -1 && i1 - i0 <= 1);
-                    u0[d] = union4(i0, w0, i1, w1, S0[d], dS[d]);
+                    ok &= (i1 - icn[d] >= -1 && i1 - icn[d] <= 1);
+                    u0[d] = union4(icn[d], wn[d], i1, w1, S0[d], dS[d]);
                 }
                 // a non-finite momentum (a NaN or infinite field) is reported and the particle
                 // removed before anything uses its position: NaN positions would give no valid
