@@ -319,6 +319,8 @@ QedParams qed_params(pic_sim *s, int i)
     q.method = s->qed.method == PIC_QED_METHOD2 ? 2 : 1;
     q.pref = alpha * s->Es * s->g.dt / (std::sqrt(3.0) * 3.14159265358979323846);
     q.inv_Es = s->Es > 0.0 ? 1.0 / s->Es : 0.0;
+    q.pref_f = (float)q.pref;
+    q.inv_Es_f = (float)q.inv_Es;
     q.emin = s->qed.photon_emin;
     q.key[0] = (uint32_t)s->seed;
     q.key[1] = (uint32_t)(s->seed >> 32);
@@ -336,6 +338,8 @@ QedParams qed_params(pic_sim *s, int i)
     const bool surr = s->qed.mode == PIC_QED_SURROGATE && net.ready && s->precision == PIC_PREC_FP32_CELLOFF;
     q.net = surr ? net.img : nullptr;
     q.nrm = net.nrm;
+    q.net_lo_f = (float)net.nrm.lnchi_lo;
+    q.net_hi_f = (float)net.nrm.lnchi_hi;
     return q;
 }
 

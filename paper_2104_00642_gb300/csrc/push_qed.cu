@@ -277,13 +277,13 @@ __global__ void __launch_bounds__(kMlpTcRows, 4) k_push_photon_tc(PartF32 P, con
             for (int d = 0; d < DIM; d++) axis_w_f32(c[d], o[d], icn[d], wn[d], ich[d], wh[d]);
             float eb[6];
             gather<float, DIM>(F, g, icn, wn, ich, wh, eb);
-            chi = chi_f32(km, kx, ky, kz, eb[0], eb[1], eb[2], eb[3], eb[4], eb[5], (float)q.inv_Es);
+            chi = chi_f32(km, kx, ky, kz, eb[0], eb[1], eb[2], eb[3], eb[4], eb[5], q.inv_Es_f);
             float lnchi;
-            inr = km > 0.f && mlp_in_range_f32(q.nrm, chi, lnchi);
+            inr = km > 0.f && mlp_in_range_f32(q.net_lo_f, q.net_hi_f, chi, lnchi);
             if (inr) {
                 const uint64_t id = q.id[p];
                 philox4x32_10((uint32_t)id, (uint32_t)(id >> 32), q.step, QP_PAIR, q.key[0], q.key[1], w);
-                mlp_inputs_f32(q.nrm, QED_PAIR, lnchi, (float)uniform24(w[0]), x0, x1);
+                mlp_inputs_f32(q.nrm, QED_PAIR, lnchi, uniform24_f32(w[0]), x0, x1);
             }
         }
         if (q.on && __syncthreads_or(inr)) {
@@ -303,7 +303,7 @@ __global__ void __launch_bounds__(kMlpTcRows, 4) k_push_photon_tc(PartF32 P, con
         float4 evd = make_float4(0.f, 0.f, 0.f, 0.f);
         if (q.on) {
             const float G = inr ? mlp_rate_f32(q.nrm, QED_PAIR, chi, y1) : qed_rate_f32(q.T, QED_PAIR, chi);
-            double tau = q.tau[p] - (km > 0.f ? (double)((float)q.pref * G / km) : 0.0);
+            double tau = q.tau[p] - (km > 0.f ? (double)(q.pref_f * G / km) : 0.0);
             if (tau <= 0.0) {
                 if (!inr) {
                     const uint64_t id = q.id[p];

@@ -25,23 +25,27 @@ __device__ __forceinline__ void qed_lepton_f32(const QedParams &q, const unsigne
                                                int *err, uint32_t &event, float4 &evd)
 {
     if (!q.on) return;
-    // chi and the rate in FP32, gamma in FP64 above 1e4, tau in FP64
+    // chi and the rate in FP32, gamma in FP64 above 1e4, tau in FP64.  FP64
+    // runs at 1/73 of the FP32 rate on this GPU: the per-step path keeps to
+    // the one FP64 add of the optical depth (and its compare); the event
+    // kinematics, the FP64 gamma island and Method II take FP64 where needed
     const float uuf = ux * ux + uy * uy + uz * uz;
-    const double uu = (double)ux * ux + (double)uy * uy + (double)uz * uz;
-    const double gam = uuf > 1e8f ? sqrt(1.0 + uu) : (double)sqrtf(1.0f + uuf);
-    const float chi = chi_f32((float)gam, ux, uy, uz, eb[0], eb[1], eb[2], eb[3], eb[4], eb[5], (float)q.inv_Es);
+    const bool island = uuf > 1e8f;
+    const float gamf = island ? (float)sqrt(1.0 + (double)ux * ux + (double)uy * uy + (double)uz * uz)
+                              : sqrtf(1.0f + uuf);
+    const float chi = chi_f32(gamf, ux, uy, uz, eb[0], eb[1], eb[2], eb[3], eb[4], eb[5], q.inv_Es_f);
     uint32_t w[4];
     bool use_net = false;
     float y0 = 0.f, y1 = 0.f;
     if constexpr (SURR) {
         float lnchi;
-        const bool inr = live && mlp_in_range_f32(q.nrm, chi, lnchi);
+        const bool inr = live && mlp_in_range_f32(q.net_lo_f, q.net_hi_f, chi, lnchi);
         if (__any_sync(0xffffffffu, inr)) {
             float x0 = 0.f, x1 = 0.f;
             if (inr) {
                 const uint64_t id = q.id[p];
                 philox4x32_10((uint32_t)id, (uint32_t)(id >> 32), q.step, QP_EMIT, q.key[0], q.key[1], w);
-                mlp_inputs_f32(q.nrm, QED_RAD, lnchi, (float)uniform24(w[0]), x0, x1);
+                mlp_inputs_f32(q.nrm, QED_RAD, lnchi, uniform24_f32(w[0]), x0, x1);
             }
             mlp_eval_warp_sparse(*reinterpret_cast<const MlpImage *>(mlp_smem), inr, x0, x1, y0, y1);
             use_net = inr;
@@ -59,13 +63,14 @@ __device__ __forceinline__ void qed_lepton_f32(const QedParams &q, const unsigne
         philox4x32_10((uint32_t)id, (uint32_t)(id >> 32), q.step, QP_EMIT, q.key[0], q.key[1], w);
         const double r1 = uniform24(w[0]), r2 = uniform24(w[1]);
         const double u0 = r1 * r1 * r1;
+        const double gam = island ? sqrt(1.0 + (double)ux * ux + (double)uy * uy + (double)uz * uz) : (double)gamf;
         const double pacc = 3.0 * r1 * r1 * q.pref * qed_spec_rad(q.T, u0, (double)chi) / gam;
         if (pacc > 1.0) atomicOr(err, ERR_QEDDT);
         emit = r2 < pacc;
         frac = u0;
     } else {
         const float G = use_net ? mlp_rate_f32(q.nrm, QED_RAD, chi, y1) : qed_rate_f32(q.T, QED_RAD, chi);
-        tau = q.tau[p] - (double)((float)q.pref * G / (float)gam);
+        tau = q.tau[p] - (double)(q.pref_f * G / gamf);
         if (tau <= 0.0) {
             if (!use_net) {
                 const uint64_t id = q.id[p];
@@ -78,6 +83,8 @@ __device__ __forceinline__ void qed_lepton_f32(const QedParams &q, const unsigne
         }
     }
     if (emit) {
+        const double uu = (double)ux * ux + (double)uy * uy + (double)uz * uz;
+        const double gam = island ? sqrt(1.0 + uu) : (double)gamf;
         const double eg = frac * gam;
         const double umag = sqrt(uu);
         const double g1 = fmax(gam * (1.0 - frac), 1.0);
@@ -107,19 +114,19 @@ __device__ __forceinline__ void qed_photon_f32(const QedParams &q, const unsigne
                                                long long p, float km, float kx, float ky, float kz, const float *eb,
                                                int *err, uint32_t &event, float4 &evd)
 {
-    const float chi = chi_f32(km, kx, ky, kz, eb[0], eb[1], eb[2], eb[3], eb[4], eb[5], (float)q.inv_Es);
+    const float chi = chi_f32(km, kx, ky, kz, eb[0], eb[1], eb[2], eb[3], eb[4], eb[5], q.inv_Es_f);
     uint32_t w[4];
     bool use_net = false;
     float y0 = 0.f, y1 = 0.f;
     if constexpr (SURR) {
         float lnchi;
-        const bool inr = live && km > 0.f && mlp_in_range_f32(q.nrm, chi, lnchi);
+        const bool inr = live && km > 0.f && mlp_in_range_f32(q.net_lo_f, q.net_hi_f, chi, lnchi);
         if (__any_sync(0xffffffffu, inr)) {
             float x0 = 0.f, x1 = 0.f;
             if (inr) {
                 const uint64_t id = q.id[p];
                 philox4x32_10((uint32_t)id, (uint32_t)(id >> 32), q.step, QP_PAIR, q.key[0], q.key[1], w);
-                mlp_inputs_f32(q.nrm, QED_PAIR, lnchi, (float)uniform24(w[0]), x0, x1);
+                mlp_inputs_f32(q.nrm, QED_PAIR, lnchi, uniform24_f32(w[0]), x0, x1);
             }
             mlp_eval_warp_sparse(*reinterpret_cast<const MlpImage *>(mlp_smem), inr, x0, x1, y0, y1);
             use_net = inr;
@@ -141,7 +148,7 @@ __device__ __forceinline__ void qed_photon_f32(const QedParams &q, const unsigne
         }
     } else {
         const float G = use_net ? mlp_rate_f32(q.nrm, QED_PAIR, chi, y1) : qed_rate_f32(q.T, QED_PAIR, chi);
-        double tau = q.tau[p] - (km > 0.f ? (double)((float)q.pref * G / km) : 0.0);
+        double tau = q.tau[p] - (km > 0.f ? (double)(q.pref_f * G / km) : 0.0);
         if (tau <= 0.0) {
             if (!use_net) {
                 const uint64_t id = q.id[p];

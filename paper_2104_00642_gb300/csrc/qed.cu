@@ -281,6 +281,8 @@ int qed_upload_tables(void *dev, QedTables *T, cudaStream_t st)
     T->bes_ymax = kYmax;
     T->lnchi0 = std::log(kChiMin);
     T->dlnchi = (std::log(kChiMax) - T->lnchi0) / (kNchi - 1);
+    T->lnchi0_f = (float)T->lnchi0;
+    T->inv_dlnchi_f = (float)(1.0 / T->dlnchi);
     return 0;
 }
 

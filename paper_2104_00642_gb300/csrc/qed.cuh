@@ -24,6 +24,7 @@ enum QedProcess { QED_RAD = 0, QED_PAIR = 1 };
 struct QedTables {
     int nchi, nr;
     double lnchi0, dlnchi;
+    float lnchi0_f, inv_dlnchi_f;  // the same in FP32 for the FP32 rate (FP64 is scarce on the device)
     const float *lnG_f[2], *inv_f[2];
     const double *lnG_d[2], *inv_d[2];
     // Bessel functions of Eqs. (23)/(24) for Method II's differential rates:
@@ -38,6 +39,8 @@ struct QedParams {
     int method;       // 1: Method I (optical depth), 2: Method II (per-step acceptance)
     double pref;      // alpha E_s dt / (sqrt3 pi): W dt = pref G(chi) / (gamma or k)
     double inv_Es;    // 1 / E_s
+    float pref_f, inv_Es_f;        // the same in FP32 (the FP32 form's rate and chi)
+    float net_lo_f, net_hi_f;      // the network's trained ln chi range in FP32
     double emin;      // lightest photon kept as a macro-photon (m c^2)
     uint32_t key[2];  // Philox key
     uint32_t step;    // step index (counter word 2)
@@ -270,7 +273,7 @@ __device__ __forceinline__ float qed_rate_f32(const QedTables &T, int p, float c
 {
     if (!(chi > 0.f)) return 0.f;
     const float *L = T.lnG_f[p];
-    const float x = (logf(chi) - (float)T.lnchi0) * (float)(1.0 / T.dlnchi);
+    const float x = (logf(chi) - T.lnchi0_f) * T.inv_dlnchi_f;
     const float sub = p == QED_PAIR ? 8.0f / (3.0f * chi) : 0.f;
     if (x <= 0.f) return p == QED_PAIR ? 0.f : expf(fmaf(x, L[1] - L[0], L[0]));
     const int n = T.nchi;
@@ -312,10 +315,16 @@ __device__ __forceinline__ float mlp_rate_f32(const MlpNorm &n, int p, float chi
 {
     return expf(fmaf(n.sd, y1, n.mu) - (p == QED_PAIR ? 8.0f / (3.0f * chi) : 0.f));
 }
-__device__ __forceinline__ bool mlp_in_range_f32(const MlpNorm &n, float chi, float &lnchi)
+__device__ __forceinline__ bool mlp_in_range_f32(float lo, float hi, float chi, float &lnchi)
 {
     lnchi = chi > 0.f ? logf(chi) : -1e30f;
-    return lnchi >= (float)n.lnchi_lo && lnchi <= (float)n.lnchi_hi;
+    return lnchi >= lo && lnchi <= hi;
+}
+// a 24-bit uniform draw as the network's FP32 input (within an ulp of
+// (float) uniform24(x): the +1/2 offset needs a 25th bit)
+__device__ __forceinline__ float uniform24_f32(uint32_t x)
+{
+    return fmaf((float)(x >> 8), 5.9604644775390625e-08f, 2.98023223876953125e-08f);
 }
 // energy fraction from the sample output y0 at CDF r
 __device__ __forceinline__ double mlp_fraction(int p, float y0, double r)
