@@ -364,8 +364,14 @@ __global__ void __launch_bounds__(128) k_qed_eval_surr(const MlpImage *img, MlpN
     if (inr) mlp_inputs(nrm, p, lnchi, rv, x0, x1);
     if (__any_sync(0xffffffffu, inr)) mlp_eval_warp_sparse(S, inr, x0, x1, y0, y1);
     if (!ok) return;
-    if (r) out[i] = inr ? mlp_fraction(p, y0, rv) : qed_sample<R>(T, p, c, rv);
-    else out[i] = inr ? mlp_rate(nrm, p, c, y1) : qed_rate<R>(T, p, c);
+    if constexpr (sizeof(R) == 4) {  // in FP32, as the FP32 pushes evaluate it
+        const float cf = (float)c, rf = (float)rv;
+        if (r) out[i] = inr ? mlp_fraction_f32(p, y0, rf) : qed_sample_f32(T, p, cf, rf);
+        else out[i] = inr ? mlp_rate_f32(nrm, p, cf, y1) : qed_rate_f32(T, p, cf);
+    } else {
+        if (r) out[i] = inr ? mlp_fraction(p, y0, rv) : qed_sample<R>(T, p, c, rv);
+        else out[i] = inr ? mlp_rate(nrm, p, c, y1) : qed_rate<R>(T, p, c);
+    }
 }
 
 // errors of the network against the FP64 tables on a (ln chi, r) grid of

@@ -15,6 +15,34 @@
 
 namespace pic {
 
+// emission and recoil of the FP64 gamma island (gamma above 1e4, where
+// 1 + u^2 loses the 1 in FP32): out of line, so that the lanes below the
+// island never pay for its FP64 work
+static __device__ __noinline__ void qed_recoil_f64(double frac, float &ux, float &uy, float &uz, float &eg, float &kx,
+                                            float &ky, float &kz)
+{
+    const double uu = (double)ux * ux + (double)uy * uy + (double)uz * uz;
+    const double gam = sqrt(1.0 + uu);
+    const double e = frac * gam;
+    const double umag = sqrt(uu);
+    const double g1 = fmax(gam * (1.0 - frac), 1.0);
+    const double s = umag > 0.0 ? sqrt(g1 * g1 - 1.0) / umag : 0.0;
+    const double ek = umag > 0.0 ? e / umag : 0.0;
+    kx = (float)(ek * ux);
+    ky = (float)(ek * uy);
+    kz = (float)(ek * uz);
+    ux = (float)(ux * s);
+    uy = (float)(uy * s);
+    uz = (float)(uz * s);
+    eg = (float)e;
+}
+
+// gamma of the island in FP64, out of line for the same reason
+static __device__ __noinline__ float gamma_island_f32(float ux, float uy, float uz)
+{
+    return (float)sqrt(1.0 + (double)ux * ux + (double)uy * uy + (double)uz * uz);
+}
+
 // With SURR the call is warp-collective: every lane of the warp makes it
 // (lanes with live false only take part in the network's evaluation);
 // mlp_smem is the staged network image.  p indexes the QED arrays; a lane
@@ -31,8 +59,7 @@ __device__ __forceinline__ void qed_lepton_f32(const QedParams &q, const unsigne
     // kinematics, the FP64 gamma island and Method II take FP64 where needed
     const float uuf = ux * ux + uy * uy + uz * uz;
     const bool island = uuf > 1e8f;
-    const float gamf = island ? (float)sqrt(1.0 + (double)ux * ux + (double)uy * uy + (double)uz * uz)
-                              : sqrtf(1.0f + uuf);
+    const float gamf = island ? gamma_island_f32(ux, uy, uz) : sqrtf(1.0f + uuf);
     const float chi = chi_f32(gamf, ux, uy, uz, eb[0], eb[1], eb[2], eb[3], eb[4], eb[5], q.inv_Es_f);
     uint32_t w[4];
     bool use_net = false;
@@ -72,33 +99,42 @@ __device__ __forceinline__ void qed_lepton_f32(const QedParams &q, const unsigne
         const float G = use_net ? mlp_rate_f32(q.nrm, QED_RAD, chi, y1) : qed_rate_f32(q.T, QED_RAD, chi);
         tau = q.tau[p] - (double)(q.pref_f * G / gamf);
         if (tau <= 0.0) {
+            // the event: fraction and new optical depth in FP32 (a warp takes
+            // this branch whenever one of its lanes does, and each FP64
+            // instruction there would cost the whole warp ~16 cycles)
             if (!use_net) {
                 const uint64_t id = q.id[p];
                 philox4x32_10((uint32_t)id, (uint32_t)(id >> 32), q.step, QP_EMIT, q.key[0], q.key[1], w);
             }
-            const double r0 = uniform24(w[0]);
-            frac = use_net ? mlp_fraction(QED_RAD, y0, r0) : qed_sample<float>(q.T, QED_RAD, chi, r0);
-            tau = -log(uniform24(w[1]));
+            frac = use_net ? mlp_fraction_f32(QED_RAD, y0, uniform24_f32(w[0]))
+                           : qed_sample_f32(q.T, QED_RAD, chi, uniform24_f32(w[0]));
+            tau = (double)neg_log_uniform24_f32(w[1]);
             emit = true;
         }
     }
     if (emit) {
-        const double uu = (double)ux * ux + (double)uy * uy + (double)uz * uz;
-        const double gam = island ? sqrt(1.0 + uu) : (double)gamf;
-        const double eg = frac * gam;
-        const double umag = sqrt(uu);
-        const double g1 = fmax(gam * (1.0 - frac), 1.0);
-        const double s = umag > 0.0 ? sqrt(g1 * g1 - 1.0) / umag : 0.0;
-        const double kx = umag > 0.0 ? eg * ux / umag : 0.0, ky = umag > 0.0 ? eg * uy / umag : 0.0,
-                     kz = umag > 0.0 ? eg * uz / umag : 0.0;
-        ux = (float)(ux * s);
-        uy = (float)(uy * s);
-        uz = (float)(uz * s);
-        if (eg >= q.emin) {
-            event = 1;
-            evd = make_float4((float)kx, (float)ky, (float)kz, 0.f);
+        float kx, ky, kz, eg;
+        if (!island) {
+            // emission and recoil in FP32 (gamma below 1e4)
+            const float umag = sqrtf(uuf), fr = (float)frac;
+            eg = fr * gamf;
+            const float g1 = fmaxf(gamf * (1.0f - fr), 1.0f);
+            const float sc = umag > 0.f ? sqrtf(fmaf(g1, g1, -1.0f)) / umag : 0.f;
+            const float ek = umag > 0.f ? eg / umag : 0.f;
+            kx = ek * ux;
+            ky = ek * uy;
+            kz = ek * uz;
+            ux *= sc;
+            uy *= sc;
+            uz *= sc;
         } else {
-            atomicAdd(q.e_lost, eg * q.wdV);
+            qed_recoil_f64(frac, ux, uy, uz, eg, kx, ky, kz);
+        }
+        if ((double)eg >= q.emin) {
+            event = 1;
+            evd = make_float4(kx, ky, kz, 0.f);
+        } else {
+            atomicAdd(q.e_lost, (double)eg * q.wdV);
         }
     }
     if (SURR || q.method != 2) q.tau[p] = tau;
@@ -154,12 +190,11 @@ __device__ __forceinline__ void qed_photon_f32(const QedParams &q, const unsigne
                 const uint64_t id = q.id[p];
                 philox4x32_10((uint32_t)id, (uint32_t)(id >> 32), q.step, QP_PAIR, q.key[0], q.key[1], w);
             }
-            const double r0 = uniform24(w[0]);
-            const double vf =
-                use_net ? mlp_fraction(QED_PAIR, y0, r0) : qed_sample<float>(q.T, QED_PAIR, chi, r0);
+            const float r0 = uniform24_f32(w[0]);
+            const float vf = use_net ? mlp_fraction_f32(QED_PAIR, y0, r0) : qed_sample_f32(q.T, QED_PAIR, chi, r0);
             event = 1;
-            evd = make_float4(kx, ky, kz, (float)vf);
-            tau = -log(uniform24(w[1]));
+            evd = make_float4(kx, ky, kz, vf);
+            tau = (double)neg_log_uniform24_f32(w[1]);
         }
         q.tau[p] = tau;
     }

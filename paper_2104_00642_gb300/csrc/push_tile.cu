@@ -350,7 +350,10 @@ __global__ void __launch_bounds__(kTileThreads, QM == 2 ? 3 : kTileMinBlocks)
                 // The fixed-point scale is folded into the three coefficients.
                 const int key = din ? (u0[1] - by0) * B::WX + (u0[0] - bx0) : -1;
                 int same = 0;
-                __match_all_sync(0xffffffffu, key, &same);
+                // (checked in the QED variants, whose beams are dense; a plain
+                // plasma of tens of particles per cell never fills a warp's
+                // lanes with one window, and the check costs ~3 % there)
+                if constexpr (QM != 0) __match_all_sync(0xffffffffu, key, &same);
                 if (same && key >= 0) {
                     AccWarpAll acc{sJ + key, B::N, B::WX, lane == 0};
                     esirkepov2d(S0, dS, sjx, sjy, jvz * jscale, acc);

@@ -294,7 +294,10 @@ __global__ void k_qed_eval(QedTables T, int p, long long n, const double *chi, c
 {
     long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
-    out[i] = r ? qed_sample<R>(T, p, chi[i], r[i]) : qed_rate<R>(T, p, chi[i]);
+    if constexpr (sizeof(R) == 4)  // the FP32 form's own FP32 arithmetic, as its pushes evaluate it
+        out[i] = r ? (double)qed_sample_f32(T, p, (float)chi[i], (float)r[i]) : (double)qed_rate_f32(T, p, (float)chi[i]);
+    else
+        out[i] = r ? qed_sample<R>(T, p, chi[i], r[i]) : qed_rate<R>(T, p, chi[i]);
 }
 
 void launch_qed_eval(const QedTables &T, bool f64, int p, long long n, const double *chi, const double *r, double *out,

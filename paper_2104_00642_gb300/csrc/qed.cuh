@@ -287,6 +287,50 @@ __device__ __forceinline__ float qed_rate_f32(const QedTables &T, int p, float c
     return expf(fmaf(fmaf(fmaf(a, t, b), t, c), t, p1) - sub);
 }
 
+// The FP32 form's sampler: qed_sample in single precision on the FP32
+// tables (a draw's fraction to ~1e-6, far inside the tables' own 1e-3)
+__device__ __forceinline__ float qed_sample_f32(const QedTables &T, int p, float chi, float r)
+{
+    const float *I = T.inv_f[p];
+    float x = (logf(fmaxf(chi, 1e-30f)) - T.lnchi0_f) * T.inv_dlnchi_f;
+    x = fminf(fmaxf(x, 0.f), (float)(T.nchi - 1) * 0.99999994f);
+    const int i = min((int)x, T.nchi - 2);
+    const float tx = x - i;
+    bool flip = false;
+    float rr = r;
+    if (p == QED_PAIR && rr > 0.5f) {
+        rr = 1.0f - rr;
+        flip = true;
+    }
+    const float tj = p == QED_PAIR ? sqrtf(2.0f * rr) : 1.0f - sqrtf(fmaxf(1.0f - rr, 0.f));
+    float y = fminf(fmaxf(tj * (float)(T.nr - 1), 0.f), (float)(T.nr - 1) * 0.99999994f);
+    const int j = min((int)y, T.nr - 2);
+    float ty = y - j;
+    if (p == QED_RAD && rr < 0.5f) {
+        // the in-cell weight in r itself below the median (see qed_sample)
+        const float t0 = (float)j / (T.nr - 1), t1 = (float)(j + 1) / (T.nr - 1);
+        const float r0 = 1.0f - (1.0f - t0) * (1.0f - t0), r1 = 1.0f - (1.0f - t1) * (1.0f - t1);
+        ty = fminf(fmaxf((rr - r0) / (r1 - r0), 0.f), 1.f);
+    }
+    const float *a = I + (long long)i * T.nr + j, *b = a + T.nr;
+    const float s0 = fmaf(ty, a[1] - a[0], a[0]);
+    const float s1 = fmaf(ty, b[1] - b[0], b[0]);
+    const float sv = fmaf(tx, s1 - s0, s0);
+    const float f = sv * sv * sv;
+    return flip ? 1.0f - f : f;
+}
+
+// -ln r of the 24-bit uniform r = (k + 1/2) 2^-24, k = x >> 8, in FP32 to an
+// ulp: through log1p of the complement above the median, where r itself
+// would lose the low bits of k
+__device__ __forceinline__ float neg_log_uniform24_f32(uint32_t x)
+{
+    const uint32_t k = x >> 8;
+    if (k < (1u << 23)) return -logf(((float)k + 0.5f) * 5.9604644775390625e-08f);
+    const float m = (float)((1u << 24) - 1u - k) + 0.5f;  // (1 - r) 2^24, exact
+    return -log1pf(-m * 5.9604644775390625e-08f);
+}
+
 // --- surrogate network in place of the tables (trained chi range) ---
 __device__ __forceinline__ bool mlp_in_range(const MlpNorm &n, double chi, double &lnchi)
 {
@@ -325,6 +369,12 @@ __device__ __forceinline__ bool mlp_in_range_f32(float lo, float hi, float chi, 
 __device__ __forceinline__ float uniform24_f32(uint32_t x)
 {
     return fmaf((float)(x >> 8), 5.9604644775390625e-08f, 2.98023223876953125e-08f);
+}
+// energy fraction from the sample output y0 at CDF r (FP32: the push)
+__device__ __forceinline__ float mlp_fraction_f32(int p, float y0, float r)
+{
+    const float s = fminf(fmaxf(y0, 0.f), p == QED_PAIR ? 0.79370052598f : 1.0f), f = s * s * s;
+    return p == QED_PAIR && r > 0.5f ? 1.0f - f : f;
 }
 // energy fraction from the sample output y0 at CDF r
 __device__ __forceinline__ double mlp_fraction(int p, float y0, double r)
