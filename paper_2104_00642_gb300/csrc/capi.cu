@@ -184,8 +184,7 @@ bool use_tile_push(const pic_sim *s, const SpeciesState &p)
     if (s->push_variant == PIC_PUSH_SIMPLE || !p.items_valid || s->precision != PIC_PREC_FP32_CELLOFF ||
         s->g.order != 2 || p.kind != PIC_KIND_MASSIVE)
         return false;
-    // QED leptons: the Monte Carlo is fused into the 2D tiled kernel only
-    if (s->g.dim == 3) return !(s->qed_on && p.qed) && tile3d_push_supported(s->g);
+    if (s->g.dim == 3) return tile3d_push_supported(s->g);
     return s->g.dim == 2 && s->g.tile_log2[0] == s->g.tile_log2[1] &&
            (s->g.tile_log2[0] == 3 || s->g.tile_log2[0] == 4);
 }
@@ -369,8 +368,12 @@ void push_species(pic_sim *s, int i, float *F)
             // the particles sorted into work items on the tiled kernel, those
             // appended since (pairs) on the one-thread-per-particle kernel
             const long long max_items = (long long)tile_items_capacity(p.n_hi, s->g.ntiles, s->g.dim);
-            launch_push_tile2d(P, p.items, p.nitems, max_items, F, s->g, push_const(s, p), s->d_err, s->d_eabs,
-                               s->st, true, &q);
+            if (s->g.dim == 3)
+                launch_push_tile3d(P, p.items, p.nitems, max_items, F, s->g, push_const(s, p), s->d_err, s->d_eabs,
+                                   p.defer + 1, p.defer, s->st, &q);
+            else
+                launch_push_tile2d(P, p.items, p.nitems, max_items, F, s->g, push_const(s, p), s->d_err,
+                                   s->d_eabs, s->st, true, &q);
             launch_push_qed_f32(P, F, s->g, push_const(s, p), q, s->d_err, s->d_eabs, s->st,
                                 p.tile_start + s->g.ntiles);
         } else {

@@ -39,9 +39,12 @@ void launch_push_photon_tile2d(const PartF32 &P, const TileItem *items, const ui
 // 3D: tiles of 4^3 cells, every n_d a multiple of 4
 bool tile3d_push_supported(const Grid &g);
 // (defer: a list of capacity >= the particle count, ndefer its device count;
-// the particles the tiled kernel defers are pushed after it on the global path)
+// the particles the tiled kernel defers are pushed after it on the global
+// path.  q: a QED lepton species' Monte Carlo, fused in -- nullptr or
+// q->on == 0 for none; nothing is deferred then, and the particles appended
+// since the sort are left to launch_push_qed_f32)
 void launch_push_tile3d(const PartF32 &P, const TileItem *items, const uint32_t *nitems, long long max_items,
                         float *F, const Grid &g, const PushConst &pc, int *err, double *e_abs, uint32_t *defer,
-                        uint32_t *ndefer, cudaStream_t st);
+                        uint32_t *ndefer, cudaStream_t st, const QedParams *q = nullptr);
 
 }  // namespace pic

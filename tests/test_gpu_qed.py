@@ -117,15 +117,18 @@ def _oracle_3d():
     return o
 
 
-@pytest.mark.parametrize("prec", [pic.FP32_CELLOFF, pic.FP64_PLAIN])
-def test_monte_carlo_3d_matches_oracle_event_by_event(prec):
+@pytest.mark.parametrize("prec,tiled", [(pic.FP32_CELLOFF, False), (pic.FP64_PLAIN, False),
+                                        (pic.FP32_CELLOFF, True)])
+def test_monte_carlo_3d_matches_oracle_event_by_event(prec, tiled):
     """The same set-up on a periodic 8^3 grid with the electrons spread in 3D
-    (the 3D QED push, photon push and spawn kernels), compared step by step
-    as in 1D; live photons of common events sit where the oracle's are (they
-    move at c along k from the parent's position), and the ensemble energy
-    is conserved."""
+    (the 3D QED push, photon push and spawn kernels; tiled: 4^3 tiles and a
+    sort every 4 steps, the leptons' Monte Carlo fused into the 3D tiled
+    push), compared step by step as in 1D; live photons of common events sit
+    where the oracle's are (they move at c along k from the parent's
+    position), and the ensemble energy is conserved."""
     o = _oracle_3d()
-    s = pic.pic_create(3, _N3, _DX3, Q.DT, Q.species_spec(), seed=Q.SEED, precision=prec)
+    kw = dict(sort_interval=4, tile=(4, 4, 4)) if tiled else {}
+    s = pic.pic_create(3, _N3, _DX3, Q.DT, Q.species_spec(), seed=Q.SEED, precision=prec, **kw)
     s.pic_set_qed(photon_sp=2, electron_sp=0, positron_sp=1, lambda_r_m=Q.LAMBDA)
     s.pic_set_field(pic.BZ, np.full(s.box(), Q.B0))
     s.pic_load_particles(0, *_electrons_3d())
