@@ -217,7 +217,11 @@ def test_surrogate_rates_within_range(trained):
         s.pic_set_qed(photon_sp=2, electron_sp=0, positron_sp=1, lambda_r_m=Q.LAMBDA, mode=pic.QED_SURROGATE)
         n_in, n_out = s.pic_qed_eval(p, c_in), s.pic_qed_eval(p, chi_out)
         assert np.array_equal(n_out, t_out)
-        assert np.max(np.abs(np.log(n_in / t_in))) < reps[p]["max_err_lnG"] * 1.01 + 1e-3
+        # (the FP32 pair rate underflows to 0 below chi ~ 0.03, exp(-8/(3 chi)),
+        # in both modes: there the tables serve both)
+        pos = t_in > 0.0
+        assert np.array_equal(n_in[~pos], t_in[~pos])
+        assert np.max(np.abs(np.log(n_in[pos] / t_in[pos]))) < reps[p]["max_err_lnG"] * 1.01 + 1e-3
     s.pic_set_qed(photon_sp=2, electron_sp=0, positron_sp=1, lambda_r_m=Q.LAMBDA, mode=pic.QED_TABLE)
 
 
