@@ -534,7 +534,9 @@ int check_flags(pic_sim *s)
         if (h & ERR_NONFINITE) return fail(s, PIC_ERR_NONFINITE, "non-finite particle momentum");
         if (h & ERR_CFL) return fail(s, PIC_ERR_CFL, "a particle moved more than one cell in a step");
         if (h & ERR_QEDDT)
-            return fail(s, PIC_ERR_CFL, "QED Method II: an acceptance probability above one (dt too long for it)");
+            return fail(s, PIC_ERR_CFL,
+                        "QED: an acceptance probability above one (Method II: dt too long for it; surrogate: the "
+                        "pair network's rate above the thinning envelope)");
         if (h & ERR_CAPACITY) return fail(s, PIC_ERR_CAPACITY, "species capacity exceeded");
         if (h & ERR_TIMEOUT)
             return fail(s, PIC_ERR_TIMEOUT, "a bounded wait in a kernel ran out (bulk copy or tensor-core commit)");

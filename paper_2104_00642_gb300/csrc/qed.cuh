@@ -89,7 +89,10 @@ __host__ __device__ inline double uniform24(uint32_t x) { return ((double)(x >> 
 // counter words 2-3 of the draws: (step, purpose)
 // (QP_TRAIN + process: training samples of the surrogate network, with the
 // sample index as counter words 0-1 and the training iteration as word 2)
-enum QedPurpose : uint32_t { QP_EMIT = 0, QP_PAIR = 1, QP_INIT = 2, QP_TRAIN = 3 };
+// (QP_THIN: the acceptance draw of a candidate conversion in the surrogate
+// form's thinned pair sampler, purpose 5: 3 and 4 are the two processes'
+// training draws)
+enum QedPurpose : uint32_t { QP_EMIT = 0, QP_PAIR = 1, QP_INIT = 2, QP_TRAIN = 3, QP_THIN = 5 };
 constexpr uint32_t kInitStep = 0xFFFFFFFFu;
 
 // initial optical depth of a particle with identity id
@@ -329,6 +332,18 @@ __device__ __forceinline__ float neg_log_uniform24_f32(uint32_t x)
     if (k < (1u << 23)) return -logf(((float)k + 0.5f) * 5.9604644775390625e-08f);
     const float m = (float)((1u << 24) - 1u - k) + 0.5f;  // (1 - r) 2^24, exact
     return -log1pf(-m * 5.9604644775390625e-08f);
+}
+
+// An analytic upper envelope of the pair rate G_pair(chi) of Eq. (24) for
+// chi in [0.1, 100]: 2.05 chi^(2/3) exp(-8/(3 chi)).  G exp(8/(3 chi)) /
+// chi^(2/3) rises from 0.57 at chi = 0.1 to 1.94 at chi = 100, so the
+// envelope lies 5.5 % above the rate at the top of the range (the network's
+// rate is within 1.3 % of the tables') and 3.6x above it at the bottom,
+// where the rate itself is ~1e-12.
+constexpr float kPairEnvelope = 2.05f;
+__device__ __forceinline__ float pair_envelope_f32(float chi)
+{
+    return kPairEnvelope * cbrtf(chi * chi) * expf(-8.0f / (3.0f * chi));
 }
 
 // --- surrogate network in place of the tables (trained chi range) ---

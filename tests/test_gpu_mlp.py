@@ -341,3 +341,23 @@ def test_what_the_network_gains(trained):
         out[mode] = time.perf_counter() - t0
     s.pic_set_qed(photon_sp=2, electron_sp=0, positron_sp=1, lambda_r_m=Q.LAMBDA, mode=pic.QED_TABLE)
     print("bytes table/net", r["table_bytes"], r["net_bytes"], "eval s", out, "train", r)
+
+
+def test_pair_network_stays_under_the_thinning_envelope(trained):
+    """the surrogate form samples pair creation by thinning an analytic
+    envelope (c chi^(2/3) exp(-8/(3 chi)), csrc/qed.cuh): the trained pair
+    network's rate must stay below it over the whole trained range, or a
+    candidate's acceptance W / W_env would exceed one"""
+    import re
+    s, _ = trained
+    src = open(os.path.join(os.path.dirname(os.path.abspath(__file__)), "..", "paper_2104_00642_gb300", "csrc",
+                            "qed.cuh")).read()
+    c = float(re.search(r"constexpr float kPairEnvelope = ([0-9.]+)f;", src).group(1))
+    s.pic_set_qed(photon_sp=2, electron_sp=0, positron_sp=1, lambda_r_m=Q.LAMBDA, mode=pic.QED_SURROGATE)
+    chi = np.geomspace(0.1, 100.0, 400)
+    g = s.pic_qed_eval(pic.QED_PAIR, chi)
+    s.pic_set_qed(photon_sp=2, electron_sp=0, positron_sp=1, lambda_r_m=Q.LAMBDA, mode=pic.QED_TABLE)
+    env = c * chi ** (2.0 / 3.0) * np.exp(-8.0 / (3.0 * chi))
+    pos = g > 0.0
+    print("largest network rate / envelope", float(np.max(g[pos] / env[pos])))
+    assert np.all(g[pos] < env[pos])
