@@ -2,6 +2,7 @@
 and gradients against the FP64 oracle network, its training against the
 tables, the spectra it samples against Eqs. (23)/(24), the fused Monte Carlo
 with it, and what it gains over the tables."""
+import os
 import time
 
 import numpy as np
