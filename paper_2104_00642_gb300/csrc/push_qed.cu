@@ -196,7 +196,7 @@ __global__ void __launch_bounds__(256, SURR ? 2 : 1) k_push_photon_f32(PartF32 P
         for (int d = 0; d < DIM; d++) axis_w_f32(c[d], o[d], icn[d], wn[d], ich[d], wh[d]);
         float eb[6];
         gather<float, DIM>(F, g, icn, wn, ich, wh, eb);
-        qed_photon_f32<SURR>(q, smem, live, p, km, kx, ky, kz, eb, err, event, evd);
+        qed_photon_f32<SURR>(q, smem, live, p, km, kx, ky, kz, eb, live ? q.tau[p] : 0.0, err, event, evd);
         if (SURR && !live) {
             if (mine && p <= P.n) q.ev[p] = 0;
             return;

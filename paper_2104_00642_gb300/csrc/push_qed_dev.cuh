@@ -146,9 +146,11 @@ __device__ __forceinline__ void qed_lepton_f32(const QedParams &q, const unsigne
 // On a conversion evd = (k, positron fraction v) and event = 1.  With SURR
 // the call is warp-collective as qed_lepton_f32's.
 template <bool SURR>
+// tau_in: the photon's optical depth (q.tau[p], read by the caller: the
+// tiled kernel stages it with the photon's state).
 __device__ __forceinline__ void qed_photon_f32(const QedParams &q, const unsigned char *mlp_smem, bool live,
                                                long long p, float km, float kx, float ky, float kz, const float *eb,
-                                               int *err, uint32_t &event, float4 &evd)
+                                               double tau_in, int *err, uint32_t &event, float4 &evd)
 {
     const float chi = chi_f32(km, kx, ky, kz, eb[0], eb[1], eb[2], eb[3], eb[4], eb[5], q.inv_Es_f);
     uint32_t w[4];
@@ -170,7 +172,7 @@ __device__ __forceinline__ void qed_photon_f32(const QedParams &q, const unsigne
         bool cand = false;
         if (inr) {
             genv = pair_envelope_f32(chi);
-            tau = q.tau[p] - (double)(q.pref_f * genv / km);
+            tau = tau_in - (double)(q.pref_f * genv / km);
             cand = tau <= 0.0;
         }
         if (__any_sync(0xffffffffu, cand)) {
@@ -217,7 +219,7 @@ __device__ __forceinline__ void qed_photon_f32(const QedParams &q, const unsigne
         }
     } else {
         const float G = use_net ? mlp_rate_f32(q.nrm, QED_PAIR, chi, y1) : qed_rate_f32(q.T, QED_PAIR, chi);
-        double tau = q.tau[p] - (km > 0.f ? (double)(q.pref_f * G / km) : 0.0);
+        double tau = tau_in - (km > 0.f ? (double)(q.pref_f * G / km) : 0.0);
         if (tau <= 0.0) {
             if (!use_net) {
                 const uint64_t id = q.id[p];

@@ -460,7 +460,12 @@ __global__ void __launch_bounds__(kTileThreads, SURR ? 3 : kTileMinBlocks)
     __shared__ uint64_t mbar;
     float *smem = smem_raw + ((128u - ((uint32_t)__cvta_generic_to_shared(smem_raw) & 127u)) & 127u) / 4u;
     float *sF = smem;  // 6 components
-    unsigned char *sNet = reinterpret_cast<unsigned char *>(smem) + ((6 * B::N * (int)sizeof(float) + 15) & ~15);
+    // the item's photon state, staged by cp.async while the field box lands:
+    // optical depth (FP64), cell, two offsets, three momentum components
+    double *sTau = reinterpret_cast<double *>(smem + ((6 * B::N + 1) & ~1));
+    uint32_t *sCell = reinterpret_cast<uint32_t *>(sTau + kChunk);
+    float *sSt = reinterpret_cast<float *>(sCell + kChunk);  // off0, off1, k0, k1, k2: kChunk each
+    unsigned char *sNet = reinterpret_cast<unsigned char *>(sSt + 5 * kChunk);
     if constexpr (SURR) mlp_stage(sNet, q.net, kMlpStageBytes);
     const int nit = (int)*nitems;
     const long long V = g.vol;
@@ -490,6 +495,17 @@ __global__ void __launch_bounds__(kTileThreads, SURR ? 3 : kTileMinBlocks)
                 sF[e] = v;
             }
         }
+        for (int i = threadIdx.x; i < m.count; i += blockDim.x) {
+            const int p = m.start + i;
+            cp_async4(sCell + i, P.cell + p);
+            cp_async4(sSt + i, P.off[0] + p);
+            cp_async4(sSt + kChunk + i, P.off[1] + p);
+            cp_async4(sSt + 2 * kChunk + i, P.u[0] + p);
+            cp_async4(sSt + 3 * kChunk + i, P.u[1] + p);
+            cp_async4(sSt + 4 * kChunk + i, P.u[2] + p);
+            if (q.on) cp_async8(sTau + i, q.tau + p);
+        }
+        cp_async_wait_all();
         bool landed = true;
         if (use_tma) {
             landed = mbar_wait(&mbar, phase, 1 << 22);
@@ -504,19 +520,21 @@ __global__ void __launch_bounds__(kTileThreads, SURR ? 3 : kTileMinBlocks)
         for (int pass = 0; pass < npass; pass++) {
             const int li = pass * kTileThreads + threadIdx.x;
             const long long p = (long long)m.start + li;
-            const uint32_t cp = li < m.count ? P.cell[p] : kDead;
+            const uint32_t cp = li < m.count ? sCell[li] : kDead;
             const bool live = cp != kDead;
             int c[2] = {0, 0};
             float o[2] = {0.f, 0.f};
             float kx = 0.f, ky = 0.f, kz = 0.f;
+            double tau0 = 0.0;
             if (live) {
                 int dummy;
                 unpack_cell(g, cp, c[0], c[1], dummy);
-                o[0] = P.off[0][p];
-                o[1] = P.off[1][p];
-                kx = P.u[0][p];
-                ky = P.u[1][p];
-                kz = P.u[2][p];
+                o[0] = sSt[li];
+                o[1] = sSt[kChunk + li];
+                kx = sSt[2 * kChunk + li];
+                ky = sSt[3 * kChunk + li];
+                kz = sSt[4 * kChunk + li];
+                if (q.on) tau0 = sTau[li];
             }
             const float km = sqrtf(kx * kx + ky * ky + kz * kz);
             const float ik = km > 0.f ? 1.0f / km : 0.f;
@@ -537,7 +555,7 @@ __global__ void __launch_bounds__(kTileThreads, SURR ? 3 : kTileMinBlocks)
                     if (gin) gather2d(sF, B::N, B::WX, bx0, by0, icn, wn, ich, wh, eb);
                     else gather2d(Fg, V, rs, 0, 0, icn, wn, ich, wh, eb);
                 }
-                qed_photon_f32<SURR>(q, sNet, live, p, km, kx, ky, kz, eb, err, event, evd);
+                qed_photon_f32<SURR>(q, sNet, live, p, km, kx, ky, kz, eb, tau0, err, event, evd);
             }
             if (li >= m.count) continue;
             if (!live) {
@@ -567,7 +585,7 @@ __global__ void __launch_bounds__(kTileThreads, SURR ? 3 : kTileMinBlocks)
             q.ev[p] = event;
             if (event) reinterpret_cast<float4 *>(q.evk)[p] = evd;
         }
-        __syncthreads();  // the next item's copy overwrites the box
+        __syncthreads();  // the next item's copies overwrite the box and the staging
     }
 }
 
@@ -692,7 +710,9 @@ static void launch_photon_T(const PartF32 &P, const TileItem *items, const uint3
                             const float *F, const Grid &g, const PushConst &pc, int *err, cudaStream_t st,
                             const QedParams &q)
 {
-    constexpr int smem = ((6 * Box2<T>::N * (int)sizeof(float) + 15) & ~15) + 128 + (SURR ? kMlpStageBytes : 0);
+    // field box + staging (tau 8 B, cell 4 B, 5 floats per photon) + network, + TMA alignment
+    constexpr int smem = ((6 * Box2<T>::N + 1) & ~1) * (int)sizeof(float) + kChunk * (8 + 4 + 20) + 128 +
+                         (SURR ? kMlpStageBytes : 0);
     static bool attr = false;
     if (!attr) {
         cudaFuncSetAttribute(k_push_photon_tile2d<T, SURR>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
