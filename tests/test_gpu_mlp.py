@@ -297,10 +297,12 @@ def test_surrogate_monte_carlo_in_the_push(trained):
 
 
 def test_photon_push_tensor_core_network_matches_warp_network(trained):
-    """The photon push evaluates the pair network per warp with mma.sync (the
-    default) or per CTA on tcgen05 (PIC_PUSH_MLP_TC): the same seeded run
-    through both gives the same photons and pairs, and the photons' optical
-    depths (driven by the network's rate) agree to FP32 rounding."""
+    """The photon push with the pair network on tcgen05 (PIC_PUSH_MLP_TC)
+    evaluates the network's rate for every photon in range each step; the
+    default push samples the same rate by thinning an envelope (the network
+    at candidates only).  The same seeded run through both emits the same
+    photons (the leptons' Monte Carlo is the same), and the two pair counts
+    agree within their Poisson noise."""
     s0, _ = trained
     params = {p: s0.pic_mlp_get(p) for p in (pic.QED_EMISSION, pic.QED_PAIR)}
     runs = {}
@@ -312,13 +314,13 @@ def test_photon_push_tensor_core_network_matches_warp_network(trained):
         s.pic_set_field(pic.BZ, np.full(s.box(), Q.B0))
         s.pic_load_particles(0, *Q.electrons())
         s.pic_step(40)
-        gid, gtau = s.pic_get_qed_state(2)
-        runs[variant] = (dict(zip(gid.tolist(), gtau.tolist())), s.pic_particle_count(1))
+        gid, _ = s.pic_get_qed_state(2)
+        runs[variant] = (set(gid.tolist()), s.pic_particle_count(1))
+        s.close()
     (ta, na), (tb, nb) = runs[pic.PUSH_MLP_TC], runs[pic.PUSH_AUTO]
-    assert len(ta) > 256 and abs(len(ta) - len(tb)) <= 2 and abs(na - nb) <= 2, (len(ta), len(tb), na, nb)
-    common = [i for i in ta if i in tb]
-    d = np.array([abs(ta[i] - tb[i]) / max(abs(tb[i]), 1e-12) for i in common])
-    assert len(common) >= len(ta) - 2 and np.median(d) < 1e-5, (len(common), np.median(d), d.max())
+    print("photons", len(ta), len(tb), "positrons", na, nb)
+    assert len(ta) > 256 and ta == tb
+    assert abs(na - nb) <= 4.0 * np.sqrt(2.0 * max(na, nb, 1)) + 2, (na, nb)
 
 
 def test_what_the_network_gains(trained):
