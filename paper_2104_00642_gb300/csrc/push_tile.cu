@@ -438,6 +438,42 @@ __global__ void __launch_bounds__(kTileThreads, QM == 2 ? 3 : kTileMinBlocks)
     }
 }
 
+// The thinned pair sampler's candidates of one warp, resolved together
+// (warp-collective): the network gives each its rate W and positron
+// fraction from one evaluation of up to 32 rows; a candidate converts with
+// probability W / W_env (its draw of purpose QP_THIN) and its optical depth
+// restarts.  Entry: (index in the item, ln chi, W_env's G, chi).
+__device__ __forceinline__ void photon_flush(const QedParams &q, const unsigned char *net, const float4 *queue,
+                                             int count, int start, const float *sSt, int *err)
+{
+    const int lane = threadIdx.x & 31;
+    const bool mine = lane < count;
+    const float4 e = mine ? queue[lane] : make_float4(0.f, 0.f, 1.f, 1.f);
+    const int li = __float_as_int(e.x);
+    const long long p = (long long)start + li;
+    uint32_t w[4] = {0u, 0u, 0u, 0u};
+    float x0 = 0.f, x1 = 0.f, y0 = 0.f, y1 = 0.f;
+    uint64_t id = 0;
+    if (mine) {
+        id = q.id[p];
+        philox4x32_10((uint32_t)id, (uint32_t)(id >> 32), q.step, QP_PAIR, q.key[0], q.key[1], w);
+        mlp_inputs_f32(q.nrm, QED_PAIR, e.y, uniform24_f32(w[0]), x0, x1);
+    }
+    mlp_eval_warp_sparse(*reinterpret_cast<const MlpImage *>(net), mine, x0, x1, y0, y1);
+    if (!mine) return;
+    const float pa = mlp_rate_f32(q.nrm, QED_PAIR, e.w, y1) / e.z;
+    if (pa > 1.0f) atomicOr(err, ERR_QEDDT);
+    uint32_t v[4];
+    philox4x32_10((uint32_t)id, (uint32_t)(id >> 32), q.step, QP_THIN, q.key[0], q.key[1], v);
+    const bool accept = uniform24_f32(v[0]) < pa;
+    q.tau[p] = (double)neg_log_uniform24_f32(w[1]);
+    q.ev[p] = accept ? 1u : 0u;
+    if (accept)
+        reinterpret_cast<float4 *>(q.evk)[p] = make_float4(sSt[2 * kChunk + li], sSt[3 * kChunk + li],
+                                                            sSt[4 * kChunk + li],
+                                                            mlp_fraction_f32(QED_PAIR, y0, uniform24_f32(w[0])));
+}
+
 // ---------------------------------------------------------------------
 // Tiled photon push (2D, FP32).  Photons carry no current, so a work item
 // only stages its tile's field box (one TMA copy) and walks its photons with
@@ -467,6 +503,8 @@ __global__ void __launch_bounds__(kTileThreads, SURR ? 3 : kTileMinBlocks)
     float *sSt = reinterpret_cast<float *>(sCell + kChunk);  // off0, off1, k0, k1, k2: kChunk each
     unsigned char *sNet = reinterpret_cast<unsigned char *>(sSt + 5 * kChunk);
     if constexpr (SURR) mlp_stage(sNet, q.net, kMlpStageBytes);
+    __shared__ float4 sQ[SURR ? kTileThreads : 1];  // SURR: each warp's queue of candidate conversions
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int nit = (int)*nitems;
     const long long V = g.vol;
     const float *Fg = F + g.origin;
@@ -517,6 +555,7 @@ __global__ void __launch_bounds__(kTileThreads, SURR ? 3 : kTileMinBlocks)
         }
         // warp-uniform passes (the network's evaluation is warp-collective)
         const int npass = (m.count + kTileThreads - 1) / kTileThreads;
+        int qn = 0;  // SURR: candidates queued by this warp (the same on every lane)
         for (int pass = 0; pass < npass; pass++) {
             const int li = pass * kTileThreads + threadIdx.x;
             const long long p = (long long)m.start + li;
@@ -543,47 +582,85 @@ __global__ void __launch_bounds__(kTileThreads, SURR ? 3 : kTileMinBlocks)
             drift_f32(c[1], o[1], d1);
             uint32_t event = 0;
             float4 evd = make_float4(0.f, 0.f, 0.f, 0.f);
-            if (q.on) {
-                float eb[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
-                if (live) {
-                    int icn[2], ich[2];
-                    float wn[2][3], wh[2][3];
-                    axis_w_f32(c[0], o[0], icn[0], wn[0], ich[0], wh[0]);
-                    axis_w_f32(c[1], o[1], icn[1], wn[1], ich[1], wh[1]);
-                    const bool gin =
-                        c[0] - 1 >= bx0 && c[0] + 2 < bx0 + B::WX && c[1] - 1 >= by0 && c[1] + 2 < by0 + B::WY;
-                    if (gin) gather2d(sF, B::N, B::WX, bx0, by0, icn, wn, ich, wh, eb);
-                    else gather2d(Fg, V, rs, 0, 0, icn, wn, ich, wh, eb);
+            bool cand = false;  // SURR: a candidate conversion, resolved when the warp's queue is flushed
+            float4 centry = make_float4(0.f, 0.f, 0.f, 0.f);
+            double tau = tau0;
+            if (q.on && live) {
+                float eb[6];
+                int icn[2], ich[2];
+                float wn[2][3], wh[2][3];
+                axis_w_f32(c[0], o[0], icn[0], wn[0], ich[0], wh[0]);
+                axis_w_f32(c[1], o[1], icn[1], wn[1], ich[1], wh[1]);
+                const bool gin =
+                    c[0] - 1 >= bx0 && c[0] + 2 < bx0 + B::WX && c[1] - 1 >= by0 && c[1] + 2 < by0 + B::WY;
+                if (gin) gather2d(sF, B::N, B::WX, bx0, by0, icn, wn, ich, wh, eb);
+                else gather2d(Fg, V, rs, 0, 0, icn, wn, ich, wh, eb);
+                if constexpr (SURR) {
+                    // the thinned sampler of qed_photon_f32, with the network's
+                    // evaluations gathered: candidates join the warp's queue
+                    // and are evaluated 32 at a time
+                    const float chi = chi_f32(km, kx, ky, kz, eb[0], eb[1], eb[2], eb[3], eb[4], eb[5], q.inv_Es_f);
+                    float lnchi;
+                    if (km > 0.f && mlp_in_range_f32(q.net_lo_f, q.net_hi_f, chi, lnchi)) {
+                        const float genv = pair_envelope_f32(chi);
+                        tau = tau0 - (double)(q.pref_f * genv / km);
+                        cand = tau <= 0.0;
+                        centry = make_float4(__int_as_float(li), lnchi, genv, chi);
+                    } else {
+                        qed_photon_f32<false>(q, sNet, true, p, km, kx, ky, kz, eb, tau0, err, event, evd);
+                        tau = -1.0;  // written by qed_photon_f32
+                    }
+                } else {
+                    qed_photon_f32<false>(q, sNet, true, p, km, kx, ky, kz, eb, tau0, err, event, evd);
+                    tau = -1.0;
                 }
-                qed_photon_f32<SURR>(q, sNet, live, p, km, kx, ky, kz, eb, tau0, err, event, evd);
+            }
+            bool dead = false;
+            if (live) {
+                drift_f32(c[0], o[0], d0);
+                drift_f32(c[1], o[1], d1);
+#pragma unroll
+                for (int d = 0; d < 2; d++) {
+                    if (g.bc[d] == PERIODIC) {
+                        if (c[d] < 0) c[d] += g.n[d];
+                        else if (c[d] >= g.n[d]) c[d] -= g.n[d];
+                    } else if (c[d] < 0 || c[d] >= g.n[d]) {
+                        dead = true;
+                    }
+                }
+                if (dead) {
+                    P.cell[p] = kDead;
+                    event = 0;  // a photon leaving through an absorbing face does not convert
+                    cand = false;
+                } else {
+                    P.cell[p] = pack_cell(g, c[0], c[1], 0);
+                }
+                P.off[0][p] = o[0];
+                P.off[1][p] = o[1];
+            }
+            if constexpr (SURR) {
+                const unsigned cm = __ballot_sync(0xffffffffu, cand);
+                const int n = __popc(cm);
+                if (qn + n > 32) {
+                    photon_flush(q, sNet, sQ + warp * 32, qn, m.start, sSt, err);
+                    qn = 0;
+                }
+                if (cand) sQ[warp * 32 + qn + __popc(cm & ((1u << lane) - 1u))] = centry;
+                qn += n;
+                __syncwarp();
             }
             if (li >= m.count) continue;
             if (!live) {
                 q.ev[p] = 0;
                 continue;
             }
-            drift_f32(c[0], o[0], d0);
-            drift_f32(c[1], o[1], d1);
-            bool dead = false;
-#pragma unroll
-            for (int d = 0; d < 2; d++) {
-                if (g.bc[d] == PERIODIC) {
-                    if (c[d] < 0) c[d] += g.n[d];
-                    else if (c[d] >= g.n[d]) c[d] -= g.n[d];
-                } else if (c[d] < 0 || c[d] >= g.n[d]) {
-                    dead = true;
-                }
-            }
-            if (dead) {
-                P.cell[p] = kDead;
-                event = 0;  // a photon leaving through an absorbing face does not convert
-            } else {
-                P.cell[p] = pack_cell(g, c[0], c[1], 0);
-            }
-            P.off[0][p] = o[0];
-            P.off[1][p] = o[1];
+            if (cand) continue;  // tau, flag and event data at the flush
+            if (SURR && q.on && tau >= 0.0) q.tau[p] = tau;  // (in range, no candidate)
             q.ev[p] = event;
             if (event) reinterpret_cast<float4 *>(q.evk)[p] = evd;
+        }
+        if constexpr (SURR) {
+            if (qn) photon_flush(q, sNet, sQ + warp * 32, qn, m.start, sSt, err);
         }
         __syncthreads();  // the next item's copies overwrite the box and the staging
     }

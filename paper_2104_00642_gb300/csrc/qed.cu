@@ -71,18 +71,6 @@ const BesselTable &bessel_table()
     return B;
 }
 
-double cr(const std::vector<double> &L, double x)
-{
-    const int n = (int)L.size();
-    int i = (int)x;
-    if (i < 0) i = 0;
-    if (i > n - 2) i = n - 2;
-    const double t = x - i;
-    const double p0 = L[std::max(i - 1, 0)], p1 = L[i], p2 = L[i + 1], p3 = L[std::min(i + 2, n - 1)];
-    return (((-0.5 * p0 + 1.5 * p1 - 1.5 * p2 + 0.5 * p3) * t + (p0 - 2.5 * p1 + 2.0 * p2 - 0.5 * p3)) * t +
-            (-0.5 * p0 + 0.5 * p2)) * t + p1;
-}
-
 // the host view of the Bessel table in the layout the device reads
 QedTables bessel_view()
 {
