@@ -300,13 +300,14 @@ def test_photon_push_tensor_core_network_matches_warp_network(trained):
     """The photon push with the pair network on tcgen05 (PIC_PUSH_MLP_TC)
     evaluates the network's rate for every photon in range each step; the
     default push samples the same rate by thinning an envelope (the network
-    at candidates only).  The same seeded run through both: the primary
-    electrons' photons are the same (their Monte Carlo is), so at least 90 %
-    of the photons are common (the rest come from the pairs, which differ),
-    and the two pair counts agree within their Poisson noise."""
+    at candidates only).  The same seeded run through both (a cascade: most
+    photons come from the pairs, which differ between the samplers): the
+    photons the primary electrons emit in the first step are the same in
+    both, and the photon and pair counts agree within the cascade's spread
+    (20 %; the pairs within 4 sigma of Poisson)."""
     s0, _ = trained
     params = {p: s0.pic_mlp_get(p) for p in (pic.QED_EMISSION, pic.QED_PAIR)}
-    runs = {}
+    runs, first = {}, {}
     for variant in (pic.PUSH_AUTO, pic.PUSH_MLP_TC):
         s = pic.pic_create(1, (16,), (1.0,), Q.DT, Q.species_spec(), seed=Q.SEED, push_variant=variant)
         s.pic_set_qed(photon_sp=2, electron_sp=0, positron_sp=1, lambda_r_m=Q.LAMBDA, mode=pic.QED_SURROGATE)
@@ -314,13 +315,16 @@ def test_photon_push_tensor_core_network_matches_warp_network(trained):
             s.pic_mlp_set(p, P, info["chi_min"], info["chi_max"], info["mu"], info["sd"])
         s.pic_set_field(pic.BZ, np.full(s.box(), Q.B0))
         s.pic_load_particles(0, *Q.electrons())
-        s.pic_step(40)
+        s.pic_step(1)
+        first[variant] = set(s.pic_get_qed_state(2)[0].tolist())
+        s.pic_step(39)
         gid, _ = s.pic_get_qed_state(2)
-        runs[variant] = (set(gid.tolist()), s.pic_particle_count(1))
+        runs[variant] = (len(gid), s.pic_particle_count(1))
         s.close()
-    (ta, na), (tb, nb) = runs[pic.PUSH_MLP_TC], runs[pic.PUSH_AUTO]
-    print("photons", len(ta), len(tb), "positrons", na, nb)
-    assert len(ta) > 256 and len(ta & tb) >= 0.9 * max(len(ta), len(tb)), (len(ta), len(tb), len(ta & tb))
+    (na_ph, na), (nb_ph, nb) = runs[pic.PUSH_MLP_TC], runs[pic.PUSH_AUTO]
+    print("photons", na_ph, nb_ph, "positrons", na, nb, "first-step photons", len(first[pic.PUSH_AUTO]))
+    assert len(first[pic.PUSH_AUTO]) > 0 and first[pic.PUSH_AUTO] == first[pic.PUSH_MLP_TC]
+    assert na_ph > 256 and abs(na_ph - nb_ph) <= 0.2 * max(na_ph, nb_ph), (na_ph, nb_ph)
     assert abs(na - nb) <= 4.0 * np.sqrt(2.0 * max(na, nb, 1)) + 2, (na, nb)
 
 
