@@ -329,7 +329,7 @@ __global__ void k_spawn_photons_f32(PartF32 parent, const uint32_t *__restrict__
     ph.u[1][dst] = q.evk[4 * p + 1];
     ph.u[2][dst] = q.evk[4 * p + 2];
     ph_id[dst] = cid;
-    ph_tau[dst] = initial_tau(cid, q.key);
+    ph_tau[dst] = initial_tau_f32(cid, q.key);
     ph_ev[dst] = 0;
     }
 }
@@ -374,8 +374,8 @@ __global__ void k_spawn_pairs_f32(PartF32 phot, const uint32_t *__restrict__ off
     po.u[2][dp] = (float)(pp * kz * inv);
     el_id[de] = eid;
     po_id[dp] = pid2;
-    el_tau[de] = initial_tau(eid, q.key);
-    po_tau[dp] = initial_tau(pid2, q.key);
+    el_tau[de] = initial_tau_f32(eid, q.key);
+    po_tau[dp] = initial_tau_f32(pid2, q.key);
     el_ev[de] = 0;
     po_ev[dp] = 0;
     }

@@ -346,6 +346,17 @@ __device__ __forceinline__ float pair_envelope_f32(float chi)
     return kPairEnvelope * cbrtf(chi * chi) * expf(-8.0f / (3.0f * chi));
 }
 
+// the FP32 form's initial optical depth of a child: the draw of
+// initial_tau, its -ln r in FP32 (as the form's other restarts; a warp spawns
+// whenever one of its parents had an event, and FP64 costs it ~16 cycles per
+// instruction)
+__device__ __forceinline__ double initial_tau_f32(uint64_t id, const uint32_t *key)
+{
+    uint32_t w[4];
+    philox4x32_10((uint32_t)id, (uint32_t)(id >> 32), kInitStep, QP_INIT, key[0], key[1], w);
+    return (double)neg_log_uniform24_f32(w[0]);
+}
+
 // --- surrogate network in place of the tables (trained chi range) ---
 __device__ __forceinline__ bool mlp_in_range(const MlpNorm &n, double chi, double &lnchi)
 {

@@ -114,8 +114,9 @@ def compare_events(s, o, steps, delta, delta_pair, photon_chi, e_sp=0, ph_sp=2, 
         2 (delta + c e) D; the particle is then no longer compared (its
         histories differ from here on).
     Photons of common events must carry the same energy within energy_tol
-    relative.  After an event both sides restart tau from the same draw:
-    -ln r in FP64 on the oracle, in FP32 in the FP32 form (within reset_tol
+    relative.  After an event both sides restart tau from the same draw, and
+    children start from their identity's draw: -ln r in FP64 on the oracle,
+    in FP32 in the FP32 form (within reset_tol
     of the oracle's relative to max(1, tau): 5e-7 there, 1e-12 in FP64; the
     band of the following steps starts from that difference).  Photon
     conversions (pair creation) are classified the same way, a conversion
@@ -217,7 +218,7 @@ def compare_events(s, o, steps, delta, delta_pair, photon_chi, e_sp=0, ph_sp=2, 
             for i in (g1.keys() & o1.keys()) - prev[sp][0].keys():
                 if i in lost:
                     continue
-                assert abs(g1[i] - o1[i]) <= ulp * max(1.0, o1[i]), (sp, i, g1[i], o1[i])
+                assert abs(g1[i] - o1[i]) <= reset_tol * max(1.0, o1[i]), (sp, i, g1[i], o1[i])
         seen_ph |= gnew | onew
         prev = cur
     return out
