@@ -219,6 +219,7 @@ def compare_events(s, o, steps, delta, delta_pair, photon_chi, e_sp=0, ph_sp=2, 
                 if i in lost:
                     continue
                 assert abs(g1[i] - o1[i]) <= reset_tol * max(1.0, o1[i]), (sp, i, g1[i], o1[i])
+                band[i] = reset_tol * max(1.0, o1[i])  # the band starts from that difference
         seen_ph |= gnew | onew
         prev = cur
     return out
