@@ -27,19 +27,10 @@ namespace pic {
 // first (optional, device): the particles below it are pushed by the tiled
 // kernel (the ones sorted into its work items); this launch takes the rest
 // (those appended since the sort) and owns their event flags.
+// one particle of k_push_qed_f32 (p0: the first particle it owns)
 template <int DIM, bool SURR>
-__global__ void __launch_bounds__(256, SURR ? 2 : 1) k_push_qed_f32(PartF32 P, float *__restrict__ F, Grid g, PushConst pc,
-                                                      QedParams q, int *err, double *e_abs,
-                                                      const uint32_t *__restrict__ first)
+__device__ __forceinline__ void k_push_qed_f32_one(PartF32 &P, float *__restrict__ F, const Grid &g, const PushConst &pc, const QedParams &q, int *err, double *e_abs, const unsigned char *smem, long long p, long long p0)
 {
-    extern __shared__ __align__(16) unsigned char smem[];
-    const long long p0 = first ? (long long)*first : 0;
-    if ((long long)(blockIdx.x + 1) * blockDim.x <= p0) return;  // the whole block is the tiled kernel's
-    if constexpr (SURR) {
-        mlp_stage(smem, q.net, kMlpStageBytes);
-        __syncthreads();
-    }
-    const long long p = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     const bool mine = p >= p0;
     const bool live = mine && p < *P.dn && P.cell[p] != kDead;
     if (!SURR || !__any_sync(0xffffffffu, live)) {
@@ -148,20 +139,35 @@ __global__ void __launch_bounds__(256, SURR ? 2 : 1) k_push_qed_f32(PartF32 P, f
     if (event) reinterpret_cast<float4 *>(q.evk)[p] = evd;
 }
 
-// SURR: the pair network inside its chi range, as in k_push_qed_f32
-// (first: as in k_push_qed_f32 -- the photons below it are the tiled kernel's)
 template <int DIM, bool SURR>
-__global__ void __launch_bounds__(256, SURR ? 2 : 1) k_push_photon_f32(PartF32 P, const float *__restrict__ F, Grid g, PushConst pc,
-                                                         QedParams q, int *err, const uint32_t *__restrict__ first)
+__global__ void __launch_bounds__(256, SURR ? 2 : 1) k_push_qed_f32(PartF32 P, float *__restrict__ F, Grid g, PushConst pc,
+                                                      QedParams q, int *err, double *e_abs,
+                                                      const uint32_t *__restrict__ first)
 {
     extern __shared__ __align__(16) unsigned char smem[];
-    const long long p0 = first ? (long long)*first : 0;
-    if ((long long)(blockIdx.x + 1) * blockDim.x <= p0) return;  // the whole block is the tiled kernel's
     if constexpr (SURR) {
         mlp_stage(smem, q.net, kMlpStageBytes);
         __syncthreads();
     }
-    const long long p = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (!first) {
+        k_push_qed_f32_one<DIM, SURR>(P, F, g, pc, q, err, e_abs, smem, (long long)blockIdx.x * blockDim.x + threadIdx.x, 0);
+        return;
+    }
+    // the tail after the tiled kernel's particles: a block-uniform grid
+    // stride over [first, P.n] (a grid over the whole range would launch a
+    // block per 256 slots only to find most of them the tiled kernel's)
+    const long long p0 = (long long)*first;
+    const long long stride = (long long)gridDim.x * blockDim.x;
+    for (long long base = (p0 / blockDim.x + blockIdx.x) * blockDim.x; base <= P.n; base += stride)
+        k_push_qed_f32_one<DIM, SURR>(P, F, g, pc, q, err, e_abs, smem, base + threadIdx.x, p0);
+}
+
+// SURR: the pair network inside its chi range, as in k_push_qed_f32
+// (first: as in k_push_qed_f32 -- the photons below it are the tiled kernel's)
+// one particle of k_push_photon_f32 (p0: the first particle it owns)
+template <int DIM, bool SURR>
+__device__ __forceinline__ void k_push_photon_f32_one(PartF32 &P, const float *__restrict__ F, const Grid &g, const PushConst &pc, const QedParams &q, int *err, const unsigned char *smem, long long p, long long p0)
+{
     const bool mine = p >= p0;
     const bool live = mine && p < *P.dn && P.cell[p] != kDead;
     if (!SURR || !__any_sync(0xffffffffu, live)) {
@@ -227,6 +233,28 @@ __global__ void __launch_bounds__(256, SURR ? 2 : 1) k_push_photon_f32(PartF32 P
     for (int d = 0; d < DIM; d++) P.off[d][p] = o[d];
     q.ev[p] = event;
     if (event) reinterpret_cast<float4 *>(q.evk)[p] = evd;
+}
+
+template <int DIM, bool SURR>
+__global__ void __launch_bounds__(256, SURR ? 2 : 1) k_push_photon_f32(PartF32 P, const float *__restrict__ F, Grid g, PushConst pc,
+                                                         QedParams q, int *err, const uint32_t *__restrict__ first)
+{
+    extern __shared__ __align__(16) unsigned char smem[];
+    if constexpr (SURR) {
+        mlp_stage(smem, q.net, kMlpStageBytes);
+        __syncthreads();
+    }
+    if (!first) {
+        k_push_photon_f32_one<DIM, SURR>(P, F, g, pc, q, err, smem, (long long)blockIdx.x * blockDim.x + threadIdx.x, 0);
+        return;
+    }
+    // the tail after the tiled kernel's particles: a block-uniform grid
+    // stride over [first, P.n] (a grid over the whole range would launch a
+    // block per 256 slots only to find most of them the tiled kernel's)
+    const long long p0 = (long long)*first;
+    const long long stride = (long long)gridDim.x * blockDim.x;
+    for (long long base = (p0 / blockDim.x + blockIdx.x) * blockDim.x; base <= P.n; base += stride)
+        k_push_photon_f32_one<DIM, SURR>(P, F, g, pc, q, err, smem, base + threadIdx.x, p0);
 }
 
 // The photon push with the pair network on the tcgen05 tensor cores:
@@ -593,7 +621,7 @@ void launch_push_qed_f32(const PartF32 &P, float *F, const Grid &g, const PushCo
 {
     if (P.n == 0) return;
     note_launch();
-    const int nb = div_up(P.n + 1, 256);
+    const int nb = first ? (int)std::min<long long>(div_up(P.n + 1, 256), 152ll * 8) : div_up(P.n + 1, 256);
     if (q.on && q.net) {
         const int sm = kMlpStageBytes;
         if (g.dim == 1) k_push_qed_f32<1, true><<<nb, 256, sm, st>>>(P, F, g, pc, q, err, e_abs, first);
@@ -611,7 +639,7 @@ void launch_push_photon_f32(const PartF32 &P, const float *F, const Grid &g, con
 {
     if (P.n == 0) return;
     note_launch();
-    const int nb = div_up(P.n + 1, 256);
+    const int nb = first ? (int)std::min<long long>(div_up(P.n + 1, 256), 152ll * 8) : div_up(P.n + 1, 256);
     if (q.on && q.net && tc && !first) {
         const int sm = (int)mlp_tc_smem_bytes();
         static bool attr = false;
