@@ -411,7 +411,7 @@ void push_species(pic_sim *s, int i, double *F)
 // Append this step's QED children, in a fixed order: first the pairs of the
 // photons that converted (electrons, then positrons, in photon order), then
 // the photons emitted by each emitting species in species order (in parent
-// order).  The event flags are exclusive-scanned in array order.
+// order).  The event flags are ranked in array order.
 template <typename R>
 void qed_spawn_views(pic_sim *s)
 {
@@ -422,14 +422,16 @@ void qed_spawn_views(pic_sim *s)
     uint32_t *off = (uint32_t *)s->sort_scratch;
     const int ph = s->qed.photon_sp, el = s->qed.electron_sp, po = s->qed.positron_sp;
     const int dim = s->g.dim;
+    // the scanned sums of the flags' blocks (the spawn kernels rank within a block)
     auto scan = [&](const SpeciesState &p) {
-        scan_exclusive(p.ev, off, p.n_hi + 1, off + p.n_hi + 64, s->st);
-        return off + p.n_hi;  // total
+        const long long nb = scan_blocks(p.n_hi + 1);
+        scan_block_sums(p.ev, p.n_hi + 1, off, off + nb + 64, s->st);
+        return off + nb;  // total
     };
     if (ph >= 0 && el >= 0 && po >= 0 && s->sp[ph].n_hi > 0) {
         SpeciesState &P = s->sp[ph], &E = s->sp[el], &O = s->sp[po];
         const uint32_t *tot = scan(P);
-        launch_spawn_pairs(view(ph), off, tot, qed_params(s, ph), view(el), E.tau[E.cur], E.id[E.cur], E.ev,
+        launch_spawn_pairs(view(ph), off, tot, P.n_hi + 1, qed_params(s, ph), view(el), E.tau[E.cur], E.id[E.cur], E.ev,
                            E.d_count, E.cap, view(po), O.tau[O.cur], O.id[O.cur], O.ev, O.d_count, O.cap, dim,
                            s->d_err, s->st);
         E.n_hi = std::min(E.cap, E.n_hi + P.n_hi);
@@ -446,7 +448,7 @@ void qed_spawn_views(pic_sim *s)
         if (p.kind == PIC_KIND_PHOTON || !p.qed || p.n_hi == 0) continue;
         SpeciesState &P = s->sp[ph];
         const uint32_t *tot = scan(p);
-        launch_spawn_photons(view(i), off, tot, qed_params(s, i), view(ph), P.tau[P.cur], P.id[P.cur], P.ev,
+        launch_spawn_photons(view(i), off, tot, p.n_hi + 1, qed_params(s, i), view(ph), P.tau[P.cur], P.id[P.cur], P.ev,
                              P.d_count, P.cap, dim, s->d_err, s->st);
         P.n_hi = std::min(P.cap, P.n_hi + p.n_hi);
         // (the photons land past the sorted ones: the photon push takes them

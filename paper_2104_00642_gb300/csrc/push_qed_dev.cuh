@@ -167,13 +167,19 @@ __device__ __forceinline__ void qed_photon_f32(const QedParams &q, const unsigne
         // evaluation -- runs at candidates only, not for every photon and step.
         float lnchi;
         const bool inr = live && km > 0.f && mlp_in_range_f32(q.net_lo_f, q.net_hi_f, chi, lnchi);
-        double tau = 0.0;
+        double tau = tau_in;
         float genv = 0.f;
-        bool cand = false;
+        bool cand = false, keep = false;
         if (inr) {
             genv = pair_envelope_f32(chi);
-            tau = tau_in - (double)(q.pref_f * genv / km);
-            cand = tau <= 0.0;
+            const float dtau = q.pref_f * genv / km;
+            // a decrement that is zero in FP32 (the envelope underflows below
+            // chi ~ 0.03) leaves the depth as it is: nothing to update or store
+            keep = dtau == 0.f && tau_in > 0.0;
+            if (!keep) {
+                tau = tau_in - (double)dtau;
+                cand = tau <= 0.0;
+            }
         }
         if (__any_sync(0xffffffffu, cand)) {
             float x0 = 0.f, x1 = 0.f;
@@ -198,7 +204,7 @@ __device__ __forceinline__ void qed_photon_f32(const QedParams &q, const unsigne
                 }
                 tau = (double)neg_log_uniform24_f32(w[1]);
             }
-            q.tau[p] = tau;
+            if (!keep) q.tau[p] = tau;
             return;
         }
         // outside the network's range: the tables, Method I, below
@@ -219,7 +225,9 @@ __device__ __forceinline__ void qed_photon_f32(const QedParams &q, const unsigne
         }
     } else {
         const float G = use_net ? mlp_rate_f32(q.nrm, QED_PAIR, chi, y1) : qed_rate_f32(q.T, QED_PAIR, chi);
-        double tau = tau_in - (km > 0.f ? (double)(q.pref_f * G / km) : 0.0);
+        const float dtau = km > 0.f ? q.pref_f * G / km : 0.f;
+        if (dtau == 0.f && tau_in > 0.0) return;  // a zero rate in FP32 (chi below ~0.03): the depth stays, unstored
+        double tau = tau_in - (double)dtau;
         if (tau <= 0.0) {
             if (!use_net) {
                 const uint64_t id = q.id[p];

@@ -603,9 +603,14 @@ __global__ void __launch_bounds__(kTileThreads, SURR ? 3 : kTileMinBlocks)
                     float lnchi;
                     if (km > 0.f && mlp_in_range_f32(q.net_lo_f, q.net_hi_f, chi, lnchi)) {
                         const float genv = pair_envelope_f32(chi);
-                        tau = tau0 - (double)(q.pref_f * genv / km);
-                        cand = tau <= 0.0;
-                        centry = make_float4(__int_as_float(li), lnchi, genv, chi);
+                        const float dtau = q.pref_f * genv / km;
+                        if (dtau == 0.f && tau0 > 0.0) {
+                            tau = -1.0;  // a zero decrement in FP32: the depth stays, unstored
+                        } else {
+                            tau = tau0 - (double)dtau;
+                            cand = tau <= 0.0;
+                            centry = make_float4(__int_as_float(li), lnchi, genv, chi);
+                        }
                     } else {
                         qed_photon_f32<false>(q, sNet, true, p, km, kx, ky, kz, eb, tau0, err, event, evd);
                         tau = -1.0;  // written by qed_photon_f32

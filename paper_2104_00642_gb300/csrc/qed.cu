@@ -17,6 +17,8 @@
 
 #include "qed.cuh"
 #include "qed_host.cuh"
+#include "scan_dev.cuh"
+#include "sort.cuh"
 
 namespace pic {
 
@@ -298,33 +300,61 @@ void launch_qed_eval(const QedTables &T, bool f64, int p, long long n, const dou
 }
 
 // ---------------------------------------------------------------------
-// spawning: the events of a species are exclusive-scanned in array order and
-// the children appended at the end of their species (deterministic order)
+// spawning: the events of a species are ranked in array order and the
+// children appended at the end of their species (deterministic order).  The
+// ranks come in two passes over the flags: the sums of blocks of kScanItems
+// flags, scanned (scan_block_sums), then the spawn kernel itself, one block
+// of 1024 threads per block of flags, which scans its own flags and adds the
+// block's offset.  A block without an event returns after reading its flags.
 // ---------------------------------------------------------------------
-// the spawn kernels stride over the parents with a grid of a few waves: most
-// parents have no event, and a grid sized to the (host upper bound of the)
-// count would spend its time launching empty blocks
-inline int spawn_blocks(long long n) { return (int)std::min<long long>(div_up(n, 256), 152 * 8); }
+__device__ __forceinline__ bool spawn_ranks(const uint32_t *__restrict__ ev, long long m,
+                                            const uint32_t *__restrict__ bsum, long long &p0, uint32_t f[4],
+                                            uint32_t &run)
+{
+    __shared__ uint32_t sh[32];
+    p0 = (long long)blockIdx.x * kScanItems + threadIdx.x * 4;
+    if (p0 + 3 < m && (reinterpret_cast<uintptr_t>(ev) & 15u) == 0) {
+        const uint4 v = *reinterpret_cast<const uint4 *>(ev + p0);
+        f[0] = v.x;
+        f[1] = v.y;
+        f[2] = v.z;
+        f[3] = v.w;
+    } else {
+#pragma unroll
+        for (int k = 0; k < 4; k++) f[k] = p0 + k < m ? ev[p0 + k] : 0u;
+    }
+    const uint32_t s = f[0] + f[1] + f[2] + f[3];
+    if (!__syncthreads_or(s != 0u)) return false;  // block-uniform
+    uint32_t tot;
+    run = block_excl_scan_1024(s, sh, tot) + bsum[blockIdx.x];
+    return true;
+}
 
-__global__ void k_spawn_photons_f32(PartF32 parent, const uint32_t *__restrict__ off,
-                                    const uint32_t *__restrict__ total, QedParams q, PartF32 ph, double *ph_tau,
+__global__ void __launch_bounds__(1024) k_spawn_photons_f32(PartF32 parent, const uint32_t *__restrict__ bsum,
+                                    const uint32_t *__restrict__ total, long long m, QedParams q, PartF32 ph, double *ph_tau,
                                     uint64_t *ph_id, uint32_t *ph_ev, long long *ph_count, long long ph_cap, int dim,
                                     int *err)
 {
-    const long long p0 = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-    const long long n = *parent.dn;
     const long long base = *ph_count;
-    if (p0 == 0 && base + *total > ph_cap) atomicOr(err, ERR_CAPACITY);
-    for (long long p = p0; p < n; p += (long long)gridDim.x * blockDim.x) {
-    if (!q.ev[p]) continue;
-    const long long dst = base + off[p];
+    if (blockIdx.x == 0 && threadIdx.x == 0 && base + *total > ph_cap) atomicOr(err, ERR_CAPACITY);
+    long long p0;
+    uint32_t f[4], run;
+    if (!spawn_ranks(q.ev, m, bsum, p0, f, run)) return;
+    for (int j = 0; j < 4; j++) {
+    const long long p = p0 + j;
+    const uint32_t rank = run;
+    run += f[j];
+    if (!f[j]) continue;
+    const long long dst = base + rank;
     if (dst >= ph_cap) continue;
     uint32_t w[4];
     const uint64_t pid = q.id[p];
     philox4x32_10((uint32_t)pid, (uint32_t)(pid >> 32), q.step, QP_EMIT, q.key[0], q.key[1], w);
     const uint64_t cid = ((uint64_t)w[3] << 32) | w[2];
     ph.cell[dst] = parent.cell[p];  // the parent's x^{n+1}
-    for (int d = 0; d < dim; d++) ph.off[d][dst] = parent.off[d][p];
+#pragma unroll
+    for (int d = 0; d < 3; d++)
+        if (d < dim) ph.off[d][dst] = parent.off[d][p];  // (constant indices: the views stay in registers)
     ph.u[0][dst] = q.evk[4 * p];
     ph.u[1][dst] = q.evk[4 * p + 1];
     ph.u[2][dst] = q.evk[4 * p + 2];
@@ -334,18 +364,23 @@ __global__ void k_spawn_photons_f32(PartF32 parent, const uint32_t *__restrict__
     }
 }
 
-__global__ void k_spawn_pairs_f32(PartF32 phot, const uint32_t *__restrict__ off, const uint32_t *__restrict__ total,
+__global__ void __launch_bounds__(1024) k_spawn_pairs_f32(PartF32 phot, const uint32_t *__restrict__ bsum, const uint32_t *__restrict__ total, long long m,
                                   QedParams q, PartF32 el, double *el_tau, uint64_t *el_id, uint32_t *el_ev,
                                   long long *el_count, long long el_cap, PartF32 po, double *po_tau, uint64_t *po_id,
                                   uint32_t *po_ev, long long *po_count, long long po_cap, int dim, int *err)
 {
-    const long long p0 = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-    const long long n = *phot.dn;
     const long long be = *el_count, bp = *po_count;
-    if (p0 == 0 && (be + *total > el_cap || bp + *total > po_cap)) atomicOr(err, ERR_CAPACITY);
-    for (long long p = p0; p < n; p += (long long)gridDim.x * blockDim.x) {
-    if (!q.ev[p]) continue;
-    const long long de = be + off[p], dp = bp + off[p];
+    if (blockIdx.x == 0 && threadIdx.x == 0 && (be + *total > el_cap || bp + *total > po_cap))
+        atomicOr(err, ERR_CAPACITY);
+    long long p0;
+    uint32_t f[4], run;
+    if (!spawn_ranks(q.ev, m, bsum, p0, f, run)) return;
+    for (int j = 0; j < 4; j++) {
+    const long long p = p0 + j;
+    const uint32_t rank = run;
+    run += f[j];
+    if (!f[j]) continue;
+    const long long de = be + rank, dp = bp + rank;
     if (de >= el_cap || dp >= po_cap) continue;
     uint32_t w[4];
     const uint64_t pid = q.id[p];
@@ -356,7 +391,9 @@ __global__ void k_spawn_pairs_f32(PartF32 phot, const uint32_t *__restrict__ off
     const double k = sqrt(kx * kx + ky * ky + kz * kz);
     // the pair is born where the photon converted (its x^{n+1}); the photon dies
     const uint32_t cell = phot.cell[p];
-    for (int d = 0; d < dim; d++) {
+#pragma unroll
+    for (int d = 0; d < 3; d++) {
+        if (d >= dim) break;
         el.off[d][de] = phot.off[d][p];
         po.off[d][dp] = phot.off[d][p];
     }
@@ -382,18 +419,22 @@ __global__ void k_spawn_pairs_f32(PartF32 phot, const uint32_t *__restrict__ off
 }
 
 // FP64 plain form: absolute positions, event data as 4 doubles per particle
-__global__ void k_spawn_photons_f64(PartF64 parent, const uint32_t *__restrict__ off,
-                                    const uint32_t *__restrict__ total, QedParams q, PartF64 ph, double *ph_tau,
+__global__ void __launch_bounds__(1024) k_spawn_photons_f64(PartF64 parent, const uint32_t *__restrict__ bsum,
+                                    const uint32_t *__restrict__ total, long long m, QedParams q, PartF64 ph, double *ph_tau,
                                     uint64_t *ph_id, uint32_t *ph_ev, long long *ph_count, long long ph_cap, int dim,
                                     int *err)
 {
-    const long long p0 = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-    const long long n = *parent.dn;
     const long long base = *ph_count;
-    if (p0 == 0 && base + *total > ph_cap) atomicOr(err, ERR_CAPACITY);
-    for (long long p = p0; p < n; p += (long long)gridDim.x * blockDim.x) {
-    if (!q.ev[p]) continue;
-    const long long dst = base + off[p];
+    if (blockIdx.x == 0 && threadIdx.x == 0 && base + *total > ph_cap) atomicOr(err, ERR_CAPACITY);
+    long long p0;
+    uint32_t f[4], run;
+    if (!spawn_ranks(q.ev, m, bsum, p0, f, run)) return;
+    for (int j = 0; j < 4; j++) {
+    const long long p = p0 + j;
+    const uint32_t rank = run;
+    run += f[j];
+    if (!f[j]) continue;
+    const long long dst = base + rank;
     if (dst >= ph_cap) continue;
     uint32_t w[4];
     const uint64_t pid = q.id[p];
@@ -401,7 +442,9 @@ __global__ void k_spawn_photons_f64(PartF64 parent, const uint32_t *__restrict__
     const uint64_t cid = ((uint64_t)w[3] << 32) | w[2];
     const double4 e = reinterpret_cast<const double4 *>(q.evk)[p];
     ph.cell[dst] = parent.cell[p];
-    for (int d = 0; d < dim; d++) ph.x[d][dst] = parent.x[d][p];
+#pragma unroll
+    for (int d = 0; d < 3; d++)
+        if (d < dim) ph.x[d][dst] = parent.x[d][p];
     ph.u[0][dst] = e.x;
     ph.u[1][dst] = e.y;
     ph.u[2][dst] = e.z;
@@ -411,18 +454,23 @@ __global__ void k_spawn_photons_f64(PartF64 parent, const uint32_t *__restrict__
     }
 }
 
-__global__ void k_spawn_pairs_f64(PartF64 phot, const uint32_t *__restrict__ off, const uint32_t *__restrict__ total,
+__global__ void __launch_bounds__(1024) k_spawn_pairs_f64(PartF64 phot, const uint32_t *__restrict__ bsum, const uint32_t *__restrict__ total, long long m,
                                   QedParams q, PartF64 el, double *el_tau, uint64_t *el_id, uint32_t *el_ev,
                                   long long *el_count, long long el_cap, PartF64 po, double *po_tau, uint64_t *po_id,
                                   uint32_t *po_ev, long long *po_count, long long po_cap, int dim, int *err)
 {
-    const long long p0 = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-    const long long n = *phot.dn;
     const long long be = *el_count, bp = *po_count;
-    if (p0 == 0 && (be + *total > el_cap || bp + *total > po_cap)) atomicOr(err, ERR_CAPACITY);
-    for (long long p = p0; p < n; p += (long long)gridDim.x * blockDim.x) {
-    if (!q.ev[p]) continue;
-    const long long de = be + off[p], dp = bp + off[p];
+    if (blockIdx.x == 0 && threadIdx.x == 0 && (be + *total > el_cap || bp + *total > po_cap))
+        atomicOr(err, ERR_CAPACITY);
+    long long p0;
+    uint32_t f[4], run;
+    if (!spawn_ranks(q.ev, m, bsum, p0, f, run)) return;
+    for (int j = 0; j < 4; j++) {
+    const long long p = p0 + j;
+    const uint32_t rank = run;
+    run += f[j];
+    if (!f[j]) continue;
+    const long long de = be + rank, dp = bp + rank;
     if (de >= el_cap || dp >= po_cap) continue;
     uint32_t w[4];
     const uint64_t pid = q.id[p];
@@ -431,7 +479,9 @@ __global__ void k_spawn_pairs_f64(PartF64 phot, const uint32_t *__restrict__ off
     const double4 e = reinterpret_cast<const double4 *>(q.evk)[p];
     const double k = sqrt(e.x * e.x + e.y * e.y + e.z * e.z);
     const uint32_t cell = phot.cell[p];
-    for (int d = 0; d < dim; d++) {
+#pragma unroll
+    for (int d = 0; d < 3; d++) {
+        if (d >= dim) break;
         el.x[d][de] = phot.x[d][p];
         po.x[d][dp] = phot.x[d][p];
     }
@@ -494,48 +544,52 @@ void launch_init_qed(long long first, long long n, uint64_t id0, uint64_t *id, d
     k_init_qed<<<div_up(n, 256), 256, 0, st>>>(first, n, id0, id, tau, key[0], key[1]);
 }
 
-void launch_spawn_photons(const PartF32 &parent, const uint32_t *off, const uint32_t *total, const QedParams &q,
+void launch_spawn_photons(const PartF32 &parent, const uint32_t *bsum, const uint32_t *total, long long m,
+                          const QedParams &q,
                           const PartF32 &ph, double *ph_tau, uint64_t *ph_id, uint32_t *ph_ev, long long *ph_count,
                           long long ph_cap, int dim, int *err, cudaStream_t st)
 {
-    if (parent.n == 0) return;
+    if (parent.n == 0 || m <= 0) return;
     note_launch(2);
-    k_spawn_photons_f32<<<spawn_blocks(parent.n), 256, 0, st>>>(parent, off, total, q, ph, ph_tau, ph_id, ph_ev,
+    k_spawn_photons_f32<<<(int)scan_blocks(m), 1024, 0, st>>>(parent, bsum, total, m, q, ph, ph_tau, ph_id, ph_ev,
                                                               ph_count, ph_cap, dim, err);
     k_add_count<<<1, 1, 0, st>>>(ph_count, total, ph_cap);
 }
 
-void launch_spawn_pairs(const PartF32 &phot, const uint32_t *off, const uint32_t *total, const QedParams &q,
+void launch_spawn_pairs(const PartF32 &phot, const uint32_t *bsum, const uint32_t *total, long long m,
+                        const QedParams &q,
                         const PartF32 &el, double *el_tau, uint64_t *el_id, uint32_t *el_ev, long long *el_count,
                         long long el_cap, const PartF32 &po, double *po_tau, uint64_t *po_id, uint32_t *po_ev,
                         long long *po_count, long long po_cap, int dim, int *err, cudaStream_t st)
 {
-    if (phot.n == 0) return;
+    if (phot.n == 0 || m <= 0) return;
     note_launch(2);
-    k_spawn_pairs_f32<<<spawn_blocks(phot.n), 256, 0, st>>>(phot, off, total, q, el, el_tau, el_id, el_ev, el_count,
+    k_spawn_pairs_f32<<<(int)scan_blocks(m), 1024, 0, st>>>(phot, bsum, total, m, q, el, el_tau, el_id, el_ev, el_count,
                                                           el_cap, po, po_tau, po_id, po_ev, po_count, po_cap, dim, err);
     k_add_pair_counts<<<1, 1, 0, st>>>(el_count, po_count, total, el_cap, po_cap);
 }
 
-void launch_spawn_photons(const PartF64 &parent, const uint32_t *off, const uint32_t *total, const QedParams &q,
+void launch_spawn_photons(const PartF64 &parent, const uint32_t *bsum, const uint32_t *total, long long m,
+                          const QedParams &q,
                           const PartF64 &ph, double *ph_tau, uint64_t *ph_id, uint32_t *ph_ev, long long *ph_count,
                           long long ph_cap, int dim, int *err, cudaStream_t st)
 {
-    if (parent.n == 0) return;
+    if (parent.n == 0 || m <= 0) return;
     note_launch(2);
-    k_spawn_photons_f64<<<spawn_blocks(parent.n), 256, 0, st>>>(parent, off, total, q, ph, ph_tau, ph_id, ph_ev,
+    k_spawn_photons_f64<<<(int)scan_blocks(m), 1024, 0, st>>>(parent, bsum, total, m, q, ph, ph_tau, ph_id, ph_ev,
                                                               ph_count, ph_cap, dim, err);
     k_add_count<<<1, 1, 0, st>>>(ph_count, total, ph_cap);
 }
 
-void launch_spawn_pairs(const PartF64 &phot, const uint32_t *off, const uint32_t *total, const QedParams &q,
+void launch_spawn_pairs(const PartF64 &phot, const uint32_t *bsum, const uint32_t *total, long long m,
+                        const QedParams &q,
                         const PartF64 &el, double *el_tau, uint64_t *el_id, uint32_t *el_ev, long long *el_count,
                         long long el_cap, const PartF64 &po, double *po_tau, uint64_t *po_id, uint32_t *po_ev,
                         long long *po_count, long long po_cap, int dim, int *err, cudaStream_t st)
 {
-    if (phot.n == 0) return;
+    if (phot.n == 0 || m <= 0) return;
     note_launch(2);
-    k_spawn_pairs_f64<<<spawn_blocks(phot.n), 256, 0, st>>>(phot, off, total, q, el, el_tau, el_id, el_ev, el_count,
+    k_spawn_pairs_f64<<<(int)scan_blocks(m), 1024, 0, st>>>(phot, bsum, total, m, q, el, el_tau, el_id, el_ev, el_count,
                                                           el_cap, po, po_tau, po_id, po_ev, po_count, po_cap, dim, err);
     k_add_pair_counts<<<1, 1, 0, st>>>(el_count, po_count, total, el_cap, po_cap);
 }

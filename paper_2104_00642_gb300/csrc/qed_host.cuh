@@ -12,17 +12,21 @@ void launch_qed_eval(const QedTables &T, bool f64, int p, long long n, const dou
                      double *out, cudaStream_t st);
 void launch_init_qed(long long first, long long n, uint64_t id0, uint64_t *id, double *tau, const uint32_t *key,
                      cudaStream_t st);
-void launch_spawn_photons(const PartF32 &parent, const uint32_t *off, const uint32_t *total, const QedParams &q,
+void launch_spawn_photons(const PartF32 &parent, const uint32_t *bsum, const uint32_t *total, long long m,
+                          const QedParams &q,
                           const PartF32 &ph, double *ph_tau, uint64_t *ph_id, uint32_t *ph_ev, long long *ph_count,
                           long long ph_cap, int dim, int *err, cudaStream_t st);
-void launch_spawn_pairs(const PartF32 &phot, const uint32_t *off, const uint32_t *total, const QedParams &q,
+void launch_spawn_pairs(const PartF32 &phot, const uint32_t *bsum, const uint32_t *total, long long m,
+                        const QedParams &q,
                         const PartF32 &el, double *el_tau, uint64_t *el_id, uint32_t *el_ev, long long *el_count,
                         long long el_cap, const PartF32 &po, double *po_tau, uint64_t *po_id, uint32_t *po_ev,
                         long long *po_count, long long po_cap, int dim, int *err, cudaStream_t st);
-void launch_spawn_photons(const PartF64 &parent, const uint32_t *off, const uint32_t *total, const QedParams &q,
+void launch_spawn_photons(const PartF64 &parent, const uint32_t *bsum, const uint32_t *total, long long m,
+                          const QedParams &q,
                           const PartF64 &ph, double *ph_tau, uint64_t *ph_id, uint32_t *ph_ev, long long *ph_count,
                           long long ph_cap, int dim, int *err, cudaStream_t st);
-void launch_spawn_pairs(const PartF64 &phot, const uint32_t *off, const uint32_t *total, const QedParams &q,
+void launch_spawn_pairs(const PartF64 &phot, const uint32_t *bsum, const uint32_t *total, long long m,
+                        const QedParams &q,
                         const PartF64 &el, double *el_tau, uint64_t *el_id, uint32_t *el_ev, long long *el_count,
                         long long el_cap, const PartF64 &po, double *po_tau, uint64_t *po_id, uint32_t *po_ev,
                         long long *po_count, long long po_cap, int dim, int *err, cudaStream_t st);

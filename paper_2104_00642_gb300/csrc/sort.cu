@@ -12,6 +12,7 @@
 // in order, 256 at a time, ranking equal digits with warp match masks and a
 // per-warp prefix.  Every pass is stable, so the final permutation is the
 // one a stable sort by key gives, independent of scheduling.
+#include "scan_dev.cuh"
 #include "sort.cuh"
 
 namespace pic {
@@ -19,7 +20,6 @@ namespace pic {
 constexpr int kSortThreads = 256;
 constexpr int kSortRounds = 16;
 constexpr int kSortItems = kSortThreads * kSortRounds;  // keys per block
-constexpr int kScanItems = 4096;                        // per scan block (1024 threads x 4)
 
 __global__ void k_make_keys(const uint32_t *__restrict__ cell, const long long *__restrict__ dn, long long n,
                             Grid g, uint32_t *key, uint32_t *val)
@@ -105,36 +105,10 @@ __global__ void __launch_bounds__(kSortThreads) k_radix_scatter(const uint32_t *
 // ---------------------------------------------------------------------
 // device-wide exclusive scan of u32 (reduce, scan of block sums, downsweep)
 // ---------------------------------------------------------------------
-__device__ __forceinline__ uint32_t block_excl_scan_1024(uint32_t v, uint32_t *sh, uint32_t &total)
+__global__ void __launch_bounds__(1024) k_scan_reduce(const uint32_t *__restrict__ in, long long m, uint32_t *sums,
+                                                     bool zero_end = false)
 {
-    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    uint32_t x = v;
-#pragma unroll
-    for (int o = 1; o < 32; o <<= 1) {
-        uint32_t y = __shfl_up_sync(0xffffffffu, x, o);
-        if (lane >= o) x += y;
-    }
-    if (lane == 31) sh[warp] = x;
-    __syncthreads();
-    if (warp == 0) {
-        uint32_t s = sh[lane];
-#pragma unroll
-        for (int o = 1; o < 32; o <<= 1) {
-            uint32_t y = __shfl_up_sync(0xffffffffu, s, o);
-            if (lane >= o) s += y;
-        }
-        sh[lane] = s;
-    }
-    __syncthreads();
-    total = sh[31];
-    uint32_t before = warp ? sh[warp - 1] : 0u;
-    uint32_t r = before + x - v;
-    __syncthreads();
-    return r;
-}
-
-__global__ void __launch_bounds__(1024) k_scan_reduce(const uint32_t *__restrict__ in, long long m, uint32_t *sums)
-{
+    if (zero_end && blockIdx.x == 0 && threadIdx.x == 0) sums[gridDim.x] = 0u;  // the slot that scans to the total
     __shared__ uint32_t sh[32];
     long long b0 = (long long)blockIdx.x * kScanItems + threadIdx.x * 4;
     uint32_t s = 0;
@@ -175,6 +149,20 @@ size_t scan_scratch_words(long long m)
     }
     return w + 32;
 }
+
+// the exclusive scan of the sums of in's blocks of kScanItems words:
+// bsum[b] = sum of in[0, b kScanItems), bsum[nb] = the total (nb + 1 words,
+// scratch past them as for scan_exclusive)
+void scan_block_sums(const uint32_t *in, long long m, uint32_t *bsum, uint32_t *scratch, cudaStream_t st)
+{
+    if (m <= 0) return;
+    const long long nb = (m + kScanItems - 1) / kScanItems;
+    note_launch();
+    k_scan_reduce<<<(int)nb, 1024, 0, st>>>(in, m, bsum, true);
+    scan_exclusive(bsum, bsum, nb + 1, scratch, st);
+}
+
+long long scan_blocks(long long m) { return (m + kScanItems - 1) / kScanItems; }
 
 // exclusive scan of m words, in may equal out
 void scan_exclusive(const uint32_t *in, uint32_t *out, long long m, uint32_t *scratch, cudaStream_t st)

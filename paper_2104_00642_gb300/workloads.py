@@ -230,7 +230,7 @@ def laser_foil_2d(nx=2048, ny=1024, cells_per_lambda=64, slab=(1024, 1088), n0=1
 
 def qed_collision_2d(nx=2048, ny=512, cells_per_lambda=32, n_beam=10_000_000, gamma0=1957.0, spread=0.01,
                      sigma_um=1.0, a0=200.0, waist_um=2.0, fwhm_fs=15.0, x_focus_um=6.5, n_peak=0.01,
-                     photon_cap=16.0, pair_cap=0.5, photon_emin=2.0, steps=3000, courant=0.95, seed=SEED0 + 7,
+                     photon_cap=24.0, pair_cap=0.5, photon_emin=2.0, steps=3000, courant=0.95, seed=SEED0 + 7,
                      tile=(16, 16, 1)):
     """Strong-field QED collision (2D3V): a linearly polarised Gaussian laser
     of amplitude a0 enters from x-min and focuses at x_focus; an electron beam
