@@ -303,68 +303,87 @@ void launch_qed_eval(const QedTables &T, bool f64, int p, long long n, const dou
 // spawning: the events of a species are ranked in array order and the
 // children appended at the end of their species (deterministic order).  The
 // ranks come in two passes over the flags: the sums of blocks of kScanItems
-// flags, scanned (scan_block_sums), then the spawn kernel itself, one block
-// of 1024 threads per block of flags, which scans its own flags and adds the
-// block's offset.  A block without an event returns after reading its flags.
+// flags, scanned (scan_block_sums), then the spawn kernel itself, which
+// strides over the blocks of flags: a block whose scanned sums show no event
+// is skipped without reading its flags; otherwise the 256 threads read 16
+// flags each, scan them and add the block's offset.
 // ---------------------------------------------------------------------
+constexpr int kSpawnThreads = 256, kSpawnPer = kScanItems / kSpawnThreads;
+
+inline int spawn_grid(long long m)
+{
+    static int nsm = 0;
+    if (!nsm) {
+        int dev = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+    }
+    return (int)std::min<long long>(scan_blocks(m), 4ll * nsm);
+}
+
+// the flags (0 or 1) of block b, kSpawnPer per thread from p0, as a bit mask,
+// and the rank of this thread's first event; false (block-uniform) when the
+// block has no event
 __device__ __forceinline__ bool spawn_ranks(const uint32_t *__restrict__ ev, long long m,
-                                            const uint32_t *__restrict__ bsum, long long &p0, uint32_t f[4],
-                                            uint32_t &run)
+                                            const uint32_t *__restrict__ bsum, long long b, long long &p0,
+                                            uint32_t &bits, uint32_t &run)
 {
     __shared__ uint32_t sh[32];
-    p0 = (long long)blockIdx.x * kScanItems + threadIdx.x * 4;
-    if (p0 + 3 < m && (reinterpret_cast<uintptr_t>(ev) & 15u) == 0) {
-        const uint4 v = *reinterpret_cast<const uint4 *>(ev + p0);
-        f[0] = v.x;
-        f[1] = v.y;
-        f[2] = v.z;
-        f[3] = v.w;
+    if (bsum[b + 1] == bsum[b]) return false;
+    p0 = b * kScanItems + (long long)threadIdx.x * kSpawnPer;
+    bits = 0;
+    if (p0 + kSpawnPer <= m && (reinterpret_cast<uintptr_t>(ev) & 15u) == 0) {
+#pragma unroll
+        for (int k = 0; k < kSpawnPer; k += 4) {
+            const uint4 v = *reinterpret_cast<const uint4 *>(ev + p0 + k);
+            bits |= (v.x ? 1u : 0u) << k | (v.y ? 2u : 0u) << k | (v.z ? 4u : 0u) << k | (v.w ? 8u : 0u) << k;
+        }
     } else {
 #pragma unroll
-        for (int k = 0; k < 4; k++) f[k] = p0 + k < m ? ev[p0 + k] : 0u;
+        for (int k = 0; k < kSpawnPer; k++)
+            if (p0 + k < m && ev[p0 + k]) bits |= 1u << k;
     }
-    const uint32_t s = f[0] + f[1] + f[2] + f[3];
-    if (!__syncthreads_or(s != 0u)) return false;  // block-uniform
     uint32_t tot;
-    run = block_excl_scan_1024(s, sh, tot) + bsum[blockIdx.x];
+    run = block_excl_scan<kSpawnThreads>((uint32_t)__popc(bits), sh, tot) + bsum[b];
     return true;
 }
 
-__global__ void __launch_bounds__(1024) k_spawn_photons_f32(PartF32 parent, const uint32_t *__restrict__ bsum,
+__global__ void __launch_bounds__(kSpawnThreads) k_spawn_photons_f32(PartF32 parent, const uint32_t *__restrict__ bsum,
                                     const uint32_t *__restrict__ total, long long m, QedParams q, PartF32 ph, double *ph_tau,
                                     uint64_t *ph_id, uint32_t *ph_ev, long long *ph_count, long long ph_cap, int dim,
                                     int *err)
 {
     const long long base = *ph_count;
     if (blockIdx.x == 0 && threadIdx.x == 0 && base + *total > ph_cap) atomicOr(err, ERR_CAPACITY);
-    long long p0;
-    uint32_t f[4], run;
-    if (!spawn_ranks(q.ev, m, bsum, p0, f, run)) return;
-    for (int j = 0; j < 4; j++) {
-    const long long p = p0 + j;
-    const uint32_t rank = run;
-    run += f[j];
-    if (!f[j]) continue;
-    const long long dst = base + rank;
-    if (dst >= ph_cap) continue;
-    uint32_t w[4];
-    const uint64_t pid = q.id[p];
-    philox4x32_10((uint32_t)pid, (uint32_t)(pid >> 32), q.step, QP_EMIT, q.key[0], q.key[1], w);
-    const uint64_t cid = ((uint64_t)w[3] << 32) | w[2];
-    ph.cell[dst] = parent.cell[p];  // the parent's x^{n+1}
+    const long long nb = (m + kScanItems - 1) / kScanItems;
+    for (long long b = blockIdx.x; b < nb; b += gridDim.x) {
+        long long p0;
+        uint32_t bits, run;
+        if (!spawn_ranks(q.ev, m, bsum, b, p0, bits, run)) continue;
+        for (; bits; bits &= bits - 1) {
+            const long long p = p0 + (__ffs(bits) - 1);
+            const uint32_t rank = run++;
+            const long long dst = base + rank;
+            if (dst >= ph_cap) continue;
+            uint32_t w[4];
+            const uint64_t pid = q.id[p];
+            philox4x32_10((uint32_t)pid, (uint32_t)(pid >> 32), q.step, QP_EMIT, q.key[0], q.key[1], w);
+            const uint64_t cid = ((uint64_t)w[3] << 32) | w[2];
+            ph.cell[dst] = parent.cell[p];  // the parent's x^{n+1}
 #pragma unroll
-    for (int d = 0; d < 3; d++)
-        if (d < dim) ph.off[d][dst] = parent.off[d][p];  // (constant indices: the views stay in registers)
-    ph.u[0][dst] = q.evk[4 * p];
-    ph.u[1][dst] = q.evk[4 * p + 1];
-    ph.u[2][dst] = q.evk[4 * p + 2];
-    ph_id[dst] = cid;
-    ph_tau[dst] = initial_tau_f32(cid, q.key);
-    ph_ev[dst] = 0;
+            for (int d = 0; d < 3; d++)
+                if (d < dim) ph.off[d][dst] = parent.off[d][p];  // (constant indices: the views stay in registers)
+            ph.u[0][dst] = q.evk[4 * p];
+            ph.u[1][dst] = q.evk[4 * p + 1];
+            ph.u[2][dst] = q.evk[4 * p + 2];
+            ph_id[dst] = cid;
+            ph_tau[dst] = initial_tau_f32(cid, q.key);
+            ph_ev[dst] = 0;
+        }
     }
 }
 
-__global__ void __launch_bounds__(1024) k_spawn_pairs_f32(PartF32 phot, const uint32_t *__restrict__ bsum, const uint32_t *__restrict__ total, long long m,
+__global__ void __launch_bounds__(kSpawnThreads) k_spawn_pairs_f32(PartF32 phot, const uint32_t *__restrict__ bsum, const uint32_t *__restrict__ total, long long m,
                                   QedParams q, PartF32 el, double *el_tau, uint64_t *el_id, uint32_t *el_ev,
                                   long long *el_count, long long el_cap, PartF32 po, double *po_tau, uint64_t *po_id,
                                   uint32_t *po_ev, long long *po_count, long long po_cap, int dim, int *err)
@@ -372,89 +391,91 @@ __global__ void __launch_bounds__(1024) k_spawn_pairs_f32(PartF32 phot, const ui
     const long long be = *el_count, bp = *po_count;
     if (blockIdx.x == 0 && threadIdx.x == 0 && (be + *total > el_cap || bp + *total > po_cap))
         atomicOr(err, ERR_CAPACITY);
-    long long p0;
-    uint32_t f[4], run;
-    if (!spawn_ranks(q.ev, m, bsum, p0, f, run)) return;
-    for (int j = 0; j < 4; j++) {
-    const long long p = p0 + j;
-    const uint32_t rank = run;
-    run += f[j];
-    if (!f[j]) continue;
-    const long long de = be + rank, dp = bp + rank;
-    if (de >= el_cap || dp >= po_cap) continue;
-    uint32_t w[4];
-    const uint64_t pid = q.id[p];
-    philox4x32_10((uint32_t)pid, (uint32_t)(pid >> 32), q.step, QP_PAIR, q.key[0], q.key[1], w);
-    const uint64_t eid = ((uint64_t)w[3] << 32) | w[2], pid2 = eid + 1;
-    // event data: the photon's momentum k and the positron fraction v
-    const double kx = q.evk[4 * p], ky = q.evk[4 * p + 1], kz = q.evk[4 * p + 2], v = q.evk[4 * p + 3];
-    const double k = sqrt(kx * kx + ky * ky + kz * kz);
-    // the pair is born where the photon converted (its x^{n+1}); the photon dies
-    const uint32_t cell = phot.cell[p];
+    const long long nb = (m + kScanItems - 1) / kScanItems;
+    for (long long b = blockIdx.x; b < nb; b += gridDim.x) {
+        long long p0;
+        uint32_t bits, run;
+        if (!spawn_ranks(q.ev, m, bsum, b, p0, bits, run)) continue;
+        for (; bits; bits &= bits - 1) {
+            const long long p = p0 + (__ffs(bits) - 1);
+            const uint32_t rank = run++;
+            const long long de = be + rank, dp = bp + rank;
+            if (de >= el_cap || dp >= po_cap) continue;
+            uint32_t w[4];
+            const uint64_t pid = q.id[p];
+            philox4x32_10((uint32_t)pid, (uint32_t)(pid >> 32), q.step, QP_PAIR, q.key[0], q.key[1], w);
+            const uint64_t eid = ((uint64_t)w[3] << 32) | w[2], pid2 = eid + 1;
+            // event data: the photon's momentum k and the positron fraction v
+            const double kx = q.evk[4 * p], ky = q.evk[4 * p + 1], kz = q.evk[4 * p + 2], v = q.evk[4 * p + 3];
+            const double k = sqrt(kx * kx + ky * ky + kz * kz);
+            // the pair is born where the photon converted (its x^{n+1}); the photon dies
+            const uint32_t cell = phot.cell[p];
 #pragma unroll
-    for (int d = 0; d < 3; d++) {
-        if (d >= dim) break;
-        el.off[d][de] = phot.off[d][p];
-        po.off[d][dp] = phot.off[d][p];
-    }
-    el.cell[de] = cell;
-    po.cell[dp] = cell;
-    phot.cell[p] = kDead;
-    const double ep = v * k, em = (1.0 - v) * k;  // eps_+ and eps_- (m c^2)
-    const double pm = sqrt(fmax(em * em - 1.0, 0.0)), pp = sqrt(fmax(ep * ep - 1.0, 0.0));
-    const double inv = k > 0.0 ? 1.0 / k : 0.0;
-    el.u[0][de] = (float)(pm * kx * inv);
-    el.u[1][de] = (float)(pm * ky * inv);
-    el.u[2][de] = (float)(pm * kz * inv);
-    po.u[0][dp] = (float)(pp * kx * inv);
-    po.u[1][dp] = (float)(pp * ky * inv);
-    po.u[2][dp] = (float)(pp * kz * inv);
-    el_id[de] = eid;
-    po_id[dp] = pid2;
-    el_tau[de] = initial_tau_f32(eid, q.key);
-    po_tau[dp] = initial_tau_f32(pid2, q.key);
-    el_ev[de] = 0;
-    po_ev[dp] = 0;
+            for (int d = 0; d < 3; d++) {
+                if (d >= dim) break;
+                el.off[d][de] = phot.off[d][p];
+                po.off[d][dp] = phot.off[d][p];
+            }
+            el.cell[de] = cell;
+            po.cell[dp] = cell;
+            phot.cell[p] = kDead;
+            const double ep = v * k, em = (1.0 - v) * k;  // eps_+ and eps_- (m c^2)
+            const double pm = sqrt(fmax(em * em - 1.0, 0.0)), pp = sqrt(fmax(ep * ep - 1.0, 0.0));
+            const double inv = k > 0.0 ? 1.0 / k : 0.0;
+            el.u[0][de] = (float)(pm * kx * inv);
+            el.u[1][de] = (float)(pm * ky * inv);
+            el.u[2][de] = (float)(pm * kz * inv);
+            po.u[0][dp] = (float)(pp * kx * inv);
+            po.u[1][dp] = (float)(pp * ky * inv);
+            po.u[2][dp] = (float)(pp * kz * inv);
+            el_id[de] = eid;
+            po_id[dp] = pid2;
+            el_tau[de] = initial_tau_f32(eid, q.key);
+            po_tau[dp] = initial_tau_f32(pid2, q.key);
+            el_ev[de] = 0;
+            po_ev[dp] = 0;
+        }
     }
 }
 
 // FP64 plain form: absolute positions, event data as 4 doubles per particle
-__global__ void __launch_bounds__(1024) k_spawn_photons_f64(PartF64 parent, const uint32_t *__restrict__ bsum,
+__global__ void __launch_bounds__(kSpawnThreads) k_spawn_photons_f64(PartF64 parent, const uint32_t *__restrict__ bsum,
                                     const uint32_t *__restrict__ total, long long m, QedParams q, PartF64 ph, double *ph_tau,
                                     uint64_t *ph_id, uint32_t *ph_ev, long long *ph_count, long long ph_cap, int dim,
                                     int *err)
 {
     const long long base = *ph_count;
     if (blockIdx.x == 0 && threadIdx.x == 0 && base + *total > ph_cap) atomicOr(err, ERR_CAPACITY);
-    long long p0;
-    uint32_t f[4], run;
-    if (!spawn_ranks(q.ev, m, bsum, p0, f, run)) return;
-    for (int j = 0; j < 4; j++) {
-    const long long p = p0 + j;
-    const uint32_t rank = run;
-    run += f[j];
-    if (!f[j]) continue;
-    const long long dst = base + rank;
-    if (dst >= ph_cap) continue;
-    uint32_t w[4];
-    const uint64_t pid = q.id[p];
-    philox4x32_10((uint32_t)pid, (uint32_t)(pid >> 32), q.step, QP_EMIT, q.key[0], q.key[1], w);
-    const uint64_t cid = ((uint64_t)w[3] << 32) | w[2];
-    const double4 e = reinterpret_cast<const double4 *>(q.evk)[p];
-    ph.cell[dst] = parent.cell[p];
+    const long long nb = (m + kScanItems - 1) / kScanItems;
+    for (long long b = blockIdx.x; b < nb; b += gridDim.x) {
+        long long p0;
+        uint32_t bits, run;
+        if (!spawn_ranks(q.ev, m, bsum, b, p0, bits, run)) continue;
+        for (; bits; bits &= bits - 1) {
+            const long long p = p0 + (__ffs(bits) - 1);
+            const uint32_t rank = run++;
+            const long long dst = base + rank;
+            if (dst >= ph_cap) continue;
+            uint32_t w[4];
+            const uint64_t pid = q.id[p];
+            philox4x32_10((uint32_t)pid, (uint32_t)(pid >> 32), q.step, QP_EMIT, q.key[0], q.key[1], w);
+            const uint64_t cid = ((uint64_t)w[3] << 32) | w[2];
+            const double4 e = reinterpret_cast<const double4 *>(q.evk)[p];
+            ph.cell[dst] = parent.cell[p];
 #pragma unroll
-    for (int d = 0; d < 3; d++)
-        if (d < dim) ph.x[d][dst] = parent.x[d][p];
-    ph.u[0][dst] = e.x;
-    ph.u[1][dst] = e.y;
-    ph.u[2][dst] = e.z;
-    ph_id[dst] = cid;
-    ph_tau[dst] = initial_tau(cid, q.key);
-    ph_ev[dst] = 0;
+            for (int d = 0; d < 3; d++)
+                if (d < dim) ph.x[d][dst] = parent.x[d][p];
+            ph.u[0][dst] = e.x;
+            ph.u[1][dst] = e.y;
+            ph.u[2][dst] = e.z;
+            ph_id[dst] = cid;
+            ph_tau[dst] = initial_tau(cid, q.key);
+            ph_ev[dst] = 0;
+        }
     }
 }
 
-__global__ void __launch_bounds__(1024) k_spawn_pairs_f64(PartF64 phot, const uint32_t *__restrict__ bsum, const uint32_t *__restrict__ total, long long m,
+__global__ void __launch_bounds__(kSpawnThreads) k_spawn_pairs_f64(PartF64 phot, const uint32_t *__restrict__ bsum, const uint32_t *__restrict__ total, long long m,
                                   QedParams q, PartF64 el, double *el_tau, uint64_t *el_id, uint32_t *el_ev,
                                   long long *el_count, long long el_cap, PartF64 po, double *po_tau, uint64_t *po_id,
                                   uint32_t *po_ev, long long *po_count, long long po_cap, int dim, int *err)
@@ -462,47 +483,48 @@ __global__ void __launch_bounds__(1024) k_spawn_pairs_f64(PartF64 phot, const ui
     const long long be = *el_count, bp = *po_count;
     if (blockIdx.x == 0 && threadIdx.x == 0 && (be + *total > el_cap || bp + *total > po_cap))
         atomicOr(err, ERR_CAPACITY);
-    long long p0;
-    uint32_t f[4], run;
-    if (!spawn_ranks(q.ev, m, bsum, p0, f, run)) return;
-    for (int j = 0; j < 4; j++) {
-    const long long p = p0 + j;
-    const uint32_t rank = run;
-    run += f[j];
-    if (!f[j]) continue;
-    const long long de = be + rank, dp = bp + rank;
-    if (de >= el_cap || dp >= po_cap) continue;
-    uint32_t w[4];
-    const uint64_t pid = q.id[p];
-    philox4x32_10((uint32_t)pid, (uint32_t)(pid >> 32), q.step, QP_PAIR, q.key[0], q.key[1], w);
-    const uint64_t eid = ((uint64_t)w[3] << 32) | w[2], pid2 = eid + 1;
-    const double4 e = reinterpret_cast<const double4 *>(q.evk)[p];
-    const double k = sqrt(e.x * e.x + e.y * e.y + e.z * e.z);
-    const uint32_t cell = phot.cell[p];
+    const long long nb = (m + kScanItems - 1) / kScanItems;
+    for (long long b = blockIdx.x; b < nb; b += gridDim.x) {
+        long long p0;
+        uint32_t bits, run;
+        if (!spawn_ranks(q.ev, m, bsum, b, p0, bits, run)) continue;
+        for (; bits; bits &= bits - 1) {
+            const long long p = p0 + (__ffs(bits) - 1);
+            const uint32_t rank = run++;
+            const long long de = be + rank, dp = bp + rank;
+            if (de >= el_cap || dp >= po_cap) continue;
+            uint32_t w[4];
+            const uint64_t pid = q.id[p];
+            philox4x32_10((uint32_t)pid, (uint32_t)(pid >> 32), q.step, QP_PAIR, q.key[0], q.key[1], w);
+            const uint64_t eid = ((uint64_t)w[3] << 32) | w[2], pid2 = eid + 1;
+            const double4 e = reinterpret_cast<const double4 *>(q.evk)[p];
+            const double k = sqrt(e.x * e.x + e.y * e.y + e.z * e.z);
+            const uint32_t cell = phot.cell[p];
 #pragma unroll
-    for (int d = 0; d < 3; d++) {
-        if (d >= dim) break;
-        el.x[d][de] = phot.x[d][p];
-        po.x[d][dp] = phot.x[d][p];
-    }
-    el.cell[de] = cell;
-    po.cell[dp] = cell;
-    phot.cell[p] = kDead;
-    const double ep = e.w * k, em = (1.0 - e.w) * k;
-    const double pm = sqrt(fmax(em * em - 1.0, 0.0)), pp = sqrt(fmax(ep * ep - 1.0, 0.0));
-    const double inv = k > 0.0 ? 1.0 / k : 0.0;
-    el.u[0][de] = pm * e.x * inv;
-    el.u[1][de] = pm * e.y * inv;
-    el.u[2][de] = pm * e.z * inv;
-    po.u[0][dp] = pp * e.x * inv;
-    po.u[1][dp] = pp * e.y * inv;
-    po.u[2][dp] = pp * e.z * inv;
-    el_id[de] = eid;
-    po_id[dp] = pid2;
-    el_tau[de] = initial_tau(eid, q.key);
-    po_tau[dp] = initial_tau(pid2, q.key);
-    el_ev[de] = 0;
-    po_ev[dp] = 0;
+            for (int d = 0; d < 3; d++) {
+                if (d >= dim) break;
+                el.x[d][de] = phot.x[d][p];
+                po.x[d][dp] = phot.x[d][p];
+            }
+            el.cell[de] = cell;
+            po.cell[dp] = cell;
+            phot.cell[p] = kDead;
+            const double ep = e.w * k, em = (1.0 - e.w) * k;
+            const double pm = sqrt(fmax(em * em - 1.0, 0.0)), pp = sqrt(fmax(ep * ep - 1.0, 0.0));
+            const double inv = k > 0.0 ? 1.0 / k : 0.0;
+            el.u[0][de] = pm * e.x * inv;
+            el.u[1][de] = pm * e.y * inv;
+            el.u[2][de] = pm * e.z * inv;
+            po.u[0][dp] = pp * e.x * inv;
+            po.u[1][dp] = pp * e.y * inv;
+            po.u[2][dp] = pp * e.z * inv;
+            el_id[de] = eid;
+            po_id[dp] = pid2;
+            el_tau[de] = initial_tau(eid, q.key);
+            po_tau[dp] = initial_tau(pid2, q.key);
+            el_ev[de] = 0;
+            po_ev[dp] = 0;
+        }
     }
 }
 
@@ -551,7 +573,7 @@ void launch_spawn_photons(const PartF32 &parent, const uint32_t *bsum, const uin
 {
     if (parent.n == 0 || m <= 0) return;
     note_launch(2);
-    k_spawn_photons_f32<<<(int)scan_blocks(m), 1024, 0, st>>>(parent, bsum, total, m, q, ph, ph_tau, ph_id, ph_ev,
+    k_spawn_photons_f32<<<spawn_grid(m), kSpawnThreads, 0, st>>>(parent, bsum, total, m, q, ph, ph_tau, ph_id, ph_ev,
                                                               ph_count, ph_cap, dim, err);
     k_add_count<<<1, 1, 0, st>>>(ph_count, total, ph_cap);
 }
@@ -564,7 +586,7 @@ void launch_spawn_pairs(const PartF32 &phot, const uint32_t *bsum, const uint32_
 {
     if (phot.n == 0 || m <= 0) return;
     note_launch(2);
-    k_spawn_pairs_f32<<<(int)scan_blocks(m), 1024, 0, st>>>(phot, bsum, total, m, q, el, el_tau, el_id, el_ev, el_count,
+    k_spawn_pairs_f32<<<spawn_grid(m), kSpawnThreads, 0, st>>>(phot, bsum, total, m, q, el, el_tau, el_id, el_ev, el_count,
                                                           el_cap, po, po_tau, po_id, po_ev, po_count, po_cap, dim, err);
     k_add_pair_counts<<<1, 1, 0, st>>>(el_count, po_count, total, el_cap, po_cap);
 }
@@ -576,7 +598,7 @@ void launch_spawn_photons(const PartF64 &parent, const uint32_t *bsum, const uin
 {
     if (parent.n == 0 || m <= 0) return;
     note_launch(2);
-    k_spawn_photons_f64<<<(int)scan_blocks(m), 1024, 0, st>>>(parent, bsum, total, m, q, ph, ph_tau, ph_id, ph_ev,
+    k_spawn_photons_f64<<<spawn_grid(m), kSpawnThreads, 0, st>>>(parent, bsum, total, m, q, ph, ph_tau, ph_id, ph_ev,
                                                               ph_count, ph_cap, dim, err);
     k_add_count<<<1, 1, 0, st>>>(ph_count, total, ph_cap);
 }
@@ -589,7 +611,7 @@ void launch_spawn_pairs(const PartF64 &phot, const uint32_t *bsum, const uint32_
 {
     if (phot.n == 0 || m <= 0) return;
     note_launch(2);
-    k_spawn_pairs_f64<<<(int)scan_blocks(m), 1024, 0, st>>>(phot, bsum, total, m, q, el, el_tau, el_id, el_ev, el_count,
+    k_spawn_pairs_f64<<<spawn_grid(m), kSpawnThreads, 0, st>>>(phot, bsum, total, m, q, el, el_tau, el_id, el_ev, el_count,
                                                           el_cap, po, po_tau, po_id, po_ev, po_count, po_cap, dim, err);
     k_add_pair_counts<<<1, 1, 0, st>>>(el_count, po_count, total, el_cap, po_cap);
 }
