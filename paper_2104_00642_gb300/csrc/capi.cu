@@ -313,8 +313,10 @@ QedParams qed_params(pic_sim *s, int i)
     SpeciesState &p = s->sp[i];
     QedParams q{};
     const double alpha = 1.0 / 137.035999084;
-    q.on = s->qed_on && (p.kind == PIC_KIND_PHOTON ? (s->qed.electron_sp >= 0 && s->qed.positron_sp >= 0)
-                                                   : (p.qed && s->qed.photon_sp >= 0));
+    // (photons: only the QED photon species converts; the spawn takes its events)
+    q.on = s->qed_on && (p.kind == PIC_KIND_PHOTON
+                             ? (i == s->qed.photon_sp && s->qed.electron_sp >= 0 && s->qed.positron_sp >= 0)
+                             : (p.qed && s->qed.photon_sp >= 0));
     q.method = s->qed.method == PIC_QED_METHOD2 ? 2 : 1;
     q.pref = alpha * s->Es * s->g.dt / (std::sqrt(3.0) * 3.14159265358979323846);
     q.inv_Es = s->Es > 0.0 ? 1.0 / s->Es : 0.0;
@@ -339,6 +341,8 @@ QedParams qed_params(pic_sim *s, int i)
     q.nrm = net.nrm;
     q.net_lo_f = (float)net.nrm.lnchi_lo;
     q.net_hi_f = (float)net.nrm.lnchi_hi;
+    q.cq = surr && p.kind == PIC_KIND_PHOTON ? s->cand_q : nullptr;
+    q.cq_n = s->cand_n;
     return q;
 }
 
@@ -352,9 +356,11 @@ void push_species(pic_sim *s, int i, float *F)
             // the photons sorted into work items on the tiled kernel, those
             // emitted since on the one-thread-per-particle kernel
             const long long max_items = (long long)tile_items_capacity(p.n_hi, s->g.ntiles, s->g.dim);
+            if (q.on && q.net) cudaMemsetAsync(q.cq_n, 0, sizeof(uint32_t), s->st);  // the candidates' queue
             launch_push_photon_tile2d(P, p.items, p.nitems, max_items, F, s->g, push_const(s, p), q, s->d_err, s->st);
             launch_push_photon_f32(P, F, s->g, push_const(s, p), q, s->d_err, s->st, false,
                                    p.tile_start + s->g.ntiles);
+            launch_photon_resolve(q, P, s->d_err, s->st);
         } else {
             launch_push_photon_f32(P, F, s->g, push_const(s, p), q, s->d_err, s->st,
                                    s->push_variant == PIC_PUSH_MLP_TC);
@@ -846,6 +852,16 @@ int pic_set_qed(pic_sim *s, const pic_qed *Q)
         int rc = dalloc(s, &s->qed_tables, qed_table_bytes());
         if (rc) return rc;
         if (qed_upload_tables(s->qed_tables, &s->T, s->st)) return fail(s, PIC_ERR_CUDA, "pic_set_qed: table upload");
+    }
+    if (Q->mode == PIC_QED_SURROGATE && Q->photon_sp >= 0 && s->precision == PIC_PREC_FP32_CELLOFF) {
+        // the queue of the thinned pair sampler's candidates: one slot per
+        // photon (each queues at most once per step), 32-bit photon indices
+        const long long cap = s->sp[Q->photon_sp].cap;
+        if (cap >= (1ll << 31)) return fail(s, PIC_ERR_ARG, "pic_set_qed: surrogate photons need a capacity below 2^31");
+        if (!s->cand_q)
+            if (int rc = dalloc(s, (void **)&s->cand_q, (size_t)(cap + 32) * sizeof(float4))) return rc;
+        if (!s->cand_n)
+            if (int rc = dalloc(s, (void **)&s->cand_n, sizeof(uint32_t))) return rc;
     }
     // E_s = m c^2 / (hbar omega_r) = m c^2 lambda_r / (h c)
     const double mc2_eV = 510998.95, hc_eVm = 1.239841984e-6;

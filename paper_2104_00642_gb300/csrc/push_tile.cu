@@ -438,40 +438,49 @@ __global__ void __launch_bounds__(kTileThreads, QM == 2 ? 3 : kTileMinBlocks)
     }
 }
 
-// The thinned pair sampler's candidates of one warp, resolved together
-// (warp-collective): the network gives each its rate W and positron
-// fraction from one evaluation of up to 32 rows; a candidate converts with
-// probability W / W_env (its draw of purpose QP_THIN) and its optical depth
-// restarts.  Entry: (index in the item, ln chi, W_env's G, chi).
-__device__ __forceinline__ void photon_flush(const QedParams &q, const unsigned char *net, const float4 *queue,
-                                             int count, int start, const float *sSt, int *err)
+// The surrogate's candidate conversions (the thinned sampler of
+// qed_photon_f32): the tiled photon push appends them to a queue, one slot
+// per photon, and this kernel resolves them, 32 per network evaluation:
+// the pair rate W and the positron fraction from one evaluation, a
+// conversion with probability W / W_env (the candidate's draw of purpose
+// QP_THIN), and the optical depth restarted from -ln r.  The network's
+// registers stay out of the push, which then runs at the table push's
+// occupancy.  Entries: (photon index, ln chi, W_env's G, chi); each
+// candidate's outcome depends on its own entry and draws only, so the
+// queue's order (that of the appends) does not change the result.
+__global__ void __launch_bounds__(256) k_photon_resolve(QedParams q, PartF32 P, int *err)
 {
-    const int lane = threadIdx.x & 31;
-    const bool mine = lane < count;
-    const float4 e = mine ? queue[lane] : make_float4(0.f, 0.f, 1.f, 1.f);
-    const int li = __float_as_int(e.x);
-    const long long p = (long long)start + li;
-    uint32_t w[4] = {0u, 0u, 0u, 0u};
-    float x0 = 0.f, x1 = 0.f, y0 = 0.f, y1 = 0.f;
-    uint64_t id = 0;
-    if (mine) {
-        id = q.id[p];
-        philox4x32_10((uint32_t)id, (uint32_t)(id >> 32), q.step, QP_PAIR, q.key[0], q.key[1], w);
-        mlp_inputs_f32(q.nrm, QED_PAIR, e.y, uniform24_f32(w[0]), x0, x1);
+    extern __shared__ __align__(16) unsigned char net[];
+    mlp_stage(net, q.net, kMlpStageBytes);
+    __syncthreads();
+    const long long n = *q.cq_n;
+    const int lane = threadIdx.x & 31, wpb = blockDim.x >> 5;
+    for (long long wb = (long long)blockIdx.x * wpb + (threadIdx.x >> 5); wb * 32 < n; wb += (long long)gridDim.x * wpb) {
+        const long long i = wb * 32 + lane;  // (warp-uniform loop: the evaluation is warp-collective)
+        const bool mine = i < n;
+        const float4 e = mine ? q.cq[i] : make_float4(0.f, 0.f, 1.f, 1.f);
+        const long long p = (long long)(uint32_t)__float_as_int(e.x);
+        uint32_t w[4] = {0u, 0u, 0u, 0u};
+        float x0 = 0.f, x1 = 0.f, y0 = 0.f, y1 = 0.f;
+        uint64_t id = 0;
+        if (mine) {
+            id = q.id[p];
+            philox4x32_10((uint32_t)id, (uint32_t)(id >> 32), q.step, QP_PAIR, q.key[0], q.key[1], w);
+            mlp_inputs_f32(q.nrm, QED_PAIR, e.y, uniform24_f32(w[0]), x0, x1);
+        }
+        mlp_eval_warp_sparse(*reinterpret_cast<const MlpImage *>(net), mine, x0, x1, y0, y1);
+        if (!mine) continue;
+        const float pa = mlp_rate_f32(q.nrm, QED_PAIR, e.w, y1) / e.z;
+        if (pa > 1.0f) atomicOr(err, ERR_QEDDT);
+        uint32_t v[4];
+        philox4x32_10((uint32_t)id, (uint32_t)(id >> 32), q.step, QP_THIN, q.key[0], q.key[1], v);
+        const bool accept = uniform24_f32(v[0]) < pa;
+        q.tau[p] = (double)neg_log_uniform24_f32(w[1]);
+        q.ev[p] = accept ? 1u : 0u;
+        if (accept)
+            reinterpret_cast<float4 *>(q.evk)[p] =
+                make_float4(P.u[0][p], P.u[1][p], P.u[2][p], mlp_fraction_f32(QED_PAIR, y0, uniform24_f32(w[0])));
     }
-    mlp_eval_warp_sparse(*reinterpret_cast<const MlpImage *>(net), mine, x0, x1, y0, y1);
-    if (!mine) return;
-    const float pa = mlp_rate_f32(q.nrm, QED_PAIR, e.w, y1) / e.z;
-    if (pa > 1.0f) atomicOr(err, ERR_QEDDT);
-    uint32_t v[4];
-    philox4x32_10((uint32_t)id, (uint32_t)(id >> 32), q.step, QP_THIN, q.key[0], q.key[1], v);
-    const bool accept = uniform24_f32(v[0]) < pa;
-    q.tau[p] = (double)neg_log_uniform24_f32(w[1]);
-    q.ev[p] = accept ? 1u : 0u;
-    if (accept)
-        reinterpret_cast<float4 *>(q.evk)[p] = make_float4(sSt[2 * kChunk + li], sSt[3 * kChunk + li],
-                                                            sSt[4 * kChunk + li],
-                                                            mlp_fraction_f32(QED_PAIR, y0, uniform24_f32(w[0])));
 }
 
 // ---------------------------------------------------------------------
@@ -486,7 +495,7 @@ __device__ __forceinline__ void photon_flush(const QedParams &q, const unsigned 
 // range (its image after the field box).
 // ---------------------------------------------------------------------
 template <int T, bool SURR>
-__global__ void __launch_bounds__(kTileThreads, SURR ? 3 : kTileMinBlocks)
+__global__ void __launch_bounds__(kTileThreads, kTileMinBlocks)
     k_push_photon_tile2d(PartF32 P, const TileItem *__restrict__ items, const uint32_t *__restrict__ nitems,
                          const float *__restrict__ F, Grid g, PushConst pc, int *err,
                          const __grid_constant__ CUtensorMap tmap, int use_tma, QedParams q)
@@ -501,10 +510,7 @@ __global__ void __launch_bounds__(kTileThreads, SURR ? 3 : kTileMinBlocks)
     double *sTau = reinterpret_cast<double *>(smem + ((6 * B::N + 1) & ~1));
     uint32_t *sCell = reinterpret_cast<uint32_t *>(sTau + kChunk);
     float *sSt = reinterpret_cast<float *>(sCell + kChunk);  // off0, off1, k0, k1, k2: kChunk each
-    unsigned char *sNet = reinterpret_cast<unsigned char *>(sSt + 5 * kChunk);
-    if constexpr (SURR) mlp_stage(sNet, q.net, kMlpStageBytes);
-    __shared__ float4 sQ[SURR ? kTileThreads : 1];  // SURR: each warp's queue of candidate conversions
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int lane = threadIdx.x & 31;
     const int nit = (int)*nitems;
     const long long V = g.vol;
     const float *Fg = F + g.origin;
@@ -553,9 +559,8 @@ __global__ void __launch_bounds__(kTileThreads, SURR ? 3 : kTileMinBlocks)
             if (threadIdx.x == 0) atomicOr(err, ERR_TIMEOUT);
             return;
         }
-        // warp-uniform passes (the network's evaluation is warp-collective)
+        // warp-uniform passes (the candidates' appends are warp-aggregated)
         const int npass = (m.count + kTileThreads - 1) / kTileThreads;
-        int qn = 0;  // SURR: candidates queued by this warp (the same on every lane)
         for (int pass = 0; pass < npass; pass++) {
             const int li = pass * kTileThreads + threadIdx.x;
             const long long p = (long long)m.start + li;
@@ -582,7 +587,7 @@ __global__ void __launch_bounds__(kTileThreads, SURR ? 3 : kTileMinBlocks)
             drift_f32(c[1], o[1], d1);
             uint32_t event = 0;
             float4 evd = make_float4(0.f, 0.f, 0.f, 0.f);
-            bool cand = false;  // SURR: a candidate conversion, resolved when the warp's queue is flushed
+            bool cand = false;  // SURR: a candidate conversion, resolved by k_photon_resolve
             float4 centry = make_float4(0.f, 0.f, 0.f, 0.f);
             double tau = tau0;
             if (q.on && live) {
@@ -597,8 +602,8 @@ __global__ void __launch_bounds__(kTileThreads, SURR ? 3 : kTileMinBlocks)
                 else gather2d(Fg, V, rs, 0, 0, icn, wn, ich, wh, eb);
                 if constexpr (SURR) {
                     // the thinned sampler of qed_photon_f32, with the network's
-                    // evaluations gathered: candidates join the warp's queue
-                    // and are evaluated 32 at a time
+                    // evaluations gathered: candidates go to the queue that
+                    // k_photon_resolve evaluates 32 at a time
                     const float chi = chi_f32(km, kx, ky, kz, eb[0], eb[1], eb[2], eb[3], eb[4], eb[5], q.inv_Es_f);
                     float lnchi;
                     if (km > 0.f && mlp_in_range_f32(q.net_lo_f, q.net_hi_f, chi, lnchi)) {
@@ -609,14 +614,14 @@ __global__ void __launch_bounds__(kTileThreads, SURR ? 3 : kTileMinBlocks)
                         } else {
                             tau = tau0 - (double)dtau;
                             cand = tau <= 0.0;
-                            centry = make_float4(__int_as_float(li), lnchi, genv, chi);
+                            centry = make_float4(__int_as_float((int)p), lnchi, genv, chi);
                         }
                     } else {
-                        qed_photon_f32<false>(q, sNet, true, p, km, kx, ky, kz, eb, tau0, err, event, evd);
+                        qed_photon_f32<false>(q, nullptr, true, p, km, kx, ky, kz, eb, tau0, err, event, evd);
                         tau = -1.0;  // written by qed_photon_f32
                     }
                 } else {
-                    qed_photon_f32<false>(q, sNet, true, p, km, kx, ky, kz, eb, tau0, err, event, evd);
+                    qed_photon_f32<false>(q, nullptr, true, p, km, kx, ky, kz, eb, tau0, err, event, evd);
                     tau = -1.0;
                 }
             }
@@ -645,27 +650,22 @@ __global__ void __launch_bounds__(kTileThreads, SURR ? 3 : kTileMinBlocks)
             }
             if constexpr (SURR) {
                 const unsigned cm = __ballot_sync(0xffffffffu, cand);
-                const int n = __popc(cm);
-                if (qn + n > 32) {
-                    photon_flush(q, sNet, sQ + warp * 32, qn, m.start, sSt, err);
-                    qn = 0;
+                if (cm) {
+                    uint32_t at = 0;
+                    if (lane == 0) at = atomicAdd(q.cq_n, (uint32_t)__popc(cm));
+                    at = __shfl_sync(0xffffffffu, at, 0);
+                    if (cand) q.cq[at + __popc(cm & ((1u << lane) - 1u))] = centry;
                 }
-                if (cand) sQ[warp * 32 + qn + __popc(cm & ((1u << lane) - 1u))] = centry;
-                qn += n;
-                __syncwarp();
             }
             if (li >= m.count) continue;
             if (!live) {
                 q.ev[p] = 0;
                 continue;
             }
-            if (cand) continue;  // tau, flag and event data at the flush
+            if (cand) continue;  // tau, flag and event data by k_photon_resolve
             if (SURR && q.on && tau >= 0.0) q.tau[p] = tau;  // (in range, no candidate)
             q.ev[p] = event;
             if (event) reinterpret_cast<float4 *>(q.evk)[p] = evd;
-        }
-        if constexpr (SURR) {
-            if (qn) photon_flush(q, sNet, sQ + warp * 32, qn, m.start, sSt, err);
         }
         __syncthreads();  // the next item's copies overwrite the box and the staging
     }
@@ -792,9 +792,8 @@ static void launch_photon_T(const PartF32 &P, const TileItem *items, const uint3
                             const float *F, const Grid &g, const PushConst &pc, int *err, cudaStream_t st,
                             const QedParams &q)
 {
-    // field box + staging (tau 8 B, cell 4 B, 5 floats per photon) + network, + TMA alignment
-    constexpr int smem = ((6 * Box2<T>::N + 1) & ~1) * (int)sizeof(float) + kChunk * (8 + 4 + 20) + 128 +
-                         (SURR ? kMlpStageBytes : 0);
+    // field box + staging (tau 8 B, cell 4 B, 5 floats per photon), + TMA alignment
+    constexpr int smem = ((6 * Box2<T>::N + 1) & ~1) * (int)sizeof(float) + kChunk * (8 + 4 + 20) + 128;
     static bool attr = false;
     if (!attr) {
         cudaFuncSetAttribute(k_push_photon_tile2d<T, SURR>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
@@ -824,7 +823,7 @@ void launch_push_photon_tile2d(const PartF32 &P, const TileItem *items, const ui
                                cudaStream_t st)
 {
     if (P.n == 0) return;
-    const bool surr = q.on && q.net;
+    const bool surr = q.on && q.net && q.cq;  // (the C ABI gives the QED photon species its queue)
     if ((1 << g.tile_log2[0]) == 16) {
         if (surr) launch_photon_T<16, true>(P, items, nitems, max_items, F, g, pc, err, st, q);
         else launch_photon_T<16, false>(P, items, nitems, max_items, F, g, pc, err, st, q);
@@ -832,6 +831,24 @@ void launch_push_photon_tile2d(const PartF32 &P, const TileItem *items, const ui
         if (surr) launch_photon_T<8, true>(P, items, nitems, max_items, F, g, pc, err, st, q);
         else launch_photon_T<8, false>(P, items, nitems, max_items, F, g, pc, err, st, q);
     }
+}
+
+void launch_photon_resolve(const QedParams &q, const PartF32 &P, int *err, cudaStream_t st)
+{
+    if (!q.on || !q.net || !q.cq) return;
+    static bool attr = false;
+    if (!attr) {
+        cudaFuncSetAttribute(k_photon_resolve, cudaFuncAttributeMaxDynamicSharedMemorySize, kMlpStageBytes);
+        attr = true;
+    }
+    static int nsm = 0;
+    if (!nsm) {
+        int dev = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+    }
+    note_launch();
+    k_photon_resolve<<<nsm, 256, kMlpStageBytes, st>>>(q, P, err);
 }
 
 }  // namespace pic

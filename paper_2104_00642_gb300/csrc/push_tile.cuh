@@ -36,6 +36,8 @@ void launch_push_tile2d(const PartF32 &P, const TileItem *items, const uint32_t 
 void launch_push_photon_tile2d(const PartF32 &P, const TileItem *items, const uint32_t *nitems, long long max_items,
                                const float *F, const Grid &g, const PushConst &pc, const QedParams &q, int *err,
                                cudaStream_t st);
+// the surrogate's candidate conversions queued by the tiled photon push (q.cq)
+void launch_photon_resolve(const QedParams &q, const PartF32 &P, int *err, cudaStream_t st);
 // 3D: tiles of 4^3 cells, every n_d a multiple of 4
 bool tile3d_push_supported(const Grid &g);
 // (defer: a list of capacity >= the particle count, ndefer its device count;

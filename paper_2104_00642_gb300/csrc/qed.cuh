@@ -53,6 +53,11 @@ struct QedParams {
     double wdV;       // weight * cell volume of this species (energy tallies)
     const MlpImage *net;  // surrogate network of this species' process (nullptr: tables only)
     MlpNorm nrm;          // its trained chi range and normalisation
+    // photons with the network: the tiled push appends the thinned sampler's
+    // candidates here (photon index, ln chi, W_env's G, chi) for
+    // k_photon_resolve; one slot per photon, cq_n counts them
+    float4 *cq;
+    uint32_t *cq_n;
 };
 
 // ---------------------------------------------------------------------

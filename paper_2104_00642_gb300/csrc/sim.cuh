@@ -57,6 +57,8 @@ struct pic_sim {
     pic_qed qed{};
     bool qed_on = false;
     void *qed_tables = nullptr;
+    float4 *cand_q = nullptr;    // the photons' candidate conversions (surrogate form), one slot per photon
+    uint32_t *cand_n = nullptr;
     pic::QedTables T{};
     double Es = 0.0;
     double *d_elost = nullptr;
