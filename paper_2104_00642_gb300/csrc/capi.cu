@@ -358,8 +358,11 @@ void push_species(pic_sim *s, int i, float *F)
             const long long max_items = (long long)tile_items_capacity(p.n_hi, s->g.ntiles, s->g.dim);
             if (q.on && q.net) cudaMemsetAsync(q.cq_n, 0, sizeof(uint32_t), s->st);  // the candidates' queue
             launch_push_photon_tile2d(P, p.items, p.nitems, max_items, F, s->g, push_const(s, p), q, s->d_err, s->st);
-            launch_push_photon_f32(P, F, s->g, push_const(s, p), q, s->d_err, s->st, false,
-                                   p.tile_start + s->g.ntiles);
+            // the photons appended since the sort: items of consecutive
+            // photons (appended in their parents' tile order), on the same kernel
+            launch_tail_items(P, p.tile_start + s->g.ntiles, s->g, p.tail_items, p.tail_nitems, q.ev, s->st);
+            launch_push_photon_tile2d(P, p.tail_items, p.tail_nitems, (long long)tail_items_capacity(p.n_hi), F, s->g,
+                                      push_const(s, p), q, s->d_err, s->st);
             launch_photon_resolve(q, P, s->d_err, s->st);
         } else {
             launch_push_photon_f32(P, F, s->g, push_const(s, p), q, s->d_err, s->st,
@@ -689,6 +692,10 @@ int pic_create(const pic_grid *grid, double dt, const pic_species *species, int 
             rc = rc ? rc : dalloc(s, (void **)&p.item_cnt, (size_t)(g.ntiles + 1) * sizeof(uint32_t));
             rc = rc ? rc : dalloc(s, (void **)&p.item_scan, scan_scratch_words(g.ntiles + 1) * sizeof(uint32_t));
             if (g.dim == 3) rc = rc ? rc : dalloc(s, (void **)&p.defer, (size_t)(p.cap + 1) * sizeof(uint32_t));
+            if (photon && g.dim == 2) {
+                rc = rc ? rc : dalloc(s, (void **)&p.tail_items, tail_items_capacity(p.cap) * sizeof(TileItem));
+                rc = rc ? rc : dalloc(s, (void **)&p.tail_nitems, sizeof(uint32_t));
+            }
         }
         for (int b = 0; b < 2 && !rc; b++) {
             rc = dalloc(s, (void **)&p.cell[b], (size_t)p.cap * 4);

@@ -833,6 +833,53 @@ void launch_push_photon_tile2d(const PartF32 &P, const TileItem *items, const ui
     }
 }
 
+// Work items over the photons appended since the last sort, [first, *dn):
+// chunks of kChunk consecutive photons.  The spawn appends children in their
+// parents' order, which is the parents' tile order, so a chunk's photons
+// mostly share a tile: the item takes the tile of its middle photon (tile 0
+// if that one is dead), and photons outside the item's field box take the
+// kernel's global gather.  The slots past the count, to n (the scan's end
+// slot), get a zero event flag.
+__global__ void k_tail_items(const uint32_t *__restrict__ cell, const long long *__restrict__ dn,
+                             const uint32_t *__restrict__ first, long long n, Grid g, TileItem *items,
+                             uint32_t *nitems, uint32_t *ev)
+{
+    const long long f = *first, cnt = *dn;
+    const long long ni = cnt > f ? (cnt - f + kChunk - 1) / kChunk : 0;
+    const long long t0 = (long long)blockIdx.x * blockDim.x + threadIdx.x, nt = (long long)gridDim.x * blockDim.x;
+    if (t0 == 0) *nitems = (uint32_t)ni;
+    for (long long k = t0; k < ni; k += nt) {
+        TileItem m;
+        m.start = (int)(f + k * kChunk);
+        m.count = (int)min((long long)kChunk, cnt - m.start);
+        m.pad = 0;
+        const uint32_t c = cell[m.start + m.count / 2];
+        m.tile = 0;
+        if (c != kDead) {
+            int a, b, d;
+            unpack_cell(g, c, a, b, d);
+            m.tile = (int)tile_of(g, a, b, d);
+        }
+        items[k] = m;
+    }
+    for (long long p = (cnt > f ? cnt : f) + t0; p <= n; p += nt) ev[p] = 0;
+}
+
+size_t tail_items_capacity(long long cap) { return (size_t)((cap + kChunk - 1) / kChunk + 1); }
+
+void launch_tail_items(const PartF32 &P, const uint32_t *first, const Grid &g, TileItem *items, uint32_t *nitems,
+                       uint32_t *ev, cudaStream_t st)
+{
+    static int nsm = 0;
+    if (!nsm) {
+        int dev = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+    }
+    note_launch();
+    k_tail_items<<<nsm * 4, 256, 0, st>>>(P.cell, P.dn, first, P.n, g, items, nitems, ev);
+}
+
 void launch_photon_resolve(const QedParams &q, const PartF32 &P, int *err, cudaStream_t st)
 {
     if (!q.on || !q.net || !q.cq) return;

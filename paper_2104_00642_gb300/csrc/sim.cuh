@@ -34,6 +34,9 @@ struct SpeciesState {
     uint32_t *defer = nullptr;      // 3D: particles the tiled push leaves to the global path ([0] = count)
     long long items_cap = 0;
     bool items_valid = false;
+    // 2D photons: work items over the photons appended since the sort (rebuilt every step)
+    TileItem *tail_items = nullptr;
+    uint32_t *tail_nitems = nullptr;
     // QED: kind, optical depth and identity (double-buffered with the
     // particle arrays), event flags and data of the current step
     int kind = PIC_KIND_MASSIVE;
