@@ -157,20 +157,22 @@ __device__ __forceinline__ void qed_photon_f32(const QedParams &q, const unsigne
     const bool use_net = false;  // (the network acts through the thinned sampler below)
     float y0 = 0.f, y1 = 0.f;
     if constexpr (SURR) {
-        // Inside the network's range the pair process is sampled by
-        // thinning: the optical depth drains at the analytic envelope
-        // W_env >= W (pair_envelope_f32); where it runs out (a candidate)
-        // the network gives W and the positron fraction, the candidate
-        // converts with probability W / W_env (a draw of its own), and the
-        // depth restarts from -ln r after every candidate.  The events are
-        // those of the network's rate W, and the network -- 17 kflop per
-        // evaluation -- runs at candidates only, not for every photon and step.
+        // Up to the top of the network's range the pair process is sampled
+        // by thinning: the optical depth drains at the analytic envelope
+        // W_env >= W (pair_envelope_f32); where it runs out (a candidate) the
+        // candidate converts with probability W / W_env (a draw of its own)
+        // and the depth restarts from -ln r after every candidate.  W and the
+        // positron fraction come from the network inside its range, from the
+        // tables below it.  The events are those of the rate W, and the
+        // network -- 17 kflop per evaluation -- runs at candidates only, not
+        // for every photon and step.
         float lnchi;
         const bool inr = live && km > 0.f && mlp_in_range_f32(q.net_lo_f, q.net_hi_f, chi, lnchi);
+        const bool thin = live && km > 0.f && lnchi <= q.net_hi_f;
         double tau = tau_in;
         float genv = 0.f;
         bool cand = false, keep = false;
-        if (inr) {
+        if (thin) {
             genv = pair_envelope_f32(chi);
             const float dtau = q.pref_f * genv / km;
             // a decrement that is zero in FP32 (the envelope underflows below
@@ -181,33 +183,36 @@ __device__ __forceinline__ void qed_photon_f32(const QedParams &q, const unsigne
                 cand = tau <= 0.0;
             }
         }
-        if (__any_sync(0xffffffffu, cand)) {
+        if (cand) {
+            const uint64_t id = q.id[p];
+            philox4x32_10((uint32_t)id, (uint32_t)(id >> 32), q.step, QP_PAIR, q.key[0], q.key[1], w);
+        }
+        if (__any_sync(0xffffffffu, cand && inr)) {
             float x0 = 0.f, x1 = 0.f;
-            if (cand) {
-                const uint64_t id = q.id[p];
-                philox4x32_10((uint32_t)id, (uint32_t)(id >> 32), q.step, QP_PAIR, q.key[0], q.key[1], w);
-                mlp_inputs_f32(q.nrm, QED_PAIR, lnchi, uniform24_f32(w[0]), x0, x1);
-            }
-            mlp_eval_warp_sparse(*reinterpret_cast<const MlpImage *>(mlp_smem), cand, x0, x1, y0, y1);
+            if (cand && inr) mlp_inputs_f32(q.nrm, QED_PAIR, lnchi, uniform24_f32(w[0]), x0, x1);
+            mlp_eval_warp_sparse(*reinterpret_cast<const MlpImage *>(mlp_smem), cand && inr, x0, x1, y0, y1);
         }
         if (!live) return;
-        if (inr) {
+        if (thin) {
             if (cand) {
-                const float pa = mlp_rate_f32(q.nrm, QED_PAIR, chi, y1) / genv;
+                const float G = inr ? mlp_rate_f32(q.nrm, QED_PAIR, chi, y1) : qed_rate_f32(q.T, QED_PAIR, chi);
+                const float pa = G / genv;
                 if (pa > 1.0f) atomicOr(err, ERR_QEDDT);
                 const uint64_t id = q.id[p];
                 uint32_t v[4];
                 philox4x32_10((uint32_t)id, (uint32_t)(id >> 32), q.step, QP_THIN, q.key[0], q.key[1], v);
                 if (uniform24_f32(v[0]) < pa) {
+                    const float r0 = uniform24_f32(w[0]);
                     event = 1;
-                    evd = make_float4(kx, ky, kz, mlp_fraction_f32(QED_PAIR, y0, uniform24_f32(w[0])));
+                    evd = make_float4(kx, ky, kz,
+                                      inr ? mlp_fraction_f32(QED_PAIR, y0, r0) : qed_sample_f32(q.T, QED_PAIR, chi, r0));
                 }
                 tau = (double)neg_log_uniform24_f32(w[1]);
             }
             if (!keep) q.tau[p] = tau;
             return;
         }
-        // outside the network's range: the tables, Method I, below
+        // above the network's range: the tables, Method I, below
     }
     if (!live) return;  // as in qed_lepton_f32
     if (!SURR && q.method == 2) {

@@ -441,7 +441,8 @@ __global__ void __launch_bounds__(kTileThreads, QM == 2 ? 3 : kTileMinBlocks)
 // The surrogate's candidate conversions (the thinned sampler of
 // qed_photon_f32): the tiled photon push appends them to a queue, one slot
 // per photon, and this kernel resolves them, 32 per network evaluation:
-// the pair rate W and the positron fraction from one evaluation, a
+// the pair rate W and the positron fraction from one evaluation (from the
+// tables for candidates below the network's chi range), a
 // conversion with probability W / W_env (the candidate's draw of purpose
 // QP_THIN), and the optical depth restarted from -ln r.  The network's
 // registers stay out of the push, which then runs at the table push's
@@ -460,26 +461,32 @@ __global__ void __launch_bounds__(256) k_photon_resolve(QedParams q, PartF32 P, 
         const bool mine = i < n;
         const float4 e = mine ? q.cq[i] : make_float4(0.f, 0.f, 1.f, 1.f);
         const long long p = (long long)(uint32_t)__float_as_int(e.x);
+        const bool row = mine && e.y >= q.net_lo_f;  // inside the network's range (else the tables)
         uint32_t w[4] = {0u, 0u, 0u, 0u};
         float x0 = 0.f, x1 = 0.f, y0 = 0.f, y1 = 0.f;
         uint64_t id = 0;
         if (mine) {
             id = q.id[p];
             philox4x32_10((uint32_t)id, (uint32_t)(id >> 32), q.step, QP_PAIR, q.key[0], q.key[1], w);
-            mlp_inputs_f32(q.nrm, QED_PAIR, e.y, uniform24_f32(w[0]), x0, x1);
+            if (row) mlp_inputs_f32(q.nrm, QED_PAIR, e.y, uniform24_f32(w[0]), x0, x1);
         }
-        mlp_eval_warp_sparse(*reinterpret_cast<const MlpImage *>(net), mine, x0, x1, y0, y1);
+        if (__any_sync(0xffffffffu, row))
+            mlp_eval_warp_sparse(*reinterpret_cast<const MlpImage *>(net), row, x0, x1, y0, y1);
         if (!mine) continue;
-        const float pa = mlp_rate_f32(q.nrm, QED_PAIR, e.w, y1) / e.z;
+        const float G = row ? mlp_rate_f32(q.nrm, QED_PAIR, e.w, y1) : qed_rate_f32(q.T, QED_PAIR, e.w);
+        const float pa = G / e.z;
         if (pa > 1.0f) atomicOr(err, ERR_QEDDT);
         uint32_t v[4];
         philox4x32_10((uint32_t)id, (uint32_t)(id >> 32), q.step, QP_THIN, q.key[0], q.key[1], v);
         const bool accept = uniform24_f32(v[0]) < pa;
         q.tau[p] = (double)neg_log_uniform24_f32(w[1]);
         q.ev[p] = accept ? 1u : 0u;
-        if (accept)
-            reinterpret_cast<float4 *>(q.evk)[p] =
-                make_float4(P.u[0][p], P.u[1][p], P.u[2][p], mlp_fraction_f32(QED_PAIR, y0, uniform24_f32(w[0])));
+        if (accept) {
+            const float r0 = uniform24_f32(w[0]);
+            reinterpret_cast<float4 *>(q.evk)[p] = make_float4(
+                P.u[0][p], P.u[1][p], P.u[2][p],
+                row ? mlp_fraction_f32(QED_PAIR, y0, r0) : qed_sample_f32(q.T, QED_PAIR, e.w, r0));
+        }
     }
 }
 
@@ -606,7 +613,8 @@ __global__ void __launch_bounds__(kTileThreads, kTileMinBlocks)
                     // k_photon_resolve evaluates 32 at a time
                     const float chi = chi_f32(km, kx, ky, kz, eb[0], eb[1], eb[2], eb[3], eb[4], eb[5], q.inv_Es_f);
                     float lnchi;
-                    if (km > 0.f && mlp_in_range_f32(q.net_lo_f, q.net_hi_f, chi, lnchi)) {
+                    mlp_in_range_f32(q.net_lo_f, q.net_hi_f, chi, lnchi);
+                    if (km > 0.f && lnchi <= q.net_hi_f) {  // thinned up to the top of the network's range
                         const float genv = pair_envelope_f32(chi);
                         const float dtau = q.pref_f * genv / km;
                         if (dtau == 0.f && tau0 > 0.0) {

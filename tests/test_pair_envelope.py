@@ -1,8 +1,10 @@
 """The analytic envelope of the pair rate that the surrogate form's thinned
 pair sampler drains the optical depth with (csrc/qed.cuh, pair_envelope_f32:
-c chi^(2/3) exp(-8/(3 chi)) over the network's chi range [0.1, 100]) lies
-above the rate of Eq. (24) -- the oracle's quadrature -- with a margin larger
-than the network's rate error (a few per cent), so that the acceptance
+c chi^(2/3) exp(-8/(3 chi)), up to the top of the network's chi range,
+chi = 100; below chi ~ 0.03 it underflows in FP32) lies above the rate of
+Eq. (24) -- the oracle's quadrature -- with a margin larger than the
+network's rate error (a few per cent) and the tables' (below the network's
+range the candidates take the tables' rate), so that the acceptance
 W / W_env of a candidate stays below one.  No GPU."""
 import math
 import os
@@ -25,7 +27,7 @@ def test_envelope_bounds_the_pair_rate_with_margin():
     c = _constant()
     L = O.lib()
     worst = np.inf
-    for chi in np.geomspace(0.1, 100.0, 241):
+    for chi in np.geomspace(0.03, 100.0, 281):
         g = L.or_qed_Gpair(chi)
         env = c * chi ** (2.0 / 3.0) * math.exp(-8.0 / (3.0 * chi))
         worst = min(worst, env / g)
