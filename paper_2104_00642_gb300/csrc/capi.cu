@@ -360,7 +360,7 @@ void push_species(pic_sim *s, int i, float *F)
             launch_push_photon_tile2d(P, p.items, p.nitems, max_items, F, s->g, push_const(s, p), q, s->d_err, s->st);
             // the photons appended since the sort: items of consecutive
             // photons (appended in their parents' tile order), on the same kernel
-            launch_tail_items(P, p.tile_start + s->g.ntiles, s->g, p.tail_items, p.tail_nitems, q.ev, s->st);
+            launch_tail_items(P, p.tile_start + s->g.ntiles, s->g, p.tail_items, p.tail_nitems, s->st);
             launch_push_photon_tile2d(P, p.tail_items, p.tail_nitems, (long long)tail_items_capacity(p.n_hi), F, s->g,
                                       push_const(s, p), q, s->d_err, s->st);
             launch_photon_resolve(q, P, s->d_err, s->st);
@@ -434,7 +434,7 @@ void qed_spawn_views(pic_sim *s)
     // the scanned sums of the flags' blocks (the spawn kernels rank within a block)
     auto scan = [&](const SpeciesState &p) {
         const long long nb = scan_blocks(p.n_hi + 1);
-        scan_block_sums(p.ev, p.n_hi + 1, off, off + nb + 64, s->st);
+        scan_block_sums(p.ev, p.n_hi + 1, off, off + nb + 64, s->st, p.d_count);
         return off + nb;  // total
     };
     if (ph >= 0 && el >= 0 && po >= 0 && s->sp[ph].n_hi > 0) {

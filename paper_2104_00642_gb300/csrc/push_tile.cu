@@ -846,11 +846,10 @@ void launch_push_photon_tile2d(const PartF32 &P, const TileItem *items, const ui
 // parents' order, which is the parents' tile order, so a chunk's photons
 // mostly share a tile: the item takes the tile of its middle photon (tile 0
 // if that one is dead), and photons outside the item's field box take the
-// kernel's global gather.  The slots past the count, to n (the scan's end
-// slot), get a zero event flag.
+// kernel's global gather.  (The slots past the count need no event flag:
+// the spawn reads flags up to the device count.)
 __global__ void k_tail_items(const uint32_t *__restrict__ cell, const long long *__restrict__ dn,
-                             const uint32_t *__restrict__ first, long long n, Grid g, TileItem *items,
-                             uint32_t *nitems, uint32_t *ev)
+                             const uint32_t *__restrict__ first, Grid g, TileItem *items, uint32_t *nitems)
 {
     const long long f = *first, cnt = *dn;
     const long long ni = cnt > f ? (cnt - f + kChunk - 1) / kChunk : 0;
@@ -870,13 +869,12 @@ __global__ void k_tail_items(const uint32_t *__restrict__ cell, const long long 
         }
         items[k] = m;
     }
-    for (long long p = (cnt > f ? cnt : f) + t0; p <= n; p += nt) ev[p] = 0;
 }
 
 size_t tail_items_capacity(long long cap) { return (size_t)((cap + kChunk - 1) / kChunk + 1); }
 
 void launch_tail_items(const PartF32 &P, const uint32_t *first, const Grid &g, TileItem *items, uint32_t *nitems,
-                       uint32_t *ev, cudaStream_t st)
+                       cudaStream_t st)
 {
     static int nsm = 0;
     if (!nsm) {
@@ -885,7 +883,7 @@ void launch_tail_items(const PartF32 &P, const uint32_t *first, const Grid &g, T
         cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
     }
     note_launch();
-    k_tail_items<<<nsm * 4, 256, 0, st>>>(P.cell, P.dn, first, P.n, g, items, nitems, ev);
+    k_tail_items<<<nsm * 4, 256, 0, st>>>(P.cell, P.dn, first, g, items, nitems);
 }
 
 void launch_photon_resolve(const QedParams &q, const PartF32 &P, int *err, cudaStream_t st)

@@ -37,10 +37,10 @@ void launch_push_photon_tile2d(const PartF32 &P, const TileItem *items, const ui
                                const float *F, const Grid &g, const PushConst &pc, const QedParams &q, int *err,
                                cudaStream_t st);
 // 2D photons: work items over the photons appended since the sort ([*first,
-// *P.dn), kChunk each), zero event flags from there to P.n
+// *P.dn), kChunk each)
 size_t tail_items_capacity(long long cap);
 void launch_tail_items(const PartF32 &P, const uint32_t *first, const Grid &g, TileItem *items, uint32_t *nitems,
-                       uint32_t *ev, cudaStream_t st);
+                       cudaStream_t st);
 // the surrogate's candidate conversions queued by the tiled photon push (q.cq)
 void launch_photon_resolve(const QedParams &q, const PartF32 &P, int *err, cudaStream_t st);
 // 3D: tiles of 4^3 cells, every n_d a multiple of 4

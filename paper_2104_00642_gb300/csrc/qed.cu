@@ -323,7 +323,8 @@ inline int spawn_grid(long long m)
 
 // the flags (0 or 1) of block b, kSpawnPer per thread from p0, as a bit mask,
 // and the rank of this thread's first event; false (block-uniform) when the
-// block has no event
+// block has no event.  m: the flags' end (the parents' device count: the
+// slots past it count as no event, as in the block sums)
 __device__ __forceinline__ bool spawn_ranks(const uint32_t *__restrict__ ev, long long m,
                                             const uint32_t *__restrict__ bsum, long long b, long long &p0,
                                             uint32_t &bits, uint32_t &run)
@@ -355,6 +356,7 @@ __global__ void __launch_bounds__(kSpawnThreads) k_spawn_photons_f32(PartF32 par
 {
     const long long base = *ph_count;
     if (blockIdx.x == 0 && threadIdx.x == 0 && base + *total > ph_cap) atomicOr(err, ERR_CAPACITY);
+    m = min(m, *parent.dn);  // (past the parents' device count: no event)
     const long long nb = (m + kScanItems - 1) / kScanItems;
     for (long long b = blockIdx.x; b < nb; b += gridDim.x) {
         long long p0;
@@ -391,6 +393,7 @@ __global__ void __launch_bounds__(kSpawnThreads) k_spawn_pairs_f32(PartF32 phot,
     const long long be = *el_count, bp = *po_count;
     if (blockIdx.x == 0 && threadIdx.x == 0 && (be + *total > el_cap || bp + *total > po_cap))
         atomicOr(err, ERR_CAPACITY);
+    m = min(m, *phot.dn);  // (past the photons' device count: no event)
     const long long nb = (m + kScanItems - 1) / kScanItems;
     for (long long b = blockIdx.x; b < nb; b += gridDim.x) {
         long long p0;
@@ -446,6 +449,7 @@ __global__ void __launch_bounds__(kSpawnThreads) k_spawn_photons_f64(PartF64 par
 {
     const long long base = *ph_count;
     if (blockIdx.x == 0 && threadIdx.x == 0 && base + *total > ph_cap) atomicOr(err, ERR_CAPACITY);
+    m = min(m, *parent.dn);  // (past the parents' device count: no event)
     const long long nb = (m + kScanItems - 1) / kScanItems;
     for (long long b = blockIdx.x; b < nb; b += gridDim.x) {
         long long p0;
@@ -483,6 +487,7 @@ __global__ void __launch_bounds__(kSpawnThreads) k_spawn_pairs_f64(PartF64 phot,
     const long long be = *el_count, bp = *po_count;
     if (blockIdx.x == 0 && threadIdx.x == 0 && (be + *total > el_cap || bp + *total > po_cap))
         atomicOr(err, ERR_CAPACITY);
+    m = min(m, *phot.dn);  // (past the photons' device count: no event)
     const long long nb = (m + kScanItems - 1) / kScanItems;
     for (long long b = blockIdx.x; b < nb; b += gridDim.x) {
         long long p0;

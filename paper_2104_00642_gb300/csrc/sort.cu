@@ -106,9 +106,10 @@ __global__ void __launch_bounds__(kSortThreads) k_radix_scatter(const uint32_t *
 // device-wide exclusive scan of u32 (reduce, scan of block sums, downsweep)
 // ---------------------------------------------------------------------
 __global__ void __launch_bounds__(1024) k_scan_reduce(const uint32_t *__restrict__ in, long long m, uint32_t *sums,
-                                                     bool zero_end = false)
+                                                     bool zero_end = false, const long long *__restrict__ dn = nullptr)
 {
     if (zero_end && blockIdx.x == 0 && threadIdx.x == 0) sums[gridDim.x] = 0u;  // the slot that scans to the total
+    if (dn && *dn < m) m = *dn < 0 ? 0 : *dn;  // words past the device count read as zero
     __shared__ uint32_t sh[32];
     long long b0 = (long long)blockIdx.x * kScanItems + threadIdx.x * 4;
     uint32_t s = 0;
@@ -152,13 +153,15 @@ size_t scan_scratch_words(long long m)
 
 // the exclusive scan of the sums of in's blocks of kScanItems words:
 // bsum[b] = sum of in[0, b kScanItems), bsum[nb] = the total (nb + 1 words,
-// scratch past them as for scan_exclusive)
-void scan_block_sums(const uint32_t *in, long long m, uint32_t *bsum, uint32_t *scratch, cudaStream_t st)
+// scratch past them as for scan_exclusive); dn (device, optional): the
+// words from *dn on count as zero
+void scan_block_sums(const uint32_t *in, long long m, uint32_t *bsum, uint32_t *scratch, cudaStream_t st,
+                     const long long *dn)
 {
     if (m <= 0) return;
     const long long nb = (m + kScanItems - 1) / kScanItems;
     note_launch();
-    k_scan_reduce<<<(int)nb, 1024, 0, st>>>(in, m, bsum, true);
+    k_scan_reduce<<<(int)nb, 1024, 0, st>>>(in, m, bsum, true, dn);
     scan_exclusive(bsum, bsum, nb + 1, scratch, st);
 }
 
