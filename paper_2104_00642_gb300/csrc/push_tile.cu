@@ -497,9 +497,10 @@ __global__ void __launch_bounds__(256) k_photon_resolve(QedParams q, PartF32 P, 
 // coalesced and the gathers of photons of one cell are shared-memory
 // broadcasts.  Each photon moves at c along k, its pair Monte Carlo is
 // qed_photon_f32 (as in the one-thread-per-particle photon push), event
-// flags are written for every photon of the items; photons appended since
-// the sort are left to that kernel.  SURR: the pair network inside its chi
-// range (its image after the field box).
+// flags are written for every photon of the items.  It runs over the sort's
+// work items and over those of the photons appended since (k_tail_items).
+// SURR: the thinned sampler up to the top of the network's chi range, its
+// candidates appended to the queue that k_photon_resolve evaluates.
 // ---------------------------------------------------------------------
 template <int T, bool SURR>
 __global__ void __launch_bounds__(kTileThreads, kTileMinBlocks)
