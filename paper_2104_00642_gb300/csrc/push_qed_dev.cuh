@@ -177,7 +177,7 @@ __device__ __forceinline__ void qed_photon_f32(const QedParams &q, const unsigne
             const float dtau = q.pref_f * genv / km;
             // a decrement that is zero in FP32 (the envelope underflows below
             // chi ~ 0.03) leaves the depth as it is: nothing to update or store
-            keep = dtau == 0.f && tau_in > 0.0;
+            keep = dtau == 0.f && depth_positive(tau_in);
             if (!keep) {
                 tau = tau_in - (double)dtau;
                 cand = tau <= 0.0;
@@ -231,7 +231,7 @@ __device__ __forceinline__ void qed_photon_f32(const QedParams &q, const unsigne
     } else {
         const float G = use_net ? mlp_rate_f32(q.nrm, QED_PAIR, chi, y1) : qed_rate_f32(q.T, QED_PAIR, chi);
         const float dtau = km > 0.f ? q.pref_f * G / km : 0.f;
-        if (dtau == 0.f && tau_in > 0.0) return;  // a zero rate in FP32 (chi below ~0.03): the depth stays, unstored
+        if (dtau == 0.f && depth_positive(tau_in)) return;  // a zero rate in FP32 (chi below ~0.03): the depth stays, unstored
         double tau = tau_in - (double)dtau;
         if (tau <= 0.0) {
             if (!use_net) {

@@ -598,6 +598,7 @@ __global__ void __launch_bounds__(kTileThreads, kTileMinBlocks)
             bool cand = false;  // SURR: a candidate conversion, resolved by k_photon_resolve
             float4 centry = make_float4(0.f, 0.f, 0.f, 0.f);
             double tau = tau0;
+            bool put_tau = false;  // SURR: store tau (thinned, not a candidate)
             if (q.on && live) {
                 float eb[6];
                 int icn[2], ich[2];
@@ -618,20 +619,17 @@ __global__ void __launch_bounds__(kTileThreads, kTileMinBlocks)
                     if (km > 0.f && lnchi <= q.net_hi_f) {  // thinned up to the top of the network's range
                         const float genv = pair_envelope_f32(chi);
                         const float dtau = q.pref_f * genv / km;
-                        if (dtau == 0.f && tau0 > 0.0) {
-                            tau = -1.0;  // a zero decrement in FP32: the depth stays, unstored
-                        } else {
+                        if (!(dtau == 0.f && depth_positive(tau0))) {  // (else the depth stays, unstored)
                             tau = tau0 - (double)dtau;
                             cand = tau <= 0.0;
+                            put_tau = !cand;
                             centry = make_float4(__int_as_float((int)p), lnchi, genv, chi);
                         }
                     } else {
                         qed_photon_f32<false>(q, nullptr, true, p, km, kx, ky, kz, eb, tau0, err, event, evd);
-                        tau = -1.0;  // written by qed_photon_f32
                     }
                 } else {
                     qed_photon_f32<false>(q, nullptr, true, p, km, kx, ky, kz, eb, tau0, err, event, evd);
-                    tau = -1.0;
                 }
             }
             bool dead = false;
@@ -672,7 +670,7 @@ __global__ void __launch_bounds__(kTileThreads, kTileMinBlocks)
                 continue;
             }
             if (cand) continue;  // tau, flag and event data by k_photon_resolve
-            if (SURR && q.on && tau >= 0.0) q.tau[p] = tau;  // (in range, no candidate)
+            if (SURR && put_tau) q.tau[p] = tau;  // (thinned, no candidate; qed_photon_f32 stores its own)
             q.ev[p] = event;
             if (event) reinterpret_cast<float4 *>(q.evk)[p] = evd;
         }
