@@ -551,9 +551,17 @@ def run_qed(args, w, pic, torch, stream, timed, rank, world, dist, local, l2_not
     achieved = alg / per_launch_s / 1e9
     kind = "photon push (pair rate" if w.species[i_dom].kind == 1 else "lepton push (gather, push, emission rate"
     kind += ", Monte Carlo" + (", surrogate network)" if modes[0] == "surrogate" else ", tables)")
+    # DRAM bytes per particle of the dominant push from the committed ncu
+    # summary (taken on a smaller beam, on the current kernel source), scaled
+    # by the particles of one launch here
+    trec = traffic_record(w.name)
+    traffic = None
+    if (trec and trec.get("form") == modes[0] and trec.get("species_kind") == w.species[i_dom].kind
+            and "bytes_per_particle" in trec):
+        traffic = trec["bytes_per_particle"] * s0["alive_mid"][i_dom]
     roof = {"bound": "hbm", "kernel": f"{kind}, species {w.species[i_dom].name}", "achieved": achieved,
             "peak": peak, "unit": "GB/s", "frac": achieved / peak, "peak_kind": f"{peak_kind} hbm_gbs",
-            "traffic": None, "algorithmic_bytes_per_launch": alg, "avg_launch_ms": per_launch_s * 1e3,
+            "traffic": traffic, "algorithmic_bytes_per_launch": alg, "avg_launch_ms": per_launch_s * 1e3,
             "bytes_per_particle": bpp, "particles_per_launch": s0["alive_mid"][i_dom],
             "share_of_step": s0["species_ms"][i_dom] / max(1e-30, float(sum(s0["prof"]["ms"].values())))}
     if modes[0] == "surrogate" and w.species[i_dom].kind == 1:
