@@ -59,7 +59,9 @@ enum { EX = 0, EY, EZ, BX, BY, BZ, JX, JY, JZ, NF };
  * solver updates the slab's own nodes [0, N) only, deposits may land in the
  * ghosts (the caller sums them into the neighbours), and a particle whose
  * position leaves [0, L) is moved to its species' outbox (the caller hands
- * it to the neighbour) instead of being wrapped or absorbed. */
+ * it to the neighbour) instead of being wrapped or absorbed.  Its QED event
+ * of that step still happens; children born outside the slab go to their
+ * species' outbox. */
 enum { BC_PERIODIC = 0, BC_ABSORB = 1, BC_SLAB = 2 };
 #define SLAB_G 4
 
@@ -998,6 +1000,9 @@ static void push_species(osim *s, osp *p)
             s->e_absorbed += p->w * p->m * (uu / (g + 1.0)) * dV;
             p->alive[a] = 0;
         } else if (leaves) {
+            /* (its photon is born at x^{n+1} outside the slab: spawn sends it
+             * to the outbox too) */
+            if (emitted) record(s, isp, a, kph, 0.0);
             to_outbox(p, a);
         } else if (emitted) {
             record(s, isp, a, kph, 0.0);  /* an emitter absorbed in the same step leaves no photon */
@@ -1060,8 +1065,8 @@ static void push_photons(osim *s, osp *p)
         }
         for (int d = 0; d < s->dim; d++) x[d] = x1[d];
         if (dead) p->alive[a] = 0;
+        else if (conv) record(s, isp, a, k, frac);  /* (leaving the slab or not: its pair goes where it is) */
         else if (leaves) to_outbox(p, a);
-        else if (conv) record(s, isp, a, k, frac);
     }
 }
 
@@ -1074,6 +1079,13 @@ static void append(osim *s, int isp, const double *x, const double *u, uint64_t 
     p->alive[b] = 1;
     p->id[b] = id;
     p->tau[b] = initial_tau(s, id);
+    /* BC_SLAB: a child born outside the slab (its parent left in the step of
+     * its event) goes to the outbox with it */
+    for (int d = 0; d < s->dim; d++)
+        if (s->bc[d] == BC_SLAB && (x[d] < 0.0 || x[d] >= (double)s->n[d] * s->dx[d])) {
+            to_outbox(p, b);
+            break;
+        }
 }
 
 /* children of this step's events: first the pairs of converted photons

@@ -81,28 +81,72 @@ def _state(o, nsp, x_off):
     return out
 
 
-def _rank_main(rank, world, port, result_path):
+# the QED case: ultra-relativistic electrons gyrating in a uniform B_z
+# (chi ~ 5 at gamma 2000, gyro-radius about 20 cells), emitting photons that
+# convert to pairs (Sec. IV, Method I); tiny weights, so the fields stay the
+# applied B_z up to round-off.  Emitters, photons and pairs cross slab faces,
+# also in the step of their events.
+QED_SEED = 0x5EED0F4
+QED_B0, QED_GAMMA, QED_N, QED_W, QED_STEPS = 1000.0, 2000.0, 24, 1e-12, 30
+
+
+def _setup_qed():
+    rng = np.random.default_rng(2105)
+    dt = 0.9 / np.sqrt(1 / DX[0] ** 2 + 1 / DX[1] ** 2)
+    L = (N[0] * DX[0], N[1] * DX[1])
+    x = rng.uniform(0.0, L[0], QED_N)
+    y = rng.uniform(0.0, L[1], QED_N)
+    phi = rng.uniform(0.0, 2 * np.pi, QED_N)
+    um = np.sqrt(QED_GAMMA ** 2 - 1.0)
+    u = np.stack([um * np.cos(phi), um * np.sin(phi), np.zeros(QED_N)], axis=1)
+    tau = rng.exponential(size=QED_N)
+    F = [np.zeros((N[1], N[0])) for _ in range(6)]
+    F[5][:] = QED_B0
+    # (q, m, w, kind, qed, x, y, u, tau): electrons, positrons, photons
+    empty = (np.zeros(0), np.zeros(0), np.zeros((0, 3)), np.zeros(0))
+    species = [(-1.0, 1.0, QED_W, 0, 1, x, y, u, tau), (1.0, 1.0, QED_W, 0, 1) + empty,
+               (0.0, 0.0, QED_W, 1, 0) + empty]
+    return dt, species, F
+
+
+def _build(O, shape, bc, dt, species, cap, sel_fn, x_off):
+    o = O.OracleSim(2, shape, DX, dt, bc=bc)
+    for isp, sp in enumerate(species):
+        q, m, w = sp[:3]
+        if len(sp) == 5:  # (q, m, x, y, u): the plasma case
+            kind, qed, x, y, u = 0, 0, sp[2], sp[3], sp[4]
+            w = 0.01
+            tau = np.zeros(len(x))
+        else:
+            kind, qed, x, y, u, tau = sp[3], sp[4], sp[5], sp[6], sp[7], sp[8]
+        o.add_species(q, m, w, cap, kind=kind, qed=qed)
+        ids = np.arange(len(x), dtype=np.uint64) + np.uint64(isp << 40)
+        sel = sel_fn(x)
+        xyz = np.stack([x[sel] - x_off, y[sel], np.zeros(sel.sum())], axis=1)
+        o.load_state(isp, xyz, u[sel], ids[sel], tau[sel])
+    if len(species[0]) > 5:
+        o.set_qed(photon_sp=2, electron_sp=0, positron_sp=1, lambda_r_m=1e-6, photon_emin=0.0, seed=QED_SEED)
+    return o
+
+
+def _rank_main(rank, world, port, result_path, case="plasma"):
     import torch.distributed as dist
     from oracle import oracle as O
     os.environ["MASTER_ADDR"] = "127.0.0.1"
     os.environ["MASTER_PORT"] = str(port)
     dist.init_process_group("gloo", rank=rank, world_size=world)
     try:
-        dt, species, F = _setup()
+        dt, species, F = _setup() if case == "plasma" else _setup_qed()
         dec = D.SlabDecomposition(N[0], DX[0], ghost=G, dist=dist)
-        o = O.OracleSim(2, (dec.n, N[1]), DX, dt, bc=(O.SLAB, O.PERIODIC))
-        cap = 4 * N[0] * N[1] * NPPC
-        for isp, (q, m, x, y, u) in enumerate(species):
-            o.add_species(q, m, 0.01, cap)
-            ids = np.arange(len(x), dtype=np.uint64) + np.uint64(isp << 40)
-            sel = (x >= dec.x0 * DX[0]) & (x < dec.x1 * DX[0])
-            xyz = np.stack([x[sel] - dec.x0 * DX[0], y[sel], np.zeros(sel.sum())], axis=1)
-            o.load_state(isp, xyz, u[sel], ids[sel], np.zeros(sel.sum()))
+        cap = 4 * N[0] * N[1] * NPPC if case == "plasma" else 200_000  # (slots of migrated particles stay)
+        o = _build(O, (dec.n, N[1]), (O.SLAB, O.PERIODIC), dt, species, cap,
+                   lambda x: (x >= dec.x0 * DX[0]) & (x < dec.x1 * DX[0]), dec.x0 * DX[0])
         eng = OracleSlab(o)
         for c in range(6):
             o.set_field(c, F[c][:, dec.x0:dec.x1][None])
         dec.start(eng)
-        for _ in range(STEPS):
+        steps = STEPS if case == "plasma" else QED_STEPS
+        for _ in range(steps):
             dec.step(eng, len(species))
         # everything to rank 0
         mine = {"fields": [o.field(c)[0] for c in range(9)], "parts": _state(o, len(species), dec.x0 * DX[0]),
@@ -110,15 +154,11 @@ def _rank_main(rank, world, port, result_path):
         got = [None] * world
         dist.all_gather_object(got, mine)
         if rank == 0:
-            ref = O.OracleSim(2, N, DX, dt)
-            for isp, (q, m, x, y, u) in enumerate(species):
-                ref.add_species(q, m, 0.01, cap)
-                ids = np.arange(len(x), dtype=np.uint64) + np.uint64(isp << 40)
-                ref.load_state(isp, np.stack([x, y, np.zeros(len(x))], axis=1), u, ids, np.zeros(len(x)))
+            ref = _build(O, N, (O.PERIODIC, O.PERIODIC), dt, species, cap, lambda x: np.ones(len(x), bool), 0.0)
             for c in range(6):
                 ref.set_field(c, F[c][None])
-            ref.step(STEPS)
-            worst_f, worst_x, worst_u, moved = 0.0, 0.0, 0.0, 0
+            ref.step(steps)
+            worst_f, worst_x, worst_u, moved, counts = 0.0, 0.0, 0.0, 0, []
             for c in range(9):
                 whole = np.concatenate([g["fields"][c] for g in sorted(got, key=lambda t: t["x0"])], axis=1)
                 r = ref.field(c)[0]
@@ -136,14 +176,18 @@ def _rank_main(rank, world, port, result_path):
                 worst_x = max(worst_x, float(np.max(np.abs(dxp))))
                 worst_u = max(worst_u, float(np.max(np.abs(u - rs[isp]["u"][rorder]))))
                 # particles that ended on another rank than they started on
-                x_start = species[isp][2][(ids[order] - np.uint64(isp << 40)).astype(np.int64)]
-                r_start = np.searchsorted([g["x0"] * DX[0] for g in sorted(got, key=lambda t: t["x0"])][1:],
-                                          x_start, side="right")
-                r_end = np.searchsorted([g["x0"] * DX[0] for g in sorted(got, key=lambda t: t["x0"])][1:],
-                                        x % Lx, side="right")
-                moved += int(np.sum(r_start != r_end))
+                # (the plasma case) / particles of each species (the QED case)
+                if case == "plasma":
+                    x_start = species[isp][2][(ids[order] - np.uint64(isp << 40)).astype(np.int64)]
+                    r_start = np.searchsorted([g["x0"] * DX[0] for g in sorted(got, key=lambda t: t["x0"])][1:],
+                                              x_start, side="right")
+                    r_end = np.searchsorted([g["x0"] * DX[0] for g in sorted(got, key=lambda t: t["x0"])][1:],
+                                            x % Lx, side="right")
+                    moved += int(np.sum(r_start != r_end))
+                else:
+                    counts.append(len(ids))
             with open(result_path, "w") as f:
-                f.write(f"{worst_f} {worst_x} {worst_u} {moved}\n")
+                f.write(f"{worst_f} {worst_x} {worst_u} {moved} {' '.join(str(c) for c in counts)}\n")
     finally:
         dist.destroy_process_group()
 
@@ -168,6 +212,22 @@ def test_slab_decomposition_matches_the_whole_grid(world, tmp_path):
     assert float(wf) < 1e-12 and float(wx) < 1e-12 and float(wu) < 1e-12
     if world > 1:
         assert int(moved) > 50
+
+
+@pytest.mark.parametrize("world", [3])
+def test_slab_decomposition_with_qed_matches_the_whole_grid(world, tmp_path):
+    """the QED case: the same electrons, photons and pairs (matched by
+    identity: children's identities come from their parents' Philox
+    streams) with the same positions and momenta to round-off, after 30
+    steps with events in slabs, at slab faces and in the step of a crossing"""
+    import torch.multiprocessing as mp
+    out = tmp_path / "result.txt"
+    mp.spawn(_rank_main, args=(world, _free_port(), str(out), "qed"), nprocs=world, join=True)
+    wf, wx, wu, _, *counts = open(out).read().split()
+    counts = [int(c) for c in counts]
+    print(world, wf, wx, wu, counts)
+    assert float(wf) < 1e-12 and float(wx) < 1e-12 and float(wu) < 1e-9
+    assert counts[2] > 100 and counts[1] > 3  # photons and pairs were made
 
 
 def test_slab_bounds_cover_the_grid():
