@@ -47,6 +47,22 @@ def test_radiated_power_larmor_limit(L):
         assert abs(p / (2.0 * math.pi / math.sqrt(3.0)) - (1.0 - 55.0 * math.sqrt(3.0) / 16.0 * chi)) < 60 * chi * chi
 
 
+def test_pair_rate_small_chi_limit(L):
+    """Int_0^1 Fpair dv of Eq. (24) -> (9 pi / (16 sqrt 2)) chi exp(-8 / (3 chi))
+    as chi -> 0: with the prefactor alpha E_s / (sqrt3 pi k) of the rate,
+    the known pair-creation limit W = (3 sqrt3 / (16 sqrt2)) alpha E_s chi
+    exp(-8/(3 chi)) / k of a photon in a weak field.  The ratio approaches 1
+    linearly in chi; its straight-line extrapolation to chi = 0 from three
+    small chi gives 1 within 2e-4 (a factor 2 or a wrong exponent fails by
+    orders of magnitude, a wrong power of chi by 10 %)"""
+    chis = np.array([0.01, 0.02, 0.04])
+    ratio = np.array([L.or_qed_Gpair(c) / (9.0 * math.pi / (16.0 * math.sqrt(2.0)) * c * math.exp(-8.0 / (3.0 * c)))
+                      for c in chis])
+    slope, intercept = np.polyfit(chis, ratio, 1)
+    assert abs(intercept - 1.0) < 2e-4, (intercept, slope)
+    assert np.all(np.abs(ratio - 1.0) < 0.25 * chis), ratio
+
+
 def test_pair_spectrum_symmetric_and_positive(L):
     for chi in (0.5, 5.0, 50.0):
         for v in (0.05, 0.2, 0.37, 0.49):
