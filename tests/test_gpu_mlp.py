@@ -229,7 +229,7 @@ def test_surrogate_rates_within_range(trained):
 @pytest.mark.parametrize("chi", [0.49, 4.9, 49.0])
 @pytest.mark.parametrize("process", [pic.QED_EMISSION, pic.QED_PAIR])
 def test_surrogate_spectrum_error(trained, chi, process):
-    """Fig. 8 setup with the network, the tables as the judge: 1e6 paired
+    """Fig. 8 setup with the network, the tables as the reference: 1e6 paired
     draws (the same r through both samplers) of the energy fraction at
     fixed chi.  Bounds: per-bin spectrum error (24 bins), error of the mean
     fraction (the radiated power, or the positron energy share).  Then the
