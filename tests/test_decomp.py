@@ -238,3 +238,33 @@ def test_slab_bounds_cover_the_grid():
         assert max(x1 - x0 for x0, x1 in b) - min(x1 - x0 for x0, x1 in b) <= 1
     with pytest.raises(ValueError):
         D.SlabDecomposition(3, 0.1, ghost=4)  # narrower than its ghost layers
+
+
+def _allreduce_main(rank, world, port, result_path):
+    import torch.distributed as dist
+    os.environ["MASTER_ADDR"] = "127.0.0.1"
+    os.environ["MASTER_PORT"] = str(port)
+    dist.init_process_group("gloo", rank=rank, world_size=world)
+    try:
+        dec = D.SlabDecomposition(N[0], DX[0], ghost=G, dist=dist)
+        # a diagnostic that each rank holds a part of: the energy of its own
+        # cells, here a value whose sum over ranks is known exactly
+        got = dec.allreduce_sum([float(dec.n), 0.1 * (rank + 1), 1e-300])
+        if rank == 0:
+            with open(result_path, "w") as f:
+                f.write(" ".join(repr(float(v)) for v in got) + "\n")
+    finally:
+        dist.destroy_process_group()
+
+
+def test_allreduce_sums_the_ranks_diagnostics(tmp_path):
+    """the global diagnostics of a decomposed run: FP64 sums over the ranks
+    (the cells of the slabs add up to the grid)"""
+    import torch.multiprocessing as mp
+    out = tmp_path / "sum.txt"
+    world = 3
+    mp.spawn(_allreduce_main, args=(world, _free_port(), str(out)), nprocs=world, join=True)
+    cells, tenths, tiny = (float(v) for v in open(out).read().split())
+    assert cells == N[0]
+    assert abs(tenths - 0.1 * (1 + 2 + 3)) < 1e-15
+    assert tiny == 3e-300
