@@ -396,10 +396,13 @@ def photon_spectrum(sim, sp, edges):
     return np.histogram(k, edges)[0]
 
 
-def qed_bytes_per_particle(dim):
+def qed_bytes_per_particle(dim, photon=False):
     """algorithmic HBM bytes of one particle in a QED push: the FP32 state
-    read and written once, the FP64 optical depth read and written, the
-    event flag written"""
+    read and written once (a photon's momentum is only read: it moves at c
+    along k), the FP64 optical depth read and written, the event flag
+    written"""
+    if photon:
+        return (4 + 4 * dim + 12) + (4 + 4 * dim) + 16 + 4
     return 2 * (4 + 4 * dim + 12) + 16 + 4
 
 
@@ -546,7 +549,7 @@ def run_qed(args, w, pic, torch, stream, timed, rank, world, dist, local, l2_not
     s0 = runs[modes[0]]
     i_dom = int(np.argmax(s0["species_ms"]))
     per_launch_s = s0["species_ms"][i_dom] / 1e3 / max(1, s0["species_pushes"][i_dom])
-    bpp = qed_bytes_per_particle(w.dim)
+    bpp = qed_bytes_per_particle(w.dim, photon=w.species[i_dom].kind == 1)
     alg = s0["alive_mid"][i_dom] * bpp
     achieved = alg / per_launch_s / 1e9
     kind = "photon push (pair rate" if w.species[i_dom].kind == 1 else "lepton push (gather, push, emission rate"
