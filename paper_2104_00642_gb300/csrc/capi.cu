@@ -353,8 +353,8 @@ void push_species(pic_sim *s, int i, float *F)
         const QedParams q = qed_params(s, i);
         const PartF32 P = view32(s, i, p.cur);
         if (use_tile_photon_push(s, p)) {
-            // the photons sorted into work items on the tiled kernel, those
-            // emitted since on the one-thread-per-particle kernel
+            // the photons sorted into work items on the tiled kernel, then
+            // those emitted since, as items of consecutive photons
             const long long max_items = (long long)tile_items_capacity(p.n_hi, s->g.ntiles, s->g.dim);
             if (q.on && q.net) cudaMemsetAsync(q.cq_n, 0, sizeof(uint32_t), s->st);  // the candidates' queue
             launch_push_photon_tile2d(P, p.items, p.nitems, max_items, F, s->g, push_const(s, p), q, s->d_err, s->st);
@@ -461,7 +461,7 @@ void qed_spawn_views(pic_sim *s)
                              P.d_count, P.cap, dim, s->d_err, s->st);
         P.n_hi = std::min(P.cap, P.n_hi + p.n_hi);
         // (the photons land past the sorted ones: the photon push takes them
-        // on its one-thread-per-particle kernel, the work items stay valid)
+        // as items of consecutive photons, the sort's work items stay valid)
     }
 }
 
@@ -865,8 +865,15 @@ int pic_set_qed(pic_sim *s, const pic_qed *Q)
         // photon (each queues at most once per step), 32-bit photon indices
         const long long cap = s->sp[Q->photon_sp].cap;
         if (cap >= (1ll << 31)) return fail(s, PIC_ERR_ARG, "pic_set_qed: surrogate photons need a capacity below 2^31");
-        if (!s->cand_q)
+        if (s->cand_q && s->cand_cap < cap) {  // (the QED photon species changed to a larger one)
+            s->allocs.erase(std::find(s->allocs.begin(), s->allocs.end(), (void *)s->cand_q));
+            raw_free(s, s->cand_q);
+            s->cand_q = nullptr;
+        }
+        if (!s->cand_q) {
             if (int rc = dalloc(s, (void **)&s->cand_q, (size_t)(cap + 32) * sizeof(float4))) return rc;
+            s->cand_cap = cap;
+        }
         if (!s->cand_n)
             if (int rc = dalloc(s, (void **)&s->cand_n, sizeof(uint32_t))) return rc;
     }

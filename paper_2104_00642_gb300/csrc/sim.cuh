@@ -61,6 +61,7 @@ struct pic_sim {
     bool qed_on = false;
     void *qed_tables = nullptr;
     float4 *cand_q = nullptr;    // the photons' candidate conversions (surrogate form), one slot per photon
+    long long cand_cap = 0;      // its slots
     uint32_t *cand_n = nullptr;
     pic::QedTables T{};
     double Es = 0.0;
